@@ -1,0 +1,267 @@
+"""FP64 CPU oracle of the PIC cycle with the pair-potential force (arXiv:1502.07722).
+
+TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU-baseline leg of the
+benchmark may import this package. The product library never imports it and shares no code
+with it; the C source (pic_oracle.c) holds the arithmetic, this module only marshals arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile pic_oracle.c into liboracle.so (plain gcc, contraction off)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OracleConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("nz", ctypes.c_int32), ("slab_k", ctypes.c_int32),
+        ("mode", ctypes.c_int32), ("ppc_ion", ctypes.c_int32), ("ppc_electron", ctypes.c_int32),
+        ("pot_mode", ctypes.c_int32), ("laser_profile", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("cfl", ctypes.c_double), ("dt_override", ctypes.c_double),
+        ("n_atoms", ctypes.c_double), ("T_ion_K", ctypes.c_double), ("T_electron_eV", ctypes.c_double),
+        ("ion_charge", ctypes.c_double), ("ion_mass_amu", ctypes.c_double),
+        ("D_eV", ctypes.c_double), ("r0", ctypes.c_double), ("c_att", ctypes.c_double),
+        ("s_rep", ctypes.c_double), ("lambda_", ctypes.c_double), ("I0", ctypes.c_double),
+        ("tau_fwhm", ctypes.c_double), ("w0", ctypes.c_double), ("t_peak", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_lib_handle = None
+
+
+def lib():
+    global _lib_handle
+    if _lib_handle is None:
+        L = ctypes.CDLL(build())
+        vp = ctypes.c_void_p
+        sig = {
+            "oracle_create": (vp, [ctypes.POINTER(OracleConfig), ctypes.c_int32]),
+            "oracle_free": (None, [vp]),
+            "oracle_num_particles": (ctypes.c_int64, [vp, ctypes.c_int32]),
+            "oracle_dt": (ctypes.c_double, [vp]),
+            "oracle_weight": (ctypes.c_double, [vp]),
+            "oracle_rho_scale": (ctypes.c_double, [vp]),
+            "oracle_step_count": (ctypes.c_int64, [vp]),
+            "oracle_get_particles": (None, [vp, ctypes.c_int32, _D, _D, _D, _D, _D]),
+            "oracle_set_particles": (None, [vp, ctypes.c_int32, ctypes.c_int64, _D, _D, _D, _D, _D]),
+            "oracle_get_field": (None, [vp, ctypes.c_int32, _D]),
+            "oracle_set_field": (None, [vp, ctypes.c_int32, _D]),
+            "oracle_get_rho": (None, [vp, _I64]),
+            "oracle_set_rho": (None, [vp, _I64]),
+            "oracle_get_current": (None, [vp, _I64]),
+            "oracle_set_current": (None, [vp, _I64]),
+            "oracle_set_step": (None, [vp, ctypes.c_int64]),
+            "oracle_pair_force": (None, [vp, _D]),
+            "oracle_gather_density": (None, [vp, ctypes.c_double, ctypes.c_double, _D]),
+            "oracle_step": (None, [vp, ctypes.c_int32]),
+            "oracle_energy": (None, [vp, _D]),
+            "oracle_laser_field": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double]),
+            "oracle_lj_U": (ctypes.c_double, [ctypes.c_double]),
+            "oracle_lj_dU": (ctypes.c_double, [ctypes.c_double]),
+            "oracle_neighbor_distances": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]),
+            "oracle_boris": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
+            "oracle_jy_code": (ctypes.c_int64, [ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+            "oracle_deposit_density": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D, _I64]),
+            "oracle_deposit_current": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                              _D, _D, _D, _D, _F, _F, _F, _I64, _I64, _I64]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib_handle = L
+    return _lib_handle
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+FIELD_NAMES = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+
+
+def make_config(phys: dict) -> OracleConfig:
+    """Fill the oracle's own configuration from a dict of physical inputs."""
+    c = OracleConfig()
+    for name, _ in OracleConfig._fields_:
+        key = "lambda" if name == "lambda_" else name
+        if key in phys:
+            setattr(c, name, phys[key])
+    return c
+
+
+class Oracle:
+    """One FP64 simulation state (2D3V). Positions are global cell coordinates."""
+
+    def __init__(self, phys: dict, with_particles: bool = True):
+        self.phys = dict(phys)
+        self.cfg = make_config(phys)
+        self._s = lib().oracle_create(ctypes.byref(self.cfg), 1 if with_particles else 0)
+        self.nx, self.nz = self.cfg.nx, self.cfg.nz
+        self.nspecies = 2 if self.cfg.mode == 0 else 1
+
+    def __del__(self):
+        if getattr(self, "_s", None):
+            lib().oracle_free(self._s)
+            self._s = None
+
+    # scalars
+    @property
+    def dt(self):
+        return lib().oracle_dt(self._s)
+
+    @property
+    def weight(self):
+        return lib().oracle_weight(self._s)
+
+    @property
+    def rho_scale(self):
+        return lib().oracle_rho_scale(self._s)
+
+    @property
+    def step_count(self):
+        return lib().oracle_step_count(self._s)
+
+    def set_step(self, n):
+        lib().oracle_set_step(self._s, int(n))
+
+    # particles
+    def num_particles(self, sp):
+        return lib().oracle_num_particles(self._s, sp)
+
+    def get_particles(self, sp):
+        n = self.num_particles(sp)
+        arrs = [np.empty(n, np.float64) for _ in range(5)]
+        lib().oracle_get_particles(self._s, sp, *[_p(a, ctypes.c_double) for a in arrs])
+        return dict(zip(("x", "z", "ux", "uy", "uz"), arrs))
+
+    def set_particles(self, sp, x, z, ux, uy, uz):
+        arrs = [_f64(a) for a in (x, z, ux, uy, uz)]
+        lib().oracle_set_particles(self._s, sp, len(arrs[0]), *[_p(a, ctypes.c_double) for a in arrs])
+
+    # grids
+    def _nn(self):
+        return self.nx * (self.nz + 1)
+
+    def get_field(self, f):
+        out = np.empty(self._nn(), np.float64)
+        lib().oracle_get_field(self._s, f, _p(out, ctypes.c_double))
+        return out.reshape(self.nz + 1, self.nx)
+
+    def set_field(self, f, a):
+        a = _f64(a).reshape(-1)
+        assert a.size == self._nn()
+        lib().oracle_set_field(self._s, f, _p(a, ctypes.c_double))
+
+    def get_rho(self):
+        out = np.empty(self._nn(), np.int64)
+        lib().oracle_get_rho(self._s, _p(out, ctypes.c_int64))
+        return out.reshape(self.nz + 1, self.nx)
+
+    def set_rho(self, a):
+        a = np.ascontiguousarray(a, np.int64).reshape(-1)
+        lib().oracle_set_rho(self._s, _p(a, ctypes.c_int64))
+
+    def get_current(self):
+        out = np.empty(3 * self._nn(), np.int64)
+        lib().oracle_get_current(self._s, _p(out, ctypes.c_int64))
+        return out.reshape(3, self.nz + 1, self.nx)
+
+    def set_current(self, a):
+        a = np.ascontiguousarray(a, np.int64).reshape(-1)
+        lib().oracle_set_current(self._s, _p(a, ctypes.c_int64))
+
+    # physics
+    def step(self, n=1):
+        lib().oracle_step(self._s, int(n))
+
+    def pair_force(self):
+        n = self.num_particles(0)
+        out = np.empty(3 * n, np.float64)
+        lib().oracle_pair_force(self._s, _p(out, ctypes.c_double))
+        return out.reshape(n, 3)
+
+    def gather_density(self, x, z):
+        out = np.empty(3, np.float64)
+        lib().oracle_gather_density(self._s, float(x), float(z), _p(out, ctypes.c_double))
+        return out
+
+    def energy(self):
+        out = np.empty(5, np.float64)
+        lib().oracle_energy(self._s, _p(out, ctypes.c_double))
+        return dict(zip(("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair"), out))
+
+    def laser_field(self, x_cells, t):
+        return lib().oracle_laser_field(self._s, float(x_cells), float(t))
+
+
+# standalone helpers --------------------------------------------------------------------
+
+def lj_U(r):
+    return lib().oracle_lj_U(float(r))
+
+
+def lj_dU(r):
+    return lib().oracle_lj_dU(float(r))
+
+
+def neighbor_distances(n, dn, r0_dx):
+    a = ctypes.c_double()
+    b = ctypes.c_double()
+    rbar = lib().oracle_neighbor_distances(float(n), float(dn), float(r0_dx), ctypes.byref(a), ctypes.byref(b))
+    return rbar, a.value, b.value
+
+
+def boris(q, m, dt, E, B, F, u):
+    E, B, F = (np.ascontiguousarray(v, np.float64) for v in (E, B, F))
+    u = np.array(u, np.float64)
+    lib().oracle_boris(q, m, dt, _p(E, ctypes.c_double), _p(B, ctypes.c_double), _p(F, ctypes.c_double),
+                       _p(u, ctypes.c_double))
+    return u
+
+
+def jy_code(ux, uy, uz):
+    return lib().oracle_jy_code(float(np.float32(ux)), float(np.float32(uy)), float(np.float32(uz)))
+
+
+def deposit_density(nx, nz, x, z):
+    x, z = _f64(x), _f64(z)
+    out = np.zeros(nx * (nz + 1), np.int64)
+    lib().oracle_deposit_density(nx, nz, len(x), _p(x, ctypes.c_double), _p(z, ctypes.c_double),
+                                 _p(out, ctypes.c_int64))
+    return out.reshape(nz + 1, nx)
+
+
+def deposit_current(nx, nz, sign, x0, z0, x1, z1, ux, uy, uz, out=None):
+    x0, z0, x1, z1 = (_f64(a) for a in (x0, z0, x1, z1))
+    ux, uy, uz = (np.ascontiguousarray(a, np.float32) for a in (ux, uy, uz))
+    if out is None:
+        out = np.zeros((3, nz + 1, nx), np.int64)
+    lib().oracle_deposit_current(nx, nz, len(x0), sign, _p(x0, ctypes.c_double), _p(z0, ctypes.c_double),
+                                 _p(x1, ctypes.c_double), _p(z1, ctypes.c_double), _p(ux, ctypes.c_float),
+                                 _p(uy, ctypes.c_float), _p(uz, ctypes.c_float),
+                                 _p(out[0], ctypes.c_int64), _p(out[1], ctypes.c_int64), _p(out[2], ctypes.c_int64))
+    return out

@@ -1,0 +1,715 @@
+/*
+ * pic_oracle.c -- plain FP64 CPU oracle of one particle-in-cell (PIC) cycle with the
+ * pair-potential force of Mitchell, Schumacher & Chowdhury, "Modeling crater formation in
+ * femtosecond-pulse laser damage from basic principles" (arXiv:1502.07722).
+ *
+ * TEST INFRASTRUCTURE. This library exists only to check the CUDA path. Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark load it. It shares no source,
+ * header, table or helper with the CUDA library, and the CUDA library never calls it.
+ *
+ * It is deliberately slow and literal: one particle at a time, one node at a time, FP64
+ * throughout, no blocking, no fusion. Each function names the passage it follows.
+ *
+ * The cycle (paper, the PIC-cycle paragraph and Fig. 1):
+ *   1. macroparticle weights are interpolated to the nearest surrounding nodes -> node density
+ *   2. node density and its gradient at the half nodes are interpolated back to each
+ *      macroparticle; the local environment gives nearest-neighbour distances (Eqs. 1-2) and
+ *      the Lennard-Jones force (Eq. 3)
+ *   3. Lorentz push (+ pair force), current deposition, Maxwell (Yee) field update.
+ *
+ * Readings where the paper is silent (all listed in the design notes of the repository):
+ *   - "nearest surrounding nodes": linear (cloud-in-cell) weights onto the 2 x 2 cell corners.
+ *     Weights are fixed point: a coordinate X = rint(x * 2^16) (x in cell units), node weight
+ *     S_j(X) = max(0, 2^16 - |X - 2^16 j|). Node sums are exact integers.
+ *   - the gradient at the half nodes is the edge difference of the node density, interpolated
+ *     linearly along the other axis; together with the bilinear node density this is the exact
+ *     gradient of the interpolated density ("self-consistent").
+ *   - densities are used in units of n0 = r0^-3, so rbar/r0 = (n/n0)^(-1/3).
+ *   - Eq. (2): the neighbour on the +x side sits at rbar / (1 - g/2), the one on the -x side at
+ *     rbar / (1 + g/2), g = d rbar / dx; a non-positive denominator puts that neighbour at
+ *     infinity (no force). The force on the atom along x is U'(dr+) - U'(dr-).
+ *   - In 2D the +-y neighbours sit at rbar (no force, counted in the energy).
+ *   - Walls at z = 0 and z = nz reflect particles; the pair density on the wall node rows is
+ *     doubled (mirror image of the slab behind the wall). x is periodic.
+ *   - current deposition (not described in the paper) is Esirkepov's charge-conserving scheme
+ *     for linear weights, evaluated in the same fixed point; J_y uses the code
+ *     V = rint(beta_y * 2^18) taken in FP32 exactly as the kernel takes it.
+ *   - push: relativistic Boris with u = gamma v / c at half steps; the pair force is added to
+ *     both half electric kicks.
+ *   - fields: 2D3V Yee, B advanced in two half steps around the E update, first-order Mur at
+ *     z = 0 and z = nz, laser launched by a J_x current sheet two node rows below the top.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018 */
+#define O_C     299792458.0
+#define O_QE    1.602176634e-19
+#define O_ME    9.1093837015e-31
+#define O_EPS0  8.8541878128e-12
+#define O_KB    1.380649e-23
+#define O_AMU   1.66053906660e-27
+#define O_PI    3.14159265358979323846
+
+#define QS 65536LL          /* fixed-point units per cell along one axis (2^16) */
+
+/* ---------------------------------------------------------------------------------------- */
+/* configuration: physical inputs                                                            */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t nx, nz;          /* cells along x (periodic) and z (walls)                       */
+    int32_t slab_k;          /* the copper slab fills cell rows k < slab_k                    */
+    int32_t mode;            /* 0: ions + electrons + fields; 1: neutral atoms only           */
+    int32_t ppc_ion, ppc_electron;
+    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (scaled branches)       */
+    int32_t laser_profile;   /* 0: none; 1: plane wave; 2: focused Gaussian beam              */
+    double dx;               /* cell size (m), square cells                                   */
+    double cfl;              /* dt = cfl * dx / (c * sqrt(2)) when dt_override <= 0          */
+    double dt_override;      /* s                                                             */
+    double n_atoms;          /* solid density (m^-3)                                          */
+    double T_ion_K, T_electron_eV;
+    double ion_charge;       /* in units of e                                                 */
+    double ion_mass_amu;
+    double D_eV;             /* dissociation energy of Eq. (3)                                */
+    double r0;               /* equilibrium distance of Eq. (3) (m); <= 0 -> n_atoms^(-1/3)  */
+    double c_att, s_rep;     /* altered potential: factor on the attractive / repulsive side */
+    double lambda, I0, tau_fwhm, w0, t_peak;   /* laser (m, W/m^2, s, m, s)                  */
+    uint64_t seed;
+} ocfg;
+
+typedef struct {
+    ocfg c;
+    double dt, w, r0, D, rho_scale;     /* rho_scale: integer node sum -> n / n0           */
+    int nsp;
+    double q[2], m[2], uth[2];
+    int pair[2];                        /* species that carries the pair force / density    */
+    int64_t np[2];
+    double *x[2], *z[2], *ux[2], *uy[2], *uz[2];
+    double *F[6];                       /* Ex Ey Ez Bx By Bz, each (nz+1)*nx, row-major k,i */
+    int64_t *rho;                       /* pair-species node sums at the current positions  */
+    int64_t *J[3];                      /* J2x (i+1/2,k), J6y (i,k), J2z (i,k+1/2)           */
+    int64_t step;
+    /* laser */
+    double E0, omega, kwave, t_ant, w_ant, R_ant, gouy_ant, amp_ant;
+    int k_ant;
+} ostate;
+
+static int64_t imod(int64_t a, int64_t n) { int64_t r = a % n; return r < 0 ? r + n : r; }
+static int64_t floordiv(int64_t a, int64_t b) { int64_t q = a / b; if ((a % b) != 0 && ((a < 0) != (b < 0))) q--; return q; }
+static int64_t hat(int64_t X, int64_t j) { int64_t d = X - QS * j; if (d < 0) d = -d; return d < QS ? QS - d : 0; }
+#define NODE(s, i, k) ((size_t)(k) * (size_t)(s)->c.nx + (size_t)(i))
+
+/* ---------------------------------------------------------------------------------------- */
+/* seeded generator for the initial state: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014),   */
+/* used counter-style: draw(key) = first output of a SplitMix64 generator seeded with        */
+/* seed ^ key.                                                                               */
+/* ---------------------------------------------------------------------------------------- */
+static uint64_t splitmix64_first(uint64_t state)
+{
+    uint64_t z = state + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+/* key = ((species * 2^40 + particle) * 8 + draw) */
+static uint64_t draw_bits(uint64_t seed, int s, uint64_t pidx, int d)
+{
+    uint64_t key = ((((uint64_t)s << 40) + pidx) << 3) + (uint64_t)d;
+    return splitmix64_first(seed ^ key);
+}
+static double draw_unit24(uint64_t b) { return (double)(b >> 40) * (1.0 / 16777216.0); }      /* [0,1) */
+static double draw_open53(uint64_t b) { return ((double)(b >> 11) + 1.0) * (1.0 / 9007199254740992.0); } /* (0,1] */
+
+/* ---------------------------------------------------------------------------------------- */
+/* Lennard-Jones pair potential, Eq. (3), in units of D with r in units of r0               */
+/* ---------------------------------------------------------------------------------------- */
+double oracle_lj_U(double r) { return pow(r, -12.0) - 2.0 * pow(r, -6.0); }
+/* dU/dr (units D / r0) */
+double oracle_lj_dU(double r) { return -12.0 * pow(r, -13.0) + 12.0 * pow(r, -7.0); }
+
+/* branch factors of the altered potential (a finite stand-in for "infinite below r0" and the
+ * multiplicative correction on the attractive side); plain Eq. (3) when pot_mode == 0 */
+static double branch_factor(const ostate* s, double r)
+{
+    if (s->c.pot_mode == 0) return 1.0;
+    return r < 1.0 ? s->c.s_rep : s->c.c_att;
+}
+
+/* Eq. (1)-(2): nearest-neighbour distances (units r0) along one axis from the local density
+ * n (units n0) and its derivative dn (units n0 per cell); r0_dx = r0 / dx.
+ * Returns rbar; *plus / *minus are the distances to the neighbours on the + and - side
+ * (INFINITY when the neighbour is pushed to infinity). */
+double oracle_neighbor_distances(double n, double dn, double r0_dx, double* plus, double* minus)
+{
+    double rbar = pow(n, -1.0 / 3.0);                                 /* rbar = n^(-1/3)    */
+    double g = -(1.0 / 3.0) * dn * pow(n, -4.0 / 3.0) * r0_dx;        /* Eq. (1)            */
+    double dp = 1.0 - 0.5 * g, dm = 1.0 + 0.5 * g;                    /* Eq. (2)            */
+    *plus = dp > 0.0 ? rbar / dp : INFINITY;
+    *minus = dm > 0.0 ? rbar / dm : INFINITY;
+    return rbar;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* node density (pair species), paper's PIC-cycle paragraph: weights to the nearest nodes   */
+/* ---------------------------------------------------------------------------------------- */
+static void deposit_density_one(int nx, int nz, int64_t* rho, double x, double z)
+{
+    int64_t X = llrint(x * (double)QS), Z = llrint(z * (double)QS);
+    int64_t j0 = floordiv(X, QS), l0 = floordiv(Z, QS);
+    for (int64_t l = l0; l <= l0 + 1; l++) {
+        int64_t sz = hat(Z, l);
+        if (sz == 0) continue;
+        for (int64_t j = j0; j <= j0 + 1; j++) {
+            int64_t sx = hat(X, j);
+            if (sx == 0) continue;
+            if (l < 0 || l > nz) abort();
+            rho[(size_t)l * nx + imod(j, nx)] += sx * sz;
+        }
+    }
+}
+
+void oracle_deposit_density(int32_t nx, int32_t nz, int64_t n, const double* x, const double* z, int64_t* rho)
+{
+    memset(rho, 0, sizeof(int64_t) * (size_t)nx * (size_t)(nz + 1));
+    for (int64_t p = 0; p < n; p++) deposit_density_one(nx, nz, rho, x[p], z[p]);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* current deposition: Esirkepov (Comput. Phys. Commun. 135, 144 (2001)) for linear weights, */
+/* in the fixed point of the density. Integer identities:                                   */
+/*   2 Wx(j,l) = dSx(j) (S0z(l) + S1z(l))      2 Wz = dSz (S0x + S1x)                        */
+/*   6 Wy(j,l) = 2 S0x S0z + S1x S0z + S0x S1z + 2 S1x S1z                                   */
+/*   J2x(j+1/2,l) = J2x(j-1/2,l) - 2 Wx(j,l)   (and the same along z)                        */
+/* so that 2 (rho1 - rho0) + div(J2) = 0 exactly.                                            */
+/* V is the J_y code of the particle.                                                        */
+/* ---------------------------------------------------------------------------------------- */
+static void deposit_current_one(int nx, int nz, int64_t* J2x, int64_t* J6y, int64_t* J2z, int64_t sign,
+                                int64_t X0, int64_t Z0, int64_t X1, int64_t Z1, int64_t V)
+{
+    int64_t bx = floordiv(X0 < X1 ? X0 : X1, QS), bz = floordiv(Z0 < Z1 ? Z0 : Z1, QS);
+    int64_t S0x[3], S1x[3], S0z[3], S1z[3];
+    for (int a = 0; a < 3; a++) {
+        S0x[a] = hat(X0, bx + a); S1x[a] = hat(X1, bx + a);
+        S0z[a] = hat(Z0, bz + a); S1z[a] = hat(Z1, bz + a);
+    }
+    /* both shapes must lie inside the 3-node window (a move of less than one cell) */
+    int64_t t0 = 0, t1 = 0, u0 = 0, u1 = 0;
+    for (int a = 0; a < 3; a++) { t0 += S0x[a]; t1 += S1x[a]; u0 += S0z[a]; u1 += S1z[a]; }
+    if (t0 != QS || t1 != QS || u0 != QS || u1 != QS) abort();
+
+    for (int b = 0; b < 3; b++) {            /* J_x along each node row */
+        int64_t acc = 0;
+        for (int a = 0; a < 2; a++) {
+            acc -= (S1x[a] - S0x[a]) * (S0z[b] + S1z[b]);
+            if (acc != 0) {
+                int64_t l = bz + b;
+                if (l < 0 || l > nz) abort();
+                J2x[(size_t)l * nx + imod(bx + a, nx)] += sign * acc;
+            }
+        }
+    }
+    for (int a = 0; a < 3; a++) {            /* J_z along each node column */
+        int64_t acc = 0;
+        for (int b = 0; b < 2; b++) {
+            acc -= (S1z[b] - S0z[b]) * (S0x[a] + S1x[a]);
+            if (acc != 0) {
+                int64_t l = bz + b;
+                if (l < 0 || l > nz - 1) abort();
+                J2z[(size_t)l * nx + imod(bx + a, nx)] += sign * acc;
+            }
+        }
+    }
+    if (V != 0) {
+        for (int b = 0; b < 3; b++)
+            for (int a = 0; a < 3; a++) {
+                int64_t w6 = 2 * S0x[a] * S0z[b] + S1x[a] * S0z[b] + S0x[a] * S1z[b] + 2 * S1x[a] * S1z[b];
+                if (w6 != 0) {
+                    int64_t l = bz + b;
+                    if (l < 0 || l > nz) abort();
+                    J6y[(size_t)l * nx + imod(bx + a, nx)] += sign * V * w6;
+                }
+            }
+    }
+}
+
+/* J_y code: V = rint(beta_y * 2^18), beta_y = u_y / sqrt(1 + u^2), all in FP32 without fused
+ * multiply-add, so that the decision is the kernel's (this file is built with contraction off) */
+int64_t oracle_jy_code(float ux, float uy, float uz)
+{
+    float u2 = ux * ux;
+    u2 = u2 + uy * uy;
+    u2 = u2 + uz * uz;
+    float g = sqrtf(1.0f + u2);
+    float by = uy / g;
+    return (int64_t)rintf(by * 262144.0f);
+}
+
+/* Unwrap the new x coordinate (periodic, period nx) to within half a period of the old one. */
+static int64_t unwrap_X(int64_t X0, int64_t X1, int nx)
+{
+    int64_t P = (int64_t)nx * QS;
+    while (X1 - X0 > P / 2) X1 -= P;
+    while (X0 - X1 > P / 2) X1 += P;
+    return X1;
+}
+
+/* Deposit the current of n particles that moved from (x0,z0) to (x1,z1) with new momenta u
+ * (FP32, the state the kernel stores). Accumulates into J2x, J6y, J2z. */
+void oracle_deposit_current(int32_t nx, int32_t nz, int64_t n, int32_t sign,
+                            const double* x0, const double* z0, const double* x1, const double* z1,
+                            const float* ux, const float* uy, const float* uz,
+                            int64_t* J2x, int64_t* J6y, int64_t* J2z)
+{
+    for (int64_t p = 0; p < n; p++) {
+        int64_t X0 = llrint(x0[p] * (double)QS), Z0 = llrint(z0[p] * (double)QS);
+        int64_t X1 = unwrap_X(X0, llrint(x1[p] * (double)QS), nx), Z1 = llrint(z1[p] * (double)QS);
+        deposit_current_one(nx, nz, J2x, J6y, J2z, sign, X0, Z0, X1, Z1, oracle_jy_code(ux[p], uy[p], uz[p]));
+    }
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* interpolation back to the particle                                                        */
+/* ---------------------------------------------------------------------------------------- */
+/* pair density at a node in units of n0; wall rows doubled (mirror image behind the wall) */
+static double nhat_node(const ostate* s, int64_t i, int64_t k)
+{
+    double v = (double)s->rho[NODE(s, imod(i, s->c.nx), k)] * s->rho_scale;
+    if (k == 0 || k == s->c.nz) v *= 2.0;
+    return v;
+}
+
+/* bilinear node density and its gradient (per cell) at (x, z): the gradient is the edge
+ * difference at the half nodes, interpolated along the other axis (paper: density gradient at
+ * the half-node positions, interpolated back self-consistently) */
+static void gather_density(const ostate* s, double x, double z, double* n, double* dn_dxi, double* dn_dzeta)
+{
+    int64_t i = (int64_t)floor(x), k = (int64_t)floor(z);
+    double fx = x - (double)i, fz = z - (double)k;
+    if (k >= s->c.nz) { k = s->c.nz - 1; fz = 1.0; }
+    double n00 = nhat_node(s, i, k), n10 = nhat_node(s, i + 1, k);
+    double n01 = nhat_node(s, i, k + 1), n11 = nhat_node(s, i + 1, k + 1);
+    *n = (1 - fx) * (1 - fz) * n00 + fx * (1 - fz) * n10 + (1 - fx) * fz * n01 + fx * fz * n11;
+    *dn_dxi = (1 - fz) * (n10 - n00) + fz * (n11 - n01);
+    *dn_dzeta = (1 - fx) * (n01 - n00) + fx * (n11 - n10);
+}
+
+/* staggered bilinear gather of a Yee component located at (i + sx, k + sz) */
+static double gather_field(const ostate* s, const double* A, double x, double z, double sx, double sz)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    double xs = x - sx, zs = z - sz;
+    int64_t rows = sz > 0 ? nz : nz + 1;      /* half-row components have nz rows */
+    if (zs < 0.0) zs = 0.0;
+    if (zs > (double)(rows - 1)) zs = (double)(rows - 1);
+    int64_t i = (int64_t)floor(xs), k = (int64_t)floor(zs);
+    double fx = xs - (double)i, fz = zs - (double)k;
+    if (k >= rows - 1) { k = rows - 2; fz = 1.0; }
+    int64_t i0 = imod(i, nx), i1 = imod(i + 1, nx);
+    return (1 - fx) * (1 - fz) * A[(size_t)k * nx + i0] + fx * (1 - fz) * A[(size_t)k * nx + i1]
+         + (1 - fx) * fz * A[(size_t)(k + 1) * nx + i0] + fx * fz * A[(size_t)(k + 1) * nx + i1];
+}
+
+/* Force (N, per atom) on an atom at (x, z) from the current node density, Eqs. (1)-(3).
+ * If energy is not NULL it receives the atom's pair energy (J): half the sum of U over its
+ * six nearest neighbours (+-x, +-z from Eq. 2, +-y at rbar). */
+static void pair_force_at(const ostate* s, double x, double z, double F[3], double* energy)
+{
+    double n, dnx, dnz;
+    gather_density(s, x, z, &n, &dnx, &dnz);
+    F[0] = F[1] = F[2] = 0.0;
+    if (energy) *energy = 0.0;
+    if (!(n > 0.0)) return;
+    double r0_dx = s->r0 / s->c.dx;
+    double ap, am, bp, bm;
+    double rbar = oracle_neighbor_distances(n, dnx, r0_dx, &ap, &am);
+    oracle_neighbor_distances(n, dnz, r0_dx, &bp, &bm);
+    double f_unit = s->D / s->r0;
+    double dUap = isinf(ap) ? 0.0 : branch_factor(s, ap) * oracle_lj_dU(ap);
+    double dUam = isinf(am) ? 0.0 : branch_factor(s, am) * oracle_lj_dU(am);
+    double dUbp = isinf(bp) ? 0.0 : branch_factor(s, bp) * oracle_lj_dU(bp);
+    double dUbm = isinf(bm) ? 0.0 : branch_factor(s, bm) * oracle_lj_dU(bm);
+    F[0] = f_unit * (dUap - dUam);
+    F[2] = f_unit * (dUbp - dUbm);
+    if (energy) {
+        double u = 0.0;
+        if (!isinf(ap)) u += branch_factor(s, ap) * oracle_lj_U(ap);
+        if (!isinf(am)) u += branch_factor(s, am) * oracle_lj_U(am);
+        if (!isinf(bp)) u += branch_factor(s, bp) * oracle_lj_U(bp);
+        if (!isinf(bm)) u += branch_factor(s, bm) * oracle_lj_U(bm);
+        u += 2.0 * branch_factor(s, rbar) * oracle_lj_U(rbar);
+        *energy = 0.5 * s->D * u;
+    }
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* relativistic Boris push (u = gamma v / c), pair force added to both half kicks            */
+/* ---------------------------------------------------------------------------------------- */
+void oracle_boris(double q, double m, double dt, const double E[3], const double B[3], const double Fp[3], double u[3])
+{
+    double eps = q * dt / (2.0 * m * O_C);          /* electric half kick per (V/m)          */
+    double fk = dt / (2.0 * m * O_C);               /* pair-force half kick per N             */
+    double um[3], up[3], t[3], sv[3], uprime[3];
+    for (int d = 0; d < 3; d++) um[d] = u[d] + eps * E[d] + fk * Fp[d];
+    double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    double tfac = q * dt / (2.0 * m * gm);
+    for (int d = 0; d < 3; d++) t[d] = tfac * B[d];
+    double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int d = 0; d < 3; d++) sv[d] = 2.0 * t[d] / (1.0 + t2);
+    uprime[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+    uprime[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+    uprime[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+    up[0] = um[0] + (uprime[1] * sv[2] - uprime[2] * sv[1]);
+    up[1] = um[1] + (uprime[2] * sv[0] - uprime[0] * sv[2]);
+    up[2] = um[2] + (uprime[0] * sv[1] - uprime[1] * sv[0]);
+    for (int d = 0; d < 3; d++) u[d] = up[d] + eps * E[d] + fk * Fp[d];
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* laser source: E_x of the incident pulse at the antenna row                                */
+/* ---------------------------------------------------------------------------------------- */
+static double laser_field(const ostate* s, double x_cells, double t)
+{
+    if (s->c.laser_profile == 0) return 0.0;
+    double tau = t - s->t_ant;
+    double env = exp(-2.0 * log(2.0) * tau * tau / (s->c.tau_fwhm * s->c.tau_fwhm));
+    if (s->c.laser_profile == 1) return s->E0 * env * sin(s->omega * tau);
+    double xr = (x_cells - 0.5 * s->c.nx) * s->c.dx;
+    double amp = s->amp_ant * exp(-xr * xr / (s->w_ant * s->w_ant));
+    double phase = -s->kwave * xr * xr / (2.0 * s->R_ant) + s->gouy_ant;
+    return s->E0 * amp * env * sin(s->omega * tau + phase);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Maxwell, 2D3V Yee (d/dy = 0). Ex(i+1/2,k) Ey(i,k) Ez(i,k+1/2) Bx(i,k+1/2) By(i+1/2,k+1/2)  */
+/* Bz(i+1/2,k); node rows k = 0..nz, half rows k = 0..nz-1                                   */
+/* ---------------------------------------------------------------------------------------- */
+static void half_step_B(ostate* s)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    double h = 0.5 * s->dt / s->c.dx;
+    double *Ex = s->F[0], *Ey = s->F[1], *Ez = s->F[2], *Bx = s->F[3], *By = s->F[4], *Bz = s->F[5];
+    for (int k = 0; k <= nz; k++)
+        for (int i = 0; i < nx; i++) {
+            int ip = (i + 1) % nx;
+            if (k < nz) {
+                /* dBx/dt = dEy/dz ; dBy/dt = dEz/dx - dEx/dz */
+                Bx[NODE(s, i, k)] += h * (Ey[NODE(s, i, k + 1)] - Ey[NODE(s, i, k)]);
+                By[NODE(s, i, k)] += h * ((Ez[NODE(s, ip, k)] - Ez[NODE(s, i, k)]) - (Ex[NODE(s, i, k + 1)] - Ex[NODE(s, i, k)]));
+            }
+            /* dBz/dt = -dEy/dx */
+            Bz[NODE(s, i, k)] -= h * (Ey[NODE(s, ip, k)] - Ey[NODE(s, i, k)]);
+        }
+}
+
+static void full_step_E(ostate* s)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    double cdt = O_C * s->dt, h = O_C * O_C * s->dt / s->c.dx;
+    double *Ex = s->F[0], *Ey = s->F[1], *Ez = s->F[2], *Bx = s->F[3], *By = s->F[4], *Bz = s->F[5];
+    size_t nn = (size_t)nx * (nz + 1);
+    double* nEx = malloc(sizeof(double) * nn);
+    double* nEy = malloc(sizeof(double) * nn);
+    /* J (integer) -> dt J / eps0 */
+    double cjx = O_QE * s->w / (8589934592.0 * s->c.dx * O_EPS0);                 /* 2^33 */
+    double cjy = O_QE * s->w * O_C * s->dt / (6.0 * 1125899906842624.0 * s->c.dx * s->c.dx * O_EPS0); /* 6*2^50 */
+    double tmid = ((double)s->step + 0.5) * s->dt;
+    for (int k = 0; k <= nz; k++)
+        for (int i = 0; i < nx; i++) {
+            int im = (i + nx - 1) % nx;
+            size_t c = NODE(s, i, k);
+            nEx[c] = Ex[c];
+            nEy[c] = Ey[c];
+            if (k > 0 && k < nz) {
+                /* dEx/dt = -c^2 dBy/dz - Jx/eps0 ; dEy/dt = c^2 (dBx/dz - dBz/dx) - Jy/eps0 */
+                nEx[c] = Ex[c] - h * (By[c] - By[NODE(s, i, k - 1)]) - cjx * (double)s->J[0][c];
+                nEy[c] = Ey[c] + h * ((Bx[c] - Bx[NODE(s, i, k - 1)]) - (Bz[c] - Bz[NODE(s, im, k)])) - cjy * (double)s->J[1][c];
+                if (k == s->k_ant) nEx[c] += 2.0 * (cdt / s->c.dx) * laser_field(s, (double)i + 0.5, tmid);
+            }
+        }
+    /* first-order Mur on the wall rows for the tangential components */
+    double alpha = (cdt - s->c.dx) / (cdt + s->c.dx);
+    for (int i = 0; i < nx; i++) {
+        size_t b0 = NODE(s, i, 0), b1 = NODE(s, i, 1), t0 = NODE(s, i, nz), t1 = NODE(s, i, nz - 1);
+        nEx[b0] = Ex[b1] + alpha * (nEx[b1] - Ex[b0]);
+        nEy[b0] = Ey[b1] + alpha * (nEy[b1] - Ey[b0]);
+        nEx[t0] = Ex[t1] + alpha * (nEx[t1] - Ex[t0]);
+        nEy[t0] = Ey[t1] + alpha * (nEy[t1] - Ey[t0]);
+    }
+    for (int k = 0; k < nz; k++)
+        for (int i = 0; i < nx; i++) {
+            int ip = (i + 1) % nx;
+            size_t c = NODE(s, i, k);
+            /* dEz/dt = c^2 dBy/dx - Jz/eps0 */
+            Ez[c] += h * (By[c] - By[NODE(s, (i + nx - 1) % nx, k)]) - cjx * (double)s->J[2][c];
+            (void)ip;
+        }
+    memcpy(Ex, nEx, sizeof(double) * nn);
+    memcpy(Ey, nEy, sizeof(double) * nn);
+    free(nEx); free(nEy);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* state management                                                                          */
+/* ---------------------------------------------------------------------------------------- */
+static void redeposit(ostate* s)
+{
+    oracle_deposit_density(s->c.nx, s->c.nz, s->np[0], s->x[0], s->z[0], s->rho);
+}
+
+static void alloc_species(ostate* s, int sp, int64_t n)
+{
+    free(s->x[sp]); free(s->z[sp]); free(s->ux[sp]); free(s->uy[sp]); free(s->uz[sp]);
+    s->np[sp] = n;
+    size_t b = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    s->x[sp] = calloc(1, b); s->z[sp] = calloc(1, b);
+    s->ux[sp] = calloc(1, b); s->uy[sp] = calloc(1, b); s->uz[sp] = calloc(1, b);
+}
+
+/* Initial state (paper: a damage simulation is initialised for target density and
+ * temperature): a slab of cell rows k < slab_k, ppc macro-ions per cell at uniformly drawn
+ * positions, Maxwellian momenta; electrons co-located with the ions (zero net charge, E = 0). */
+static void init_particles(ostate* s)
+{
+    const ocfg* c = &s->c;
+    int64_t ncell = (int64_t)c->nx * c->slab_k;
+    for (int sp = 0; sp < s->nsp; sp++) {
+        int ppc = sp == 0 ? c->ppc_ion : c->ppc_electron;
+        alloc_species(s, sp, ncell * ppc);
+        int64_t p = 0;
+        for (int k = 0; k < c->slab_k; k++)
+            for (int i = 0; i < c->nx; i++)
+                for (int j = 0; j < ppc; j++, p++) {
+                    uint64_t cellidx = (uint64_t)k * (uint64_t)c->nx + (uint64_t)i;
+                    /* positions: electrons reuse the ion draws of the same (cell, slot) */
+                    int pos_sp = (sp == 1 && c->ppc_electron == c->ppc_ion) ? 0 : sp;
+                    uint64_t pid_pos = cellidx * (uint64_t)ppc + (uint64_t)j;
+                    s->x[sp][p] = (double)i + draw_unit24(draw_bits(c->seed, pos_sp, pid_pos, 0));
+                    s->z[sp][p] = (double)k + draw_unit24(draw_bits(c->seed, pos_sp, pid_pos, 1));
+                    /* Box-Muller normals from two pairs of draws */
+                    double r1 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid_pos, 2))));
+                    double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 3));
+                    double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid_pos, 4))));
+                    double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 5));
+                    s->ux[sp][p] = s->uth[sp] * r1 * cos(a1);
+                    s->uy[sp][p] = s->uth[sp] * r1 * sin(a1);
+                    s->uz[sp][p] = s->uth[sp] * r2 * cos(a2);
+                }
+    }
+}
+
+ostate* oracle_create(const ocfg* cfg, int32_t with_particles)
+{
+    ostate* s = calloc(1, sizeof(ostate));
+    s->c = *cfg;
+    const ocfg* c = &s->c;
+    s->dt = c->dt_override > 0 ? c->dt_override : c->cfl * c->dx / (O_C * sqrt(2.0));
+    s->nsp = c->mode == 0 ? 2 : 1;
+    s->w = c->n_atoms * c->dx * c->dx / (double)c->ppc_ion;          /* atoms per metre of y */
+    s->r0 = c->r0 > 0 ? c->r0 : pow(c->n_atoms, -1.0 / 3.0);
+    s->D = c->D_eV * O_QE;
+    /* node sum (units 2^-32 of one macro-atom) -> density in units of n0 = r0^-3 */
+    s->rho_scale = s->w / (4294967296.0 * c->dx * c->dx) * pow(s->r0, 3.0);
+    s->q[0] = c->ion_charge * O_QE;
+    s->m[0] = c->ion_mass_amu * O_AMU;
+    s->uth[0] = sqrt(O_KB * c->T_ion_K / (s->m[0] * O_C * O_C));
+    s->pair[0] = 1;
+    s->q[1] = -O_QE;
+    s->m[1] = O_ME;
+    s->uth[1] = sqrt(c->T_electron_eV * O_QE / (O_ME * O_C * O_C));
+    s->pair[1] = 0;
+    size_t nn = (size_t)c->nx * (c->nz + 1);
+    for (int f = 0; f < 6; f++) s->F[f] = calloc(nn, sizeof(double));
+    for (int f = 0; f < 3; f++) s->J[f] = calloc(nn, sizeof(int64_t));
+    s->rho = calloc(nn, sizeof(int64_t));
+    /* laser: E0 from the peak intensity, pulse peak at the slab surface at t_peak */
+    s->E0 = sqrt(2.0 * c->I0 / (O_EPS0 * O_C));
+    s->omega = c->lambda > 0 ? 2.0 * O_PI * O_C / c->lambda : 0.0;
+    s->kwave = s->omega / O_C;
+    s->k_ant = c->nz - 2;
+    double L = (double)(s->k_ant - c->slab_k) * c->dx;                 /* antenna -> focus */
+    s->t_ant = c->t_peak - L / O_C;
+    if (c->laser_profile == 2) {
+        double zR = O_PI * c->w0 * c->w0 / c->lambda, sa = -L;
+        s->w_ant = c->w0 * sqrt(1.0 + (sa / zR) * (sa / zR));
+        s->R_ant = sa + zR * zR / sa;
+        s->gouy_ant = 0.5 * atan(sa / zR);
+        s->amp_ant = sqrt(c->w0 / s->w_ant);
+    }
+    if (with_particles) init_particles(s);
+    else for (int sp = 0; sp < s->nsp; sp++) alloc_species(s, sp, 0);
+    redeposit(s);
+    return s;
+}
+
+void oracle_free(ostate* s)
+{
+    if (!s) return;
+    for (int sp = 0; sp < 2; sp++) { free(s->x[sp]); free(s->z[sp]); free(s->ux[sp]); free(s->uy[sp]); free(s->uz[sp]); }
+    for (int f = 0; f < 6; f++) free(s->F[f]);
+    for (int f = 0; f < 3; f++) free(s->J[f]);
+    free(s->rho);
+    free(s);
+}
+
+int64_t oracle_num_particles(const ostate* s, int32_t sp) { return sp < s->nsp ? s->np[sp] : 0; }
+double oracle_dt(const ostate* s) { return s->dt; }
+double oracle_weight(const ostate* s) { return s->w; }
+double oracle_rho_scale(const ostate* s) { return s->rho_scale; }
+int64_t oracle_step_count(const ostate* s) { return s->step; }
+
+void oracle_get_particles(const ostate* s, int32_t sp, double* x, double* z, double* ux, double* uy, double* uz)
+{
+    int64_t n = s->np[sp];
+    memcpy(x, s->x[sp], sizeof(double) * n); memcpy(z, s->z[sp], sizeof(double) * n);
+    memcpy(ux, s->ux[sp], sizeof(double) * n); memcpy(uy, s->uy[sp], sizeof(double) * n);
+    memcpy(uz, s->uz[sp], sizeof(double) * n);
+}
+
+void oracle_set_particles(ostate* s, int32_t sp, int64_t n, const double* x, const double* z,
+                          const double* ux, const double* uy, const double* uz)
+{
+    alloc_species(s, sp, n);
+    memcpy(s->x[sp], x, sizeof(double) * n); memcpy(s->z[sp], z, sizeof(double) * n);
+    memcpy(s->ux[sp], ux, sizeof(double) * n); memcpy(s->uy[sp], uy, sizeof(double) * n);
+    memcpy(s->uz[sp], uz, sizeof(double) * n);
+    if (sp == 0) redeposit(s);
+}
+
+void oracle_get_field(const ostate* s, int32_t f, double* out)
+{
+    memcpy(out, s->F[f], sizeof(double) * (size_t)s->c.nx * (s->c.nz + 1));
+}
+void oracle_set_field(ostate* s, int32_t f, const double* in)
+{
+    memcpy(s->F[f], in, sizeof(double) * (size_t)s->c.nx * (s->c.nz + 1));
+}
+void oracle_get_rho(const ostate* s, int64_t* out) { memcpy(out, s->rho, sizeof(int64_t) * (size_t)s->c.nx * (s->c.nz + 1)); }
+void oracle_set_rho(ostate* s, const int64_t* in) { memcpy(s->rho, in, sizeof(int64_t) * (size_t)s->c.nx * (s->c.nz + 1)); }
+void oracle_get_current(const ostate* s, int64_t* out3)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    for (int f = 0; f < 3; f++) memcpy(out3 + f * nn, s->J[f], sizeof(int64_t) * nn);
+}
+void oracle_set_current(ostate* s, const int64_t* in3)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    for (int f = 0; f < 3; f++) memcpy(s->J[f], in3 + f * nn, sizeof(int64_t) * nn);
+}
+void oracle_set_step(ostate* s, int64_t step) { s->step = step; }
+
+/* per-atom pair force (N) on every macro-ion at its current position */
+void oracle_pair_force(const ostate* s, double* F)
+{
+    for (int64_t p = 0; p < s->np[0]; p++) pair_force_at(s, s->x[0][p], s->z[0][p], F + 3 * p, NULL);
+}
+
+/* density and gradient seen by a point (units n0, n0 per cell), for pinning the gather */
+void oracle_gather_density(const ostate* s, double x, double z, double out[3])
+{
+    gather_density(s, x, z, &out[0], &out[1], &out[2]);
+}
+
+/* advance a single particle: gather, pair force, Boris, move with walls */
+static void push_particle(ostate* s, int sp, int64_t p)
+{
+    double x = s->x[sp][p], z = s->z[sp][p];
+    double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, Fp[3] = {0, 0, 0};
+    if (s->c.mode == 0) {
+        E[0] = gather_field(s, s->F[0], x, z, 0.5, 0.0);
+        E[1] = gather_field(s, s->F[1], x, z, 0.0, 0.0);
+        E[2] = gather_field(s, s->F[2], x, z, 0.0, 0.5);
+        B[0] = gather_field(s, s->F[3], x, z, 0.0, 0.5);
+        B[1] = gather_field(s, s->F[4], x, z, 0.5, 0.5);
+        B[2] = gather_field(s, s->F[5], x, z, 0.5, 0.0);
+    }
+    if (s->pair[sp]) pair_force_at(s, x, z, Fp, NULL);
+    double u[3] = {s->ux[sp][p], s->uy[sp][p], s->uz[sp][p]};
+    oracle_boris(s->q[sp], s->m[sp], s->dt, E, B, Fp, u);
+    double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double xn = x + u[0] * O_C * s->dt / (g * s->c.dx);
+    double zn = z + u[2] * O_C * s->dt / (g * s->c.dx);
+    if (xn < 0.0) xn += s->c.nx;
+    if (xn >= s->c.nx) xn -= s->c.nx;
+    if (zn < 0.0) { zn = -zn; u[2] = -u[2]; }
+    if (zn >= s->c.nz) { zn = 2.0 * s->c.nz - zn; u[2] = -u[2]; }
+    s->x[sp][p] = xn; s->z[sp][p] = zn;
+    s->ux[sp][p] = u[0]; s->uy[sp][p] = u[1]; s->uz[sp][p] = u[2];
+}
+
+/* One PIC cycle (paper, PIC-cycle paragraph): pair force from the node density at x^n,
+ * Lorentz + pair push, current from x^n -> x^(n+1), node density at x^(n+1), Maxwell. */
+void oracle_step(ostate* s, int32_t nsteps)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    for (int it = 0; it < nsteps; it++) {
+        for (int f = 0; f < 3; f++) memset(s->J[f], 0, sizeof(int64_t) * nn);
+        for (int sp = 0; sp < s->nsp; sp++) {
+            int64_t n = s->np[sp];
+            double* x0 = malloc(sizeof(double) * (n ? n : 1));
+            double* z0 = malloc(sizeof(double) * (n ? n : 1));
+            memcpy(x0, s->x[sp], sizeof(double) * n);
+            memcpy(z0, s->z[sp], sizeof(double) * n);
+            for (int64_t p = 0; p < n; p++) push_particle(s, sp, p);      /* uses rho at x^n */
+            if (s->c.mode == 0 && s->q[sp] != 0.0) {
+                int sign = s->q[sp] > 0 ? 1 : -1;
+                for (int64_t p = 0; p < n; p++) {
+                    float fux = (float)s->ux[sp][p], fuy = (float)s->uy[sp][p], fuz = (float)s->uz[sp][p];
+                    oracle_deposit_current(s->c.nx, s->c.nz, 1, sign, x0 + p, z0 + p, s->x[sp] + p, s->z[sp] + p,
+                                           &fux, &fuy, &fuz, s->J[0], s->J[1], s->J[2]);
+                }
+            }
+            free(x0); free(z0);
+        }
+        redeposit(s);                                                    /* rho at x^(n+1) */
+        if (s->c.mode == 0) {
+            half_step_B(s);
+            full_step_E(s);
+            half_step_B(s);
+        }
+        s->step++;
+    }
+}
+
+/* Energies (J per metre of y): out = {kinetic ions, kinetic electrons, field E, field B, pair}.
+ * Kinetic uses the stored u (half step); field energy weights the wall node rows by 1/2. */
+void oracle_energy(const ostate* s, double out[5])
+{
+    for (int i = 0; i < 5; i++) out[i] = 0.0;
+    for (int sp = 0; sp < s->nsp; sp++) {
+        double acc = 0.0;
+        for (int64_t p = 0; p < s->np[sp]; p++) {
+            double u2 = s->ux[sp][p] * s->ux[sp][p] + s->uy[sp][p] * s->uy[sp][p] + s->uz[sp][p] * s->uz[sp][p];
+            acc += u2 / (sqrt(1.0 + u2) + 1.0);
+        }
+        out[sp] = acc * s->w * s->m[sp] * O_C * O_C;
+    }
+    int nx = s->c.nx, nz = s->c.nz;
+    double vol = s->c.dx * s->c.dx, mu0 = 1.0 / (O_EPS0 * O_C * O_C);
+    double eE = 0.0, eB = 0.0;
+    for (int k = 0; k <= nz; k++) {
+        double wn = (k == 0 || k == nz) ? 0.5 : 1.0;       /* node-row components */
+        for (int i = 0; i < nx; i++) {
+            size_t c = NODE(s, i, k);
+            eE += wn * (s->F[0][c] * s->F[0][c] + s->F[1][c] * s->F[1][c]);
+            eB += wn * s->F[5][c] * s->F[5][c];
+            if (k < nz) {
+                eE += s->F[2][c] * s->F[2][c];
+                eB += s->F[3][c] * s->F[3][c] + s->F[4][c] * s->F[4][c];
+            }
+        }
+    }
+    out[2] = 0.5 * O_EPS0 * eE * vol;
+    out[3] = 0.5 / mu0 * eB * vol;
+    double pe = 0.0;
+    for (int64_t p = 0; p < s->np[0]; p++) {
+        double F[3], e;
+        pair_force_at(s, s->x[0][p], s->z[0][p], F, &e);
+        pe += e;
+    }
+    out[4] = pe * s->w;
+}
+
+/* E_x the antenna launches at (x in cells, t), for pinning the source */
+double oracle_laser_field(const ostate* s, double x_cells, double t) { return laser_field(s, x_cells, t); }

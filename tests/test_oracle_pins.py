@@ -1,0 +1,534 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a closed form, an exact
+integer invariant, a brute-force count, or a property stated in the paper.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_07722_gb300.workloads import workload
+from tests import inputs
+
+C = 299792458.0
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+EPS0 = 8.8541878128e-12
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = []
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append([float(v) for v in line.split()])
+    return np.array(rows)
+
+
+# ---- Eq. (3): Lennard-Jones -------------------------------------------------------------
+
+def test_lj_golden_points():
+    """Eq. (3) fixes U(r0) = -D (the minimum) and U = 0 at r = 2^(-1/6) r0."""
+    for r, u, du in _golden("lj_eq3.txt"):
+        assert oracle.lj_U(r) == pytest.approx(u, abs=1e-14)
+        assert oracle.lj_dU(r) == pytest.approx(du, abs=1e-12)
+
+
+def test_lj_curvature_at_minimum():
+    """U''(r0) = 72 D / r0^2, from central differences of the oracle's U'."""
+    h = 1e-5
+    d2 = (oracle.lj_dU(1 + h) - oracle.lj_dU(1 - h)) / (2 * h)
+    assert d2 == pytest.approx(72.0, rel=1e-8)
+    # U' is the derivative of U
+    for r in (0.9, 1.05, 1.3, 2.0):
+        fd = (oracle.lj_U(r + h) - oracle.lj_U(r - h)) / (2 * h)
+        assert oracle.lj_dU(r) == pytest.approx(fd, rel=1e-8, abs=1e-9)
+
+
+# ---- Eq. (1)-(2): neighbour distances -----------------------------------------------------
+
+def test_eq1_gradient_matches_finite_difference():
+    """Eq. (1): d rbar/dx = -(1/3) dn/dx n^(-4/3); checked against a finite difference of
+    rbar = n^(-1/3) along a density ramp n(x) = n_a + s x (x in cells)."""
+    r0_dx = 0.0227
+    for n_a, s in ((1.0, 0.1), (0.4, -0.05), (2.5, 0.3)):
+        rbar, plus, minus = oracle.neighbor_distances(n_a, s, r0_dx)
+        # invert Eq. (2): plus = rbar/(1 - g/2) -> g = 2 (1 - rbar/plus)
+        g = 2.0 * (1.0 - rbar / plus)
+        h = 1e-6
+        drbar_dcell = ((n_a + s * h) ** (-1 / 3) - (n_a - s * h) ** (-1 / 3)) / (2 * h)
+        # rbar in units of r0, x in cells: d rbar/dx (dimensionless) = drbar_dcell * r0 / dx
+        assert g == pytest.approx(drbar_dcell * r0_dx, rel=1e-7)
+        assert rbar == pytest.approx(n_a ** (-1 / 3), rel=1e-15)
+
+
+def test_eq2_midpoint_condition():
+    """Paper, Eq. (2) text: with rbar varying linearly, the mean spacing midway between an atom
+    and its neighbour equals their distance. So the neighbour on the + side at distance a
+    satisfies rbar(x + a/2) = a, and the one on the - side rbar(x - b/2) = b."""
+    for rbar0, g in ((1.0, 0.01), (1.3, -0.2), (0.8, 0.5), (1.1, -1.2)):
+        # pick n, dn and r0/dx such that rbar = rbar0 and d rbar/dx = g
+        n = rbar0 ** -3
+        r0_dx = 1.0
+        dn = -3.0 * g * n ** (4 / 3) / r0_dx
+        rb, a, b = oracle.neighbor_distances(n, dn, r0_dx)
+        assert rb == pytest.approx(rbar0, rel=1e-14)
+        assert rbar0 + g * a / 2 == pytest.approx(a, rel=1e-13)
+        assert rbar0 - g * b / 2 == pytest.approx(b, rel=1e-13)
+        if g > 0:
+            assert a > b
+
+
+def test_eq2_neighbour_pushed_to_infinity():
+    """A gradient so steep that rbar(x + a/2) = a has no positive root leaves no neighbour."""
+    n = 1.0
+    g = 2.5                       # 1 - g/2 < 0
+    dn = -3.0 * g * n ** (4 / 3)
+    _, a, b = oracle.neighbor_distances(n, dn, 1.0)
+    assert math.isinf(a)
+    assert b == pytest.approx(1.0 / (1 + g / 2), rel=1e-14)
+
+
+# ---- node density ---------------------------------------------------------------------------
+
+def test_density_total_weight_and_first_moment():
+    """Interpolation to the nearest nodes conserves weight exactly and, being linear,
+    reproduces every particle's position as the first moment of its node weights."""
+    nx, nz = 32, 24
+    p = inputs.edge_particles(3, nx, nz, 4000, 0.0)
+    rho = oracle.deposit_density(nx, nz, p["x"], p["z"])
+    assert rho.sum() == len(p["x"]) * 2 ** 32
+    # first moment along z (no wrap): sum_l l * rho(l) = sum_p Z_p * 2^16 with Z = rint(z 2^16)
+    Z = np.rint(p["z"] * 65536).astype(np.int64)
+    l = np.arange(nz + 1, dtype=np.int64)[:, None]
+    assert int((rho * l).sum()) == int(Z.sum()) * 65536
+    # along x the moment is taken modulo the period (a node at j = nx is node 0)
+    X = np.rint(p["x"] * 65536).astype(np.int64)
+    j = np.arange(nx, dtype=np.int64)[None, :]
+    lhs = int((rho * j).sum()) % (nx * 2 ** 16)
+    rhs = (int(X.sum()) * 65536) % (nx * 2 ** 16)
+    assert lhs == rhs
+
+
+def test_density_brute_force_points():
+    """A particle on a node puts all of its weight there; one at a cell centre puts a
+    quarter on each corner; a particle on the periodic seam wraps."""
+    nx, nz = 8, 6
+    rho = oracle.deposit_density(nx, nz, [3.0], [2.0])
+    assert rho[2, 3] == 2 ** 32 and rho.sum() == 2 ** 32
+    rho = oracle.deposit_density(nx, nz, [3.5], [2.5])
+    assert (rho[2:4, 3:5] == 2 ** 30).all() and rho.sum() == 2 ** 32
+    rho = oracle.deposit_density(nx, nz, [7.75], [0.0])
+    assert rho[0, 7] == 2 ** 30 and rho[0, 0] == 3 * 2 ** 30
+
+
+# ---- current deposition ---------------------------------------------------------------------
+
+def _random_moves(seed, nx, nz, n):
+    rng = np.random.default_rng(seed)
+    p = inputs.edge_particles(seed, nx, nz, n, 0.0)
+    d = rng.uniform(-0.95, 0.95, size=(2, n))
+    d[:, : n // 4] = 0.0                                        # some particles do not move
+    x1 = p["x"] + d[0]
+    z1 = p["z"] + d[1]
+    x1 = np.mod(x1, nx)
+    z1 = np.where(z1 < 0, -z1, z1)
+    z1 = np.where(z1 >= nz, 2 * nz - z1 - 1e-6, z1)
+    # snap to FP32 cell + offset
+    x1 = np.floor(x1) + np.floor((x1 - np.floor(x1)) * (1 << 24)) / (1 << 24)
+    z1 = np.floor(z1) + np.floor((z1 - np.floor(z1)) * (1 << 24)) / (1 << 24)
+    u = rng.normal(0, 0.01, size=(3, n)).astype(np.float32)
+    return p["x"], p["z"], x1, z1, u
+
+
+def test_current_continuity_exact():
+    """Charge conservation: 2 (rho1 - rho0) + div(J2) = 0 at every node, exactly, for
+    moves across cells, across the periodic seam and off the walls."""
+    nx, nz = 16, 12
+    x0, z0, x1, z1, u = _random_moves(5, nx, nz, 3000)
+    J = oracle.deposit_current(nx, nz, 1, x0, z0, x1, z1, *u)
+    r0 = oracle.deposit_density(nx, nz, x0, z0)
+    r1 = oracle.deposit_density(nx, nz, x1, z1)
+    div = np.zeros_like(r0)
+    div += J[0] - np.roll(J[0], 1, axis=1)              # J2x(i+1/2) - J2x(i-1/2)
+    div[0:nz] += J[2][0:nz]                              # J2z(k+1/2)
+    div[1:nz + 1] -= J[2][0:nz]                          # - J2z(k-1/2)
+    assert np.array_equal(2 * (r1 - r0) + div, np.zeros_like(div))
+    assert not J[2][nz].any()                            # no edge above the top wall
+
+
+def test_current_dipole_and_rest():
+    """Sum of J over the grid equals the change of the dipole moment: sum J2x = 2^17 dX,
+    sum J2z = 2^17 dZ (fixed-point units); a particle at rest carries no J_x, J_z; the sum of
+    J6y over the nodes is 6 * 2^32 * V."""
+    nx, nz = 16, 12
+    x0, z0, x1, z1, u = _random_moves(9, nx, nz, 500)
+    for p in range(0, 500, 7):
+        J = oracle.deposit_current(nx, nz, 1, x0[p:p + 1], z0[p:p + 1], x1[p:p + 1], z1[p:p + 1],
+                                   u[0][p:p + 1], u[1][p:p + 1], u[2][p:p + 1])
+        X0, X1 = round(x0[p] * 65536), round(x1[p] * 65536)
+        P = nx * 65536
+        dX = (X1 - X0 + P // 2) % P - P // 2
+        dZ = round(z1[p] * 65536) - round(z0[p] * 65536)
+        assert int(J[0].sum()) == dX * 2 ** 17
+        assert int(J[2].sum()) == dZ * 2 ** 17
+        V = oracle.jy_code(u[0][p], u[1][p], u[2][p])
+        assert int(J[1].sum()) == 6 * 2 ** 32 * V
+        if dX == 0 and dZ == 0:
+            assert not J[0].any() and not J[2].any()
+
+
+def test_jy_code_is_fp32_decision():
+    """V = rint(beta_y 2^18) taken in FP32: check against numpy's FP32 arithmetic."""
+    rng = np.random.default_rng(1)
+    u = rng.normal(0, 0.3, size=(3, 2000)).astype(np.float32)
+    for a, b, c in u.T[:200]:
+        u2 = np.float32(a * a)
+        u2 = np.float32(u2 + np.float32(b * b))
+        u2 = np.float32(u2 + np.float32(c * c))
+        g = np.sqrt(np.float32(1) + u2, dtype=np.float32)
+        by = np.float32(b / g)
+        assert oracle.jy_code(a, b, c) == int(np.rint(np.float32(by * np.float32(262144.0))))
+
+
+# ---- pair force from the local environment ----------------------------------------------
+
+def _grid_oracle(nx=16, nz=16):
+    w = workload("tiny", nx=nx, nz=nz, slab_k=nz, laser_profile=0)
+    return oracle.Oracle(w, with_particles=False)
+
+
+def test_uniform_lattice_gives_zero_force():
+    """A uniform lattice has zero density gradient, hence Eq. (2) gives equal distances on
+    both sides and the pair force vanishes exactly, at every particle position."""
+    nx, nz = 16, 12
+    o = oracle.Oracle(workload("tiny", nx=nx, nz=nz, slab_k=nz, laser_profile=0), with_particles=False)
+    rng = np.random.default_rng(0)
+    n = nx * nz * 4
+    cell = np.repeat(np.arange(nx * nz), 4)
+    fx = np.tile(rng.random(4), nx * nz)            # the same 4 x-offsets in every cell
+    x = cell % nx + fx
+    z = cell // nx + 0.5                             # cell centres in z (mirror walls)
+    o.set_particles(0, x, z, np.zeros(n), np.zeros(n), np.zeros(n))
+    rho = o.get_rho()
+    inner = rho[1:nz]
+    assert (inner == inner[0, 0]).all()
+    assert (2 * rho[0] == inner[0, 0]).all() and (2 * rho[nz] == inner[0, 0]).all()
+    F = o.pair_force()
+    assert not F.any()
+
+
+def test_gather_reproduces_linear_density():
+    """The interpolated density of a grid that is linear in x and z is the linear function
+    itself, and the interpolated gradient is its slope (self-consistent interpolation)."""
+    o = _grid_oracle(16, 16)
+    nz, nx = 16, 16
+    k, i = np.mgrid[0:nz + 1, 0:nx]
+    a, bx, bz = 2 ** 34, 2 ** 28, 3 * 2 ** 27
+    lin = a + bx * np.minimum(i, 12) + bz * k          # linear away from the periodic seam
+    rho = lin.copy()
+    rho[0] //= 2
+    rho[nz] //= 2                                    # undo the wall mirror factor
+    o.set_rho(rho)
+    s = o.rho_scale
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        x = rng.uniform(0.0, 11.99)
+        z = rng.uniform(0.0, 15.99)
+        n, dnx, dnz = o.gather_density(x, z)
+        assert n == pytest.approx((a + bx * x + bz * z) * s, rel=1e-13)
+        assert dnx == pytest.approx(bx * s, rel=1e-12)
+        assert dnz == pytest.approx(bz * s, rel=1e-12)
+
+
+def test_pair_force_first_order_closed_form_and_sign():
+    """For a small gradient, Eqs. (1)-(3) reduce to F = U''(rbar) * (a - b) with
+    a - b = rbar g (to first order): F_x ~ -(1/3) U''(rbar) rbar n^(-4/3) dn/dx. Atoms in a
+    compressed region (rbar < r0) are pushed down the density gradient."""
+    o = _grid_oracle(16, 16)
+    nz, nx = 16, 16
+    k, i = np.mgrid[0:nz + 1, 0:nx]
+    s = o.rho_scale
+    r0_dx = o.phys.get("r0") or (o.phys["n_atoms"] ** (-1 / 3))
+    r0_dx = r0_dx / o.phys["dx"]
+    D = o.phys["D_eV"] * QE
+    r0 = r0_dx * o.phys["dx"]
+    for n_a, slope in ((1.2, 1e-4), (0.9, -2e-4), (1.0, 5e-5), (0.5, 1e-4)):
+        grid = np.rint((n_a + slope * np.minimum(i, 12)) / s).astype(np.int64)
+        grid[0] //= 2
+        grid[nz] //= 2
+        o.set_rho(grid)
+        x, z = 5.3, 7.6
+        o.set_particles(0, [x], [z], [0.0], [0.0], [0.0])
+        o.set_rho(grid)
+        F = o.pair_force()[0]
+        n, dnx, dnz = o.gather_density(x, z)
+        rbar = n ** (-1 / 3)
+        h = 1e-4
+        U2 = (oracle.lj_dU(rbar + h) - oracle.lj_dU(rbar - h)) / (2 * h)      # units D/r0^2
+        g = -(1 / 3) * dnx * n ** (-4 / 3) * r0_dx
+        F_lin = (D / r0) * U2 * rbar * g
+        assert F[0] == pytest.approx(F_lin, rel=2e-3)
+        assert F[1] == 0.0
+        if n_a > 1.0 and slope > 0:
+            assert F[0] < 0                            # compressed: pushed towards lower density
+        if n_a == 0.5:
+            assert F[0] > 0                            # beyond the inflection: pulled towards higher density
+
+
+# ---- Boris push -------------------------------------------------------------------------
+
+def test_boris_gyration_closed_form():
+    """In a uniform B along z, du/dt = w (u_y, -u_x) with w = q B / (m gamma): the Boris
+    rotation turns u by exactly -2 atan(w dt / 2) per step and keeps |u|."""
+    q, m, dt = -QE, ME, 2.24e-17
+    B = np.array([0.0, 0.0, 3000.0])
+    u = np.array([0.01, 0.0, 0.002])
+    g = math.sqrt(1 + u @ u)
+    theta = 2 * math.atan(q * B[2] * dt / (2 * m * g))
+    nstep = 500
+    for _ in range(nstep):
+        u = oracle.boris(q, m, dt, np.zeros(3), B, np.zeros(3), u)
+    ang = math.atan2(u[1], u[0])
+    expect = math.remainder(-nstep * theta, 2 * math.pi)
+    assert ang == pytest.approx(expect, abs=1e-10)
+    assert math.hypot(u[0], u[1]) == pytest.approx(0.01, rel=1e-13)
+    assert u[2] == 0.002
+
+
+def test_boris_pure_electric_and_pair_kicks():
+    """Without B, u grows linearly: du = (q E + F) dt / (m c) per step."""
+    q, m, dt = QE, 1.0552e-25, 2.24e-17
+    E = np.array([1e9, -2e8, 3e8])
+    F = np.array([1e-10, 0.0, -2e-10])
+    u = np.zeros(3)
+    for _ in range(10):
+        u = oracle.boris(q, m, dt, E, np.zeros(3), F, u)
+    np.testing.assert_allclose(u, 10 * (q * E + F) * dt / (m * C), rtol=1e-13)
+
+
+def test_boris_exb_drift():
+    """Crossed E and B: the mean velocity is E x B / B^2."""
+    q, m = -QE, ME
+    B = np.array([0.0, 0.0, 1000.0])
+    E = np.array([2e4, 0.0, 0.0])
+    wc = abs(q) * B[2] / m
+    dt = 0.05 / wc
+    u = np.zeros(3)
+    vs = []
+    for _ in range(40000):
+        u = oracle.boris(q, m, dt, E, B, np.zeros(3), u)
+        vs.append(u * C / math.sqrt(1 + u @ u))
+    v = np.mean(vs, axis=0)
+    vd = np.cross(E, B) / (B @ B)
+    assert v[1] == pytest.approx(vd[1], rel=2e-3)
+
+
+# ---- Maxwell (Yee) --------------------------------------------------------------------------
+
+def _vacuum(nx, nz, **kw):
+    w = workload("tiny", nx=nx, nz=nz, slab_k=nz // 2, laser_profile=0, **kw)
+    return oracle.Oracle(w, with_particles=False)
+
+
+@pytest.mark.parametrize("pol", ["TM", "TE"])
+def test_yee_vacuum_dispersion(pol):
+    """A Fourier mode along x obeys E^(n+1) + E^(n-1) = 2 cos(w dt) E^n with the Yee
+    dispersion relation sin(w dt/2) = (c dt / dx) sin(k dx / 2)."""
+    nx, nz = 16, 20
+    o = _vacuum(nx, nz)
+    kx = 2 * math.pi * 3 / nx
+    a = C * o.dt / o.phys["dx"]
+    two_cos = 2 - 4 * a * a * math.sin(kx / 2) ** 2
+    i = np.arange(nx)
+    rows = np.ones((nz + 1, 1))
+    if pol == "TM":
+        o.set_field(2, rows * np.cos(kx * i))                     # Ez
+        o.set_field(4, rows * 0.3 / C * np.sin(kx * (i + 0.5)))   # By
+        f = 2
+        sl = slice(0, nz)
+    else:
+        o.set_field(1, rows * np.cos(kx * i))                     # Ey
+        o.set_field(5, rows * -0.2 / C * np.sin(kx * (i + 0.5)))  # Bz
+        f = 1
+        sl = slice(4, nz - 3)                                     # away from the Mur rows
+    e0 = o.get_field(f)
+    o.step(1)
+    e1 = o.get_field(f)
+    o.step(1)
+    e2 = o.get_field(f)
+    np.testing.assert_allclose((e2 + e0)[sl], (two_cos * e1)[sl], atol=1e-12)
+
+
+def test_mur_absorbs_outgoing_pulse():
+    """A pulse leaving through the bottom wall is absorbed: under 1 % of its energy remains."""
+    nx, nz = 4, 160
+    o = _vacuum(nx, nz)
+    k = np.arange(nz + 1)[:, None] * np.ones((1, nx))
+    f = np.exp(-((k - 100.0) / 8.0) ** 2)
+    fh = np.exp(-((k + 0.5 - 100.0) / 8.0) ** 2)
+    o.set_field(0, 1e9 * f)                 # Ex
+    o.set_field(4, -1e9 / C * fh)           # By: E x B along -z
+    e_init = sum(v for key, v in o.energy().items() if key.startswith("field"))
+    o.step(260)
+    e_left = sum(v for key, v in o.energy().items() if key.startswith("field"))
+    assert e_left < 1e-2 * e_init
+
+
+def test_antenna_launches_the_requested_amplitude():
+    """The current-sheet antenna launches E0 = sqrt(2 I0 / (eps0 c)) towards the slab."""
+    nx, nz = 4, 300
+    w = workload("tiny", nx=nx, nz=nz, slab_k=100, laser_profile=1, I0=1e17, tau_fwhm=5e-15,
+                 t_peak=15e-15)
+    o = oracle.Oracle(w, with_particles=False)
+    E0 = math.sqrt(2 * 1e17 / (EPS0 * C))
+    peak = 0.0
+    for _ in range(1300 // 20):
+        o.step(20)
+        peak = max(peak, np.abs(o.get_field(0)[100]).max())
+    assert peak == pytest.approx(E0, rel=0.03)
+    # nothing leaks upwards past the top wall region
+    assert np.abs(o.get_field(0)[nz - 1]).max() < 0.05 * E0
+
+
+def test_gauss_law_is_preserved():
+    """Esirkepov deposition + Yee keep div E = rho / eps0 on the interior nodes when the
+    system starts neutral with E = 0 (plane-wave source carries no divergence)."""
+    w = workload("tiny", nx=16, nz=24, slab_k=12, ppc_ion=4, ppc_electron=4, T_electron_eV=50.0,
+                 I0=1e19, t_peak=20 * 2.24e-17)
+    o = oracle.Oracle(w)
+    o.step(40)
+    ions, els = o.get_particles(0), o.get_particles(1)
+    nx, nz, dx = 16, 24, w["dx"]
+    rq = oracle.deposit_density(nx, nz, ions["x"], ions["z"]) - oracle.deposit_density(nx, nz, els["x"], els["z"])
+    rho = rq * QE * o.weight / (2 ** 32 * dx * dx)
+    Ex, Ez = o.get_field(0), o.get_field(2)
+    div = (Ex - np.roll(Ex, 1, axis=1)) / dx
+    div[1:nz] += (Ez[1:nz] - Ez[0:nz - 1]) / dx
+    scale = np.abs(rho[1:nz] / EPS0).max()
+    assert scale > 0
+    np.testing.assert_allclose(div[1:nz], rho[1:nz] / EPS0, atol=1e-9 * scale)
+
+
+# ---- initial state, determinism, energy -------------------------------------------------
+
+def test_initial_state_statistics():
+    w = workload("tiny", nx=32, nz=16, slab_k=8, ppc_ion=16, ppc_electron=16, T_electron_eV=1.0)
+    o = oracle.Oracle(w)
+    ions, els = o.get_particles(0), o.get_particles(1)
+    assert len(ions["x"]) == 32 * 8 * 16
+    assert np.array_equal(ions["x"], els["x"]) and np.array_equal(ions["z"], els["z"])
+    assert ions["z"].max() < 8 and ions["z"].min() >= 0
+    cell = np.floor(ions["z"]).astype(int) * 32 + np.floor(ions["x"]).astype(int)
+    assert np.array_equal(np.bincount(cell, minlength=256), np.full(256, 16))
+    uth = math.sqrt(1.0 * QE / (ME * C * C))
+    for comp in ("ux", "uy", "uz"):
+        v = els[comp]
+        assert abs(v.mean()) < 4 * uth / math.sqrt(len(v))
+        assert v.std() == pytest.approx(uth, rel=0.06)
+    assert o.get_rho().sum() == len(ions["x"]) * 2 ** 32
+
+
+def test_determinism_same_seed():
+    w = workload("tiny", nx=16, nz=16, slab_k=8)
+    a, b = oracle.Oracle(w), oracle.Oracle(w)
+    a.step(3)
+    b.step(3)
+    for sp in (0, 1):
+        pa, pb = a.get_particles(sp), b.get_particles(sp)
+        for key in pa:
+            assert np.array_equal(pa[key], pb[key])
+    assert np.array_equal(a.get_field(0), b.get_field(0))
+
+
+def test_transport_mode_energy_bounded_and_converged():
+    """Paper: the pair-potential cycle is stable and energy conserving for long runs. A hot
+    neutral slab in the transport mode relaxes from its random start and then keeps its total
+    energy bounded (no secular growth), and halving the time step changes the energy history by
+    far less than the relaxation itself (the time integration is converged)."""
+    w = workload("transport", nx=16, nz=16, slab_k=8, ppc_ion=8)
+    totals = {}
+    for dt in (12e-15, 6e-15):
+        o = oracle.Oracle(dict(w, dt_override=dt))
+        e0 = o.energy()
+        ke0 = e0["kinetic_ion"]
+        tot0 = e0["kinetic_ion"] + e0["pair"]
+        nst = int(round(300e-15 / dt))
+        hist = []
+        for _ in range(16):
+            o.step(nst)
+            e = o.energy()
+            hist.append(e["kinetic_ion"] + e["pair"] - tot0)
+        totals[dt] = np.array(hist)
+    h = totals[12e-15]
+    second = h[8:]
+    assert second.max() - second.min() < 0.1 * ke0
+    assert np.abs(h).max() < 0.5 * ke0
+    assert np.abs(totals[12e-15] - totals[6e-15]).max() < 0.01 * ke0
+
+
+def test_kinetic_energy_matches_temperature():
+    """The Maxwellian start carries (3/2) k T per particle (non-relativistic temperatures)."""
+    w = workload("tiny", nx=32, nz=16, slab_k=16, ppc_ion=16, ppc_electron=16, T_electron_eV=2.0,
+                 T_ion_K=500.0, laser_profile=0)
+    o = oracle.Oracle(w)
+    e = o.energy()
+    n = o.num_particles(0)
+    kT_e = 2.0 * QE
+    kT_i = 1.380649e-23 * 500.0
+    assert e["kinetic_electron"] == pytest.approx(1.5 * kT_e * n * o.weight, rel=0.03)
+    assert e["kinetic_ion"] == pytest.approx(1.5 * kT_i * n * o.weight, rel=0.03)
+
+
+def test_field_energy_of_uniform_fields():
+    """A uniform field fills the nx * nz cells: energy (eps0 E^2 / 2 + B^2 / (2 mu0)) * area."""
+    nx, nz = 8, 10
+    o = _vacuum(nx, nz)
+    dx = o.phys["dx"]
+    for f in range(6):
+        o.set_field(f, np.full((nz + 1, nx), 1e8 if f < 3 else 0.5))
+    e = o.energy()
+    area = nx * nz * dx * dx
+    assert e["field_E"] == pytest.approx(3 * 0.5 * EPS0 * 1e16 * area, rel=1e-13)
+    mu0 = 1.0 / (EPS0 * C * C)
+    assert e["field_B"] == pytest.approx(3 * 0.25 / (2 * mu0) * area, rel=1e-13)
+
+
+def test_pair_energy_of_equilibrium_lattice():
+    """At the equilibrium density every atom has its six cubic-lattice neighbours at r0:
+    pair energy per atom = (1/2) * 6 * U(r0) = -3 D."""
+    nx, nz = 16, 12
+    o = oracle.Oracle(workload("tiny", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, laser_profile=0),
+                      with_particles=False)
+    n = nx * nz * 4
+    cell = np.repeat(np.arange(nx * nz), 4)
+    x = cell % nx + np.tile([0.1, 0.35, 0.6, 0.85], nx * nz)
+    z = cell // nx + 0.5
+    o.set_particles(0, x, z, np.zeros(n), np.zeros(n), np.zeros(n))
+    D = 0.41 * QE
+    assert o.energy()["pair"] == pytest.approx(-3 * D * n * o.weight, rel=1e-12)
+
+
+def test_jy_current_drives_ey():
+    """A uniform electron drift along y is a current J_y = -e n v_y; Ampere's law gives
+    E_y = -dt J_y / eps0 after the first step from rest (B = 0)."""
+    nx, nz = 8, 12
+    w = workload("tiny", nx=nx, nz=nz, slab_k=12, ppc_ion=4, ppc_electron=4, laser_profile=0,
+                 T_ion_K=0.0, T_electron_eV=0.0)
+    o = oracle.Oracle(w)
+    els = o.get_particles(1)
+    uy = np.float32(0.004)
+    n = len(els["x"])
+    o.set_particles(1, els["x"], els["z"], np.zeros(n), np.full(n, float(uy)), np.zeros(n))
+    V = oracle.jy_code(0.0, uy, 0.0)
+    vy = C * V / 2 ** 18                                  # the deposited (coded) velocity
+    rho_e = oracle.deposit_density(nx, nz, els["x"], els["z"])
+    n_e = rho_e * o.weight / (2 ** 32 * w["dx"] ** 2)
+    o.step(1)
+    Ey = o.get_field(1)
+    expect = o.dt * QE * n_e * vy / EPS0
+    np.testing.assert_allclose(Ey[1:nz], expect[1:nz], rtol=1e-12)
