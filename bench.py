@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Throughput of the full PIC cycle with the pair-potential force on a synthetic copper slab.
+
+Default workload: 2048 x 2048 cells of 10 nm, slab depth 1024 cells, 32 Cu+ and 32 electron
+macroparticles per slab cell (134,217,728 particles), 800 nm pulse focused to a 2 um waist at
+5e13 W/cm^2. A step is one full cycle (pair force + Lorentz push + current and density
+deposition + Maxwell update) over every particle. The metric is macroparticle updates per second
+over all GPUs; each GPU runs its own slab (replicas: the method has no data exchange between
+independent slabs).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "macroparticle-updates/s per full PIC step w/ pair force; % of HBM roofline"
+UNIT = "macroparticle-updates/s"
+
+# Algorithmic bytes of the particle kernel (one launch = one step over all particles):
+#   per particle: read + write of the 24-byte SoA record            48 B
+#   per node:     E, B read (6 x 4 B), node density read (8 B), node density written (8 B),
+#                 current written (3 x 8 B)                           64 B
+BYTES_PER_PARTICLE = 48
+BYTES_PER_NODE = 64
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large2d")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the particle kernel from a committed ncu summary, if the kernel
+    source has not changed since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "particle_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    for name in ("particles.cu", "pic_device.cuh", "pic_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1502_07722_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if d.get("source_sha256") != h.hexdigest():
+        return None
+    return d
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, device_index):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_1502_07722_gb300.workloads import workload
+    w = workload(args.workload)
+    sample = dict(w, nx=128, nz=128, slab_k=64, w0=min(w.get("w0", 0.0), 0.5e-6) if w.get("w0") else 0.0)
+    o = oracle.Oracle(sample)
+    n = sum(o.num_particles(s) for s in range(o.nspecies))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    desc = (f"FP64 C oracle, 1 thread, {args.steps} steps of a 128 x 128-cell strip of the '{args.workload}' "
+            f"workload (same cell size, ppc, dt and laser intensity; {n} particles)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "sample": "128x128 cells, slab 64 rows"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args):
+    import oracle
+    from paper_1502_07722_gb300.workloads import workload
+    w = workload(args.workload)
+    sample = dict(w, nx=128, nz=128, slab_k=64, w0=min(w.get("w0", 0.0), 0.5e-6) if w.get("w0") else 0.0)
+    o = oracle.Oracle(sample)
+    n = sum(o.num_particles(s) for s in range(o.nspecies))
+    o.step(1)
+    steps = 6
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of a 128 x 128-cell strip of '{args.workload}' (slab 64 rows, same ppc, "
+                      f"dx, dt, laser intensity; {n} particles), single-threaded FP64 C"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1502_07722_gb300 as gb
+    from paper_1502_07722_gb300 import _build
+    from paper_1502_07722_gb300.workloads import workload
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    gb.load_library()
+
+    w = workload(args.workload, seed=workload(args.workload)["seed"] + 1000 * rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = gb.Simulation(w, stream=stream, sort_every=w.get("sort_every", 20))
+    info = sim.info()
+    n_local = sum(info["num_particles"])
+    nodes = (w["nz"] + 1) * w["nx"]
+
+    sim.step(args.warmup)
+    gb.pic_set_timing(sim.h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler() as clk:
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kms, kn = gb.pic_get_timing(sim.h)
+    gb.pic_set_timing(sim.h, False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n_local * world * args.steps / (ms_max * 1e-3)
+
+    # roofline of the particle kernel (the dominant kernel)
+    peak, peak_kind = peaks()
+    k_ms = kms[0] / max(kn[0], 1)
+    alg_bytes = BYTES_PER_PARTICLE * n_local + BYTES_PER_NODE * nodes
+    achieved = alg_bytes / (k_ms * 1e-3) / 1e9
+    tr = kernel_traffic()
+    traffic = None
+    if tr is not None and tr.get("workload") == args.workload:
+        traffic = tr["dram_bytes_per_launch"]
+
+    # end to end through the C ABI with host buffers: upload the state from pinned host memory,
+    # step with a status read back every step, download the node density map
+    e2e = None
+    if not args.no_e2e:
+        host = [sim.get_particles(s) for s in range(sim.nspecies)]
+        pinned = [{k: v.cpu().pin_memory() for k, v in h.items()} for h in host]
+        dens_host = torch.empty((w["nz"] + 1, w["nx"]), dtype=torch.int64).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for h in pinned for v in h.values())
+        d2h = 4 * args.steps + dens_host.numel() * 8
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for s, h in enumerate(pinned):
+            gb.pic_set_particles(sim.h, s, h["cell"].numel(),
+                                 [h[k].data_ptr() for k in ("cell", "fx", "fz", "ux", "uy", "uz")], True)
+        for _ in range(args.steps):
+            gb.pic_step(sim.h, 1)
+        gb.pic_get_density(sim.h, dens_host.data_ptr(), True)
+        e2e_s = time.perf_counter() - t0
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": n_local * world * args.steps / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "pinned host state uploaded once per job of K steps (bytes amortised per step), "
+                       "status word read back every step, node density downloaded at the end"}
+
+    if rank == 0:
+        clocks = clk.summary(torch.cuda.current_device())
+        cpu = cpu_baseline(args) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic copper slab (seeded Maxwellian start), one independent slab per GPU",
+            "config": {"workload": args.workload, "nx": w["nx"], "nz": w["nz"], "slab_k": w["slab_k"],
+                       "ppc": [w["ppc_ion"], w["ppc_electron"]], "particles_per_gpu": n_local,
+                       "tile": sim.cfg.tile or 16, "sort_every": sim.cfg.sort_every,
+                       "l2": "inputs larger than L2 (particle state %.1f GB)" % (24 * n_local / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_particles",
+                         "peak_source": peak_kind, "kernel_ms": k_ms,
+                         "alg_bytes_per_launch": alg_bytes},
+            "kernel_ms_per_step": {"particles": k_ms, "fields": kms[1] / max(args.steps, 1),
+                                   "sort": kms[2] / max(args.steps, 1)},
+            "gpu_launches": int(kn[3]),
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * pic.h -- C ABI of the GB300 particle-in-cell cycle with the pair-potential force of
+ * Mitchell, Schumacher & Chowdhury, "Modeling crater formation in femtosecond-pulse laser
+ * damage from basic principles" (arXiv:1502.07722).
+ *
+ * One simulation = one context (pic_ctx) on the current CUDA device. The library computes every
+ * step of the cycle in its own CUDA kernels (sm_103a). It never allocates device memory: the
+ * caller hands it one device workspace of pic_workspace_size() bytes (the Python binding takes
+ * it from PyTorch's allocator) and a CUDA stream. All work is queued on that stream.
+ *
+ * Geometry (paper: 2D simulation with three-component vectors, positions in-plane):
+ *   cells (i, k), i = 0..nx-1 along x (periodic), k = 0..nz-1 along z (walls at z = 0, nz).
+ *   Node rows k = 0..nz; grids are (nz+1) x nx, row-major (index k*nx + i), even for the
+ *   half-row components (their row nz is unused).
+ *   Yee positions: Ex (i+1/2,k)  Ey (i,k)  Ez (i,k+1/2)  Bx (i,k+1/2)  By (i+1/2,k+1/2)  Bz (i+1/2,k).
+ *   A particle is (cell = k*nx + i, fx, fz in [0,1), ux, uy, uz = gamma v / c), FP32.
+ *   Species 0: Cu ions (or neutral atoms in the transport mode) -- the pair-potential species.
+ *   Species 1: electrons (full mode only).
+ *
+ * Fixed point: a coordinate x (cells) deposits with X = i*2^16 + rint(f * 2^16); node weight
+ * S_j = max(0, 2^16 - |X - 2^16 j|). Node sums are int64 and exact, so they are identical for
+ * any summation order (deterministic) and bit-comparable with a CPU reference.
+ *
+ * Return codes: 0 on success, a negative PIC_E* code on error. Errors raised inside kernels
+ * (non-finite momentum, a move of a cell or more) are sticky: pic_step reports them and every
+ * later call on the context returns them until pic_free.
+ */
+#ifndef GBPIC_PIC_H
+#define GBPIC_PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PIC_API __attribute__((visibility("default")))
+#else
+#define PIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PIC_OK = 0,
+    PIC_EINVAL = -1,     /* bad argument or configuration                                  */
+    PIC_ENOMEM = -2,     /* workspace too small / particle count above capacity            */
+    PIC_ECUDA = -3,      /* a CUDA runtime call failed                                     */
+    PIC_ENAN = -4,       /* a particle momentum became non-finite                          */
+    PIC_EMOVE = -5,      /* a particle moved a cell or more in one step (CFL is violated)  */
+    PIC_ESTATE = -6      /* call not valid in this mode (e.g. fields in transport mode)    */
+};
+
+enum { PIC_MODE_FULL = 0, PIC_MODE_TRANSPORT = 1 };
+enum { PIC_LASER_NONE = 0, PIC_LASER_PLANE = 1, PIC_LASER_GAUSSIAN = 2 };
+enum { PIC_EX = 0, PIC_EY = 1, PIC_EZ = 2, PIC_BX = 3, PIC_BY = 4, PIC_BZ = 5 };
+
+/* Physical inputs. Derived quantities (dt, weights, E0, ...) are computed by pic_init. */
+typedef struct pic_config {
+    int32_t nx, nz;          /* cells along x (periodic) and z (walls); 3 <= n < 32768          */
+    int32_t slab_k;          /* the slab fills cell rows k < slab_k at init                     */
+    int32_t mode;            /* PIC_MODE_FULL: Cu+ ions, electrons, fields (ion_charge = 1);
+                                PIC_MODE_TRANSPORT: neutral atoms and the pair force only        */
+    int32_t ppc_ion, ppc_electron;   /* macroparticles per slab cell (equal in the full mode)   */
+    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (s_rep below r0, c_att above) */
+    int32_t laser_profile;   /* PIC_LASER_*                                                     */
+    int32_t tile;            /* tile edge in cells for particle binning (0: 16)                 */
+    int32_t sort_every;      /* steps between cell sorts (0: only after init / set_particles)  */
+    int64_t max_particles;   /* per-species capacity (0: the initial count)                    */
+    double dx;               /* cell size (m), square cells                                     */
+    double cfl;              /* dt = cfl * dx / (c sqrt 2) unless dt_override > 0               */
+    double dt_override;      /* s                                                               */
+    double n_atoms;          /* solid density (m^-3), paper: 8.5e22 cm^-3 for copper            */
+    double T_ion_K, T_electron_eV;   /* Maxwellian start                                        */
+    double ion_charge;       /* e units: 1 (full mode) or 0 (transport mode)                    */
+    double ion_mass_amu;
+    double D_eV;             /* Eq. (3) dissociation energy                                     */
+    double r0;               /* Eq. (3) equilibrium distance (m); <= 0: n_atoms^(-1/3)          */
+    double c_att, s_rep;     /* altered-potential factors (pot_mode 1)                          */
+    double lambda, I0, tau_fwhm, w0, t_peak;  /* laser: m, W/m^2, s (intensity FWHM), m, s:
+                                the pulse peak reaches the slab surface z = slab_k at t_peak    */
+    uint64_t seed;           /* initial-state generator seed                                    */
+} pic_config;
+
+typedef struct pic_info {
+    double dt;               /* s                                                               */
+    double weight;           /* real atoms (or electrons) per macroparticle, per metre of y     */
+    double rho_scale;        /* pair node sum -> density in units of n0 = r0^-3                  */
+    double r0;               /* m                                                               */
+    double time;             /* s, simulated time of the current state                          */
+    int64_t step;
+    int64_t num_particles[2];
+    int32_t nspecies;
+    int32_t ntiles;
+} pic_info;
+
+/* Energies in J per metre of y. Kinetic energies use the stored (half-step) momenta; field
+ * energy weights the wall node rows by 1/2; pair energy is, per atom, half the sum of U over its
+ * six cubic-lattice neighbours (+-x, +-z from Eq. 2, +-y at rbar). */
+typedef struct pic_energy_t {
+    double kinetic_ion, kinetic_electron, field_E, field_B, pair;
+    int64_t step;
+} pic_energy_t;
+
+typedef struct pic_ctx pic_ctx;
+
+/* Bytes of device workspace pic_init needs for cfg. */
+PIC_API int pic_workspace_size(const pic_config* cfg, size_t* bytes);
+
+/* Create a simulation on the current device: generate the initial slab (paper: the damage
+ * simulation is initialised for target density and temperature), sort it into tiles and
+ * deposit the initial node density. workspace: device pointer, 256-byte aligned, owned by the
+ * caller and kept alive until pic_free. stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out receives the context (host memory owned by the library). */
+PIC_API int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* stream, pic_ctx** out);
+
+/* Release the host-side context. The workspace stays the caller's. NULL is accepted. */
+PIC_API void pic_free(pic_ctx* ctx);
+
+/* Advance nsteps PIC cycles (paper: the PIC cycle is evaluated for each time step):
+ * node density -> pair force (Eqs. 1-3) -> Lorentz + pair push -> current deposition ->
+ * node density at the new positions -> Maxwell (Yee) update. Synchronises the stream at the end
+ * to read the sticky status word; returns it. */
+PIC_API int pic_step(pic_ctx* ctx, int32_t nsteps);
+
+/* Node density of the pair species at the current positions (paper: weights interpolated to
+ * the nearest surrounding nodes give the node density): dev_out receives (nz+1)*nx int64 sums
+ * in units 2^-32 of one macroparticle (device pointer, caller-owned). *scale_out (host, may be
+ * NULL) receives the factor from a sum to a density in m^-3. Recomputed from the particles. */
+PIC_API int pic_deposit_density(pic_ctx* ctx, int64_t* dev_out, double* scale_out);
+
+/* Pair-potential force (N, per atom) on every macro-ion from the current node density
+ * (paper: Eqs. 1-3, density and gradient interpolated back to the particle). dev_out:
+ * device float[3 * num_particles(0)], (Fx, Fy, Fz) per particle, in the context's particle order. */
+PIC_API int pic_pair_force(pic_ctx* ctx, float* dev_out);
+
+/* Total energies of the current state, FP64 reductions on the device (paper: the pair-potential
+ * cycle is energy conserving). Synchronises. host_out: host pointer. */
+PIC_API int pic_energy(pic_ctx* ctx, pic_energy_t* host_out);
+
+/* Scalars of the context. host_out: host pointer. */
+PIC_API int pic_get_info(pic_ctx* ctx, pic_info* host_out);
+
+/* Copy particles of one species out of / into the context, in the context's order. Pointers are
+ * host memory when on_host != 0 (the call then synchronises), device memory otherwise.
+ * pic_set_particles replaces the species (n <= capacity), re-sorts it into tiles (which
+ * permutes it: read it back with pic_get_particles) and re-deposits the node density. */
+PIC_API int pic_get_particles(pic_ctx* ctx, int32_t species, int32_t* cell, float* fx, float* fz,
+                      float* ux, float* uy, float* uz, int32_t on_host);
+PIC_API int pic_set_particles(pic_ctx* ctx, int32_t species, int64_t n, const int32_t* cell, const float* fx,
+                      const float* fz, const float* ux, const float* uy, const float* uz, int32_t on_host);
+
+/* One field component (PIC_EX..PIC_BZ), (nz+1)*nx FP32. */
+PIC_API int pic_get_field(pic_ctx* ctx, int32_t which, float* out, int32_t on_host);
+PIC_API int pic_set_field(pic_ctx* ctx, int32_t which, const float* in, int32_t on_host);
+
+/* Current of the last step, int64 fixed point, 3 planes of (nz+1)*nx: J2x at (i+1/2,k),
+ * J6y at (i,k), J2z at (i,k+1/2). J_x = J2x * e w / (2^33 dx dt) A/m^2 (per unit charge sign),
+ * J_y = J6y * e w c / (6 * 2^50 dx^2). */
+PIC_API int pic_get_current(pic_ctx* ctx, int64_t* out3, int32_t on_host);
+
+/* The node density the next step reads (pair species at the current positions). */
+PIC_API int pic_get_density(pic_ctx* ctx, int64_t* out, int32_t on_host);
+
+/* Sort both species by cell into tiles now (permutes the particle order). */
+PIC_API int pic_sort(pic_ctx* ctx);
+
+/* Per-kernel timing with CUDA events on the context stream. enable != 0 starts recording;
+ * pic_get_timing returns the summed milliseconds and launch counts since enabling:
+ * ms[0], n[0]: particle kernel; ms[1], n[1]: field kernels; ms[2], n[2]: sorts;
+ * n[3]: all kernels launched by pic_step. */
+PIC_API int pic_set_timing(pic_ctx* ctx, int32_t enable);
+PIC_API int pic_get_timing(pic_ctx* ctx, double ms[3], int64_t n[4]);
+
+/* Static text for a return code. */
+PIC_API const char* pic_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -19,11 +19,17 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 def build(force: bool = False) -> str:
     """Compile pic_oracle.c into liboracle.so (plain gcc, contraction off)."""
+    import platform
+    stamp = _LIB + ".arch"
+    if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
+        force = True
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(platform.machine() + "\n")
     return _LIB
 
 
@@ -73,6 +79,7 @@ def lib():
             "oracle_pair_force": (None, [vp, _D]),
             "oracle_gather_density": (None, [vp, ctypes.c_double, ctypes.c_double, _D]),
             "oracle_step": (None, [vp, ctypes.c_int32]),
+            "oracle_maxwell": (None, [vp]),
             "oracle_energy": (None, [vp, _D]),
             "oracle_laser_field": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double]),
             "oracle_lj_U": (ctypes.c_double, [ctypes.c_double]),
@@ -197,6 +204,9 @@ class Oracle:
     # physics
     def step(self, n=1):
         lib().oracle_step(self._s, int(n))
+
+    def maxwell(self):
+        lib().oracle_maxwell(self._s)
 
     def pair_force(self):
         n = self.num_particles(0)

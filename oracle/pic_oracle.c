@@ -638,6 +638,15 @@ static void push_particle(ostate* s, int sp, int64_t p)
     s->ux[sp][p] = u[0]; s->uy[sp][p] = u[1]; s->uz[sp][p] = u[2];
 }
 
+/* The Maxwell part of the cycle alone, from the stored current (for checking a field update
+ * against a current computed elsewhere). */
+void oracle_maxwell(ostate* s)
+{
+    half_step_B(s);
+    full_step_E(s);
+    half_step_B(s);
+}
+
 /* One PIC cycle (paper, PIC-cycle paragraph): pair force from the node density at x^n,
  * Lorentz + pair push, current from x^n -> x^(n+1), node density at x^(n+1), Maxwell. */
 void oracle_step(ostate* s, int32_t nsteps)

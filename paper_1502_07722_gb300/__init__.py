@@ -1,0 +1,298 @@
+"""GB300 particle-in-cell cycle with the pair-potential force of Mitchell, Schumacher & Chowdhury,
+"Modeling crater formation in femtosecond-pulse laser damage from basic principles"
+(arXiv:1502.07722).
+
+This module is a thin ctypes binding of the C ABI in include/pic.h (libgbpic.so, built for
+sm_103a by `_build.build()`). Every step of the cycle runs in the library's CUDA kernels; the
+binding only marshals arguments. PyTorch provides the device workspace and the stream.
+There is no CPU fallback: if the library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libgbpic.so")
+
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENAN, PIC_EMOVE, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PIC_MODE_FULL, PIC_MODE_TRANSPORT = 0, 1
+PIC_LASER_NONE, PIC_LASER_PLANE, PIC_LASER_GAUSSIAN = 0, 1, 2
+FIELDS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+
+
+class pic_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("nz", ctypes.c_int32), ("slab_k", ctypes.c_int32), ("mode", ctypes.c_int32),
+        ("ppc_ion", ctypes.c_int32), ("ppc_electron", ctypes.c_int32), ("pot_mode", ctypes.c_int32),
+        ("laser_profile", ctypes.c_int32), ("tile", ctypes.c_int32), ("sort_every", ctypes.c_int32),
+        ("max_particles", ctypes.c_int64),
+        ("dx", ctypes.c_double), ("cfl", ctypes.c_double), ("dt_override", ctypes.c_double),
+        ("n_atoms", ctypes.c_double), ("T_ion_K", ctypes.c_double), ("T_electron_eV", ctypes.c_double),
+        ("ion_charge", ctypes.c_double), ("ion_mass_amu", ctypes.c_double), ("D_eV", ctypes.c_double),
+        ("r0", ctypes.c_double), ("c_att", ctypes.c_double), ("s_rep", ctypes.c_double),
+        ("lambda_", ctypes.c_double), ("I0", ctypes.c_double), ("tau_fwhm", ctypes.c_double),
+        ("w0", ctypes.c_double), ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+class pic_info(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("weight", ctypes.c_double), ("rho_scale", ctypes.c_double),
+                ("r0", ctypes.c_double), ("time", ctypes.c_double), ("step", ctypes.c_int64),
+                ("num_particles", ctypes.c_int64 * 2), ("nspecies", ctypes.c_int32), ("ntiles", ctypes.c_int32)]
+
+
+class pic_energy_t(ctypes.Structure):
+    _fields_ = [("kinetic_ion", ctypes.c_double), ("kinetic_electron", ctypes.c_double),
+                ("field_E", ctypes.c_double), ("field_B", ctypes.c_double), ("pair", ctypes.c_double),
+                ("step", ctypes.c_int64)]
+
+
+# name -> (restype, argtypes) of every exported C entry point
+_VP = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_SIGNATURES = {
+    "pic_workspace_size": (ctypes.c_int, [ctypes.POINTER(pic_config), ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_init": (ctypes.c_int, [ctypes.POINTER(pic_config), _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "pic_free": (None, [_VP]),
+    "pic_step": (ctypes.c_int, [_VP, _I32]),
+    "pic_deposit_density": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
+    "pic_pair_force": (ctypes.c_int, [_VP, _VP]),
+    "pic_energy": (ctypes.c_int, [_VP, ctypes.POINTER(pic_energy_t)]),
+    "pic_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pic_info)]),
+    "pic_get_particles": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
+    "pic_set_particles": (ctypes.c_int, [_VP, _I32, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
+    "pic_get_field": (ctypes.c_int, [_VP, _I32, _VP, _I32]),
+    "pic_set_field": (ctypes.c_int, [_VP, _I32, _VP, _I32]),
+    "pic_get_current": (ctypes.c_int, [_VP, _VP, _I32]),
+    "pic_get_density": (ctypes.c_int, [_VP, _VP, _I32]),
+    "pic_sort": (ctypes.c_int, [_VP]),
+    "pic_set_timing": (ctypes.c_int, [_VP, _I32]),
+    "pic_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "pic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def load_library():
+    """Load libgbpic.so; raise if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"{LIBPATH} is missing: build it with paper_1502_07722_gb300._build.build()")
+        L = ctypes.CDLL(LIBPATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load_library().pic_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def _check(code, where):
+    if code != PIC_OK:
+        raise PicError(code, where)
+    return code
+
+
+def make_config(phys: dict, **over) -> pic_config:
+    """pic_config from a dict of physical inputs (see workloads.py)."""
+    d = dict(phys)
+    d.update(over)
+    c = pic_config()
+    for name, _ in pic_config._fields_:
+        key = "lambda" if name == "lambda_" else name
+        if key in d:
+            setattr(c, name, d[key])
+    return c
+
+
+# ---- C-ABI names, argument marshalling only -------------------------------------------------
+
+def pic_workspace_size(cfg: pic_config) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().pic_workspace_size(ctypes.byref(cfg), ctypes.byref(n)), "pic_workspace_size")
+    return n.value
+
+
+def pic_init(cfg: pic_config, workspace_ptr: int, workspace_bytes: int, stream_ptr: int):
+    h = _VP()
+    _check(load_library().pic_init(ctypes.byref(cfg), workspace_ptr, workspace_bytes, stream_ptr, ctypes.byref(h)),
+           "pic_init")
+    return h
+
+
+def pic_free(h):
+    load_library().pic_free(h)
+
+
+def pic_step(h, nsteps: int) -> int:
+    return _check(load_library().pic_step(h, int(nsteps)), "pic_step")
+
+
+def pic_deposit_density(h, dev_out_ptr: int) -> float:
+    s = ctypes.c_double()
+    _check(load_library().pic_deposit_density(h, dev_out_ptr, ctypes.byref(s)), "pic_deposit_density")
+    return s.value
+
+
+def pic_pair_force(h, dev_out_ptr: int):
+    _check(load_library().pic_pair_force(h, dev_out_ptr), "pic_pair_force")
+
+
+def pic_energy(h) -> dict:
+    e = pic_energy_t()
+    _check(load_library().pic_energy(h, ctypes.byref(e)), "pic_energy")
+    return {k: getattr(e, k) for k, _ in pic_energy_t._fields_}
+
+
+def pic_get_info(h) -> dict:
+    i = pic_info()
+    _check(load_library().pic_get_info(h, ctypes.byref(i)), "pic_get_info")
+    return dict(dt=i.dt, weight=i.weight, rho_scale=i.rho_scale, r0=i.r0, time=i.time, step=i.step,
+                num_particles=(i.num_particles[0], i.num_particles[1]), nspecies=i.nspecies, ntiles=i.ntiles)
+
+
+def pic_get_particles(h, species, ptrs, on_host):
+    _check(load_library().pic_get_particles(h, species, *ptrs, 1 if on_host else 0), "pic_get_particles")
+
+
+def pic_set_particles(h, species, n, ptrs, on_host):
+    _check(load_library().pic_set_particles(h, species, int(n), *ptrs, 1 if on_host else 0), "pic_set_particles")
+
+
+def pic_get_field(h, which, ptr, on_host):
+    _check(load_library().pic_get_field(h, which, ptr, 1 if on_host else 0), "pic_get_field")
+
+
+def pic_set_field(h, which, ptr, on_host):
+    _check(load_library().pic_set_field(h, which, ptr, 1 if on_host else 0), "pic_set_field")
+
+
+def pic_get_current(h, ptr, on_host):
+    _check(load_library().pic_get_current(h, ptr, 1 if on_host else 0), "pic_get_current")
+
+
+def pic_get_density(h, ptr, on_host):
+    _check(load_library().pic_get_density(h, ptr, 1 if on_host else 0), "pic_get_density")
+
+
+def pic_sort(h):
+    _check(load_library().pic_sort(h), "pic_sort")
+
+
+def pic_set_timing(h, enable):
+    _check(load_library().pic_set_timing(h, 1 if enable else 0), "pic_set_timing")
+
+
+def pic_get_timing(h):
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 4)()
+    _check(load_library().pic_get_timing(h, ms, n), "pic_get_timing")
+    return list(ms), list(n)
+
+
+# ---- convenience wrapper: torch owns the workspace and the stream -----------------------------
+
+class Simulation:
+    """One simulation on the current CUDA device; device memory comes from torch."""
+
+    def __init__(self, phys: dict, stream=None, **over):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.torch = torch
+        self.cfg = make_config(phys, **over)
+        nbytes = pic_workspace_size(self.cfg)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = pic_init(self.cfg, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        info = self.info()
+        self.nx, self.nz = self.cfg.nx, self.cfg.nz
+        self.nspecies = info["nspecies"]
+
+    def close(self):
+        if getattr(self, "h", None):
+            pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return pic_get_info(self.h)
+
+    def step(self, n=1):
+        return pic_step(self.h, n)
+
+    def energy(self):
+        return pic_energy(self.h)
+
+    def sort(self):
+        pic_sort(self.h)
+
+    def _grid(self, dtype):
+        return self.torch.empty((self.nz + 1, self.nx), dtype=dtype, device="cuda")
+
+    def deposit_density(self):
+        out = self._grid(self.torch.int64)
+        scale = pic_deposit_density(self.h, out.data_ptr())
+        return out, scale
+
+    def pair_force(self):
+        n = self.info()["num_particles"][0]
+        out = self.torch.empty((n, 3), dtype=self.torch.float32, device="cuda")
+        pic_pair_force(self.h, out.data_ptr())
+        return out
+
+    def get_particles(self, species):
+        n = self.info()["num_particles"][species]
+        t = self.torch
+        arrs = [t.empty(n, dtype=t.int32, device="cuda")] + [t.empty(n, dtype=t.float32, device="cuda") for _ in range(5)]
+        if n:
+            pic_get_particles(self.h, species, [a.data_ptr() for a in arrs], False)
+        self.stream.synchronize()
+        return dict(zip(("cell", "fx", "fz", "ux", "uy", "uz"), arrs))
+
+    def set_particles(self, species, cell, fx, fz, ux, uy, uz):
+        t = self.torch
+        arrs = [t.as_tensor(cell, dtype=t.int32).cuda().contiguous()] + \
+               [t.as_tensor(a, dtype=t.float32).cuda().contiguous() for a in (fx, fz, ux, uy, uz)]
+        self.stream.synchronize()
+        pic_set_particles(self.h, species, arrs[0].numel(), [a.data_ptr() for a in arrs], False)
+
+    def get_field(self, which):
+        out = self._grid(self.torch.float32)
+        pic_get_field(self.h, which, out.data_ptr(), False)
+        self.stream.synchronize()
+        return out
+
+    def set_field(self, which, values):
+        v = self.torch.as_tensor(values, dtype=self.torch.float32).cuda().contiguous()
+        assert v.numel() == (self.nz + 1) * self.nx
+        self.stream.synchronize()
+        pic_set_field(self.h, which, v.data_ptr(), False)
+
+    def get_current(self):
+        out = self.torch.empty((3, self.nz + 1, self.nx), dtype=self.torch.int64, device="cuda")
+        pic_get_current(self.h, out.data_ptr(), False)
+        self.stream.synchronize()
+        return out
+
+    def get_density(self):
+        out = self._grid(self.torch.int64)
+        pic_get_density(self.h, out.data_ptr(), False)
+        self.stream.synchronize()
+        return out

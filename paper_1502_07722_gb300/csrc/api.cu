@@ -1,0 +1,604 @@
+// Host side of the C ABI declared in include/pic.h: configuration, workspace layout, the step
+// loop and data movement. Every operation of the cycle itself runs in the kernels of this
+// directory; nothing here computes on particles or grids.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+int tile_window(int T);
+int energy_blocks(const Ctx& c);
+void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* launches);
+}  // namespace gbpic
+
+using namespace gbpic;
+
+struct pic_ctx {
+    Ctx c;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<int> evkind;    // 0 particle, 1 fields, 2 sort (pairs of events)
+};
+
+#define CK(x)                                              \
+    do {                                                   \
+        cudaError_t e_ = (x);                              \
+        if (e_ != cudaSuccess) return PIC_ECUDA;           \
+    } while (0)
+
+namespace {
+
+constexpr int kMaxEnergyBlocks = 1024;
+
+struct Layout {
+    int32_t nx, nz, T, ntx, ntz, ntiles, nkeys, nsp;
+    size_t nn;
+    int64_t cap[2], n0[2];
+    size_t total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int derive_layout(const pic_config* cfg, Layout& L)
+{
+    if (!cfg) return PIC_EINVAL;
+    if (cfg->nx < 3 || cfg->nz < 4 || cfg->nx >= 32768 || cfg->nz >= 32768) return PIC_EINVAL;
+    if (cfg->slab_k < 0 || cfg->slab_k > cfg->nz) return PIC_EINVAL;
+    if (cfg->mode != PIC_MODE_FULL && cfg->mode != PIC_MODE_TRANSPORT) return PIC_EINVAL;
+    if (cfg->ppc_ion < 0 || cfg->ppc_electron < 0) return PIC_EINVAL;
+    if (!(cfg->dx > 0) || !(cfg->n_atoms > 0) || !(cfg->ion_mass_amu > 0)) return PIC_EINVAL;
+    if (cfg->dt_override <= 0 && !(cfg->cfl > 0 && cfg->cfl <= 1.0)) return PIC_EINVAL;
+    if (cfg->mode == PIC_MODE_FULL) {
+        if (cfg->ion_charge != 1.0) return PIC_EINVAL;            // equal |q| w across species
+        if (cfg->ppc_electron != cfg->ppc_ion) return PIC_EINVAL;
+    } else if (cfg->ion_charge != 0.0) {
+        return PIC_EINVAL;
+    }
+    if (cfg->laser_profile < 0 || cfg->laser_profile > 2) return PIC_EINVAL;
+    if (cfg->laser_profile != PIC_LASER_NONE && cfg->mode == PIC_MODE_FULL &&
+        !(cfg->lambda > 0 && cfg->tau_fwhm > 0))
+        return PIC_EINVAL;
+    if (cfg->laser_profile == PIC_LASER_GAUSSIAN && !(cfg->w0 > 0)) return PIC_EINVAL;
+    if (cfg->pot_mode != 0 && cfg->pot_mode != 1) return PIC_EINVAL;
+    L.nx = cfg->nx;
+    L.nz = cfg->nz;
+    L.T = cfg->tile > 0 ? cfg->tile : 16;
+    if (L.T < 2 || L.T > 64) return PIC_EINVAL;
+    L.ntx = (L.nx + L.T - 1) / L.T;
+    L.ntz = (L.nz + L.T - 1) / L.T;
+    L.ntiles = L.ntx * L.ntz;
+    const int64_t nkeys = (int64_t)L.ntiles * L.T * L.T;
+    if (nkeys >= (1LL << 31) - 1) return PIC_EINVAL;
+    L.nkeys = (int32_t)nkeys;
+    L.nn = (size_t)L.nx * (L.nz + 1);
+    L.nsp = cfg->mode == PIC_MODE_FULL ? 2 : 1;
+    const int64_t ncell = (int64_t)cfg->nx * cfg->slab_k;
+    for (int s = 0; s < 2; s++) {
+        const int ppc = s == 0 ? cfg->ppc_ion : cfg->ppc_electron;
+        L.n0[s] = s < L.nsp ? ncell * ppc : 0;
+        L.cap[s] = s < L.nsp ? (cfg->max_particles > 0 ? cfg->max_particles : L.n0[s]) : 0;
+        if (L.cap[s] < L.n0[s] || L.cap[s] >= (1LL << 31)) return PIC_EINVAL;
+    }
+    size_t t = 0;
+    for (int s = 0; s < 2; s++) t += 2 * 6 * align256(4 * (size_t)L.cap[s]) + align256(4 * (size_t)(L.ntiles + 1));
+    t += 6 * align256(4 * L.nn) + 5 * align256(8 * L.nn);
+    t += align256(4 * 8 * (size_t)L.nx) + 2 * align256(4 * (size_t)L.nx);
+    t += 2 * align256(4 * ((size_t)L.nkeys + 1));
+    t += align256(4 * (((size_t)L.nkeys + 2047) / 2048 + 1));
+    t += align256(8 * 5 * (size_t)kMaxEnergyBlocks) + align256(8 * 8) + align256(16);
+    L.total = t;
+    return PIC_OK;
+}
+
+struct Carver {
+    char* p;
+    char* end;
+    template <class T>
+    T* take(size_t count)
+    {
+        T* r = reinterpret_cast<T*>(p);
+        p += align256(sizeof(T) * count);
+        return r;
+    }
+};
+
+int finish_status(pic_ctx* h)
+{
+    Ctx& c = h->c;
+    unsigned st = 0;
+    CK(cudaMemcpyAsync(&st, c.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (c.timing) {
+        for (size_t j = 0; j + 1 < h->evpool.size() && j / 2 < h->evkind.size(); j += 2) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->evpool[j], h->evpool[j + 1]));
+            const int kind = h->evkind[j / 2];
+            c.ms[kind] += ms;
+        }
+        h->evkind.clear();
+    }
+    if (st & kErrNan) c.sticky = PIC_ENAN;
+    else if (st & kErrMove) c.sticky = PIC_EMOVE;
+    return c.sticky;
+}
+
+int ev_begin(pic_ctx* h, int kind)
+{
+    if (!h->c.timing) return PIC_OK;
+    const size_t j = 2 * h->evkind.size();
+    while (h->evpool.size() < j + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->evpool.push_back(e);
+    }
+    h->evkind.push_back(kind);
+    CK(cudaEventRecord(h->evpool[j], h->c.stream));
+    return PIC_OK;
+}
+
+int ev_end(pic_ctx* h)
+{
+    if (!h->c.timing) return PIC_OK;
+    const size_t j = 2 * h->evkind.size() - 1;
+    CK(cudaEventRecord(h->evpool[j], h->c.stream));
+    return PIC_OK;
+}
+
+int sort_all(pic_ctx* h)
+{
+    Ctx& c = h->c;
+    int r = ev_begin(h, 2);
+    if (r) return r;
+    const int64_t before = c.nlaunch[2];
+    for (int s = 0; s < c.nsp; s++) launch_sort_species(c, s, c.stream, &c.nlaunch[2]);
+    c.nlaunch[3] += c.nlaunch[2] - before;
+    r = ev_end(h);
+    if (r) return r;
+    CK(cudaGetLastError());
+    c.steps_since_sort = 0;
+    return PIC_OK;
+}
+
+int redeposit(Ctx& c)
+{
+    launch_deposit_density(c, c.rho[c.cur], c.stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+}  // namespace
+
+namespace gbpic {
+
+StepArgs make_step_args(Ctx& c)
+{
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nx = c.nx;
+    a.nz = c.nz;
+    a.T = c.T;
+    a.ntx = c.ntx;
+    a.ntz = c.ntz;
+    a.ntiles = c.ntiles;
+    a.W = c.W;
+    a.full = c.cfg.mode == PIC_MODE_FULL;
+    a.cdt_dx = (float)(kC * c.dt / c.cfg.dx);
+    a.rho_s = (float)c.rho_scale;
+    a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
+    a.pot_mode = c.cfg.pot_mode;
+    a.c_att = (float)c.cfg.c_att;
+    a.s_rep = (float)c.cfg.s_rep;
+    for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
+    a.rho_cur = c.rho[c.cur];
+    a.rho_next = c.rho[1 - c.cur];
+    for (int q = 0; q < 3; q++) a.J[q] = c.J[q];
+    a.status = c.status;
+    a.nsp = c.nsp;
+    for (int s = 0; s < 2; s++) a.sp[s] = c.sp[s];
+    return a;
+}
+
+}  // namespace gbpic
+
+extern "C" {
+
+int pic_workspace_size(const pic_config* cfg, size_t* bytes)
+{
+    if (!bytes) return PIC_EINVAL;
+    Layout L;
+    int r = derive_layout(cfg, L);
+    if (r) return r;
+    *bytes = L.total;
+    return PIC_OK;
+}
+
+int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* stream, pic_ctx** out)
+{
+    if (!out) return PIC_EINVAL;
+    *out = nullptr;
+    Layout L;
+    int r = derive_layout(cfg, L);
+    if (r) return r;
+    if (!workspace || ((uintptr_t)workspace & 255)) return PIC_EINVAL;
+    if (workspace_bytes < L.total) return PIC_ENOMEM;
+    pic_ctx* h = new (std::nothrow) pic_ctx();
+    if (!h) return PIC_ENOMEM;
+    Ctx& c = h->c;
+    c.cfg = *cfg;
+    c.stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) {
+        delete h;
+        return PIC_ECUDA;
+    }
+    c.nx = L.nx;
+    c.nz = L.nz;
+    c.T = L.T;
+    c.ntx = L.ntx;
+    c.ntz = L.ntz;
+    c.ntiles = L.ntiles;
+    c.W = tile_window(L.T);
+    c.nkeys = L.nkeys;
+    c.nn = L.nn;
+    c.nsp = L.nsp;
+    c.k_ant = L.nz - 2;
+    // derived physics
+    c.dt = cfg->dt_override > 0 ? cfg->dt_override : cfg->cfl * cfg->dx / (kC * sqrt(2.0));
+    c.w = cfg->n_atoms * cfg->dx * cfg->dx / (double)(cfg->ppc_ion > 0 ? cfg->ppc_ion : 1);
+    c.r0 = cfg->r0 > 0 ? cfg->r0 : pow(cfg->n_atoms, -1.0 / 3.0);
+    c.D = cfg->D_eV * kQe;
+    c.rho_scale = c.w / (4294967296.0 * cfg->dx * cfg->dx) * c.r0 * c.r0 * c.r0;
+    c.E0 = sqrt(2.0 * cfg->I0 / (kEps0 * kC));
+    c.omega = cfg->lambda > 0 ? 2.0 * kPi * kC / cfg->lambda : 0.0;
+    const double Lant = (double)(c.k_ant - cfg->slab_k) * cfg->dx;
+    c.t_ant = cfg->t_peak - Lant / kC;
+    // workspace
+    Carver cv{(char*)workspace, (char*)workspace + workspace_bytes};
+    for (int s = 0; s < 2; s++) {
+        Species& S = c.sp[s];
+        memset(&S, 0, sizeof(S));
+        SpeciesBuf* bufs[2] = {&S.a, &S.b};
+        for (int b = 0; b < 2; b++) {
+            bufs[b]->cell = cv.take<int32_t>(L.cap[s]);
+            bufs[b]->fx = cv.take<float>(L.cap[s]);
+            bufs[b]->fz = cv.take<float>(L.cap[s]);
+            bufs[b]->ux = cv.take<float>(L.cap[s]);
+            bufs[b]->uy = cv.take<float>(L.cap[s]);
+            bufs[b]->uz = cv.take<float>(L.cap[s]);
+        }
+        S.tile_start = cv.take<int32_t>(L.ntiles + 1);
+        S.n = L.n0[s];
+        S.cap = L.cap[s];
+    }
+    for (int q = 0; q < 6; q++) c.F[q] = cv.take<float>(L.nn);
+    for (int q = 0; q < 3; q++) c.J[q] = cv.take<u64>(L.nn);
+    for (int q = 0; q < 2; q++) c.rho[q] = cv.take<u64>(L.nn);
+    c.mur_save = cv.take<float>(8 * (size_t)L.nx);
+    c.ant_c = cv.take<float>(L.nx);
+    c.ant_s = cv.take<float>(L.nx);
+    c.keys_count = cv.take<int32_t>((size_t)L.nkeys + 1);
+    c.keys_off = cv.take<int32_t>((size_t)L.nkeys + 1);
+    c.scan_tmp = cv.take<int32_t>(((size_t)L.nkeys + 2047) / 2048 + 1);
+    c.partials = cv.take<double>(5 * (size_t)kMaxEnergyBlocks);
+    c.red_out = cv.take<double>(8);
+    c.status = cv.take<unsigned>(4);
+    if (cv.p > cv.end) {
+        delete h;
+        return PIC_ENOMEM;
+    }
+    if (energy_blocks(c) > kMaxEnergyBlocks) {
+        delete h;
+        return PIC_EINVAL;
+    }
+    // species constants
+    const double mi = cfg->ion_mass_amu * kAmu;
+    const double qi = cfg->ion_charge * kQe;
+    const double uth_i = sqrt(kKb * cfg->T_ion_K / (mi * kC * kC));
+    const double uth_e = sqrt(cfg->T_electron_eV * kQe / (kMe * kC * kC));
+    const double qs[2] = {qi, -kQe}, ms[2] = {mi, kMe}, uths[2] = {uth_i, uth_e};
+    for (int s = 0; s < 2; s++) {
+        Species& S = c.sp[s];
+        S.ppc = s == 0 ? cfg->ppc_ion : cfg->ppc_electron;
+        S.mass = ms[s];
+        S.uth = uths[s];
+        S.e_kick = (float)(qs[s] * c.dt / (2.0 * ms[s] * kC));
+        S.b_rot = (float)(qs[s] * c.dt / (2.0 * ms[s]));
+        S.pair = s == 0;
+        S.p_kick = S.pair ? (float)(c.dt * (c.D / c.r0) / (2.0 * ms[s] * kC)) : 0.0f;
+        S.jsign = (cfg->mode == PIC_MODE_FULL) ? (s == 0 ? 1 : -1) : 0;
+    }
+    // antenna table (x = i + 1/2, FP64 -> FP32)
+    {
+        std::vector<float> ac(L.nx, 0.f), as(L.nx, 0.f);
+        if (cfg->laser_profile == PIC_LASER_PLANE) {
+            for (int i = 0; i < L.nx; i++) ac[i] = 1.0f;
+        } else if (cfg->laser_profile == PIC_LASER_GAUSSIAN) {
+            const double zR = kPi * cfg->w0 * cfg->w0 / cfg->lambda, sa = -Lant;
+            const double wa = cfg->w0 * sqrt(1.0 + (sa / zR) * (sa / zR));
+            const double Ra = sa + zR * zR / sa;
+            const double gouy = 0.5 * atan(sa / zR);
+            const double amp0 = sqrt(cfg->w0 / wa);
+            const double kw = c.omega / kC;
+            for (int i = 0; i < L.nx; i++) {
+                const double xr = ((double)i + 0.5 - 0.5 * L.nx) * cfg->dx;
+                const double amp = amp0 * exp(-xr * xr / (wa * wa));
+                const double ph = -kw * xr * xr / (2.0 * Ra) + gouy;
+                ac[i] = (float)(amp * cos(ph));
+                as[i] = (float)(amp * sin(ph));
+            }
+        }
+        if (cudaMemcpyAsync(c.ant_c, ac.data(), 4 * L.nx, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
+            cudaMemcpyAsync(c.ant_s, as.data(), 4 * L.nx, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
+            cudaStreamSynchronize(c.stream) != cudaSuccess) {
+            delete h;
+            return PIC_ECUDA;
+        }
+    }
+    bool ok = true;
+    for (int q = 0; q < 6; q++) ok &= cudaMemsetAsync(c.F[q], 0, 4 * L.nn, c.stream) == cudaSuccess;
+    for (int q = 0; q < 3; q++) ok &= cudaMemsetAsync(c.J[q], 0, 8 * L.nn, c.stream) == cudaSuccess;
+    for (int q = 0; q < 2; q++) ok &= cudaMemsetAsync(c.rho[q], 0, 8 * L.nn, c.stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(c.mur_save, 0, 4 * 8 * (size_t)L.nx, c.stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(c.status, 0, 16, c.stream) == cudaSuccess;
+    if (!ok) {
+        delete h;
+        return PIC_ECUDA;
+    }
+    c.cur = 0;
+    // initial particles into the second buffers, then sort into tiles
+    for (int s = 0; s < c.nsp; s++) {
+        launch_init_particles(c, s, c.stream);
+        sort_species_impl(c, s, c.stream, 1, nullptr);
+    }
+    r = redeposit(c);
+    if (r == PIC_OK && (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c.stream) != cudaSuccess))
+        r = PIC_ECUDA;
+    if (r) {
+        delete h;
+        return r;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+void pic_free(pic_ctx* h)
+{
+    if (!h) return;
+    for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    delete h;
+}
+
+int pic_step(pic_ctx* h, int32_t nsteps)
+{
+    if (!h || nsteps < 0) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.sticky) return c.sticky;
+    for (int it = 0; it < nsteps; it++) {
+        if (c.cfg.sort_every > 0 && c.steps_since_sort >= c.cfg.sort_every) {
+            int r = sort_all(h);
+            if (r) return r;
+        }
+        for (int q = 0; q < 3; q++) CK(cudaMemsetAsync(c.J[q], 0, 8 * c.nn, c.stream));
+        CK(cudaMemsetAsync(c.rho[1 - c.cur], 0, 8 * c.nn, c.stream));
+        StepArgs a = make_step_args(c);
+        int r = ev_begin(h, 0);
+        if (r) return r;
+        launch_particle_step(c, a, c.stream);
+        r = ev_end(h);
+        if (r) return r;
+        c.nlaunch[0]++;
+        c.nlaunch[3]++;
+        if (c.cfg.mode == PIC_MODE_FULL) {
+            r = ev_begin(h, 1);
+            if (r) return r;
+            launch_fields(c, c.stream, ((double)c.step + 0.5) * c.dt, &c.nlaunch[1]);
+            r = ev_end(h);
+            if (r) return r;
+            c.nlaunch[3] += 3;
+        }
+        CK(cudaGetLastError());
+        c.cur = 1 - c.cur;
+        c.step++;
+        c.steps_since_sort++;
+    }
+    return finish_status(h);
+}
+
+int pic_deposit_density(pic_ctx* h, int64_t* dev_out, double* scale_out)
+{
+    if (!h || !dev_out) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.sticky) return c.sticky;
+    launch_deposit_density(c, (u64*)dev_out, c.stream);
+    CK(cudaGetLastError());
+    if (scale_out) *scale_out = c.w / (4294967296.0 * c.cfg.dx * c.cfg.dx);
+    return PIC_OK;
+}
+
+int pic_pair_force(pic_ctx* h, float* dev_out)
+{
+    if (!h || !dev_out) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.sticky) return c.sticky;
+    launch_pair_force(c, dev_out, c.stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+int pic_energy(pic_ctx* h, pic_energy_t* out)
+{
+    if (!h || !out) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.sticky) return c.sticky;
+    double e[5];
+    launch_energy(c, c.stream, e);
+    CK(cudaGetLastError());
+    out->kinetic_ion = e[0];
+    out->kinetic_electron = e[1];
+    out->field_E = e[2];
+    out->field_B = e[3];
+    out->pair = e[4];
+    out->step = c.step;
+    return PIC_OK;
+}
+
+int pic_get_info(pic_ctx* h, pic_info* out)
+{
+    if (!h || !out) return PIC_EINVAL;
+    const Ctx& c = h->c;
+    out->dt = c.dt;
+    out->weight = c.w;
+    out->rho_scale = c.rho_scale;
+    out->r0 = c.r0;
+    out->time = (double)c.step * c.dt;
+    out->step = c.step;
+    out->num_particles[0] = c.sp[0].n;
+    out->num_particles[1] = c.nsp > 1 ? c.sp[1].n : 0;
+    out->nspecies = c.nsp;
+    out->ntiles = c.ntiles;
+    return PIC_OK;
+}
+
+static cudaMemcpyKind kind_out(int32_t on_host) { return on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+static cudaMemcpyKind kind_in(int32_t on_host) { return on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+
+int pic_get_particles(pic_ctx* h, int32_t s, int32_t* cell, float* fx, float* fz, float* ux, float* uy, float* uz,
+                      int32_t on_host)
+{
+    if (!h || s < 0 || s >= h->c.nsp) return PIC_EINVAL;
+    Ctx& c = h->c;
+    const Species& S = c.sp[s];
+    const size_t n = (size_t)S.n;
+    if (n == 0) return PIC_OK;
+    if (!cell || !fx || !fz || !ux || !uy || !uz) return PIC_EINVAL;
+    CK(cudaMemcpyAsync(cell, S.a.cell, 4 * n, kind_out(on_host), c.stream));
+    CK(cudaMemcpyAsync(fx, S.a.fx, 4 * n, kind_out(on_host), c.stream));
+    CK(cudaMemcpyAsync(fz, S.a.fz, 4 * n, kind_out(on_host), c.stream));
+    CK(cudaMemcpyAsync(ux, S.a.ux, 4 * n, kind_out(on_host), c.stream));
+    CK(cudaMemcpyAsync(uy, S.a.uy, 4 * n, kind_out(on_host), c.stream));
+    CK(cudaMemcpyAsync(uz, S.a.uz, 4 * n, kind_out(on_host), c.stream));
+    if (on_host) CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_set_particles(pic_ctx* h, int32_t s, int64_t n, const int32_t* cell, const float* fx, const float* fz,
+                      const float* ux, const float* uy, const float* uz, int32_t on_host)
+{
+    if (!h || s < 0 || s >= h->c.nsp || n < 0) return PIC_EINVAL;
+    Ctx& c = h->c;
+    Species& S = c.sp[s];
+    if (n > S.cap) return PIC_ENOMEM;
+    if (n > 0 && (!cell || !fx || !fz || !ux || !uy || !uz)) return PIC_EINVAL;
+    const size_t b = 4 * (size_t)n;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(S.b.cell, cell, b, kind_in(on_host), c.stream));
+        CK(cudaMemcpyAsync(S.b.fx, fx, b, kind_in(on_host), c.stream));
+        CK(cudaMemcpyAsync(S.b.fz, fz, b, kind_in(on_host), c.stream));
+        CK(cudaMemcpyAsync(S.b.ux, ux, b, kind_in(on_host), c.stream));
+        CK(cudaMemcpyAsync(S.b.uy, uy, b, kind_in(on_host), c.stream));
+        CK(cudaMemcpyAsync(S.b.uz, uz, b, kind_in(on_host), c.stream));
+        // reject cells outside the grid and offsets outside the cell before any kernel uses them
+        unsigned* bad = c.status + 1;
+        CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), c.stream));
+        launch_validate(c, S.b, n, bad, c.stream);
+        CK(cudaGetLastError());
+        unsigned hbad = 0;
+        CK(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+        if (hbad) return PIC_EINVAL;
+    }
+    S.n = n;
+    sort_species_impl(c, s, c.stream, 1, nullptr);
+    CK(cudaGetLastError());
+    if (s == 0) {
+        int r = redeposit(c);
+        if (r) return r;
+    }
+    CK(cudaStreamSynchronize(c.stream));
+    c.steps_since_sort = 0;
+    return PIC_OK;
+}
+
+int pic_get_field(pic_ctx* h, int32_t which, float* out, int32_t on_host)
+{
+    if (!h || which < 0 || which > 5 || !out) return PIC_EINVAL;
+    Ctx& c = h->c;
+    CK(cudaMemcpyAsync(out, c.F[which], 4 * c.nn, kind_out(on_host), c.stream));
+    if (on_host) CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_set_field(pic_ctx* h, int32_t which, const float* in, int32_t on_host)
+{
+    if (!h || which < 0 || which > 5 || !in) return PIC_EINVAL;
+    Ctx& c = h->c;
+    CK(cudaMemcpyAsync(c.F[which], in, 4 * c.nn, kind_in(on_host), c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_get_current(pic_ctx* h, int64_t* out3, int32_t on_host)
+{
+    if (!h || !out3) return PIC_EINVAL;
+    Ctx& c = h->c;
+    for (int q = 0; q < 3; q++)
+        CK(cudaMemcpyAsync(out3 + q * c.nn, c.J[q], 8 * c.nn, kind_out(on_host), c.stream));
+    if (on_host) CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_get_density(pic_ctx* h, int64_t* out, int32_t on_host)
+{
+    if (!h || !out) return PIC_EINVAL;
+    Ctx& c = h->c;
+    CK(cudaMemcpyAsync(out, c.rho[c.cur], 8 * c.nn, kind_out(on_host), c.stream));
+    if (on_host) CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_sort(pic_ctx* h)
+{
+    if (!h) return PIC_EINVAL;
+    int r = sort_all(h);
+    if (r) return r;
+    CK(cudaStreamSynchronize(h->c.stream));
+    return PIC_OK;
+}
+
+int pic_set_timing(pic_ctx* h, int32_t enable)
+{
+    if (!h) return PIC_EINVAL;
+    Ctx& c = h->c;
+    c.timing = enable != 0;
+    for (int q = 0; q < 3; q++) c.ms[q] = 0.0;
+    for (int q = 0; q < 4; q++) c.nlaunch[q] = 0;
+    h->evkind.clear();
+    return PIC_OK;
+}
+
+int pic_get_timing(pic_ctx* h, double ms[3], int64_t n[4])
+{
+    if (!h || !ms || !n) return PIC_EINVAL;
+    for (int q = 0; q < 3; q++) ms[q] = h->c.ms[q];
+    for (int q = 0; q < 4; q++) n[q] = h->c.nlaunch[q];
+    return PIC_OK;
+}
+
+const char* pic_strerror(int code)
+{
+    switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or configuration";
+    case PIC_ENOMEM: return "workspace too small or particle count above capacity";
+    case PIC_ECUDA: return "CUDA runtime error";
+    case PIC_ENAN: return "non-finite particle momentum";
+    case PIC_EMOVE: return "a particle moved one cell or more in one step";
+    case PIC_ESTATE: return "operation not valid in this mode";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

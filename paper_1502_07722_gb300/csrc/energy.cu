@@ -1,0 +1,134 @@
+// Energy diagnostics in FP64 (paper: the pair-potential cycle is energy conserving):
+// kinetic energy per species, electric and magnetic field energy, pair-potential energy.
+// Each block reduces its share into a fixed slot of a partials array; a single block then adds
+// the partials in block order, so the result does not depend on scheduling.
+#include "pic_device.cuh"
+
+namespace gbpic {
+
+constexpr int kEBlock = 256;
+constexpr int kSlots = 5;   // 0 KE ions, 1 KE electrons, 2 field E, 3 field B, 4 pair
+
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = kEBlock / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+struct EnergyArgs {
+    int nx, nz, nsp;
+    SpeciesBuf sp[2];
+    int64_t n[2];
+    const float* F[6];
+    const u64* rho;
+    float rho_s, h_coef, c_att, s_rep;
+    int pot_mode;
+    double* partials;   // gridDim.x * kSlots
+};
+
+__global__ void __launch_bounds__(kEBlock) k_energy(const EnergyArgs a)
+{
+    __shared__ double sh[kEBlock];
+    const int64_t tid = blockIdx.x * (int64_t)kEBlock + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * kEBlock;
+    double ke[2] = {0.0, 0.0}, pe = 0.0, fe = 0.0, fb = 0.0;
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        if (s >= a.nsp) break;
+        const SpeciesBuf& S = a.sp[s];
+        for (int64_t p = tid; p < a.n[s]; p += stride) {
+            const float ux = S.ux[p], uy = S.uy[p], uz = S.uz[p];
+            const float u2 = ux * ux + uy * uy + uz * uz;
+            ke[s] += (double)(u2 / (sqrtf(1.0f + u2) + 1.0f));
+            if (s == 0) {
+                const int c = S.cell[p];
+                const int k = c / a.nx, i = c - k * a.nx;
+                float n, dnx, dnz;
+                gather_density(a.rho, a.nx, a.nz, a.rho_s, i, k, S.fx[p], S.fz[p], n, dnx, dnz);
+                if (n > 0.0f) {
+                    const float cr = cbrtf(n);
+                    const float inv43 = 1.0f / (n * cr);
+                    float e = pair_energy_axis(cr, inv43, dnx, a.h_coef, a.pot_mode, a.c_att, a.s_rep) +
+                              pair_energy_axis(cr, inv43, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep) +
+                              2.0f * branch(a.pot_mode, a.c_att, a.s_rep, cr) * lj_U_inv(cr);
+                    pe += (double)e;
+                }
+            }
+        }
+    }
+    const int64_t nn = (int64_t)(a.nz + 1) * a.nx;
+    for (int64_t c = tid; c < nn; c += stride) {
+        const int k = (int)(c / a.nx);
+        const double wn = (k == 0 || k == a.nz) ? 0.5 : 1.0;
+        const double ex = a.F[0][c], ey = a.F[1][c], bz = a.F[5][c];
+        fe += wn * (ex * ex + ey * ey);
+        fb += wn * bz * bz;
+        if (k < a.nz) {
+            const double ez = a.F[2][c], bx = a.F[3][c], by = a.F[4][c];
+            fe += ez * ez;
+            fb += bx * bx + by * by;
+        }
+    }
+    const double r0 = block_sum(ke[0], sh), r1 = block_sum(ke[1], sh), r2 = block_sum(fe, sh),
+                 r3 = block_sum(fb, sh), r4 = block_sum(pe, sh);
+    if (threadIdx.x == 0) {
+        double* o = a.partials + (size_t)blockIdx.x * kSlots;
+        o[0] = r0; o[1] = r1; o[2] = r2; o[3] = r3; o[4] = r4;
+    }
+}
+
+__global__ void k_energy_final(const double* __restrict__ partials, int nb, double* out)
+{
+    __shared__ double sh[kEBlock];
+    for (int s = 0; s < kSlots; s++) {
+        double v = 0.0;
+        // fixed assignment of blocks to threads, then a fixed-shape tree
+        for (int b = threadIdx.x; b < nb; b += kEBlock) v += partials[(size_t)b * kSlots + s];
+        const double r = block_sum(v, sh);
+        if (threadIdx.x == 0) out[s] = r;
+    }
+}
+
+int energy_blocks(const Ctx& c) { return c.nsm * 4; }
+
+void launch_energy(Ctx& c, cudaStream_t st, double* host_out5)
+{
+    EnergyArgs a;
+    a.nx = c.nx;
+    a.nz = c.nz;
+    a.nsp = c.nsp;
+    for (int s = 0; s < 2; s++) {
+        a.sp[s] = c.sp[s].a;
+        a.n[s] = c.sp[s].n;
+    }
+    for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
+    a.rho = c.rho[c.cur];
+    a.rho_s = (float)c.rho_scale;
+    a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
+    a.c_att = (float)c.cfg.c_att;
+    a.s_rep = (float)c.cfg.s_rep;
+    a.pot_mode = c.cfg.pot_mode;
+    a.partials = c.partials;
+    const int nb = energy_blocks(c);
+    k_energy<<<nb, kEBlock, 0, st>>>(a);
+    k_energy_final<<<1, kEBlock, 0, st>>>(c.partials, nb, c.red_out);
+    double raw[kSlots];
+    cudaMemcpyAsync(raw, c.red_out, sizeof(raw), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    const double vol = c.cfg.dx * c.cfg.dx;
+    const double mu0 = 1.0 / (kEps0 * kC * kC);
+    host_out5[0] = raw[0] * c.w * c.sp[0].mass * kC * kC;
+    host_out5[1] = c.nsp > 1 ? raw[1] * c.w * c.sp[1].mass * kC * kC : 0.0;
+    host_out5[2] = 0.5 * kEps0 * raw[2] * vol;
+    host_out5[3] = 0.5 / mu0 * raw[3] * vol;
+    host_out5[4] = 0.5 * c.D * raw[4] * c.w;
+}
+
+}  // namespace gbpic

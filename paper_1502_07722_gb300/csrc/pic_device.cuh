@@ -1,0 +1,168 @@
+// Device-side building blocks of the PIC cycle: interpolation back to the particle, the
+// pair-potential force of Eqs. (1)-(3), the Boris push and fixed-point shapes.
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+__device__ __forceinline__ int wrap_x(int i, int nx) { return i < 0 ? i + nx : (i >= nx ? i - nx : i); }
+
+// Pair-species node sum with the wall rows doubled (mirror image of the slab behind a wall).
+__device__ __forceinline__ long long rho_node(const u64* __restrict__ rho, int nx, int nz, int i, int k)
+{
+    long long v = (long long)__ldg(rho + (size_t)k * nx + i);
+    return (k == 0 || k == nz) ? 2 * v : v;
+}
+
+// Node density (units n0) and its gradient (units n0 per cell) at a particle in cell (i, k) with
+// offsets (fx, fz): bilinear density; the gradient is the edge difference of the node density
+// interpolated along the other axis, i.e. the exact gradient of the bilinear density.
+// Differences are taken in integers before the single rounding to FP32.
+__device__ __forceinline__ void gather_density(const u64* __restrict__ rho, int nx, int nz, float rho_s,
+                                               int i, int k, float fx, float fz,
+                                               float& n, float& dnx, float& dnz)
+{
+    int i1 = wrap_x(i + 1, nx);
+    long long r00 = rho_node(rho, nx, nz, i, k), r10 = rho_node(rho, nx, nz, i1, k);
+    long long r01 = rho_node(rho, nx, nz, i, k + 1), r11 = rho_node(rho, nx, nz, i1, k + 1);
+    float gx = 1.0f - fx, gz = 1.0f - fz;
+    float a00 = (float)r00, a10 = (float)r10, a01 = (float)r01, a11 = (float)r11;
+    n = rho_s * (gz * (gx * a00 + fx * a10) + fz * (gx * a01 + fx * a11));
+    dnx = rho_s * (gz * (float)(r10 - r00) + fz * (float)(r11 - r01));
+    dnz = rho_s * (gx * (float)(r01 - r00) + fx * (float)(r11 - r10));
+}
+
+// Lennard-Jones derivative U'(r) (units D/r0) from inv = r0 / r.
+__device__ __forceinline__ float lj_dU_inv(float inv)
+{
+    float i2 = inv * inv, i6 = i2 * i2 * i2;
+    return 12.0f * i6 * inv * (1.0f - i6);
+}
+__device__ __forceinline__ float lj_U_inv(float inv)
+{
+    float i2 = inv * inv, i6 = i2 * i2 * i2;
+    return i6 * (i6 - 2.0f);
+}
+
+// Branch factor of the altered potential: s_rep inside r0 (inv > 1), c_att outside.
+__device__ __forceinline__ float branch(int pot_mode, float c_att, float s_rep, float inv)
+{
+    return pot_mode == 0 ? 1.0f : (inv > 1.0f ? s_rep : c_att);
+}
+
+// Dimensionless pair force along one axis (units D / r0) on an atom at local density n (> 0)
+// with c = n^(1/3) and gradient dn along that axis.
+//   Eq. (1): g = d rbar / dx = -(1/3) (r0 / dx) n^(-4/3) dn;  h = g / 2
+//   Eq. (2): neighbour distances rbar / (1 -+ h) -> r0 / dist = c (1 -+ h)
+//   Eq. (3): F = U'(dist+) - U'(dist-).
+// With both neighbours finite and on the same branch the difference is evaluated without
+// cancellation: (1-h)^p - (1+h)^p = -2 P_p(h), P_p the odd part of (1+h)^p, so
+//   F = 24 [ c n^4 P13(h) - c n^2 P7(h) ].
+__device__ __forceinline__ float pair_axis(float n, float c, float inv43, float dn, float h_coef,
+                                           int pot_mode, float c_att, float s_rep)
+{
+    float h = -h_coef * dn * inv43;
+    float ip = c * (1.0f - h);      // r0 / dist to the neighbour on the + side
+    float im = c * (1.0f + h);      // r0 / dist to the neighbour on the - side
+    if (ip > 0.0f && im > 0.0f) {
+        float fp = branch(pot_mode, c_att, s_rep, ip), fm = branch(pot_mode, c_att, s_rep, im);
+        if (fp == fm) {
+            float h2 = h * h;
+            float p7 = h * (7.0f + h2 * (35.0f + h2 * (21.0f + h2)));
+            float p13 = h * (13.0f + h2 * (286.0f + h2 * (1287.0f + h2 * (1716.0f + h2 * (715.0f + h2 * (78.0f + h2))))));
+            float n2 = n * n;
+            return fp * 24.0f * c * n2 * (n2 * p13 - p7);
+        }
+        return fp * lj_dU_inv(ip) - fm * lj_dU_inv(im);
+    }
+    float f = 0.0f;
+    if (ip > 0.0f) f += branch(pot_mode, c_att, s_rep, ip) * lj_dU_inv(ip);
+    if (im > 0.0f) f -= branch(pot_mode, c_att, s_rep, im) * lj_dU_inv(im);
+    return f;
+}
+
+// Pair energy per atom (units D): half the sum of U over the six neighbours.
+__device__ __forceinline__ float pair_energy_axis(float c, float inv43, float dn, float h_coef,
+                                                  int pot_mode, float c_att, float s_rep)
+{
+    float h = -h_coef * dn * inv43;
+    float ip = c * (1.0f - h), im = c * (1.0f + h);
+    float e = 0.0f;
+    if (ip > 0.0f) e += branch(pot_mode, c_att, s_rep, ip) * lj_U_inv(ip);
+    if (im > 0.0f) e += branch(pot_mode, c_att, s_rep, im) * lj_U_inv(im);
+    return e;
+}
+
+// Staggered bilinear field gather. (hx, hz) = 1 when the component sits half a cell up in x / z.
+// Half-row components exist on rows 0..nz-1; positions outside that range take the edge row.
+__device__ __forceinline__ float gather_field(const float* __restrict__ A, int nx, int nz, int i, int k,
+                                              float fx, float fz, int hx, int hz)
+{
+    int i0 = i;
+    float wx = fx;
+    if (hx) {
+        if (fx >= 0.5f) { wx = fx - 0.5f; }
+        else { i0 = wrap_x(i - 1, nx); wx = fx + 0.5f; }
+    }
+    int i1 = wrap_x(i0 + 1, nx);
+    int r0 = k, r1 = k + 1;
+    float wz = fz;
+    if (hz) {
+        if (fz >= 0.5f) {
+            wz = fz - 0.5f;
+            if (k >= nz - 1) { r0 = nz - 2; r1 = nz - 1; wz = 1.0f; }
+        } else if (k >= 1) {
+            r0 = k - 1; r1 = k; wz = fz + 0.5f;
+        } else {
+            r0 = 0; r1 = 1; wz = 0.0f;
+        }
+    }
+    const float* row0 = A + (size_t)r0 * nx;
+    const float* row1 = A + (size_t)r1 * nx;
+    float a = __ldg(row0 + i0), b = __ldg(row0 + i1), cc = __ldg(row1 + i0), d = __ldg(row1 + i1);
+    return (1.0f - wz) * ((1.0f - wx) * a + wx * b) + wz * ((1.0f - wx) * cc + wx * d);
+}
+
+// Relativistic Boris push of u = gamma v / c with the pair force added to both half kicks.
+__device__ __forceinline__ void boris(float& ux, float& uy, float& uz, float ex, float ey, float ez,
+                                      float bx, float by, float bz, float e_kick, float b_rot)
+{
+    ux += e_kick * ex; uy += e_kick * ey; uz += e_kick * ez;
+    float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+    float tx = b_rot * ig * bx, ty = b_rot * ig * by, tz = b_rot * ig * bz;
+    float s = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+    float px = ux + (uy * tz - uz * ty);
+    float py = uy + (uz * tx - ux * tz);
+    float pz = uz + (ux * ty - uy * tx);
+    ux += s * (py * tz - pz * ty);
+    uy += s * (pz * tx - px * tz);
+    uz += s * (px * ty - py * tx);
+    ux += e_kick * ex; uy += e_kick * ey; uz += e_kick * ez;
+}
+
+// J_y code V = rint(beta_y 2^18), taken in FP32 with explicit rounding (no fused multiply-add)
+// so that it is reproducible outside the GPU.
+__device__ __forceinline__ int jy_code(float ux, float uy, float uz)
+{
+    float u2 = __fmul_rn(ux, ux);
+    u2 = __fadd_rn(u2, __fmul_rn(uy, uy));
+    u2 = __fadd_rn(u2, __fmul_rn(uz, uz));
+    float g = __fsqrt_rn(__fadd_rn(1.0f, u2));
+    float by = __fdiv_rn(uy, g);
+    return __float2int_rn(__fmul_rn(by, 262144.0f));
+}
+
+// Fixed-point offset Q(f) = rint(f 2^16) in [0, 2^16].
+__device__ __forceinline__ int qoff(float f) { return __float2int_rn(f * 65536.0f); }
+
+// Linear (hat) weights of a fixed-point coordinate d (relative to node 0 of a 3-node stencil,
+// 0 <= d <= 2^17) on nodes 0, 1, 2.
+__device__ __forceinline__ void hat3(int d, int& s0, int& s1, int& s2)
+{
+    s0 = max(0, kQOne - d);
+    s1 = kQOne - abs(d - kQOne);
+    s2 = max(0, d - kQOne);
+}
+
+}  // namespace gbpic

@@ -1,0 +1,120 @@
+// Internal types and launch declarations of the GB300 PIC library (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pic.h"
+
+namespace gbpic {
+
+// CODATA 2018
+constexpr double kC = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kKb = 1.380649e-23;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kQBits = 16;           // fixed-point bits per cell along one axis
+constexpr int32_t kQOne = 1 << kQBits;
+
+// status word bits (device, sticky)
+constexpr unsigned kErrNan = 1u;
+constexpr unsigned kErrMove = 2u;
+
+typedef unsigned long long u64;
+
+// One species in structure-of-arrays form. Two buffers: `a` is the live one, `b` the target of
+// the cell sort (swapped after each sort).
+struct SpeciesBuf {
+    int32_t* cell;
+    float* fx;
+    float* fz;
+    float* ux;
+    float* uy;
+    float* uz;
+};
+
+struct Species {
+    SpeciesBuf a, b;
+    int32_t* tile_start;   // ntiles + 1 offsets into `a` (from the last sort)
+    int64_t n, cap;
+    int32_t ppc;
+    float e_kick;          // q dt / (2 m c)          per V/m
+    float b_rot;           // q dt / (2 m)            per T (divided by gamma)
+    float p_kick;          // dt (D / r0) / (2 m c)    per unit dimensionless pair force
+    int32_t jsign;         // charge sign for the current (0: neutral)
+    int32_t pair;          // carries the pair force and the node density
+    double mass, uth;
+};
+
+// Everything a kernel of the step needs, passed by value.
+struct StepArgs {
+    int32_t nx, nz, T, ntx, ntz, ntiles, W;   // W: window edge (nodes) of a tile
+    int32_t full;                             // fields and Lorentz force on
+    float cdt_dx;                             // c dt / dx
+    float rho_s;                              // node sum -> n / n0
+    float h_coef;                             // r0 / (6 dx): h = -h_coef * dn * n^(-4/3)
+    int32_t pot_mode;
+    float c_att, s_rep;
+    const float* F[6];
+    const u64* rho_cur;
+    u64* rho_next;
+    u64* J[3];
+    unsigned* status;
+    int32_t nsp;
+    Species sp[2];
+};
+
+struct Ctx {
+    pic_config cfg;
+    cudaStream_t stream;
+    int device;
+    int nsm;
+    // derived
+    double dt, w, r0, D, rho_scale, E0, omega, t_ant;
+    int32_t nx, nz, T, ntx, ntz, ntiles, W, k_ant;
+    size_t nn;            // (nz + 1) * nx
+    int32_t nkeys;        // ntiles * T * T
+    int32_t nsp;
+    Species sp[2];
+    // grids
+    float* F[6];
+    u64* J[3];
+    u64* rho[2];
+    int32_t cur;          // rho[cur] holds the node density at the current positions
+    float* mur_save;      // 8 * nx
+    float* ant_c;         // nx: amplitude * cos(phase(x)) at x = i + 1/2
+    float* ant_s;         // nx: amplitude * sin(phase(x))
+    // scratch
+    int32_t* keys_count;  // nkeys + 1
+    int32_t* keys_off;    // nkeys + 1
+    int32_t* scan_tmp;    // block sums
+    double* partials;     // energy block partials
+    double* red_out;      // 8 doubles
+    unsigned* status;
+    int64_t step;
+    int32_t steps_since_sort;
+    int sticky;
+    // timing
+    int timing;
+    cudaEvent_t ev[4];
+    double ms[3];
+    int64_t nlaunch[4];
+};
+
+// kernels launched from the host side of the library (defined in the .cu files)
+void launch_init_particles(Ctx& c, int s, cudaStream_t st);
+void launch_sort_species(Ctx& c, int s, cudaStream_t st, int64_t* launches);
+void launch_deposit_density(Ctx& c, u64* out, cudaStream_t st);
+void launch_pair_force(Ctx& c, float* out, cudaStream_t st);
+void launch_validate(Ctx& c, const SpeciesBuf& b, int64_t n, unsigned* bad, cudaStream_t st);
+void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st);
+void launch_fields(Ctx& c, cudaStream_t st, double t_half, int64_t* launches);
+void launch_energy(Ctx& c, cudaStream_t st, double* host_out5);
+StepArgs make_step_args(Ctx& c);
+
+}  // namespace gbpic

@@ -1,0 +1,153 @@
+// Cell sort of one species into tiles (counting sort by a tile-major cell key):
+// count per key -> exclusive scan -> scatter into the second buffer -> swap.
+// The key of cell (i, k) is tile * T^2 + (k mod T) * T + (i mod T), tile = (k / T) * ntx + i / T,
+// so the particles of a tile are contiguous and, within a tile, ordered by cell.
+// The order of particles inside one cell is not fixed (atomic cursors); nothing downstream
+// depends on it because every deposit is an exact integer sum.
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 2 * kScanBlock;
+
+__device__ __forceinline__ int cell_key(int cell, int nx, int T, int ntx)
+{
+    const int k = cell / nx, i = cell - k * nx;
+    const int tz = k / T, tx = i / T;
+    return (tz * ntx + tx) * T * T + (k - tz * T) * T + (i - tx * T);
+}
+
+__global__ void k_count(const int32_t* __restrict__ cell, int64_t n, int nx, int T, int ntx, int32_t* count)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(count + cell_key(cell[p], nx, T, ntx), 1);
+}
+
+// exclusive scan of kScanItems elements per block; block totals to bsum
+__global__ void k_scan_block(const int32_t* __restrict__ in, int32_t* out, int32_t* bsum, int n)
+{
+    __shared__ int32_t s[kScanItems];
+    const int base = blockIdx.x * kScanItems;
+    for (int j = threadIdx.x; j < kScanItems; j += blockDim.x) s[j] = base + j < n ? in[base + j] : 0;
+    __syncthreads();
+    // Blelloch up-sweep / down-sweep
+    int off = 1;
+    for (int d = kScanItems >> 1; d > 0; d >>= 1) {
+        __syncthreads();
+        if ((int)threadIdx.x < d) {
+            const int ai = off * (2 * threadIdx.x + 1) - 1, bi = off * (2 * threadIdx.x + 2) - 1;
+            s[bi] += s[ai];
+        }
+        off <<= 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = s[kScanItems - 1];
+        s[kScanItems - 1] = 0;
+    }
+    for (int d = 1; d < kScanItems; d <<= 1) {
+        off >>= 1;
+        __syncthreads();
+        if ((int)threadIdx.x < d) {
+            const int ai = off * (2 * threadIdx.x + 1) - 1, bi = off * (2 * threadIdx.x + 2) - 1;
+            const int32_t t = s[ai];
+            s[ai] = s[bi];
+            s[bi] += t;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kScanItems; j += blockDim.x)
+        if (base + j < n) out[base + j] = s[j];
+}
+
+// exclusive scan of the block totals in place (one block, sequential over chunks)
+__global__ void k_scan_sums(int32_t* bsum, int nb)
+{
+    __shared__ int32_t s[kScanBlock];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kScanBlock) {
+        const int j = base + threadIdx.x;
+        const int32_t v = j < nb ? bsum[j] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int d = 1; d < kScanBlock; d <<= 1) {     // Hillis-Steele inclusive
+            const int32_t t = (int)threadIdx.x >= d ? s[threadIdx.x - d] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (j < nb) bsum[j] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) carry += s[kScanBlock - 1];
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int32_t* out, const int32_t* __restrict__ bsum, int n, int32_t* cursor, int32_t total)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        const int32_t v = out[j] + bsum[j / kScanItems];
+        out[j] = v;
+        cursor[j] = v;
+    }
+    if (j == 0) out[n] = total;
+}
+
+__global__ void k_tile_starts(const int32_t* __restrict__ off, int ntiles, int TT, int32_t* tile_start)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= ntiles) tile_start[t] = off[(size_t)t * TT];
+}
+
+__global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, int nx, int T, int ntx, int32_t* cursor)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int c = src.cell[p];
+        const int q = atomicAdd(cursor + cell_key(c, nx, T, ntx), 1);
+        dst.cell[q] = c;
+        dst.fx[q] = src.fx[p];
+        dst.fz[q] = src.fz[p];
+        dst.ux[q] = src.ux[p];
+        dst.uy[q] = src.uy[p];
+        dst.uz[q] = src.uz[p];
+    }
+}
+
+// Sort species s: its particles are read from `b` when from_b != 0 (fresh data), else from `a`;
+// the sorted result always ends in `a`.
+void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* launches)
+{
+    Species& S = c.sp[s];
+    const int TT = c.T * c.T;
+    int64_t g = (S.n + 255) / 256;
+    if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
+    if (g < 1) g = 1;
+    cudaMemsetAsync(c.keys_count, 0, sizeof(int32_t) * (size_t)(c.nkeys + 1), st);
+    SpeciesBuf src = from_b ? S.b : S.a;
+    SpeciesBuf dst = from_b ? S.a : S.b;
+    if (S.n > 0) k_count<<<(int)g, 256, 0, st>>>(src.cell, S.n, c.nx, c.T, c.ntx, c.keys_count);
+    const int nb = (c.nkeys + kScanItems - 1) / kScanItems;
+    k_scan_block<<<nb, kScanBlock, 0, st>>>(c.keys_count, c.keys_off, c.scan_tmp, c.nkeys);
+    k_scan_sums<<<1, kScanBlock, 0, st>>>(c.scan_tmp, nb);
+    // the cursor reuses the count array (counts are consumed by the scan)
+    k_scan_add<<<(c.nkeys + 255) / 256, 256, 0, st>>>(c.keys_off, c.scan_tmp, c.nkeys, c.keys_count, (int32_t)S.n);
+    k_tile_starts<<<(c.ntiles + 1 + 255) / 256, 256, 0, st>>>(c.keys_off, c.ntiles, TT, S.tile_start);
+    if (S.n > 0) k_scatter<<<(int)g, 256, 0, st>>>(src, dst, S.n, c.nx, c.T, c.ntx, c.keys_count);
+    if (!from_b) {
+        SpeciesBuf t = S.a;
+        S.a = S.b;
+        S.b = t;
+    }
+    if (launches) *launches += 5 + (S.n > 0 ? 2 : 0);
+}
+
+void launch_sort_species(Ctx& c, int s, cudaStream_t st, int64_t* launches)
+{
+    sort_species_impl(c, s, st, 0, launches);
+}
+
+}  // namespace gbpic
