@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large2d")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
 
@@ -275,7 +276,7 @@ def main():
 
     if rank == 0:
         clocks = clk.summary(torch.cuda.current_device())
-        cpu = cpu_baseline(args) if world == 1 else None
+        cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
