@@ -184,6 +184,7 @@ StepArgs make_step_args(Ctx& c)
     a.ntz = c.ntz;
     a.ntiles = c.ntiles;
     a.W = c.W;
+    a.nx_magic = (unsigned)(4294967296ULL / (unsigned long long)c.nx);
     a.full = c.cfg.mode == PIC_MODE_FULL;
     a.cdt_dx = (float)(kC * c.dt / c.cfg.dx);
     a.rho_s = (float)c.rho_scale;

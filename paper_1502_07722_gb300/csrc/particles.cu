@@ -3,17 +3,35 @@
 // (pair-potential force, Eqs. 1-3) -> relativistic Boris push -> move -> charge-conserving
 // current deposition (Esirkepov, fixed point) -> node density at the new position.
 //
-// One CTA owns one tile of T x T cells at a time (particles are sorted into tiles). The
-// deposits of a tile go into int64 accumulators in shared memory that cover the tile plus a
-// margin, and are flushed to global memory with one atomic per non-zero node. Particles that
-// drifted beyond the margin since the last sort deposit straight into global memory. Integer
-// sums make the result independent of the order of the atomics.
+// Work decomposition (GB300):
+//  * one CTA owns one tile of T x T cells at a time (particles are sorted into tiles, and by
+//    cell inside a tile);
+//  * the CTA stages a window of (T + 2M + 3)^2 nodes in shared memory: the six field
+//    components and the pair density n / n0 in FP32, and four exact 64-bit accumulators (new
+//    node density, J_x, J_y, J_z), each kept as a (high, low) pair of 32-bit words: the low word
+//    is added atomically with its old value returned and the carry goes to the high word. 32-bit
+//    shared atomics are native; 64-bit ones are not, and with a whole warp on one address they
+//    cost ~20x more;
+//  * particles stream through shared memory in chunks of up to 1024: loaded and stored with
+//    coalesced accesses, processed transposed, so that lane l of a warp takes the particle R
+//    places after lane l-1 in the cell-sorted order. Lanes then sit in different cells and their
+//    deposits rarely meet on one address;
+//  * a particle that stays in its cell (almost all of them) deposits on the four corners of the
+//    cell; a particle that crossed a cell edge uses the 3 x 3 Esirkepov stencil; a particle that
+//    drifted beyond the margin since the last sort uses global memory (rare);
+//  * the window is flushed with one global 64-bit atomic per non-zero node.
+// Integer sums make every result independent of the order of the additions.
 #include "pic_device.cuh"
 
 namespace gbpic {
 
-constexpr int kMargin = 2;          // cells a particle may drift out of its tile between sorts
+constexpr int kMargin = 2;              // cells a particle may drift out of its tile between sorts
 constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+constexpr int kChunkRows = 32;          // particles per lane row of a full chunk
+constexpr int kChunk = 32 * kChunkRows; // particles per chunk
+constexpr int kPitch = kChunkRows + 1;  // padded row pitch of the chunk arrays (conflict-free)
+constexpr int kChunkWords = 32 * kPitch;
 
 __device__ __forceinline__ int wrap_any(int i, int nx)
 {
@@ -21,54 +39,186 @@ __device__ __forceinline__ int wrap_any(int i, int nx)
     return r < 0 ? r + nx : r;
 }
 
-__device__ __forceinline__ void dep(bool local, u64* s, u64* g, int W, int nx, int lb, int la, int gb, int ga,
-                                    long long v)
+// exact 64-bit accumulation into a (hi, lo) pair of shared 32-bit words
+__device__ __forceinline__ void acc64(unsigned* lo, int* hi, long long v)
 {
-    if (v == 0) return;
-    if (local) atomicAdd(s + lb * W + la, (u64)v);
-    else atomicAdd(g + (size_t)gb * nx + wrap_any(ga, nx), (u64)v);
+    const unsigned l = (unsigned)v;
+    int h = (int)(v >> 32);
+    const unsigned old = atomicAdd(lo, l);
+    h += (old + l < old) ? 1 : 0;
+    if (h != 0) atomicAdd(hi, h);
 }
 
-template <bool FULL>
-__device__ __forceinline__ void process_particle(const StepArgs& a, const Species& S, int p, u64* s_rho, u64* s_jx,
-                                                 u64* s_jy, u64* s_jz, int ox, int oz)
-{
-    const int nx = a.nx, nz = a.nz, W = a.W;
-    const int cell = S.a.cell[p];
-    const float fx = S.a.fx[p], fz = S.a.fz[p];
-    float ux = S.a.ux[p], uy = S.a.uy[p], uz = S.a.uz[p];
-    const int k = cell / nx, i = cell - k * nx;
+struct Window {
+    unsigned* lo[4];     // 0: node density, 1: J_x, 2: J_y, 3: J_z
+    int* hi[4];
+    float* f[6];
+    float* nh;
+    int ox, oz, W;
+};
 
-    // half kick (electric + pair force), rotation field
-    float kx = 0.f, ky = 0.f, kz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-    if (FULL) {
-        kx = S.e_kick * gather_field(a.F[0], nx, nz, i, k, fx, fz, 1, 0);
-        ky = S.e_kick * gather_field(a.F[1], nx, nz, i, k, fx, fz, 0, 0);
-        kz = S.e_kick * gather_field(a.F[2], nx, nz, i, k, fx, fz, 0, 1);
-        bx = gather_field(a.F[3], nx, nz, i, k, fx, fz, 0, 1);
-        by = gather_field(a.F[4], nx, nz, i, k, fx, fz, 1, 1);
-        bz = gather_field(a.F[5], nx, nz, i, k, fx, fz, 1, 0);
+__device__ __forceinline__ void wadd(const Window& w, int q, int idx, long long v)
+{
+    if (v != 0) acc64(w.lo[q] + idx, w.hi[q] + idx, v);
+}
+
+// exact cell -> (i, k): q = floor(cell / nx) from a multiply-high and one correction
+__device__ __forceinline__ void split_cell(int cell, int nx, unsigned magic, int& i, int& k)
+{
+    unsigned q = __umulhi((unsigned)cell, magic);
+    int r = cell - (int)q * nx;
+    if (r >= nx) { q++; r -= nx; }
+    k = (int)q;
+    i = r;
+}
+
+// bilinear gather of a staged component; (hx, hz) = 1 where it sits half a cell up
+__device__ __forceinline__ float win_gather(const float* A, int W, int lx, int lz, float fx, float fz, int hx, int hz)
+{
+    int c = lx, r = lz;
+    float wx = fx, wz = fz;
+    if (hx) {
+        const bool up = fx >= 0.5f;
+        c = up ? lx : lx - 1;
+        wx = up ? fx - 0.5f : fx + 0.5f;
     }
-    if (S.pair) {
-        float n, dnx, dnz;
-        gather_density(a.rho_cur, nx, nz, a.rho_s, i, k, fx, fz, n, dnx, dnz);
-        if (n > 0.0f) {
-            float c = cbrtf(n);
-            float inv43 = 1.0f / (n * c);
-            kx += S.p_kick * pair_axis(n, c, inv43, dnx, a.h_coef, a.pot_mode, a.c_att, a.s_rep);
-            kz += S.p_kick * pair_axis(n, c, inv43, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+    if (hz) {
+        const bool up = fz >= 0.5f;
+        r = up ? lz : lz - 1;
+        wz = up ? fz - 0.5f : fz + 0.5f;
+    }
+    const float* p = A + r * W + c;
+    const float a = p[0], b = p[1], d = p[W], e = p[W + 1];
+    return (1.0f - wz) * ((1.0f - wx) * a + wx * b) + wz * ((1.0f - wx) * d + wx * e);
+}
+
+// Rare path: fields and node density straight from global memory (particle outside the window).
+__device__ __noinline__ void gather_global(const float* F0, const float* F1, const float* F2, const float* F3,
+                                           const float* F4, const float* F5, const u64* rho, int nx, int nz,
+                                           float rho_s, int full, int pair, int i, int k, float fx, float fz,
+                                           float* g)
+{
+    if (full) {
+        g[0] = gather_field(F0, nx, nz, i, k, fx, fz, 1, 0);
+        g[1] = gather_field(F1, nx, nz, i, k, fx, fz, 0, 0);
+        g[2] = gather_field(F2, nx, nz, i, k, fx, fz, 0, 1);
+        g[3] = gather_field(F3, nx, nz, i, k, fx, fz, 0, 1);
+        g[4] = gather_field(F4, nx, nz, i, k, fx, fz, 1, 1);
+        g[5] = gather_field(F5, nx, nz, i, k, fx, fz, 1, 0);
+    }
+    if (pair) gather_density(rho, nx, nz, rho_s, i, k, fx, fz, g[6], g[7], g[8]);
+}
+
+// Rare path: 3 x 3 Esirkepov stencil and new node density with global atomics. (X, Z) are
+// global fixed-point coordinates; X1 may lie outside [0, nx 2^16) (periodic x).
+__device__ __noinline__ void deposit_global(u64* rho_next, u64* Jx, u64* Jy, u64* Jz, int nx, int X0, int Z0,
+                                            int X1, int Z1, int jsign, int V, int pair)
+{
+    const int bx = min(X0, X1) >> kQBits, bz = min(Z0, Z1) >> kQBits;
+    int S0x[3], S1x[3], S0z[3], S1z[3];
+    hat3(X0 - bx * kQOne, S0x[0], S0x[1], S0x[2]);
+    hat3(X1 - bx * kQOne, S1x[0], S1x[1], S1x[2]);
+    hat3(Z0 - bz * kQOne, S0z[0], S0z[1], S0z[2]);
+    hat3(Z1 - bz * kQOne, S1z[0], S1z[1], S1z[2]);
+    const long long sg = jsign;
+    for (int b = 0; b < 3; b++) {
+        const size_t row = (size_t)(bz + b) * nx;
+        if (jsign != 0) {
+            const long long wz = (long long)(S0z[b] + S1z[b]);
+            long long acc = 0;
+            for (int c = 0; c < 2; c++) {
+                acc -= (long long)(S1x[c] - S0x[c]) * wz;
+                if (acc != 0) atomicAdd(Jx + row + wrap_any(bx + c, nx), (u64)(sg * acc));
+            }
         }
+        for (int c = 0; c < 3; c++) {
+            const size_t g = row + wrap_any(bx + c, nx);
+            if (jsign != 0 && V != 0) {
+                const long long w6 = 2LL * S0x[c] * S0z[b] + (long long)S1x[c] * S0z[b] + (long long)S0x[c] * S1z[b] +
+                                     2LL * S1x[c] * S1z[b];
+                if (w6 != 0) atomicAdd(Jy + g, (u64)(sg * V * w6));
+            }
+            if (pair) {
+                const long long r = (long long)S1x[c] * S1z[b];
+                if (r != 0) atomicAdd(rho_next + g, (u64)r);
+            }
+        }
+    }
+    if (jsign != 0) {
+        for (int c = 0; c < 3; c++) {
+            const long long wx = (long long)(S0x[c] + S1x[c]);
+            long long acc = 0;
+            for (int b = 0; b < 2; b++) {
+                acc -= (long long)(S1z[b] - S0z[b]) * wx;
+                if (acc != 0) atomicAdd(Jz + (size_t)(bz + b) * nx + wrap_any(bx + c, nx), (u64)(sg * acc));
+            }
+        }
+    }
+}
+
+// One particle: state in (cell, fx, fz, ux, uy, uz) is replaced by the new state.
+template <bool FULL>
+__device__ __forceinline__ void process_particle(const StepArgs& a, const Species& S, const Window& w, int& cell,
+                                                 float& fx_io, float& fz_io, float& ux, float& uy, float& uz)
+{
+    const int nx = a.nx, nz = a.nz, W = w.W;
+    const float fx = fx_io, fz = fz_io;
+    int i, k;
+    split_cell(cell, nx, a.nx_magic, i, k);
+
+    // window coordinates (x is periodic: take the image closest to the window centre)
+    int lx = i - w.ox;
+    const int centre = W / 2;
+    if (lx - centre > nx / 2) lx -= nx;
+    else if (centre - lx > nx / 2) lx += nx;
+    const int lz = k - w.oz;
+    const bool inwin = lx >= 1 && lx + 2 < W && lz >= 1 && lz + 2 < W;
+
+    float kx = 0.f, ky = 0.f, kz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    float n = 0.f, dnx = 0.f, dnz = 0.f;
+    if (inwin) {
+        if (FULL) {
+            kx = S.e_kick * win_gather(w.f[0], W, lx, lz, fx, fz, 1, 0);
+            ky = S.e_kick * win_gather(w.f[1], W, lx, lz, fx, fz, 0, 0);
+            kz = S.e_kick * win_gather(w.f[2], W, lx, lz, fx, fz, 0, 1);
+            bx = win_gather(w.f[3], W, lx, lz, fx, fz, 0, 1);
+            by = win_gather(w.f[4], W, lx, lz, fx, fz, 1, 1);
+            bz = win_gather(w.f[5], W, lx, lz, fx, fz, 1, 0);
+        }
+        if (S.pair) {
+            const float* q = w.nh + lz * W + lx;
+            const float n00 = q[0], n10 = q[1], n01 = q[W], n11 = q[W + 1];
+            const float gx = 1.0f - fx, gz = 1.0f - fz;
+            n = gz * (gx * n00 + fx * n10) + fz * (gx * n01 + fx * n11);
+            dnx = gz * (n10 - n00) + fz * (n11 - n01);
+            dnz = gx * (n01 - n00) + fx * (n11 - n10);
+        }
+    } else {
+        float g[9];
+        gather_global(a.F[0], a.F[1], a.F[2], a.F[3], a.F[4], a.F[5], a.rho_cur, nx, nz, a.rho_s, FULL ? 1 : 0,
+                      S.pair, i, k, fx, fz, g);
+        if (FULL) {
+            kx = S.e_kick * g[0]; ky = S.e_kick * g[1]; kz = S.e_kick * g[2];
+            bx = g[3]; by = g[4]; bz = g[5];
+        }
+        if (S.pair) { n = g[6]; dnx = g[7]; dnz = g[8]; }
+    }
+    if (S.pair && n > 0.0f) {
+        const float c = cbrtf(n);
+        const float inv43 = 1.0f / (n * c);
+        kx += S.p_kick * pair_axis(n, c, inv43, dnx, a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+        kz += S.p_kick * pair_axis(n, c, inv43, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep);
     }
     const float ux0 = ux, uy0 = uy, uz0 = uz;
     // relativistic Boris: half kick, rotation, half kick
     ux += kx; uy += ky; uz += kz;
     if (FULL) {
-        float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
-        float tx = S.b_rot * ig * bx, ty = S.b_rot * ig * by, tz = S.b_rot * ig * bz;
-        float s = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
-        float px = ux + (uy * tz - uz * ty);
-        float py = uy + (uz * tx - ux * tz);
-        float pz = uz + (ux * ty - uy * tx);
+        const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        const float tx = S.b_rot * ig * bx, ty = S.b_rot * ig * by, tz = S.b_rot * ig * bz;
+        const float s = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+        const float px = ux + (uy * tz - uz * ty);
+        const float py = uy + (uz * tx - ux * tz);
+        const float pz = uz + (ux * ty - uy * tx);
         ux += s * (py * tz - pz * ty);
         uy += s * (pz * tx - px * tz);
         uz += s * (px * ty - py * tx);
@@ -76,7 +226,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     ux += kx; uy += ky; uz += kz;
 
     // move (in-plane), cells per step = u c dt / (gamma dx)
-    float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+    const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
     float dxi = ux * a.cdt_dx * ig, dze = uz * a.cdt_dx * ig;
     if (!(fabsf(dxi) < 1.0f && fabsf(dze) < 1.0f)) {
         atomicOr(a.status, (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? kErrMove : kErrNan);
@@ -87,134 +237,230 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     nfx -= (float)di;
     if (nfx >= 1.0f) { nfx = 0.0f; di += 1; }
     float nfz = fz + dze;
-    int k1 = k;
+    int dk = 0;
     if (k == 0 && nfz < 0.0f) {                   // reflect off the wall z = 0
         nfz = -nfz; uz = -uz;
     } else if (k == nz - 1 && nfz >= 1.0f) {      // reflect off the wall z = nz
         nfz = 2.0f - nfz; uz = -uz;
     } else {
-        int dk = (int)floorf(nfz);
+        dk = (int)floorf(nfz);
         nfz -= (float)dk;
         if (nfz >= 1.0f) { nfz = 0.0f; dk += 1; }
-        k1 = k + dk;
     }
-    const int i1u = i + di;
-    const int i1 = wrap_x(i1u, nx);
 
-    // fixed-point coordinates relative to the tile window
-    int lx0 = i - ox;
-    const int centre = W / 2;
-    if (lx0 - centre > nx / 2) lx0 -= nx;
-    else if (centre - lx0 > nx / 2) lx0 += nx;
-    const int XL0 = lx0 * kQOne + qoff(fx);
-    const int XL1 = XL0 + (i1u - i) * kQOne + qoff(nfx) - qoff(fx);
-    const int ZL0 = (k - oz) * kQOne + qoff(fz);
-    const int ZL1 = ZL0 + (k1 - k) * kQOne + qoff(nfz) - qoff(fz);
-    const int bxl = min(XL0, XL1) >> kQBits;
-    const int bzl = min(ZL0, ZL1) >> kQBits;
-    const bool local = bxl >= 0 && bxl + 2 < W && bzl >= 0 && bzl + 2 < W;
-    const int gbx = bxl + ox, gbz = bzl + oz;
-    int S0x[3], S1x[3], S0z[3], S1z[3];
-    hat3(XL0 - bxl * kQOne, S0x[0], S0x[1], S0x[2]);
-    hat3(XL1 - bxl * kQOne, S1x[0], S1x[1], S1x[2]);
-    hat3(ZL0 - bzl * kQOne, S0z[0], S0z[1], S0z[2]);
-    hat3(ZL1 - bzl * kQOne, S1z[0], S1z[1], S1z[2]);
-
-    if (S.jsign != 0) {
-        const long long sg = S.jsign;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {                       // J_x on node row b
-            long long wz = (long long)(S0z[b] + S1z[b]);
-            if (wz == 0) continue;
-            long long acc = -(long long)(S1x[0] - S0x[0]) * wz;
-            dep(local, s_jx, a.J[0], W, nx, bzl + b, bxl, gbz + b, gbx, sg * acc);
-            acc -= (long long)(S1x[1] - S0x[1]) * wz;
-            dep(local, s_jx, a.J[0], W, nx, bzl + b, bxl + 1, gbz + b, gbx + 1, sg * acc);
+    const int x0 = qoff(fx), x1 = qoff(nfx), z0 = qoff(fz), z1 = qoff(nfz);
+    const long long sg = S.jsign;
+    // |u_y| < 2^-19 gives |beta_y| 2^18 < 1/2, i.e. V = 0 without evaluating the code
+    const int V = (S.jsign != 0 && fabsf(uy) >= 1.9073486328125e-06f) ? jy_code(ux, uy, uz) : 0;
+    if (inwin && di == 0 && dk == 0) {
+        // the particle stays in its cell: stencil = the four corners of the cell
+        const int base = lz * W + lx;
+        if (S.jsign != 0) {
+            const int dX = x1 - x0, dZ = z1 - z0;
+            if (dX != 0) {
+                wadd(w, 1, base, sg * ((long long)dX * (2 * kQOne - z0 - z1)));
+                wadd(w, 1, base + W, sg * ((long long)dX * (z0 + z1)));
+            }
+            if (dZ != 0) {
+                wadd(w, 3, base, sg * ((long long)dZ * (2 * kQOne - x0 - x1)));
+                wadd(w, 3, base + 1, sg * ((long long)dZ * (x0 + x1)));
+            }
+            if (V != 0) {
+                // 6 Wy = 6 Q^2 - 3 Q (x0 + x1) - 3 Q (z0 + z1) + P on the lower-left corner, etc.
+                const long long P = 2LL * x0 * z0 + (long long)x1 * z0 + (long long)x0 * z1 + 2LL * x1 * z1;
+                const long long sx = 3LL * kQOne * (x0 + x1), sz = 3LL * kQOne * (z0 + z1);
+                const long long sv = sg * (long long)V;
+                wadd(w, 2, base, sv * (6LL * kQOne * kQOne - sx - sz + P));
+                wadd(w, 2, base + 1, sv * (sx - P));
+                wadd(w, 2, base + W, sv * (sz - P));
+                wadd(w, 2, base + W + 1, sv * P);
+            }
         }
-#pragma unroll
-        for (int c = 0; c < 3; c++) {                       // J_z on node column c
-            long long wx = (long long)(S0x[c] + S1x[c]);
-            if (wx == 0) continue;
-            long long acc = -(long long)(S1z[0] - S0z[0]) * wx;
-            dep(local, s_jz, a.J[2], W, nx, bzl, bxl + c, gbz, gbx + c, sg * acc);
-            acc -= (long long)(S1z[1] - S0z[1]) * wx;
-            dep(local, s_jz, a.J[2], W, nx, bzl + 1, bxl + c, gbz + 1, gbx + c, sg * acc);
+        if (S.pair) {
+            const long long ax = kQOne - x1, az = kQOne - z1;
+            wadd(w, 0, base, ax * az);
+            wadd(w, 0, base + 1, (long long)x1 * az);
+            wadd(w, 0, base + W, ax * z1);
+            wadd(w, 0, base + W + 1, (long long)x1 * z1);
         }
-        const int V = jy_code(ux, uy, uz);
-        if (V != 0) {
-            const long long sv = sg * (long long)V;
+    } else if (inwin) {
+        // a cell edge was crossed: 3 x 3 Esirkepov stencil in the window
+        const int XL0 = lx * kQOne + x0, XL1 = XL0 + di * kQOne + x1 - x0;
+        const int ZL0 = lz * kQOne + z0, ZL1 = ZL0 + dk * kQOne + z1 - z0;
+        const int bxl = min(XL0, XL1) >> kQBits, bzl = min(ZL0, ZL1) >> kQBits;
+        int S0x[3], S1x[3], S0z[3], S1z[3];
+        hat3(XL0 - bxl * kQOne, S0x[0], S0x[1], S0x[2]);
+        hat3(XL1 - bxl * kQOne, S1x[0], S1x[1], S1x[2]);
+        hat3(ZL0 - bzl * kQOne, S0z[0], S0z[1], S0z[2]);
+        hat3(ZL1 - bzl * kQOne, S1z[0], S1z[1], S1z[2]);
+        const int b0 = bzl * W + bxl;
+        if (S.jsign != 0) {
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                const long long wz = (long long)(S0z[b] + S1z[b]);
+                long long acc = -(long long)(S1x[0] - S0x[0]) * wz;
+                wadd(w, 1, b0 + b * W, sg * acc);
+                acc -= (long long)(S1x[1] - S0x[1]) * wz;
+                wadd(w, 1, b0 + b * W + 1, sg * acc);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const long long wx = (long long)(S0x[c] + S1x[c]);
+                long long acc = -(long long)(S1z[0] - S0z[0]) * wx;
+                wadd(w, 3, b0 + c, sg * acc);
+                acc -= (long long)(S1z[1] - S0z[1]) * wx;
+                wadd(w, 3, b0 + W + c, sg * acc);
+            }
+            if (V != 0) {
+                const long long sv = sg * (long long)V;
+#pragma unroll
+                for (int b = 0; b < 3; b++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        wadd(w, 2, b0 + b * W + c,
+                             sv * (2LL * S0x[c] * S0z[b] + (long long)S1x[c] * S0z[b] + (long long)S0x[c] * S1z[b] +
+                                   2LL * S1x[c] * S1z[b]));
+            }
+        }
+        if (S.pair) {
 #pragma unroll
             for (int b = 0; b < 3; b++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    long long w6 = 2LL * S0x[c] * S0z[b] + (long long)S1x[c] * S0z[b] + (long long)S0x[c] * S1z[b] +
-                                   2LL * S1x[c] * S1z[b];
-                    dep(local, s_jy, a.J[1], W, nx, bzl + b, bxl + c, gbz + b, gbx + c, sv * w6);
-                }
+                for (int c = 0; c < 3; c++) wadd(w, 0, b0 + b * W + c, (long long)S1x[c] * S1z[b]);
         }
-    }
-    if (S.pair) {                                           // node density at the new position
-#pragma unroll
-        for (int b = 0; b < 3; b++)
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                dep(local, s_rho, a.rho_next, W, nx, bzl + b, bxl + c, gbz + b, gbx + c,
-                    (long long)S1x[c] * S1z[b]);
+    } else {
+        deposit_global(a.rho_next, a.J[0], a.J[1], a.J[2], nx, i * kQOne + x0, k * kQOne + z0,
+                       (i + di) * kQOne + x1, (k + dk) * kQOne + z1, S.jsign, V, S.pair);
     }
 
-    S.a.cell[p] = k1 * nx + i1;
-    S.a.fx[p] = nfx;
-    S.a.fz[p] = nfz;
-    S.a.ux[p] = ux;
-    S.a.uy[p] = uy;
-    S.a.uz[p] = uz;
+    cell = (k + dk) * nx + wrap_x(i + di, nx);
+    fx_io = nfx;
+    fz_io = nfz;
 }
 
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock) k_particles(const StepArgs a)
+__global__ void __launch_bounds__(kBlock, 3) k_particles(const StepArgs a)
 {
-    extern __shared__ u64 smem[];
+    extern __shared__ unsigned smem[];
     const int W = a.W, WW = W * W;
-    u64* s_rho = smem;
-    u64* s_jx = smem + WW;
-    u64* s_jy = smem + 2 * WW;
-    u64* s_jz = smem + 3 * WW;
+    Window w;
+    w.W = W;
+    for (int q = 0; q < 4; q++) {
+        w.lo[q] = smem + (2 * q) * WW;
+        w.hi[q] = reinterpret_cast<int*>(smem + (2 * q + 1) * WW);
+    }
+    float* fbase = reinterpret_cast<float*>(smem + 8 * WW);
+    for (int q = 0; q < 6; q++) w.f[q] = fbase + q * WW;
+    w.nh = fbase + 6 * WW;
+    unsigned* chunk = smem + 15 * WW;
+    int* c_cell = reinterpret_cast<int*>(chunk);
+    float* c_f[5];
+    for (int q = 0; q < 5; q++) c_f[q] = reinterpret_cast<float*>(chunk + (q + 1) * kChunkWords);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         int cnt = 0;
 #pragma unroll
         for (int s = 0; s < 2; s++)
             if (s < a.nsp) cnt += a.sp[s].tile_start[t + 1] - a.sp[s].tile_start[t];
         if (cnt == 0) continue;
-        for (int j = threadIdx.x; j < 4 * WW; j += blockDim.x) smem[j] = 0;
-        __syncthreads();
         const int tx = t % a.ntx, tz = t / a.ntx;
-        const int ox = tx * a.T - kMargin - 1, oz = tz * a.T - kMargin - 1;
+        w.ox = tx * a.T - kMargin - 1;
+        w.oz = tz * a.T - kMargin - 1;
+        // stage the window: zero accumulators, fields, pair density (wall rows doubled)
+        for (int j = threadIdx.x; j < WW; j += blockDim.x) {
+            const int b = j / W, c = j - b * W;
+#pragma unroll
+            for (int q = 0; q < 4; q++) { w.lo[q][j] = 0u; w.hi[q][j] = 0; }
+            const int gx = wrap_any(w.ox + c, a.nx);
+            const int gz = w.oz + b;
+            const int gn = min(max(gz, 0), a.nz);          // node rows 0..nz
+            const int gh = min(max(gz, 0), a.nz - 1);      // half rows 0..nz-1 (edge rows repeat)
+            const size_t in = (size_t)gn * a.nx + gx, ih = (size_t)gh * a.nx + gx;
+            if (FULL) {
+                w.f[0][j] = __ldg(a.F[0] + in);
+                w.f[1][j] = __ldg(a.F[1] + in);
+                w.f[2][j] = __ldg(a.F[2] + ih);
+                w.f[3][j] = __ldg(a.F[3] + ih);
+                w.f[4][j] = __ldg(a.F[4] + ih);
+                w.f[5][j] = __ldg(a.F[5] + in);
+            }
+            const long long r = (long long)__ldg(a.rho_cur + in);
+            w.nh[j] = a.rho_s * (float)((gn == 0 || gn == a.nz) ? 2 * r : r);
+        }
+        __syncthreads();
 #pragma unroll
         for (int s = 0; s < 2; s++) {
             if (s >= a.nsp) break;
-            const int p0 = a.sp[s].tile_start[t], p1 = a.sp[s].tile_start[t + 1];
-            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x)
-                process_particle<FULL>(a, a.sp[s], p, s_rho, s_jx, s_jy, s_jz, ox, oz);
+            const Species& S = a.sp[s];
+            const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
+            for (int c0 = p0; c0 < p1; c0 += kChunk) {
+                const int n = min(kChunk, p1 - c0);
+                const int rows = (n + 31) >> 5;            // particles per lane row
+                // coalesced load: chunk index ci -> (row ci / rows, column ci % rows)
+                for (int ci = threadIdx.x; ci < n; ci += kBlock) {
+                    const int r = ci / rows, col = ci - r * rows;
+                    const int slot = col * kPitch + r;
+                    c_cell[slot] = S.a.cell[c0 + ci];
+                    c_f[0][slot] = S.a.fx[c0 + ci];
+                    c_f[1][slot] = S.a.fz[c0 + ci];
+                    c_f[2][slot] = S.a.ux[c0 + ci];
+                    c_f[3][slot] = S.a.uy[c0 + ci];
+                    c_f[4][slot] = S.a.uz[c0 + ci];
+                }
+                __syncthreads();
+                // transposed processing: lane l takes row l, so lanes are `rows` particles apart
+                for (int col = warp; col < rows; col += kWarps) {
+                    const int ci = lane * rows + col;
+                    if (ci < n) {
+                        const int slot = col * kPitch + lane;
+                        int cell = c_cell[slot];
+                        float fx = c_f[0][slot], fz = c_f[1][slot], ux = c_f[2][slot], uy = c_f[3][slot],
+                              uz = c_f[4][slot];
+                        process_particle<FULL>(a, S, w, cell, fx, fz, ux, uy, uz);
+                        c_cell[slot] = cell;
+                        c_f[0][slot] = fx;
+                        c_f[1][slot] = fz;
+                        c_f[2][slot] = ux;
+                        c_f[3][slot] = uy;
+                        c_f[4][slot] = uz;
+                    }
+                }
+                __syncthreads();
+                for (int ci = threadIdx.x; ci < n; ci += kBlock) {
+                    const int r = ci / rows, col = ci - r * rows;
+                    const int slot = col * kPitch + r;
+                    S.a.cell[c0 + ci] = c_cell[slot];
+                    S.a.fx[c0 + ci] = c_f[0][slot];
+                    S.a.fz[c0 + ci] = c_f[1][slot];
+                    S.a.ux[c0 + ci] = c_f[2][slot];
+                    S.a.uy[c0 + ci] = c_f[3][slot];
+                    S.a.uz[c0 + ci] = c_f[4][slot];
+                }
+                __syncthreads();
+            }
         }
-        __syncthreads();
         for (int j = threadIdx.x; j < WW; j += blockDim.x) {
             const int b = j / W, c = j - b * W;
-            const int gz = oz + b;
+            const int gz = w.oz + b;
             if (gz < 0 || gz > a.nz) continue;
-            const size_t g = (size_t)gz * a.nx + wrap_any(ox + c, a.nx);
-            u64 v;
-            if ((v = s_rho[j]) != 0) atomicAdd(a.rho_next + g, v);
-            if ((v = s_jx[j]) != 0) atomicAdd(a.J[0] + g, v);
-            if ((v = s_jy[j]) != 0) atomicAdd(a.J[1] + g, v);
-            if ((v = s_jz[j]) != 0) atomicAdd(a.J[2] + g, v);
+            const size_t g = (size_t)gz * a.nx + wrap_any(w.ox + c, a.nx);
+            u64* dst[4] = {a.rho_next, a.J[0], a.J[1], a.J[2]};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const long long v = ((long long)w.hi[q][j] << 32) + (long long)w.lo[q][j];
+                if (v != 0) atomicAdd(dst[q] + g, (u64)v);
+            }
         }
         __syncthreads();
     }
 }
 
+size_t particle_smem_bytes(int W) { return sizeof(unsigned) * ((size_t)15 * W * W + 6 * kChunkWords); }
+
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
 {
-    const size_t shmem = 4 * sizeof(u64) * (size_t)a.W * a.W;
+    const size_t shmem = particle_smem_bytes(a.W);
     static size_t configured = 0;
     if (shmem > 48 * 1024 && shmem > configured) {
         cudaFuncSetAttribute(k_particles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
@@ -222,7 +468,7 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
         configured = shmem;
     }
     int grid = a.ntiles;
-    const int cap = c.nsm * 4;
+    const int cap = c.nsm * 3;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     if (a.full) k_particles<true><<<grid, kBlock, shmem, st>>>(a);

@@ -54,6 +54,7 @@ struct Species {
 // Everything a kernel of the step needs, passed by value.
 struct StepArgs {
     int32_t nx, nz, T, ntx, ntz, ntiles, W;   // W: window edge (nodes) of a tile
+    unsigned nx_magic;                        // floor(2^32 / nx) for the cell -> (i, k) split
     int32_t full;                             // fields and Lorentz force on
     float cdt_dx;                             // c dt / dx
     float rho_s;                              // node sum -> n / n0
