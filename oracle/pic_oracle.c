@@ -234,15 +234,25 @@ static void deposit_current_one(int nx, int nz, int64_t* J2x, int64_t* J6y, int6
     }
 }
 
-/* J_y code: V = rint(beta_y * 2^18), beta_y = u_y / sqrt(1 + u^2), all in FP32 without fused
- * multiply-add, so that the decision is the kernel's (this file is built with contraction off) */
+/* J_y code: V = rint(beta_y * 2^18), beta_y = u_y / gamma, all in FP32 without fused
+ * multiply-add, so that the decision is the kernel's (this file is built with contraction off).
+ * The kernel's definition of 1/gamma: for u^2 < 2^-10 the series 1 - u^2 (1/2 - 3/8 u^2),
+ * otherwise 1 / sqrt(1 + u^2). */
 int64_t oracle_jy_code(float ux, float uy, float uz)
 {
     float u2 = ux * ux;
     u2 = u2 + uy * uy;
     u2 = u2 + uz * uz;
-    float g = sqrtf(1.0f + u2);
-    float by = uy / g;
+    float by;
+    if (u2 < 0.0009765625f) {
+        float t = u2 * 0.375f;
+        t = 0.5f - t;
+        t = u2 * t;
+        by = uy * (1.0f - t);
+    } else {
+        float g = sqrtf(1.0f + u2);
+        by = uy / g;
+    }
     return (int64_t)rintf(by * 262144.0f);
 }
 

@@ -32,16 +32,11 @@ __global__ void k_pair_force(const int32_t* __restrict__ cell, const float* __re
         const int k = c / nx, i = c - k * nx;
         float dens, dnx, dnz;
         gather_density(rho, nx, nz, rho_s, i, k, fx[p], fz[p], dens, dnx, dnz);
-        float Fx = 0.f, Fz = 0.f;
-        if (dens > 0.0f) {
-            const float cr = cbrtf(dens);
-            const float inv43 = 1.0f / (dens * cr);
-            Fx = f_unit * pair_axis(dens, cr, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
-            Fz = f_unit * pair_axis(dens, cr, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
-        }
-        out[3 * p + 0] = Fx;
+        float Fx, Fz;
+        pair_force_xz(dens, dnx, dnz, h_coef, pot_mode, c_att, s_rep, Fx, Fz);
+        out[3 * p + 0] = f_unit * Fx;
         out[3 * p + 1] = 0.0f;
-        out[3 * p + 2] = Fz;
+        out[3 * p + 2] = f_unit * Fz;
     }
 }
 

@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(kEBlock) k_energy(const EnergyArgs a)
                 float n, dnx, dnz;
                 gather_density(a.rho, a.nx, a.nz, a.rho_s, i, k, S.fx[p], S.fz[p], n, dnx, dnz);
                 if (n > 0.0f) {
-                    const float cr = cbrtf(n);
-                    const float inv43 = 1.0f / (n * cr);
+                    const float cr = fast_cbrt(n);
+                    const float inv43 = fast_rcp(n * cr);
                     float e = pair_energy_axis(cr, inv43, dnx, a.h_coef, a.pot_mode, a.c_att, a.s_rep) +
                               pair_energy_axis(cr, inv43, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep) +
                               2.0f * branch(a.pot_mode, a.c_att, a.s_rep, cr) * lj_U_inv(cr);

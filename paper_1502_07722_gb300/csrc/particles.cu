@@ -49,17 +49,38 @@ __device__ __forceinline__ void acc64(unsigned* lo, int* hi, long long v)
     if (h != 0) atomicAdd(hi, h);
 }
 
+// shared-memory 32-bit reduction without a returned value
+__device__ __forceinline__ void sred32(unsigned* p, unsigned v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
 struct Window {
     unsigned* lo[4];     // 0: node density, 1: J_x, 2: J_y, 3: J_z
     int* hi[4];
     float* f[6];
     float* nh;
     int ox, oz, W;
+    bool rho16;          // node density kept as (sum of high 16 bits, sum of low 16 bits)
 };
 
 __device__ __forceinline__ void wadd(const Window& w, int q, int idx, long long v)
 {
     if (v != 0) acc64(w.lo[q] + idx, w.hi[q] + idx, v);
+}
+
+// Node-density deposit r (0 <= r <= 2^32). When the tile holds fewer than 2^16 pair particles,
+// the low and high 16 bits are summed separately with plain reductions (neither sum can reach
+// 2^32); otherwise the exact carry form is used.
+__device__ __forceinline__ void wrho(const Window& w, int idx, unsigned long long r)
+{
+    if (r == 0) return;
+    if (w.rho16) {
+        sred32(w.lo[0] + idx, (unsigned)(r & 0xFFFFu));
+        sred32(reinterpret_cast<unsigned*>(w.hi[0]) + idx, (unsigned)(r >> 16));
+    } else {
+        acc64(w.lo[0] + idx, w.hi[0] + idx, (long long)r);
+    }
 }
 
 // exact cell -> (i, k): q = floor(cell / nx) from a multiply-high and one correction
@@ -203,11 +224,11 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
         }
         if (S.pair) { n = g[6]; dnx = g[7]; dnz = g[8]; }
     }
-    if (S.pair && n > 0.0f) {
-        const float c = cbrtf(n);
-        const float inv43 = 1.0f / (n * c);
-        kx += S.p_kick * pair_axis(n, c, inv43, dnx, a.h_coef, a.pot_mode, a.c_att, a.s_rep);
-        kz += S.p_kick * pair_axis(n, c, inv43, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+    if (S.pair) {
+        float pfx, pfz;
+        pair_force_xz(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz);
+        kx += S.p_kick * pfx;
+        kz += S.p_kick * pfz;
     }
     const float ux0 = ux, uy0 = uy, uz0 = uz;
     // relativistic Boris: half kick, rotation, half kick
@@ -215,7 +236,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     if (FULL) {
         const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
         const float tx = S.b_rot * ig * bx, ty = S.b_rot * ig * by, tz = S.b_rot * ig * bz;
-        const float s = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+        const float s = 2.0f * fast_rcp(1.0f + tx * tx + ty * ty + tz * tz);
         const float px = ux + (uy * tz - uz * ty);
         const float py = uy + (uz * tx - ux * tz);
         const float pz = uz + (ux * ty - uy * tx);
@@ -277,11 +298,11 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
             }
         }
         if (S.pair) {
-            const long long ax = kQOne - x1, az = kQOne - z1;
-            wadd(w, 0, base, ax * az);
-            wadd(w, 0, base + 1, (long long)x1 * az);
-            wadd(w, 0, base + W, ax * z1);
-            wadd(w, 0, base + W + 1, (long long)x1 * z1);
+            const unsigned ax = kQOne - x1, az = kQOne - z1;
+            wrho(w, base, (unsigned long long)ax * az);
+            wrho(w, base + 1, (unsigned long long)x1 * az);
+            wrho(w, base + W, (unsigned long long)ax * (unsigned)z1);
+            wrho(w, base + W + 1, (unsigned long long)x1 * (unsigned)z1);
         }
     } else if (inwin) {
         // a cell edge was crossed: 3 x 3 Esirkepov stencil in the window
@@ -326,7 +347,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
 #pragma unroll
             for (int b = 0; b < 3; b++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) wadd(w, 0, b0 + b * W + c, (long long)S1x[c] * S1z[b]);
+                for (int c = 0; c < 3; c++) wrho(w, b0 + b * W + c, (unsigned long long)S1x[c] * (unsigned)S1z[b]);
         }
     } else {
         deposit_global(a.rho_next, a.J[0], a.J[1], a.J[2], nx, i * kQOne + x0, k * kQOne + z0,
@@ -339,7 +360,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
 }
 
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock, 3) k_particles(const StepArgs a)
+__global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
 {
     extern __shared__ unsigned smem[];
     const int W = a.W, WW = W * W;
@@ -367,6 +388,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_particles(const StepArgs a)
         const int tx = t % a.ntx, tz = t / a.ntx;
         w.ox = tx * a.T - kMargin - 1;
         w.oz = tz * a.T - kMargin - 1;
+        w.rho16 = a.sp[0].tile_start[t + 1] - a.sp[0].tile_start[t] < 65536;
         // stage the window: zero accumulators, fields, pair density (wall rows doubled)
         for (int j = threadIdx.x; j < WW; j += blockDim.x) {
             const int b = j / W, c = j - b * W;
@@ -448,7 +470,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_particles(const StepArgs a)
             u64* dst[4] = {a.rho_next, a.J[0], a.J[1], a.J[2]};
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const long long v = ((long long)w.hi[q][j] << 32) + (long long)w.lo[q][j];
+                long long v = ((long long)w.hi[q][j] << 32) + (long long)w.lo[q][j];
+                if (q == 0 && w.rho16) v = ((long long)(unsigned)w.hi[q][j] << 16) + (long long)w.lo[q][j];
                 if (v != 0) atomicAdd(dst[q] + g, (u64)v);
             }
         }
@@ -462,13 +485,16 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
 {
     const size_t shmem = particle_smem_bytes(a.W);
     static size_t configured = 0;
-    if (shmem > 48 * 1024 && shmem > configured) {
+    if (shmem > configured) {
         cudaFuncSetAttribute(k_particles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         cudaFuncSetAttribute(k_particles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+        // the largest carve-out, so that several CTAs fit on one SM
+        cudaFuncSetAttribute(k_particles<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_particles<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         configured = shmem;
     }
     int grid = a.ntiles;
-    const int cap = c.nsm * 3;
+    const int cap = c.nsm * 4;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     if (a.full) k_particles<true><<<grid, kBlock, shmem, st>>>(a);

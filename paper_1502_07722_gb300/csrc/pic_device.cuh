@@ -141,17 +141,48 @@ __device__ __forceinline__ void boris(float& ux, float& uy, float& uz, float ex,
     ux += e_kick * ex; uy += e_kick * ey; uz += e_kick * ez;
 }
 
-// J_y code V = rint(beta_y 2^18), taken in FP32 with explicit rounding (no fused multiply-add)
-// so that it is reproducible outside the GPU.
+// J_y code V = rint(beta_y 2^18), beta_y = u_y / gamma, taken in FP32 with explicit rounding (no
+// fused multiply-add) so that it is reproducible outside the GPU. For u^2 < 2^-10 the inverse
+// Lorentz factor is the series 1 - u^2 (1/2 - 3/8 u^2) (next term 5/16 u^6 < 3e-10); otherwise
+// it is 1 / sqrt(1 + u^2) with IEEE square root and division.
 __device__ __forceinline__ int jy_code(float ux, float uy, float uz)
 {
     float u2 = __fmul_rn(ux, ux);
     u2 = __fadd_rn(u2, __fmul_rn(uy, uy));
     u2 = __fadd_rn(u2, __fmul_rn(uz, uz));
-    float g = __fsqrt_rn(__fadd_rn(1.0f, u2));
-    float by = __fdiv_rn(uy, g);
+    float by;
+    if (u2 < 0.0009765625f) {
+        float t = __fmul_rn(u2, 0.375f);
+        t = __fsub_rn(0.5f, t);
+        t = __fmul_rn(u2, t);
+        by = __fmul_rn(uy, __fsub_rn(1.0f, t));
+    } else {
+        by = __fdiv_rn(uy, __fsqrt_rn(__fadd_rn(1.0f, u2)));
+    }
     return __float2int_rn(__fmul_rn(by, 262144.0f));
 }
+
+// approximate transcendental helpers (hardware ex2 / lg2 / rcp, relative error ~1e-7)
+__device__ __forceinline__ float fast_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fast_lg2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fast_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// n^(1/3) for n > 0
+__device__ __forceinline__ float fast_cbrt(float n) { return fast_ex2(fast_lg2(n) * (1.0f / 3.0f)); }
 
 // Fixed-point offset Q(f) = rint(f 2^16) in [0, 2^16].
 __device__ __forceinline__ int qoff(float f) { return __float2int_rn(f * 65536.0f); }
@@ -163,6 +194,25 @@ __device__ __forceinline__ void hat3(int d, int& s0, int& s1, int& s2)
     s0 = max(0, kQOne - d);
     s1 = kQOne - abs(d - kQOne);
     s2 = max(0, d - kQOne);
+}
+
+}  // namespace gbpic
+
+namespace gbpic {
+
+// Pair-potential half kick components (units D / r0) along x and z at local density n (units
+// n0) with gradient (dnx, dnz) per cell: Eqs. (1)-(3) via pair_axis.
+__device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, float h_coef, int pot_mode, float c_att,
+                                              float s_rep, float& fx, float& fz)
+{
+    fx = 0.0f;
+    fz = 0.0f;
+    if (n > 0.0f) {
+        const float c = fast_cbrt(n);
+        const float inv43 = fast_rcp(n * c);
+        fx = pair_axis(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
+        fz = pair_axis(n, c, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
+    }
 }
 
 }  // namespace gbpic

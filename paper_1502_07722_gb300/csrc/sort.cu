@@ -18,10 +18,19 @@ __device__ __forceinline__ int cell_key(int cell, int nx, int T, int ntx)
     return (tz * ntx + tx) * T * T + (k - tz * T) * T + (i - tx * T);
 }
 
+// Particles arrive nearly sorted (the previous sort plus a few steps of drift), so the lanes of
+// a warp usually share one or two keys: one atomic per distinct key per warp.
 __global__ void k_count(const int32_t* __restrict__ cell, int64_t n, int nx, int T, int ntx, int32_t* count)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(count + cell_key(cell[p], nx, T, ntx), 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nround = (n + 31) & ~(int64_t)31;     // whole warps stay in the loop together
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nround; p += stride) {
+        const bool valid = p < n;
+        const int key = valid ? cell_key(cell[p], nx, T, ntx) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(count + key, __popc(peers));
+    }
 }
 
 // exclusive scan of kScanItems elements per block; block totals to bsum
@@ -105,9 +114,21 @@ __global__ void k_tile_starts(const int32_t* __restrict__ off, int ntiles, int T
 
 __global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, int nx, int T, int ntx, int32_t* cursor)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const int c = src.cell[p];
-        const int q = atomicAdd(cursor + cell_key(c, nx, T, ntx), 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nround = (n + 31) & ~(int64_t)31;
+    const unsigned lane = threadIdx.x & 31;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nround; p += stride) {
+        const bool valid = p < n;
+        const int c = valid ? src.cell[p] : 0;
+        const int key = valid ? cell_key(c, nx, T, ntx) : -1;
+        // one cursor atomic per distinct key in the warp; lanes take consecutive slots
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (valid && (int)lane == leader) base = atomicAdd(cursor + key, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (!valid) continue;
+        const int q = base + __popc(peers & ((1u << lane) - 1u));
         dst.cell[q] = c;
         dst.fx[q] = src.fx[p];
         dst.fz[q] = src.fz[p];
