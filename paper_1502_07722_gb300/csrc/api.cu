@@ -383,7 +383,8 @@ int pic_step(pic_ctx* h, int32_t nsteps)
             if (r) return r;
         }
         for (int q = 0; q < 3; q++) CK(cudaMemsetAsync(c.J[q], 0, 8 * c.nn, c.stream));
-        CK(cudaMemsetAsync(c.rho[1 - c.cur], 0, 8 * c.nn, c.stream));
+        // the next node density starts from the current one; the particle kernel adds the changes
+        CK(cudaMemcpyAsync(c.rho[1 - c.cur], c.rho[c.cur], 8 * c.nn, cudaMemcpyDeviceToDevice, c.stream));
         StepArgs a = make_step_args(c);
         int r = ev_begin(h, 0);
         if (r) return r;

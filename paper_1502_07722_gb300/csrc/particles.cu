@@ -16,9 +16,15 @@
 //    coalesced accesses, processed transposed, so that lane l of a warp takes the particle R
 //    places after lane l-1 in the cell-sorted order. Lanes then sit in different cells and their
 //    deposits rarely meet on one address;
+//  * the node density is updated incrementally: the next density starts as a copy of the
+//    current one and each pair particle adds S(new) - S(old) only when its fixed-point position
+//    changed. Ions move ~1e-7 cells per step against a quantum of 1.5e-5 cells, so most of them
+//    deposit nothing; the integer result equals a full re-deposit bit for bit;
 //  * a particle that stays in its cell (almost all of them) deposits on the four corners of the
 //    cell; a particle that crossed a cell edge uses the 3 x 3 Esirkepov stencil; a particle that
 //    drifted beyond the margin since the last sort uses global memory (rare);
+//  * the code is specialised per species kind (ion, electron, neutral atom), so no per-particle
+//    branch tests a species property;
 //  * the window is flushed with one global 64-bit atomic per non-zero node.
 // Integer sums make every result independent of the order of the additions.
 #include "pic_device.cuh"
@@ -49,38 +55,17 @@ __device__ __forceinline__ void acc64(unsigned* lo, int* hi, long long v)
     if (h != 0) atomicAdd(hi, h);
 }
 
-// shared-memory 32-bit reduction without a returned value
-__device__ __forceinline__ void sred32(unsigned* p, unsigned v)
-{
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
-}
-
 struct Window {
-    unsigned* lo[4];     // 0: node density, 1: J_x, 2: J_y, 3: J_z
+    unsigned* lo[4];     // 0: node density change, 1: J_x, 2: J_y, 3: J_z
     int* hi[4];
     float* f[6];
     float* nh;
     int ox, oz, W;
-    bool rho16;          // node density kept as (sum of high 16 bits, sum of low 16 bits)
 };
 
 __device__ __forceinline__ void wadd(const Window& w, int q, int idx, long long v)
 {
     if (v != 0) acc64(w.lo[q] + idx, w.hi[q] + idx, v);
-}
-
-// Node-density deposit r (0 <= r <= 2^32). When the tile holds fewer than 2^16 pair particles,
-// the low and high 16 bits are summed separately with plain reductions (neither sum can reach
-// 2^32); otherwise the exact carry form is used.
-__device__ __forceinline__ void wrho(const Window& w, int idx, unsigned long long r)
-{
-    if (r == 0) return;
-    if (w.rho16) {
-        sred32(w.lo[0] + idx, (unsigned)(r & 0xFFFFu));
-        sred32(reinterpret_cast<unsigned*>(w.hi[0]) + idx, (unsigned)(r >> 16));
-    } else {
-        acc64(w.lo[0] + idx, w.hi[0] + idx, (long long)r);
-    }
 }
 
 // exact cell -> (i, k): q = floor(cell / nx) from a multiply-high and one correction
@@ -134,6 +119,7 @@ __device__ __noinline__ void gather_global(const float* F0, const float* F1, con
 // global fixed-point coordinates; X1 may lie outside [0, nx 2^16) (periodic x).
 __device__ __noinline__ void deposit_global(u64* rho_next, u64* Jx, u64* Jy, u64* Jz, int nx, int X0, int Z0,
                                             int X1, int Z1, int jsign, int V, int pair)
+// pair != 0: the node density changes by S(X1, Z1) - S(X0, Z0)
 {
     const int bx = min(X0, X1) >> kQBits, bz = min(Z0, Z1) >> kQBits;
     int S0x[3], S1x[3], S0z[3], S1z[3];
@@ -160,7 +146,7 @@ __device__ __noinline__ void deposit_global(u64* rho_next, u64* Jx, u64* Jy, u64
                 if (w6 != 0) atomicAdd(Jy + g, (u64)(sg * V * w6));
             }
             if (pair) {
-                const long long r = (long long)S1x[c] * S1z[b];
+                const long long r = (long long)S1x[c] * S1z[b] - (long long)S0x[c] * S0z[b];
                 if (r != 0) atomicAdd(rho_next + g, (u64)r);
             }
         }
@@ -177,11 +163,21 @@ __device__ __noinline__ void deposit_global(u64* rho_next, u64* Jx, u64* Jy, u64
     }
 }
 
+// Species kinds the particle code is specialised for.
+enum Kind { kIon = 0, kElectron = 1, kAtom = 2 };
+
 // One particle: state in (cell, fx, fz, ux, uy, uz) is replaced by the new state.
-template <bool FULL>
+//   kIon:      Lorentz force + pair force, current (charge +e), node density
+//   kElectron: Lorentz force, current (charge -e)
+//   kAtom:     pair force, node density (neutral atoms of the transport stage)
+template <int KIND>
 __device__ __forceinline__ void process_particle(const StepArgs& a, const Species& S, const Window& w, int& cell,
                                                  float& fx_io, float& fz_io, float& ux, float& uy, float& uz)
 {
+    constexpr bool kFields = KIND != kAtom;
+    constexpr bool kPair = KIND != kElectron;
+    constexpr bool kCurrent = KIND != kAtom;
+    constexpr int kSign = KIND == kElectron ? -1 : 1;
     const int nx = a.nx, nz = a.nz, W = w.W;
     const float fx = fx_io, fz = fz_io;
     int i, k;
@@ -198,7 +194,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     float kx = 0.f, ky = 0.f, kz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
     float n = 0.f, dnx = 0.f, dnz = 0.f;
     if (inwin) {
-        if (FULL) {
+        if (kFields) {
             kx = S.e_kick * win_gather(w.f[0], W, lx, lz, fx, fz, 1, 0);
             ky = S.e_kick * win_gather(w.f[1], W, lx, lz, fx, fz, 0, 0);
             kz = S.e_kick * win_gather(w.f[2], W, lx, lz, fx, fz, 0, 1);
@@ -206,7 +202,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
             by = win_gather(w.f[4], W, lx, lz, fx, fz, 1, 1);
             bz = win_gather(w.f[5], W, lx, lz, fx, fz, 1, 0);
         }
-        if (S.pair) {
+        if (kPair) {
             const float* q = w.nh + lz * W + lx;
             const float n00 = q[0], n10 = q[1], n01 = q[W], n11 = q[W + 1];
             const float gx = 1.0f - fx, gz = 1.0f - fz;
@@ -216,15 +212,15 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
         }
     } else {
         float g[9];
-        gather_global(a.F[0], a.F[1], a.F[2], a.F[3], a.F[4], a.F[5], a.rho_cur, nx, nz, a.rho_s, FULL ? 1 : 0,
-                      S.pair, i, k, fx, fz, g);
-        if (FULL) {
+        gather_global(a.F[0], a.F[1], a.F[2], a.F[3], a.F[4], a.F[5], a.rho_cur, nx, nz, a.rho_s, kFields ? 1 : 0,
+                      kPair ? 1 : 0, i, k, fx, fz, g);
+        if (kFields) {
             kx = S.e_kick * g[0]; ky = S.e_kick * g[1]; kz = S.e_kick * g[2];
             bx = g[3]; by = g[4]; bz = g[5];
         }
-        if (S.pair) { n = g[6]; dnx = g[7]; dnz = g[8]; }
+        if (kPair) { n = g[6]; dnx = g[7]; dnz = g[8]; }
     }
-    if (S.pair) {
+    if (kPair) {
         float pfx, pfz;
         pair_force_xz(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz);
         kx += S.p_kick * pfx;
@@ -233,7 +229,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     const float ux0 = ux, uy0 = uy, uz0 = uz;
     // relativistic Boris: half kick, rotation, half kick
     ux += kx; uy += ky; uz += kz;
-    if (FULL) {
+    if (kFields) {
         const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
         const float tx = S.b_rot * ig * bx, ty = S.b_rot * ig * by, tz = S.b_rot * ig * bz;
         const float s = 2.0f * fast_rcp(1.0f + tx * tx + ty * ty + tz * tz);
@@ -268,41 +264,46 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
         nfz -= (float)dk;
         if (nfz >= 1.0f) { nfz = 0.0f; dk += 1; }
     }
+    cell = (k + dk) * nx + wrap_x(i + di, nx);
+    fx_io = nfx;
+    fz_io = nfz;
 
     const int x0 = qoff(fx), x1 = qoff(nfx), z0 = qoff(fz), z1 = qoff(nfz);
-    const long long sg = S.jsign;
+    const bool moved = (di | dk) != 0 || x1 != x0 || z1 != z0;
     // |u_y| < 2^-19 gives |beta_y| 2^18 < 1/2, i.e. V = 0 without evaluating the code
-    const int V = (S.jsign != 0 && fabsf(uy) >= 1.9073486328125e-06f) ? jy_code(ux, uy, uz) : 0;
-    if (inwin && di == 0 && dk == 0) {
+    const int V = (kCurrent && fabsf(uy) >= 1.9073486328125e-06f) ? kSign * jy_code(ux, uy, uz) : 0;
+    if (!moved && V == 0) return;                 // nothing to deposit (most ions)
+
+    if (inwin && (di | dk) == 0) {
         // the particle stays in its cell: stencil = the four corners of the cell
         const int base = lz * W + lx;
-        if (S.jsign != 0) {
-            const int dX = x1 - x0, dZ = z1 - z0;
+        if (kCurrent) {
+            const int dX = kSign * (x1 - x0), dZ = kSign * (z1 - z0);
             if (dX != 0) {
-                wadd(w, 1, base, sg * ((long long)dX * (2 * kQOne - z0 - z1)));
-                wadd(w, 1, base + W, sg * ((long long)dX * (z0 + z1)));
+                acc64(w.lo[1] + base, w.hi[1] + base, (long long)dX * (2 * kQOne - z0 - z1));
+                acc64(w.lo[1] + base + W, w.hi[1] + base + W, (long long)dX * (z0 + z1));
             }
             if (dZ != 0) {
-                wadd(w, 3, base, sg * ((long long)dZ * (2 * kQOne - x0 - x1)));
-                wadd(w, 3, base + 1, sg * ((long long)dZ * (x0 + x1)));
+                acc64(w.lo[3] + base, w.hi[3] + base, (long long)dZ * (2 * kQOne - x0 - x1));
+                acc64(w.lo[3] + base + 1, w.hi[3] + base + 1, (long long)dZ * (x0 + x1));
             }
             if (V != 0) {
                 // 6 Wy = 6 Q^2 - 3 Q (x0 + x1) - 3 Q (z0 + z1) + P on the lower-left corner, etc.
-                const long long P = 2LL * x0 * z0 + (long long)x1 * z0 + (long long)x0 * z1 + 2LL * x1 * z1;
+                const long long P = (long long)x0 * (2 * z0 + z1) + (long long)x1 * (z0 + 2 * z1);
                 const long long sx = 3LL * kQOne * (x0 + x1), sz = 3LL * kQOne * (z0 + z1);
-                const long long sv = sg * (long long)V;
-                wadd(w, 2, base, sv * (6LL * kQOne * kQOne - sx - sz + P));
-                wadd(w, 2, base + 1, sv * (sx - P));
-                wadd(w, 2, base + W, sv * (sz - P));
-                wadd(w, 2, base + W + 1, sv * P);
+                wadd(w, 2, base, V * (6LL * kQOne * kQOne - sx - sz + P));
+                wadd(w, 2, base + 1, V * (sx - P));
+                wadd(w, 2, base + W, V * (sz - P));
+                wadd(w, 2, base + W + 1, V * P);
             }
         }
-        if (S.pair) {
-            const unsigned ax = kQOne - x1, az = kQOne - z1;
-            wrho(w, base, (unsigned long long)ax * az);
-            wrho(w, base + 1, (unsigned long long)x1 * az);
-            wrho(w, base + W, (unsigned long long)ax * (unsigned)z1);
-            wrho(w, base + W + 1, (unsigned long long)x1 * (unsigned)z1);
+        if (kPair && moved) {
+            // node density change: S(new) - S(old) on the four corners
+            const long long a0 = kQOne - x0, a1 = kQOne - x1, c0 = kQOne - z0, c1 = kQOne - z1;
+            wadd(w, 0, base, a1 * c1 - a0 * c0);
+            wadd(w, 0, base + 1, (long long)x1 * c1 - (long long)x0 * c0);
+            wadd(w, 0, base + W, a1 * z1 - a0 * z0);
+            wadd(w, 0, base + W + 1, (long long)x1 * z1 - (long long)x0 * z0);
         }
     } else if (inwin) {
         // a cell edge was crossed: 3 x 3 Esirkepov stencil in the window
@@ -315,48 +316,45 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
         hat3(ZL0 - bzl * kQOne, S0z[0], S0z[1], S0z[2]);
         hat3(ZL1 - bzl * kQOne, S1z[0], S1z[1], S1z[2]);
         const int b0 = bzl * W + bxl;
-        if (S.jsign != 0) {
+        if (kCurrent) {
 #pragma unroll
             for (int b = 0; b < 3; b++) {
-                const long long wz = (long long)(S0z[b] + S1z[b]);
+                const long long wz = kSign * (long long)(S0z[b] + S1z[b]);
                 long long acc = -(long long)(S1x[0] - S0x[0]) * wz;
-                wadd(w, 1, b0 + b * W, sg * acc);
+                wadd(w, 1, b0 + b * W, acc);
                 acc -= (long long)(S1x[1] - S0x[1]) * wz;
-                wadd(w, 1, b0 + b * W + 1, sg * acc);
+                wadd(w, 1, b0 + b * W + 1, acc);
             }
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const long long wx = (long long)(S0x[c] + S1x[c]);
+                const long long wx = kSign * (long long)(S0x[c] + S1x[c]);
                 long long acc = -(long long)(S1z[0] - S0z[0]) * wx;
-                wadd(w, 3, b0 + c, sg * acc);
+                wadd(w, 3, b0 + c, acc);
                 acc -= (long long)(S1z[1] - S0z[1]) * wx;
-                wadd(w, 3, b0 + W + c, sg * acc);
+                wadd(w, 3, b0 + W + c, acc);
             }
             if (V != 0) {
-                const long long sv = sg * (long long)V;
 #pragma unroll
                 for (int b = 0; b < 3; b++)
 #pragma unroll
                     for (int c = 0; c < 3; c++)
                         wadd(w, 2, b0 + b * W + c,
-                             sv * (2LL * S0x[c] * S0z[b] + (long long)S1x[c] * S0z[b] + (long long)S0x[c] * S1z[b] +
-                                   2LL * S1x[c] * S1z[b]));
+                             V * (2LL * S0x[c] * S0z[b] + (long long)S1x[c] * S0z[b] + (long long)S0x[c] * S1z[b] +
+                                  2LL * S1x[c] * S1z[b]));
             }
         }
-        if (S.pair) {
+        if (kPair) {
 #pragma unroll
             for (int b = 0; b < 3; b++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) wrho(w, b0 + b * W + c, (unsigned long long)S1x[c] * (unsigned)S1z[b]);
+                for (int c = 0; c < 3; c++)
+                    wadd(w, 0, b0 + b * W + c, (long long)S1x[c] * S1z[b] - (long long)S0x[c] * S0z[b]);
         }
     } else {
+        // deposit_global applies the charge sign itself: hand it the unsigned code kSign * V
         deposit_global(a.rho_next, a.J[0], a.J[1], a.J[2], nx, i * kQOne + x0, k * kQOne + z0,
-                       (i + di) * kQOne + x1, (k + dk) * kQOne + z1, S.jsign, V, S.pair);
+                       (i + di) * kQOne + x1, (k + dk) * kQOne + z1, kCurrent ? kSign : 0, kSign * V, kPair ? 1 : 0);
     }
-
-    cell = (k + dk) * nx + wrap_x(i + di, nx);
-    fx_io = nfx;
-    fz_io = nfz;
 }
 
 template <bool FULL>
@@ -388,7 +386,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
         const int tx = t % a.ntx, tz = t / a.ntx;
         w.ox = tx * a.T - kMargin - 1;
         w.oz = tz * a.T - kMargin - 1;
-        w.rho16 = a.sp[0].tile_start[t + 1] - a.sp[0].tile_start[t] < 65536;
         // stage the window: zero accumulators, fields, pair density (wall rows doubled)
         for (int j = threadIdx.x; j < WW; j += blockDim.x) {
             const int b = j / W, c = j - b * W;
@@ -439,7 +436,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
                         int cell = c_cell[slot];
                         float fx = c_f[0][slot], fz = c_f[1][slot], ux = c_f[2][slot], uy = c_f[3][slot],
                               uz = c_f[4][slot];
-                        process_particle<FULL>(a, S, w, cell, fx, fz, ux, uy, uz);
+                        if (s == 0) process_particle<FULL ? kIon : kAtom>(a, S, w, cell, fx, fz, ux, uy, uz);
+                        else process_particle<kElectron>(a, S, w, cell, fx, fz, ux, uy, uz);
                         c_cell[slot] = cell;
                         c_f[0][slot] = fx;
                         c_f[1][slot] = fz;
@@ -470,8 +468,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
             u64* dst[4] = {a.rho_next, a.J[0], a.J[1], a.J[2]};
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                long long v = ((long long)w.hi[q][j] << 32) + (long long)w.lo[q][j];
-                if (q == 0 && w.rho16) v = ((long long)(unsigned)w.hi[q][j] << 16) + (long long)w.lo[q][j];
+                const long long v = ((long long)w.hi[q][j] << 32) + (long long)w.lo[q][j];
                 if (v != 0) atomicAdd(dst[q] + g, (u64)v);
             }
         }
