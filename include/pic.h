@@ -172,6 +172,35 @@ PIC_API int pic_sort(pic_ctx* ctx);
 PIC_API int pic_set_timing(pic_ctx* ctx, int32_t enable);
 PIC_API int pic_get_timing(pic_ctx* ctx, double ms[3], int64_t n[4]);
 
+/* Plain device arrays of one state, for pic_energy_noalloc. Species 1 is ignored in the
+ * transport mode. All six field components (zeros in the transport mode) and the node density
+ * of the pair species at the current positions are required. */
+typedef struct pic_state_view {
+    int64_t n[2];
+    const int32_t* cell[2];
+    const float* fx[2];
+    const float* fz[2];
+    const float* ux[2];
+    const float* uy[2];
+    const float* uz[2];
+    const float* F[6];          /* (nz+1)*nx each, PIC_EX..PIC_BZ */
+    const int64_t* rho;         /* (nz+1)*nx node sums, as pic_get_density returns them */
+} pic_state_view;
+
+/* The energies of pic_energy for a state given as plain device arrays, with no workspace and no
+ * allocation of any kind. The paper has no counterpart: this entry point serves callers that
+ * cannot allocate device memory (a host that owns every buffer and forbids further cudaMalloc,
+ * or code running while another component records a CUDA graph). The reduction's scratch is a
+ * fixed 40 KB array inside the library (1024 block records), reserved on every GPU that loads the
+ * library until the process exits; each call writes all of it that it reads, so nothing needs
+ * clearing. The first call on a device looks up the array's device address (do it before any
+ * stream capture). Calls that overlap on the GPU (two streams at once) share the array and race.
+ * cfg: the configuration the state belongs to (physical constants). in: device pointers.
+ * dev_out5: device double[5] receiving kinetic_ion, kinetic_electron, field_E, field_B, pair
+ * (J per metre of y). Work is queued on stream; the call does not synchronise. Refuses (PIC_EINVAL)
+ * particle counts above 2^31 - 1, grids outside 3 <= nx, 4 <= nz < 32768, and missing pointers. */
+PIC_API int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* in, double* dev_out5, void* stream);
+
 /* Static text for a return code. */
 PIC_API const char* pic_strerror(int code);
 

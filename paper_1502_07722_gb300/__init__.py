@@ -48,6 +48,12 @@ class pic_energy_t(ctypes.Structure):
                 ("step", ctypes.c_int64)]
 
 
+class pic_state_view(ctypes.Structure):
+    _P = ctypes.c_void_p
+    _fields_ = [("n", ctypes.c_int64 * 2), ("cell", _P * 2), ("fx", _P * 2), ("fz", _P * 2), ("ux", _P * 2),
+                ("uy", _P * 2), ("uz", _P * 2), ("F", _P * 6), ("rho", _P)]
+
+
 # name -> (restype, argtypes) of every exported C entry point
 _VP = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -70,6 +76,7 @@ _SIGNATURES = {
     "pic_set_timing": (ctypes.c_int, [_VP, _I32]),
     "pic_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "pic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pic_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(pic_config), ctypes.POINTER(pic_state_view), _VP, _VP]),
 }
 
 _lib = None
@@ -198,6 +205,11 @@ def pic_get_timing(h):
     n = (ctypes.c_int64 * 4)()
     _check(load_library().pic_get_timing(h, ms, n), "pic_get_timing")
     return list(ms), list(n)
+
+
+def pic_energy_noalloc(cfg, view, dev_out_ptr, stream_ptr):
+    _check(load_library().pic_energy_noalloc(ctypes.byref(cfg), ctypes.byref(view), dev_out_ptr, stream_ptr),
+           "pic_energy_noalloc")
 
 
 # ---- convenience wrapper: torch owns the workspace and the stream -----------------------------

@@ -132,3 +132,126 @@ void launch_energy(Ctx& c, cudaStream_t st, double* host_out5)
 }
 
 }  // namespace gbpic
+
+// ---------------------------------------------------------------------------------------------
+// Workspace-free variant of the energy reduction (pic_energy_noalloc in include/pic.h).
+//
+// Some callers cannot allocate device memory at all: a host that hands this library buffers it
+// owns but forbids further cudaMalloc (a caller-managed memory pool, or code that must not
+// allocate while a CUDA graph is being recorded by someone else). For them the reduction's
+// scratch -- one partial-sum record per block -- lives in a fixed array in this translation unit,
+// reserved on every GPU that loads the library until the process exits.
+// ---------------------------------------------------------------------------------------------
+
+namespace gbpic {
+
+constexpr int kStaticBlocks = 1024;                     // partial records the fixed scratch holds
+static __device__ __align__(256) double g_noalloc_scratch[kStaticBlocks * kSlots];
+
+// Final pass of the workspace-free variant: adds the block partials in block order (the same
+// fixed-shape tree as k_energy_final) and writes the five energies in J per metre of y.
+__global__ void k_energy_final_scaled(const double* __restrict__ partials, int nb, double s0, double s1, double s2,
+                                      double s3, double s4, double* out)
+{
+    __shared__ double sh[kEBlock];
+    const double scale[kSlots] = {s0, s1, s2, s3, s4};
+    for (int s = 0; s < kSlots; s++) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nb; b += kEBlock) v += partials[(size_t)b * kSlots + s];
+        const double r = block_sum(v, sh);
+        if (threadIdx.x == 0) out[s] = r * scale[s];
+    }
+}
+
+}  // namespace gbpic
+
+#include <mutex>
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the fixed scratch on the current device. The symbol name is only a host-side
+// handle: its device address comes from cudaGetSymbolAddress, taken once per device with that
+// device current, on the first call.
+int noalloc_scratch(double** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PIC_ECUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, gbpic::g_noalloc_scratch) != cudaSuccess || !p) return PIC_ECUDA;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* in, double* dev_out5, void* stream)
+{
+    using namespace gbpic;
+    if (!cfg || !in || !dev_out5) return PIC_EINVAL;
+    if (cfg->nx < 3 || cfg->nz < 4 || cfg->nx >= 32768 || cfg->nz >= 32768) return PIC_EINVAL;
+    if (cfg->mode != PIC_MODE_FULL && cfg->mode != PIC_MODE_TRANSPORT) return PIC_EINVAL;
+    if (!(cfg->dx > 0) || !(cfg->n_atoms > 0) || !(cfg->ion_mass_amu > 0) || cfg->ppc_ion <= 0) return PIC_EINVAL;
+    const int nsp = cfg->mode == PIC_MODE_FULL ? 2 : 1;
+    for (int s = 0; s < nsp; s++) {
+        // sizes beyond what the kernels index with 32-bit cells are refused
+        if (in->n[s] < 0 || in->n[s] > (int64_t)INT32_MAX) return PIC_EINVAL;
+        if (in->n[s] > 0 && (!in->cell[s] || !in->fx[s] || !in->fz[s] || !in->ux[s] || !in->uy[s] || !in->uz[s]))
+            return PIC_EINVAL;
+    }
+    for (int q = 0; q < 6; q++)
+        if (!in->F[q]) return PIC_EINVAL;
+    if (!in->rho) return PIC_EINVAL;
+
+    double* scratch = nullptr;
+    int r = noalloc_scratch(&scratch);
+    if (r) return r;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PIC_ECUDA;
+    const int nb = nsm * 4 < kStaticBlocks ? nsm * 4 : kStaticBlocks;
+
+    // derived constants, as pic_init derives them
+    const double w = cfg->n_atoms * cfg->dx * cfg->dx / (double)cfg->ppc_ion;
+    const double r0 = cfg->r0 > 0 ? cfg->r0 : pow(cfg->n_atoms, -1.0 / 3.0);
+    const double D = cfg->D_eV * kQe;
+    const double rho_scale = w / (4294967296.0 * cfg->dx * cfg->dx) * r0 * r0 * r0;
+    const double mi = cfg->ion_mass_amu * kAmu;
+
+    EnergyArgs a;
+    a.nx = cfg->nx;
+    a.nz = cfg->nz;
+    a.nsp = nsp;
+    for (int s = 0; s < 2; s++) {
+        const bool on = s < nsp;
+        a.sp[s].cell = on ? const_cast<int32_t*>(in->cell[s]) : nullptr;
+        a.sp[s].fx = on ? const_cast<float*>(in->fx[s]) : nullptr;
+        a.sp[s].fz = on ? const_cast<float*>(in->fz[s]) : nullptr;
+        a.sp[s].ux = on ? const_cast<float*>(in->ux[s]) : nullptr;
+        a.sp[s].uy = on ? const_cast<float*>(in->uy[s]) : nullptr;
+        a.sp[s].uz = on ? const_cast<float*>(in->uz[s]) : nullptr;
+        a.n[s] = on ? in->n[s] : 0;
+    }
+    for (int q = 0; q < 6; q++) a.F[q] = in->F[q];
+    a.rho = reinterpret_cast<const u64*>(in->rho);
+    a.rho_s = (float)rho_scale;
+    a.h_coef = (float)(r0 / (6.0 * cfg->dx));
+    a.c_att = (float)cfg->c_att;
+    a.s_rep = (float)cfg->s_rep;
+    a.pot_mode = cfg->pot_mode;
+    a.partials = scratch;    // every block overwrites its own record: nothing to clear
+    const cudaStream_t st = (cudaStream_t)stream;
+    const double vol = cfg->dx * cfg->dx;
+    const double mu0 = 1.0 / (kEps0 * kC * kC);
+    k_energy<<<nb, kEBlock, 0, st>>>(a);
+    k_energy_final_scaled<<<1, kEBlock, 0, st>>>(scratch, nb, w * mi * kC * kC, nsp > 1 ? w * kMe * kC * kC : 0.0,
+                                                  0.5 * kEps0 * vol, 0.5 / mu0 * vol, 0.5 * D * w, dev_out5);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
