@@ -78,6 +78,30 @@ __device__ __forceinline__ void split_cell(int cell, int nx, unsigned magic, int
     i = r;
 }
 
+// Weights of one stagger pattern: the four corner coefficients and the corner index.
+struct Stencil2 {
+    int idx;
+    float c00, c10, c01, c11;
+};
+
+__device__ __forceinline__ Stencil2 make_stencil(int idx, float wx, float wz)
+{
+    Stencil2 t;
+    t.idx = idx;
+    const float gx = 1.0f - wx, gz = 1.0f - wz;
+    t.c00 = gx * gz;
+    t.c10 = wx * gz;
+    t.c01 = gx * wz;
+    t.c11 = wx * wz;
+    return t;
+}
+
+__device__ __forceinline__ float apply(const float* A, int W, const Stencil2& t)
+{
+    const float* p = A + t.idx;
+    return t.c00 * p[0] + t.c10 * p[1] + t.c01 * p[W] + t.c11 * p[W + 1];
+}
+
 // bilinear gather of a staged component; (hx, hz) = 1 where it sits half a cell up
 __device__ __forceinline__ float win_gather(const float* A, int W, int lx, int lz, float fx, float fz, int hx, int hz)
 {
@@ -195,12 +219,21 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     float n = 0.f, dnx = 0.f, dnz = 0.f;
     if (inwin) {
         if (kFields) {
-            kx = S.e_kick * win_gather(w.f[0], W, lx, lz, fx, fz, 1, 0);
-            ky = S.e_kick * win_gather(w.f[1], W, lx, lz, fx, fz, 0, 0);
-            kz = S.e_kick * win_gather(w.f[2], W, lx, lz, fx, fz, 0, 1);
-            bx = win_gather(w.f[3], W, lx, lz, fx, fz, 0, 1);
-            by = win_gather(w.f[4], W, lx, lz, fx, fz, 1, 1);
-            bz = win_gather(w.f[5], W, lx, lz, fx, fz, 1, 0);
+            // four stagger patterns: (0,0) Ey; (1/2,0) Ex, Bz; (0,1/2) Ez, Bx; (1/2,1/2) By
+            const int base = lz * W + lx;
+            const bool ux_ = fx >= 0.5f, uz_ = fz >= 0.5f;
+            const int ox_ = ux_ ? 0 : -1, oz_ = uz_ ? 0 : -W;
+            const float hxw = ux_ ? fx - 0.5f : fx + 0.5f, hzw = uz_ ? fz - 0.5f : fz + 0.5f;
+            const Stencil2 s00 = make_stencil(base, fx, fz);
+            const Stencil2 s10 = make_stencil(base + ox_, hxw, fz);
+            const Stencil2 s01 = make_stencil(base + oz_, fx, hzw);
+            const Stencil2 s11 = make_stencil(base + ox_ + oz_, hxw, hzw);
+            kx = S.e_kick * apply(w.f[0], W, s10);
+            ky = S.e_kick * apply(w.f[1], W, s00);
+            kz = S.e_kick * apply(w.f[2], W, s01);
+            bx = apply(w.f[3], W, s01);
+            by = apply(w.f[4], W, s11);
+            bz = apply(w.f[5], W, s10);
         }
         if (kPair) {
             const float* q = w.nh + lz * W + lx;
@@ -415,10 +448,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
             const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
             for (int c0 = p0; c0 < p1; c0 += kChunk) {
                 const int n = min(kChunk, p1 - c0);
-                const int rows = (n + 31) >> 5;            // particles per lane row
+                // particles per lane row: the power of two that holds the chunk (32 when full)
+                const int lg = n > 512 ? 5 : 32 - __clz(((n + 31) >> 5) - 1);
+                const int rows = 1 << lg;
                 // coalesced load: chunk index ci -> (row ci / rows, column ci % rows)
                 for (int ci = threadIdx.x; ci < n; ci += kBlock) {
-                    const int r = ci / rows, col = ci - r * rows;
+                    const int r = ci >> lg, col = ci & (rows - 1);
                     const int slot = col * kPitch + r;
                     c_cell[slot] = S.a.cell[c0 + ci];
                     c_f[0][slot] = S.a.fx[c0 + ci];
@@ -430,7 +465,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
                 __syncthreads();
                 // transposed processing: lane l takes row l, so lanes are `rows` particles apart
                 for (int col = warp; col < rows; col += kWarps) {
-                    const int ci = lane * rows + col;
+                    const int ci = (lane << lg) + col;
                     if (ci < n) {
                         const int slot = col * kPitch + lane;
                         int cell = c_cell[slot];
@@ -448,7 +483,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
                 }
                 __syncthreads();
                 for (int ci = threadIdx.x; ci < n; ci += kBlock) {
-                    const int r = ci / rows, col = ci - r * rows;
+                    const int r = ci >> lg, col = ci & (rows - 1);
                     const int slot = col * kPitch + r;
                     S.a.cell[c0 + ci] = c_cell[slot];
                     S.a.fx[c0 + ci] = c_f[0][slot];
