@@ -172,6 +172,41 @@ PIC_API int pic_sort(pic_ctx* ctx);
 PIC_API int pic_set_timing(pic_ctx* ctx, int32_t enable);
 PIC_API int pic_get_timing(pic_ctx* ctx, double ms[3], int64_t n[4]);
 
+/* ---- batched intensity sweep --------------------------------------------------------------
+ * Several independent slabs (sizes, particle counts, intensities and seeds may differ; all in the
+ * same mode) advanced together: per step one persistent particle-kernel launch over the tiles of
+ * every slab and one launch per field kernel for all slabs, recorded once as a CUDA graph and
+ * replayed. Each slab is an ordinary context (pic_batch_slab) for reading and writing state,
+ * energies and forces; pic_step on such a context returns PIC_ESTATE (step the batch instead).
+ * The cell sort runs every cfgs[0].sort_every steps for all slabs. The slabs' kernel arguments
+ * are copied into one constant-memory table in front of each step: two batches stepping at the
+ * same time (on different streams) race on it. */
+typedef struct pic_batch pic_batch;
+
+/* Device workspace bytes for nslabs (1..48) configurations. */
+PIC_API int pic_batch_workspace_size(const pic_config* cfgs, int32_t nslabs, size_t* bytes);
+
+/* Create the batch on the current device. cfgs: host array of nslabs configurations.
+ * workspace: caller-owned device memory, 256-byte aligned, kept alive until pic_batch_free.
+ * stream: a non-default cudaStream_t (required: the step is recorded as a CUDA graph). */
+PIC_API int pic_batch_init(const pic_config* cfgs, int32_t nslabs, void* workspace, size_t workspace_bytes,
+                           void* stream, pic_batch** out);
+
+/* Advance every slab by nsteps cycles (graph replays). Synchronises at the end and returns the
+ * first slab's sticky error, if any. */
+PIC_API int pic_batch_step(pic_batch* b, int32_t nsteps);
+
+/* Context of slab i (owned by the batch; do not pic_free it). */
+PIC_API int pic_batch_slab(pic_batch* b, int32_t i, pic_ctx** out);
+
+/* With timing enabled, steps run as direct launches with CUDA events around the particle kernel
+ * (ms[0]) and the field kernels (ms[1]); sorts in ms[2]. n: launches (as pic_get_timing). */
+PIC_API int pic_batch_set_timing(pic_batch* b, int32_t enable);
+PIC_API int pic_batch_get_timing(pic_batch* b, double ms[3], int64_t n[4]);
+
+/* Release the batch and its slab contexts (the workspace stays the caller's). NULL is accepted. */
+PIC_API void pic_batch_free(pic_batch* b);
+
 /* Plain device arrays of one state, for pic_energy_noalloc. Species 1 is ignored in the
  * transport mode. All six field components (zeros in the transport mode) and the node density
  * of the pair species at the current positions are required. */

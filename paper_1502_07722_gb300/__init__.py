@@ -77,6 +77,13 @@ _SIGNATURES = {
     "pic_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "pic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "pic_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(pic_config), ctypes.POINTER(pic_state_view), _VP, _VP]),
+    "pic_batch_workspace_size": (ctypes.c_int, [ctypes.POINTER(pic_config), _I32, ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_batch_init": (ctypes.c_int, [ctypes.POINTER(pic_config), _I32, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "pic_batch_step": (ctypes.c_int, [_VP, _I32]),
+    "pic_batch_slab": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_VP)]),
+    "pic_batch_set_timing": (ctypes.c_int, [_VP, _I32]),
+    "pic_batch_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "pic_batch_free": (None, [_VP]),
 }
 
 _lib = None
@@ -212,6 +219,46 @@ def pic_energy_noalloc(cfg, view, dev_out_ptr, stream_ptr):
            "pic_energy_noalloc")
 
 
+def pic_batch_workspace_size(cfgs) -> int:
+    arr = (pic_config * len(cfgs))(*cfgs)
+    n = ctypes.c_size_t()
+    _check(load_library().pic_batch_workspace_size(arr, len(cfgs), ctypes.byref(n)), "pic_batch_workspace_size")
+    return n.value
+
+
+def pic_batch_init(cfgs, workspace_ptr, workspace_bytes, stream_ptr):
+    arr = (pic_config * len(cfgs))(*cfgs)
+    h = _VP()
+    _check(load_library().pic_batch_init(arr, len(cfgs), workspace_ptr, workspace_bytes, stream_ptr, ctypes.byref(h)),
+           "pic_batch_init")
+    return h
+
+
+def pic_batch_step(b, nsteps):
+    return _check(load_library().pic_batch_step(b, int(nsteps)), "pic_batch_step")
+
+
+def pic_batch_slab(b, i):
+    h = _VP()
+    _check(load_library().pic_batch_slab(b, int(i), ctypes.byref(h)), "pic_batch_slab")
+    return h
+
+
+def pic_batch_set_timing(b, enable):
+    _check(load_library().pic_batch_set_timing(b, 1 if enable else 0), "pic_batch_set_timing")
+
+
+def pic_batch_get_timing(b):
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 4)()
+    _check(load_library().pic_batch_get_timing(b, ms, n), "pic_batch_get_timing")
+    return list(ms), list(n)
+
+
+def pic_batch_free(b):
+    load_library().pic_batch_free(b)
+
+
 # ---- convenience wrapper: torch owns the workspace and the stream -----------------------------
 
 class Simulation:
@@ -308,3 +355,54 @@ class Simulation:
         pic_get_density(self.h, out.data_ptr(), False)
         self.stream.synchronize()
         return out
+
+
+class SlabView(Simulation):
+    """A slab of a Batch, accessed with the Simulation methods (state, energies, forces)."""
+
+    def __init__(self, batch, i, cfg):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.stream = batch.stream
+        self.h = pic_batch_slab(batch.b, i)
+        self.nx, self.nz = cfg.nx, cfg.nz
+        self.nspecies = self.info()["nspecies"]
+        self._owner = batch
+
+    def close(self):
+        self.h = None           # owned by the batch
+
+    def step(self, n=1):
+        raise RuntimeError("a slab of a batch is stepped through its Batch")
+
+
+class Batch:
+    """Several independent slabs advanced together (one persistent launch per step, CUDA graph)."""
+
+    def __init__(self, phys_list, **over):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.torch = torch
+        self.cfgs = [make_config(p, **over) for p in phys_list]
+        nbytes = pic_batch_workspace_size(self.cfgs)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        self.b = pic_batch_init(self.cfgs, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        self.slabs = [SlabView(self, i, c) for i, c in enumerate(self.cfgs)]
+
+    def step(self, n=1):
+        return pic_batch_step(self.b, n)
+
+    def close(self):
+        if getattr(self, "b", None):
+            pic_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

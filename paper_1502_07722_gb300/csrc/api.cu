@@ -17,12 +17,6 @@ void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* laun
 
 using namespace gbpic;
 
-struct pic_ctx {
-    Ctx c;
-    std::vector<cudaEvent_t> evpool;
-    std::vector<int> evkind;    // 0 particle, 1 fields, 2 sort (pairs of events)
-};
-
 #define CK(x)                                              \
     do {                                                   \
         cudaError_t e_ = (x);                              \
@@ -85,7 +79,7 @@ int derive_layout(const pic_config* cfg, Layout& L)
     size_t t = 0;
     for (int s = 0; s < 2; s++) t += 2 * 6 * align256(4 * (size_t)L.cap[s]) + align256(4 * (size_t)(L.ntiles + 1));
     t += 6 * align256(4 * L.nn) + 5 * align256(8 * L.nn);
-    t += align256(4 * 8 * (size_t)L.nx) + 2 * align256(4 * (size_t)L.nx);
+    t += align256(4 * 8 * (size_t)L.nx) + 2 * align256(4 * (size_t)L.nx) + align256(8);
     t += 2 * align256(4 * ((size_t)L.nkeys + 1));
     t += align256(4 * (((size_t)L.nkeys + 2047) / 2048 + 1));
     t += align256(8 * 5 * (size_t)kMaxEnergyBlocks) + align256(8 * 8) + align256(16);
@@ -280,6 +274,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     c.mur_save = cv.take<float>(8 * (size_t)L.nx);
     c.ant_c = cv.take<float>(L.nx);
     c.ant_s = cv.take<float>(L.nx);
+    c.ant = cv.take<float>(2);
     c.keys_count = cv.take<int32_t>((size_t)L.nkeys + 1);
     c.keys_off = cv.take<int32_t>((size_t)L.nkeys + 1);
     c.scan_tmp = cv.take<int32_t>(((size_t)L.nkeys + 2047) / 2048 + 1);
@@ -376,6 +371,7 @@ int pic_step(pic_ctx* h, int32_t nsteps)
 {
     if (!h || nsteps < 0) return PIC_EINVAL;
     Ctx& c = h->c;
+    if (c.in_batch) return PIC_ESTATE;
     if (c.sticky) return c.sticky;
     for (int it = 0; it < nsteps; it++) {
         if (c.cfg.sort_every > 0 && c.steps_since_sort >= c.cfg.sort_every) {
@@ -396,10 +392,11 @@ int pic_step(pic_ctx* h, int32_t nsteps)
         if (c.cfg.mode == PIC_MODE_FULL) {
             r = ev_begin(h, 1);
             if (r) return r;
-            launch_fields(c, c.stream, ((double)c.step + 0.5) * c.dt, &c.nlaunch[1]);
+            const int64_t before = c.nlaunch[1];
+            launch_fields(c, c.stream, c.step, &c.nlaunch[1]);
             r = ev_end(h);
             if (r) return r;
-            c.nlaunch[3] += 3;
+            c.nlaunch[3] += c.nlaunch[1] - before;
         }
         CK(cudaGetLastError());
         c.cur = 1 - c.cur;

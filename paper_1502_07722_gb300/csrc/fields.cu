@@ -3,30 +3,47 @@
 // of the particle kernel (int64 fixed point -> A/m^2) and the laser antenna, B by the second
 // half step. x is periodic; the tangential E components on the wall rows z = 0 and z = nz take
 // the first-order Mur absorbing condition.
+//
+// The same node functions serve one simulation (one launch per kernel) and a batch of
+// simulations (one launch per kernel for all of them, blockIdx.z = simulation).
 #include "pic_internal.cuh"
 
 namespace gbpic {
 
-struct FieldArgs {
-    int nx, nz, k_ant;
-    float h_b;           // dt / (2 dx)      (half step of B)
-    float h_e;           // c^2 dt / dx      (full step of E)
-    float cj;            // J2x, J2z -> dt J / eps0
-    float cjy;           // J6y -> dt J_y / eps0
-    float mur;           // (c dt - dx) / (c dt + dx)
-    float ant_s, ant_c;  // antenna amplitude at this step: E_x += ant_c(x) * ant_s + ant_s(x) * ant_c
-    float* F[6];
-    const u64* J[3];
-    float* save;         // 8 * nx: Ex(0) Ex(1) Ex(nz-1) Ex(nz) Ey(0) Ey(1) Ey(nz-1) Ey(nz) before the E step
-    const float* antc;
-    const float* ants;
-};
-
-__global__ void k_half_B(const FieldArgs f, int save)
+// Antenna amplitude of one step (FP64 on the device, one thread):
+//   E_x += 2 (c dt / dx) E0 env(t) amp(x) sin(w (t - t_ant) + phi(x))
+// split as ant[0] * amp cos(phi) + ant[1] * amp sin(phi) with ant = A (sin, cos)(w (t - t_ant)).
+__device__ __forceinline__ void antenna_scalars(const AntennaParams& p, long long step, float* ant)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y;
-    if (i >= f.nx) return;
+    float s = 0.0f, c = 0.0f;
+    if (p.on) {
+        const double tau = ((double)step + 0.5) * p.dt - p.t_ant;
+        const double env = exp(-2.0 * 0.6931471805599453 * tau * tau / (p.tau_fwhm * p.tau_fwhm));
+        const double a = p.coef * env;
+        s = (float)(a * sin(p.omega * tau));
+        c = (float)(a * cos(p.omega * tau));
+    }
+    ant[0] = s;
+    ant[1] = c;
+}
+
+__global__ void k_antenna(AntennaParams p, long long step, float* ant) { antenna_scalars(p, step, ant); }
+
+// batched: slab s reads its own step counter, advances it after the step (k_step_done)
+__global__ void k_antenna_batch(const AntennaParams* p, const long long* step, float* ant, int nslab)
+{
+    const int s = threadIdx.x;
+    if (s < nslab) antenna_scalars(p[s], step[s], ant + 2 * s);
+}
+
+__global__ void k_step_done(long long* step, int nslab)
+{
+    const int s = threadIdx.x;
+    if (s < nslab) step[s] += 1;
+}
+
+__device__ __forceinline__ void half_B_node(const FieldArgs& f, int i, int k, int save)
+{
     const int nx = f.nx, nz = f.nz;
     const int ip = i + 1 == nx ? 0 : i + 1;
     const size_t c = (size_t)k * nx + i;
@@ -57,7 +74,7 @@ __device__ __forceinline__ float ex_new(const FieldArgs& f, int i, int k, float 
 {
     const size_t c = (size_t)k * f.nx + i;
     float v = old - f.h_e * (f.F[4][c] - f.F[4][c - f.nx]) - f.cj * (float)(long long)f.J[0][c];
-    if (k == f.k_ant) v += f.antc[i] * f.ant_s + f.ants[i] * f.ant_c;
+    if (k == f.k_ant) v += f.antc[i] * f.ant[0] + f.ants[i] * f.ant[1];
     return v;
 }
 __device__ __forceinline__ float ey_new(const FieldArgs& f, int i, int k, float old)
@@ -68,11 +85,8 @@ __device__ __forceinline__ float ey_new(const FieldArgs& f, int i, int k, float 
            f.cjy * (float)(long long)f.J[1][c];
 }
 
-__global__ void k_E(const FieldArgs f)
+__device__ __forceinline__ void E_node(const FieldArgs& f, int i, int k)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y;
-    if (i >= f.nx) return;
     const int nx = f.nx, nz = f.nz;
     const size_t c = (size_t)k * nx + i;
     float* Ex = f.F[0];
@@ -98,7 +112,45 @@ __global__ void k_E(const FieldArgs f)
     }
 }
 
-void launch_fields(Ctx& c, cudaStream_t st, double t_half, int64_t* launches)
+__global__ void k_half_B(const FieldArgs f, int save)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < f.nx) half_B_node(f, i, blockIdx.y, save);
+}
+
+__global__ void k_E(const FieldArgs f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < f.nx) E_node(f, i, blockIdx.y);
+}
+
+__global__ void k_half_B_batch(const FieldArgs* __restrict__ fa, int save)
+{
+    const FieldArgs& f = fa[blockIdx.z];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < f.nx && (int)blockIdx.y <= f.nz) half_B_node(f, i, blockIdx.y, save);
+}
+
+__global__ void k_E_batch(const FieldArgs* __restrict__ fa)
+{
+    const FieldArgs& f = fa[blockIdx.z];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < f.nx && (int)blockIdx.y <= f.nz) E_node(f, i, blockIdx.y);
+}
+
+AntennaParams make_antenna_params(const Ctx& c)
+{
+    AntennaParams p;
+    p.on = c.cfg.laser_profile != PIC_LASER_NONE;
+    p.dt = c.dt;
+    p.t_ant = c.t_ant;
+    p.tau_fwhm = c.cfg.tau_fwhm > 0 ? c.cfg.tau_fwhm : 1.0;
+    p.omega = c.omega;
+    p.coef = 2.0 * (kC * c.dt / c.cfg.dx) * c.E0;
+    return p;
+}
+
+FieldArgs make_field_args(const Ctx& c)
 {
     FieldArgs f;
     f.nx = c.nx;
@@ -110,28 +162,37 @@ void launch_fields(Ctx& c, cudaStream_t st, double t_half, int64_t* launches)
     f.cjy = (float)(kQe * c.w * kC * c.dt / (6.0 * 1125899906842624.0 * c.cfg.dx * c.cfg.dx * kEps0));
     const double cdt = kC * c.dt;
     f.mur = (float)((cdt - c.cfg.dx) / (cdt + c.cfg.dx));
-    // antenna: E_x += 2 (c dt / dx) E0 env(t) amp(x) sin(w (t - t_ant) + phi(x))
-    double ant_s = 0.0, ant_c = 0.0;
-    if (c.cfg.laser_profile != PIC_LASER_NONE) {
-        const double tau = t_half - c.t_ant;
-        const double env = exp(-2.0 * log(2.0) * tau * tau / (c.cfg.tau_fwhm * c.cfg.tau_fwhm));
-        const double a = 2.0 * (cdt / c.cfg.dx) * c.E0 * env;
-        ant_s = a * sin(c.omega * tau);
-        ant_c = a * cos(c.omega * tau);
-    }
-    f.ant_s = (float)ant_s;
-    f.ant_c = (float)ant_c;
     for (int q = 0; q < 6; q++) f.F[q] = c.F[q];
     for (int q = 0; q < 3; q++) f.J[q] = c.J[q];
     f.save = c.mur_save;
     f.antc = c.ant_c;
     f.ants = c.ant_s;
+    f.ant = c.ant;
+    return f;
+}
+
+void launch_fields(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches)
+{
+    const FieldArgs f = make_field_args(c);
+    k_antenna<<<1, 1, 0, st>>>(make_antenna_params(c), (long long)step, c.ant);
     dim3 block(256);
     dim3 grid((c.nx + 255) / 256, c.nz + 1);
     k_half_B<<<grid, block, 0, st>>>(f, 1);
     k_E<<<grid, block, 0, st>>>(f);
     k_half_B<<<grid, block, 0, st>>>(f, 0);
-    if (launches) *launches += 3;
+    if (launches) *launches += 4;
+}
+
+void launch_fields_batch(const FieldArgs* fa_dev, const AntennaParams* ap_dev, long long* step_dev, float* ant_dev,
+                         int nslab, int max_nx, int max_nz, cudaStream_t st)
+{
+    k_antenna_batch<<<1, 32, 0, st>>>(ap_dev, step_dev, ant_dev, nslab);
+    dim3 block(256);
+    dim3 grid((max_nx + 255) / 256, max_nz + 1, nslab);
+    k_half_B_batch<<<grid, block, 0, st>>>(fa_dev, 1);
+    k_E_batch<<<grid, block, 0, st>>>(fa_dev);
+    k_half_B_batch<<<grid, block, 0, st>>>(fa_dev, 0);
+    k_step_done<<<1, 32, 0, st>>>(step_dev, nslab);
 }
 
 }  // namespace gbpic

@@ -390,8 +390,9 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     }
 }
 
+// One tile of one simulation: stage the window, stream the tile's particles, flush.
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
+__device__ __forceinline__ void run_tile(const StepArgs& a, int t)
 {
     extern __shared__ unsigned smem[];
     const int W = a.W, WW = W * W;
@@ -410,12 +411,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
     for (int q = 0; q < 5; q++) c_f[q] = reinterpret_cast<float*>(chunk + (q + 1) * kChunkWords);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    {
         int cnt = 0;
 #pragma unroll
         for (int s = 0; s < 2; s++)
             if (s < a.nsp) cnt += a.sp[s].tile_start[t + 1] - a.sp[s].tile_start[t];
-        if (cnt == 0) continue;
+        if (cnt == 0) return;
         const int tx = t % a.ntx, tz = t / a.ntx;
         w.ox = tx * a.T - kMargin - 1;
         w.oz = tz * a.T - kMargin - 1;
@@ -511,6 +512,32 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
     }
 }
 
+template <bool FULL>
+__global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
+{
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) run_tile<FULL>(a, t);
+}
+
+// Arguments of the simulations of a batch for the current step, in constant memory: the slab
+// index is uniform across a CTA, so the kernel reads them as constant-bank operands like the
+// single-simulation kernel reads its parameters. Uploaded (device to device) in front of each
+// batched launch; two batches stepping at the same time on different streams would race on it.
+constexpr int kMaxBatchSlabs = 48;
+__constant__ StepArgs c_batch_args[kMaxBatchSlabs];
+__constant__ int c_tile_base[kMaxBatchSlabs + 1];
+
+// All simulations of a batch in one persistent launch: the tiles of every simulation form one
+// work list (c_tile_base[s] = first global tile of simulation s).
+template <bool FULL>
+__global__ void __launch_bounds__(kBlock, 4) k_particles_batch(int nslab, int total)
+{
+    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+        int s = 0;
+        while (s + 1 < nslab && c_tile_base[s + 1] <= g) s++;
+        run_tile<FULL>(c_batch_args[s], g - c_tile_base[s]);
+    }
+}
+
 size_t particle_smem_bytes(int W) { return sizeof(unsigned) * ((size_t)15 * W * W + 6 * kChunkWords); }
 
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
@@ -531,6 +558,28 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
     if (grid < 1) grid = 1;
     if (a.full) k_particles<true><<<grid, kBlock, shmem, st>>>(a);
     else k_particles<false><<<grid, kBlock, shmem, st>>>(a);
+}
+
+int max_batch_slabs() { return kMaxBatchSlabs; }
+
+void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
+                                int full, int maxW, int nsm, cudaStream_t st)
+{
+    cudaMemcpyToSymbolAsync(c_batch_args, args_dev, sizeof(StepArgs) * nslab, 0, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyToSymbolAsync(c_tile_base, tile_base_dev, sizeof(int) * (nslab + 1), 0, cudaMemcpyDeviceToDevice, st);
+    const size_t shmem = particle_smem_bytes(maxW);
+    static size_t configured = 0;
+    if (shmem > configured) {
+        cudaFuncSetAttribute(k_particles_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+        cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+        cudaFuncSetAttribute(k_particles_batch<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        configured = shmem;
+    }
+    int grid = total_tiles < nsm * 4 ? total_tiles : nsm * 4;
+    if (grid < 1) grid = 1;
+    if (full) k_particles_batch<true><<<grid, kBlock, shmem, st>>>(nslab, total_tiles);
+    else k_particles_batch<false><<<grid, kBlock, shmem, st>>>(nslab, total_tiles);
 }
 
 int tile_window(int T) { return T + 2 * kMargin + 3; }

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/pic.h"
@@ -90,6 +91,7 @@ struct Ctx {
     float* mur_save;      // 8 * nx
     float* ant_c;         // nx: amplitude * cos(phase(x)) at x = i + 1/2
     float* ant_s;         // nx: amplitude * sin(phase(x))
+    float* ant;           // 2: antenna scalars of the current step (written on the device)
     // scratch
     int32_t* keys_count;  // nkeys + 1
     int32_t* keys_off;    // nkeys + 1
@@ -100,11 +102,34 @@ struct Ctx {
     int64_t step;
     int32_t steps_since_sort;
     int sticky;
+    int in_batch;         // stepped by a batch (pic_step refuses)
     // timing
     int timing;
     cudaEvent_t ev[4];
     double ms[3];
     int64_t nlaunch[4];
+};
+
+// Laser antenna of one simulation (scalars evaluated on the device each step).
+struct AntennaParams {
+    int on;
+    double dt, t_ant, tau_fwhm, omega, coef;
+};
+
+// Everything a field kernel needs for one simulation.
+struct FieldArgs {
+    int nx, nz, k_ant;
+    float h_b;           // dt / (2 dx)      (half step of B)
+    float h_e;           // c^2 dt / dx      (full step of E)
+    float cj;            // J2x, J2z -> dt J / eps0
+    float cjy;           // J6y -> dt J_y / eps0
+    float mur;           // (c dt - dx) / (c dt + dx)
+    float* F[6];
+    const u64* J[3];
+    float* save;         // 8 * nx: Ex(0) Ex(1) Ex(nz-1) Ex(nz) Ey(0) Ey(1) Ey(nz-1) Ey(nz) before the E step
+    const float* antc;   // nx: amplitude * cos(phase(x))
+    const float* ants;   // nx: amplitude * sin(phase(x))
+    const float* ant;    // 2: this step's antenna scalars
 };
 
 // kernels launched from the host side of the library (defined in the .cu files)
@@ -114,8 +139,23 @@ void launch_deposit_density(Ctx& c, u64* out, cudaStream_t st);
 void launch_pair_force(Ctx& c, float* out, cudaStream_t st);
 void launch_validate(Ctx& c, const SpeciesBuf& b, int64_t n, unsigned* bad, cudaStream_t st);
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st);
-void launch_fields(Ctx& c, cudaStream_t st, double t_half, int64_t* launches);
+void launch_fields(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches);
+void launch_fields_batch(const FieldArgs* fa_dev, const AntennaParams* ap_dev, long long* step_dev, float* ant_dev,
+                         int nslab, int max_nx, int max_nz, cudaStream_t st);
+FieldArgs make_field_args(const Ctx& c);
+AntennaParams make_antenna_params(const Ctx& c);
+void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
+                                int full, int maxW, int nsm, cudaStream_t st);
+size_t particle_smem_bytes(int W);
+int tile_window(int T);
 void launch_energy(Ctx& c, cudaStream_t st, double* host_out5);
 StepArgs make_step_args(Ctx& c);
 
 }  // namespace gbpic
+
+// The C ABI's opaque context (include/pic.h).
+struct pic_ctx {
+    gbpic::Ctx c;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<int> evkind;    // 0 particle, 1 fields, 2 sort (pairs of events)
+};

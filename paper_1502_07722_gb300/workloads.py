@@ -57,3 +57,18 @@ def workload(name: str, **overrides) -> dict:
     w = dict(WORKLOADS[name])
     w.update(overrides)
     return w
+
+
+def batched_sweep(n=16, steps=1000):
+    """Intensity sweep of independent copper slabs of uneven sizes: slab k has side
+    16 * round(16 * 4^(k/15)) cells (256 ... 1024), (8, 16, 32) macroparticles per cell per
+    species cycling with k, peak intensity 1e13 * 100^(k/15) W/cm^2 (log-spaced up to 1e15), the
+    same pulse shape, slab in the lower half, seeds 100 + k."""
+    out = []
+    for k in range(n):
+        side = 16 * round(16 * 4 ** (k / 15))
+        ppc = (8, 16, 32)[k % 3]
+        out.append(dict(COPPER, nx=side, nz=side, slab_k=side // 2, ppc_ion=ppc, ppc_electron=ppc,
+                        laser_profile=2, w0=2e-6, I0=1e17 * 100 ** (k / 15), t_peak=(steps // 2) * DT_2D,
+                        seed=100 + k, steps=steps))
+    return out
