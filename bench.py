@@ -183,10 +183,12 @@ def run_batched(args, world, rank, dist, gb):
     import torch
 
     from paper_1502_07722_gb300.workloads import batched_sweep
+    from paper_1502_07722_gb300.autotune import tune_batch
     ws = batched_sweep()
     for i, w in enumerate(ws):
         w["seed"] += 1000 * rank
-    batch = gb.Batch(ws, sort_every=20)
+    tuned = tune_batch(ws)
+    batch = gb.Batch(ws, tile=tuned["tile"], sort_every=tuned["sort_every"])
     stream = batch.stream
     n_local = sum(sum(s.info()["num_particles"]) for s in batch.slabs)
     nodes = sum((w["nz"] + 1) * w["nx"] for w in ws)
@@ -221,7 +223,9 @@ def run_batched(args, world, rank, dist, gb):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic copper slabs (seeded Maxwellian start)",
             "config": {"workload": "batched", "slabs": len(ws), "sides": [w["nx"] for w in ws],
-                       "particles_per_gpu": n_local, "sort_every": 20, "graph": True,
+                       "particles_per_gpu": n_local, "tile": tuned["tile"], "sort_every": tuned["sort_every"],
+                       "autotuned": [(t["tile"], t["sort_every"], round(t["ms_per_step"], 4)) for t in tuned["trials"]],
+                       "graph": True,
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (24 * n_local / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": alg / (k_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
@@ -272,7 +276,7 @@ def main():
     w = workload(args.workload, seed=workload(args.workload)["seed"] + 1000 * rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = gb.Simulation(w, stream=stream, sort_every=w.get("sort_every", 20))
+        sim = gb.Simulation(w, stream=stream, sort_every=w.get("sort_every", 40))
     info = sim.info()
     n_local = sum(info["num_particles"])
     nodes = (w["nz"] + 1) * w["nx"]

@@ -89,3 +89,14 @@ def test_full_sweep_initialises_and_steps(gb):
         assert torch.equal(fresh, sl.get_density()), i
         assert fresh.sum().item() == sl.info()["num_particles"][0] * 2 ** 32
     batch.close()
+
+
+def test_autotuner_picks_and_caches(gb, tmp_path, monkeypatch):
+    from paper_1502_07722_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "cache.json"))
+    ws = small_sweep()
+    r = autotune.tune_batch(ws, tiles=(8, 16), sorts=(2, 4), warmup=1)
+    assert r["tile"] in (8, 16) and r["sort_every"] in (2, 4)
+    assert len(r["trials"]) == 4 and r["ms_per_step"] == min(t["ms_per_step"] for t in r["trials"])
+    again = autotune.tune_batch(ws, tiles=(8, 16), sorts=(2, 4), warmup=1)
+    assert again == r                      # served from the cache
