@@ -48,6 +48,21 @@ class OracleConfig(ctypes.Structure):
     ]
 
 
+class OracleConfig3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("slab_k", ctypes.c_int32),
+        ("mode", ctypes.c_int32), ("ppc_ion", ctypes.c_int32), ("ppc_electron", ctypes.c_int32),
+        ("pot_mode", ctypes.c_int32), ("laser_profile", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("cfl", ctypes.c_double), ("dt_override", ctypes.c_double),
+        ("n_atoms", ctypes.c_double), ("T_ion_K", ctypes.c_double), ("T_electron_eV", ctypes.c_double),
+        ("ion_charge", ctypes.c_double), ("ion_mass_amu", ctypes.c_double),
+        ("D_eV", ctypes.c_double), ("r0", ctypes.c_double), ("c_att", ctypes.c_double),
+        ("s_rep", ctypes.c_double), ("lambda_", ctypes.c_double), ("I0", ctypes.c_double),
+        ("tau_fwhm", ctypes.c_double), ("w0", ctypes.c_double), ("t_peak", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 _F = ctypes.POINTER(ctypes.c_float)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -91,6 +106,31 @@ def lib():
             "oracle_deposit_current": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                               _D, _D, _D, _D, _F, _F, _F, _I64, _I64, _I64]),
         }
+        sig.update({
+            "oracle3_create": (vp, [ctypes.POINTER(OracleConfig3), ctypes.c_int32]),
+            "oracle3_free": (None, [vp]),
+            "oracle3_num_particles": (ctypes.c_int64, [vp, ctypes.c_int32]),
+            "oracle3_dt": (ctypes.c_double, [vp]),
+            "oracle3_weight": (ctypes.c_double, [vp]),
+            "oracle3_rho_scale": (ctypes.c_double, [vp]),
+            "oracle3_set_step": (None, [vp, ctypes.c_int64]),
+            "oracle3_get_particles": (None, [vp, ctypes.c_int32, _D, _D, _D, _D, _D, _D]),
+            "oracle3_set_particles": (None, [vp, ctypes.c_int32, ctypes.c_int64, _D, _D, _D, _D, _D, _D]),
+            "oracle3_get_field": (None, [vp, ctypes.c_int32, _D]),
+            "oracle3_set_field": (None, [vp, ctypes.c_int32, _D]),
+            "oracle3_get_rho": (None, [vp, _I64]),
+            "oracle3_set_rho": (None, [vp, _I64]),
+            "oracle3_get_current": (None, [vp, _I64]),
+            "oracle3_set_current": (None, [vp, _I64]),
+            "oracle3_pair_force": (None, [vp, _D]),
+            "oracle3_maxwell": (None, [vp]),
+            "oracle3_step": (None, [vp, ctypes.c_int32]),
+            "oracle3_energy": (None, [vp, _D]),
+            "oracle3_deposit_density": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                               _D, _D, _D, _I64]),
+            "oracle3_deposit_current": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                               ctypes.c_int32, _D, _D, _D, _D, _D, _D, _I64, _I64, _I64]),
+        })
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
             fn.restype = res
@@ -274,4 +314,121 @@ def deposit_current(nx, nz, sign, x0, z0, x1, z1, ux, uy, uz, out=None):
                                  _p(x1, ctypes.c_double), _p(z1, ctypes.c_double), _p(ux, ctypes.c_float),
                                  _p(uy, ctypes.c_float), _p(uz, ctypes.c_float),
                                  _p(out[0], ctypes.c_int64), _p(out[1], ctypes.c_int64), _p(out[2], ctypes.c_int64))
+    return out
+
+
+class Oracle3D:
+    """One FP64 simulation state in 3D (x, y periodic; walls in z). Positions in cells."""
+
+    def __init__(self, phys: dict, with_particles: bool = True):
+        self.phys = dict(phys)
+        c = OracleConfig3()
+        for name, _ in OracleConfig3._fields_:
+            key = "lambda" if name == "lambda_" else name
+            if key in phys:
+                setattr(c, name, phys[key])
+        self.cfg = c
+        self._s = lib().oracle3_create(ctypes.byref(c), 1 if with_particles else 0)
+        self.nx, self.ny, self.nz = c.nx, c.ny, c.nz
+        self.nspecies = 2 if c.mode == 0 else 1
+
+    def __del__(self):
+        if getattr(self, "_s", None):
+            lib().oracle3_free(self._s)
+            self._s = None
+
+    @property
+    def dt(self):
+        return lib().oracle3_dt(self._s)
+
+    @property
+    def weight(self):
+        return lib().oracle3_weight(self._s)
+
+    @property
+    def rho_scale(self):
+        return lib().oracle3_rho_scale(self._s)
+
+    def set_step(self, n):
+        lib().oracle3_set_step(self._s, int(n))
+
+    def _shape(self):
+        return (self.nz + 1, self.ny, self.nx)
+
+    def _nn(self):
+        return (self.nz + 1) * self.ny * self.nx
+
+    def num_particles(self, sp):
+        return lib().oracle3_num_particles(self._s, sp)
+
+    def get_particles(self, sp):
+        n = self.num_particles(sp)
+        arrs = [np.empty(n, np.float64) for _ in range(6)]
+        lib().oracle3_get_particles(self._s, sp, *[_p(a, ctypes.c_double) for a in arrs])
+        return dict(zip(("x", "y", "z", "ux", "uy", "uz"), arrs))
+
+    def set_particles(self, sp, x, y, z, ux, uy, uz):
+        arrs = [_f64(a) for a in (x, y, z, ux, uy, uz)]
+        lib().oracle3_set_particles(self._s, sp, len(arrs[0]), *[_p(a, ctypes.c_double) for a in arrs])
+
+    def get_field(self, f):
+        out = np.empty(self._nn(), np.float64)
+        lib().oracle3_get_field(self._s, f, _p(out, ctypes.c_double))
+        return out.reshape(self._shape())
+
+    def set_field(self, f, a):
+        a = _f64(a).reshape(-1)
+        assert a.size == self._nn()
+        lib().oracle3_set_field(self._s, f, _p(a, ctypes.c_double))
+
+    def get_rho(self):
+        out = np.empty(self._nn(), np.int64)
+        lib().oracle3_get_rho(self._s, _p(out, ctypes.c_int64))
+        return out.reshape(self._shape())
+
+    def set_rho(self, a):
+        a = np.ascontiguousarray(a, np.int64).reshape(-1)
+        lib().oracle3_set_rho(self._s, _p(a, ctypes.c_int64))
+
+    def get_current(self):
+        out = np.empty(3 * self._nn(), np.int64)
+        lib().oracle3_get_current(self._s, _p(out, ctypes.c_int64))
+        return out.reshape((3,) + self._shape())
+
+    def set_current(self, a):
+        a = np.ascontiguousarray(a, np.int64).reshape(-1)
+        lib().oracle3_set_current(self._s, _p(a, ctypes.c_int64))
+
+    def pair_force(self):
+        n = self.num_particles(0)
+        out = np.empty(3 * n, np.float64)
+        lib().oracle3_pair_force(self._s, _p(out, ctypes.c_double))
+        return out.reshape(n, 3)
+
+    def maxwell(self):
+        lib().oracle3_maxwell(self._s)
+
+    def step(self, n=1):
+        lib().oracle3_step(self._s, int(n))
+
+    def energy(self):
+        out = np.empty(5, np.float64)
+        lib().oracle3_energy(self._s, _p(out, ctypes.c_double))
+        return dict(zip(("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair"), out))
+
+
+def deposit_density3(nx, ny, nz, x, y, z):
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    out = np.zeros(nx * ny * (nz + 1), np.int64)
+    lib().oracle3_deposit_density(nx, ny, nz, len(x), _p(x, ctypes.c_double), _p(y, ctypes.c_double),
+                                  _p(z, ctypes.c_double), _p(out, ctypes.c_int64))
+    return out.reshape(nz + 1, ny, nx)
+
+
+def deposit_current3(nx, ny, nz, sign, x0, y0, z0, x1, y1, z1, out=None):
+    a = [_f64(v) for v in (x0, y0, z0, x1, y1, z1)]
+    if out is None:
+        out = np.zeros((3, nz + 1, ny, nx), np.int64)
+    lib().oracle3_deposit_current(nx, ny, nz, len(a[0]), sign, *[_p(v, ctypes.c_double) for v in a],
+                                  _p(out[0], ctypes.c_int64), _p(out[1], ctypes.c_int64), _p(out[2], ctypes.c_int64))
     return out

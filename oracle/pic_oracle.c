@@ -131,10 +131,14 @@ double oracle_lj_dU(double r) { return -12.0 * pow(r, -13.0) + 12.0 * pow(r, -7.
 
 /* branch factors of the altered potential (a finite stand-in for "infinite below r0" and the
  * multiplicative correction on the attractive side); plain Eq. (3) when pot_mode == 0 */
+static double branch_factor_p(int pot_mode, double c_att, double s_rep, double r)
+{
+    if (pot_mode == 0) return 1.0;
+    return r < 1.0 ? s_rep : c_att;
+}
 static double branch_factor(const ostate* s, double r)
 {
-    if (s->c.pot_mode == 0) return 1.0;
-    return r < 1.0 ? s->c.s_rep : s->c.c_att;
+    return branch_factor_p(s->c.pot_mode, s->c.c_att, s->c.s_rep, r);
 }
 
 /* Eq. (1)-(2): nearest-neighbour distances (units r0) along one axis from the local density
@@ -732,3 +736,508 @@ void oracle_energy(const ostate* s, double out[5])
 
 /* E_x the antenna launches at (x in cells, t), for pinning the source */
 double oracle_laser_field(const ostate* s, double x_cells, double t) { return laser_field(s, x_cells, t); }
+
+/* ======================================================================================== */
+/* 3D3V cycle (the paper's method in three dimensions: Eqs. (1)-(3) along x, y and z, the    */
+/* cubic lattice's six neighbours). Fixed point 2^14 per axis keeps the int64 sums far from  */
+/* overflow (a particle's weight product is at most 2^42).                                   */
+/* Grids: (nz+1) node rows of ny x nx, index (k*ny + j)*nx + i. Yee positions: Ex (i+1/2,j,k) */
+/* Ey (i,j+1/2,k) Ez (i,j,k+1/2) Bx (i,j+1/2,k+1/2) By (i+1/2,j,k+1/2) Bz (i+1/2,j+1/2,k).   */
+/* x and y periodic, walls at z = 0 and z = nz.                                               */
+/* ======================================================================================== */
+#define Q3 16384LL
+
+typedef struct {
+    int32_t nx, ny, nz, slab_k, mode, ppc_ion, ppc_electron, pot_mode, laser_profile;
+    double dx, cfl, dt_override, n_atoms, T_ion_K, T_electron_eV, ion_charge, ion_mass_amu;
+    double D_eV, r0, c_att, s_rep, lambda, I0, tau_fwhm, w0, t_peak;
+    uint64_t seed;
+} ocfg3;
+
+typedef struct {
+    ocfg3 c;
+    double dt, w, r0, D, rho_scale;
+    int nsp;
+    double q[2], m[2], uth[2];
+    int64_t np[2];
+    double *x[2], *y[2], *z[2], *ux[2], *uy[2], *uz[2];
+    double *F[6];
+    int64_t *rho, *J[3];
+    int64_t step;
+    double E0, omega, kwave, t_ant, w_ant, R_ant, gouy_ant, amp_ant;
+    int k_ant;
+} ostate3;
+
+static int64_t hat3q(int64_t X, int64_t j) { int64_t d = X - Q3 * j; if (d < 0) d = -d; return d < Q3 ? Q3 - d : 0; }
+#define N3(s, i, j, k) (((size_t)(k) * (size_t)(s)->c.ny + (size_t)(j)) * (size_t)(s)->c.nx + (size_t)(i))
+static size_t nn3(const ostate3* s) { return (size_t)s->c.nx * s->c.ny * (s->c.nz + 1); }
+
+/* node density: weights to the 8 nearest nodes */
+void oracle3_deposit_density(int32_t nx, int32_t ny, int32_t nz, int64_t n, const double* x, const double* y,
+                             const double* z, int64_t* rho)
+{
+    memset(rho, 0, sizeof(int64_t) * (size_t)nx * ny * (nz + 1));
+    for (int64_t p = 0; p < n; p++) {
+        int64_t X = llrint(x[p] * (double)Q3), Y = llrint(y[p] * (double)Q3), Z = llrint(z[p] * (double)Q3);
+        int64_t i0 = floordiv(X, Q3), j0 = floordiv(Y, Q3), l0 = floordiv(Z, Q3);
+        for (int64_t l = l0; l <= l0 + 1; l++)
+            for (int64_t j = j0; j <= j0 + 1; j++)
+                for (int64_t i = i0; i <= i0 + 1; i++) {
+                    int64_t w = hat3q(X, i) * hat3q(Y, j) * hat3q(Z, l);
+                    if (w == 0) continue;
+                    if (l < 0 || l > nz) abort();
+                    rho[((size_t)l * ny + imod(j, ny)) * nx + imod(i, nx)] += w;
+                }
+    }
+}
+
+/* Esirkepov current in 3D for linear weights:
+ *   6 Wx = dSx (2 S0y S0z + S1y S0z + S0y S1z + 2 S1y S1z)   (and cyclically)
+ *   J6x(i+1/2) = J6x(i-1/2) - 6 Wx(i)  along each x line
+ * so that 6 (rho1 - rho0) + div(J6) = 0 in integers (units 2^-42). */
+static void deposit_current3_one(int nx, int ny, int nz, int64_t* J6x, int64_t* J6y, int64_t* J6z, int64_t sign,
+                                 int64_t X0, int64_t Y0, int64_t Z0, int64_t X1, int64_t Y1, int64_t Z1)
+{
+    int64_t bx = floordiv(X0 < X1 ? X0 : X1, Q3), by = floordiv(Y0 < Y1 ? Y0 : Y1, Q3), bz = floordiv(Z0 < Z1 ? Z0 : Z1, Q3);
+    int64_t S0x[3], S1x[3], S0y[3], S1y[3], S0z[3], S1z[3];
+    for (int a = 0; a < 3; a++) {
+        S0x[a] = hat3q(X0, bx + a); S1x[a] = hat3q(X1, bx + a);
+        S0y[a] = hat3q(Y0, by + a); S1y[a] = hat3q(Y1, by + a);
+        S0z[a] = hat3q(Z0, bz + a); S1z[a] = hat3q(Z1, bz + a);
+    }
+    for (int c = 0; c < 3; c++)                /* J_x along x lines (b = y, c = z) */
+        for (int b = 0; b < 3; b++) {
+            int64_t P = 2 * S0y[b] * S0z[c] + S1y[b] * S0z[c] + S0y[b] * S1z[c] + 2 * S1y[b] * S1z[c];
+            int64_t acc = 0;
+            for (int a = 0; a < 2; a++) {
+                acc -= (S1x[a] - S0x[a]) * P;
+                if (acc != 0) {
+                    int64_t l = bz + c;
+                    if (l < 0 || l > nz) abort();
+                    J6x[((size_t)l * ny + imod(by + b, ny)) * nx + imod(bx + a, nx)] += sign * acc;
+                }
+            }
+        }
+    for (int c = 0; c < 3; c++)                /* J_y along y lines */
+        for (int a = 0; a < 3; a++) {
+            int64_t P = 2 * S0x[a] * S0z[c] + S1x[a] * S0z[c] + S0x[a] * S1z[c] + 2 * S1x[a] * S1z[c];
+            int64_t acc = 0;
+            for (int b = 0; b < 2; b++) {
+                acc -= (S1y[b] - S0y[b]) * P;
+                if (acc != 0) {
+                    int64_t l = bz + c;
+                    if (l < 0 || l > nz) abort();
+                    J6y[((size_t)l * ny + imod(by + b, ny)) * nx + imod(bx + a, nx)] += sign * acc;
+                }
+            }
+        }
+    for (int b = 0; b < 3; b++)                /* J_z along z lines */
+        for (int a = 0; a < 3; a++) {
+            int64_t P = 2 * S0x[a] * S0y[b] + S1x[a] * S0y[b] + S0x[a] * S1y[b] + 2 * S1x[a] * S1y[b];
+            int64_t acc = 0;
+            for (int c = 0; c < 2; c++) {
+                acc -= (S1z[c] - S0z[c]) * P;
+                if (acc != 0) {
+                    int64_t l = bz + c;
+                    if (l < 0 || l > nz - 1) abort();
+                    J6z[((size_t)l * ny + imod(by + b, ny)) * nx + imod(bx + a, nx)] += sign * acc;
+                }
+            }
+        }
+}
+
+void oracle3_deposit_current(int32_t nx, int32_t ny, int32_t nz, int64_t n, int32_t sign, const double* x0,
+                             const double* y0, const double* z0, const double* x1, const double* y1, const double* z1,
+                             int64_t* J6x, int64_t* J6y, int64_t* J6z)
+{
+    int64_t Px = (int64_t)nx * Q3, Py = (int64_t)ny * Q3;
+    for (int64_t p = 0; p < n; p++) {
+        int64_t X0 = llrint(x0[p] * (double)Q3), Y0 = llrint(y0[p] * (double)Q3), Z0 = llrint(z0[p] * (double)Q3);
+        int64_t X1 = llrint(x1[p] * (double)Q3), Y1 = llrint(y1[p] * (double)Q3), Z1 = llrint(z1[p] * (double)Q3);
+        while (X1 - X0 > Px / 2) X1 -= Px;
+        while (X0 - X1 > Px / 2) X1 += Px;
+        while (Y1 - Y0 > Py / 2) Y1 -= Py;
+        while (Y0 - Y1 > Py / 2) Y1 += Py;
+        deposit_current3_one(nx, ny, nz, J6x, J6y, J6z, sign, X0, Y0, Z0, X1, Y1, Z1);
+    }
+}
+
+static double nhat3(const ostate3* s, int64_t i, int64_t j, int64_t k)
+{
+    double v = (double)s->rho[N3(s, imod(i, s->c.nx), imod(j, s->c.ny), k)] * s->rho_scale;
+    if (k == 0 || k == s->c.nz) v *= 2.0;
+    return v;
+}
+
+/* trilinear density and its exact gradient (per cell) */
+static void gather_density3(const ostate3* s, double x, double y, double z, double* n, double g[3])
+{
+    int64_t i = (int64_t)floor(x), j = (int64_t)floor(y), k = (int64_t)floor(z);
+    double f[3] = {x - (double)i, y - (double)j, z - (double)k};
+    if (k >= s->c.nz) { k = s->c.nz - 1; f[2] = 1.0; }
+    double v[2][2][2];
+    for (int c = 0; c < 2; c++)
+        for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) v[c][b][a] = nhat3(s, i + a, j + b, k + c);
+    *n = 0.0; g[0] = g[1] = g[2] = 0.0;
+    for (int c = 0; c < 2; c++)
+        for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) {
+                double wx = a ? f[0] : 1 - f[0], wy = b ? f[1] : 1 - f[1], wz = c ? f[2] : 1 - f[2];
+                double sx = a ? 1.0 : -1.0, sy = b ? 1.0 : -1.0, sz = c ? 1.0 : -1.0;
+                *n += wx * wy * wz * v[c][b][a];
+                g[0] += sx * wy * wz * v[c][b][a];
+                g[1] += wx * sy * wz * v[c][b][a];
+                g[2] += wx * wy * sz * v[c][b][a];
+            }
+}
+
+static double gather_field3(const ostate3* s, const double* A, double x, double y, double z, double sx, double sy, double sz)
+{
+    int nx = s->c.nx, ny = s->c.ny, nz = s->c.nz;
+    double xs = x - sx, ys = y - sy, zs = z - sz;
+    int64_t rows = sz > 0 ? nz : nz + 1;
+    if (zs < 0.0) zs = 0.0;
+    if (zs > (double)(rows - 1)) zs = (double)(rows - 1);
+    int64_t i = (int64_t)floor(xs), j = (int64_t)floor(ys), k = (int64_t)floor(zs);
+    double fx = xs - i, fy = ys - j, fz = zs - k;
+    if (k >= rows - 1) { k = rows - 2; fz = 1.0; }
+    double v = 0.0;
+    for (int c = 0; c < 2; c++)
+        for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) {
+                double w = (a ? fx : 1 - fx) * (b ? fy : 1 - fy) * (c ? fz : 1 - fz);
+                v += w * A[((size_t)(k + c) * ny + imod(j + b, ny)) * nx + imod(i + a, nx)];
+            }
+    return v;
+}
+
+/* Eqs. (1)-(3) along x, y and z; energy = half the sum of U over the six neighbours */
+static void pair_force3_at(const ostate3* s, double x, double y, double z, double F[3], double* energy)
+{
+    double n, g[3];
+    gather_density3(s, x, y, z, &n, g);
+    F[0] = F[1] = F[2] = 0.0;
+    if (energy) *energy = 0.0;
+    if (!(n > 0.0)) return;
+    double r0_dx = s->r0 / s->c.dx, f_unit = s->D / s->r0, u = 0.0;
+    int pm = s->c.pot_mode;
+    for (int d = 0; d < 3; d++) {
+        double ap, am;
+        oracle_neighbor_distances(n, g[d], r0_dx, &ap, &am);
+        double dUp = isinf(ap) ? 0.0 : branch_factor_p(pm, s->c.c_att, s->c.s_rep, ap) * oracle_lj_dU(ap);
+        double dUm = isinf(am) ? 0.0 : branch_factor_p(pm, s->c.c_att, s->c.s_rep, am) * oracle_lj_dU(am);
+        F[d] = f_unit * (dUp - dUm);
+        if (!isinf(ap)) u += branch_factor_p(pm, s->c.c_att, s->c.s_rep, ap) * oracle_lj_U(ap);
+        if (!isinf(am)) u += branch_factor_p(pm, s->c.c_att, s->c.s_rep, am) * oracle_lj_U(am);
+    }
+    if (energy) *energy = 0.5 * s->D * u;
+}
+
+static double laser_field3(const ostate3* s, double x_cells, double y_cells, double t)
+{
+    if (s->c.laser_profile == 0) return 0.0;
+    double tau = t - s->t_ant;
+    double env = exp(-2.0 * log(2.0) * tau * tau / (s->c.tau_fwhm * s->c.tau_fwhm));
+    if (s->c.laser_profile == 1) return s->E0 * env * sin(s->omega * tau);
+    double xr = (x_cells - 0.5 * s->c.nx) * s->c.dx, yr = (y_cells - 0.5 * s->c.ny) * s->c.dx;
+    double r2 = xr * xr + yr * yr;
+    double amp = s->amp_ant * exp(-r2 / (s->w_ant * s->w_ant));
+    double phase = -s->kwave * r2 / (2.0 * s->R_ant) + s->gouy_ant;
+    return s->E0 * amp * env * sin(s->omega * tau + phase);
+}
+
+/* 3D Yee: B half step, E step, B half step */
+static void half_step_B3(ostate3* s)
+{
+    int nx = s->c.nx, ny = s->c.ny, nz = s->c.nz;
+    double h = 0.5 * s->dt / s->c.dx;
+    double *Ex = s->F[0], *Ey = s->F[1], *Ez = s->F[2], *Bx = s->F[3], *By = s->F[4], *Bz = s->F[5];
+    for (int k = 0; k <= nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                int ip = (i + 1) % nx, jp = (j + 1) % ny;
+                size_t c = N3(s, i, j, k);
+                if (k < nz) {
+                    /* dBx/dt = dEy/dz - dEz/dy ; dBy/dt = dEz/dx - dEx/dz */
+                    Bx[c] += h * ((Ey[N3(s, i, j, k + 1)] - Ey[c]) - (Ez[N3(s, i, jp, k)] - Ez[c]));
+                    By[c] += h * ((Ez[N3(s, ip, j, k)] - Ez[c]) - (Ex[N3(s, i, j, k + 1)] - Ex[c]));
+                }
+                /* dBz/dt = dEx/dy - dEy/dx */
+                Bz[c] += h * ((Ex[N3(s, i, jp, k)] - Ex[c]) - (Ey[N3(s, ip, j, k)] - Ey[c]));
+            }
+}
+
+static void full_step_E3(ostate3* s)
+{
+    int nx = s->c.nx, ny = s->c.ny, nz = s->c.nz;
+    double cdt = O_C * s->dt, h = O_C * O_C * s->dt / s->c.dx;
+    double *Ex = s->F[0], *Ey = s->F[1], *Ez = s->F[2], *Bx = s->F[3], *By = s->F[4], *Bz = s->F[5];
+    size_t nn = nn3(s);
+    double* nEx = malloc(sizeof(double) * nn);
+    double* nEy = malloc(sizeof(double) * nn);
+    double cj = O_QE * s->w / (6.0 * 4398046511104.0 * s->c.dx * s->c.dx * O_EPS0);    /* 6 * 2^42 */
+    double tmid = ((double)s->step + 0.5) * s->dt;
+    for (int k = 0; k <= nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                int im = (i + nx - 1) % nx, jm = (j + ny - 1) % ny;
+                size_t c = N3(s, i, j, k);
+                nEx[c] = Ex[c];
+                nEy[c] = Ey[c];
+                if (k > 0 && k < nz) {
+                    /* dEx/dt = c^2 (dBz/dy - dBy/dz) - Jx/eps0 ; dEy/dt = c^2 (dBx/dz - dBz/dx) - Jy/eps0 */
+                    nEx[c] = Ex[c] + h * ((Bz[c] - Bz[N3(s, i, jm, k)]) - (By[c] - By[N3(s, i, j, k - 1)])) - cj * (double)s->J[0][c];
+                    nEy[c] = Ey[c] + h * ((Bx[c] - Bx[N3(s, i, j, k - 1)]) - (Bz[c] - Bz[N3(s, im, j, k)])) - cj * (double)s->J[1][c];
+                    if (k == s->k_ant) nEx[c] += 2.0 * (cdt / s->c.dx) * laser_field3(s, (double)i + 0.5, (double)j, tmid);
+                }
+            }
+    double alpha = (cdt - s->c.dx) / (cdt + s->c.dx);
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            size_t b0 = N3(s, i, j, 0), b1 = N3(s, i, j, 1), t0 = N3(s, i, j, nz), t1 = N3(s, i, j, nz - 1);
+            nEx[b0] = Ex[b1] + alpha * (nEx[b1] - Ex[b0]);
+            nEy[b0] = Ey[b1] + alpha * (nEy[b1] - Ey[b0]);
+            nEx[t0] = Ex[t1] + alpha * (nEx[t1] - Ex[t0]);
+            nEy[t0] = Ey[t1] + alpha * (nEy[t1] - Ey[t0]);
+        }
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                int im = (i + nx - 1) % nx, jm = (j + ny - 1) % ny;
+                size_t c = N3(s, i, j, k);
+                /* dEz/dt = c^2 (dBy/dx - dBx/dy) - Jz/eps0 */
+                Ez[c] += h * ((By[c] - By[N3(s, im, j, k)]) - (Bx[c] - Bx[N3(s, i, jm, k)])) - cj * (double)s->J[2][c];
+            }
+    memcpy(Ex, nEx, sizeof(double) * nn);
+    memcpy(Ey, nEy, sizeof(double) * nn);
+    free(nEx); free(nEy);
+}
+
+static void alloc_species3(ostate3* s, int sp, int64_t n)
+{
+    free(s->x[sp]); free(s->y[sp]); free(s->z[sp]); free(s->ux[sp]); free(s->uy[sp]); free(s->uz[sp]);
+    s->np[sp] = n;
+    size_t b = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    s->x[sp] = calloc(1, b); s->y[sp] = calloc(1, b); s->z[sp] = calloc(1, b);
+    s->ux[sp] = calloc(1, b); s->uy[sp] = calloc(1, b); s->uz[sp] = calloc(1, b);
+}
+
+static void redeposit3(ostate3* s)
+{
+    oracle3_deposit_density(s->c.nx, s->c.ny, s->c.nz, s->np[0], s->x[0], s->y[0], s->z[0], s->rho);
+}
+
+/* initial slab: cell rows k < slab_k over all (i, j); positions draws 0 (x), 6 (y), 1 (z) */
+static void init_particles3(ostate3* s)
+{
+    const ocfg3* c = &s->c;
+    int64_t ncell = (int64_t)c->nx * c->ny * c->slab_k;
+    for (int sp = 0; sp < s->nsp; sp++) {
+        int ppc = sp == 0 ? c->ppc_ion : c->ppc_electron;
+        alloc_species3(s, sp, ncell * ppc);
+        int64_t p = 0;
+        for (int k = 0; k < c->slab_k; k++)
+            for (int j = 0; j < c->ny; j++)
+                for (int i = 0; i < c->nx; i++)
+                    for (int q = 0; q < ppc; q++, p++) {
+                        uint64_t cellidx = ((uint64_t)k * c->ny + (uint64_t)j) * (uint64_t)c->nx + (uint64_t)i;
+                        int pos_sp = (sp == 1 && c->ppc_electron == c->ppc_ion) ? 0 : sp;
+                        uint64_t pid = cellidx * (uint64_t)ppc + (uint64_t)q;
+                        s->x[sp][p] = (double)i + draw_unit24(draw_bits(c->seed, pos_sp, pid, 0));
+                        s->y[sp][p] = (double)j + draw_unit24(draw_bits(c->seed, pos_sp, pid, 6));
+                        s->z[sp][p] = (double)k + draw_unit24(draw_bits(c->seed, pos_sp, pid, 1));
+                        double r1 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid, 2))));
+                        double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 3));
+                        double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid, 4))));
+                        double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 5));
+                        s->ux[sp][p] = s->uth[sp] * r1 * cos(a1);
+                        s->uy[sp][p] = s->uth[sp] * r1 * sin(a1);
+                        s->uz[sp][p] = s->uth[sp] * r2 * cos(a2);
+                    }
+    }
+}
+
+ostate3* oracle3_create(const ocfg3* cfg, int32_t with_particles)
+{
+    ostate3* s = calloc(1, sizeof(ostate3));
+    s->c = *cfg;
+    const ocfg3* c = &s->c;
+    s->dt = c->dt_override > 0 ? c->dt_override : c->cfl * c->dx / (O_C * sqrt(3.0));
+    s->nsp = c->mode == 0 ? 2 : 1;
+    s->w = c->n_atoms * c->dx * c->dx * c->dx / (double)c->ppc_ion;
+    s->r0 = c->r0 > 0 ? c->r0 : pow(c->n_atoms, -1.0 / 3.0);
+    s->D = c->D_eV * O_QE;
+    s->rho_scale = s->w / (4398046511104.0 * c->dx * c->dx * c->dx) * pow(s->r0, 3.0);   /* 2^42 */
+    s->q[0] = c->ion_charge * O_QE; s->m[0] = c->ion_mass_amu * O_AMU;
+    s->uth[0] = sqrt(O_KB * c->T_ion_K / (s->m[0] * O_C * O_C));
+    s->q[1] = -O_QE; s->m[1] = O_ME;
+    s->uth[1] = sqrt(c->T_electron_eV * O_QE / (O_ME * O_C * O_C));
+    size_t nn = nn3(s);
+    for (int f = 0; f < 6; f++) s->F[f] = calloc(nn, sizeof(double));
+    for (int f = 0; f < 3; f++) s->J[f] = calloc(nn, sizeof(int64_t));
+    s->rho = calloc(nn, sizeof(int64_t));
+    s->E0 = sqrt(2.0 * c->I0 / (O_EPS0 * O_C));
+    s->omega = c->lambda > 0 ? 2.0 * O_PI * O_C / c->lambda : 0.0;
+    s->kwave = s->omega / O_C;
+    s->k_ant = c->nz - 2;
+    double L = (double)(s->k_ant - c->slab_k) * c->dx;
+    s->t_ant = c->t_peak - L / O_C;
+    if (c->laser_profile == 2) {
+        /* 3D paraxial Gaussian beam converging on the slab surface */
+        double zR = O_PI * c->w0 * c->w0 / c->lambda, sa = -L;
+        s->w_ant = c->w0 * sqrt(1.0 + (sa / zR) * (sa / zR));
+        s->R_ant = sa + zR * zR / sa;
+        s->gouy_ant = atan(sa / zR);
+        s->amp_ant = c->w0 / s->w_ant;
+    }
+    if (with_particles) init_particles3(s);
+    else for (int sp = 0; sp < s->nsp; sp++) alloc_species3(s, sp, 0);
+    redeposit3(s);
+    return s;
+}
+
+void oracle3_free(ostate3* s)
+{
+    if (!s) return;
+    for (int sp = 0; sp < 2; sp++) { free(s->x[sp]); free(s->y[sp]); free(s->z[sp]); free(s->ux[sp]); free(s->uy[sp]); free(s->uz[sp]); }
+    for (int f = 0; f < 6; f++) free(s->F[f]);
+    for (int f = 0; f < 3; f++) free(s->J[f]);
+    free(s->rho);
+    free(s);
+}
+
+int64_t oracle3_num_particles(const ostate3* s, int32_t sp) { return sp < s->nsp ? s->np[sp] : 0; }
+double oracle3_dt(const ostate3* s) { return s->dt; }
+double oracle3_weight(const ostate3* s) { return s->w; }
+double oracle3_rho_scale(const ostate3* s) { return s->rho_scale; }
+void oracle3_set_step(ostate3* s, int64_t step) { s->step = step; }
+
+void oracle3_get_particles(const ostate3* s, int32_t sp, double* x, double* y, double* z, double* ux, double* uy, double* uz)
+{
+    size_t b = sizeof(double) * (size_t)s->np[sp];
+    memcpy(x, s->x[sp], b); memcpy(y, s->y[sp], b); memcpy(z, s->z[sp], b);
+    memcpy(ux, s->ux[sp], b); memcpy(uy, s->uy[sp], b); memcpy(uz, s->uz[sp], b);
+}
+
+void oracle3_set_particles(ostate3* s, int32_t sp, int64_t n, const double* x, const double* y, const double* z,
+                           const double* ux, const double* uy, const double* uz)
+{
+    alloc_species3(s, sp, n);
+    size_t b = sizeof(double) * (size_t)n;
+    memcpy(s->x[sp], x, b); memcpy(s->y[sp], y, b); memcpy(s->z[sp], z, b);
+    memcpy(s->ux[sp], ux, b); memcpy(s->uy[sp], uy, b); memcpy(s->uz[sp], uz, b);
+    if (sp == 0) redeposit3(s);
+}
+
+void oracle3_get_field(const ostate3* s, int32_t f, double* out) { memcpy(out, s->F[f], sizeof(double) * nn3(s)); }
+void oracle3_set_field(ostate3* s, int32_t f, const double* in) { memcpy(s->F[f], in, sizeof(double) * nn3(s)); }
+void oracle3_get_rho(const ostate3* s, int64_t* out) { memcpy(out, s->rho, sizeof(int64_t) * nn3(s)); }
+void oracle3_set_rho(ostate3* s, const int64_t* in) { memcpy(s->rho, in, sizeof(int64_t) * nn3(s)); }
+void oracle3_get_current(const ostate3* s, int64_t* out3)
+{
+    for (int f = 0; f < 3; f++) memcpy(out3 + f * nn3(s), s->J[f], sizeof(int64_t) * nn3(s));
+}
+void oracle3_set_current(ostate3* s, const int64_t* in3)
+{
+    for (int f = 0; f < 3; f++) memcpy(s->J[f], in3 + f * nn3(s), sizeof(int64_t) * nn3(s));
+}
+
+void oracle3_pair_force(const ostate3* s, double* F)
+{
+    for (int64_t p = 0; p < s->np[0]; p++) pair_force3_at(s, s->x[0][p], s->y[0][p], s->z[0][p], F + 3 * p, NULL);
+}
+
+void oracle3_maxwell(ostate3* s)
+{
+    half_step_B3(s);
+    full_step_E3(s);
+    half_step_B3(s);
+}
+
+static void push_particle3(ostate3* s, int sp, int64_t p)
+{
+    double x = s->x[sp][p], y = s->y[sp][p], z = s->z[sp][p];
+    double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, Fp[3] = {0, 0, 0};
+    if (s->c.mode == 0) {
+        E[0] = gather_field3(s, s->F[0], x, y, z, 0.5, 0.0, 0.0);
+        E[1] = gather_field3(s, s->F[1], x, y, z, 0.0, 0.5, 0.0);
+        E[2] = gather_field3(s, s->F[2], x, y, z, 0.0, 0.0, 0.5);
+        B[0] = gather_field3(s, s->F[3], x, y, z, 0.0, 0.5, 0.5);
+        B[1] = gather_field3(s, s->F[4], x, y, z, 0.5, 0.0, 0.5);
+        B[2] = gather_field3(s, s->F[5], x, y, z, 0.5, 0.5, 0.0);
+    }
+    if (sp == 0) pair_force3_at(s, x, y, z, Fp, NULL);
+    double u[3] = {s->ux[sp][p], s->uy[sp][p], s->uz[sp][p]};
+    oracle_boris(s->q[sp], s->m[sp], s->dt, E, B, Fp, u);
+    double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double k = O_C * s->dt / (g * s->c.dx);
+    double xn = x + u[0] * k, yn = y + u[1] * k, zn = z + u[2] * k;
+    if (xn < 0.0) xn += s->c.nx;
+    if (xn >= s->c.nx) xn -= s->c.nx;
+    if (yn < 0.0) yn += s->c.ny;
+    if (yn >= s->c.ny) yn -= s->c.ny;
+    if (zn < 0.0) { zn = -zn; u[2] = -u[2]; }
+    if (zn >= s->c.nz) { zn = 2.0 * s->c.nz - zn; u[2] = -u[2]; }
+    s->x[sp][p] = xn; s->y[sp][p] = yn; s->z[sp][p] = zn;
+    s->ux[sp][p] = u[0]; s->uy[sp][p] = u[1]; s->uz[sp][p] = u[2];
+}
+
+void oracle3_step(ostate3* s, int32_t nsteps)
+{
+    size_t nn = nn3(s);
+    for (int it = 0; it < nsteps; it++) {
+        for (int f = 0; f < 3; f++) memset(s->J[f], 0, sizeof(int64_t) * nn);
+        for (int sp = 0; sp < s->nsp; sp++) {
+            int64_t n = s->np[sp];
+            size_t b = sizeof(double) * (n ? n : 1);
+            double *x0 = malloc(b), *y0 = malloc(b), *z0 = malloc(b);
+            memcpy(x0, s->x[sp], b); memcpy(y0, s->y[sp], b); memcpy(z0, s->z[sp], b);
+            for (int64_t p = 0; p < n; p++) push_particle3(s, sp, p);
+            if (s->c.mode == 0)
+                oracle3_deposit_current(s->c.nx, s->c.ny, s->c.nz, n, s->q[sp] > 0 ? 1 : -1, x0, y0, z0, s->x[sp], s->y[sp],
+                                        s->z[sp], s->J[0], s->J[1], s->J[2]);
+            free(x0); free(y0); free(z0);
+        }
+        redeposit3(s);
+        if (s->c.mode == 0) oracle3_maxwell(s);
+        s->step++;
+    }
+}
+
+void oracle3_energy(const ostate3* s, double out[5])
+{
+    for (int i = 0; i < 5; i++) out[i] = 0.0;
+    for (int sp = 0; sp < s->nsp; sp++) {
+        double acc = 0.0;
+        for (int64_t p = 0; p < s->np[sp]; p++) {
+            double u2 = s->ux[sp][p] * s->ux[sp][p] + s->uy[sp][p] * s->uy[sp][p] + s->uz[sp][p] * s->uz[sp][p];
+            acc += u2 / (sqrt(1.0 + u2) + 1.0);
+        }
+        out[sp] = acc * s->w * s->m[sp] * O_C * O_C;
+    }
+    int nx = s->c.nx, ny = s->c.ny, nz = s->c.nz;
+    double vol = s->c.dx * s->c.dx * s->c.dx, mu0 = 1.0 / (O_EPS0 * O_C * O_C), eE = 0.0, eB = 0.0;
+    for (int k = 0; k <= nz; k++) {
+        double wn = (k == 0 || k == nz) ? 0.5 : 1.0;
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t c = N3(s, i, j, k);
+                eE += wn * (s->F[0][c] * s->F[0][c] + s->F[1][c] * s->F[1][c]);
+                eB += wn * s->F[5][c] * s->F[5][c];
+                if (k < nz) {
+                    eE += s->F[2][c] * s->F[2][c];
+                    eB += s->F[3][c] * s->F[3][c] + s->F[4][c] * s->F[4][c];
+                }
+            }
+    }
+    out[2] = 0.5 * O_EPS0 * eE * vol;
+    out[3] = 0.5 / mu0 * eB * vol;
+    double pe = 0.0;
+    for (int64_t p = 0; p < s->np[0]; p++) {
+        double F[3], e;
+        pair_force3_at(s, s->x[0][p], s->y[0][p], s->z[0][p], F, &e);
+        pe += e;
+    }
+    out[4] = pe * s->w;
+}
