@@ -279,7 +279,11 @@ def main():
         sim = gb.Simulation(w, stream=stream, sort_every=w.get("sort_every", 40))
     info = sim.info()
     n_local = sum(info["num_particles"])
-    nodes = (w["nz"] + 1) * w["nx"]
+    nodes = (w["nz"] + 1) * w["nx"] * sim.ny
+    if sim.dims == 3:
+        # per particle 56 B (28-byte record read and written), per node the same 64 B
+        global BYTES_PER_PARTICLE
+        BYTES_PER_PARTICLE = 56
 
     sim.step(args.warmup)
     gb.pic_set_timing(sim.h, True)
@@ -319,16 +323,17 @@ def main():
     if not args.no_e2e:
         host = [sim.get_particles(s) for s in range(sim.nspecies)]
         pinned = [{k: v.cpu().pin_memory() for k, v in h.items()} for h in host]
-        dens_host = torch.empty((w["nz"] + 1, w["nx"]), dtype=torch.int64).pin_memory()
+        dens_host = torch.empty(sim._shape(), dtype=torch.int64).pin_memory()
         h2d = sum(v.numel() * v.element_size() for h in pinned for v in h.values())
         d2h = 4 * args.steps + dens_host.numel() * 8
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
+        names = ("cell", "fx", "fy", "fz", "ux", "uy", "uz")
         for s, h in enumerate(pinned):
             gb.pic_set_particles(sim.h, s, h["cell"].numel(),
-                                 [h[k].data_ptr() for k in ("cell", "fx", "fz", "ux", "uy", "uz")], True)
+                                 [h[k].data_ptr() if k in h else None for k in names], True)
         for _ in range(args.steps):
             gb.pic_step(sim.h, 1)
         gb.pic_get_density(sim.h, dens_host.data_ptr(), True)
@@ -351,7 +356,8 @@ def main():
             "data": "synthetic copper slab (seeded Maxwellian start), one independent slab per GPU",
             "config": {"workload": args.workload, "nx": w["nx"], "nz": w["nz"], "slab_k": w["slab_k"],
                        "ppc": [w["ppc_ion"], w["ppc_electron"]], "particles_per_gpu": n_local,
-                       "tile": sim.cfg.tile or 16, "sort_every": sim.cfg.sort_every,
+                       "tile": sim.cfg.tile or (8 if sim.dims == 3 else 16), "sort_every": sim.cfg.sort_every,
+                       "dims": sim.dims, "ny": sim.ny,
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (24 * n_local / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

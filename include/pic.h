@@ -80,6 +80,11 @@ typedef struct pic_config {
     double lambda, I0, tau_fwhm, w0, t_peak;  /* laser: m, W/m^2, s (intensity FWHM), m, s:
                                 the pulse peak reaches the slab surface z = slab_k at t_peak    */
     uint64_t seed;           /* initial-state generator seed                                    */
+    int32_t ny;              /* cells along y (periodic), 3D only                               */
+    int32_t dims;            /* 2 (default when 0) or 3. In 3D: grids (nz+1) x ny x nx, index
+                                (k*ny + j)*nx + i; a particle also has fy; fixed point 2^14 per
+                                axis (weights of a node sum in units 2^-42); current J6x, J6y, J6z
+                                with J_x = J6x * e w / (6 * 2^42 dx^2 dt); dt = cfl dx / (c sqrt 3) */
 } pic_config;
 
 typedef struct pic_info {
@@ -142,13 +147,15 @@ PIC_API int pic_energy(pic_ctx* ctx, pic_energy_t* host_out);
 PIC_API int pic_get_info(pic_ctx* ctx, pic_info* host_out);
 
 /* Copy particles of one species out of / into the context, in the context's order. Pointers are
- * host memory when on_host != 0 (the call then synchronises), device memory otherwise.
+ * host memory when on_host != 0 (the call then synchronises), device memory otherwise. fy is the
+ * y offset in 3D and is ignored (may be NULL) in 2D.
  * pic_set_particles replaces the species (n <= capacity), re-sorts it into tiles (which
  * permutes it: read it back with pic_get_particles) and re-deposits the node density. */
-PIC_API int pic_get_particles(pic_ctx* ctx, int32_t species, int32_t* cell, float* fx, float* fz,
+PIC_API int pic_get_particles(pic_ctx* ctx, int32_t species, int32_t* cell, float* fx, float* fy, float* fz,
                       float* ux, float* uy, float* uz, int32_t on_host);
 PIC_API int pic_set_particles(pic_ctx* ctx, int32_t species, int64_t n, const int32_t* cell, const float* fx,
-                      const float* fz, const float* ux, const float* uy, const float* uz, int32_t on_host);
+                      const float* fy, const float* fz, const float* ux, const float* uy, const float* uz,
+                      int32_t on_host);
 
 /* One field component (PIC_EX..PIC_BZ), (nz+1)*nx FP32. */
 PIC_API int pic_get_field(pic_ctx* ctx, int32_t which, float* out, int32_t on_host);

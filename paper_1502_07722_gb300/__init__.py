@@ -33,6 +33,7 @@ class pic_config(ctypes.Structure):
         ("r0", ctypes.c_double), ("c_att", ctypes.c_double), ("s_rep", ctypes.c_double),
         ("lambda_", ctypes.c_double), ("I0", ctypes.c_double), ("tau_fwhm", ctypes.c_double),
         ("w0", ctypes.c_double), ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("ny", ctypes.c_int32), ("dims", ctypes.c_int32),
     ]
 
 
@@ -66,8 +67,8 @@ _SIGNATURES = {
     "pic_pair_force": (ctypes.c_int, [_VP, _VP]),
     "pic_energy": (ctypes.c_int, [_VP, ctypes.POINTER(pic_energy_t)]),
     "pic_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pic_info)]),
-    "pic_get_particles": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
-    "pic_set_particles": (ctypes.c_int, [_VP, _I32, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
+    "pic_get_particles": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
+    "pic_set_particles": (ctypes.c_int, [_VP, _I32, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
     "pic_get_field": (ctypes.c_int, [_VP, _I32, _VP, _I32]),
     "pic_set_field": (ctypes.c_int, [_VP, _I32, _VP, _I32]),
     "pic_get_current": (ctypes.c_int, [_VP, _VP, _I32]),
@@ -277,6 +278,8 @@ class Simulation:
         self.h = pic_init(self.cfg, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
         info = self.info()
         self.nx, self.nz = self.cfg.nx, self.cfg.nz
+        self.dims = 3 if self.cfg.dims == 3 else 2
+        self.ny = self.cfg.ny if self.dims == 3 else 1
         self.nspecies = info["nspecies"]
 
     def close(self):
@@ -302,8 +305,11 @@ class Simulation:
     def sort(self):
         pic_sort(self.h)
 
+    def _shape(self):
+        return (self.nz + 1, self.ny, self.nx) if self.dims == 3 else (self.nz + 1, self.nx)
+
     def _grid(self, dtype):
-        return self.torch.empty((self.nz + 1, self.nx), dtype=dtype, device="cuda")
+        return self.torch.empty(self._shape(), dtype=dtype, device="cuda")
 
     def deposit_density(self):
         out = self._grid(self.torch.int64)
@@ -319,18 +325,28 @@ class Simulation:
     def get_particles(self, species):
         n = self.info()["num_particles"][species]
         t = self.torch
-        arrs = [t.empty(n, dtype=t.int32, device="cuda")] + [t.empty(n, dtype=t.float32, device="cuda") for _ in range(5)]
+        names = ("cell", "fx", "fy", "fz", "ux", "uy", "uz")
+        arrs = [t.empty(n, dtype=t.int32, device="cuda")] + [t.empty(n, dtype=t.float32, device="cuda") for _ in range(6)]
         if n:
-            pic_get_particles(self.h, species, [a.data_ptr() for a in arrs], False)
+            ptrs = [a.data_ptr() for a in arrs]
+            if self.dims == 2:
+                ptrs[2] = None
+            pic_get_particles(self.h, species, ptrs, False)
         self.stream.synchronize()
-        return dict(zip(("cell", "fx", "fz", "ux", "uy", "uz"), arrs))
+        out = dict(zip(names, arrs))
+        if self.dims == 2:
+            del out["fy"]
+        return out
 
-    def set_particles(self, species, cell, fx, fz, ux, uy, uz):
+    def set_particles(self, species, cell, fx, fz, ux, uy, uz, fy=None):
         t = self.torch
         arrs = [t.as_tensor(cell, dtype=t.int32).cuda().contiguous()] + \
                [t.as_tensor(a, dtype=t.float32).cuda().contiguous() for a in (fx, fz, ux, uy, uz)]
+        fyt = t.as_tensor(fy, dtype=t.float32).cuda().contiguous() if fy is not None else None
         self.stream.synchronize()
-        pic_set_particles(self.h, species, arrs[0].numel(), [a.data_ptr() for a in arrs], False)
+        ptrs = [a.data_ptr() for a in arrs]
+        ptrs.insert(2, fyt.data_ptr() if fyt is not None else None)
+        pic_set_particles(self.h, species, arrs[0].numel(), ptrs, False)
 
     def get_field(self, which):
         out = self._grid(self.torch.float32)
@@ -340,12 +356,12 @@ class Simulation:
 
     def set_field(self, which, values):
         v = self.torch.as_tensor(values, dtype=self.torch.float32).cuda().contiguous()
-        assert v.numel() == (self.nz + 1) * self.nx
+        assert v.numel() == (self.nz + 1) * self.ny * self.nx
         self.stream.synchronize()
         pic_set_field(self.h, which, v.data_ptr(), False)
 
     def get_current(self):
-        out = self.torch.empty((3, self.nz + 1, self.nx), dtype=self.torch.int64, device="cuda")
+        out = self.torch.empty((3,) + self._shape(), dtype=self.torch.int64, device="cuda")
         pic_get_current(self.h, out.data_ptr(), False)
         self.stream.synchronize()
         return out
@@ -367,6 +383,7 @@ class SlabView(Simulation):
         self.stream = batch.stream
         self.h = pic_batch_slab(batch.b, i)
         self.nx, self.nz = cfg.nx, cfg.nz
+        self.dims, self.ny = 2, 1
         self.nspecies = self.info()["nspecies"]
         self._owner = batch
 

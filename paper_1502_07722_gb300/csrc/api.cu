@@ -28,7 +28,7 @@ namespace {
 constexpr int kMaxEnergyBlocks = 1024;
 
 struct Layout {
-    int32_t nx, nz, T, ntx, ntz, ntiles, nkeys, nsp;
+    int32_t dims, nx, ny, nz, T, ntx, nty, ntz, ntiles, nkeys, nsp;
     size_t nn;
     int64_t cap[2], n0[2];
     size_t total;
@@ -39,7 +39,12 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int derive_layout(const pic_config* cfg, Layout& L)
 {
     if (!cfg) return PIC_EINVAL;
+    L.dims = cfg->dims == 0 ? 2 : cfg->dims;
+    if (L.dims != 2 && L.dims != 3) return PIC_EINVAL;
+    L.ny = L.dims == 3 ? cfg->ny : 1;
     if (cfg->nx < 3 || cfg->nz < 4 || cfg->nx >= 32768 || cfg->nz >= 32768) return PIC_EINVAL;
+    if (L.dims == 3 && (L.ny < 3 || L.ny >= 32768 || (int64_t)cfg->nx * L.ny * (cfg->nz + 1) >= (1LL << 31)))
+        return PIC_EINVAL;
     if (cfg->slab_k < 0 || cfg->slab_k > cfg->nz) return PIC_EINVAL;
     if (cfg->mode != PIC_MODE_FULL && cfg->mode != PIC_MODE_TRANSPORT) return PIC_EINVAL;
     if (cfg->ppc_ion < 0 || cfg->ppc_electron < 0) return PIC_EINVAL;
@@ -59,17 +64,18 @@ int derive_layout(const pic_config* cfg, Layout& L)
     if (cfg->pot_mode != 0 && cfg->pot_mode != 1) return PIC_EINVAL;
     L.nx = cfg->nx;
     L.nz = cfg->nz;
-    L.T = cfg->tile > 0 ? cfg->tile : 16;
+    L.T = cfg->tile > 0 ? cfg->tile : (L.dims == 3 ? 8 : 16);
     if (L.T < 2 || L.T > 64) return PIC_EINVAL;
     L.ntx = (L.nx + L.T - 1) / L.T;
+    L.nty = L.dims == 3 ? (L.ny + L.T - 1) / L.T : 1;
     L.ntz = (L.nz + L.T - 1) / L.T;
-    L.ntiles = L.ntx * L.ntz;
-    const int64_t nkeys = (int64_t)L.ntiles * L.T * L.T;
+    L.ntiles = L.ntx * L.nty * L.ntz;
+    const int64_t nkeys = (int64_t)L.ntiles * L.T * L.T * (L.dims == 3 ? L.T : 1);
     if (nkeys >= (1LL << 31) - 1) return PIC_EINVAL;
     L.nkeys = (int32_t)nkeys;
-    L.nn = (size_t)L.nx * (L.nz + 1);
+    L.nn = (size_t)L.nx * L.ny * (L.nz + 1);
     L.nsp = cfg->mode == PIC_MODE_FULL ? 2 : 1;
-    const int64_t ncell = (int64_t)cfg->nx * cfg->slab_k;
+    const int64_t ncell = (int64_t)cfg->nx * L.ny * cfg->slab_k;
     for (int s = 0; s < 2; s++) {
         const int ppc = s == 0 ? cfg->ppc_ion : cfg->ppc_electron;
         L.n0[s] = s < L.nsp ? ncell * ppc : 0;
@@ -77,9 +83,11 @@ int derive_layout(const pic_config* cfg, Layout& L)
         if (L.cap[s] < L.n0[s] || L.cap[s] >= (1LL << 31)) return PIC_EINVAL;
     }
     size_t t = 0;
-    for (int s = 0; s < 2; s++) t += 2 * 6 * align256(4 * (size_t)L.cap[s]) + align256(4 * (size_t)(L.ntiles + 1));
+    const int arrays = L.dims == 3 ? 7 : 6;
+    for (int s = 0; s < 2; s++) t += 2 * arrays * align256(4 * (size_t)L.cap[s]) + align256(4 * (size_t)(L.ntiles + 1));
     t += 6 * align256(4 * L.nn) + 5 * align256(8 * L.nn);
-    t += align256(4 * 8 * (size_t)L.nx) + 2 * align256(4 * (size_t)L.nx) + align256(8);
+    const size_t plane = (size_t)L.nx * L.ny;
+    t += align256(4 * 8 * plane) + 2 * align256(4 * plane) + align256(8);
     t += 2 * align256(4 * ((size_t)L.nkeys + 1));
     t += align256(4 * (((size_t)L.nkeys + 2047) / 2048 + 1));
     t += align256(8 * 5 * (size_t)kMaxEnergyBlocks) + align256(8 * 8) + align256(16);
@@ -158,7 +166,8 @@ int sort_all(pic_ctx* h)
 
 int redeposit(Ctx& c)
 {
-    launch_deposit_density(c, c.rho[c.cur], c.stream);
+    if (c.dims == 3) launch_deposit_density3(c, c.rho[c.cur], c.stream);
+    else launch_deposit_density(c, c.rho[c.cur], c.stream);
     CK(cudaGetLastError());
     return PIC_OK;
 }
@@ -229,10 +238,13 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
         delete h;
         return PIC_ECUDA;
     }
+    c.dims = L.dims;
     c.nx = L.nx;
+    c.ny = L.ny;
     c.nz = L.nz;
     c.T = L.T;
     c.ntx = L.ntx;
+    c.nty = L.nty;
     c.ntz = L.ntz;
     c.ntiles = L.ntiles;
     c.W = tile_window(L.T);
@@ -241,11 +253,15 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     c.nsp = L.nsp;
     c.k_ant = L.nz - 2;
     // derived physics
-    c.dt = cfg->dt_override > 0 ? cfg->dt_override : cfg->cfl * cfg->dx / (kC * sqrt(2.0));
-    c.w = cfg->n_atoms * cfg->dx * cfg->dx / (double)(cfg->ppc_ion > 0 ? cfg->ppc_ion : 1);
+    const bool d3 = L.dims == 3;
+    c.dt = cfg->dt_override > 0 ? cfg->dt_override : cfg->cfl * cfg->dx / (kC * sqrt(d3 ? 3.0 : 2.0));
+    // atoms per macroparticle (per metre of y in 2D)
+    c.w = cfg->n_atoms * cfg->dx * cfg->dx * (d3 ? cfg->dx : 1.0) / (double)(cfg->ppc_ion > 0 ? cfg->ppc_ion : 1);
     c.r0 = cfg->r0 > 0 ? cfg->r0 : pow(cfg->n_atoms, -1.0 / 3.0);
     c.D = cfg->D_eV * kQe;
-    c.rho_scale = c.w / (4294967296.0 * cfg->dx * cfg->dx) * c.r0 * c.r0 * c.r0;
+    // node sum -> n / n0; a node sum counts one macroparticle as 2^32 (2D) or 2^42 (3D)
+    c.rho_scale = d3 ? c.w / (4398046511104.0 * cfg->dx * cfg->dx * cfg->dx) * c.r0 * c.r0 * c.r0
+                     : c.w / (4294967296.0 * cfg->dx * cfg->dx) * c.r0 * c.r0 * c.r0;
     c.E0 = sqrt(2.0 * cfg->I0 / (kEps0 * kC));
     c.omega = cfg->lambda > 0 ? 2.0 * kPi * kC / cfg->lambda : 0.0;
     const double Lant = (double)(c.k_ant - cfg->slab_k) * cfg->dx;
@@ -259,6 +275,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
         for (int b = 0; b < 2; b++) {
             bufs[b]->cell = cv.take<int32_t>(L.cap[s]);
             bufs[b]->fx = cv.take<float>(L.cap[s]);
+            bufs[b]->fy = d3 ? cv.take<float>(L.cap[s]) : nullptr;
             bufs[b]->fz = cv.take<float>(L.cap[s]);
             bufs[b]->ux = cv.take<float>(L.cap[s]);
             bufs[b]->uy = cv.take<float>(L.cap[s]);
@@ -271,9 +288,10 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     for (int q = 0; q < 6; q++) c.F[q] = cv.take<float>(L.nn);
     for (int q = 0; q < 3; q++) c.J[q] = cv.take<u64>(L.nn);
     for (int q = 0; q < 2; q++) c.rho[q] = cv.take<u64>(L.nn);
-    c.mur_save = cv.take<float>(8 * (size_t)L.nx);
-    c.ant_c = cv.take<float>(L.nx);
-    c.ant_s = cv.take<float>(L.nx);
+    const size_t plane = (size_t)L.nx * L.ny;
+    c.mur_save = cv.take<float>(8 * plane);
+    c.ant_c = cv.take<float>(plane);
+    c.ant_s = cv.take<float>(plane);
     c.ant = cv.take<float>(2);
     c.keys_count = cv.take<int32_t>((size_t)L.nkeys + 1);
     c.keys_off = cv.take<int32_t>((size_t)L.nkeys + 1);
@@ -308,26 +326,32 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     }
     // antenna table (x = i + 1/2, FP64 -> FP32)
     {
-        std::vector<float> ac(L.nx, 0.f), as(L.nx, 0.f);
+        // paraxial Gaussian beam converging on the slab surface, evaluated at the antenna: width w_a,
+        // curvature R_a, Gouy phase (half of it for a 2D line focus), amplitude (w0/w_a)^(1/2) in 2D,
+        // w0/w_a in 3D; E_x sits at (i + 1/2, j)
+        std::vector<float> ac(plane, 0.f), as(plane, 0.f);
         if (cfg->laser_profile == PIC_LASER_PLANE) {
-            for (int i = 0; i < L.nx; i++) ac[i] = 1.0f;
+            for (size_t q = 0; q < plane; q++) ac[q] = 1.0f;
         } else if (cfg->laser_profile == PIC_LASER_GAUSSIAN) {
             const double zR = kPi * cfg->w0 * cfg->w0 / cfg->lambda, sa = -Lant;
             const double wa = cfg->w0 * sqrt(1.0 + (sa / zR) * (sa / zR));
             const double Ra = sa + zR * zR / sa;
-            const double gouy = 0.5 * atan(sa / zR);
-            const double amp0 = sqrt(cfg->w0 / wa);
+            const double gouy = (d3 ? 1.0 : 0.5) * atan(sa / zR);
+            const double amp0 = d3 ? cfg->w0 / wa : sqrt(cfg->w0 / wa);
             const double kw = c.omega / kC;
-            for (int i = 0; i < L.nx; i++) {
-                const double xr = ((double)i + 0.5 - 0.5 * L.nx) * cfg->dx;
-                const double amp = amp0 * exp(-xr * xr / (wa * wa));
-                const double ph = -kw * xr * xr / (2.0 * Ra) + gouy;
-                ac[i] = (float)(amp * cos(ph));
-                as[i] = (float)(amp * sin(ph));
-            }
+            for (int j = 0; j < L.ny; j++)
+                for (int i = 0; i < L.nx; i++) {
+                    const double xr = ((double)i + 0.5 - 0.5 * L.nx) * cfg->dx;
+                    const double yr = d3 ? ((double)j - 0.5 * L.ny) * cfg->dx : 0.0;
+                    const double r2 = xr * xr + yr * yr;
+                    const double amp = amp0 * exp(-r2 / (wa * wa));
+                    const double ph = -kw * r2 / (2.0 * Ra) + gouy;
+                    ac[(size_t)j * L.nx + i] = (float)(amp * cos(ph));
+                    as[(size_t)j * L.nx + i] = (float)(amp * sin(ph));
+                }
         }
-        if (cudaMemcpyAsync(c.ant_c, ac.data(), 4 * L.nx, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
-            cudaMemcpyAsync(c.ant_s, as.data(), 4 * L.nx, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
+        if (cudaMemcpyAsync(c.ant_c, ac.data(), 4 * plane, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
+            cudaMemcpyAsync(c.ant_s, as.data(), 4 * plane, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
             cudaStreamSynchronize(c.stream) != cudaSuccess) {
             delete h;
             return PIC_ECUDA;
@@ -337,7 +361,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     for (int q = 0; q < 6; q++) ok &= cudaMemsetAsync(c.F[q], 0, 4 * L.nn, c.stream) == cudaSuccess;
     for (int q = 0; q < 3; q++) ok &= cudaMemsetAsync(c.J[q], 0, 8 * L.nn, c.stream) == cudaSuccess;
     for (int q = 0; q < 2; q++) ok &= cudaMemsetAsync(c.rho[q], 0, 8 * L.nn, c.stream) == cudaSuccess;
-    ok &= cudaMemsetAsync(c.mur_save, 0, 4 * 8 * (size_t)L.nx, c.stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(c.mur_save, 0, 4 * 8 * plane, c.stream) == cudaSuccess;
     ok &= cudaMemsetAsync(c.status, 0, 16, c.stream) == cudaSuccess;
     if (!ok) {
         delete h;
@@ -346,7 +370,8 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     c.cur = 0;
     // initial particles into the second buffers, then sort into tiles
     for (int s = 0; s < c.nsp; s++) {
-        launch_init_particles(c, s, c.stream);
+        if (d3) launch_init_particles3(c, s, c.stream);
+        else launch_init_particles(c, s, c.stream);
         sort_species_impl(c, s, c.stream, 1, nullptr);
     }
     r = redeposit(c);
@@ -381,10 +406,10 @@ int pic_step(pic_ctx* h, int32_t nsteps)
         for (int q = 0; q < 3; q++) CK(cudaMemsetAsync(c.J[q], 0, 8 * c.nn, c.stream));
         // the next node density starts from the current one; the particle kernel adds the changes
         CK(cudaMemcpyAsync(c.rho[1 - c.cur], c.rho[c.cur], 8 * c.nn, cudaMemcpyDeviceToDevice, c.stream));
-        StepArgs a = make_step_args(c);
         int r = ev_begin(h, 0);
         if (r) return r;
-        launch_particle_step(c, a, c.stream);
+        if (c.dims == 3) launch_particle_step3(c, c.stream);
+        else launch_particle_step(c, make_step_args(c), c.stream);
         r = ev_end(h);
         if (r) return r;
         c.nlaunch[0]++;
@@ -393,7 +418,8 @@ int pic_step(pic_ctx* h, int32_t nsteps)
             r = ev_begin(h, 1);
             if (r) return r;
             const int64_t before = c.nlaunch[1];
-            launch_fields(c, c.stream, c.step, &c.nlaunch[1]);
+            if (c.dims == 3) launch_fields3(c, c.stream, c.step, &c.nlaunch[1]);
+            else launch_fields(c, c.stream, c.step, &c.nlaunch[1]);
             r = ev_end(h);
             if (r) return r;
             c.nlaunch[3] += c.nlaunch[1] - before;
@@ -411,9 +437,12 @@ int pic_deposit_density(pic_ctx* h, int64_t* dev_out, double* scale_out)
     if (!h || !dev_out) return PIC_EINVAL;
     Ctx& c = h->c;
     if (c.sticky) return c.sticky;
-    launch_deposit_density(c, (u64*)dev_out, c.stream);
+    if (c.dims == 3) launch_deposit_density3(c, (u64*)dev_out, c.stream);
+    else launch_deposit_density(c, (u64*)dev_out, c.stream);
     CK(cudaGetLastError());
-    if (scale_out) *scale_out = c.w / (4294967296.0 * c.cfg.dx * c.cfg.dx);
+    if (scale_out)
+        *scale_out = c.dims == 3 ? c.w / (4398046511104.0 * c.cfg.dx * c.cfg.dx * c.cfg.dx)
+                                 : c.w / (4294967296.0 * c.cfg.dx * c.cfg.dx);
     return PIC_OK;
 }
 
@@ -422,7 +451,8 @@ int pic_pair_force(pic_ctx* h, float* dev_out)
     if (!h || !dev_out) return PIC_EINVAL;
     Ctx& c = h->c;
     if (c.sticky) return c.sticky;
-    launch_pair_force(c, dev_out, c.stream);
+    if (c.dims == 3) launch_pair_force3(c, dev_out, c.stream);
+    else launch_pair_force(c, dev_out, c.stream);
     CK(cudaGetLastError());
     return PIC_OK;
 }
@@ -433,7 +463,8 @@ int pic_energy(pic_ctx* h, pic_energy_t* out)
     Ctx& c = h->c;
     if (c.sticky) return c.sticky;
     double e[5];
-    launch_energy(c, c.stream, e);
+    if (c.dims == 3) launch_energy3(c, c.stream, e);
+    else launch_energy(c, c.stream, e);
     CK(cudaGetLastError());
     out->kinetic_ion = e[0];
     out->kinetic_electron = e[1];
@@ -464,17 +495,18 @@ int pic_get_info(pic_ctx* h, pic_info* out)
 static cudaMemcpyKind kind_out(int32_t on_host) { return on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
 static cudaMemcpyKind kind_in(int32_t on_host) { return on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
 
-int pic_get_particles(pic_ctx* h, int32_t s, int32_t* cell, float* fx, float* fz, float* ux, float* uy, float* uz,
-                      int32_t on_host)
+int pic_get_particles(pic_ctx* h, int32_t s, int32_t* cell, float* fx, float* fy, float* fz, float* ux, float* uy,
+                      float* uz, int32_t on_host)
 {
     if (!h || s < 0 || s >= h->c.nsp) return PIC_EINVAL;
     Ctx& c = h->c;
     const Species& S = c.sp[s];
     const size_t n = (size_t)S.n;
     if (n == 0) return PIC_OK;
-    if (!cell || !fx || !fz || !ux || !uy || !uz) return PIC_EINVAL;
+    if (!cell || !fx || !fz || !ux || !uy || !uz || (c.dims == 3 && !fy)) return PIC_EINVAL;
     CK(cudaMemcpyAsync(cell, S.a.cell, 4 * n, kind_out(on_host), c.stream));
     CK(cudaMemcpyAsync(fx, S.a.fx, 4 * n, kind_out(on_host), c.stream));
+    if (c.dims == 3) CK(cudaMemcpyAsync(fy, S.a.fy, 4 * n, kind_out(on_host), c.stream));
     CK(cudaMemcpyAsync(fz, S.a.fz, 4 * n, kind_out(on_host), c.stream));
     CK(cudaMemcpyAsync(ux, S.a.ux, 4 * n, kind_out(on_host), c.stream));
     CK(cudaMemcpyAsync(uy, S.a.uy, 4 * n, kind_out(on_host), c.stream));
@@ -483,18 +515,19 @@ int pic_get_particles(pic_ctx* h, int32_t s, int32_t* cell, float* fx, float* fz
     return PIC_OK;
 }
 
-int pic_set_particles(pic_ctx* h, int32_t s, int64_t n, const int32_t* cell, const float* fx, const float* fz,
-                      const float* ux, const float* uy, const float* uz, int32_t on_host)
+int pic_set_particles(pic_ctx* h, int32_t s, int64_t n, const int32_t* cell, const float* fx, const float* fy,
+                      const float* fz, const float* ux, const float* uy, const float* uz, int32_t on_host)
 {
     if (!h || s < 0 || s >= h->c.nsp || n < 0) return PIC_EINVAL;
     Ctx& c = h->c;
     Species& S = c.sp[s];
     if (n > S.cap) return PIC_ENOMEM;
-    if (n > 0 && (!cell || !fx || !fz || !ux || !uy || !uz)) return PIC_EINVAL;
+    if (n > 0 && (!cell || !fx || !fz || !ux || !uy || !uz || (c.dims == 3 && !fy))) return PIC_EINVAL;
     const size_t b = 4 * (size_t)n;
     if (n > 0) {
         CK(cudaMemcpyAsync(S.b.cell, cell, b, kind_in(on_host), c.stream));
         CK(cudaMemcpyAsync(S.b.fx, fx, b, kind_in(on_host), c.stream));
+        if (c.dims == 3) CK(cudaMemcpyAsync(S.b.fy, fy, b, kind_in(on_host), c.stream));
         CK(cudaMemcpyAsync(S.b.fz, fz, b, kind_in(on_host), c.stream));
         CK(cudaMemcpyAsync(S.b.ux, ux, b, kind_in(on_host), c.stream));
         CK(cudaMemcpyAsync(S.b.uy, uy, b, kind_in(on_host), c.stream));

@@ -123,7 +123,7 @@ int pic_batch_workspace_size(const pic_config* cfgs, int32_t n, size_t* bytes)
     if (!cfgs || !bytes || n < 1 || n > kMaxSlabs) return PIC_EINVAL;
     size_t t = 0;
     for (int s = 0; s < n; s++) {
-        if (cfgs[s].mode != cfgs[0].mode) return PIC_EINVAL;
+        if (cfgs[s].mode != cfgs[0].mode || (cfgs[s].dims != 0 && cfgs[s].dims != 2)) return PIC_EINVAL;
         size_t b = 0;
         const int r = pic_workspace_size(&cfgs[s], &b);
         if (r) return r;

@@ -42,12 +42,14 @@ __global__ void k_pair_force(const int32_t* __restrict__ cell, const float* __re
 
 // Flags particles outside the grid or with offsets outside [0,1) x [0,1] (bit 0 of *bad).
 __global__ void k_validate(const int32_t* __restrict__ cell, const float* __restrict__ fx,
-                           const float* __restrict__ fz, int64_t n, int64_t ncell, unsigned* bad)
+                           const float* __restrict__ fy, const float* __restrict__ fz, int64_t n, int64_t ncell,
+                           unsigned* bad)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int c = cell[p];
-        const float a = fx[p], b = fz[p];
-        if (c < 0 || c >= ncell || !(a >= 0.0f && a < 1.0f && b >= 0.0f && b <= 1.0f)) atomicOr(bad, 1u);
+        const float a = fx[p], b = fz[p], y = fy ? fy[p] : 0.0f;
+        if (c < 0 || c >= ncell || !(a >= 0.0f && a < 1.0f && b >= 0.0f && b <= 1.0f && y >= 0.0f && y < 1.0f))
+            atomicOr(bad, 1u);
     }
 }
 
@@ -70,7 +72,8 @@ void launch_deposit_density(Ctx& c, u64* out, cudaStream_t st)
 void launch_validate(Ctx& c, const SpeciesBuf& b, int64_t n, unsigned* bad, cudaStream_t st)
 {
     if (n == 0) return;
-    k_validate<<<grid_for(c, n), 256, 0, st>>>(b.cell, b.fx, b.fz, n, (int64_t)c.nx * c.nz, bad);
+    k_validate<<<grid_for(c, n), 256, 0, st>>>(b.cell, b.fx, c.dims == 3 ? b.fy : nullptr, b.fz, n,
+                                               (int64_t)c.nx * c.ny * c.nz, bad);
 }
 
 void launch_pair_force(Ctx& c, float* out, cudaStream_t st)

@@ -196,6 +196,7 @@ extern "C" int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* i
 {
     using namespace gbpic;
     if (!cfg || !in || !dev_out5) return PIC_EINVAL;
+    if (cfg->dims != 0 && cfg->dims != 2) return PIC_EINVAL;     // 2D states only
     if (cfg->nx < 3 || cfg->nz < 4 || cfg->nx >= 32768 || cfg->nz >= 32768) return PIC_EINVAL;
     if (cfg->mode != PIC_MODE_FULL && cfg->mode != PIC_MODE_TRANSPORT) return PIC_EINVAL;
     if (!(cfg->dx > 0) || !(cfg->n_atoms > 0) || !(cfg->ion_mass_amu > 0) || cfg->ppc_ion <= 0) return PIC_EINVAL;

@@ -1,0 +1,786 @@
+// The PIC cycle with the pair-potential force in three dimensions (3D3V): the same method as the
+// 2D kernels with Eqs. (1)-(3) along x, y and z (the cubic lattice's six neighbours), trilinear
+// weights, Esirkepov's 3D current and the 3D Yee scheme. x and y are periodic, z has walls.
+// Fixed point: 2^14 per axis (a particle's weight product is at most 2^42). Grids are
+// (nz+1) x ny x nx, index (k*ny + j)*nx + i. Yee positions: Ex (i+1/2,j,k), Ey (i,j+1/2,k),
+// Ez (i,j,k+1/2), Bx (i,j+1/2,k+1/2), By (i+1/2,j,k+1/2), Bz (i+1/2,j+1/2,k).
+//
+// The particle kernel streams each tile's particles through shared memory and processes them
+// transposed (lanes in different cells), like the 2D kernel; fields and the node density are
+// gathered from global memory (L1-resident within a tile) and deposits use global 64-bit
+// reductions, which are native in L2.
+#include "pic_device.cuh"
+
+namespace gbpic {
+
+constexpr int kQ3Bits = 14;
+constexpr int kQ3 = 1 << kQ3Bits;
+constexpr int kBlock3 = 256;
+constexpr int kRows3 = 32;
+constexpr int kPitch3 = 33;
+constexpr int kChunk3 = 32 * kRows3;
+constexpr int kChunkWords3 = kRows3 * kPitch3;
+
+__device__ __forceinline__ int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+__device__ __forceinline__ int qoff3(float f) { return __float2int_rn(f * 16384.0f); }
+
+__device__ __forceinline__ void hat3q(int d, int& s0, int& s1, int& s2)
+{
+    s0 = max(0, kQ3 - d);
+    s1 = kQ3 - abs(d - kQ3);
+    s2 = max(0, d - kQ3);
+}
+
+struct Geo3 {
+    int nx, ny, nz;
+    unsigned mag_x, mag_y;     // floor(2^32 / nx), floor(2^32 / ny)
+};
+
+__device__ __forceinline__ void split3(int cell, const Geo3& g, int& i, int& j, int& k)
+{
+    unsigned q = __umulhi((unsigned)cell, g.mag_x);
+    int r = cell - (int)q * g.nx;
+    if (r >= g.nx) { q++; r -= g.nx; }
+    i = r;
+    unsigned q2 = __umulhi(q, g.mag_y);
+    int r2 = (int)q - (int)q2 * g.ny;
+    if (r2 >= g.ny) { q2++; r2 -= g.ny; }
+    j = r2;
+    k = (int)q2;
+}
+
+__device__ __forceinline__ size_t idx3(const Geo3& g, int i, int j, int k)
+{
+    return ((size_t)k * g.ny + j) * g.nx + i;
+}
+
+// staggered trilinear gather; (hx, hy, hz) = 1 where the component sits half a cell up
+__device__ __forceinline__ float gather3(const float* __restrict__ A, const Geo3& g, int i, int j, int k, float fx,
+                                         float fy, float fz, int hx, int hy, int hz)
+{
+    int i0 = i, j0 = j, r0 = k, r1 = k + 1;
+    float wx = fx, wy = fy, wz = fz;
+    if (hx) {
+        if (fx >= 0.5f) wx = fx - 0.5f;
+        else { i0 = wrapn(i - 1, g.nx); wx = fx + 0.5f; }
+    }
+    if (hy) {
+        if (fy >= 0.5f) wy = fy - 0.5f;
+        else { j0 = wrapn(j - 1, g.ny); wy = fy + 0.5f; }
+    }
+    if (hz) {
+        if (fz >= 0.5f) {
+            wz = fz - 0.5f;
+            if (k >= g.nz - 1) { r0 = g.nz - 2; r1 = g.nz - 1; wz = 1.0f; }
+        } else if (k >= 1) {
+            r0 = k - 1; r1 = k; wz = fz + 0.5f;
+        } else {
+            r0 = 0; r1 = 1; wz = 0.0f;
+        }
+    }
+    const int i1 = wrapn(i0 + 1, g.nx), j1 = wrapn(j0 + 1, g.ny);
+    const float a000 = __ldg(A + idx3(g, i0, j0, r0)), a100 = __ldg(A + idx3(g, i1, j0, r0));
+    const float a010 = __ldg(A + idx3(g, i0, j1, r0)), a110 = __ldg(A + idx3(g, i1, j1, r0));
+    const float a001 = __ldg(A + idx3(g, i0, j0, r1)), a101 = __ldg(A + idx3(g, i1, j0, r1));
+    const float a011 = __ldg(A + idx3(g, i0, j1, r1)), a111 = __ldg(A + idx3(g, i1, j1, r1));
+    const float b00 = a000 + wx * (a100 - a000), b10 = a010 + wx * (a110 - a010);
+    const float b01 = a001 + wx * (a101 - a001), b11 = a011 + wx * (a111 - a011);
+    const float c0 = b00 + wy * (b10 - b00), c1 = b01 + wy * (b11 - b01);
+    return c0 + wz * (c1 - c0);
+}
+
+// trilinear node density (units n0) and its exact gradient (units n0 per cell); wall rows doubled
+__device__ __forceinline__ void density3(const u64* __restrict__ rho, const Geo3& g, float rho_s, int i, int j, int k,
+                                         float fx, float fy, float fz, float& n, float* grad)
+{
+    const int i1 = wrapn(i + 1, g.nx), j1 = wrapn(j + 1, g.ny);
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                long long r = (long long)__ldg(rho + idx3(g, a ? i1 : i, b ? j1 : j, k + c));
+                if (k + c == 0 || k + c == g.nz) r *= 2;
+                v[c * 4 + b * 2 + a] = rho_s * (float)r;
+            }
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    // along x: differences of the x-pairs weighted in y and z
+    const float dx00 = v[1] - v[0], dx10 = v[3] - v[2], dx01 = v[5] - v[4], dx11 = v[7] - v[6];
+    grad[0] = gz * (gy * dx00 + fy * dx10) + fz * (gy * dx01 + fy * dx11);
+    const float dy00 = v[2] - v[0], dy10 = v[3] - v[1], dy01 = v[6] - v[4], dy11 = v[7] - v[5];
+    grad[1] = gz * (gx * dy00 + fx * dy10) + fz * (gx * dy01 + fx * dy11);
+    const float dz00 = v[4] - v[0], dz10 = v[5] - v[1], dz01 = v[6] - v[2], dz11 = v[7] - v[3];
+    grad[2] = gy * (gx * dz00 + fx * dz10) + fy * (gx * dz01 + fx * dz11);
+    n = gz * (gy * (gx * v[0] + fx * v[1]) + fy * (gx * v[2] + fx * v[3])) +
+        fz * (gy * (gx * v[4] + fx * v[5]) + fy * (gx * v[6] + fx * v[7]));
+}
+
+struct Species3 {
+    int32_t* cell;
+    float *fx, *fy, *fz, *ux, *uy, *uz;
+    const int32_t* tile_start;
+    float e_kick, b_rot, p_kick;
+    int jsign, pair;
+};
+
+struct Args3 {
+    Geo3 g;
+    int ntiles, nsp, full, pot_mode;
+    float cdt_dx, rho_s, h_coef, c_att, s_rep;
+    const float* F[6];
+    const u64* rho_cur;
+    u64* rho_next;
+    u64* J[3];
+    unsigned* status;
+    Species3 sp[2];
+};
+
+__device__ __forceinline__ void red64(u64* p, long long v)
+{
+    if (v != 0) atomicAdd(p, (u64)v);
+}
+
+// General 3 x 3 x 3 Esirkepov stencil and node-density change with global reductions.
+// (X, Y, Z) global fixed-point coordinates; X1, Y1 may lie outside the periodic range.
+__device__ __noinline__ void deposit3_general(Geo3 g, u64* J0, u64* J1, u64* J2, u64* rho_next, int X0, int Y0,
+                                              int Z0, int X1, int Y1, int Z1, int jsign, int pair)
+{
+    const int bx = min(X0, X1) >> kQ3Bits, by = min(Y0, Y1) >> kQ3Bits, bz = min(Z0, Z1) >> kQ3Bits;
+    int S0x[3], S1x[3], S0y[3], S1y[3], S0z[3], S1z[3];
+    hat3q(X0 - bx * kQ3, S0x[0], S0x[1], S0x[2]);
+    hat3q(X1 - bx * kQ3, S1x[0], S1x[1], S1x[2]);
+    hat3q(Y0 - by * kQ3, S0y[0], S0y[1], S0y[2]);
+    hat3q(Y1 - by * kQ3, S1y[0], S1y[1], S1y[2]);
+    hat3q(Z0 - bz * kQ3, S0z[0], S0z[1], S0z[2]);
+    hat3q(Z1 - bz * kQ3, S1z[0], S1z[1], S1z[2]);
+    const long long sg = jsign;
+    for (int c = 0; c < 3; c++)
+        for (int b = 0; b < 3; b++) {
+            const int jj = wrapn(by + b, g.ny);
+            if (jsign) {
+                const long long P = 2LL * S0y[b] * S0z[c] + (long long)S1y[b] * S0z[c] + (long long)S0y[b] * S1z[c] +
+                                    2LL * S1y[b] * S1z[c];
+                long long acc = 0;
+                for (int q = 0; q < 2; q++) {
+                    acc -= (long long)(S1x[q] - S0x[q]) * P;
+                    red64(J0 + idx3(g, wrapn(bx + q, g.nx), jj, bz + c), sg * acc);
+                }
+            }
+            if (pair)
+                for (int q = 0; q < 3; q++)
+                    red64(rho_next + idx3(g, wrapn(bx + q, g.nx), jj, bz + c),
+                          (long long)S1x[q] * S1y[b] * S1z[c] - (long long)S0x[q] * S0y[b] * S0z[c]);
+        }
+    if (!jsign) return;
+    for (int c = 0; c < 3; c++)
+        for (int q = 0; q < 3; q++) {
+            const long long P = 2LL * S0x[q] * S0z[c] + (long long)S1x[q] * S0z[c] + (long long)S0x[q] * S1z[c] +
+                                2LL * S1x[q] * S1z[c];
+            long long acc = 0;
+            for (int b = 0; b < 2; b++) {
+                acc -= (long long)(S1y[b] - S0y[b]) * P;
+                red64(J1 + idx3(g, wrapn(bx + q, g.nx), wrapn(by + b, g.ny), bz + c), sg * acc);
+            }
+        }
+    for (int b = 0; b < 3; b++)
+        for (int q = 0; q < 3; q++) {
+            const long long P = 2LL * S0x[q] * S0y[b] + (long long)S1x[q] * S0y[b] + (long long)S0x[q] * S1y[b] +
+                                2LL * S1x[q] * S1y[b];
+            long long acc = 0;
+            for (int c = 0; c < 2; c++) {
+                acc -= (long long)(S1z[c] - S0z[c]) * P;
+                red64(J2 + idx3(g, wrapn(bx + q, g.nx), wrapn(by + b, g.ny), bz + c), sg * acc);
+            }
+        }
+}
+
+template <bool FULL, bool PAIR>
+__device__ __forceinline__ void process3(const Args3& a, const Species3& S, int& cell, float& fx_io, float& fy_io,
+                                         float& fz_io, float& ux, float& uy, float& uz)
+{
+    const Geo3& g = a.g;
+    const float fx = fx_io, fy = fy_io, fz = fz_io;
+    int i, j, k;
+    split3(cell, g, i, j, k);
+    float kx = 0.f, ky = 0.f, kz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    if (FULL) {
+        kx = S.e_kick * gather3(a.F[0], g, i, j, k, fx, fy, fz, 1, 0, 0);
+        ky = S.e_kick * gather3(a.F[1], g, i, j, k, fx, fy, fz, 0, 1, 0);
+        kz = S.e_kick * gather3(a.F[2], g, i, j, k, fx, fy, fz, 0, 0, 1);
+        bx = gather3(a.F[3], g, i, j, k, fx, fy, fz, 0, 1, 1);
+        by = gather3(a.F[4], g, i, j, k, fx, fy, fz, 1, 0, 1);
+        bz = gather3(a.F[5], g, i, j, k, fx, fy, fz, 1, 1, 0);
+    }
+    if (PAIR) {
+        float n, gr[3];
+        density3(a.rho_cur, g, a.rho_s, i, j, k, fx, fy, fz, n, gr);
+        if (n > 0.0f) {
+            const float c = fast_cbrt(n);
+            const float inv43 = fast_rcp(n * c);
+            kx += S.p_kick * pair_axis(n, c, inv43, gr[0], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+            ky += S.p_kick * pair_axis(n, c, inv43, gr[1], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+            kz += S.p_kick * pair_axis(n, c, inv43, gr[2], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+        }
+    }
+    const float ux0 = ux, uy0 = uy, uz0 = uz;
+    ux += kx; uy += ky; uz += kz;
+    if (FULL) {
+        const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        const float tx = S.b_rot * ig * bx, ty = S.b_rot * ig * by, tz = S.b_rot * ig * bz;
+        const float s = 2.0f * fast_rcp(1.0f + tx * tx + ty * ty + tz * tz);
+        const float px = ux + (uy * tz - uz * ty);
+        const float py = uy + (uz * tx - ux * tz);
+        const float pz = uz + (ux * ty - uy * tx);
+        ux += s * (py * tz - pz * ty);
+        uy += s * (pz * tx - px * tz);
+        uz += s * (px * ty - py * tx);
+    }
+    ux += kx; uy += ky; uz += kz;
+    const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+    float dxi = ux * a.cdt_dx * ig, dyi = uy * a.cdt_dx * ig, dze = uz * a.cdt_dx * ig;
+    if (!(fabsf(dxi) < 1.0f && fabsf(dyi) < 1.0f && fabsf(dze) < 1.0f)) {
+        atomicOr(a.status, (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? kErrMove : kErrNan);
+        ux = ux0; uy = uy0; uz = uz0; dxi = dyi = dze = 0.0f;
+    }
+    float nfx = fx + dxi, nfy = fy + dyi, nfz = fz + dze;
+    int di = (int)floorf(nfx);
+    nfx -= (float)di;
+    if (nfx >= 1.0f) { nfx = 0.0f; di += 1; }
+    int dj = (int)floorf(nfy);
+    nfy -= (float)dj;
+    if (nfy >= 1.0f) { nfy = 0.0f; dj += 1; }
+    int dk = 0;
+    if (k == 0 && nfz < 0.0f) {
+        nfz = -nfz; uz = -uz;
+    } else if (k == g.nz - 1 && nfz >= 1.0f) {
+        nfz = 2.0f - nfz; uz = -uz;
+    } else {
+        dk = (int)floorf(nfz);
+        nfz -= (float)dk;
+        if (nfz >= 1.0f) { nfz = 0.0f; dk += 1; }
+    }
+    cell = (int)idx3(g, wrapn(i + di, g.nx), wrapn(j + dj, g.ny), k + dk);
+    fx_io = nfx;
+    fy_io = nfy;
+    fz_io = nfz;
+
+    const int x0 = qoff3(fx), x1 = qoff3(nfx), y0 = qoff3(fy), y1 = qoff3(nfy), z0 = qoff3(fz), z1 = qoff3(nfz);
+    const bool moved = (di | dj | dk) != 0 || x1 != x0 || y1 != y0 || z1 != z0;
+    if (!moved) return;
+    if ((di | dj | dk) == 0) {
+        // stays in its cell: edges and corners of the cell only
+        const int i1 = wrapn(i + 1, g.nx), j1 = wrapn(j + 1, g.ny);
+        if (S.jsign) {
+            const long long sg = S.jsign;
+            const long long ay0 = kQ3 - y0, ay1 = kQ3 - y1, az0 = kQ3 - z0, az1 = kQ3 - z1, ax0 = kQ3 - x0,
+                            ax1 = kQ3 - x1;
+            const int dX = x1 - x0, dY = y1 - y0, dZ = z1 - z0;
+            if (dX) {
+                // J6x(i+1/2, j+b, k+c) = dX (2 S0y S0z + S1y S0z + S0y S1z + 2 S1y S1z)
+                const long long p00 = 2 * ay0 * az0 + ay1 * az0 + ay0 * az1 + 2 * ay1 * az1;
+                const long long p10 = 2LL * y0 * az0 + (long long)y1 * az0 + (long long)y0 * az1 + 2LL * y1 * az1;
+                const long long p01 = 2 * ay0 * z0 + ay1 * z0 + ay0 * z1 + 2 * ay1 * z1;
+                const long long p11 = 2LL * y0 * z0 + (long long)y1 * z0 + (long long)y0 * z1 + 2LL * y1 * z1;
+                red64(a.J[0] + idx3(g, i, j, k), sg * dX * p00);
+                red64(a.J[0] + idx3(g, i, j1, k), sg * dX * p10);
+                red64(a.J[0] + idx3(g, i, j, k + 1), sg * dX * p01);
+                red64(a.J[0] + idx3(g, i, j1, k + 1), sg * dX * p11);
+            }
+            if (dY) {
+                const long long p00 = 2 * ax0 * az0 + ax1 * az0 + ax0 * az1 + 2 * ax1 * az1;
+                const long long p10 = 2LL * x0 * az0 + (long long)x1 * az0 + (long long)x0 * az1 + 2LL * x1 * az1;
+                const long long p01 = 2 * ax0 * z0 + ax1 * z0 + ax0 * z1 + 2 * ax1 * z1;
+                const long long p11 = 2LL * x0 * z0 + (long long)x1 * z0 + (long long)x0 * z1 + 2LL * x1 * z1;
+                red64(a.J[1] + idx3(g, i, j, k), sg * dY * p00);
+                red64(a.J[1] + idx3(g, i1, j, k), sg * dY * p10);
+                red64(a.J[1] + idx3(g, i, j, k + 1), sg * dY * p01);
+                red64(a.J[1] + idx3(g, i1, j, k + 1), sg * dY * p11);
+            }
+            if (dZ) {
+                const long long p00 = 2 * ax0 * ay0 + ax1 * ay0 + ax0 * ay1 + 2 * ax1 * ay1;
+                const long long p10 = 2LL * x0 * ay0 + (long long)x1 * ay0 + (long long)x0 * ay1 + 2LL * x1 * ay1;
+                const long long p01 = 2 * ax0 * y0 + ax1 * y0 + ax0 * y1 + 2 * ax1 * y1;
+                const long long p11 = 2LL * x0 * y0 + (long long)x1 * y0 + (long long)x0 * y1 + 2LL * x1 * y1;
+                red64(a.J[2] + idx3(g, i, j, k), sg * dZ * p00);
+                red64(a.J[2] + idx3(g, i1, j, k), sg * dZ * p10);
+                red64(a.J[2] + idx3(g, i, j1, k), sg * dZ * p01);
+                red64(a.J[2] + idx3(g, i1, j1, k), sg * dZ * p11);
+            }
+        }
+        if (PAIR) {
+            const long long sx0[2] = {kQ3 - x0, x0}, sx1[2] = {kQ3 - x1, x1};
+            const long long sy0[2] = {kQ3 - y0, y0}, sy1[2] = {kQ3 - y1, y1};
+            const long long sz0[2] = {kQ3 - z0, z0}, sz1[2] = {kQ3 - z1, z1};
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int b = 0; b < 2; b++)
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        red64(a.rho_next + idx3(g, q ? i1 : i, b ? j1 : j, k + c),
+                              sx1[q] * sy1[b] * sz1[c] - sx0[q] * sy0[b] * sz0[c]);
+        }
+    } else {
+        deposit3_general(g, a.J[0], a.J[1], a.J[2], a.rho_next, i * kQ3 + x0, j * kQ3 + y0, k * kQ3 + z0,
+                         (i + di) * kQ3 + x1, (j + dj) * kQ3 + y1, (k + dk) * kQ3 + z1, S.jsign, PAIR ? 1 : 0);
+    }
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(kBlock3, 3) k_particles3(const Args3 a)
+{
+    __shared__ unsigned chunk[7 * kChunkWords3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* c_cell = reinterpret_cast<int*>(chunk);
+    float* c_f = reinterpret_cast<float*>(chunk + kChunkWords3);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            if (s >= a.nsp) break;
+            const Species3& S = a.sp[s];
+            const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
+            for (int c0 = p0; c0 < p1; c0 += kChunk3) {
+                const int n = min(kChunk3, p1 - c0);
+                const int lg = n > kChunk3 / 2 ? 5 : 32 - __clz(((n + 31) >> 5) - 1);
+                const int rows = 1 << lg;
+                for (int ci = threadIdx.x; ci < n; ci += kBlock3) {
+                    const int slot = (ci & (rows - 1)) * kPitch3 + (ci >> lg);
+                    c_cell[slot] = S.cell[c0 + ci];
+                    c_f[slot] = S.fx[c0 + ci];
+                    c_f[kChunkWords3 + slot] = S.fy[c0 + ci];
+                    c_f[2 * kChunkWords3 + slot] = S.fz[c0 + ci];
+                    c_f[3 * kChunkWords3 + slot] = S.ux[c0 + ci];
+                    c_f[4 * kChunkWords3 + slot] = S.uy[c0 + ci];
+                    c_f[5 * kChunkWords3 + slot] = S.uz[c0 + ci];
+                }
+                __syncthreads();
+                for (int col = warp; col < rows; col += kBlock3 / 32) {
+                    const int ci = (lane << lg) + col;
+                    if (ci < n) {
+                        const int slot = col * kPitch3 + lane;
+                        int cell = c_cell[slot];
+                        float fx = c_f[slot], fy = c_f[kChunkWords3 + slot], fz = c_f[2 * kChunkWords3 + slot];
+                        float ux = c_f[3 * kChunkWords3 + slot], uy = c_f[4 * kChunkWords3 + slot],
+                              uz = c_f[5 * kChunkWords3 + slot];
+                        if (s == 0) process3<FULL, true>(a, S, cell, fx, fy, fz, ux, uy, uz);
+                        else process3<FULL, false>(a, S, cell, fx, fy, fz, ux, uy, uz);
+                        c_cell[slot] = cell;
+                        c_f[slot] = fx;
+                        c_f[kChunkWords3 + slot] = fy;
+                        c_f[2 * kChunkWords3 + slot] = fz;
+                        c_f[3 * kChunkWords3 + slot] = ux;
+                        c_f[4 * kChunkWords3 + slot] = uy;
+                        c_f[5 * kChunkWords3 + slot] = uz;
+                    }
+                }
+                __syncthreads();
+                for (int ci = threadIdx.x; ci < n; ci += kBlock3) {
+                    const int slot = (ci & (rows - 1)) * kPitch3 + (ci >> lg);
+                    S.cell[c0 + ci] = c_cell[slot];
+                    S.fx[c0 + ci] = c_f[slot];
+                    S.fy[c0 + ci] = c_f[kChunkWords3 + slot];
+                    S.fz[c0 + ci] = c_f[2 * kChunkWords3 + slot];
+                    S.ux[c0 + ci] = c_f[3 * kChunkWords3 + slot];
+                    S.uy[c0 + ci] = c_f[4 * kChunkWords3 + slot];
+                    S.uz[c0 + ci] = c_f[5 * kChunkWords3 + slot];
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+static Geo3 geo_of(const Ctx& c)
+{
+    Geo3 g;
+    g.nx = c.nx;
+    g.ny = c.ny;
+    g.nz = c.nz;
+    g.mag_x = (unsigned)(4294967296ULL / (unsigned long long)c.nx);
+    g.mag_y = (unsigned)(4294967296ULL / (unsigned long long)c.ny);
+    return g;
+}
+
+void launch_particle_step3(Ctx& c, cudaStream_t st)
+{
+    Args3 a;
+    memset(&a, 0, sizeof(a));
+    a.g = geo_of(c);
+    a.ntiles = c.ntiles;
+    a.nsp = c.nsp;
+    a.full = c.cfg.mode == PIC_MODE_FULL;
+    a.pot_mode = c.cfg.pot_mode;
+    a.cdt_dx = (float)(kC * c.dt / c.cfg.dx);
+    a.rho_s = (float)c.rho_scale;
+    a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
+    a.c_att = (float)c.cfg.c_att;
+    a.s_rep = (float)c.cfg.s_rep;
+    for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
+    a.rho_cur = c.rho[c.cur];
+    a.rho_next = c.rho[1 - c.cur];
+    for (int q = 0; q < 3; q++) a.J[q] = c.J[q];
+    a.status = c.status;
+    for (int s = 0; s < 2; s++) {
+        const Species& S = c.sp[s];
+        Species3& d = a.sp[s];
+        d.cell = S.a.cell; d.fx = S.a.fx; d.fy = S.a.fy; d.fz = S.a.fz;
+        d.ux = S.a.ux; d.uy = S.a.uy; d.uz = S.a.uz;
+        d.tile_start = S.tile_start;
+        d.e_kick = S.e_kick; d.b_rot = S.b_rot; d.p_kick = S.p_kick;
+        d.jsign = S.jsign; d.pair = S.pair;
+    }
+    int grid = c.ntiles < c.nsm * 3 ? c.ntiles : c.nsm * 3;
+    if (grid < 1) grid = 1;
+    if (a.full) k_particles3<true><<<grid, kBlock3, 0, st>>>(a);
+    else k_particles3<false><<<grid, kBlock3, 0, st>>>(a);
+}
+
+// ---- stand-alone node density and pair force ------------------------------------------------
+
+__global__ void k_deposit_density3(const int32_t* __restrict__ cell, const float* __restrict__ fx,
+                                   const float* __restrict__ fy, const float* __restrict__ fz, int64_t n, Geo3 g,
+                                   u64* out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(cell[p], g, i, j, k);
+        const long long x = qoff3(fx[p]), y = qoff3(fy[p]), z = qoff3(fz[p]);
+        const long long sx[2] = {kQ3 - x, x}, sy[2] = {kQ3 - y, y}, sz[2] = {kQ3 - z, z};
+        const int i1 = wrapn(i + 1, g.nx), j1 = wrapn(j + 1, g.ny);
+        for (int c = 0; c < 2; c++)
+            for (int b = 0; b < 2; b++)
+                for (int q = 0; q < 2; q++) red64(out + idx3(g, q ? i1 : i, b ? j1 : j, k + c), sx[q] * sy[b] * sz[c]);
+    }
+}
+
+__global__ void k_pair_force3(const int32_t* __restrict__ cell, const float* __restrict__ fx,
+                              const float* __restrict__ fy, const float* __restrict__ fz, int64_t n, Geo3 g,
+                              const u64* __restrict__ rho, float rho_s, float h_coef, int pot_mode, float c_att,
+                              float s_rep, float f_unit, float* __restrict__ out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(cell[p], g, i, j, k);
+        float dens, gr[3];
+        density3(rho, g, rho_s, i, j, k, fx[p], fy[p], fz[p], dens, gr);
+        float F[3] = {0.f, 0.f, 0.f};
+        if (dens > 0.0f) {
+            const float cr = fast_cbrt(dens);
+            const float inv43 = fast_rcp(dens * cr);
+            for (int d = 0; d < 3; d++) F[d] = f_unit * pair_axis(dens, cr, inv43, gr[d], h_coef, pot_mode, c_att, s_rep);
+        }
+        out[3 * p] = F[0];
+        out[3 * p + 1] = F[1];
+        out[3 * p + 2] = F[2];
+    }
+}
+
+static int grid3(const Ctx& c, int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)c.nsm * 8) g = (int64_t)c.nsm * 8;
+    return g < 1 ? 1 : (int)g;
+}
+
+void launch_deposit_density3(Ctx& c, u64* out, cudaStream_t st)
+{
+    cudaMemsetAsync(out, 0, sizeof(u64) * c.nn, st);
+    const Species& S = c.sp[0];
+    if (S.n == 0) return;
+    k_deposit_density3<<<grid3(c, S.n), 256, 0, st>>>(S.a.cell, S.a.fx, S.a.fy, S.a.fz, S.n, geo_of(c), out);
+}
+
+void launch_pair_force3(Ctx& c, float* out, cudaStream_t st)
+{
+    const Species& S = c.sp[0];
+    if (S.n == 0) return;
+    k_pair_force3<<<grid3(c, S.n), 256, 0, st>>>(S.a.cell, S.a.fx, S.a.fy, S.a.fz, S.n, geo_of(c), c.rho[c.cur],
+                                                  (float)c.rho_scale, (float)(c.r0 / (6.0 * c.cfg.dx)),
+                                                  c.cfg.pot_mode, (float)c.cfg.c_att, (float)c.cfg.s_rep,
+                                                  (float)(c.D / c.r0), out);
+}
+
+// ---- 3D Yee --------------------------------------------------------------------------------
+
+struct Field3 {
+    Geo3 g;
+    int k_ant;
+    float h_b, h_e, cj, mur;
+    float* F[6];
+    const u64* J[3];
+    float* save;          // 8 planes of nx*ny: Ex(0) Ex(1) Ex(nz-1) Ex(nz) Ey(0) Ey(1) Ey(nz-1) Ey(nz)
+    const float* antc;    // nx*ny
+    const float* ants;
+    const float* ant;
+};
+
+__global__ void k_half_B3(const Field3 f, int save)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const Geo3& g = f.g;
+    if (i >= g.nx) return;
+    const int ip = i + 1 == g.nx ? 0 : i + 1, jp = j + 1 == g.ny ? 0 : j + 1;
+    const size_t c = idx3(g, i, j, k);
+    const float *Ex = f.F[0], *Ey = f.F[1], *Ez = f.F[2];
+    float *Bx = f.F[3], *By = f.F[4], *Bz = f.F[5];
+    const float ex = Ex[c], ey = Ey[c];
+    if (k < g.nz) {
+        const float ez = Ez[c];
+        const size_t up = c + (size_t)g.nx * g.ny;
+        Bx[c] += f.h_b * ((Ey[up] - ey) - (Ez[idx3(g, i, jp, k)] - ez));
+        By[c] += f.h_b * ((Ez[idx3(g, ip, j, k)] - ez) - (Ex[up] - ex));
+    }
+    Bz[c] += f.h_b * ((Ex[idx3(g, i, jp, k)] - ex) - (Ey[idx3(g, ip, j, k)] - ey));
+    if (save) {
+        int slot = -1;
+        if (k == 0) slot = 0;
+        else if (k == 1) slot = 1;
+        else if (k == g.nz - 1) slot = 2;
+        else if (k == g.nz) slot = 3;
+        if (slot >= 0) {
+            const size_t plane = (size_t)g.nx * g.ny, q = (size_t)j * g.nx + i;
+            f.save[slot * plane + q] = ex;
+            f.save[(4 + slot) * plane + q] = ey;
+        }
+    }
+}
+
+__device__ __forceinline__ float ex3_new(const Field3& f, int i, int j, int k, float old)
+{
+    const Geo3& g = f.g;
+    const size_t c = idx3(g, i, j, k);
+    const int jm = j == 0 ? g.ny - 1 : j - 1;
+    float v = old + f.h_e * ((f.F[5][c] - f.F[5][idx3(g, i, jm, k)]) - (f.F[4][c] - f.F[4][idx3(g, i, j, k - 1)])) -
+              f.cj * (float)(long long)f.J[0][c];
+    if (k == f.k_ant) {
+        const size_t q = (size_t)j * g.nx + i;
+        v += f.antc[q] * f.ant[0] + f.ants[q] * f.ant[1];
+    }
+    return v;
+}
+__device__ __forceinline__ float ey3_new(const Field3& f, int i, int j, int k, float old)
+{
+    const Geo3& g = f.g;
+    const size_t c = idx3(g, i, j, k);
+    const int im = i == 0 ? g.nx - 1 : i - 1;
+    return old + f.h_e * ((f.F[3][c] - f.F[3][idx3(g, i, j, k - 1)]) - (f.F[5][c] - f.F[5][idx3(g, im, j, k)])) -
+           f.cj * (float)(long long)f.J[1][c];
+}
+
+__global__ void k_E3(const Field3 f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const Geo3& g = f.g;
+    if (i >= g.nx) return;
+    const size_t c = idx3(g, i, j, k), plane = (size_t)g.nx * g.ny, q = (size_t)j * g.nx + i;
+    float* Ex = f.F[0];
+    float* Ey = f.F[1];
+    if (k > 0 && k < g.nz) {
+        Ex[c] = ex3_new(f, i, j, k, Ex[c]);
+        Ey[c] = ey3_new(f, i, j, k, Ey[c]);
+    } else if (k == 0) {
+        const float x0 = f.save[q], x1 = f.save[plane + q], y0 = f.save[4 * plane + q], y1 = f.save[5 * plane + q];
+        Ex[c] = x1 + f.mur * (ex3_new(f, i, j, 1, x1) - x0);
+        Ey[c] = y1 + f.mur * (ey3_new(f, i, j, 1, y1) - y0);
+    } else {
+        const float x1 = f.save[2 * plane + q], x0 = f.save[3 * plane + q], y1 = f.save[6 * plane + q],
+                    y0 = f.save[7 * plane + q];
+        Ex[c] = x1 + f.mur * (ex3_new(f, i, j, g.nz - 1, x1) - x0);
+        Ey[c] = y1 + f.mur * (ey3_new(f, i, j, g.nz - 1, y1) - y0);
+    }
+    if (k < g.nz) {
+        const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+        f.F[2][c] += f.h_e * ((f.F[4][c] - f.F[4][idx3(g, im, j, k)]) - (f.F[3][c] - f.F[3][idx3(g, i, jm, k)])) -
+                     f.cj * (float)(long long)f.J[2][c];
+    }
+}
+
+__global__ void k_antenna3(AntennaParams p, long long step, float* ant)
+{
+    float s = 0.0f, c = 0.0f;
+    if (p.on) {
+        const double tau = ((double)step + 0.5) * p.dt - p.t_ant;
+        const double env = exp(-2.0 * 0.6931471805599453 * tau * tau / (p.tau_fwhm * p.tau_fwhm));
+        const double a = p.coef * env;
+        s = (float)(a * sin(p.omega * tau));
+        c = (float)(a * cos(p.omega * tau));
+    }
+    ant[0] = s;
+    ant[1] = c;
+}
+
+void launch_fields3(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches)
+{
+    Field3 f;
+    f.g = geo_of(c);
+    f.k_ant = c.k_ant;
+    f.h_b = (float)(0.5 * c.dt / c.cfg.dx);
+    f.h_e = (float)(kC * kC * c.dt / c.cfg.dx);
+    f.cj = (float)(kQe * c.w / (6.0 * 4398046511104.0 * c.cfg.dx * c.cfg.dx * kEps0));
+    const double cdt = kC * c.dt;
+    f.mur = (float)((cdt - c.cfg.dx) / (cdt + c.cfg.dx));
+    for (int q = 0; q < 6; q++) f.F[q] = c.F[q];
+    for (int q = 0; q < 3; q++) f.J[q] = c.J[q];
+    f.save = c.mur_save;
+    f.antc = c.ant_c;
+    f.ants = c.ant_s;
+    f.ant = c.ant;
+    k_antenna3<<<1, 1, 0, st>>>(make_antenna_params(c), (long long)step, c.ant);
+    dim3 block(256), grid((c.nx + 255) / 256, c.ny, c.nz + 1);
+    k_half_B3<<<grid, block, 0, st>>>(f, 1);
+    k_E3<<<grid, block, 0, st>>>(f);
+    k_half_B3<<<grid, block, 0, st>>>(f, 0);
+    if (launches) *launches += 4;
+}
+
+// ---- energies ------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_energy3(const Species3 s0, const Species3 s1, int64_t n0, int64_t n1, int nsp, Geo3 g,
+                                                 const float* F0, const float* F1, const float* F2, const float* F3,
+                                                 const float* F4, const float* F5, const u64* rho, float rho_s,
+                                                 float h_coef, int pot_mode, float c_att, float s_rep, double* partials)
+{
+    __shared__ double sh[256];
+    const int64_t tid = blockIdx.x * (int64_t)256 + threadIdx.x, stride = (int64_t)gridDim.x * 256;
+    double ke[2] = {0.0, 0.0}, pe = 0.0, fe = 0.0, fb = 0.0;
+    for (int s = 0; s < nsp; s++) {
+        const Species3& S = s == 0 ? s0 : s1;
+        const int64_t ns = s == 0 ? n0 : n1;
+        for (int64_t p = tid; p < ns; p += stride) {
+            const float ux = S.ux[p], uy = S.uy[p], uz = S.uz[p];
+            const float u2 = ux * ux + uy * uy + uz * uz;
+            ke[s] += (double)(u2 / (sqrtf(1.0f + u2) + 1.0f));
+            if (s == 0) {
+                int i, j, k;
+                split3(S.cell[p], g, i, j, k);
+                float dens, gr[3];
+                density3(rho, g, rho_s, i, j, k, S.fx[p], S.fy[p], S.fz[p], dens, gr);
+                if (dens > 0.0f) {
+                    const float cr = fast_cbrt(dens), inv43 = fast_rcp(dens * cr);
+                    float e = 0.0f;
+                    for (int d = 0; d < 3; d++) e += pair_energy_axis(cr, inv43, gr[d], h_coef, pot_mode, c_att, s_rep);
+                    pe += (double)e;
+                }
+            }
+        }
+    }
+    const int64_t nn = (int64_t)(g.nz + 1) * g.ny * g.nx, plane = (int64_t)g.ny * g.nx;
+    for (int64_t c = tid; c < nn; c += stride) {
+        const int k = (int)(c / plane);
+        const double wn = (k == 0 || k == g.nz) ? 0.5 : 1.0;
+        const double ex = F0[c], ey = F1[c], bz = F5[c];
+        fe += wn * (ex * ex + ey * ey);
+        fb += wn * bz * bz;
+        if (k < g.nz) {
+            const double ez = F2[c], bx = F3[c], by = F4[c];
+            fe += ez * ez;
+            fb += bx * bx + by * by;
+        }
+    }
+    double vals[5] = {ke[0], ke[1], fe, fb, pe};
+    for (int q = 0; q < 5; q++) {
+        sh[threadIdx.x] = vals[q];
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 5 + q] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_energy3_final(const double* __restrict__ partials, int nb, double* out)
+{
+    __shared__ double sh[256];
+    for (int q = 0; q < 5; q++) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nb; b += 256) v += partials[(size_t)b * 5 + q];
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = sh[0];
+        __syncthreads();
+    }
+}
+
+void launch_energy3(Ctx& c, cudaStream_t st, double* host_out5)
+{
+    Species3 sp[2];
+    memset(sp, 0, sizeof(sp));
+    for (int s = 0; s < 2; s++) {
+        const Species& S = c.sp[s];
+        sp[s].cell = S.a.cell; sp[s].fx = S.a.fx; sp[s].fy = S.a.fy; sp[s].fz = S.a.fz;
+        sp[s].ux = S.a.ux; sp[s].uy = S.a.uy; sp[s].uz = S.a.uz;
+    }
+    const int nb = c.nsm * 4;
+    k_energy3<<<nb, 256, 0, st>>>(sp[0], sp[1], c.sp[0].n, c.nsp > 1 ? c.sp[1].n : 0, c.nsp, geo_of(c), c.F[0], c.F[1],
+                                  c.F[2], c.F[3], c.F[4], c.F[5], c.rho[c.cur], (float)c.rho_scale,
+                                  (float)(c.r0 / (6.0 * c.cfg.dx)), c.cfg.pot_mode, (float)c.cfg.c_att,
+                                  (float)c.cfg.s_rep, c.partials);
+    k_energy3_final<<<1, 256, 0, st>>>(c.partials, nb, c.red_out);
+    double raw[5];
+    cudaMemcpyAsync(raw, c.red_out, sizeof(raw), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    const double vol = c.cfg.dx * c.cfg.dx * c.cfg.dx, mu0 = 1.0 / (kEps0 * kC * kC);
+    host_out5[0] = raw[0] * c.w * c.sp[0].mass * kC * kC;
+    host_out5[1] = c.nsp > 1 ? raw[1] * c.w * c.sp[1].mass * kC * kC : 0.0;
+    host_out5[2] = 0.5 * kEps0 * raw[2] * vol;
+    host_out5[3] = 0.5 / mu0 * raw[3] * vol;
+    host_out5[4] = 0.5 * c.D * raw[4] * c.w;
+}
+
+// ---- initial state -------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t smix3(uint64_t state)
+{
+    uint64_t z = state + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t draw3(uint64_t seed, int s, uint64_t pid, int d)
+{
+    return smix3(seed ^ (((((uint64_t)s << 40) + pid) << 3) + (uint64_t)d));
+}
+
+// slab cells k < slab_k over all (i, j), row-major; positions from draws 0 (x), 6 (y), 1 (z)
+__global__ void k_init3(SpeciesBuf out, int64_t n, int ppc, int nx, int ny, int species, int pos_species, double uth,
+                        uint64_t seed)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t cellidx = (uint64_t)p / (uint64_t)ppc;
+        out.cell[p] = (int32_t)cellidx;
+        out.fx[p] = (float)(draw3(seed, pos_species, (uint64_t)p, 0) >> 40) * (1.0f / 16777216.0f);
+        out.fy[p] = (float)(draw3(seed, pos_species, (uint64_t)p, 6) >> 40) * (1.0f / 16777216.0f);
+        out.fz[p] = (float)(draw3(seed, pos_species, (uint64_t)p, 1) >> 40) * (1.0f / 16777216.0f);
+        const double u1 = ((double)(draw3(seed, species, (uint64_t)p, 2) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+        const double a1 = 2.0 * kPi * (double)(draw3(seed, species, (uint64_t)p, 3) >> 40) * (1.0 / 16777216.0);
+        const double u2 = ((double)(draw3(seed, species, (uint64_t)p, 4) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+        const double a2 = 2.0 * kPi * (double)(draw3(seed, species, (uint64_t)p, 5) >> 40) * (1.0 / 16777216.0);
+        const double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u2));
+        out.ux[p] = (float)(uth * r1 * cos(a1));
+        out.uy[p] = (float)(uth * r1 * sin(a1));
+        out.uz[p] = (float)(uth * r2 * cos(a2));
+    }
+    (void)nx;
+    (void)ny;
+}
+
+void launch_init_particles3(Ctx& c, int s, cudaStream_t st)
+{
+    Species& S = c.sp[s];
+    if (S.n == 0) return;
+    int64_t g = (S.n + 255) / 256;
+    if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
+    const int pos_species = (s == 1 && c.cfg.ppc_electron == c.cfg.ppc_ion) ? 0 : s;
+    k_init3<<<(int)g, 256, 0, st>>>(S.b, S.n, S.ppc, c.nx, c.ny, s, pos_species, S.uth, c.cfg.seed);
+}
+
+}  // namespace gbpic

@@ -33,6 +33,7 @@ typedef unsigned long long u64;
 struct SpeciesBuf {
     int32_t* cell;
     float* fx;
+    float* fy;           // 3D only (NULL in 2D)
     float* fz;
     float* ux;
     float* uy;
@@ -78,6 +79,7 @@ struct Ctx {
     int nsm;
     // derived
     double dt, w, r0, D, rho_scale, E0, omega, t_ant;
+    int32_t dims, ny, nty;  // 2 or 3; cells and tiles along y (1 in 2D)
     int32_t nx, nz, T, ntx, ntz, ntiles, W, k_ant;
     size_t nn;            // (nz + 1) * nx
     int32_t nkeys;        // ntiles * T * T
@@ -147,6 +149,12 @@ AntennaParams make_antenna_params(const Ctx& c);
 void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
                                 int full, int maxW, int nsm, cudaStream_t st);
 size_t particle_smem_bytes(int W);
+void launch_particle_step3(Ctx& c, cudaStream_t st);
+void launch_deposit_density3(Ctx& c, u64* out, cudaStream_t st);
+void launch_pair_force3(Ctx& c, float* out, cudaStream_t st);
+void launch_fields3(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches);
+void launch_energy3(Ctx& c, cudaStream_t st, double* host_out5);
+void launch_init_particles3(Ctx& c, int s, cudaStream_t st);
 int tile_window(int T);
 void launch_energy(Ctx& c, cudaStream_t st, double* host_out5);
 StepArgs make_step_args(Ctx& c);

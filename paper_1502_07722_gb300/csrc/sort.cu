@@ -1,7 +1,8 @@
 // Cell sort of one species into tiles (counting sort by a tile-major cell key):
 // count per key -> exclusive scan -> scatter into the second buffer -> swap.
-// The key of cell (i, k) is tile * T^2 + (k mod T) * T + (i mod T), tile = (k / T) * ntx + i / T,
-// so the particles of a tile are contiguous and, within a tile, ordered by cell.
+// The key of cell (i, k) is tile * T^2 + (k mod T) * T + (i mod T), tile = (k / T) * ntx + i / T
+// (in 3D likewise with T^3 cells per tile), so the particles of a tile are contiguous and, within
+// a tile, ordered by cell.
 // The order of particles inside one cell is not fixed (atomic cursors); nothing downstream
 // depends on it because every deposit is an exact integer sum.
 #include "pic_internal.cuh"
@@ -11,22 +12,33 @@ namespace gbpic {
 constexpr int kScanBlock = 1024;
 constexpr int kScanItems = 2 * kScanBlock;
 
-__device__ __forceinline__ int cell_key(int cell, int nx, int T, int ntx)
+struct KeyGeo {
+    int nx, ny, T, ntx, nty, dims;
+};
+
+// 2D: cell = k*nx + i; 3D: cell = (k*ny + j)*nx + i. Tiles of T^dims cells, tile-major.
+__device__ __forceinline__ int cell_key(int cell, const KeyGeo& g)
 {
-    const int k = cell / nx, i = cell - k * nx;
-    const int tz = k / T, tx = i / T;
-    return (tz * ntx + tx) * T * T + (k - tz * T) * T + (i - tx * T);
+    const int i = cell % g.nx, q = cell / g.nx;
+    if (g.dims == 2) {
+        const int k = q, tz = k / g.T, tx = i / g.T;
+        return (tz * g.ntx + tx) * g.T * g.T + (k - tz * g.T) * g.T + (i - tx * g.T);
+    }
+    const int j = q % g.ny, k = q / g.ny;
+    const int tx = i / g.T, ty = j / g.T, tz = k / g.T;
+    const int tile = (tz * g.nty + ty) * g.ntx + tx;
+    return ((tile * g.T + (k - tz * g.T)) * g.T + (j - ty * g.T)) * g.T + (i - tx * g.T);
 }
 
 // Particles arrive nearly sorted (the previous sort plus a few steps of drift), so the lanes of
 // a warp usually share one or two keys: one atomic per distinct key per warp.
-__global__ void k_count(const int32_t* __restrict__ cell, int64_t n, int nx, int T, int ntx, int32_t* count)
+__global__ void k_count(const int32_t* __restrict__ cell, int64_t n, KeyGeo kg, int32_t* count)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nround = (n + 31) & ~(int64_t)31;     // whole warps stay in the loop together
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nround; p += stride) {
         const bool valid = p < n;
-        const int key = valid ? cell_key(cell[p], nx, T, ntx) : -1;
+        const int key = valid ? cell_key(cell[p], kg) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
         if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(count + key, __popc(peers));
@@ -112,7 +124,7 @@ __global__ void k_tile_starts(const int32_t* __restrict__ off, int ntiles, int T
     if (t <= ntiles) tile_start[t] = off[(size_t)t * TT];
 }
 
-__global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, int nx, int T, int ntx, int32_t* cursor)
+__global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, KeyGeo kg, int32_t* cursor)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nround = (n + 31) & ~(int64_t)31;
@@ -120,7 +132,7 @@ __global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, int nx, int
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nround; p += stride) {
         const bool valid = p < n;
         const int c = valid ? src.cell[p] : 0;
-        const int key = valid ? cell_key(c, nx, T, ntx) : -1;
+        const int key = valid ? cell_key(c, kg) : -1;
         // one cursor atomic per distinct key in the warp; lanes take consecutive slots
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
@@ -131,6 +143,7 @@ __global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, int nx, int
         const int q = base + __popc(peers & ((1u << lane) - 1u));
         dst.cell[q] = c;
         dst.fx[q] = src.fx[p];
+        if (kg.dims == 3) dst.fy[q] = src.fy[p];
         dst.fz[q] = src.fz[p];
         dst.ux[q] = src.ux[p];
         dst.uy[q] = src.uy[p];
@@ -143,21 +156,22 @@ __global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, int nx, int
 void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* launches)
 {
     Species& S = c.sp[s];
-    const int TT = c.T * c.T;
+    const int TT = c.dims == 3 ? c.T * c.T * c.T : c.T * c.T;
+    const KeyGeo kg = {c.nx, c.ny, c.T, c.ntx, c.nty, c.dims};
     int64_t g = (S.n + 255) / 256;
     if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
     if (g < 1) g = 1;
     cudaMemsetAsync(c.keys_count, 0, sizeof(int32_t) * (size_t)(c.nkeys + 1), st);
     SpeciesBuf src = from_b ? S.b : S.a;
     SpeciesBuf dst = from_b ? S.a : S.b;
-    if (S.n > 0) k_count<<<(int)g, 256, 0, st>>>(src.cell, S.n, c.nx, c.T, c.ntx, c.keys_count);
+    if (S.n > 0) k_count<<<(int)g, 256, 0, st>>>(src.cell, S.n, kg, c.keys_count);
     const int nb = (c.nkeys + kScanItems - 1) / kScanItems;
     k_scan_block<<<nb, kScanBlock, 0, st>>>(c.keys_count, c.keys_off, c.scan_tmp, c.nkeys);
     k_scan_sums<<<1, kScanBlock, 0, st>>>(c.scan_tmp, nb);
     // the cursor reuses the count array (counts are consumed by the scan)
     k_scan_add<<<(c.nkeys + 255) / 256, 256, 0, st>>>(c.keys_off, c.scan_tmp, c.nkeys, c.keys_count, (int32_t)S.n);
     k_tile_starts<<<(c.ntiles + 1 + 255) / 256, 256, 0, st>>>(c.keys_off, c.ntiles, TT, S.tile_start);
-    if (S.n > 0) k_scatter<<<(int)g, 256, 0, st>>>(src, dst, S.n, c.nx, c.T, c.ntx, c.keys_count);
+    if (S.n > 0) k_scatter<<<(int)g, 256, 0, st>>>(src, dst, S.n, kg, c.keys_count);
     if (!from_b) {
         SpeciesBuf t = S.a;
         S.a = S.b;

@@ -29,8 +29,9 @@ COPPER = dict(
     tau_fwhm=30e-15,
 )
 
-# dt of the 2D copper grid: 0.95 * 10 nm / (c sqrt 2)
+# dt of the copper grids: 0.95 * 10 nm / (c sqrt 2) in 2D, / (c sqrt 3) in 3D
 DT_2D = 2.2407216199121996e-17
+DT_3D = 1.829541541469147e-17
 
 WORKLOADS = {
     # 64 x 64 cells, slab in the lower half, 8 + 8 ppc, plane wave 1e13 W/cm^2, 200 steps
@@ -46,6 +47,13 @@ WORKLOADS = {
     # 512 x 512 cells, 16 + 16 ppc, 2 um focus at 3e13 W/cm^2, 200 steps
     "diff512": dict(COPPER, nx=512, nz=512, slab_k=256, ppc_ion=16, ppc_electron=16, laser_profile=2,
                     I0=3e17, w0=2e-6, t_peak=100 * DT_2D, seed=5, steps=200),
+    # 3D: 384 x 384 x 256 cells, slab in the lower 128 z-cells, 8 + 8 ppc (302 M particles),
+    # Gaussian focus 1.5 um waist at 1e14 W/cm^2, 500 steps
+    "3d": dict(COPPER, dims=3, nx=384, ny=384, nz=256, slab_k=128, ppc_ion=8, ppc_electron=8, laser_profile=2,
+               I0=1e18, w0=1.5e-6, t_peak=250 * DT_3D, seed=3, steps=500),
+    # 3D at an eighth of the size (37.7 M particles), for profiling captures
+    "small3d": dict(COPPER, dims=3, nx=192, ny=192, nz=128, slab_k=64, ppc_ion=8, ppc_electron=8, laser_profile=2,
+                    I0=1e18, w0=1.5e-6, t_peak=250 * DT_3D, seed=4, steps=500),
     # atomic-transport stage: neutral Cu, 12 fs steps, hot slab (pair force only, no fields)
     "transport": dict(COPPER, nx=64, nz=64, slab_k=32, ppc_ion=16, ppc_electron=0, mode=1,
                       ion_charge=0.0, T_ion_K=3000.0, dt_override=12e-15, laser_profile=0,

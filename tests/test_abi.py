@@ -44,6 +44,13 @@ def test_workspace_size_and_validation(lib):
         with pytest.raises(gb.PicError) as e:
             gb.pic_workspace_size(gb.make_config(workload("tiny"), **bad))
         assert e.value.code == gb.PIC_EINVAL
+    # 3D needs ny; batches and the allocation-free energy are 2D only
+    c3 = gb.make_config(workload("tiny"), dims=3, ny=32)
+    assert gb.pic_workspace_size(c3) > gb.pic_workspace_size(gb.make_config(workload("tiny")))
+    with pytest.raises(gb.PicError):
+        gb.pic_workspace_size(gb.make_config(workload("tiny"), dims=3, ny=2))
+    with pytest.raises(gb.PicError):
+        gb.pic_workspace_size(gb.make_config(workload("tiny"), dims=4))
     # transport mode: neutral atoms only
     gb.pic_workspace_size(gb.make_config(workload("transport")))
     with pytest.raises(gb.PicError):
@@ -62,7 +69,7 @@ def test_init_rejects_bad_workspace_without_touching_the_gpu(lib):
 
 
 def test_config_struct_layout_matches_header():
-    # 10 int32 + 1 int64 + 17 double + 1 uint64
-    assert ctypes.sizeof(gb.pic_config) == 10 * 4 + 8 + 17 * 8 + 8
+    # 10 int32 + 1 int64 + 17 double + 1 uint64 + 2 int32
+    assert ctypes.sizeof(gb.pic_config) == 10 * 4 + 8 + 17 * 8 + 8 + 2 * 4
     assert gb.pic_config.max_particles.offset == 40
     assert ctypes.sizeof(gb.pic_energy_t) == 6 * 8
