@@ -107,6 +107,11 @@ def lib():
                                               _D, _D, _D, _D, _F, _F, _F, _I64, _I64, _I64]),
         }
         sig.update({
+            "oracle_transport_grad": (None, [vp, ctypes.c_int32, _D, ctypes.c_double, _D]),
+            "oracle_transport_loss": (ctypes.c_double, [vp, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_double,
+                                                        ctypes.c_double]),
+            "oracle_D": (ctypes.c_double, [vp]),
+            "oracle_r0": (ctypes.c_double, [vp]),
             "oracle3_create": (vp, [ctypes.POINTER(OracleConfig3), ctypes.c_int32]),
             "oracle3_free": (None, [vp]),
             "oracle3_num_particles": (ctypes.c_int64, [vp, ctypes.c_int32]),
@@ -263,6 +268,26 @@ class Oracle:
         out = np.empty(5, np.float64)
         lib().oracle_energy(self._s, _p(out, ctypes.c_double))
         return dict(zip(("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair"), out))
+
+    def transport_grad(self, nsteps, cw, kin):
+        """Continuous-deposition transport run of nsteps with the loss sum(cw * n^) + kin * KE and
+        its gradient: returns (L, dL/dD, dL/dr0). Advances the state."""
+        cw = _f64(cw).reshape(-1)
+        out = np.empty(3, np.float64)
+        lib().oracle_transport_grad(self._s, int(nsteps), _p(cw, ctypes.c_double), float(kin), _p(out, ctypes.c_double))
+        return tuple(out)
+
+    def transport_loss(self, nsteps, cw, kin, D, r0):
+        cw = _f64(cw).reshape(-1)
+        return lib().oracle_transport_loss(self._s, int(nsteps), _p(cw, ctypes.c_double), float(kin), float(D), float(r0))
+
+    @property
+    def D(self):
+        return lib().oracle_D(self._s)
+
+    @property
+    def r0(self):
+        return lib().oracle_r0(self._s)
 
     def laser_field(self, x_cells, t):
         return lib().oracle_laser_field(self._s, float(x_cells), float(t))

@@ -1241,3 +1241,255 @@ void oracle3_energy(const ostate3* s, double out[5])
     }
     out[4] = pe * s->w;
 }
+
+/* ======================================================================================== */
+/* Differentiable transport stage (2D, neutral atoms, pair force only) with continuous       */
+/* deposition (no fixed point) and its exact reverse-mode adjoint, in FP64.                 */
+/* Loss L = sum_nodes cw(node) n^(node) at the final step + kin * (total kinetic energy).   */
+/* Gradients with respect to D and r0 (r0 enters the force scale D/r0, Eq. (1)'s r0/dx and  */
+/* the density unit n0 = r0^-3).                                                              */
+/* ======================================================================================== */
+
+/* continuous node density in units of n0, wall rows doubled */
+static void dens_cont(const ostate* s, const double* x, const double* z, int64_t n, double* nh)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    size_t nn = (size_t)nx * (nz + 1);
+    memset(nh, 0, sizeof(double) * nn);
+    double unit = s->w / (s->c.dx * s->c.dx) * pow(s->r0, 3.0);
+    for (int64_t p = 0; p < n; p++) {
+        int64_t i = (int64_t)floor(x[p]), k = (int64_t)floor(z[p]);
+        double fx = x[p] - i, fz = z[p] - k;
+        if (k >= nz) { k = nz - 1; fz = 1.0; }
+        double wx[2] = {1 - fx, fx}, wz[2] = {1 - fz, fz};
+        for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) nh[(size_t)(k + b) * nx + imod(i + a, nx)] += unit * wx[a] * wz[b];
+    }
+    for (int i = 0; i < nx; i++) { nh[i] *= 2.0; nh[(size_t)nz * nx + i] *= 2.0; }
+}
+
+/* bilinear density, gradient and the mixed second derivative at (x, z) from a node array */
+static void gather_cont(const ostate* s, const double* nh, double x, double z, double* n, double* gx, double* gz,
+                        double* gxz, int64_t* ci, int64_t* ck, double* cfx, double* cfz)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    int64_t i = (int64_t)floor(x), k = (int64_t)floor(z);
+    double fx = x - i, fz = z - k;
+    if (k >= nz) { k = nz - 1; fz = 1.0; }
+    double n00 = nh[(size_t)k * nx + imod(i, nx)], n10 = nh[(size_t)k * nx + imod(i + 1, nx)];
+    double n01 = nh[(size_t)(k + 1) * nx + imod(i, nx)], n11 = nh[(size_t)(k + 1) * nx + imod(i + 1, nx)];
+    *n = (1 - fx) * (1 - fz) * n00 + fx * (1 - fz) * n10 + (1 - fx) * fz * n01 + fx * fz * n11;
+    *gx = (1 - fz) * (n10 - n00) + fz * (n11 - n01);
+    *gz = (1 - fx) * (n01 - n00) + fx * (n11 - n10);
+    *gxz = n11 - n01 - n10 + n00;
+    *ci = i; *ck = k; *cfx = fx; *cfz = fz;
+}
+
+/* Force along one axis (N) and its partial derivatives, Eqs. (1)-(3):
+ * F = (D/r0)[U'(a) - U'(b)], a = rbar/(1-h), b = rbar/(1+h), rbar = n^(-1/3),
+ * h = -(1/6)(r0/dx) n^(-4/3) q.  Outputs dF/dn, dF/dq and dF/dr0 at fixed (n, q). */
+static double axis_force_d(double n, double q, double D, double r0, double dx, double* dFdn, double* dFdq, double* dFdr0)
+{
+    *dFdn = *dFdq = *dFdr0 = 0.0;
+    if (!(n > 0.0)) return 0.0;
+    double rbar = pow(n, -1.0 / 3.0);
+    double h = -(1.0 / 6.0) * (r0 / dx) * pow(n, -4.0 / 3.0) * q;
+    double drbar_dn = -(1.0 / 3.0) * pow(n, -4.0 / 3.0);
+    double dh_dn = (2.0 / 9.0) * (r0 / dx) * pow(n, -7.0 / 3.0) * q;
+    double dh_dq = -(1.0 / 6.0) * (r0 / dx) * pow(n, -4.0 / 3.0);
+    double dh_dr0 = h / r0;
+    double fu = D / r0, F = 0.0, dF_drbar = 0.0, dF_dh = 0.0;
+    if (1.0 - h > 0.0) {
+        double a = rbar / (1.0 - h);
+        double up = oracle_lj_dU(a), upp = (156.0 * pow(a, -14.0) - 84.0 * pow(a, -8.0));
+        F += fu * up;
+        dF_drbar += fu * upp / (1.0 - h);
+        dF_dh += fu * upp * rbar / ((1.0 - h) * (1.0 - h));
+    }
+    if (1.0 + h > 0.0) {
+        double b = rbar / (1.0 + h);
+        double up = oracle_lj_dU(b), upp = (156.0 * pow(b, -14.0) - 84.0 * pow(b, -8.0));
+        F -= fu * up;
+        dF_drbar -= fu * upp / (1.0 + h);
+        dF_dh += fu * upp * rbar / ((1.0 + h) * (1.0 + h));
+    }
+    *dFdn = dF_drbar * drbar_dn + dF_dh * dh_dn;
+    *dFdq = dF_dh * dh_dq;
+    *dFdr0 = -F / r0 + dF_dh * dh_dr0;
+    return F;
+}
+
+/* one forward transport step with continuous deposition; positions in cells, u = gamma v / c */
+static void transport_step_cont(ostate* s, double* x, double* z, double* ux, double* uy, double* uz, int64_t n,
+                                double* nh, int* refl)
+{
+    dens_cont(s, x, z, n, nh);
+    double kick = s->dt / (s->m[0] * O_C);
+    for (int64_t p = 0; p < n; p++) {
+        double nn_, gx, gz, gxz, fx, fz; int64_t i, k;
+        gather_cont(s, nh, x[p], z[p], &nn_, &gx, &gz, &gxz, &i, &k, &fx, &fz);
+        double d1, d2, d3;
+        double Fx = axis_force_d(nn_, gx, s->D, s->r0, s->c.dx, &d1, &d2, &d3);
+        double Fz = axis_force_d(nn_, gz, s->D, s->r0, s->c.dx, &d1, &d2, &d3);
+        ux[p] += kick * Fx;
+        uz[p] += kick * Fz;
+        double g = sqrt(1.0 + ux[p] * ux[p] + uy[p] * uy[p] + uz[p] * uz[p]);
+        double step = O_C * s->dt / (g * s->c.dx);
+        x[p] += ux[p] * step;
+        z[p] += uz[p] * step;
+        if (x[p] < 0.0) x[p] += s->c.nx;
+        if (x[p] >= s->c.nx) x[p] -= s->c.nx;
+        refl[p] = 0;
+        if (z[p] < 0.0) { z[p] = -z[p]; uz[p] = -uz[p]; refl[p] = 1; }
+        if (z[p] >= s->c.nz) { z[p] = 2.0 * s->c.nz - z[p]; uz[p] = -uz[p]; refl[p] = 1; }
+    }
+}
+
+/* Adds to lx, lz the derivative of sum_nodes lam(node) nh(node) with respect to each particle's
+ * position (the transpose of the deposition), lam in units of 1 / n0. */
+static void deposit_transpose(const ostate* s, const double* lam, const double* x, const double* z, int64_t n,
+                              double* lx, double* lz)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    double unit = s->w / (s->c.dx * s->c.dx) * pow(s->r0, 3.0);
+    for (int64_t p = 0; p < n; p++) {
+        int64_t i = (int64_t)floor(x[p]), k = (int64_t)floor(z[p]);
+        double fx = x[p] - i, fz = z[p] - k;
+        if (k >= nz) { k = nz - 1; fz = 1.0; }
+        double m0 = (k == 0) ? 2.0 : 1.0, m1 = (k + 1 == nz) ? 2.0 : 1.0;
+        double l00 = m0 * lam[(size_t)k * nx + imod(i, nx)], l10 = m0 * lam[(size_t)k * nx + imod(i + 1, nx)];
+        double l01 = m1 * lam[(size_t)(k + 1) * nx + imod(i, nx)], l11 = m1 * lam[(size_t)(k + 1) * nx + imod(i + 1, nx)];
+        lx[p] += unit * ((1 - fz) * (l10 - l00) + fz * (l11 - l01));
+        lz[p] += unit * ((1 - fx) * (l01 - l00) + fx * (l11 - l10));
+    }
+}
+
+/* Forward nsteps from the current state (continuous deposition), loss and its gradient.
+ * cw: node weights of the crater functional ((nz+1)*nx, units 1/n0), kin: weight of the kinetic
+ * energy (1/J). out[0] = L, out[1] = dL/dD (1/J), out[2] = dL/dr0 (1/m). The state is advanced. */
+void oracle_transport_grad(ostate* s, int32_t nsteps, const double* cw, double kin, double* out)
+{
+    int64_t n = s->np[0];
+    int nx = s->c.nx, nz = s->c.nz;
+    size_t nn = (size_t)nx * (nz + 1);
+    double *X = malloc(sizeof(double) * n * (nsteps + 1)), *Z = malloc(sizeof(double) * n * (nsteps + 1));
+    double *UX = malloc(sizeof(double) * n * (nsteps + 1)), *UY = malloc(sizeof(double) * n * (nsteps + 1));
+    double *UZ = malloc(sizeof(double) * n * (nsteps + 1));
+    int* RF = malloc(sizeof(int) * (size_t)n * (nsteps > 0 ? nsteps : 1));
+    double* nh = malloc(sizeof(double) * nn);
+    memcpy(X, s->x[0], sizeof(double) * n); memcpy(Z, s->z[0], sizeof(double) * n);
+    memcpy(UX, s->ux[0], sizeof(double) * n); memcpy(UY, s->uy[0], sizeof(double) * n); memcpy(UZ, s->uz[0], sizeof(double) * n);
+    for (int t = 0; t < nsteps; t++) {
+        double *x = X + (size_t)(t + 1) * n, *z = Z + (size_t)(t + 1) * n;
+        double *ux = UX + (size_t)(t + 1) * n, *uy = UY + (size_t)(t + 1) * n, *uz = UZ + (size_t)(t + 1) * n;
+        memcpy(x, X + (size_t)t * n, sizeof(double) * n); memcpy(z, Z + (size_t)t * n, sizeof(double) * n);
+        memcpy(ux, UX + (size_t)t * n, sizeof(double) * n); memcpy(uy, UY + (size_t)t * n, sizeof(double) * n);
+        memcpy(uz, UZ + (size_t)t * n, sizeof(double) * n);
+        transport_step_cont(s, x, z, ux, uy, uz, n, nh, RF + (size_t)t * n);
+    }
+    /* loss */
+    double *xN = X + (size_t)nsteps * n, *zN = Z + (size_t)nsteps * n;
+    double *uxN = UX + (size_t)nsteps * n, *uyN = UY + (size_t)nsteps * n, *uzN = UZ + (size_t)nsteps * n;
+    dens_cont(s, xN, zN, n, nh);
+    double L = 0.0;
+    for (size_t c = 0; c < nn; c++) L += cw[c] * nh[c];
+    double mc2w = s->w * s->m[0] * O_C * O_C, ke = 0.0;
+    for (int64_t p = 0; p < n; p++) {
+        double u2 = uxN[p] * uxN[p] + uyN[p] * uyN[p] + uzN[p] * uzN[p];
+        ke += mc2w * u2 / (sqrt(1.0 + u2) + 1.0);
+    }
+    L += kin * ke;
+    /* adjoint seeds: lambda_x = transpose of the final deposition; lambda_u = kin * w m c^2 u / gamma */
+    double *lx = calloc(n, sizeof(double)), *lz = calloc(n, sizeof(double));
+    double *lux = calloc(n, sizeof(double)), *luy = calloc(n, sizeof(double)), *luz = calloc(n, sizeof(double));
+    double* lam = malloc(sizeof(double) * nn);
+    deposit_transpose(s, cw, xN, zN, n, lx, lz);
+    /* The r0 dependence of the final density (n0 = r0^-3 scales every node): dn^/dr0 = 3 n^/r0 */
+    double gD = 0.0, gr0 = 0.0;
+    for (size_t c = 0; c < nn; c++) gr0 += cw[c] * 3.0 * nh[c] / s->r0;
+    for (int64_t p = 0; p < n; p++) {
+        double u2 = uxN[p] * uxN[p] + uyN[p] * uyN[p] + uzN[p] * uzN[p], g = sqrt(1.0 + u2);
+        lux[p] = kin * mc2w * uxN[p] / g; luy[p] = kin * mc2w * uyN[p] / g; luz[p] = kin * mc2w * uzN[p] / g;
+    }
+    double kick = s->dt / (s->m[0] * O_C);
+    for (int t = nsteps - 1; t >= 0; t--) {
+        double *x0 = X + (size_t)t * n, *z0 = Z + (size_t)t * n;
+        double *ux1 = UX + (size_t)(t + 1) * n, *uy1 = UY + (size_t)(t + 1) * n, *uz1 = UZ + (size_t)(t + 1) * n;
+        int* rf = RF + (size_t)t * n;
+        dens_cont(s, x0, z0, n, nh);
+        memset(lam, 0, sizeof(double) * nn);
+        for (int64_t p = 0; p < n; p++) {
+            /* position update: x1 = x0 + c dt u / (gamma dx) (then the wall mirror) */
+            double lzp = lz[p], luzp = luz[p];
+            double ux = ux1[p], uy = uy1[p], uz = uz1[p];
+            if (rf[p]) { lzp = -lzp; luzp = -luzp; uz = -uz; }   /* undo the mirror: z1 = -z', u_z1 = -u_z' */
+            double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz), cs = O_C * s->dt / (s->c.dx * g);
+            double lu[3] = {lux[p], luy[p], luzp};
+            double u[3] = {ux, uy, uz}, lp[3] = {lx[p], 0.0, lzp};
+            double udl = (u[0] * lp[0] + u[2] * lp[2]) / (g * g);
+            for (int d = 0; d < 3; d++) lu[d] += cs * (lp[d] - u[d] * udl);
+            /* kick: u' = u + kick F(x0): lambda_u unchanged backwards, lambda_F = kick lambda_u */
+            double nn_, gx, gz, gxz, fx, fz; int64_t i, k;
+            gather_cont(s, nh, x0[p], z0[p], &nn_, &gx, &gz, &gxz, &i, &k, &fx, &fz);
+            double dxn, dxq, dxr, dzn, dzq, dzr;
+            double Fx = axis_force_d(nn_, gx, s->D, s->r0, s->c.dx, &dxn, &dxq, &dxr);
+            double Fz = axis_force_d(nn_, gz, s->D, s->r0, s->c.dx, &dzn, &dzq, &dzr);
+            double lFx = kick * lu[0], lFz = kick * lu[2];
+            gD += (lFx * Fx + lFz * Fz) / s->D;
+            /* r0: explicit part, and the n0 = r0^-3 scaling of n and q (both proportional to r0^3) */
+            gr0 += lFx * (dxr + dxn * 3.0 * nn_ / s->r0 + dxq * 3.0 * gx / s->r0);
+            gr0 += lFz * (dzr + dzn * 3.0 * nn_ / s->r0 + dzq * 3.0 * gz / s->r0);
+            double ln = lFx * dxn + lFz * dzn, lqx = lFx * dxq, lqz = lFz * dzq;
+            /* gather: n = bilinear, q_x = d/dxi, q_z = d/dzeta; their position derivatives */
+            lx[p] = lp[0] + ln * gx + lqx * 0.0 + lqz * gxz;
+            lz[p] = lp[2] + ln * gz + lqx * gxz + lqz * 0.0;
+            lux[p] = lu[0]; luy[p] = lu[1]; luz[p] = lu[2];
+            /* transpose of the gather onto the nodes */
+            double w00 = (1 - fx) * (1 - fz), w10 = fx * (1 - fz), w01 = (1 - fx) * fz, w11 = fx * fz;
+            size_t c00 = (size_t)k * nx + imod(i, nx), c10 = (size_t)k * nx + imod(i + 1, nx);
+            size_t c01 = (size_t)(k + 1) * nx + imod(i, nx), c11 = (size_t)(k + 1) * nx + imod(i + 1, nx);
+            lam[c00] += ln * w00 + lqx * (-(1 - fz)) + lqz * (-(1 - fx));
+            lam[c10] += ln * w10 + lqx * (1 - fz) + lqz * (-fx);
+            lam[c01] += ln * w01 + lqx * (-fz) + lqz * (1 - fx);
+            lam[c11] += ln * w11 + lqx * fz + lqz * fx;
+        }
+        /* the nodes depend on every particle's position: transpose of the deposition */
+        deposit_transpose(s, lam, x0, z0, n, lx, lz);
+        /* and on r0 through n0 = r0^-3 (already counted in the force terms above) */
+    }
+    out[0] = L; out[1] = gD; out[2] = gr0;
+    /* leave the final state in the context */
+    memcpy(s->x[0], xN, sizeof(double) * n); memcpy(s->z[0], zN, sizeof(double) * n);
+    memcpy(s->ux[0], uxN, sizeof(double) * n); memcpy(s->uy[0], uyN, sizeof(double) * n); memcpy(s->uz[0], uzN, sizeof(double) * n);
+    free(X); free(Z); free(UX); free(UY); free(UZ); free(RF); free(nh); free(lx); free(lz); free(lux); free(luy); free(luz); free(lam);
+}
+
+/* Loss of the same functional after nsteps forward (continuous deposition), no gradient: for
+ * finite differences. D and r0 override the configuration's values for this call. */
+double oracle_transport_loss(ostate* s, int32_t nsteps, const double* cw, double kin, double D_J, double r0_m)
+{
+    int64_t n = s->np[0];
+    double Dsave = s->D, r0save = s->r0;
+    s->D = D_J; s->r0 = r0_m;
+    double *x = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    double *ux = malloc(sizeof(double) * n), *uy = malloc(sizeof(double) * n), *uz = malloc(sizeof(double) * n);
+    int* rf = malloc(sizeof(int) * (n ? n : 1));
+    memcpy(x, s->x[0], sizeof(double) * n); memcpy(z, s->z[0], sizeof(double) * n);
+    memcpy(ux, s->ux[0], sizeof(double) * n); memcpy(uy, s->uy[0], sizeof(double) * n); memcpy(uz, s->uz[0], sizeof(double) * n);
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    double* nh = malloc(sizeof(double) * nn);
+    for (int t = 0; t < nsteps; t++) transport_step_cont(s, x, z, ux, uy, uz, n, nh, rf);
+    dens_cont(s, x, z, n, nh);
+    double L = 0.0, mc2w = s->w * s->m[0] * O_C * O_C;
+    for (size_t c = 0; c < nn; c++) L += cw[c] * nh[c];
+    for (int64_t p = 0; p < n; p++) {
+        double u2 = ux[p] * ux[p] + uy[p] * uy[p] + uz[p] * uz[p];
+        L += kin * mc2w * u2 / (sqrt(1.0 + u2) + 1.0);
+    }
+    s->D = Dsave; s->r0 = r0save;
+    free(x); free(z); free(ux); free(uy); free(uz); free(rf); free(nh);
+    return L;
+}
+
+double oracle_D(const ostate* s) { return s->D; }
+double oracle_r0(const ostate* s) { return s->r0; }
