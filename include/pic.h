@@ -243,6 +243,36 @@ typedef struct pic_state_view {
  * particle counts above 2^31 - 1, grids outside 3 <= nx, 4 <= nz < 32768, and missing pointers. */
 PIC_API int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* in, double* dev_out5, void* stream);
 
+/* ---- checkpoint / resume ------------------------------------------------------------------
+ * A checkpoint is a device buffer (caller-owned, 256-byte aligned, pic_checkpoint_size bytes) with
+ * the particles, tile offsets, fields, node density, current and step counter of a context.
+ * Restoring it into the same context resumes bit for bit: same grids, same particle set (a cell sort
+ * after the restore may order the particles of one cell differently). */
+PIC_API int pic_checkpoint_size(pic_ctx* ctx, size_t* bytes);
+PIC_API int pic_checkpoint_save(pic_ctx* ctx, void* dev_buf);
+PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
+
+/* ---- differentiable transport stage (2D, PIC_MODE_TRANSPORT, sort_every = 0, pot_mode 0) ------
+ * Gradients of L = sum_nodes w(node) n(node)/n0 (at the final state) + kin * (total kinetic energy)
+ * with respect to the pair-potential parameters D (J) and r0 (m), by hand-written adjoint kernels
+ * (FP64) of the transport step: node density -> Eqs. (1)-(3) force -> kick -> move. The fixed-point
+ * deposition is differentiated as the continuous linear shape. The paper has no adjoint; the
+ * stage and the parameters are the paper's (the transport simulation with the pair potential).
+ *
+ * pic_node_functional: *host_out = sum_nodes w n/n0 at the current state (w: device double
+ *   (nz+1)*nx, e.g. a crater-depth weighting).
+ * pic_adjoint_seed: at the final state, initialise the adjoints: lam_u = kin * w m c^2 u / gamma,
+ *   lam_pos = d/dx of sum w n/n0; *host_dLdr0 receives the r0 derivative of the density unit in
+ *   the functional (add it to the r0 gradient). lam_pos: device double[2 n] (x, z per atom),
+ *   lam_u: double[3 n], lam_nodes: double[(nz+1)*nx] scratch.
+ * pic_adjoint_step: with the context at the state x^t, u^t of step t (restore it from a
+ *   checkpoint), map the adjoints of step t+1 to step t in place and add dL/dD, dL/dr0 of this
+ *   step to dev_grads (device double[2]). Returns PIC_ESTATE outside the supported mode. */
+PIC_API int pic_node_functional(pic_ctx* ctx, const double* dev_weights, double* host_out);
+PIC_API int pic_adjoint_seed(pic_ctx* ctx, double kin, const double* dev_weights, double* lam_pos, double* lam_u,
+                             double* lam_nodes, double* host_dLdr0);
+PIC_API int pic_adjoint_step(pic_ctx* ctx, double* lam_pos, double* lam_u, double* lam_nodes, double* dev_grads);
+
 /* Static text for a return code. */
 PIC_API const char* pic_strerror(int code);
 

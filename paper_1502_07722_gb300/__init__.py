@@ -85,6 +85,12 @@ _SIGNATURES = {
     "pic_batch_set_timing": (ctypes.c_int, [_VP, _I32]),
     "pic_batch_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "pic_batch_free": (None, [_VP]),
+    "pic_checkpoint_size": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_checkpoint_save": (ctypes.c_int, [_VP, _VP]),
+    "pic_checkpoint_restore": (ctypes.c_int, [_VP, _VP]),
+    "pic_node_functional": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
+    "pic_adjoint_seed": (ctypes.c_int, [_VP, ctypes.c_double, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
+    "pic_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
 }
 
 _lib = None
@@ -260,6 +266,38 @@ def pic_batch_free(b):
     load_library().pic_batch_free(b)
 
 
+def pic_checkpoint_size(h) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().pic_checkpoint_size(h, ctypes.byref(n)), "pic_checkpoint_size")
+    return n.value
+
+
+def pic_checkpoint_save(h, dev_ptr):
+    _check(load_library().pic_checkpoint_save(h, dev_ptr), "pic_checkpoint_save")
+
+
+def pic_checkpoint_restore(h, dev_ptr):
+    _check(load_library().pic_checkpoint_restore(h, dev_ptr), "pic_checkpoint_restore")
+
+
+def pic_node_functional(h, dev_weights_ptr) -> float:
+    v = ctypes.c_double()
+    _check(load_library().pic_node_functional(h, dev_weights_ptr, ctypes.byref(v)), "pic_node_functional")
+    return v.value
+
+
+def pic_adjoint_seed(h, kin, dev_weights_ptr, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr) -> float:
+    v = ctypes.c_double()
+    _check(load_library().pic_adjoint_seed(h, float(kin), dev_weights_ptr, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr,
+                                           ctypes.byref(v)), "pic_adjoint_seed")
+    return v.value
+
+
+def pic_adjoint_step(h, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr, dev_grads_ptr):
+    _check(load_library().pic_adjoint_step(h, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr, dev_grads_ptr),
+           "pic_adjoint_step")
+
+
 # ---- convenience wrapper: torch owns the workspace and the stream -----------------------------
 
 class Simulation:
@@ -304,6 +342,16 @@ class Simulation:
 
     def sort(self):
         pic_sort(self.h)
+
+    def checkpoint(self, out=None):
+        """Save the whole state into a device buffer (allocated when not given) and return it."""
+        if out is None:
+            out = self.torch.empty(pic_checkpoint_size(self.h), dtype=self.torch.uint8, device="cuda")
+        pic_checkpoint_save(self.h, out.data_ptr())
+        return out
+
+    def restore(self, buf):
+        pic_checkpoint_restore(self.h, buf.data_ptr())
 
     def _shape(self):
         return (self.nz + 1, self.ny, self.nx) if self.dims == 3 else (self.nz + 1, self.nx)

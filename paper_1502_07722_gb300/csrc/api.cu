@@ -619,6 +619,158 @@ int pic_get_timing(pic_ctx* h, double ms[3], int64_t n[4])
     return PIC_OK;
 }
 
+// ---- checkpoint / resume ---------------------------------------------------------------------
+
+namespace {
+
+struct CkptHeader {
+    int64_t magic, step, n[2];
+    int32_t steps_since_sort, nsp;
+};
+constexpr int64_t kCkptMagic = 0x504943434b505431LL;
+
+size_t ckpt_layout(const Ctx& c, size_t* off_sp, size_t* off_tiles, size_t* off_f, size_t* off_rho, size_t* off_j)
+{
+    size_t t = align256(sizeof(CkptHeader));
+    const int arrays = c.dims == 3 ? 7 : 6;
+    for (int s = 0; s < 2; s++) {
+        off_sp[s] = t;
+        t += arrays * align256(4 * (size_t)(c.sp[s].cap > 0 ? c.sp[s].cap : 1));
+        off_tiles[s] = t;
+        t += align256(4 * (size_t)(c.ntiles + 1));
+    }
+    *off_f = t;
+    t += 6 * align256(4 * c.nn);
+    *off_rho = t;
+    t += align256(8 * c.nn);
+    *off_j = t;
+    t += 3 * align256(8 * c.nn);
+    return t;
+}
+
+int ckpt_copy(pic_ctx* h, char* buf, bool save)
+{
+    Ctx& c = h->c;
+    size_t osp[2], otl[2], of, orho, oj;
+    ckpt_layout(c, osp, otl, &of, &orho, &oj);
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    auto cp = [&](void* dev, size_t off, size_t bytes) -> cudaError_t {
+        return save ? cudaMemcpyAsync(buf + off, dev, bytes, k, c.stream) : cudaMemcpyAsync(dev, buf + off, bytes, k, c.stream);
+    };
+    for (int s = 0; s < c.nsp; s++) {
+        Species& S = c.sp[s];
+        const size_t b = 4 * (size_t)S.n, slot = align256(4 * (size_t)S.cap);
+        void* arr[7] = {S.a.cell, S.a.fx, S.a.fz, S.a.ux, S.a.uy, S.a.uz, S.a.fy};
+        const int arrays = c.dims == 3 ? 7 : 6;
+        for (int q = 0; q < arrays; q++)
+            if (b) CK(cp(arr[q], osp[s] + q * slot, b));
+        CK(cp(S.tile_start, otl[s], 4 * (size_t)(c.ntiles + 1)));
+    }
+    for (int q = 0; q < 6; q++) CK(cp(c.F[q], of + q * align256(4 * c.nn), 4 * c.nn));
+    CK(cp(c.rho[c.cur], orho, 8 * c.nn));
+    for (int q = 0; q < 3; q++) CK(cp(c.J[q], oj + q * align256(8 * c.nn), 8 * c.nn));
+    return PIC_OK;
+}
+
+}  // namespace
+
+int pic_checkpoint_size(pic_ctx* h, size_t* bytes)
+{
+    if (!h || !bytes) return PIC_EINVAL;
+    size_t osp[2], otl[2], of, orho, oj;
+    *bytes = ckpt_layout(h->c, osp, otl, &of, &orho, &oj);
+    return PIC_OK;
+}
+
+int pic_checkpoint_save(pic_ctx* h, void* dev_buf)
+{
+    if (!h || !dev_buf || ((uintptr_t)dev_buf & 255)) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.sticky) return c.sticky;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.magic = kCkptMagic;
+    hd.step = c.step;
+    hd.n[0] = c.sp[0].n;
+    hd.n[1] = c.nsp > 1 ? c.sp[1].n : 0;
+    hd.steps_since_sort = c.steps_since_sort;
+    hd.nsp = c.nsp;
+    CK(cudaMemcpyAsync(dev_buf, &hd, sizeof(hd), cudaMemcpyHostToDevice, c.stream));
+    int r = ckpt_copy(h, (char*)dev_buf, true);
+    if (r) return r;
+    CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_checkpoint_restore(pic_ctx* h, const void* dev_buf)
+{
+    if (!h || !dev_buf || ((uintptr_t)dev_buf & 255)) return PIC_EINVAL;
+    Ctx& c = h->c;
+    CkptHeader hd;
+    CK(cudaMemcpyAsync(&hd, dev_buf, sizeof(hd), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (hd.magic != kCkptMagic || hd.nsp != c.nsp) return PIC_EINVAL;
+    for (int s = 0; s < c.nsp; s++)
+        if (hd.n[s] < 0 || hd.n[s] > c.sp[s].cap) return PIC_EINVAL;
+    for (int s = 0; s < c.nsp; s++) c.sp[s].n = hd.n[s];
+    int r = ckpt_copy(h, (char*)const_cast<void*>(dev_buf), false);
+    if (r) return r;
+    c.step = hd.step;
+    c.steps_since_sort = hd.steps_since_sort;
+    CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+// ---- differentiable transport stage -------------------------------------------------------
+
+static int adjoint_ok(const Ctx& c)
+{
+    if (c.sticky) return c.sticky;
+    if (c.dims != 2 || c.cfg.mode != PIC_MODE_TRANSPORT || c.cfg.sort_every != 0 || c.cfg.pot_mode != 0)
+        return PIC_ESTATE;
+    return PIC_OK;
+}
+
+int pic_node_functional(pic_ctx* h, const double* dev_weights, double* host_out)
+{
+    if (!h || !dev_weights || !host_out) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.dims != 2) return PIC_ESTATE;
+    double* tmp = c.red_out + 7;
+    launch_node_functional(c, dev_weights, tmp, c.stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, tmp, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_adjoint_seed(pic_ctx* h, double kin, const double* dev_weights, double* lam_pos, double* lam_u,
+                     double* lam_nodes, double* host_dLdr0)
+{
+    if (!h || !dev_weights || !lam_pos || !lam_u || !lam_nodes || !host_dLdr0) return PIC_EINVAL;
+    Ctx& c = h->c;
+    int r = adjoint_ok(c);
+    if (r) return r;
+    double* tmp = c.red_out + 6;
+    CK(cudaMemsetAsync(tmp, 0, sizeof(double), c.stream));
+    launch_adjoint_seed(c, kin, dev_weights, lam_pos, lam_u, lam_nodes, tmp, c.stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_dLdr0, tmp, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return PIC_OK;
+}
+
+int pic_adjoint_step(pic_ctx* h, double* lam_pos, double* lam_u, double* lam_nodes, double* dev_grads)
+{
+    if (!h || !lam_pos || !lam_u || !lam_nodes || !dev_grads) return PIC_EINVAL;
+    Ctx& c = h->c;
+    int r = adjoint_ok(c);
+    if (r) return r;
+    launch_adjoint_step(c, lam_pos, lam_u, lam_nodes, dev_grads, c.stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
 const char* pic_strerror(int code)
 {
     switch (code) {
