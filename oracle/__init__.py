@@ -111,6 +111,12 @@ def lib():
             "oracle_transport_loss": (ctypes.c_double, [vp, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_double,
                                                         ctypes.c_double]),
             "oracle_D": (ctypes.c_double, [vp]),
+            "oracle_E0": (ctypes.c_double, [vp]),
+            "oracle_full_grad": (None, [vp, ctypes.c_int32, _D, ctypes.c_double, _D]),
+            "oracle_full_loss": (ctypes.c_double, [vp, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_double]),
+            "oracle_maxwell_cont": (None, [vp, _D, _D, ctypes.c_double, ctypes.c_int64]),
+            "oracle_maxwell_cont_T": (None, [vp, _D, _D, ctypes.c_int64, _D]),
             "oracle_r0": (ctypes.c_double, [vp]),
             "oracle3_create": (vp, [ctypes.POINTER(OracleConfig3), ctypes.c_int32]),
             "oracle3_free": (None, [vp]),
@@ -280,6 +286,41 @@ class Oracle:
     def transport_loss(self, nsteps, cw, kin, D, r0):
         cw = _f64(cw).reshape(-1)
         return lib().oracle_transport_loss(self._s, int(nsteps), _p(cw, ctypes.c_double), float(kin), float(D), float(r0))
+
+    def full_grad(self, nsteps, cw, kin):
+        """Continuous-deposition full cycle (ions, electrons, fields, laser) of nsteps from the
+        current state with the loss sum(cw * n^) + kin * (kinetic energy of all species) and its
+        gradient: returns (L, dL/dD, dL/dr0, dL/dI0). The state is left unchanged."""
+        cw = _f64(cw).reshape(-1)
+        out = np.empty(4, np.float64)
+        lib().oracle_full_grad(self._s, int(nsteps), _p(cw, ctypes.c_double), float(kin), _p(out, ctypes.c_double))
+        return tuple(out)
+
+    def full_loss(self, nsteps, cw, kin, D, r0, I0):
+        cw = _f64(cw).reshape(-1)
+        return lib().oracle_full_loss(self._s, int(nsteps), _p(cw, ctypes.c_double), float(kin), float(D), float(r0),
+                                      float(I0))
+
+    def maxwell_cont(self, F, j, E0, step):
+        """One Maxwell update of the continuous cycle: F (6, nz+1, nx) fields, j (3, nz+1, nx) the
+        scaled current dt J / eps0; returns the new fields."""
+        F = _f64(F).copy()
+        j = _f64(j)
+        lib().oracle_maxwell_cont(self._s, _p(F, ctypes.c_double), _p(j, ctypes.c_double), float(E0), int(step))
+        return F
+
+    def maxwell_cont_T(self, lF, step):
+        """Transpose of maxwell_cont: returns (adjoint of the old fields, adjoint of j, dL/dE0)."""
+        lF = _f64(lF).copy()
+        lj = np.zeros((3,) + lF.shape[1:], np.float64)
+        g = np.zeros(1, np.float64)
+        lib().oracle_maxwell_cont_T(self._s, _p(lF, ctypes.c_double), _p(lj, ctypes.c_double), int(step),
+                                    _p(g, ctypes.c_double))
+        return lF, lj, g[0]
+
+    @property
+    def E0(self):
+        return lib().oracle_E0(self._s)
 
     @property
     def D(self):

@@ -1493,3 +1493,659 @@ double oracle_transport_loss(ostate* s, int32_t nsteps, const double* cw, double
 
 double oracle_D(const ostate* s) { return s->D; }
 double oracle_r0(const ostate* s) { return s->r0; }
+
+/* ======================================================================================== */
+/* Differentiable full cycle (2D: ions, electrons, fields, laser) with continuous            */
+/* deposition (linear weights of the unrounded positions, no fixed point) and its exact      */
+/* reverse mode, in FP64.                                                                     */
+/* Loss L = sum_nodes cw(node) n^(node) of the final ion density + kin * (total kinetic       */
+/* energy of all species). Gradients with respect to D, r0 (pair potential, Eqs. 1-3) and    */
+/* the peak intensity I0 (E0 = sqrt(2 I0 / (eps0 c)) scales the antenna source).              */
+/*                                                                                            */
+/* One forward step from the state (X, U, F) at step t:                                       */
+/*   n^ = dens(X_ions); per particle: E, B gathered at x, pair force F_p(n^) for ions,        */
+/*   Boris -> u', x' = x + c dt u'/(gamma' dx), walls; current j = J(x, x', u'_y/gamma');     */
+/*   Maxwell: B += H E (half), E = M(E, B, j) with Mur walls and the antenna, B += H E (half).*/
+/* j is held as the scaled arrays dt J / eps0 that the E update subtracts.                   */
+/* ======================================================================================== */
+
+static double hat_c(double d) { double a = fabs(d); return a < 1.0 ? 1.0 - a : 0.0; }
+static double dhat_c(double d) { return fabs(d) < 1.0 ? (d > 0.0 ? -1.0 : 1.0) : 0.0; }
+
+/* dt J / eps0 per unit of the continuous Esirkepov sums (2 Wx, 6 Wy beta, 2 Wz) */
+static double cur_cx(const ostate* s) { return O_QE * s->w / (2.0 * s->c.dx * O_EPS0); }
+static double cur_cy(const ostate* s) { return O_QE * s->w * O_C * s->dt / (6.0 * s->c.dx * s->c.dx * O_EPS0); }
+
+/* Esirkepov current (linear weights) of one particle moving (x0, z0) -> (x1, z1) (x1 unwrapped
+ * to within half a period of x0, z1 after the wall mirror), with beta_y = by; sg = charge sign. */
+static void cur_cont(const ostate* s, double sg, double x0, double z0, double x1, double z1, double by,
+                     double* jx, double* jy, double* jz)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    double bx = floor(x0 < x1 ? x0 : x1), bz = floor(z0 < z1 ? z0 : z1);
+    double S0x[3], S1x[3], S0z[3], S1z[3];
+    for (int a = 0; a < 3; a++) {
+        S0x[a] = hat_c(x0 - (bx + a)); S1x[a] = hat_c(x1 - (bx + a));
+        S0z[a] = hat_c(z0 - (bz + a)); S1z[a] = hat_c(z1 - (bz + a));
+    }
+    double cx = sg * cur_cx(s), cy = sg * cur_cy(s) * by;
+    int64_t ib = (int64_t)bx, kb = (int64_t)bz;
+    for (int b = 0; b < 3; b++) {
+        int64_t l = kb + b;
+        if (l > nz) continue;                        /* weights there are zero */
+        double acc = 0.0;
+        for (int a = 0; a < 2; a++) {
+            acc -= (S1x[a] - S0x[a]) * (S0z[b] + S1z[b]);
+            jx[(size_t)l * nx + imod(ib + a, nx)] += cx * acc;
+        }
+        for (int a = 0; a < 3; a++)
+            jy[(size_t)l * nx + imod(ib + a, nx)] +=
+                cy * (2 * S0x[a] * S0z[b] + S1x[a] * S0z[b] + S0x[a] * S1z[b] + 2 * S1x[a] * S1z[b]);
+    }
+    for (int a = 0; a < 3; a++) {
+        double acc = 0.0;
+        for (int b = 0; b < 2; b++) {
+            int64_t l = kb + b;
+            acc -= (S1z[b] - S0z[b]) * (S0x[a] + S1x[a]);
+            if (l <= nz) jz[(size_t)l * nx + imod(ib + a, nx)] += cur_cx(s) * sg * acc;
+        }
+    }
+}
+
+/* Transpose of cur_cont: with node adjoints lj (of jx, jy, jz), adds d/d(x0, z0, x1, z1, by) of
+ * sum lj * j into g[0..4]. */
+static void cur_cont_T(const ostate* s, double sg, double x0, double z0, double x1, double z1, double by,
+                       const double* ljx, const double* ljy, const double* ljz, double g[5])
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    double bx = floor(x0 < x1 ? x0 : x1), bz = floor(z0 < z1 ? z0 : z1);
+    int64_t ib = (int64_t)bx, kb = (int64_t)bz;
+    double S0x[3], S1x[3], S0z[3], S1z[3];
+    for (int a = 0; a < 3; a++) {
+        S0x[a] = hat_c(x0 - (bx + a)); S1x[a] = hat_c(x1 - (bx + a));
+        S0z[a] = hat_c(z0 - (bz + a)); S1z[a] = hat_c(z1 - (bz + a));
+    }
+    double Lx[3][3], Ly[3][3], Lz[3][3];              /* [a][b] */
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            int64_t l = kb + b;
+            size_t c = (size_t)l * nx + imod(ib + a, nx);
+            Lx[a][b] = l <= nz ? ljx[c] : 0.0;
+            Ly[a][b] = l <= nz ? ljy[c] : 0.0;
+            Lz[a][b] = l <= nz ? ljz[c] : 0.0;
+        }
+    double cx = sg * cur_cx(s), cy = sg * cur_cy(s);
+    double dS0x[3] = {0, 0, 0}, dS1x[3] = {0, 0, 0}, dS0z[3] = {0, 0, 0}, dS1z[3] = {0, 0, 0};
+    /* x current: value = cx sum_b (S0z+S1z)[b] * (-sum_{a<=1} dSx[a] Rx[a][b]),
+     * Rx[a][b] = sum_{a' = a..1} Lx[a'][b] */
+    for (int b = 0; b < 3; b++) {
+        double Rx1 = Lx[1][b], Rx0 = Lx[0][b] + Lx[1][b];
+        double zsum = S0z[b] + S1z[b];
+        double dx0 = S1x[0] - S0x[0], dx1 = S1x[1] - S0x[1];
+        dS1x[0] += -cx * zsum * Rx0; dS0x[0] += cx * zsum * Rx0;
+        dS1x[1] += -cx * zsum * Rx1; dS0x[1] += cx * zsum * Rx1;
+        double zz = -cx * (dx0 * Rx0 + dx1 * Rx1);
+        dS0z[b] += zz; dS1z[b] += zz;
+    }
+    /* z current */
+    for (int a = 0; a < 3; a++) {
+        double Rz1 = Lz[a][1], Rz0 = Lz[a][0] + Lz[a][1];
+        double xsum = S0x[a] + S1x[a];
+        double dz0 = S1z[0] - S0z[0], dz1 = S1z[1] - S0z[1];
+        dS1z[0] += -cx * xsum * Rz0; dS0z[0] += cx * xsum * Rz0;
+        dS1z[1] += -cx * xsum * Rz1; dS0z[1] += cx * xsum * Rz1;
+        double xx = -cx * (dz0 * Rz0 + dz1 * Rz1);
+        dS0x[a] += xx; dS1x[a] += xx;
+    }
+    /* y current: value = cy by sum Ly w6 */
+    double gby = 0.0;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            double L = Ly[a][b] * cy;
+            gby += L * (2 * S0x[a] * S0z[b] + S1x[a] * S0z[b] + S0x[a] * S1z[b] + 2 * S1x[a] * S1z[b]);
+            dS0x[a] += by * L * (2 * S0z[b] + S1z[b]);
+            dS1x[a] += by * L * (S0z[b] + 2 * S1z[b]);
+            dS0z[b] += by * L * (2 * S0x[a] + S1x[a]);
+            dS1z[b] += by * L * (S0x[a] + 2 * S1x[a]);
+        }
+    for (int a = 0; a < 3; a++) {
+        g[0] += dS0x[a] * dhat_c(x0 - (bx + a));
+        g[1] += dS0z[a] * dhat_c(z0 - (bz + a));
+        g[2] += dS1x[a] * dhat_c(x1 - (bx + a));
+        g[3] += dS1z[a] * dhat_c(z1 - (bz + a));
+    }
+    g[4] += gby;
+}
+
+/* Yee half step of B from E (the arrays of one state) */
+static void hb_cont(const ostate* s, double* F)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    size_t nn = (size_t)nx * (nz + 1);
+    double h = 0.5 * s->dt / s->c.dx;
+    double *Ex = F, *Ey = F + nn, *Ez = F + 2 * nn, *Bx = F + 3 * nn, *By = F + 4 * nn, *Bz = F + 5 * nn;
+    for (int k = 0; k <= nz; k++)
+        for (int i = 0; i < nx; i++) {
+            int ip = (i + 1) % nx;
+            size_t c = (size_t)k * nx + i;
+            if (k < nz) {
+                Bx[c] += h * (Ey[c + nx] - Ey[c]);
+                By[c] += h * ((Ez[(size_t)k * nx + ip] - Ez[c]) - (Ex[c + nx] - Ex[c]));
+            }
+            Bz[c] -= h * (Ey[(size_t)k * nx + ip] - Ey[c]);
+        }
+}
+
+/* transpose of hb_cont: lamE += H^T lamB (lamB unchanged) */
+static void hb_cont_T(const ostate* s, double* lF)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    size_t nn = (size_t)nx * (nz + 1);
+    double h = 0.5 * s->dt / s->c.dx;
+    double *lEx = lF, *lEy = lF + nn, *lEz = lF + 2 * nn, *lBx = lF + 3 * nn, *lBy = lF + 4 * nn, *lBz = lF + 5 * nn;
+    for (int k = 0; k <= nz; k++)
+        for (int i = 0; i < nx; i++) {
+            int ip = (i + 1) % nx;
+            size_t c = (size_t)k * nx + i;
+            if (k < nz) {
+                lEy[c + nx] += h * lBx[c]; lEy[c] -= h * lBx[c];
+                lEz[(size_t)k * nx + ip] += h * lBy[c]; lEz[c] -= h * lBy[c];
+                lEx[c + nx] -= h * lBy[c]; lEx[c] += h * lBy[c];
+            }
+            lEy[(size_t)k * nx + ip] -= h * lBz[c]; lEy[c] += h * lBz[c];
+        }
+}
+
+/* laser source per unit E0 (E_x of the incident pulse at x, t divided by E0) */
+static double laser_shape(ostate* s, double x_cells, double t)
+{
+    double save = s->E0;
+    s->E0 = 1.0;
+    double v = laser_field(s, x_cells, t);
+    s->E0 = save;
+    return v;
+}
+
+/* E update of the Yee scheme with Mur walls and the antenna (E0 given), j = dt J / eps0 */
+static void fe_cont(ostate* s, double* F, const double* jx, const double* jy, const double* jz, double E0, double tmid)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    size_t nn = (size_t)nx * (nz + 1);
+    double cdt = O_C * s->dt, h = O_C * O_C * s->dt / s->c.dx;
+    double *Ex = F, *Ey = F + nn, *Ez = F + 2 * nn, *Bx = F + 3 * nn, *By = F + 4 * nn, *Bz = F + 5 * nn;
+    double* nEx = malloc(sizeof(double) * nn);
+    double* nEy = malloc(sizeof(double) * nn);
+    for (int k = 0; k <= nz; k++)
+        for (int i = 0; i < nx; i++) {
+            int im = (i + nx - 1) % nx;
+            size_t c = (size_t)k * nx + i;
+            nEx[c] = Ex[c];
+            nEy[c] = Ey[c];
+            if (k > 0 && k < nz) {
+                nEx[c] = Ex[c] - h * (By[c] - By[c - nx]) - jx[c];
+                nEy[c] = Ey[c] + h * ((Bx[c] - Bx[c - nx]) - (Bz[c] - Bz[(size_t)k * nx + im])) - jy[c];
+                if (k == s->k_ant) nEx[c] += 2.0 * (cdt / s->c.dx) * E0 * laser_shape(s, (double)i + 0.5, tmid);
+            }
+        }
+    double alpha = (cdt - s->c.dx) / (cdt + s->c.dx);
+    for (int i = 0; i < nx; i++) {
+        size_t b0 = i, b1 = (size_t)nx + i, t0 = (size_t)nz * nx + i, t1 = (size_t)(nz - 1) * nx + i;
+        nEx[b0] = Ex[b1] + alpha * (nEx[b1] - Ex[b0]);
+        nEy[b0] = Ey[b1] + alpha * (nEy[b1] - Ey[b0]);
+        nEx[t0] = Ex[t1] + alpha * (nEx[t1] - Ex[t0]);
+        nEy[t0] = Ey[t1] + alpha * (nEy[t1] - Ey[t0]);
+    }
+    for (int k = 0; k < nz; k++)
+        for (int i = 0; i < nx; i++) {
+            size_t c = (size_t)k * nx + i;
+            Ez[c] += h * (By[c] - By[(size_t)k * nx + (i + nx - 1) % nx]) - jz[c];
+        }
+    memcpy(Ex, nEx, sizeof(double) * nn);
+    memcpy(Ey, nEy, sizeof(double) * nn);
+    free(nEx); free(nEy);
+}
+
+/* Transpose of fe_cont. lF holds the adjoints of the new E (and of B, unchanged by this part);
+ * on return it holds those of the old E and of B, lj the adjoints of jx, jy, jz, and *gE0 has
+ * the derivative with respect to E0 added. */
+static void fe_cont_T(ostate* s, double* lF, double* ljx, double* ljy, double* ljz, double tmid, double* gE0)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    size_t nn = (size_t)nx * (nz + 1);
+    double cdt = O_C * s->dt, h = O_C * O_C * s->dt / s->c.dx;
+    double *lEx = lF, *lEy = lF + nn, *lEz = lF + 2 * nn, *lBx = lF + 3 * nn, *lBy = lF + 4 * nn, *lBz = lF + 5 * nn;
+    double* lnEx = malloc(sizeof(double) * nn);
+    double* lnEy = malloc(sizeof(double) * nn);
+    memcpy(lnEx, lEx, sizeof(double) * nn);
+    memcpy(lnEy, lEy, sizeof(double) * nn);
+    memset(lEx, 0, sizeof(double) * nn);
+    memset(lEy, 0, sizeof(double) * nn);
+    memset(ljx, 0, sizeof(double) * nn);
+    memset(ljy, 0, sizeof(double) * nn);
+    memset(ljz, 0, sizeof(double) * nn);
+    /* Ez (in place): old Ez passes through; B and jz receive */
+    for (int k = 0; k < nz; k++)
+        for (int i = 0; i < nx; i++) {
+            size_t c = (size_t)k * nx + i;
+            double v = lEz[c];
+            lBy[c] += h * v;
+            lBy[(size_t)k * nx + (i + nx - 1) % nx] -= h * v;
+            ljz[c] = -v;
+        }
+    /* Mur rows (they overwrite the wall values of the new E) */
+    double alpha = (cdt - s->c.dx) / (cdt + s->c.dx);
+    for (int i = 0; i < nx; i++) {
+        size_t b0 = i, b1 = (size_t)nx + i, t0 = (size_t)nz * nx + i, t1 = (size_t)(nz - 1) * nx + i;
+        double v;
+        v = lnEx[b0]; lEx[b1] += v; lnEx[b1] += alpha * v; lEx[b0] -= alpha * v; lnEx[b0] = 0.0;
+        v = lnEy[b0]; lEy[b1] += v; lnEy[b1] += alpha * v; lEy[b0] -= alpha * v; lnEy[b0] = 0.0;
+        v = lnEx[t0]; lEx[t1] += v; lnEx[t1] += alpha * v; lEx[t0] -= alpha * v; lnEx[t0] = 0.0;
+        v = lnEy[t0]; lEy[t1] += v; lnEy[t1] += alpha * v; lEy[t0] -= alpha * v; lnEy[t0] = 0.0;
+    }
+    for (int k = 1; k < nz; k++)
+        for (int i = 0; i < nx; i++) {
+            int im = (i + nx - 1) % nx;
+            size_t c = (size_t)k * nx + i;
+            double v = lnEx[c];
+            lEx[c] += v;
+            lBy[c] -= h * v;
+            lBy[c - nx] += h * v;
+            ljx[c] = -v;
+            if (k == s->k_ant) *gE0 += v * 2.0 * (cdt / s->c.dx) * laser_shape(s, (double)i + 0.5, tmid);
+            v = lnEy[c];
+            lEy[c] += v;
+            lBx[c] += h * v;
+            lBx[c - nx] -= h * v;
+            lBz[c] -= h * v;
+            lBz[(size_t)k * nx + im] += h * v;
+            ljy[c] = -v;
+        }
+    free(lnEx); free(lnEy);
+}
+
+/* Maxwell part of one step on the arrays F (6 nn) with the scaled current j (3 nn) */
+static void maxwell_cont(ostate* s, double* F, const double* j, double E0, int64_t step)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    hb_cont(s, F);
+    fe_cont(s, F, j, j + nn, j + 2 * nn, E0, ((double)step + 0.5) * s->dt);
+    hb_cont(s, F);
+}
+
+/* its transpose: lF (adjoint of the new fields) -> adjoint of the old fields; lj receives the
+ * current's adjoint; *gE0 accumulates the E0 derivative */
+static void maxwell_cont_T(ostate* s, double* lF, double* lj, int64_t step, double* gE0)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    hb_cont_T(s, lF);
+    fe_cont_T(s, lF, lj, lj + nn, lj + 2 * nn, ((double)step + 0.5) * s->dt, gE0);
+    hb_cont_T(s, lF);
+}
+
+void oracle_maxwell_cont(ostate* s, double* F, const double* j, double E0, int64_t step)
+{
+    maxwell_cont(s, F, j, E0, step);
+}
+
+void oracle_maxwell_cont_T(ostate* s, double* lF, double* lj, int64_t step, double* gE0)
+{
+    maxwell_cont_T(s, lF, lj, step, gE0);
+}
+
+/* staggered bilinear gather from an array (as gather_field) and its transpose: adds lv * weights
+ * into lA and the position derivatives lv * dA/dx, lv * dA/dz into *lx, *lz */
+static double gather_arr(const ostate* s, const double* A, double x, double z, double sx, double sz,
+                         double* lA, double lv, double* lx, double* lz)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    double xs = x - sx, zs = z - sz;
+    int64_t rows = sz > 0 ? nz : nz + 1;
+    int clamped = 0;
+    if (zs < 0.0) { zs = 0.0; clamped = 1; }
+    if (zs > (double)(rows - 1)) { zs = (double)(rows - 1); clamped = 1; }
+    int64_t i = (int64_t)floor(xs), k = (int64_t)floor(zs);
+    double fx = xs - (double)i, fz = zs - (double)k;
+    if (k >= rows - 1) { k = rows - 2; fz = 1.0; }
+    size_t c00 = (size_t)k * nx + imod(i, nx), c10 = (size_t)k * nx + imod(i + 1, nx);
+    size_t c01 = c00 + nx, c11 = c10 + nx;
+    double a00 = A[c00], a10 = A[c10], a01 = A[c01], a11 = A[c11];
+    double v = (1 - fx) * (1 - fz) * a00 + fx * (1 - fz) * a10 + (1 - fx) * fz * a01 + fx * fz * a11;
+    if (lA) {
+        lA[c00] += lv * (1 - fx) * (1 - fz); lA[c10] += lv * fx * (1 - fz);
+        lA[c01] += lv * (1 - fx) * fz;       lA[c11] += lv * fx * fz;
+        *lx += lv * ((1 - fz) * (a10 - a00) + fz * (a11 - a01));
+        if (!clamped) *lz += lv * ((1 - fx) * (a01 - a00) + fx * (a11 - a10));
+    }
+    return v;
+}
+
+static const double k_stag[6][2] = {{0.5, 0.0}, {0.0, 0.0}, {0.0, 0.5}, {0.0, 0.5}, {0.5, 0.5}, {0.5, 0.0}};
+
+/* the intermediate values of one particle's forward step, kept for its transpose */
+typedef struct {
+    double E[3], B[3], Fp[3];
+    double n, qx, qz, gxz, dxn, dxq, dxr, dzn, dzq, dzr;   /* pair-force pieces (ions) */
+    double um[3], gm, tfac, t[3], t2, sv[3], upr[3], uf[3];
+    double g, cs, xn, zn, x1u, z1, ufin[3], gfin, by;
+    int refl;
+} pstep;
+
+static void particle_fwd(ostate* s, int sp, const double* F, const double* nh, double x, double z, const double u[3],
+                         pstep* P)
+{
+    for (int d = 0; d < 3; d++) { P->E[d] = P->B[d] = P->Fp[d] = 0.0; }
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    if (s->c.mode == 0)
+        for (int f = 0; f < 6; f++) {
+            double v = gather_arr(s, F + f * nn, x, z, k_stag[f][0], k_stag[f][1], NULL, 0, NULL, NULL);
+            if (f < 3) P->E[f] = v; else P->B[f - 3] = v;
+        }
+    if (s->pair[sp]) {
+        int64_t i, k; double fx, fz;
+        gather_cont(s, nh, x, z, &P->n, &P->qx, &P->qz, &P->gxz, &i, &k, &fx, &fz);
+        P->Fp[0] = axis_force_d(P->n, P->qx, s->D, s->r0, s->c.dx, &P->dxn, &P->dxq, &P->dxr);
+        P->Fp[2] = axis_force_d(P->n, P->qz, s->D, s->r0, s->c.dx, &P->dzn, &P->dzq, &P->dzr);
+    }
+    /* Boris, the steps of oracle_boris kept */
+    double q = s->q[sp], m = s->m[sp], dt = s->dt;
+    double eps = q * dt / (2.0 * m * O_C), fk = dt / (2.0 * m * O_C);
+    for (int d = 0; d < 3; d++) P->um[d] = u[d] + eps * P->E[d] + fk * P->Fp[d];
+    P->gm = sqrt(1.0 + P->um[0] * P->um[0] + P->um[1] * P->um[1] + P->um[2] * P->um[2]);
+    P->tfac = q * dt / (2.0 * m * P->gm);
+    for (int d = 0; d < 3; d++) P->t[d] = P->tfac * P->B[d];
+    P->t2 = P->t[0] * P->t[0] + P->t[1] * P->t[1] + P->t[2] * P->t[2];
+    for (int d = 0; d < 3; d++) P->sv[d] = 2.0 * P->t[d] / (1.0 + P->t2);
+    const double* um = P->um; const double* t = P->t; const double* sv = P->sv;
+    P->upr[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+    P->upr[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+    P->upr[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+    double up[3];
+    up[0] = um[0] + (P->upr[1] * sv[2] - P->upr[2] * sv[1]);
+    up[1] = um[1] + (P->upr[2] * sv[0] - P->upr[0] * sv[2]);
+    up[2] = um[2] + (P->upr[0] * sv[1] - P->upr[1] * sv[0]);
+    for (int d = 0; d < 3; d++) P->uf[d] = up[d] + eps * P->E[d] + fk * P->Fp[d];
+    /* move and walls */
+    P->g = sqrt(1.0 + P->uf[0] * P->uf[0] + P->uf[1] * P->uf[1] + P->uf[2] * P->uf[2]);
+    P->cs = O_C * dt / (P->g * s->c.dx);
+    P->xn = x + P->uf[0] * P->cs;
+    P->zn = z + P->uf[2] * P->cs;
+    for (int d = 0; d < 3; d++) P->ufin[d] = P->uf[d];
+    P->refl = 0;
+    P->z1 = P->zn;
+    if (P->zn < 0.0) { P->z1 = -P->zn; P->ufin[2] = -P->uf[2]; P->refl = 1; }
+    if (P->zn >= s->c.nz) { P->z1 = 2.0 * s->c.nz - P->zn; P->ufin[2] = -P->uf[2]; P->refl = 1; }
+    P->x1u = P->xn;                                 /* unwrapped: within a cell of x */
+    P->gfin = P->g;
+    P->by = P->ufin[1] / P->gfin;
+}
+
+static double wrap_x(const ostate* s, double x)
+{
+    if (x < 0.0) x += s->c.nx;
+    if (x >= s->c.nx) x -= s->c.nx;
+    return x;
+}
+
+/* one forward step of the continuous full cycle on the state arrays (positions, momenta of both
+ * species, fields); j: scratch 3 nn; nh: scratch nn */
+static void full_step_cont(ostate* s, double** X, double** Z, double** U, double* F, double* j, double* nh,
+                           double E0, int64_t step)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    if (s->pair[0]) dens_cont(s, X[0], Z[0], s->np[0], nh);
+    memset(j, 0, sizeof(double) * 3 * nn);
+    for (int sp = 0; sp < s->nsp; sp++) {
+        double sg = s->q[sp] > 0 ? 1.0 : (s->q[sp] < 0 ? -1.0 : 0.0);
+        for (int64_t p = 0; p < s->np[sp]; p++) {
+            pstep P;
+            double* u = U[sp] + 3 * p;
+            particle_fwd(s, sp, F, nh, X[sp][p], Z[sp][p], u, &P);
+            if (s->c.mode == 0 && sg != 0.0)
+                cur_cont(s, sg, X[sp][p], Z[sp][p], P.x1u, P.z1, P.by, j, j + nn, j + 2 * nn);
+            X[sp][p] = wrap_x(s, P.xn);
+            Z[sp][p] = P.z1;
+            for (int d = 0; d < 3; d++) u[d] = P.ufin[d];
+        }
+    }
+    if (s->c.mode == 0) maxwell_cont(s, F, j, E0, step);
+}
+
+/* kinetic energy of all species from packed momenta */
+static double kinetic_all(const ostate* s, double** U)
+{
+    double ke = 0.0;
+    for (int sp = 0; sp < s->nsp; sp++) {
+        double acc = 0.0;
+        for (int64_t p = 0; p < s->np[sp]; p++) {
+            const double* u = U[sp] + 3 * p;
+            double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            acc += u2 / (sqrt(1.0 + u2) + 1.0);
+        }
+        ke += acc * s->w * s->m[sp] * O_C * O_C;
+    }
+    return ke;
+}
+
+typedef struct {
+    int nsteps;
+    double *X[2], *Z[2], *U[2];     /* (nsteps + 1) * np each (U: 3 per particle) */
+    double* F;                      /* (nsteps + 1) * 6 nn */
+} ftraj;
+
+static void traj_alloc(const ostate* s, ftraj* T, int nsteps)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    T->nsteps = nsteps;
+    for (int sp = 0; sp < 2; sp++) {
+        size_t n = sp < s->nsp ? (size_t)s->np[sp] : 0;
+        T->X[sp] = malloc(sizeof(double) * (n ? n : 1) * (nsteps + 1));
+        T->Z[sp] = malloc(sizeof(double) * (n ? n : 1) * (nsteps + 1));
+        T->U[sp] = malloc(sizeof(double) * 3 * (n ? n : 1) * (nsteps + 1));
+        for (size_t p = 0; p < n; p++) {
+            T->X[sp][p] = s->x[sp][p]; T->Z[sp][p] = s->z[sp][p];
+            T->U[sp][3 * p] = s->ux[sp][p]; T->U[sp][3 * p + 1] = s->uy[sp][p]; T->U[sp][3 * p + 2] = s->uz[sp][p];
+        }
+    }
+    T->F = malloc(sizeof(double) * 6 * nn * (nsteps + 1));
+    for (int f = 0; f < 6; f++) memcpy(T->F + f * nn, s->F[f], sizeof(double) * nn);
+}
+
+static void traj_free(ftraj* T)
+{
+    for (int sp = 0; sp < 2; sp++) { free(T->X[sp]); free(T->Z[sp]); free(T->U[sp]); }
+    free(T->F);
+}
+
+/* run the stored trajectory forward; returns the loss of its final state */
+static double traj_forward(ostate* s, ftraj* T, const double* cw, double kin, double E0)
+{
+    size_t nn = (size_t)s->c.nx * (s->c.nz + 1);
+    double* j = malloc(sizeof(double) * 3 * nn);
+    double* nh = malloc(sizeof(double) * nn);
+    for (int t = 0; t < T->nsteps; t++) {
+        double *X[2], *Z[2], *U[2];
+        for (int sp = 0; sp < s->nsp; sp++) {
+            size_t n = (size_t)s->np[sp];
+            X[sp] = T->X[sp] + (t + 1) * n; Z[sp] = T->Z[sp] + (t + 1) * n; U[sp] = T->U[sp] + 3 * (t + 1) * n;
+            memcpy(X[sp], T->X[sp] + t * n, sizeof(double) * n);
+            memcpy(Z[sp], T->Z[sp] + t * n, sizeof(double) * n);
+            memcpy(U[sp], T->U[sp] + 3 * t * n, sizeof(double) * 3 * n);
+        }
+        double* F = T->F + (size_t)(t + 1) * 6 * nn;
+        memcpy(F, T->F + (size_t)t * 6 * nn, sizeof(double) * 6 * nn);
+        full_step_cont(s, X, Z, U, F, j, nh, E0, s->step + t);
+    }
+    double L = 0.0;
+    int N = T->nsteps;
+    if (s->pair[0]) {
+        dens_cont(s, T->X[0] + (size_t)N * s->np[0], T->Z[0] + (size_t)N * s->np[0], s->np[0], nh);
+        for (size_t c = 0; c < nn; c++) L += cw[c] * nh[c];
+    }
+    double* UN[2];
+    for (int sp = 0; sp < s->nsp; sp++) UN[sp] = T->U[sp] + 3 * (size_t)N * s->np[sp];
+    L += kin * kinetic_all(s, UN);
+    free(j); free(nh);
+    return L;
+}
+
+/* Forward nsteps of the continuous full cycle from the current state and the reverse sweep.
+ * out[0] = L, out[1] = dL/dD (1/J), out[2] = dL/dr0 (1/m), out[3] = dL/dI0 (m^2/W).
+ * The context's state is left unchanged. */
+void oracle_full_grad(ostate* s, int32_t nsteps, const double* cw, double kin, double* out)
+{
+    int nx = s->c.nx, nz = s->c.nz;
+    size_t nn = (size_t)nx * (nz + 1);
+    ftraj T;
+    traj_alloc(s, &T, nsteps);
+    double L = traj_forward(s, &T, cw, kin, s->E0);
+    int N = nsteps;
+    /* adjoints of the final state */
+    double *lX[2] = {0, 0}, *lZ[2] = {0, 0}, *lU[2] = {0, 0};
+    for (int sp = 0; sp < s->nsp; sp++) {
+        size_t n = (size_t)s->np[sp];
+        lX[sp] = calloc(n ? n : 1, sizeof(double));
+        lZ[sp] = calloc(n ? n : 1, sizeof(double));
+        lU[sp] = calloc(3 * (n ? n : 1), sizeof(double));
+        double mc2w = s->w * s->m[sp] * O_C * O_C;
+        const double* u = T.U[sp] + 3 * (size_t)N * n;
+        for (size_t p = 0; p < n; p++) {
+            double g = sqrt(1.0 + u[3 * p] * u[3 * p] + u[3 * p + 1] * u[3 * p + 1] + u[3 * p + 2] * u[3 * p + 2]);
+            for (int d = 0; d < 3; d++) lU[sp][3 * p + d] = kin * mc2w * u[3 * p + d] / g;
+        }
+    }
+    double gD = 0.0, gr0 = 0.0, gE0 = 0.0;
+    double* nh = malloc(sizeof(double) * nn);
+    double* lam = calloc(nn, sizeof(double));
+    double* lF = calloc(6 * nn, sizeof(double));
+    double* lj = calloc(3 * nn, sizeof(double));
+    if (s->pair[0]) {
+        double *xN = T.X[0] + (size_t)N * s->np[0], *zN = T.Z[0] + (size_t)N * s->np[0];
+        dens_cont(s, xN, zN, s->np[0], nh);
+        deposit_transpose(s, cw, xN, zN, s->np[0], lX[0], lZ[0]);
+        for (size_t c = 0; c < nn; c++) gr0 += cw[c] * 3.0 * nh[c] / s->r0;
+    }
+    for (int t = N - 1; t >= 0; t--) {
+        const double* F = T.F + (size_t)t * 6 * nn;
+        /* Maxwell of step t: adjoint of the new fields -> of the old fields and of j */
+        if (s->c.mode == 0) maxwell_cont_T(s, lF, lj, s->step + t, &gE0);
+        else memset(lj, 0, sizeof(double) * 3 * nn);
+        if (s->pair[0]) dens_cont(s, T.X[0] + (size_t)t * s->np[0], T.Z[0] + (size_t)t * s->np[0], s->np[0], nh);
+        memset(lam, 0, sizeof(double) * nn);
+        for (int sp = 0; sp < s->nsp; sp++) {
+            size_t n = (size_t)s->np[sp];
+            double sg = s->q[sp] > 0 ? 1.0 : (s->q[sp] < 0 ? -1.0 : 0.0);
+            double q = s->q[sp], m = s->m[sp], dt = s->dt;
+            double eps = q * dt / (2.0 * m * O_C), fk = dt / (2.0 * m * O_C);
+            for (size_t p = 0; p < n; p++) {
+                double x = T.X[sp][t * n + p], z = T.Z[sp][t * n + p];
+                const double* u = T.U[sp] + 3 * (t * n + p);
+                pstep P;
+                particle_fwd(s, sp, F, nh, x, z, u, &P);
+                /* adjoints of the new state, plus the current's dependence on it */
+                double lx1 = lX[sp][p], lz1 = lZ[sp][p], luf[3];
+                for (int d = 0; d < 3; d++) luf[d] = lU[sp][3 * p + d];
+                double lx0 = 0.0, lz0 = 0.0;
+                if (s->c.mode == 0 && sg != 0.0) {
+                    double g5[5] = {0, 0, 0, 0, 0};
+                    cur_cont_T(s, sg, x, z, P.x1u, P.z1, P.by, lj, lj + nn, lj + 2 * nn, g5);
+                    lx0 += g5[0]; lz0 += g5[1]; lx1 += g5[2]; lz1 += g5[3];
+                    /* by = ufin_y / gamma */
+                    double gg = P.gfin;
+                    for (int d = 0; d < 3; d++) luf[d] += g5[4] * ((d == 1 ? 1.0 / gg : 0.0) - P.ufin[1] * P.ufin[d] / (gg * gg * gg));
+                }
+                /* wall mirror */
+                double lzn = lz1;
+                if (P.refl) { lzn = -lz1; luf[2] = -luf[2]; }
+                /* move: xn = x + cs uf_x, zn = z + cs uf_z, cs = c dt / (gamma dx) */
+                double udl = (P.uf[0] * lx1 + P.uf[2] * lzn) / (P.g * P.g);
+                double lu[3];
+                lu[0] = luf[0] + P.cs * (lx1 - P.uf[0] * udl);
+                lu[1] = luf[1] + P.cs * (0.0 - P.uf[1] * udl);
+                lu[2] = luf[2] + P.cs * (lzn - P.uf[2] * udl);
+                lx0 += lx1;
+                lz0 += lzn;
+                /* Boris transpose: lu is the adjoint of uf = up + a */
+                double la[3], lup[3], lupr[3], lsv[3], lt[3], lum[3];
+                for (int d = 0; d < 3; d++) { la[d] = lu[d]; lup[d] = lu[d]; }
+                /* up = um + upr x sv */
+                for (int d = 0; d < 3; d++) lum[d] = lup[d];
+                lupr[0] = P.sv[1] * lup[2] - P.sv[2] * lup[1];
+                lupr[1] = P.sv[2] * lup[0] - P.sv[0] * lup[2];
+                lupr[2] = P.sv[0] * lup[1] - P.sv[1] * lup[0];
+                lsv[0] = lup[1] * P.upr[2] - lup[2] * P.upr[1];
+                lsv[1] = lup[2] * P.upr[0] - lup[0] * P.upr[2];
+                lsv[2] = lup[0] * P.upr[1] - lup[1] * P.upr[0];
+                /* upr = um + um x t */
+                lum[0] += lupr[0] + (P.t[1] * lupr[2] - P.t[2] * lupr[1]);
+                lum[1] += lupr[1] + (P.t[2] * lupr[0] - P.t[0] * lupr[2]);
+                lum[2] += lupr[2] + (P.t[0] * lupr[1] - P.t[1] * lupr[0]);
+                lt[0] = lupr[1] * P.um[2] - lupr[2] * P.um[1];
+                lt[1] = lupr[2] * P.um[0] - lupr[0] * P.um[2];
+                lt[2] = lupr[0] * P.um[1] - lupr[1] * P.um[0];
+                /* sv = 2 t / (1 + t.t) */
+                double tl = P.t[0] * lsv[0] + P.t[1] * lsv[1] + P.t[2] * lsv[2], d1 = 1.0 + P.t2;
+                for (int d = 0; d < 3; d++) lt[d] += 2.0 * lsv[d] / d1 - 4.0 * tl * P.t[d] / (d1 * d1);
+                /* t = tfac B, tfac = q dt / (2 m gm) */
+                double lB[3], ltf = 0.0;
+                for (int d = 0; d < 3; d++) { lB[d] = P.tfac * lt[d]; ltf += P.B[d] * lt[d]; }
+                double lgm = -P.tfac / P.gm * ltf;
+                for (int d = 0; d < 3; d++) lum[d] += lgm * P.um[d] / P.gm;
+                /* um = u + a */
+                for (int d = 0; d < 3; d++) la[d] += lum[d];
+                for (int d = 0; d < 3; d++) lU[sp][3 * p + d] = lum[d];
+                /* a = eps E + fk Fp: field gathers */
+                if (s->c.mode == 0)
+                    for (int f = 0; f < 6; f++) {
+                        double lv = f < 3 ? eps * la[f] : lB[f - 3];
+                        gather_arr(s, F + f * nn, x, z, k_stag[f][0], k_stag[f][1], lF + f * nn, lv, &lx0, &lz0);
+                    }
+                if (s->pair[sp]) {
+                    double lFx = fk * la[0], lFz = fk * la[2];
+                    gD += (lFx * P.Fp[0] + lFz * P.Fp[2]) / s->D;
+                    gr0 += lFx * (P.dxr + P.dxn * 3.0 * P.n / s->r0 + P.dxq * 3.0 * P.qx / s->r0);
+                    gr0 += lFz * (P.dzr + P.dzn * 3.0 * P.n / s->r0 + P.dzq * 3.0 * P.qz / s->r0);
+                    double ln = lFx * P.dxn + lFz * P.dzn, lqx = lFx * P.dxq, lqz = lFz * P.dzq;
+                    lx0 += ln * P.qx + lqz * P.gxz;
+                    lz0 += ln * P.qz + lqx * P.gxz;
+                    int64_t i, k; double fx, fz, n_, a1, a2, a3;
+                    gather_cont(s, nh, x, z, &n_, &a1, &a2, &a3, &i, &k, &fx, &fz);
+                    size_t c00 = (size_t)k * nx + imod(i, nx), c10 = (size_t)k * nx + imod(i + 1, nx);
+                    size_t c01 = (size_t)(k + 1) * nx + imod(i, nx), c11 = (size_t)(k + 1) * nx + imod(i + 1, nx);
+                    lam[c00] += ln * (1 - fx) * (1 - fz) - lqx * (1 - fz) - lqz * (1 - fx);
+                    lam[c10] += ln * fx * (1 - fz) + lqx * (1 - fz) - lqz * fx;
+                    lam[c01] += ln * (1 - fx) * fz - lqx * fz + lqz * (1 - fx);
+                    lam[c11] += ln * fx * fz + lqx * fz + lqz * fx;
+                }
+                lX[sp][p] = lx0;
+                lZ[sp][p] = lz0;
+            }
+        }
+        if (s->pair[0]) deposit_transpose(s, lam, T.X[0] + (size_t)t * s->np[0], T.Z[0] + (size_t)t * s->np[0],
+                                          s->np[0], lX[0], lZ[0]);
+    }
+    out[0] = L;
+    out[1] = gD;
+    out[2] = gr0;
+    out[3] = s->c.I0 > 0 ? gE0 * s->E0 / (2.0 * s->c.I0) : 0.0;
+    for (int sp = 0; sp < s->nsp; sp++) { free(lX[sp]); free(lZ[sp]); free(lU[sp]); }
+    free(nh); free(lam); free(lF); free(lj);
+    traj_free(&T);
+}
+
+/* Loss of the continuous full cycle after nsteps with D, r0, I0 overriding the configuration
+ * (for finite differences); the context's state is left unchanged. */
+double oracle_full_loss(ostate* s, int32_t nsteps, const double* cw, double kin, double D_J, double r0_m, double I0)
+{
+    double Dsave = s->D, r0save = s->r0;
+    s->D = D_J;
+    s->r0 = r0_m;
+    ftraj T;
+    traj_alloc(s, &T, nsteps);
+    double L = traj_forward(s, &T, cw, kin, sqrt(2.0 * I0 / (O_EPS0 * O_C)));
+    traj_free(&T);
+    s->D = Dsave;
+    s->r0 = r0save;
+    return L;
+}
+
+double oracle_E0(const ostate* s) { return s->E0; }
