@@ -252,26 +252,48 @@ PIC_API int pic_checkpoint_size(pic_ctx* ctx, size_t* bytes);
 PIC_API int pic_checkpoint_save(pic_ctx* ctx, void* dev_buf);
 PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
 
-/* ---- differentiable transport stage (2D, PIC_MODE_TRANSPORT, sort_every = 0, pot_mode 0) ------
- * Gradients of L = sum_nodes w(node) n(node)/n0 (at the final state) + kin * (total kinetic energy)
- * with respect to the pair-potential parameters D (J) and r0 (m), by hand-written adjoint kernels
- * (FP64) of the transport step: node density -> Eqs. (1)-(3) force -> kick -> move. The fixed-point
- * deposition is differentiated as the continuous linear shape. The paper has no adjoint; the
- * stage and the parameters are the paper's (the transport simulation with the pair potential).
+/* ---- differentiable cycle (2D, sort_every = 0, pot_mode 0) ----------------------------------
+ * Gradients of L = sum_nodes w(node) n(node)/n0 (pair-species density at the final state)
+ *                 + kin * (total kinetic energy of all species, J per metre of y)
+ * with respect to the pair-potential parameters D (J) and r0 (m) and, in PIC_MODE_FULL, the laser
+ * peak intensity I0 (W/m^2), by hand-written FP64 adjoint kernels of the step. In
+ * PIC_MODE_TRANSPORT the step is node density -> Eqs. (1)-(3) force -> kick -> move; in
+ * PIC_MODE_FULL it is the whole cycle: density, pair force, staggered E/B gather, Boris push,
+ * move, walls, charge-conserving current, Yee update with Mur walls and the antenna (E0 =
+ * sqrt(2 I0 / (eps0 c)) scales the source). The fixed-point deposition and current are
+ * differentiated as the continuous linear shape. The paper has no adjoint; the method, the
+ * parameters and the stage are the paper's.
+ *
+ * Adjoint buffers (device, caller-owned, double):
+ *   lam_pos[s]: 2 n_s, (x, z) adjoints per particle of species s, in the context's particle order;
+ *   lam_u[s]:   3 n_s;
+ *   lam_nodes:  (nz+1) nx scratch;
+ *   lam_F:      9 (nz+1) nx: adjoints of Ex Ey Ez Bx By Bz and three scratch grids (FULL only);
+ *   lam_j:      3 (nz+1) nx scratch (FULL only);
+ *   grads:      3, accumulated by pic_adjoint_step: dL/dD (1/J), dL/dr0 (1/m), dL/dI0 (m^2/W).
+ * Unused pointers (second species, FULL-only buffers in transport mode) may be NULL.
  *
  * pic_node_functional: *host_out = sum_nodes w n/n0 at the current state (w: device double
  *   (nz+1)*nx, e.g. a crater-depth weighting).
- * pic_adjoint_seed: at the final state, initialise the adjoints: lam_u = kin * w m c^2 u / gamma,
- *   lam_pos = d/dx of sum w n/n0; *host_dLdr0 receives the r0 derivative of the density unit in
- *   the functional (add it to the r0 gradient). lam_pos: device double[2 n] (x, z per atom),
- *   lam_u: double[3 n], lam_nodes: double[(nz+1)*nx] scratch.
- * pic_adjoint_step: with the context at the state x^t, u^t of step t (restore it from a
- *   checkpoint), map the adjoints of step t+1 to step t in place and add dL/dD, dL/dr0 of this
- *   step to dev_grads (device double[2]). Returns PIC_ESTATE outside the supported mode. */
+ * pic_adjoint_seed: at the final state, set the adjoints of the loss (momenta: kin w m c^2 u/gamma,
+ *   positions: the gradient of the density functional, fields: 0); *host_dLdr0 receives the r0
+ *   derivative of the density unit in the functional (add it to grads[1]).
+ * pic_adjoint_step: with the context at the state of step t (restore it from a checkpoint), map the
+ *   adjoints of step t+1 to step t in place and add this step's parameter derivatives to grads.
+ * Both return PIC_ESTATE outside 2D, sort_every = 0 and pot_mode 0. */
+typedef struct {
+    double* lam_pos[2];
+    double* lam_u[2];
+    double* lam_nodes;
+    double* lam_F;
+    double* lam_j;
+    double* grads;
+} pic_adjoint_buffers;
+
 PIC_API int pic_node_functional(pic_ctx* ctx, const double* dev_weights, double* host_out);
-PIC_API int pic_adjoint_seed(pic_ctx* ctx, double kin, const double* dev_weights, double* lam_pos, double* lam_u,
-                             double* lam_nodes, double* host_dLdr0);
-PIC_API int pic_adjoint_step(pic_ctx* ctx, double* lam_pos, double* lam_u, double* lam_nodes, double* dev_grads);
+PIC_API int pic_adjoint_seed(pic_ctx* ctx, double kin, const double* dev_weights, const pic_adjoint_buffers* bufs,
+                             double* host_dLdr0);
+PIC_API int pic_adjoint_step(pic_ctx* ctx, const pic_adjoint_buffers* bufs);
 
 /* Static text for a return code. */
 PIC_API const char* pic_strerror(int code);

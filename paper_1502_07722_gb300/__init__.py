@@ -55,6 +55,12 @@ class pic_state_view(ctypes.Structure):
                 ("uy", _P * 2), ("uz", _P * 2), ("F", _P * 6), ("rho", _P)]
 
 
+class pic_adjoint_buffers(ctypes.Structure):
+    _P = ctypes.c_void_p
+    _fields_ = [("lam_pos", _P * 2), ("lam_u", _P * 2), ("lam_nodes", _P), ("lam_F", _P), ("lam_j", _P),
+                ("grads", _P)]
+
+
 # name -> (restype, argtypes) of every exported C entry point
 _VP = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -89,8 +95,9 @@ _SIGNATURES = {
     "pic_checkpoint_save": (ctypes.c_int, [_VP, _VP]),
     "pic_checkpoint_restore": (ctypes.c_int, [_VP, _VP]),
     "pic_node_functional": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
-    "pic_adjoint_seed": (ctypes.c_int, [_VP, ctypes.c_double, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
-    "pic_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "pic_adjoint_seed": (ctypes.c_int, [_VP, ctypes.c_double, _VP, ctypes.POINTER(pic_adjoint_buffers),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "pic_adjoint_step": (ctypes.c_int, [_VP, ctypes.POINTER(pic_adjoint_buffers)]),
 }
 
 _lib = None
@@ -286,16 +293,15 @@ def pic_node_functional(h, dev_weights_ptr) -> float:
     return v.value
 
 
-def pic_adjoint_seed(h, kin, dev_weights_ptr, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr) -> float:
+def pic_adjoint_seed(h, kin, dev_weights_ptr, bufs) -> float:
     v = ctypes.c_double()
-    _check(load_library().pic_adjoint_seed(h, float(kin), dev_weights_ptr, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr,
-                                           ctypes.byref(v)), "pic_adjoint_seed")
+    _check(load_library().pic_adjoint_seed(h, float(kin), dev_weights_ptr, ctypes.byref(bufs), ctypes.byref(v)),
+           "pic_adjoint_seed")
     return v.value
 
 
-def pic_adjoint_step(h, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr, dev_grads_ptr):
-    _check(load_library().pic_adjoint_step(h, lam_pos_ptr, lam_u_ptr, lam_nodes_ptr, dev_grads_ptr),
-           "pic_adjoint_step")
+def pic_adjoint_step(h, bufs):
+    _check(load_library().pic_adjoint_step(h, ctypes.byref(bufs)), "pic_adjoint_step")
 
 
 # ---- convenience wrapper: torch owns the workspace and the stream -----------------------------

@@ -723,11 +723,14 @@ int pic_checkpoint_restore(pic_ctx* h, const void* dev_buf)
 
 // ---- differentiable transport stage -------------------------------------------------------
 
-static int adjoint_ok(const Ctx& c)
+static int adjoint_ok(const Ctx& c, const pic_adjoint_buffers* b)
 {
     if (c.sticky) return c.sticky;
-    if (c.dims != 2 || c.cfg.mode != PIC_MODE_TRANSPORT || c.cfg.sort_every != 0 || c.cfg.pot_mode != 0)
-        return PIC_ESTATE;
+    if (c.dims != 2 || c.cfg.sort_every != 0 || c.cfg.pot_mode != 0) return PIC_ESTATE;
+    for (int s = 0; s < c.nsp; s++)
+        if (!b->lam_pos[s] || !b->lam_u[s]) return PIC_EINVAL;
+    if (!b->lam_nodes || !b->grads) return PIC_EINVAL;
+    if (c.cfg.mode == PIC_MODE_FULL && (!b->lam_F || !b->lam_j)) return PIC_EINVAL;
     return PIC_OK;
 }
 
@@ -744,29 +747,36 @@ int pic_node_functional(pic_ctx* h, const double* dev_weights, double* host_out)
     return PIC_OK;
 }
 
-int pic_adjoint_seed(pic_ctx* h, double kin, const double* dev_weights, double* lam_pos, double* lam_u,
-                     double* lam_nodes, double* host_dLdr0)
+int pic_adjoint_seed(pic_ctx* h, double kin, const double* dev_weights, const pic_adjoint_buffers* b,
+                     double* host_dLdr0)
 {
-    if (!h || !dev_weights || !lam_pos || !lam_u || !lam_nodes || !host_dLdr0) return PIC_EINVAL;
+    if (!h || !dev_weights || !b || !host_dLdr0) return PIC_EINVAL;
     Ctx& c = h->c;
-    int r = adjoint_ok(c);
+    int r = adjoint_ok(c, b);
     if (r) return r;
     double* tmp = c.red_out + 6;
     CK(cudaMemsetAsync(tmp, 0, sizeof(double), c.stream));
-    launch_adjoint_seed(c, kin, dev_weights, lam_pos, lam_u, lam_nodes, tmp, c.stream);
+    if (c.cfg.mode == PIC_MODE_FULL)
+        launch_adjoint_seed_full(c, kin, dev_weights, b->lam_pos, b->lam_u, b->lam_nodes, b->lam_F, b->lam_j, tmp,
+                                 c.stream);
+    else
+        launch_adjoint_seed(c, kin, dev_weights, b->lam_pos[0], b->lam_u[0], b->lam_nodes, tmp, c.stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(host_dLdr0, tmp, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     return PIC_OK;
 }
 
-int pic_adjoint_step(pic_ctx* h, double* lam_pos, double* lam_u, double* lam_nodes, double* dev_grads)
+int pic_adjoint_step(pic_ctx* h, const pic_adjoint_buffers* b)
 {
-    if (!h || !lam_pos || !lam_u || !lam_nodes || !dev_grads) return PIC_EINVAL;
+    if (!h || !b) return PIC_EINVAL;
     Ctx& c = h->c;
-    int r = adjoint_ok(c);
+    int r = adjoint_ok(c, b);
     if (r) return r;
-    launch_adjoint_step(c, lam_pos, lam_u, lam_nodes, dev_grads, c.stream);
+    if (c.cfg.mode == PIC_MODE_FULL)
+        launch_adjoint_step_full(c, b->lam_pos, b->lam_u, b->lam_nodes, b->lam_F, b->lam_j, b->grads, c.stream);
+    else
+        launch_adjoint_step(c, b->lam_pos[0], b->lam_u[0], b->lam_nodes, b->grads, c.stream);
     CK(cudaGetLastError());
     return PIC_OK;
 }

@@ -159,6 +159,10 @@ void launch_adjoint_seed(Ctx& c, double kin, const double* w_nodes, double* lam_
                          double* r0_out, cudaStream_t st);
 void launch_adjoint_step(Ctx& c, double* lam_pos, double* lam_u, double* lam_nodes, double* grads, cudaStream_t st);
 void launch_node_functional(Ctx& c, const double* w_nodes, double* dev_out, cudaStream_t st);
+void launch_adjoint_seed_full(Ctx& c, double kin, const double* w_nodes, double* const* lam_pos, double* const* lam_u,
+                              double* lam_nodes, double* lF, double* lj, double* r0_out, cudaStream_t st);
+void launch_adjoint_step_full(Ctx& c, double* const* lam_pos, double* const* lam_u, double* lam_nodes, double* lF,
+                              double* lj, double* grads, cudaStream_t st);
 int tile_window(int T);
 void launch_energy(Ctx& c, cudaStream_t st, double* host_out5);
 StepArgs make_step_args(Ctx& c);

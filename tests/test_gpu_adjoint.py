@@ -67,30 +67,31 @@ def _weights(w):
     return cw
 
 
-def _gpu_grad(gb, w, nsteps, kin, every, grid=False, orc=None):
+def _gpu_grad(gb, w, nsteps, kin, every, grid=False, orc=None, full=False):
     """GPU loss and gradient; with grid=True the initial offsets are first rounded to the 2^-16
     deposition grid (so the GPU's fixed-point density of the initial state is the continuous one).
     orc, if given, receives the same initial state."""
     from paper_1502_07722_gb300 import diff
     o = oracle.Oracle(w, with_particles=False)
-    run = diff.TransportRun(w, o.D, o.r0, every)
-    p = run.sim.get_particles(0)
-    cell = p["cell"].cpu().numpy().astype(np.int64)
-    fx = p["fx"].cpu().numpy().astype(np.float64)
-    fz = p["fz"].cpu().numpy().astype(np.float64)
-    if grid:
-        fx = np.minimum(np.round(fx * 65536) / 65536, 65535 / 65536)
-        fz = np.minimum(np.round(fz * 65536) / 65536, 65535 / 65536)
-        u = [p[k].cpu().numpy() for k in ("ux", "uy", "uz")]
-        run.sim.set_particles(0, cell.astype(np.int32), fx.astype(np.float32), fz.astype(np.float32), *u)
-    if orc is not None:
-        u = [p[k].cpu().numpy().astype(np.float64) for k in ("ux", "uy", "uz")]
-        orc.set_particles(0, cell % w["nx"] + fx, cell // w["nx"] + fz, *u)
+    run = diff.DiffRun(w, o.D, o.r0, None, every)
+    for s in range(run.sim.nspecies):
+        p = run.sim.get_particles(s)
+        cell = p["cell"].cpu().numpy().astype(np.int64)
+        fx = p["fx"].cpu().numpy().astype(np.float64)
+        fz = p["fz"].cpu().numpy().astype(np.float64)
+        if grid:
+            fx = np.minimum(np.round(fx * 65536) / 65536, 65535 / 65536)
+            fz = np.minimum(np.round(fz * 65536) / 65536, 65535 / 65536)
+            u = [p[k].cpu().numpy() for k in ("ux", "uy", "uz")]
+            run.sim.set_particles(s, cell.astype(np.int32), fx.astype(np.float32), fz.astype(np.float32), *u)
+        if orc is not None:
+            u = [p[k].cpu().numpy().astype(np.float64) for k in ("ux", "uy", "uz")]
+            orc.set_particles(s, cell % w["nx"] + fx, cell // w["nx"] + fz, *u)
     wt = torch.tensor(_weights(w), dtype=torch.float64, device="cuda")
     L = run.forward(nsteps, wt, kin)
-    gD, gR = run.backward(wt, kin)
+    gD, gR, gI = run.backward(wt, kin)
     run.close()
-    return L, gD, gR
+    return (L, gD, gR, gI) if full else (L, gD, gR)
 
 
 def _both(gb, w, nsteps, kin, every=7, grid=True):
@@ -167,10 +168,77 @@ def test_autograd_function(gb):
 
 
 def test_adjoint_refuses_other_modes(gb):
-    sim = gb.Simulation(workload("tiny"))
-    n = 8
-    buf = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    """With the cell sort on (the particle order changes) the adjoint is refused before any launch."""
+    import ctypes
+    sim = gb.Simulation(workload("tiny"), sort_every=5)
+    b = gb.pic_adjoint_buffers()
     lib = gb.load_library()
-    p = buf.data_ptr()
-    assert lib.pic_adjoint_step(sim.h, p, p + 8 * n, p + 16 * n, p + 32 * n) == gb.PIC_ESTATE
+    assert lib.pic_adjoint_step(sim.h, ctypes.byref(b)) == gb.PIC_ESTATE
     sim.close()
+
+
+# ---- full cycle (ions, electrons, fields, laser) --------------------------------------------
+
+def small_full(**kw):
+    d = dict(nx=12, nz=14, slab_k=8, ppc_ion=2, ppc_electron=2, laser_profile=1, I0=1e18,
+             t_peak=10 * 2.24e-17, T_electron_eV=5.0, seed=21)
+    d.update(kw)
+    return workload("tiny", **d)
+
+
+def _both_full(gb, w, nsteps, kin, every=7):
+    o = oracle.Oracle(w, with_particles=False)
+    g = _gpu_grad(gb, w, nsteps, kin, every, grid=True, orc=o, full=True)
+    return g, o.full_grad(nsteps, _weights(w), kin)
+
+
+def test_full_seed_only(gb):
+    (L, gD, gR, gI), (Lo, gDo, gRo, gIo) = _both_full(gb, small_full(), 0, 0.0)
+    assert rel(L, Lo) < 1e-12 and rel(gR, gRo) < 1e-12
+    assert gD == gDo == 0.0 and gI == gIo == 0.0
+
+
+@pytest.mark.parametrize("kin", [0.0, 1e-3])
+@pytest.mark.parametrize("nsteps", [1, 6, 12])
+def test_full_cycle_gradient_matches_oracle(gb, kin, nsteps):
+    """Same initial state on the deposition grid; the GPU runs the fixed-point FP32 cycle forward
+    and the FP64 adjoint kernels backward, the oracle the continuous FP64 cycle and its exact
+    reverse sweep. The I0 derivative is that of a ~1e-5 share of the kinetic energy (the pulse
+    against 5 eV electrons), so the forward's FP32 and fixed-point rounding shows more there."""
+    (L, gD, gR, gI), (Lo, gDo, gRo, gIo) = _both_full(gb, small_full(), nsteps, kin)
+    assert rel(L, Lo) < 1e-4
+    assert rel(gD, gDo) < 3e-4 and rel(gR, gRo) < 2e-4
+    if gIo != 0.0:
+        assert rel(gI, gIo) < 2e-2
+
+
+def test_full_cycle_intensity_gradient_cold_electrons(gb):
+    """Cold electrons (0.01 eV) in a stronger pulse: the absorbed energy is the pulse's, and its
+    I0 derivative follows the oracle closely."""
+    w = small_full(T_electron_eV=0.01, I0=1e19)
+    (L, gD, gR, gI), (Lo, gDo, gRo, gIo) = _both_full(gb, w, 12, 1e-3)
+    assert gIo > 0.0
+    assert rel(L, Lo) < 1e-4 and rel(gI, gIo) < 2e-3
+
+
+def test_full_cycle_checkpoint_interval_invariance(gb):
+    w = small_full()
+    res = [_gpu_grad(gb, w, 12, 1e-3, every, full=True) for every in (1, 5, 12)]
+    for r in res[1:]:
+        assert r[0] == res[0][0]
+        for q in (1, 2, 3):
+            assert rel(r[q], res[0][q]) < 1e-11
+
+
+def test_full_cycle_autograd(gb):
+    from paper_1502_07722_gb300 import diff
+    w = small_full()
+    o = oracle.Oracle(w, with_particles=False)
+    D = torch.tensor(o.D, dtype=torch.float64, requires_grad=True)
+    r0 = torch.tensor(o.r0, dtype=torch.float64, requires_grad=True)
+    I0 = torch.tensor(w["I0"], dtype=torch.float64, requires_grad=True)
+    wt = torch.tensor(_weights(w), dtype=torch.float64, device="cuda")
+    L = diff.pic_loss(D, r0, I0, w, 8, wt, 1e-3, 3)
+    L.backward()
+    _, gD, gR, gI = _gpu_grad(gb, w, 8, 1e-3, 4, full=True)
+    assert rel(D.grad.item(), gD) < 1e-11 and rel(r0.grad.item(), gR) < 1e-11 and rel(I0.grad.item(), gI) < 1e-11
