@@ -243,7 +243,8 @@ def run_batched(args, world, rank, dist, gb):
 
 
 def run_differentiable(args, world, rank, dist, gb):
-    """The differentiable form on the 512^2-cell workload (16 + 16 ppc, 3e13 W/cm^2): K forward
+    """The differentiable form on the 512^2-cell workload (16 + 16 ppc, 3e13 W/cm^2, slab of 448
+    rows): K forward
     steps with a device checkpoint every 20 steps, then the reverse pass (segment replay and the
     adjoint kernels) giving dL/dD, dL/dr0, dL/dI0 of L = smooth crater depth + 1e-3 x absorbed
     energy. A step is one forward plus one reverse step; the plain forward of the same run is
@@ -298,16 +299,16 @@ def run_differentiable(args, world, rank, dist, gb):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     nodes = (w["nz"] + 1) * w["nx"]
-    # adjoint step, algorithmic bytes: per particle the FP32 state read (24 B) and the FP64
-    # adjoints read and written (2 x 40 B); per node 6 FP32 fields read, 9 FP64 field adjoints
-    # read and written, 3 FP64 current adjoints written and read, density and its adjoint
-    alg = 104 * n_local + (24 + 144 + 48 + 8 + 16) * nodes
+    # adjoint step, algorithmic bytes: per particle the FP32 state read (24 B) and the FP32
+    # adjoints read and written (2 x 20 B); per node 6 FP32 fields read, 9 FP64 field adjoints
+    # read and written, 3 FP32 current adjoints written and read, density and its adjoint
+    alg = 64 * n_local + (24 + 144 + 24 + 8 + 16) * nodes
     peak, peak_kind = peaks()
     if rank == 0:
         line = {
             "metric": METRIC, "value": n_local * world * args.steps / (ms_max * 1e-3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 forward, f64 adjoint",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (adjoint: f32 per particle, f64 node and parameter sums)",
             "data": "synthetic copper slab (seeded Maxwellian start)",
             "config": {"workload": args.workload, "form": "differentiable (forward + reverse per step)",
                        "nx": w["nx"], "nz": w["nz"], "ppc": [w["ppc_ion"], w["ppc_electron"]],
@@ -365,7 +366,7 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args, world, rank, dist, gb)
-    if args.workload == "diff512":
+    if args.workload == "differentiable":
         return run_differentiable(args, world, rank, dist, gb)
     w = workload(args.workload, seed=workload(args.workload)["seed"] + 1000 * rank)
     stream = torch.cuda.Stream()

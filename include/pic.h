@@ -264,13 +264,15 @@ PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
  * differentiated as the continuous linear shape. The paper has no adjoint; the method, the
  * parameters and the stage are the paper's.
  *
- * Adjoint buffers (device, caller-owned, double):
- *   lam_pos[s]: 2 n_s, (x, z) adjoints per particle of species s, in the context's particle order;
- *   lam_u[s]:   3 n_s;
- *   lam_nodes:  (nz+1) nx scratch;
- *   lam_F:      9 (nz+1) nx: adjoints of Ex Ey Ez Bx By Bz and three scratch grids (FULL only);
- *   lam_j:      3 (nz+1) nx scratch (FULL only);
- *   grads:      3, accumulated by pic_adjoint_step: dL/dD (1/J), dL/dr0 (1/m), dL/dI0 (m^2/W).
+ * Adjoint buffers (device, caller-owned). Per-particle adjoints are FP32 (the precision of the push),
+ * node adjoints and parameter derivatives FP64:
+ *   lam_pos[s]: float, 2 n_s, (x, z) adjoints per particle of species s (per cell), in the
+ *               context's particle order;
+ *   lam_u[s]:   float, 3 n_s;
+ *   lam_nodes:  double, (nz+1) nx scratch;
+ *   lam_F:      double, 9 (nz+1) nx: adjoints of Ex Ey Ez Bx By Bz and three scratch grids (FULL only);
+ *   lam_j:      float, 3 (nz+1) nx scratch (FULL only);
+ *   grads:      double, 3, accumulated by pic_adjoint_step: dL/dD (1/J), dL/dr0 (1/m), dL/dI0 (m^2/W).
  * Unused pointers (second species, FULL-only buffers in transport mode) may be NULL.
  *
  * pic_node_functional: *host_out = sum_nodes w n/n0 at the current state (w: device double
@@ -282,11 +284,11 @@ PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
  *   adjoints of step t+1 to step t in place and add this step's parameter derivatives to grads.
  * Both return PIC_ESTATE outside 2D, sort_every = 0 and pot_mode 0. */
 typedef struct {
-    double* lam_pos[2];
-    double* lam_u[2];
+    float* lam_pos[2];
+    float* lam_u[2];
     double* lam_nodes;
     double* lam_F;
-    double* lam_j;
+    float* lam_j;
     double* grads;
 } pic_adjoint_buffers;
 

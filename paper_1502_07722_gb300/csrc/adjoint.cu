@@ -2,76 +2,132 @@
 // respect to the pair-potential parameters D and r0 (r0 sets Eq. (3)'s equilibrium distance, the
 // r0/dx of Eq. (1), and the density unit n0 = r0^-3) and, with fields, the laser peak intensity.
 //
+// Precision: the per-particle transposes run in FP32 (the precision of the forward push); node
+// adjoints are accumulated in FP64 (atomics from many particles), the Maxwell transpose runs in
+// FP64 on the nodes, and the parameter derivatives are summed in FP64. The deposition is
+// differentiated as the continuous linear shape (straight-through on the fixed point). Node
+// density differences are taken exactly in integers before scaling.
+//
 // Part 1: the atomic-transport stage (neutral atoms, pair force only; paper: the transport
 // simulation evolves the target with the pair potential).
-//
 // Forward step (per atom): node density n(x) -> gather (n, dn/dxi, dn/dzeta) -> force F(n, q) of
 // Eqs. (1)-(3) -> u += F dt / (m c) -> x += c dt u / (gamma dx) -> wall mirror.
-// The adjoint treats the fixed-point deposition as the continuous linear shape (straight-through)
-// and runs in FP64. One reverse step (adjoint kernels A and B) maps the adjoints of
-// (x^(t+1), u^(t+1)) to those of (x^t, u^t) and accumulates the parameter gradients:
+// One reverse step (kernels A and B) maps the adjoints of (x^(t+1), u^(t+1)) to those of
+// (x^t, u^t) and accumulates the parameter gradients:
 //   A: per atom -- transpose of the position update and of the kick, force derivatives, the
-//      gather's position derivatives, and the gather's transpose onto the nodes (FP64 atomics);
+//      gather's position derivatives, and the gather's transpose onto the nodes;
 //   B: per atom -- transpose of the deposition: the node adjoints' interpolated gradient.
 #include "pic_device.cuh"
 
 namespace gbpic {
 
-struct AdjArgs {
-    int nx, nz;
-    unsigned nx_magic;
-    int64_t n;
-    const int32_t* cell;
-    const float *fx, *fz, *ux, *uy, *uz;
-    const u64* rho;        // fixed-point node sums at the current positions
-    double rho_s;          // node sum -> n / n0
-    double unit;           // one atom's full weight on a node, in units of n0 (rho_s * 2^32)
-    double D, r0, dx, kick, cs0;   // kick = dt / (m c); cs0 = c dt / dx
-    double* lam_pos;       // 2 n: (x, z) adjoints, per cell
-    double* lam_u;         // 3 n
-    double* lam_nodes;     // (nz + 1) nx node adjoints (units 1 / n0)
-    double* grads;         // 2: dL/dD, dL/dr0
+// ---- pair force of one axis and its derivatives, Eqs. (1)-(3) -----------------------------------
+// With c = n^(1/3) (n in units of n0) and h = g/2 = -(1/6)(r0/dx) n^(-4/3) q, the neighbours sit at
+// 1/(c(1-h)) and 1/(c(1+h)) (units of r0), and
+//   F = (D/r0) [U'(a) - U'(b)] = 12 (D/r0) c^7 (c^6 P13(h) - P7(h)),
+//   P_m(h) = (1+h)^m - (1-h)^m (odd polynomials, written out), which has no cancellation between
+// the two neighbours' terms; for |h| >= 1 a neighbour is at infinity and the terms are separate.
+struct PairD {
+    float F, dn, dq, dr0;   // force (N) and dF/dn, dF/dq (fixed n, q), dF/dr0 (fixed n, q)
 };
 
-__device__ __forceinline__ double node_n(const AdjArgs& a, int i, int k)
+__device__ __forceinline__ PairD pair_axis_d(float n, float q, float r0_dx, float fu, float inv_r0)
 {
-    const long long v = (long long)a.rho[(size_t)k * a.nx + i];
-    return a.rho_s * (double)((k == 0 || k == a.nz) ? 2 * v : v);
+    PairD o = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (!(n > 0.0f)) return o;
+    const float c = cbrtf(n);
+    const float inc = 1.0f / (n * c);                       // n^(-4/3)
+    const float h = -(1.0f / 6.0f) * r0_dx * q * inc;
+    const float c2 = c * c, c6 = c2 * c2 * c2, c7 = c6 * c;
+    float F, dFdc, dFdh;
+    if (fabsf(h) < 1.0f) {
+        const float h2 = h * h;
+        const float P7 = 2.0f * h * (7.0f + h2 * (35.0f + h2 * (21.0f + h2)));
+        const float P13 = 2.0f * h * (13.0f + h2 * (286.0f + h2 * (1287.0f + h2 * (1716.0f + h2 * (715.0f + h2 * (78.0f + h2))))));
+        const float D7 = 14.0f * (1.0f + h2 * (15.0f + h2 * (15.0f + h2)));
+        const float D13 = 26.0f * (1.0f + h2 * (66.0f + h2 * (495.0f + h2 * (924.0f + h2 * (495.0f + h2 * (66.0f + h2))))));
+        F = 12.0f * fu * c7 * (c6 * P13 - P7);
+        dFdc = 12.0f * fu * c6 * (13.0f * c6 * P13 - 7.0f * P7);
+        dFdh = 12.0f * fu * c7 * (c6 * D13 - D7);
+    } else {
+        F = dFdc = dFdh = 0.0f;
+        if (1.0f - h > 0.0f) {
+            const float ia = c * (1.0f - h), i2 = ia * ia, i6 = i2 * i2 * i2;
+            const float d = 12.0f * fu * i6 * (7.0f - 13.0f * i6);    // (D/r0) dU'(a)/d(1/a)
+            F += 12.0f * fu * i6 * ia * (1.0f - i6);
+            dFdc += d * (1.0f - h);
+            dFdh -= d * c;
+        }
+        if (1.0f + h > 0.0f) {
+            const float ib = c * (1.0f + h), i2 = ib * ib, i6 = i2 * i2 * i2;
+            const float d = 12.0f * fu * i6 * (7.0f - 13.0f * i6);
+            F -= 12.0f * fu * i6 * ib * (1.0f - i6);
+            dFdc -= d * (1.0f + h);
+            dFdh -= d * c;
+        }
+    }
+    const float inv_n = 1.0f / n;
+    o.F = F;
+    o.dn = dFdc * c * (1.0f / 3.0f) * inv_n - dFdh * (4.0f / 3.0f) * h * inv_n;
+    o.dq = -dFdh * (1.0f / 6.0f) * r0_dx * inc;
+    o.dr0 = (dFdh * h - F) * inv_r0;
+    return o;
 }
 
-// F (N) and partial derivatives along one axis from (n, q), Eqs. (1)-(3)
-__device__ __forceinline__ double axis_force_d(double n, double q, double D, double r0, double dx, double& dFdn,
-                                               double& dFdq, double& dFdr0)
+// the pair-species density around a particle: bilinear value, exact edge differences, and the
+// pieces the transpose needs
+struct DensAt {
+    float n, qx, qz, gxz, fx, fz;
+    int i, i1, k;
+};
+
+__device__ __forceinline__ long long node_sum(const u64* rho, int nx, int nz, int i, int k)
 {
-    dFdn = dFdq = dFdr0 = 0.0;
-    if (!(n > 0.0)) return 0.0;
-    const double c = cbrt(n);                     // n^(1/3)
-    const double rbar = 1.0 / c;
-    const double n43 = 1.0 / (n * c);             // n^(-4/3)
-    const double h = -(1.0 / 6.0) * (r0 / dx) * n43 * q;
-    const double drbar_dn = -(1.0 / 3.0) * n43;
-    const double dh_dn = (2.0 / 9.0) * (r0 / dx) * n43 / n * q;
-    const double dh_dq = -(1.0 / 6.0) * (r0 / dx) * n43;
-    const double fu = D / r0;
-    double F = 0.0, dF_drbar = 0.0, dF_dh = 0.0;
-    if (1.0 - h > 0.0) {
-        const double ia = c * (1.0 - h), i2 = ia * ia, i6 = i2 * i2 * i2, i7 = i6 * ia, i8 = i6 * i2;
-        const double up = 12.0 * i7 * (1.0 - i6), upp = i8 * (156.0 * i6 - 84.0);
-        F += fu * up;
-        dF_drbar += fu * upp / (1.0 - h);
-        dF_dh += fu * upp * rbar / ((1.0 - h) * (1.0 - h));
-    }
-    if (1.0 + h > 0.0) {
-        const double ib = c * (1.0 + h), i2 = ib * ib, i6 = i2 * i2 * i2, i7 = i6 * ib, i8 = i6 * i2;
-        const double up = 12.0 * i7 * (1.0 - i6), upp = i8 * (156.0 * i6 - 84.0);
-        F -= fu * up;
-        dF_drbar -= fu * upp / (1.0 + h);
-        dF_dh += fu * upp * rbar / ((1.0 + h) * (1.0 + h));
-    }
-    dFdn = dF_drbar * drbar_dn + dF_dh * dh_dn;
-    dFdq = dF_dh * dh_dq;
-    dFdr0 = -F / r0 + dF_dh * h / r0;
-    return F;
+    const long long v = (long long)rho[(size_t)k * nx + i];
+    return (k == 0 || k == nz) ? 2 * v : v;
+}
+
+__device__ __forceinline__ DensAt dens_at(const u64* rho, float rho_s, int nx, int nz, int ci, int ck, float fx,
+                                          float fz)
+{
+    DensAt d;
+    if (ck >= nz) { ck = nz - 1; fz = 1.0f; }
+    d.i = ci;
+    d.i1 = ci + 1 == nx ? 0 : ci + 1;
+    d.k = ck;
+    d.fx = fx;
+    d.fz = fz;
+    const long long N00 = node_sum(rho, nx, nz, d.i, ck), N10 = node_sum(rho, nx, nz, d.i1, ck);
+    const long long N01 = node_sum(rho, nx, nz, d.i, ck + 1), N11 = node_sum(rho, nx, nz, d.i1, ck + 1);
+    const float n00 = rho_s * (float)N00, n10 = rho_s * (float)N10, n01 = rho_s * (float)N01, n11 = rho_s * (float)N11;
+    d.n = (1 - fx) * (1 - fz) * n00 + fx * (1 - fz) * n10 + (1 - fx) * fz * n01 + fx * fz * n11;
+    const float ex0 = rho_s * (float)(N10 - N00), ex1 = rho_s * (float)(N11 - N01);
+    const float ez0 = rho_s * (float)(N01 - N00), ez1 = rho_s * (float)(N11 - N10);
+    d.qx = (1 - fz) * ex0 + fz * ex1;
+    d.qz = (1 - fx) * ez0 + fx * ez1;
+    d.gxz = rho_s * (float)(N11 - N01 - N10 + N00);
+    return d;
+}
+
+// transpose of the pair force given the adjoints of (Fx, Fz): position adjoints (added to lx, lz),
+// node adjoints (FP64 atomics), and the D, r0 derivative terms (gFF += lF . F, gR += dL/dr0 part)
+__device__ __forceinline__ void pair_T(const DensAt& d, const PairD& px, const PairD& pz, float lFx, float lFz,
+                                       float inv_r0, int nx, double* lam_nodes, float& lx, float& lz, double& gFF,
+                                       double& gR)
+{
+    gFF += (double)(lFx * px.F + lFz * pz.F);
+    gR += (double)(lFx * (px.dr0 + 3.0f * inv_r0 * (px.dn * d.n + px.dq * d.qx)) +
+                   lFz * (pz.dr0 + 3.0f * inv_r0 * (pz.dn * d.n + pz.dq * d.qz)));
+    const float ln = lFx * px.dn + lFz * pz.dn, lqx = lFx * px.dq, lqz = lFz * pz.dq;
+    lx += ln * d.qx + lqz * d.gxz;
+    lz += ln * d.qz + lqx * d.gxz;
+    const float fx = d.fx, fz = d.fz;
+    double* L0 = lam_nodes + (size_t)d.k * nx;
+    double* L1 = L0 + nx;
+    atomicAdd(L0 + d.i, (double)(ln * (1 - fx) * (1 - fz) - lqx * (1 - fz) - lqz * (1 - fx)));
+    atomicAdd(L0 + d.i1, (double)(ln * fx * (1 - fz) + lqx * (1 - fz) - lqz * fx));
+    atomicAdd(L1 + d.i, (double)(ln * (1 - fx) * fz - lqx * fz + lqz * (1 - fx)));
+    atomicAdd(L1 + d.i1, (double)(ln * fx * fz + lqx * fz + lqz * fx));
 }
 
 __device__ __forceinline__ void split2(int cell, int nx, unsigned magic, int& i, int& k)
@@ -96,59 +152,59 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh)
     return r;
 }
 
+struct AdjArgs {
+    int nx, nz;
+    unsigned nx_magic;
+    int64_t n;
+    const int32_t* cell;
+    const float *fx, *fz, *ux, *uy, *uz;
+    const u64* rho;        // fixed-point node sums at the current positions
+    double rho_s;          // node sum -> n / n0
+    double unit;           // one particle's full weight on a node, in units of n0 (rho_s * 2^32)
+    double D, r0, dx, kick, cs0;   // kick = dt / (m c); cs0 = c dt / dx
+    float* lam_pos;        // 2 n: (x, z) adjoints
+    float* lam_u;          // 3 n
+    double* lam_nodes;     // (nz + 1) nx node adjoints (units 1 / n0)
+    double* grads;         // 3: dL/dD, dL/dr0, dL/dI0
+};
+
 __global__ void __launch_bounds__(256) k_adjoint_a(const AdjArgs a)
 {
     __shared__ double sh[256];
-    double gD = 0.0, gR = 0.0;
+    double gFF = 0.0, gR = 0.0;
+    const float r0_dx = (float)(a.r0 / a.dx), fu = (float)(a.D / a.r0), inv_r0 = (float)(1.0 / a.r0);
+    const float rho_s = (float)a.rho_s, kick = (float)a.kick, cs0 = (float)a.cs0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-        int i, k;
-        split2(a.cell[p], a.nx, a.nx_magic, i, k);
-        double fx = a.fx[p], fz = a.fz[p];
-        if (k >= a.nz) { k = a.nz - 1; fz = 1.0; }
-        const int i1 = i + 1 == a.nx ? 0 : i + 1;
-        const double n00 = node_n(a, i, k), n10 = node_n(a, i1, k), n01 = node_n(a, i, k + 1), n11 = node_n(a, i1, k + 1);
-        const double n = (1 - fx) * (1 - fz) * n00 + fx * (1 - fz) * n10 + (1 - fx) * fz * n01 + fx * fz * n11;
-        const double qx = (1 - fz) * (n10 - n00) + fz * (n11 - n01);
-        const double qz = (1 - fx) * (n01 - n00) + fx * (n11 - n10);
-        const double gxz = n11 - n01 - n10 + n00;
-        double dxn, dxq, dxr, dzn, dzq, dzr;
-        const double Fx = axis_force_d(n, qx, a.D, a.r0, a.dx, dxn, dxq, dxr);
-        const double Fz = axis_force_d(n, qz, a.D, a.r0, a.dx, dzn, dzq, dzr);
+        int ci, ck;
+        split2(a.cell[p], a.nx, a.nx_magic, ci, ck);
+        const float fx = a.fx[p], fz = a.fz[p];
+        const DensAt d = dens_at(a.rho, rho_s, a.nx, a.nz, ci, ck, fx, fz);
+        const PairD px = pair_axis_d(d.n, d.qx, r0_dx, fu, inv_r0), pz = pair_axis_d(d.n, d.qz, r0_dx, fu, inv_r0);
         // forward quantities of this step: kicked momentum (before the wall mirror), move
-        const double ux = (double)a.ux[p] + a.kick * Fx, uy = (double)a.uy[p], uz = (double)a.uz[p] + a.kick * Fz;
-        const double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz), cs = a.cs0 / g;
-        const double zn = (double)k + fz + uz * cs;
-        const bool refl = zn < 0.0 || zn >= (double)a.nz;
-        double lpx = a.lam_pos[2 * p], lpz = a.lam_pos[2 * p + 1];
-        double lux = a.lam_u[3 * p], luy = a.lam_u[3 * p + 1], luz = a.lam_u[3 * p + 2];
+        const float ux = a.ux[p] + kick * px.F, uy = a.uy[p], uz = a.uz[p] + kick * pz.F;
+        const float g = sqrtf(1.0f + ux * ux + uy * uy + uz * uz), cs = cs0 / g;
+        const float zl = fz + uz * cs;
+        const bool refl = (ck == 0 && zl < 0.0f) || (ck == a.nz - 1 && zl >= 1.0f);
+        float lpx = a.lam_pos[2 * p], lpz = a.lam_pos[2 * p + 1];
+        float lux = a.lam_u[3 * p], luy = a.lam_u[3 * p + 1], luz = a.lam_u[3 * p + 2];
         if (refl) { lpz = -lpz; luz = -luz; }
         // position update x' = x + cs u: dx'/du = cs (I - u u^T / gamma^2)
-        const double udl = (ux * lpx + uz * lpz) / (g * g);
+        const float udl = (ux * lpx + uz * lpz) / (g * g);
         lux += cs * (lpx - ux * udl);
-        luy += cs * (0.0 - uy * udl);
+        luy += cs * (0.0f - uy * udl);
         luz += cs * (lpz - uz * udl);
         // kick u' = u + kick F
-        const double lFx = a.kick * lux, lFz = a.kick * luz;
-        gD += (lFx * Fx + lFz * Fz) / a.D;
-        gR += lFx * (dxr + dxn * 3.0 * n / a.r0 + dxq * 3.0 * qx / a.r0) +
-              lFz * (dzr + dzn * 3.0 * n / a.r0 + dzq * 3.0 * qz / a.r0);
-        const double ln = lFx * dxn + lFz * dzn, lqx = lFx * dxq, lqz = lFz * dzq;
-        a.lam_pos[2 * p] = lpx + ln * qx + lqz * gxz;
-        a.lam_pos[2 * p + 1] = lpz + ln * qz + lqx * gxz;
+        float lx = lpx, lz = lpz;
+        pair_T(d, px, pz, kick * lux, kick * luz, inv_r0, a.nx, a.lam_nodes, lx, lz, gFF, gR);
+        a.lam_pos[2 * p] = lx;
+        a.lam_pos[2 * p + 1] = lz;
         a.lam_u[3 * p] = lux;
         a.lam_u[3 * p + 1] = luy;
         a.lam_u[3 * p + 2] = luz;
-        // transpose of the gather onto the four corners
-        double* L0 = a.lam_nodes + (size_t)k * a.nx;
-        double* L1 = L0 + a.nx;
-        atomicAdd(L0 + i, ln * (1 - fx) * (1 - fz) - lqx * (1 - fz) - lqz * (1 - fx));
-        atomicAdd(L0 + i1, ln * fx * (1 - fz) + lqx * (1 - fz) - lqz * fx);
-        atomicAdd(L1 + i, ln * (1 - fx) * fz - lqx * fz + lqz * (1 - fx));
-        atomicAdd(L1 + i1, ln * fx * fz + lqx * fz + lqz * fx);
     }
-    const double sD = block_sum_d(gD, sh), sR = block_sum_d(gR, sh);
+    const double sD = block_sum_d(gFF, sh), sR = block_sum_d(gR, sh);
     if (threadIdx.x == 0) {
-        atomicAdd(a.grads, sD);
+        atomicAdd(a.grads, sD / a.D);
         atomicAdd(a.grads + 1, sR);
     }
 }
@@ -159,36 +215,40 @@ __global__ void k_adjoint_b(const AdjArgs a)
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
         int i, k;
         split2(a.cell[p], a.nx, a.nx_magic, i, k);
-        double fx = a.fx[p], fz = a.fz[p];
-        if (k >= a.nz) { k = a.nz - 1; fz = 1.0; }
+        float fx = a.fx[p], fz = a.fz[p];
+        if (k >= a.nz) { k = a.nz - 1; fz = 1.0f; }
         const int i1 = i + 1 == a.nx ? 0 : i + 1;
         const double m0 = k == 0 ? 2.0 : 1.0, m1 = k + 1 == a.nz ? 2.0 : 1.0;
         const double* L0 = a.lam_nodes + (size_t)k * a.nx;
         const double* L1 = L0 + a.nx;
         const double l00 = m0 * L0[i], l10 = m0 * L0[i1], l01 = m1 * L1[i], l11 = m1 * L1[i1];
-        a.lam_pos[2 * p] += a.unit * ((1 - fz) * (l10 - l00) + fz * (l11 - l01));
-        a.lam_pos[2 * p + 1] += a.unit * ((1 - fx) * (l01 - l00) + fx * (l11 - l10));
+        const float u = (float)a.unit;
+        const float ex0 = (float)(l10 - l00), ex1 = (float)(l11 - l01), ez0 = (float)(l01 - l00), ez1 = (float)(l11 - l10);
+        a.lam_pos[2 * p] += u * ((1 - fz) * ex0 + fz * ex1);
+        a.lam_pos[2 * p + 1] += u * ((1 - fx) * ez0 + fx * ez1);
     }
 }
 
-// seed: lam_u = kin * w m c^2 u / gamma; sum of lam_nodes * 3 n / r0 (the density unit's r0 dependence)
+// seed: lam_u = kin * w m c^2 u / gamma (lam_pos = 0); sum of lam_nodes * 3 n / r0 (the density
+// unit's r0 dependence)
 __global__ void __launch_bounds__(256) k_adjoint_seed(const AdjArgs a, double kin_mc2w, const double* w_nodes,
                                                       int64_t nn, double* r0_out)
 {
     __shared__ double sh[256];
     double acc = 0.0;
+    const float kw = (float)kin_mc2w;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-        const double ux = a.ux[p], uy = a.uy[p], uz = a.uz[p];
-        const double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
-        a.lam_u[3 * p] = kin_mc2w * ux / g;
-        a.lam_u[3 * p + 1] = kin_mc2w * uy / g;
-        a.lam_u[3 * p + 2] = kin_mc2w * uz / g;
-        a.lam_pos[2 * p] = 0.0;
-        a.lam_pos[2 * p + 1] = 0.0;
+        const float ux = a.ux[p], uy = a.uy[p], uz = a.uz[p];
+        const float ig = kw / sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        a.lam_u[3 * p] = ig * ux;
+        a.lam_u[3 * p + 1] = ig * uy;
+        a.lam_u[3 * p + 2] = ig * uz;
+        a.lam_pos[2 * p] = 0.0f;
+        a.lam_pos[2 * p + 1] = 0.0f;
     }
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nn; c += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(c / a.nx), i = (int)(c - (int64_t)k * a.nx);
-        acc += w_nodes[c] * 3.0 * node_n(a, i, k) / a.r0;
+        acc += w_nodes[c] * 3.0 * a.rho_s * (double)node_sum(a.rho, a.nx, a.nz, i, k) / a.r0;
     }
     const double s = block_sum_d(acc, sh);
     if (threadIdx.x == 0) atomicAdd(r0_out, s);
@@ -209,13 +269,13 @@ __global__ void __launch_bounds__(256) k_node_functional(const u64* rho, int nx,
     if (threadIdx.x == 0) atomicAdd(out, s);
 }
 
-static AdjArgs make_adj(Ctx& c, double* lam_pos, double* lam_u, double* lam_nodes, double* grads)
+static AdjArgs make_adj(Ctx& c, int s, float* lam_pos, float* lam_u, double* lam_nodes, double* grads)
 {
     AdjArgs a;
     a.nx = c.nx;
     a.nz = c.nz;
     a.nx_magic = (unsigned)(4294967296ULL / (unsigned long long)c.nx);
-    const Species& S = c.sp[0];
+    const Species& S = c.sp[s];
     a.n = S.n;
     a.cell = S.a.cell;
     a.fx = S.a.fx;
@@ -245,21 +305,28 @@ static int agrid(const Ctx& c, int64_t n)
     return g < 1 ? 1 : (int)g;
 }
 
-void launch_adjoint_seed(Ctx& c, double kin, const double* w_nodes, double* lam_pos, double* lam_u, double* lam_nodes,
-                         double* r0_out, cudaStream_t st)
+// seed of the pair species: momenta (kin), the final density functional's position adjoints and
+// its r0 term
+static void seed_pair_species(Ctx& c, double kin, const double* w_nodes, float* lam_pos, float* lam_u,
+                              double* lam_nodes, double* r0_out, cudaStream_t st)
 {
-    AdjArgs a = make_adj(c, lam_pos, lam_u, lam_nodes, nullptr);
+    AdjArgs a = make_adj(c, 0, lam_pos, lam_u, lam_nodes, nullptr);
     const int64_t nn = (int64_t)c.nn;
     k_adjoint_seed<<<agrid(c, a.n > nn ? a.n : nn), 256, 0, st>>>(a, kin * c.w * c.sp[0].mass * kC * kC, w_nodes, nn,
                                                                    r0_out);
-    // the final node density's dependence on the positions
     cudaMemcpyAsync(lam_nodes, w_nodes, sizeof(double) * c.nn, cudaMemcpyDeviceToDevice, st);
     k_adjoint_b<<<agrid(c, a.n), 256, 0, st>>>(a);
 }
 
-void launch_adjoint_step(Ctx& c, double* lam_pos, double* lam_u, double* lam_nodes, double* grads, cudaStream_t st)
+void launch_adjoint_seed(Ctx& c, double kin, const double* w_nodes, float* lam_pos, float* lam_u, double* lam_nodes,
+                         double* r0_out, cudaStream_t st)
 {
-    AdjArgs a = make_adj(c, lam_pos, lam_u, lam_nodes, grads);
+    seed_pair_species(c, kin, w_nodes, lam_pos, lam_u, lam_nodes, r0_out, st);
+}
+
+void launch_adjoint_step(Ctx& c, float* lam_pos, float* lam_u, double* lam_nodes, double* grads, cudaStream_t st)
+{
+    AdjArgs a = make_adj(c, 0, lam_pos, lam_u, lam_nodes, grads);
     cudaMemsetAsync(lam_nodes, 0, sizeof(double) * c.nn, st);
     k_adjoint_a<<<agrid(c, a.n), 256, 0, st>>>(a);
     k_adjoint_b<<<agrid(c, a.n), 256, 0, st>>>(a);
@@ -272,7 +339,6 @@ void launch_node_functional(Ctx& c, const double* w_nodes, double* dev_out, cuda
                                                                 (int64_t)c.nn, dev_out);
 }
 
-
 // ==============================================================================================
 // Part 2: the full cycle (ions, electrons, Yee fields, laser antenna). Forward step t:
 //   n^ = dens(ions); per particle: E, B gathered (staggered bilinear), pair force (ions), Boris,
@@ -280,17 +346,16 @@ void launch_node_functional(Ctx& c, const double* w_nodes, double* dev_out, cuda
 //   Maxwell: B += H E (half), E = M(E, B, j) with Mur walls and the antenna, B += H E (half).
 // Reverse step t: Maxwell transpose (field adjoints of t+1 -> of t, current adjoints, dL/dI0),
 // then per particle the transposes of the current, move, walls, Boris, gathers and pair force,
-// then the density transpose. j is the scaled current dt J / eps0 with the deposition taken as
-// the continuous linear shape (straight-through on the fixed point).
+// then the density transpose. j is the scaled current dt J / eps0.
 // Adjoint field layout (lam_F): 9 grids of (nz + 1) nx doubles: Ex Ey Ez Bx By Bz, then three
-// scratch grids for the new E adjoints.
+// scratch grids for the new E adjoints. Current adjoints (lam_j): 3 grids of floats.
 // ==============================================================================================
 
 struct MaxAdjArgs {
     int nx, nz, k_ant;
     double hb, he, mur;        // dt / (2 dx), c^2 dt / dx, (c dt - dx) / (c dt + dx)
     double* lF;                // 9 grids
-    double* lj;                // 3 grids
+    float* lj;                 // 3 grids
     const float *antc, *ants;  // antenna tables (amplitude * cos / sin of the phase)
     AntennaParams ap;          // coef = 2 c dt / dx (per unit E0)
     long long step;
@@ -355,9 +420,9 @@ __global__ void __launch_bounds__(256) k_adj_feT(const MaxAdjArgs a)
         lBy[c] += a.he * (lnE(a, 0, i, k + 1) - lx) + (k < nz ? a.he * (lez - lF_at(a, 2, ip, k)) : 0.0);
         lBx[c] += a.he * (ly - lnE(a, 1, i, k + 1));
         lBz[c] += a.he * (lnE(a, 1, ip, k) - ly);
-        a.lj[c] = -lx;
-        a.lj[nn + c] = -ly;
-        a.lj[2 * nn + c] = k < nz ? -lez : 0.0;
+        a.lj[c] = (float)-lx;
+        a.lj[nn + c] = (float)-ly;
+        a.lj[2 * nn + c] = k < nz ? (float)-lez : 0.0f;
         if (k == a.k_ant && a.ap.on) {
             const double tau = ((double)a.step + 0.5) * a.ap.dt - a.ap.t_ant;
             const double env = exp(-2.0 * 0.6931471805599453 * tau * tau / (a.ap.tau_fwhm * a.ap.tau_fwhm));
@@ -379,72 +444,70 @@ struct FullAdjArgs {
     const float *fx, *fz, *ux, *uy, *uz;
     const float* F[6];
     const u64* rho;
-    double rho_s;
-    double D, r0, dx, dt;
-    double q, m, sg;          // charge (C), mass (kg), charge sign of the current
+    float rho_s;
+    float r0_dx, fu, inv_r0;  // r0 / dx, D / r0, 1 / r0
+    float eps, fk, tq, cs0;   // q dt / (2 m c), dt / (2 m c), q dt / (2 m), c dt / dx
+    float sg;                 // charge sign of the current
     int pair;
-    double cx, cy;            // scaled current per unit Esirkepov sum: x/z and y
-    double* lam_pos;
-    double* lam_u;
+    float cx, cy;             // scaled current per unit Esirkepov sum: x/z and y
+    float* lam_pos;
+    float* lam_u;
     double* lF;               // 6 grids (accumulated)
-    const double* lj;         // 3 grids
+    const float* lj;          // 3 grids
     double* lam_nodes;
     double* grads;
+    double inv_D;
 };
 
-__device__ __forceinline__ double hat_c(double d)
+__device__ __forceinline__ float hat_c(float d)
 {
-    const double a = fabs(d);
-    return a < 1.0 ? 1.0 - a : 0.0;
+    const float a = fabsf(d);
+    return a < 1.0f ? 1.0f - a : 0.0f;
 }
-__device__ __forceinline__ double dhat_c(double d) { return fabs(d) < 1.0 ? (d > 0.0 ? -1.0 : 1.0) : 0.0; }
+__device__ __forceinline__ float dhat_c(float d) { return fabsf(d) < 1.0f ? (d > 0.0f ? -1.0f : 1.0f) : 0.0f; }
 
-// staggered bilinear gather of a Yee component at (i + sx, k + sz) and, if lv != 0, its transpose
-__device__ __forceinline__ double gather_stag(const FullAdjArgs& a, int f, double x, double z, double sx, double sz,
-                                              double lv, double& lx, double& lz)
+// staggered bilinear gather of a Yee component at (i + sx, k + sz) for a particle at cell (ci, ck),
+// offsets (fx, fz); with lv != 0 also its transpose (node adjoints, position adjoints)
+__device__ __forceinline__ float gather_stag(const FullAdjArgs& a, int f, int ci, int ck, float fx, float fz, float sx,
+                                             float sz, float lv, float& lx, float& lz)
 {
     const int nx = a.nx, nz = a.nz;
-    const double xs = x - sx;
-    double zs = z - sz;
-    const int rows = sz > 0 ? nz : nz + 1;
+    float xs = fx - sx, fzz = fz - sz;
+    int i = ci, k = ck;
+    if (xs < 0.0f) { xs += 1.0f; i -= 1; }
+    if (fzz < 0.0f) { fzz += 1.0f; k -= 1; }
+    const int rows = sz > 0.0f ? nz : nz + 1;      // half-row components have nz rows
     bool clamped = false;
-    if (zs < 0.0) { zs = 0.0; clamped = true; }
-    if (zs > (double)(rows - 1)) { zs = (double)(rows - 1); clamped = true; }
-    int i = (int)floor(xs), k = (int)floor(zs);
-    double fx = xs - (double)i, fz = zs - (double)k;
-    if (k >= rows - 1) { k = rows - 2; fz = 1.0; }
-    const int i0 = i < 0 ? i + nx : (i >= nx ? i - nx : i);
+    if (k < 0) { k = 0; fzz = 0.0f; clamped = true; }
+    else if (k > rows - 1 || (k == rows - 1 && fzz > 0.0f)) { k = rows - 1; fzz = 0.0f; clamped = true; }
+    if (k >= rows - 1) { k = rows - 2; fzz = 1.0f; }
+    const int i0 = i < 0 ? i + nx : i;
     const int i1 = i0 + 1 == nx ? 0 : i0 + 1;
     const float* A = a.F[f];
     const size_t r0 = (size_t)k * nx, r1 = r0 + nx;
-    const double a00 = A[r0 + i0], a10 = A[r0 + i1], a01 = A[r1 + i0], a11 = A[r1 + i1];
-    if (lv != 0.0) {
+    const float a00 = A[r0 + i0], a10 = A[r0 + i1], a01 = A[r1 + i0], a11 = A[r1 + i1];
+    if (lv != 0.0f) {
         double* L = a.lF + (size_t)f * (nz + 1) * nx;
-        atomicAdd(L + r0 + i0, lv * (1 - fx) * (1 - fz));
-        atomicAdd(L + r0 + i1, lv * fx * (1 - fz));
-        atomicAdd(L + r1 + i0, lv * (1 - fx) * fz);
-        atomicAdd(L + r1 + i1, lv * fx * fz);
-        lx += lv * ((1 - fz) * (a10 - a00) + fz * (a11 - a01));
-        if (!clamped) lz += lv * ((1 - fx) * (a01 - a00) + fx * (a11 - a10));
+        atomicAdd(L + r0 + i0, (double)(lv * (1 - xs) * (1 - fzz)));
+        atomicAdd(L + r0 + i1, (double)(lv * xs * (1 - fzz)));
+        atomicAdd(L + r1 + i0, (double)(lv * (1 - xs) * fzz));
+        atomicAdd(L + r1 + i1, (double)(lv * xs * fzz));
+        lx += lv * ((1 - fzz) * (a10 - a00) + fzz * (a11 - a01));
+        if (!clamped) lz += lv * ((1 - xs) * (a01 - a00) + xs * (a11 - a10));
     }
-    return (1 - fx) * (1 - fz) * a00 + fx * (1 - fz) * a10 + (1 - fx) * fz * a01 + fx * fz * a11;
+    return (1 - xs) * (1 - fzz) * a00 + xs * (1 - fzz) * a10 + (1 - xs) * fzz * a01 + xs * fzz * a11;
 }
 
-__device__ __forceinline__ double node_n_full(const FullAdjArgs& a, int i, int k)
-{
-    const long long v = (long long)a.rho[(size_t)k * a.nx + i];
-    return a.rho_s * (double)((k == 0 || k == a.nz) ? 2 * v : v);
-}
-
-// transpose of the continuous Esirkepov current of one particle: adds d/d(x0, z0, x1, z1, by) of
-// sum lj * j into g[0..4]
-__device__ void cur_T(const FullAdjArgs& a, double x0, double z0, double x1, double z1, double by, double g[5])
+// transpose of the continuous Esirkepov current of one particle moving (x0, z0) -> (x1, z1) in
+// coordinates local to its start cell (ci, ck): adds d/d(x0, z0, x1, z1, by) of sum lj * j into g
+__device__ void cur_T(const FullAdjArgs& a, int ci, int ck, float x0, float z0, float x1, float z1, float by,
+                      float g[5])
 {
     const int nx = a.nx, nz = a.nz;
-    const double bx = floor(fmin(x0, x1)), bz = floor(fmin(z0, z1));
-    const int ib = (int)bx, kb = (int)bz;
-    double S0x[3], S1x[3], S0z[3], S1z[3];
-    double Lx[3][3], Ly[3][3], Lz[3][3];
+    const float bx = floorf(fminf(x0, x1)), bz = floorf(fminf(z0, z1));
+    const int ib = ci + (int)bx, kb = ck + (int)bz;
+    float S0x[3], S1x[3], S0z[3], S1z[3];
+    float Lx[3][3], Ly[3][3], Lz[3][3];
     const size_t nn = (size_t)(nz + 1) * nx;
 #pragma unroll
     for (int q = 0; q < 3; q++) {
@@ -461,36 +524,36 @@ __device__ void cur_T(const FullAdjArgs& a, double x0, double z0, double x1, dou
         for (int b = 0; b < 3; b++) {
             const int l = kb + b;
             const bool ok = l >= 0 && l <= nz;
-            const size_t c = (size_t)l * nx + ii;
-            Lx[ia][b] = ok ? a.lj[c] : 0.0;
-            Ly[ia][b] = ok ? a.lj[nn + c] : 0.0;
-            Lz[ia][b] = ok ? a.lj[2 * nn + c] : 0.0;
+            const size_t c = (size_t)(ok ? l : 0) * nx + ii;
+            Lx[ia][b] = ok ? a.lj[c] : 0.0f;
+            Ly[ia][b] = ok ? a.lj[nn + c] : 0.0f;
+            Lz[ia][b] = ok ? a.lj[2 * nn + c] : 0.0f;
         }
     }
-    const double cx = a.sg * a.cx, cy = a.sg * a.cy;
-    double dS0x[3] = {0, 0, 0}, dS1x[3] = {0, 0, 0}, dS0z[3] = {0, 0, 0}, dS1z[3] = {0, 0, 0};
+    const float cx = a.sg * a.cx, cy = a.sg * a.cy;
+    float dS0x[3] = {0, 0, 0}, dS1x[3] = {0, 0, 0}, dS0z[3] = {0, 0, 0}, dS1z[3] = {0, 0, 0};
 #pragma unroll
     for (int b = 0; b < 3; b++) {
-        const double Rx1 = Lx[1][b], Rx0 = Lx[0][b] + Lx[1][b], zsum = S0z[b] + S1z[b];
+        const float Rx1 = Lx[1][b], Rx0 = Lx[0][b] + Lx[1][b], zsum = S0z[b] + S1z[b];
         dS1x[0] -= cx * zsum * Rx0; dS0x[0] += cx * zsum * Rx0;
         dS1x[1] -= cx * zsum * Rx1; dS0x[1] += cx * zsum * Rx1;
-        const double zz = -cx * ((S1x[0] - S0x[0]) * Rx0 + (S1x[1] - S0x[1]) * Rx1);
+        const float zz = -cx * ((S1x[0] - S0x[0]) * Rx0 + (S1x[1] - S0x[1]) * Rx1);
         dS0z[b] += zz; dS1z[b] += zz;
     }
 #pragma unroll
     for (int ia = 0; ia < 3; ia++) {
-        const double Rz1 = Lz[ia][1], Rz0 = Lz[ia][0] + Lz[ia][1], xsum = S0x[ia] + S1x[ia];
+        const float Rz1 = Lz[ia][1], Rz0 = Lz[ia][0] + Lz[ia][1], xsum = S0x[ia] + S1x[ia];
         dS1z[0] -= cx * xsum * Rz0; dS0z[0] += cx * xsum * Rz0;
         dS1z[1] -= cx * xsum * Rz1; dS0z[1] += cx * xsum * Rz1;
-        const double xx = -cx * ((S1z[0] - S0z[0]) * Rz0 + (S1z[1] - S0z[1]) * Rz1);
+        const float xx = -cx * ((S1z[0] - S0z[0]) * Rz0 + (S1z[1] - S0z[1]) * Rz1);
         dS0x[ia] += xx; dS1x[ia] += xx;
     }
-    double gby = 0.0;
+    float gby = 0.0f;
 #pragma unroll
     for (int ia = 0; ia < 3; ia++)
 #pragma unroll
         for (int b = 0; b < 3; b++) {
-            const double L = Ly[ia][b] * cy;
+            const float L = Ly[ia][b] * cy;
             gby += L * (2 * S0x[ia] * S0z[b] + S1x[ia] * S0z[b] + S0x[ia] * S1z[b] + 2 * S1x[ia] * S1z[b]);
             dS0x[ia] += by * L * (2 * S0z[b] + S1z[b]);
             dS1x[ia] += by * L * (S0z[b] + 2 * S1z[b]);
@@ -507,93 +570,83 @@ __device__ void cur_T(const FullAdjArgs& a, double x0, double z0, double x1, dou
     g[4] += gby;
 }
 
-__device__ __constant__ double c_stag[6][2] = {{0.5, 0.0}, {0.0, 0.0}, {0.0, 0.5}, {0.0, 0.5}, {0.5, 0.5}, {0.5, 0.0}};
+__device__ __constant__ float c_stag[6][2] = {{0.5f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.5f},
+                                              {0.0f, 0.5f}, {0.5f, 0.5f}, {0.5f, 0.0f}};
 
 __global__ void __launch_bounds__(256) k_adjoint_full(const FullAdjArgs a)
 {
     __shared__ double sh[256];
-    double gD = 0.0, gR = 0.0;
+    double gFF = 0.0, gR = 0.0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
         int ci, ck;
         split2(a.cell[p], a.nx, a.nx_magic, ci, ck);
-        const double x = (double)ci + (double)a.fx[p], z = (double)ck + (double)a.fz[p];
-        // ---- forward recompute (FP64) ----
-        double E[3], B[3], dummy = 0.0;
+        const float fx = a.fx[p], fz = a.fz[p];
+        // ---- forward recompute (FP32, positions local to the cell) ----
+        float E[3], B[3], dummy = 0.0f;
 #pragma unroll
         for (int f = 0; f < 6; f++) {
-            const double v = gather_stag(a, f, x, z, c_stag[f][0], c_stag[f][1], 0.0, dummy, dummy);
+            const float v = gather_stag(a, f, ci, ck, fx, fz, c_stag[f][0], c_stag[f][1], 0.0f, dummy, dummy);
             if (f < 3) E[f] = v; else B[f - 3] = v;
         }
-        double Fp[3] = {0.0, 0.0, 0.0};
-        double n = 0, qx = 0, qz = 0, gxz = 0, dxn = 0, dxq = 0, dxr = 0, dzn = 0, dzq = 0, dzr = 0, pfx = 0, pfz = 0;
-        int pi = 0, pk = 0;
+        DensAt d = {};
+        PairD px = {0.0f, 0.0f, 0.0f, 0.0f}, pz = px;
         if (a.pair) {
-            double fx = a.fx[p], fz = a.fz[p];
-            pi = ci; pk = ck;
-            if (pk >= a.nz) { pk = a.nz - 1; fz = 1.0; }
-            const int i1 = pi + 1 == a.nx ? 0 : pi + 1;
-            const double n00 = node_n_full(a, pi, pk), n10 = node_n_full(a, i1, pk);
-            const double n01 = node_n_full(a, pi, pk + 1), n11 = node_n_full(a, i1, pk + 1);
-            n = (1 - fx) * (1 - fz) * n00 + fx * (1 - fz) * n10 + (1 - fx) * fz * n01 + fx * fz * n11;
-            qx = (1 - fz) * (n10 - n00) + fz * (n11 - n01);
-            qz = (1 - fx) * (n01 - n00) + fx * (n11 - n10);
-            gxz = n11 - n01 - n10 + n00;
-            Fp[0] = axis_force_d(n, qx, a.D, a.r0, a.dx, dxn, dxq, dxr);
-            Fp[2] = axis_force_d(n, qz, a.D, a.r0, a.dx, dzn, dzq, dzr);
-            pfx = fx; pfz = fz;
+            d = dens_at(a.rho, a.rho_s, a.nx, a.nz, ci, ck, fx, fz);
+            px = pair_axis_d(d.n, d.qx, a.r0_dx, a.fu, a.inv_r0);
+            pz = pair_axis_d(d.n, d.qz, a.r0_dx, a.fu, a.inv_r0);
         }
-        const double eps = a.q * a.dt / (2.0 * a.m * kC), fk = a.dt / (2.0 * a.m * kC);
-        double um[3], t[3], sv[3], upr[3], uf[3];
-        const double u0[3] = {(double)a.ux[p], (double)a.uy[p], (double)a.uz[p]};
+        const float Fp[3] = {px.F, 0.0f, pz.F};
+        float um[3], t[3], sv[3], upr[3], uf[3];
+        const float u0[3] = {a.ux[p], a.uy[p], a.uz[p]};
 #pragma unroll
-        for (int d = 0; d < 3; d++) um[d] = u0[d] + eps * E[d] + fk * Fp[d];
-        const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-        const double tfac = a.q * a.dt / (2.0 * a.m * gm);
+        for (int q = 0; q < 3; q++) um[q] = u0[q] + a.eps * E[q] + a.fk * Fp[q];
+        const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+        const float tfac = a.tq / gm;
 #pragma unroll
-        for (int d = 0; d < 3; d++) t[d] = tfac * B[d];
-        const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+        for (int q = 0; q < 3; q++) t[q] = tfac * B[q];
+        const float t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
 #pragma unroll
-        for (int d = 0; d < 3; d++) sv[d] = 2.0 * t[d] / (1.0 + t2);
+        for (int q = 0; q < 3; q++) sv[q] = 2.0f * t[q] / (1.0f + t2);
         upr[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
         upr[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
         upr[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
-        uf[0] = um[0] + (upr[1] * sv[2] - upr[2] * sv[1]) + eps * E[0] + fk * Fp[0];
-        uf[1] = um[1] + (upr[2] * sv[0] - upr[0] * sv[2]) + eps * E[1] + fk * Fp[1];
-        uf[2] = um[2] + (upr[0] * sv[1] - upr[1] * sv[0]) + eps * E[2] + fk * Fp[2];
-        const double g = sqrt(1.0 + uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
-        const double cs = kC * a.dt / (g * a.dx);
-        const double xn = x + uf[0] * cs, zn = z + uf[2] * cs;
-        double z1 = zn, ufz_fin = uf[2];
+        uf[0] = um[0] + (upr[1] * sv[2] - upr[2] * sv[1]) + a.eps * E[0] + a.fk * Fp[0];
+        uf[1] = um[1] + (upr[2] * sv[0] - upr[0] * sv[2]) + a.eps * E[1] + a.fk * Fp[1];
+        uf[2] = um[2] + (upr[0] * sv[1] - upr[1] * sv[0]) + a.eps * E[2] + a.fk * Fp[2];
+        const float g = sqrtf(1.0f + uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
+        const float cs = a.cs0 / g;
+        const float xl = fx + uf[0] * cs, zl = fz + uf[2] * cs;   // new position, local to (ci, ck)
+        float z1 = zl, ufz_fin = uf[2];
         bool refl = false;
-        if (zn < 0.0) { z1 = -zn; ufz_fin = -uf[2]; refl = true; }
-        if (zn >= (double)a.nz) { z1 = 2.0 * a.nz - zn; ufz_fin = -uf[2]; refl = true; }
-        const double by = uf[1] / g;
+        if (ck == 0 && zl < 0.0f) { z1 = -zl; ufz_fin = -uf[2]; refl = true; }
+        if (ck == a.nz - 1 && zl >= 1.0f) { z1 = 2.0f - zl; ufz_fin = -uf[2]; refl = true; }
+        const float by = uf[1] / g;
         // ---- reverse ----
-        double lx1 = a.lam_pos[2 * p], lz1 = a.lam_pos[2 * p + 1];
-        double luf[3] = {a.lam_u[3 * p], a.lam_u[3 * p + 1], a.lam_u[3 * p + 2]};
-        double lx0 = 0.0, lz0 = 0.0;
-        if (a.sg != 0.0) {
-            double g5[5] = {0, 0, 0, 0, 0};
-            cur_T(a, x, z, xn, z1, by, g5);
+        float lx1 = a.lam_pos[2 * p], lz1 = a.lam_pos[2 * p + 1];
+        float luf[3] = {a.lam_u[3 * p], a.lam_u[3 * p + 1], a.lam_u[3 * p + 2]};
+        float lx0 = 0.0f, lz0 = 0.0f;
+        if (a.sg != 0.0f) {
+            float g5[5] = {0, 0, 0, 0, 0};
+            cur_T(a, ci, ck, fx, fz, xl, z1, by, g5);
             lx0 += g5[0]; lz0 += g5[1]; lx1 += g5[2]; lz1 += g5[3];
-            const double ufin[3] = {uf[0], uf[1], ufz_fin};
-            const double g3 = g * g * g;
-#pragma unroll
-            for (int d = 0; d < 3; d++) luf[d] += g5[4] * ((d == 1 ? 1.0 / g : 0.0) - ufin[1] * ufin[d] / g3);
+            const float ig = 1.0f / g, ig3 = ig * ig * ig;
+            luf[0] -= g5[4] * uf[1] * uf[0] * ig3;
+            luf[1] += g5[4] * (ig - uf[1] * uf[1] * ig3);
+            luf[2] -= g5[4] * uf[1] * ufz_fin * ig3;
         }
-        double lzn = lz1;
+        float lzn = lz1;
         if (refl) { lzn = -lz1; luf[2] = -luf[2]; }
-        const double udl = (uf[0] * lx1 + uf[2] * lzn) / (g * g);
-        double lu[3];
+        const float udl = (uf[0] * lx1 + uf[2] * lzn) / (g * g);
+        float lu[3];
         lu[0] = luf[0] + cs * (lx1 - uf[0] * udl);
-        lu[1] = luf[1] + cs * (0.0 - uf[1] * udl);
+        lu[1] = luf[1] + cs * (0.0f - uf[1] * udl);
         lu[2] = luf[2] + cs * (lzn - uf[2] * udl);
         lx0 += lx1;
         lz0 += lzn;
         // Boris transpose
-        double la[3], lum[3], lupr[3], lsv[3], lt[3];
+        float la[3], lum[3], lupr[3], lsv[3], lt[3];
 #pragma unroll
-        for (int d = 0; d < 3; d++) { la[d] = lu[d]; lum[d] = lu[d]; }
+        for (int q = 0; q < 3; q++) { la[q] = lu[q]; lum[q] = lu[q]; }
         lupr[0] = sv[1] * lu[2] - sv[2] * lu[1];
         lupr[1] = sv[2] * lu[0] - sv[0] * lu[2];
         lupr[2] = sv[0] * lu[1] - sv[1] * lu[0];
@@ -606,17 +659,17 @@ __global__ void __launch_bounds__(256) k_adjoint_full(const FullAdjArgs a)
         lt[0] = lupr[1] * um[2] - lupr[2] * um[1];
         lt[1] = lupr[2] * um[0] - lupr[0] * um[2];
         lt[2] = lupr[0] * um[1] - lupr[1] * um[0];
-        const double tl = t[0] * lsv[0] + t[1] * lsv[1] + t[2] * lsv[2], d1 = 1.0 + t2;
+        const float tl = t[0] * lsv[0] + t[1] * lsv[1] + t[2] * lsv[2], d1 = 1.0f / (1.0f + t2);
 #pragma unroll
-        for (int d = 0; d < 3; d++) lt[d] += 2.0 * lsv[d] / d1 - 4.0 * tl * t[d] / (d1 * d1);
-        double lB[3], ltf = 0.0;
+        for (int q = 0; q < 3; q++) lt[q] += 2.0f * lsv[q] * d1 - 4.0f * tl * t[q] * d1 * d1;
+        float lB[3], ltf = 0.0f;
 #pragma unroll
-        for (int d = 0; d < 3; d++) { lB[d] = tfac * lt[d]; ltf += B[d] * lt[d]; }
-        const double lgm = -tfac / gm * ltf;
+        for (int q = 0; q < 3; q++) { lB[q] = tfac * lt[q]; ltf += B[q] * lt[q]; }
+        const float lgm = -tfac / gm * ltf;
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            lum[d] += lgm * um[d] / gm;
-            la[d] += lum[d];
+        for (int q = 0; q < 3; q++) {
+            lum[q] += lgm * um[q] / gm;
+            la[q] += lum[q];
         }
         a.lam_u[3 * p] = lum[0];
         a.lam_u[3 * p + 1] = lum[1];
@@ -624,55 +677,38 @@ __global__ void __launch_bounds__(256) k_adjoint_full(const FullAdjArgs a)
         // field gathers
 #pragma unroll
         for (int f = 0; f < 6; f++) {
-            const double lv = f < 3 ? eps * la[f] : lB[f - 3];
-            gather_stag(a, f, x, z, c_stag[f][0], c_stag[f][1], lv, lx0, lz0);
+            const float lv = f < 3 ? a.eps * la[f] : lB[f - 3];
+            gather_stag(a, f, ci, ck, fx, fz, c_stag[f][0], c_stag[f][1], lv, lx0, lz0);
         }
-        // pair force (ions)
-        if (a.pair) {
-            const double lFx = fk * la[0], lFz = fk * la[2];
-            gD += (lFx * Fp[0] + lFz * Fp[2]) / a.D;
-            gR += lFx * (dxr + dxn * 3.0 * n / a.r0 + dxq * 3.0 * qx / a.r0) +
-                  lFz * (dzr + dzn * 3.0 * n / a.r0 + dzq * 3.0 * qz / a.r0);
-            const double ln = lFx * dxn + lFz * dzn, lqx = lFx * dxq, lqz = lFz * dzq;
-            lx0 += ln * qx + lqz * gxz;
-            lz0 += ln * qz + lqx * gxz;
-            const int i1 = pi + 1 == a.nx ? 0 : pi + 1;
-            double* L0 = a.lam_nodes + (size_t)pk * a.nx;
-            double* L1 = L0 + a.nx;
-            const double fx = pfx, fz = pfz;
-            atomicAdd(L0 + pi, ln * (1 - fx) * (1 - fz) - lqx * (1 - fz) - lqz * (1 - fx));
-            atomicAdd(L0 + i1, ln * fx * (1 - fz) + lqx * (1 - fz) - lqz * fx);
-            atomicAdd(L1 + pi, ln * (1 - fx) * fz - lqx * fz + lqz * (1 - fx));
-            atomicAdd(L1 + i1, ln * fx * fz + lqx * fz + lqz * fx);
-        }
+        if (a.pair) pair_T(d, px, pz, a.fk * la[0], a.fk * la[2], a.inv_r0, a.nx, a.lam_nodes, lx0, lz0, gFF, gR);
         a.lam_pos[2 * p] = lx0;
         a.lam_pos[2 * p + 1] = lz0;
     }
     if (a.pair) {
-        const double sD = block_sum_d(gD, sh), sR = block_sum_d(gR, sh);
+        const double sD = block_sum_d(gFF, sh), sR = block_sum_d(gR, sh);
         if (threadIdx.x == 0) {
-            atomicAdd(a.grads, sD);
+            atomicAdd(a.grads, sD * a.inv_D);
             atomicAdd(a.grads + 1, sR);
         }
     }
 }
 
-__global__ void k_adjoint_seed_u(int64_t n, const float* ux, const float* uy, const float* uz, double kin_mc2w,
-                                 double* lam_pos, double* lam_u)
+__global__ void k_adjoint_seed_u(int64_t n, const float* ux, const float* uy, const float* uz, float kin_mc2w,
+                                 float* lam_pos, float* lam_u)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const double x = ux[p], y = uy[p], z = uz[p];
-        const double g = sqrt(1.0 + x * x + y * y + z * z);
-        lam_u[3 * p] = kin_mc2w * x / g;
-        lam_u[3 * p + 1] = kin_mc2w * y / g;
-        lam_u[3 * p + 2] = kin_mc2w * z / g;
-        lam_pos[2 * p] = 0.0;
-        lam_pos[2 * p + 1] = 0.0;
+        const float x = ux[p], y = uy[p], z = uz[p];
+        const float ig = kin_mc2w / sqrtf(1.0f + x * x + y * y + z * z);
+        lam_u[3 * p] = ig * x;
+        lam_u[3 * p + 1] = ig * y;
+        lam_u[3 * p + 2] = ig * z;
+        lam_pos[2 * p] = 0.0f;
+        lam_pos[2 * p + 1] = 0.0f;
     }
 }
 
-static FullAdjArgs make_full_adj(Ctx& c, int s, double* const* lam_pos, double* const* lam_u, double* lam_nodes,
-                                 double* lF, const double* lj, double* grads)
+static FullAdjArgs make_full_adj(Ctx& c, int s, float* const* lam_pos, float* const* lam_u, double* lam_nodes,
+                                 double* lF, const float* lj, double* grads)
 {
     FullAdjArgs a;
     a.nx = c.nx;
@@ -688,50 +724,46 @@ static FullAdjArgs make_full_adj(Ctx& c, int s, double* const* lam_pos, double* 
     a.uz = S.a.uz;
     for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
     a.rho = c.rho[c.cur];
-    a.rho_s = c.rho_scale;
-    a.D = c.D;
-    a.r0 = c.r0;
-    a.dx = c.cfg.dx;
-    a.dt = c.dt;
-    a.q = s == 0 ? c.cfg.ion_charge * kQe : -kQe;
-    a.m = S.mass;
-    a.sg = (double)S.jsign;
+    a.rho_s = (float)c.rho_scale;
+    a.r0_dx = (float)(c.r0 / c.cfg.dx);
+    a.fu = (float)(c.D / c.r0);
+    a.inv_r0 = (float)(1.0 / c.r0);
+    const double q = s == 0 ? c.cfg.ion_charge * kQe : -kQe;
+    a.eps = (float)(q * c.dt / (2.0 * S.mass * kC));
+    a.fk = (float)(c.dt / (2.0 * S.mass * kC));
+    a.tq = (float)(q * c.dt / (2.0 * S.mass));
+    a.cs0 = (float)(kC * c.dt / c.cfg.dx);
+    a.sg = (float)S.jsign;
     a.pair = S.pair;
-    a.cx = kQe * c.w / (2.0 * c.cfg.dx * kEps0);
-    a.cy = kQe * c.w * kC * c.dt / (6.0 * c.cfg.dx * c.cfg.dx * kEps0);
+    a.cx = (float)(kQe * c.w / (2.0 * c.cfg.dx * kEps0));
+    a.cy = (float)(kQe * c.w * kC * c.dt / (6.0 * c.cfg.dx * c.cfg.dx * kEps0));
     a.lam_pos = lam_pos[s];
     a.lam_u = lam_u[s];
     a.lF = lF;
     a.lj = lj;
     a.lam_nodes = lam_nodes;
     a.grads = grads;
+    a.inv_D = 1.0 / c.D;
     return a;
 }
 
-void launch_adjoint_seed_full(Ctx& c, double kin, const double* w_nodes, double* const* lam_pos, double* const* lam_u,
-                              double* lam_nodes, double* lF, double* lj, double* r0_out, cudaStream_t st)
+void launch_adjoint_seed_full(Ctx& c, double kin, const double* w_nodes, float* const* lam_pos, float* const* lam_u,
+                              double* lam_nodes, double* lF, float* lj, double* r0_out, cudaStream_t st)
 {
     const size_t nn = c.nn;
     cudaMemsetAsync(lF, 0, sizeof(double) * 9 * nn, st);
-    cudaMemsetAsync(lj, 0, sizeof(double) * 3 * nn, st);
+    cudaMemsetAsync(lj, 0, sizeof(float) * 3 * nn, st);
     for (int s = 0; s < c.nsp; s++) {
         const Species& S = c.sp[s];
-        k_adjoint_seed_u<<<agrid(c, S.n), 256, 0, st>>>(S.n, S.a.ux, S.a.uy, S.a.uz, kin * c.w * S.mass * kC * kC,
-                                                         lam_pos[s], lam_u[s]);
+        if (s == 0 && S.pair) continue;          // seeded with its density below
+        k_adjoint_seed_u<<<agrid(c, S.n), 256, 0, st>>>(S.n, S.a.ux, S.a.uy, S.a.uz,
+                                                         (float)(kin * c.w * S.mass * kC * kC), lam_pos[s], lam_u[s]);
     }
-    if (c.sp[0].pair) {
-        // the pair species' density: r0 term and the transpose of the final deposition
-        AdjArgs a = make_adj(c, lam_pos[0], lam_u[0], lam_nodes, nullptr);
-        AdjArgs nodes_only = a;
-        nodes_only.n = 0;                                  // momenta seeded above
-        k_adjoint_seed<<<agrid(c, (int64_t)nn), 256, 0, st>>>(nodes_only, 0.0, w_nodes, (int64_t)nn, r0_out);
-        cudaMemcpyAsync(lam_nodes, w_nodes, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st);
-        k_adjoint_b<<<agrid(c, a.n), 256, 0, st>>>(a);
-    }
+    if (c.sp[0].pair) seed_pair_species(c, kin, w_nodes, lam_pos[0], lam_u[0], lam_nodes, r0_out, st);
 }
 
-void launch_adjoint_step_full(Ctx& c, double* const* lam_pos, double* const* lam_u, double* lam_nodes, double* lF,
-                              double* lj, double* grads, cudaStream_t st)
+void launch_adjoint_step_full(Ctx& c, float* const* lam_pos, float* const* lam_u, double* lam_nodes, double* lF,
+                              float* lj, double* grads, cudaStream_t st)
 {
     const size_t nn = c.nn;
     MaxAdjArgs m;
@@ -762,7 +794,7 @@ void launch_adjoint_step_full(Ctx& c, double* const* lam_pos, double* const* lam
         if (a.n > 0) k_adjoint_full<<<agrid(c, a.n), 256, 0, st>>>(a);
     }
     if (c.sp[0].pair) {
-        AdjArgs b = make_adj(c, lam_pos[0], lam_u[0], lam_nodes, grads);
+        AdjArgs b = make_adj(c, 0, lam_pos[0], lam_u[0], lam_nodes, grads);
         k_adjoint_b<<<agrid(c, b.n), 256, 0, st>>>(b);
     }
 }

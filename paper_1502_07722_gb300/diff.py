@@ -79,11 +79,12 @@ class DiffRun:
     def _buffers(self, nn):
         info = self.sim.info()
         dev = dict(dtype=torch.float64, device="cuda")
+        dev32 = dict(dtype=torch.float32, device="cuda")
         self._keep = []
         b = pic_adjoint_buffers()
         for s in range(self.sim.nspecies):
             n = info["num_particles"][s]
-            lp, lu = torch.empty(2 * max(n, 1), **dev), torch.empty(3 * max(n, 1), **dev)
+            lp, lu = torch.empty(2 * max(n, 1), **dev32), torch.empty(3 * max(n, 1), **dev32)
             self._keep += [lp, lu]
             b.lam_pos[s], b.lam_u[s] = lp.data_ptr(), lu.data_ptr()
         lam_nodes = torch.empty(nn, **dev)
@@ -91,7 +92,7 @@ class DiffRun:
         self._keep += [lam_nodes, grads]
         b.lam_nodes, b.grads = lam_nodes.data_ptr(), grads.data_ptr()
         if self.full:
-            lF, lj = torch.empty(9 * nn, **dev), torch.empty(3 * nn, **dev)
+            lF, lj = torch.empty(9 * nn, **dev), torch.empty(3 * nn, **dev32)
             self._keep += [lF, lj]
             b.lam_F, b.lam_j = lF.data_ptr(), lj.data_ptr()
         return b, grads

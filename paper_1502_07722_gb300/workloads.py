@@ -47,6 +47,12 @@ WORKLOADS = {
     # 512 x 512 cells, 16 + 16 ppc, 2 um focus at 3e13 W/cm^2, 200 steps
     "diff512": dict(COPPER, nx=512, nz=512, slab_k=256, ppc_ion=16, ppc_electron=16, laser_profile=2,
                     I0=3e17, w0=2e-6, t_peak=100 * DT_2D, seed=5, steps=200),
+    # differentiable form: 512 x 512 cells, 16 + 16 ppc, 2 um focus at 3e13 W/cm^2, 200 steps with a
+    # checkpoint every 20. The slab fills rows k < 448 so that the antenna (row 510) is 62 cells
+    # above the surface and the pulse, whose peak reaches the surface at step 100, acts within the
+    # run (7,340,032 particles)
+    "differentiable": dict(COPPER, nx=512, nz=512, slab_k=448, ppc_ion=16, ppc_electron=16, laser_profile=2,
+                           I0=3e17, w0=2e-6, t_peak=100 * DT_2D, seed=6, steps=200),
     # 3D: 384 x 384 x 256 cells, slab in the lower 128 z-cells, 8 + 8 ppc (302 M particles),
     # Gaussian focus 1.5 um waist at 1e14 W/cm^2, 500 steps
     "3d": dict(COPPER, dims=3, nx=384, ny=384, nz=256, slab_k=128, ppc_ion=8, ppc_electron=8, laser_profile=2,
