@@ -139,6 +139,14 @@ __device__ __forceinline__ void split2(int cell, int nx, unsigned magic, int& i,
     i = r;
 }
 
+// Particle of this thread in chunk `ch` (blocks of 256 threads take chunks of 256 consecutive
+// particles): the lanes of a warp take particles 8 apart, so that the cell-sorted particles of one
+// cell fall to different warps and a warp's node atomics rarely share an address.
+__device__ __forceinline__ int64_t spread_index(int64_t ch)
+{
+    return ch * 256 + (int64_t)((threadIdx.x & 31) * 8 + (threadIdx.x >> 5));
+}
+
 __device__ __forceinline__ double block_sum_d(double v, double* sh)
 {
     sh[threadIdx.x] = v;
@@ -174,7 +182,9 @@ __global__ void __launch_bounds__(256) k_adjoint_a(const AdjArgs a)
     double gFF = 0.0, gR = 0.0;
     const float r0_dx = (float)(a.r0 / a.dx), fu = (float)(a.D / a.r0), inv_r0 = (float)(1.0 / a.r0);
     const float rho_s = (float)a.rho_s, kick = (float)a.kick, cs0 = (float)a.cs0;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ch = blockIdx.x; ch * 256 < a.n; ch += gridDim.x) {
+        const int64_t p = spread_index(ch);
+        if (p >= a.n) continue;
         int ci, ck;
         split2(a.cell[p], a.nx, a.nx_magic, ci, ck);
         const float fx = a.fx[p], fz = a.fz[p];
@@ -210,9 +220,11 @@ __global__ void __launch_bounds__(256) k_adjoint_a(const AdjArgs a)
 }
 
 // lam_pos += d/dx of sum_nodes lam_nodes * n^(nodes) (transpose of the deposition)
-__global__ void k_adjoint_b(const AdjArgs a)
+__global__ void __launch_bounds__(256) k_adjoint_b(const AdjArgs a)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ch = blockIdx.x; ch * 256 < a.n; ch += gridDim.x) {
+        const int64_t p = spread_index(ch);
+        if (p >= a.n) continue;
         int i, k;
         split2(a.cell[p], a.nx, a.nx_magic, i, k);
         float fx = a.fx[p], fz = a.fz[p];
@@ -573,11 +585,13 @@ __device__ void cur_T(const FullAdjArgs& a, int ci, int ck, float x0, float z0, 
 __device__ __constant__ float c_stag[6][2] = {{0.5f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.5f},
                                               {0.0f, 0.5f}, {0.5f, 0.5f}, {0.5f, 0.0f}};
 
-__global__ void __launch_bounds__(256) k_adjoint_full(const FullAdjArgs a)
+__global__ void __launch_bounds__(256, 2) k_adjoint_full(const FullAdjArgs a)
 {
     __shared__ double sh[256];
     double gFF = 0.0, gR = 0.0;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ch = blockIdx.x; ch * 256 < a.n; ch += gridDim.x) {
+        const int64_t p = spread_index(ch);
+        if (p >= a.n) continue;
         int ci, ck;
         split2(a.cell[p], a.nx, a.nx_magic, ci, ck);
         const float fx = a.fx[p], fz = a.fz[p];
