@@ -132,6 +132,22 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x, world, dist, device):
+    """The maximum of a per-rank time over all ranks (the job ends with its slowest rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_workload(name, rank):
+    """The workload of one rank: the same slab with its own seed (independent replicas)."""
+    from paper_1502_07722_gb300.workloads import workload
+    return workload(name, seed=workload(name)["seed"] + 1000 * rank)
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
     if rank != 0:
@@ -202,11 +218,7 @@ def run_batched(args, world, rank, dist, gb):
         gb.pic_batch_step(batch.b, args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), world, dist, "cuda")
     # per-kernel times from direct launches with events (same kernels as the graph)
     gb.pic_batch_set_timing(batch.b, True)
     nt = max(3, min(args.steps, 10))
@@ -253,7 +265,7 @@ def run_differentiable(args, world, rank, dist, gb):
 
     from paper_1502_07722_gb300 import diff
     from paper_1502_07722_gb300.workloads import workload
-    w = workload(args.workload, seed=workload(args.workload)["seed"] + 1000 * rank)
+    w = rank_workload(args.workload, rank)
     every = 20
     kin = 1e-3
     QE = 1.602176634e-19
@@ -294,10 +306,7 @@ def run_differentiable(args, world, rank, dist, gb):
     ad_ms = e0.elapsed_time(e1) / reps
     run._keep = []
     run.close()
-    t = torch.tensor([fwd_ms + bwd_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(fwd_ms + bwd_ms, world, dist, "cuda")
     nodes = (w["nz"] + 1) * w["nx"]
     # adjoint step, algorithmic bytes: per particle the FP32 state read (24 B) and the FP32
     # adjoints read and written (2 x 20 B); per node 6 FP32 fields read, 9 FP64 field adjoints
@@ -368,7 +377,7 @@ def main():
         return run_batched(args, world, rank, dist, gb)
     if args.workload == "differentiable":
         return run_differentiable(args, world, rank, dist, gb)
-    w = workload(args.workload, seed=workload(args.workload)["seed"] + 1000 * rank)
+    w = rank_workload(args.workload, rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = gb.Simulation(w, stream=stream, sort_every=w.get("sort_every", 40))
@@ -396,10 +405,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     kms, kn = gb.pic_get_timing(sim.h)
     gb.pic_set_timing(sim.h, False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dist, "cuda")
     value = n_local * world * args.steps / (ms_max * 1e-3)
 
     # roofline of the particle kernel (the dominant kernel)
@@ -433,10 +439,8 @@ def main():
             gb.pic_step(sim.h, 1)
         gb.pic_get_density(sim.h, dens_host.data_ptr(), True)
         e2e_s = time.perf_counter() - t0
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": n_local * world * args.steps / float(te.item()), "unit": UNIT,
+        e2e_max = max_over_ranks(e2e_s, world, dist, "cuda")
+        e2e = {"value": n_local * world * args.steps / e2e_max, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "note": "pinned host state uploaded once per job of K steps (bytes amortised per step), "
                        "status word read back every step, node density downloaded at the end"}
