@@ -148,40 +148,47 @@ def rank_workload(name, rank):
     return workload(name, seed=workload(name)["seed"] + 1000 * rank)
 
 
+def oracle_sample(name):
+    """The oracle on a bounded strip of a workload: the same cell size, ppc, dt and laser intensity
+    on 128 x 128 cells (2D) or 32 x 32 x 32 cells (3D), slab in the lower half, the focus narrowed
+    to fit the strip. Returns (oracle, description of the sample)."""
+    import oracle
+    from paper_1502_07722_gb300.workloads import workload
+    w = workload(name)
+    if name == "batched":
+        w = workload("mid2d")
+    w0 = min(w.get("w0", 0.0), 0.5e-6 if w.get("dims") != 3 else 0.15e-6) if w.get("w0") else 0.0
+    if w.get("dims") == 3:
+        o = oracle.Oracle3D(dict(w, nx=32, ny=32, nz=32, slab_k=16, w0=w0))
+        return o, "32 x 32 x 32 cells, slab 16 rows"
+    o = oracle.Oracle(dict(w, nx=128, nz=128, slab_k=64, w0=w0))
+    return o, "128 x 128 cells, slab 64 rows"
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-
-    import oracle
-    from paper_1502_07722_gb300.workloads import workload
-    w = workload(args.workload)
-    sample = dict(w, nx=128, nz=128, slab_k=64, w0=min(w.get("w0", 0.0), 0.5e-6) if w.get("w0") else 0.0)
-    o = oracle.Oracle(sample)
+    o, where = oracle_sample(args.workload)
     n = sum(o.num_particles(s) for s in range(o.nspecies))
     o.step(args.warmup)
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
     v = n * args.steps / dt
-    desc = (f"FP64 C oracle, 1 thread, {args.steps} steps of a 128 x 128-cell strip of the '{args.workload}' "
+    desc = (f"FP64 C oracle, 1 thread, {args.steps} steps of a {where} strip of the '{args.workload}' "
             f"workload (same cell size, ppc, dt and laser intensity; {n} particles)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "sample": "128x128 cells, slab 64 rows"},
+            "data": "synthetic", "config": {"workload": args.workload, "sample": where},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(args):
-    import oracle
-    from paper_1502_07722_gb300.workloads import workload
-    w = workload(args.workload)
-    sample = dict(w, nx=128, nz=128, slab_k=64, w0=min(w.get("w0", 0.0), 0.5e-6) if w.get("w0") else 0.0)
-    o = oracle.Oracle(sample)
+    o, where = oracle_sample(args.workload)
     n = sum(o.num_particles(s) for s in range(o.nspecies))
     o.step(1)
     steps = 6
@@ -189,8 +196,8 @@ def cpu_baseline(args):
     o.step(steps)
     dt = time.perf_counter() - t0
     return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of a 128 x 128-cell strip of '{args.workload}' (slab 64 rows, same ppc, "
-                      f"dx, dt, laser intensity; {n} particles), single-threaded FP64 C"}
+            "sample": f"{steps} steps of a {where} strip of '{args.workload}' (same ppc, dx, dt, laser "
+                      f"intensity; {n} particles), single-threaded FP64 C"}
 
 
 def run_batched(args, world, rank, dist, gb):

@@ -128,6 +128,7 @@ struct Species3 {
 struct Args3 {
     Geo3 g;
     int ntiles, nsp, full, pot_mode;
+    int T, ntx, nty, W;     // tile edge, tiles along x and y, staged window edge (0: no window)
     float cdt_dx, rho_s, h_coef, c_att, s_rep;
     const float* F[6];
     const u64* rho_cur;
@@ -196,26 +197,118 @@ __device__ __noinline__ void deposit3_general(Geo3 g, u64* J0, u64* J1, u64* J2,
         }
 }
 
+// A tile's staged window: the six field components and the pair density (units n0, wall rows
+// doubled) on W^3 nodes from (ox, oy, oz); x and y wrap, z rows outside 0..nz repeat the edge row
+// (the same values the global gathers clamp to).
+struct Win3 {
+    const float* f[6];
+    const float* nh;
+    int ox, oy, oz, W;
+};
+
+// staggered trilinear gather from the window (the same arithmetic as gather3)
+__device__ __forceinline__ float wgather3(const float* A, int W, int lx, int ly, int lz, float fx, float fy, float fz,
+                                          int hx, int hy, int hz)
+{
+    float wx = fx, wy = fy, wz = fz;
+    if (hx) {
+        if (fx >= 0.5f) wx = fx - 0.5f;
+        else { lx -= 1; wx = fx + 0.5f; }
+    }
+    if (hy) {
+        if (fy >= 0.5f) wy = fy - 0.5f;
+        else { ly -= 1; wy = fy + 0.5f; }
+    }
+    if (hz) {
+        if (fz >= 0.5f) wz = fz - 0.5f;
+        else { lz -= 1; wz = fz + 0.5f; }
+    }
+    const int sy = W, sz = W * W;
+    const float* p = A + (lz * W + ly) * W + lx;
+    const float a000 = p[0], a100 = p[1], a010 = p[sy], a110 = p[sy + 1];
+    const float a001 = p[sz], a101 = p[sz + 1], a011 = p[sz + sy], a111 = p[sz + sy + 1];
+    const float b00 = a000 + wx * (a100 - a000), b10 = a010 + wx * (a110 - a010);
+    const float b01 = a001 + wx * (a101 - a001), b11 = a011 + wx * (a111 - a011);
+    const float c0 = b00 + wy * (b10 - b00), c1 = b01 + wy * (b11 - b01);
+    return c0 + wz * (c1 - c0);
+}
+
+// trilinear density and exact gradient from the window (the same arithmetic as density3)
+__device__ __forceinline__ void wdensity3(const float* nh, int W, int lx, int ly, int lz, float fx, float fy, float fz,
+                                          float& n, float* grad)
+{
+    const float* p = nh + (lz * W + ly) * W + lx;
+    const int sy = W, sz = W * W;
+    const float v[8] = {p[0], p[1], p[sy], p[sy + 1], p[sz], p[sz + 1], p[sz + sy], p[sz + sy + 1]};
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float dx00 = v[1] - v[0], dx10 = v[3] - v[2], dx01 = v[5] - v[4], dx11 = v[7] - v[6];
+    grad[0] = gz * (gy * dx00 + fy * dx10) + fz * (gy * dx01 + fy * dx11);
+    const float dy00 = v[2] - v[0], dy10 = v[3] - v[1], dy01 = v[6] - v[4], dy11 = v[7] - v[5];
+    grad[1] = gz * (gx * dy00 + fx * dy10) + fz * (gx * dy01 + fx * dy11);
+    const float dz00 = v[4] - v[0], dz10 = v[5] - v[1], dz01 = v[6] - v[2], dz11 = v[7] - v[3];
+    grad[2] = gy * (gx * dz00 + fx * dz10) + fy * (gx * dz01 + fx * dz11);
+    n = gz * (gy * (gx * v[0] + fx * v[1]) + fy * (gx * v[2] + fx * v[3])) +
+        fz * (gy * (gx * v[4] + fx * v[5]) + fy * (gx * v[6] + fx * v[7]));
+}
+
+// rare path (a particle outside its tile's window): everything from global memory.
+// out: E x3, B x3, n, grad x3
+__device__ __noinline__ void gather_global3(const float* F0, const float* F1, const float* F2, const float* F3,
+                                            const float* F4, const float* F5, const u64* rho, Geo3 g, float rho_s,
+                                            int fields, int pair, int i, int j, int k, float fx, float fy, float fz,
+                                            float* out)
+{
+    if (fields) {
+        out[0] = gather3(F0, g, i, j, k, fx, fy, fz, 1, 0, 0);
+        out[1] = gather3(F1, g, i, j, k, fx, fy, fz, 0, 1, 0);
+        out[2] = gather3(F2, g, i, j, k, fx, fy, fz, 0, 0, 1);
+        out[3] = gather3(F3, g, i, j, k, fx, fy, fz, 0, 1, 1);
+        out[4] = gather3(F4, g, i, j, k, fx, fy, fz, 1, 0, 1);
+        out[5] = gather3(F5, g, i, j, k, fx, fy, fz, 1, 1, 0);
+    }
+    if (pair) density3(rho, g, rho_s, i, j, k, fx, fy, fz, out[6], out + 7);
+}
+
 template <bool FULL, bool PAIR>
-__device__ __forceinline__ void process3(const Args3& a, const Species3& S, int& cell, float& fx_io, float& fy_io,
-                                         float& fz_io, float& ux, float& uy, float& uz)
+__device__ __forceinline__ void process3(const Args3& a, const Species3& S, const Win3& w, int& cell, float& fx_io,
+                                         float& fy_io, float& fz_io, float& ux, float& uy, float& uz)
 {
     const Geo3& g = a.g;
     const float fx = fx_io, fy = fy_io, fz = fz_io;
     int i, j, k;
     split3(cell, g, i, j, k);
+    // window coordinates (x, y periodic: the image closest to the window centre)
+    const int W = w.W, cen = W / 2;
+    int lx = i - w.ox, ly = j - w.oy;
+    if (lx - cen > g.nx / 2) lx -= g.nx;
+    else if (cen - lx > g.nx / 2) lx += g.nx;
+    if (ly - cen > g.ny / 2) ly -= g.ny;
+    else if (cen - ly > g.ny / 2) ly += g.ny;
+    const int lz = k - w.oz;
+    const bool inwin = W > 0 && lx >= 1 && lx + 2 < W && ly >= 1 && ly + 2 < W && lz >= 1 && lz + 2 < W;
     float kx = 0.f, ky = 0.f, kz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-    if (FULL) {
-        kx = S.e_kick * gather3(a.F[0], g, i, j, k, fx, fy, fz, 1, 0, 0);
-        ky = S.e_kick * gather3(a.F[1], g, i, j, k, fx, fy, fz, 0, 1, 0);
-        kz = S.e_kick * gather3(a.F[2], g, i, j, k, fx, fy, fz, 0, 0, 1);
-        bx = gather3(a.F[3], g, i, j, k, fx, fy, fz, 0, 1, 1);
-        by = gather3(a.F[4], g, i, j, k, fx, fy, fz, 1, 0, 1);
-        bz = gather3(a.F[5], g, i, j, k, fx, fy, fz, 1, 1, 0);
+    float n = 0.f, gr[3] = {0.f, 0.f, 0.f};
+    if (inwin) {
+        if (FULL) {
+            kx = S.e_kick * wgather3(w.f[0], W, lx, ly, lz, fx, fy, fz, 1, 0, 0);
+            ky = S.e_kick * wgather3(w.f[1], W, lx, ly, lz, fx, fy, fz, 0, 1, 0);
+            kz = S.e_kick * wgather3(w.f[2], W, lx, ly, lz, fx, fy, fz, 0, 0, 1);
+            bx = wgather3(w.f[3], W, lx, ly, lz, fx, fy, fz, 0, 1, 1);
+            by = wgather3(w.f[4], W, lx, ly, lz, fx, fy, fz, 1, 0, 1);
+            bz = wgather3(w.f[5], W, lx, ly, lz, fx, fy, fz, 1, 1, 0);
+        }
+        if (PAIR) wdensity3(w.nh, W, lx, ly, lz, fx, fy, fz, n, gr);
+    } else {
+        float o[10];
+        gather_global3(a.F[0], a.F[1], a.F[2], a.F[3], a.F[4], a.F[5], a.rho_cur, g, a.rho_s, FULL ? 1 : 0,
+                       PAIR ? 1 : 0, i, j, k, fx, fy, fz, o);
+        if (FULL) {
+            kx = S.e_kick * o[0]; ky = S.e_kick * o[1]; kz = S.e_kick * o[2];
+            bx = o[3]; by = o[4]; bz = o[5];
+        }
+        if (PAIR) { n = o[6]; gr[0] = o[7]; gr[1] = o[8]; gr[2] = o[9]; }
     }
     if (PAIR) {
-        float n, gr[3];
-        density3(a.rho_cur, g, a.rho_s, i, j, k, fx, fy, fz, n, gr);
         if (n > 0.0f) {
             const float c = fast_cbrt(n);
             const float inv43 = fast_rcp(n * c);
@@ -331,11 +424,49 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, int&
 template <bool FULL>
 __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const Args3 a)
 {
-    __shared__ unsigned chunk[7 * kChunkWords3];
+    extern __shared__ unsigned smem3[];
+    const int W = a.W, WW = W * W, WWW = WW * W;
+    unsigned* chunk = smem3 + 7 * WWW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* c_cell = reinterpret_cast<int*>(chunk);
     float* c_f = reinterpret_cast<float*>(chunk + kChunkWords3);
+    Win3 w;
+    w.W = W;
+    float* wf = reinterpret_cast<float*>(smem3);
+    for (int q = 0; q < 6; q++) w.f[q] = wf + q * WWW;
+    w.nh = wf + 6 * WWW;
+    const Geo3& g = a.g;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        int cnt = 0;
+        for (int s = 0; s < a.nsp; s++) cnt += a.sp[s].tile_start[t + 1] - a.sp[s].tile_start[t];
+        if (cnt == 0) continue;
+        const int tx = t % a.ntx, ty = (t / a.ntx) % a.nty, tz = t / (a.ntx * a.nty);
+        w.ox = tx * a.T - 1;
+        w.oy = ty * a.T - 1;
+        w.oz = tz * a.T - 1;
+        if (W > 0) {
+            __syncthreads();                       // the previous tile is done with the window
+            for (int q = threadIdx.x; q < WWW; q += blockDim.x) {
+                const int c = q / WW, r = q - c * WW, b = r / W, e = r - b * W;
+                int gx = (w.ox + e) % g.nx, gy = (w.oy + b) % g.ny;
+                gx = gx < 0 ? gx + g.nx : gx;
+                gy = gy < 0 ? gy + g.ny : gy;
+                const int gz = w.oz + c;
+                const int gn = min(max(gz, 0), g.nz), gh = min(max(gz, 0), g.nz - 1);
+                const size_t in = idx3(g, gx, gy, gn), ih = idx3(g, gx, gy, gh);
+                if (FULL) {
+                    wf[q] = __ldg(a.F[0] + in);
+                    wf[WWW + q] = __ldg(a.F[1] + in);
+                    wf[2 * WWW + q] = __ldg(a.F[2] + ih);
+                    wf[3 * WWW + q] = __ldg(a.F[3] + ih);
+                    wf[4 * WWW + q] = __ldg(a.F[4] + ih);
+                    wf[5 * WWW + q] = __ldg(a.F[5] + in);
+                }
+                const long long r0 = (long long)__ldg(a.rho_cur + in);
+                wf[6 * WWW + q] = a.rho_s * (float)((gn == 0 || gn == g.nz) ? 2 * r0 : r0);
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int s = 0; s < 2; s++) {
             if (s >= a.nsp) break;
@@ -364,8 +495,8 @@ __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const Args3 a)
                         float fx = c_f[slot], fy = c_f[kChunkWords3 + slot], fz = c_f[2 * kChunkWords3 + slot];
                         float ux = c_f[3 * kChunkWords3 + slot], uy = c_f[4 * kChunkWords3 + slot],
                               uz = c_f[5 * kChunkWords3 + slot];
-                        if (s == 0) process3<FULL, true>(a, S, cell, fx, fy, fz, ux, uy, uz);
-                        else process3<FULL, false>(a, S, cell, fx, fy, fz, ux, uy, uz);
+                        if (s == 0) process3<FULL, true>(a, S, w, cell, fx, fy, fz, ux, uy, uz);
+                        else process3<FULL, false>(a, S, w, cell, fx, fy, fz, ux, uy, uz);
                         c_cell[slot] = cell;
                         c_f[slot] = fx;
                         c_f[kChunkWords3 + slot] = fy;
@@ -431,10 +562,26 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
         d.e_kick = S.e_kick; d.b_rot = S.b_rot; d.p_kick = S.p_kick;
         d.jsign = S.jsign; d.pair = S.pair;
     }
+    a.T = c.T;
+    a.ntx = c.ntx;
+    a.nty = c.nty;
+    // window of the tile plus one node below and two above on each axis; staged when it fits next
+    // to the particle chunk with three CTAs per SM
+    const int W = c.T + 3;
+    a.W = (size_t)7 * W * W * W * 4 <= 40 * 1024 ? W : 0;
+    const size_t shmem = sizeof(unsigned) * ((size_t)7 * a.W * a.W * a.W + 7 * kChunkWords3);
+    static size_t configured = 0;
+    if (shmem > configured) {
+        cudaFuncSetAttribute(k_particles3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+        cudaFuncSetAttribute(k_particles3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+        cudaFuncSetAttribute(k_particles3<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_particles3<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        configured = shmem;
+    }
     int grid = c.ntiles < c.nsm * 3 ? c.ntiles : c.nsm * 3;
     if (grid < 1) grid = 1;
-    if (a.full) k_particles3<true><<<grid, kBlock3, 0, st>>>(a);
-    else k_particles3<false><<<grid, kBlock3, 0, st>>>(a);
+    if (a.full) k_particles3<true><<<grid, kBlock3, shmem, st>>>(a);
+    else k_particles3<false><<<grid, kBlock3, shmem, st>>>(a);
 }
 
 // ---- stand-alone node density and pair force ------------------------------------------------
