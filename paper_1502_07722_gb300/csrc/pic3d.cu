@@ -269,9 +269,11 @@ __device__ __noinline__ void gather_global3(const float* F0, const float* F1, co
     if (pair) density3(rho, g, rho_s, i, j, k, fx, fy, fz, out[6], out + 7);
 }
 
-template <bool FULL, bool PAIR>
-__device__ __forceinline__ void process3(const Args3& a, const Species3& S, const Win3& w, int& cell, float& fx_io,
-                                         float& fy_io, float& fz_io, float& ux, float& uy, float& uz)
+// One particle. PAIR is a run-time flag (the pair species): one instance of this code serves both
+// species, which keeps the kernel inside the instruction cache.
+template <bool FULL>
+__device__ __forceinline__ void process3(const Args3& a, const Species3& S, const Win3& w, const bool PAIR, int& cell,
+                                         float& fx_io, float& fy_io, float& fz_io, float& ux, float& uy, float& uz)
 {
     const Geo3& g = a.g;
     const float fx = fx_io, fy = fy_io, fz = fz_io;
@@ -467,10 +469,10 @@ __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const Args3 a)
             }
             __syncthreads();
         }
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < 2; s++) {
             if (s >= a.nsp) break;
-            const Species3& S = a.sp[s];
+            const Species3 S = s == 0 ? a.sp[0] : a.sp[1];
             const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
             for (int c0 = p0; c0 < p1; c0 += kChunk3) {
                 const int n = min(kChunk3, p1 - c0);
@@ -495,8 +497,7 @@ __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const Args3 a)
                         float fx = c_f[slot], fy = c_f[kChunkWords3 + slot], fz = c_f[2 * kChunkWords3 + slot];
                         float ux = c_f[3 * kChunkWords3 + slot], uy = c_f[4 * kChunkWords3 + slot],
                               uz = c_f[5 * kChunkWords3 + slot];
-                        if (s == 0) process3<FULL, true>(a, S, w, cell, fx, fy, fz, ux, uy, uz);
-                        else process3<FULL, false>(a, S, w, cell, fx, fy, fz, ux, uy, uz);
+                        process3<FULL>(a, S, w, S.pair != 0, cell, fx, fy, fz, ux, uy, uz);
                         c_cell[slot] = cell;
                         c_f[slot] = fx;
                         c_f[kChunkWords3 + slot] = fy;
