@@ -247,7 +247,9 @@ PIC_API int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* in, 
  * A checkpoint is a device buffer (caller-owned, 256-byte aligned, pic_checkpoint_size bytes) with
  * the particles, tile offsets, fields, node density, current and step counter of a context.
  * Restoring it into the same context resumes bit for bit: same grids, same particle set (a cell sort
- * after the restore may order the particles of one cell differently). */
+ * after the restore may order the particles of one cell differently). pic_checkpoint_save is
+ * asynchronous on the context's stream; pic_checkpoint_restore synchronises (it checks the
+ * buffer's header) and returns PIC_EINVAL for a buffer that holds no checkpoint of this layout. */
 PIC_API int pic_checkpoint_size(pic_ctx* ctx, size_t* bytes);
 PIC_API int pic_checkpoint_save(pic_ctx* ctx, void* dev_buf);
 PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
@@ -264,12 +266,12 @@ PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
  * differentiated as the continuous linear shape. The paper has no adjoint; the method, the
  * parameters and the stage are the paper's.
  *
- * Adjoint buffers (device, caller-owned). Per-particle adjoints are FP32 (the precision of the push),
- * node adjoints and parameter derivatives FP64:
+ * Adjoint buffers (device, caller-owned). Per-particle adjoints and the particles' scatter onto
+ * the nodes are FP32 (the precision of the push), field adjoints and parameter derivatives FP64:
  *   lam_pos[s]: float, 2 n_s, (x, z) adjoints per particle of species s (per cell), in the
  *               context's particle order;
  *   lam_u[s]:   float, 3 n_s;
- *   lam_nodes:  double, (nz+1) nx scratch;
+ *   lam_nodes:  float, (nz+1) nx scratch;
  *   lam_F:      double, 9 (nz+1) nx: adjoints of Ex Ey Ez Bx By Bz and three scratch grids (FULL only);
  *   lam_j:      float, 3 (nz+1) nx scratch (FULL only);
  *   grads:      double, 3, accumulated by pic_adjoint_step: dL/dD (1/J), dL/dr0 (1/m), dL/dI0 (m^2/W).
@@ -286,7 +288,7 @@ PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
 typedef struct {
     float* lam_pos[2];
     float* lam_u[2];
-    double* lam_nodes;
+    float* lam_nodes;
     double* lam_F;
     float* lam_j;
     double* grads;

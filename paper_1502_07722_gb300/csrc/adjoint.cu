@@ -2,9 +2,10 @@
 // respect to the pair-potential parameters D and r0 (r0 sets Eq. (3)'s equilibrium distance, the
 // r0/dx of Eq. (1), and the density unit n0 = r0^-3) and, with fields, the laser peak intensity.
 //
-// Precision: the per-particle transposes run in FP32 (the precision of the forward push); node
-// adjoints are accumulated in FP64 (atomics from many particles), the Maxwell transpose runs in
-// FP64 on the nodes, and the parameter derivatives are summed in FP64. The deposition is
+// Precision: the per-particle transposes run in FP32 (the precision of the forward push) and
+// scatter onto the nodes with FP32 atomics; the field adjoints are held and transposed through
+// the Yee step in FP64 on the nodes (the particle scatter is folded in once per step), and the
+// parameter derivatives are summed in FP64. The deposition is
 // differentiated as the continuous linear shape (straight-through on the fixed point). Node
 // density differences are taken exactly in integers before scaling.
 //
@@ -112,7 +113,7 @@ __device__ __forceinline__ DensAt dens_at(const u64* rho, float rho_s, int nx, i
 // transpose of the pair force given the adjoints of (Fx, Fz): position adjoints (added to lx, lz),
 // node adjoints (FP64 atomics), and the D, r0 derivative terms (gFF += lF . F, gR += dL/dr0 part)
 __device__ __forceinline__ void pair_T(const DensAt& d, const PairD& px, const PairD& pz, float lFx, float lFz,
-                                       float inv_r0, int nx, double* lam_nodes, float& lx, float& lz, double& gFF,
+                                       float inv_r0, int nx, float* lam_nodes, float& lx, float& lz, double& gFF,
                                        double& gR)
 {
     gFF += (double)(lFx * px.F + lFz * pz.F);
@@ -122,12 +123,12 @@ __device__ __forceinline__ void pair_T(const DensAt& d, const PairD& px, const P
     lx += ln * d.qx + lqz * d.gxz;
     lz += ln * d.qz + lqx * d.gxz;
     const float fx = d.fx, fz = d.fz;
-    double* L0 = lam_nodes + (size_t)d.k * nx;
-    double* L1 = L0 + nx;
-    atomicAdd(L0 + d.i, (double)(ln * (1 - fx) * (1 - fz) - lqx * (1 - fz) - lqz * (1 - fx)));
-    atomicAdd(L0 + d.i1, (double)(ln * fx * (1 - fz) + lqx * (1 - fz) - lqz * fx));
-    atomicAdd(L1 + d.i, (double)(ln * (1 - fx) * fz - lqx * fz + lqz * (1 - fx)));
-    atomicAdd(L1 + d.i1, (double)(ln * fx * fz + lqx * fz + lqz * fx));
+    float* L0 = lam_nodes + (size_t)d.k * nx;
+    float* L1 = L0 + nx;
+    atomicAdd(L0 + d.i, ln * (1 - fx) * (1 - fz) - lqx * (1 - fz) - lqz * (1 - fx));
+    atomicAdd(L0 + d.i1, ln * fx * (1 - fz) + lqx * (1 - fz) - lqz * fx);
+    atomicAdd(L1 + d.i, ln * (1 - fx) * fz - lqx * fz + lqz * (1 - fx));
+    atomicAdd(L1 + d.i1, ln * fx * fz + lqx * fz + lqz * fx);
 }
 
 __device__ __forceinline__ void split2(int cell, int nx, unsigned magic, int& i, int& k)
@@ -172,7 +173,7 @@ struct AdjArgs {
     double D, r0, dx, kick, cs0;   // kick = dt / (m c); cs0 = c dt / dx
     float* lam_pos;        // 2 n: (x, z) adjoints
     float* lam_u;          // 3 n
-    double* lam_nodes;     // (nz + 1) nx node adjoints (units 1 / n0)
+    float* lam_nodes;      // (nz + 1) nx node adjoints (units 1 / n0)
     double* grads;         // 3: dL/dD, dL/dr0, dL/dI0
 };
 
@@ -230,12 +231,12 @@ __global__ void __launch_bounds__(256) k_adjoint_b(const AdjArgs a)
         float fx = a.fx[p], fz = a.fz[p];
         if (k >= a.nz) { k = a.nz - 1; fz = 1.0f; }
         const int i1 = i + 1 == a.nx ? 0 : i + 1;
-        const double m0 = k == 0 ? 2.0 : 1.0, m1 = k + 1 == a.nz ? 2.0 : 1.0;
-        const double* L0 = a.lam_nodes + (size_t)k * a.nx;
-        const double* L1 = L0 + a.nx;
-        const double l00 = m0 * L0[i], l10 = m0 * L0[i1], l01 = m1 * L1[i], l11 = m1 * L1[i1];
+        const float m0 = k == 0 ? 2.0f : 1.0f, m1 = k + 1 == a.nz ? 2.0f : 1.0f;
+        const float* L0 = a.lam_nodes + (size_t)k * a.nx;
+        const float* L1 = L0 + a.nx;
+        const float l00 = m0 * L0[i], l10 = m0 * L0[i1], l01 = m1 * L1[i], l11 = m1 * L1[i1];
         const float u = (float)a.unit;
-        const float ex0 = (float)(l10 - l00), ex1 = (float)(l11 - l01), ez0 = (float)(l01 - l00), ez1 = (float)(l11 - l10);
+        const float ex0 = l10 - l00, ex1 = l11 - l01, ez0 = l01 - l00, ez1 = l11 - l10;
         a.lam_pos[2 * p] += u * ((1 - fz) * ex0 + fz * ex1);
         a.lam_pos[2 * p + 1] += u * ((1 - fx) * ez0 + fx * ez1);
     }
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(256) k_adjoint_seed(const AdjArgs a, double ki
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nn; c += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(c / a.nx), i = (int)(c - (int64_t)k * a.nx);
         acc += w_nodes[c] * 3.0 * a.rho_s * (double)node_sum(a.rho, a.nx, a.nz, i, k) / a.r0;
+        a.lam_nodes[c] = (float)w_nodes[c];                  // the final density's node adjoints
     }
     const double s = block_sum_d(acc, sh);
     if (threadIdx.x == 0) atomicAdd(r0_out, s);
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(256) k_node_functional(const u64* rho, int nx,
     if (threadIdx.x == 0) atomicAdd(out, s);
 }
 
-static AdjArgs make_adj(Ctx& c, int s, float* lam_pos, float* lam_u, double* lam_nodes, double* grads)
+static AdjArgs make_adj(Ctx& c, int s, float* lam_pos, float* lam_u, float* lam_nodes, double* grads)
 {
     AdjArgs a;
     a.nx = c.nx;
@@ -320,26 +322,25 @@ static int agrid(const Ctx& c, int64_t n)
 // seed of the pair species: momenta (kin), the final density functional's position adjoints and
 // its r0 term
 static void seed_pair_species(Ctx& c, double kin, const double* w_nodes, float* lam_pos, float* lam_u,
-                              double* lam_nodes, double* r0_out, cudaStream_t st)
+                              float* lam_nodes, double* r0_out, cudaStream_t st)
 {
     AdjArgs a = make_adj(c, 0, lam_pos, lam_u, lam_nodes, nullptr);
     const int64_t nn = (int64_t)c.nn;
     k_adjoint_seed<<<agrid(c, a.n > nn ? a.n : nn), 256, 0, st>>>(a, kin * c.w * c.sp[0].mass * kC * kC, w_nodes, nn,
                                                                    r0_out);
-    cudaMemcpyAsync(lam_nodes, w_nodes, sizeof(double) * c.nn, cudaMemcpyDeviceToDevice, st);
     k_adjoint_b<<<agrid(c, a.n), 256, 0, st>>>(a);
 }
 
-void launch_adjoint_seed(Ctx& c, double kin, const double* w_nodes, float* lam_pos, float* lam_u, double* lam_nodes,
+void launch_adjoint_seed(Ctx& c, double kin, const double* w_nodes, float* lam_pos, float* lam_u, float* lam_nodes,
                          double* r0_out, cudaStream_t st)
 {
     seed_pair_species(c, kin, w_nodes, lam_pos, lam_u, lam_nodes, r0_out, st);
 }
 
-void launch_adjoint_step(Ctx& c, float* lam_pos, float* lam_u, double* lam_nodes, double* grads, cudaStream_t st)
+void launch_adjoint_step(Ctx& c, float* lam_pos, float* lam_u, float* lam_nodes, double* grads, cudaStream_t st)
 {
     AdjArgs a = make_adj(c, 0, lam_pos, lam_u, lam_nodes, grads);
-    cudaMemsetAsync(lam_nodes, 0, sizeof(double) * c.nn, st);
+    cudaMemsetAsync(lam_nodes, 0, sizeof(float) * c.nn, st);
     k_adjoint_a<<<agrid(c, a.n), 256, 0, st>>>(a);
     k_adjoint_b<<<agrid(c, a.n), 256, 0, st>>>(a);
 }
@@ -360,7 +361,9 @@ void launch_node_functional(Ctx& c, const double* w_nodes, double* dev_out, cuda
 // then per particle the transposes of the current, move, walls, Boris, gathers and pair force,
 // then the density transpose. j is the scaled current dt J / eps0.
 // Adjoint field layout (lam_F): 9 grids of (nz + 1) nx doubles: Ex Ey Ez Bx By Bz, then three
-// scratch grids for the new E adjoints. Current adjoints (lam_j): 3 grids of floats.
+// scratch grids: the new E adjoints during the Maxwell transpose, then (as six float grids) the
+// particles' FP32 scatter onto the field nodes, folded into the first six grids after the particle
+// kernels. Current adjoints (lam_j): 3 grids of floats.
 // ==============================================================================================
 
 struct MaxAdjArgs {
@@ -464,9 +467,9 @@ struct FullAdjArgs {
     float cx, cy;             // scaled current per unit Esirkepov sum: x/z and y
     float* lam_pos;
     float* lam_u;
-    double* lF;               // 6 grids (accumulated)
+    float* lF;                // 6 float grids: the particles' scatter onto the field nodes
     const float* lj;          // 3 grids
-    double* lam_nodes;
+    float* lam_nodes;
     double* grads;
     double inv_D;
 };
@@ -499,11 +502,11 @@ __device__ __forceinline__ float gather_stag(const FullAdjArgs& a, int f, int ci
     const size_t r0 = (size_t)k * nx, r1 = r0 + nx;
     const float a00 = A[r0 + i0], a10 = A[r0 + i1], a01 = A[r1 + i0], a11 = A[r1 + i1];
     if (lv != 0.0f) {
-        double* L = a.lF + (size_t)f * (nz + 1) * nx;
-        atomicAdd(L + r0 + i0, (double)(lv * (1 - xs) * (1 - fzz)));
-        atomicAdd(L + r0 + i1, (double)(lv * xs * (1 - fzz)));
-        atomicAdd(L + r1 + i0, (double)(lv * (1 - xs) * fzz));
-        atomicAdd(L + r1 + i1, (double)(lv * xs * fzz));
+        float* L = a.lF + (size_t)f * (nz + 1) * nx;
+        atomicAdd(L + r0 + i0, lv * (1 - xs) * (1 - fzz));
+        atomicAdd(L + r0 + i1, lv * xs * (1 - fzz));
+        atomicAdd(L + r1 + i0, lv * (1 - xs) * fzz);
+        atomicAdd(L + r1 + i1, lv * xs * fzz);
         lx += lv * ((1 - fzz) * (a10 - a00) + fzz * (a11 - a01));
         if (!clamped) lz += lv * ((1 - xs) * (a01 - a00) + xs * (a11 - a10));
     }
@@ -721,8 +724,15 @@ __global__ void k_adjoint_seed_u(int64_t n, const float* ux, const float* uy, co
     }
 }
 
-static FullAdjArgs make_full_adj(Ctx& c, int s, float* const* lam_pos, float* const* lam_u, double* lam_nodes,
-                                 double* lF, const float* lj, double* grads)
+// the particles' FP32 scatter added into the FP64 field adjoints
+__global__ void k_fold_scatter(double* __restrict__ lF, const float* __restrict__ scatter, int64_t n)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        lF[q] += (double)scatter[q];
+}
+
+static FullAdjArgs make_full_adj(Ctx& c, int s, float* const* lam_pos, float* const* lam_u, float* lam_nodes,
+                                 float* lF, const float* lj, double* grads)
 {
     FullAdjArgs a;
     a.nx = c.nx;
@@ -762,7 +772,7 @@ static FullAdjArgs make_full_adj(Ctx& c, int s, float* const* lam_pos, float* co
 }
 
 void launch_adjoint_seed_full(Ctx& c, double kin, const double* w_nodes, float* const* lam_pos, float* const* lam_u,
-                              double* lam_nodes, double* lF, float* lj, double* r0_out, cudaStream_t st)
+                              float* lam_nodes, double* lF, float* lj, double* r0_out, cudaStream_t st)
 {
     const size_t nn = c.nn;
     cudaMemsetAsync(lF, 0, sizeof(double) * 9 * nn, st);
@@ -776,7 +786,7 @@ void launch_adjoint_seed_full(Ctx& c, double kin, const double* w_nodes, float* 
     if (c.sp[0].pair) seed_pair_species(c, kin, w_nodes, lam_pos[0], lam_u[0], lam_nodes, r0_out, st);
 }
 
-void launch_adjoint_step_full(Ctx& c, float* const* lam_pos, float* const* lam_u, double* lam_nodes, double* lF,
+void launch_adjoint_step_full(Ctx& c, float* const* lam_pos, float* const* lam_u, float* lam_nodes, double* lF,
                               float* lj, double* grads, cudaStream_t st)
 {
     const size_t nn = c.nn;
@@ -802,11 +812,14 @@ void launch_adjoint_step_full(Ctx& c, float* const* lam_pos, float* const* lam_u
     k_adj_feT<<<grid, block, 0, st>>>(m);
     cudaMemcpyAsync(lF, lF + 6 * nn, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, st);
     k_adj_hbT<<<grid, block, 0, st>>>(m);
-    if (c.sp[0].pair) cudaMemsetAsync(lam_nodes, 0, sizeof(double) * nn, st);
+    if (c.sp[0].pair) cudaMemsetAsync(lam_nodes, 0, sizeof(float) * nn, st);
+    float* scatter = reinterpret_cast<float*>(lF + 6 * nn);        // six float grids
+    cudaMemsetAsync(scatter, 0, sizeof(float) * 6 * nn, st);
     for (int s = 0; s < c.nsp; s++) {
-        FullAdjArgs a = make_full_adj(c, s, lam_pos, lam_u, lam_nodes, lF, lj, grads);
+        FullAdjArgs a = make_full_adj(c, s, lam_pos, lam_u, lam_nodes, scatter, lj, grads);
         if (a.n > 0) k_adjoint_full<<<agrid(c, a.n), 256, 0, st>>>(a);
     }
+    k_fold_scatter<<<agrid(c, (int64_t)(6 * nn)), 256, 0, st>>>(lF, scatter, (int64_t)(6 * nn));
     if (c.sp[0].pair) {
         AdjArgs b = make_adj(c, 0, lam_pos[0], lam_u[0], lam_nodes, grads);
         k_adjoint_b<<<agrid(c, b.n), 256, 0, st>>>(b);

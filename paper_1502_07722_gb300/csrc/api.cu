@@ -695,11 +695,9 @@ int pic_checkpoint_save(pic_ctx* h, void* dev_buf)
     hd.n[1] = c.nsp > 1 ? c.sp[1].n : 0;
     hd.steps_since_sort = c.steps_since_sort;
     hd.nsp = c.nsp;
+    // a pageable source: the call returns once the header has been staged, so hd may go out of scope
     CK(cudaMemcpyAsync(dev_buf, &hd, sizeof(hd), cudaMemcpyHostToDevice, c.stream));
-    int r = ckpt_copy(h, (char*)dev_buf, true);
-    if (r) return r;
-    CK(cudaStreamSynchronize(c.stream));
-    return PIC_OK;
+    return ckpt_copy(h, (char*)dev_buf, true);
 }
 
 int pic_checkpoint_restore(pic_ctx* h, const void* dev_buf)

@@ -155,13 +155,13 @@ void launch_pair_force3(Ctx& c, float* out, cudaStream_t st);
 void launch_fields3(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches);
 void launch_energy3(Ctx& c, cudaStream_t st, double* host_out5);
 void launch_init_particles3(Ctx& c, int s, cudaStream_t st);
-void launch_adjoint_seed(Ctx& c, double kin, const double* w_nodes, float* lam_pos, float* lam_u, double* lam_nodes,
+void launch_adjoint_seed(Ctx& c, double kin, const double* w_nodes, float* lam_pos, float* lam_u, float* lam_nodes,
                          double* r0_out, cudaStream_t st);
-void launch_adjoint_step(Ctx& c, float* lam_pos, float* lam_u, double* lam_nodes, double* grads, cudaStream_t st);
+void launch_adjoint_step(Ctx& c, float* lam_pos, float* lam_u, float* lam_nodes, double* grads, cudaStream_t st);
 void launch_node_functional(Ctx& c, const double* w_nodes, double* dev_out, cudaStream_t st);
 void launch_adjoint_seed_full(Ctx& c, double kin, const double* w_nodes, float* const* lam_pos, float* const* lam_u,
-                              double* lam_nodes, double* lF, float* lj, double* r0_out, cudaStream_t st);
-void launch_adjoint_step_full(Ctx& c, float* const* lam_pos, float* const* lam_u, double* lam_nodes, double* lF,
+                              float* lam_nodes, double* lF, float* lj, double* r0_out, cudaStream_t st);
+void launch_adjoint_step_full(Ctx& c, float* const* lam_pos, float* const* lam_u, float* lam_nodes, double* lF,
                               float* lj, double* grads, cudaStream_t st);
 int tile_window(int T);
 void launch_energy(Ctx& c, cudaStream_t st, double* host_out5);

@@ -87,7 +87,7 @@ class DiffRun:
             lp, lu = torch.empty(2 * max(n, 1), **dev32), torch.empty(3 * max(n, 1), **dev32)
             self._keep += [lp, lu]
             b.lam_pos[s], b.lam_u[s] = lp.data_ptr(), lu.data_ptr()
-        lam_nodes = torch.empty(nn, **dev)
+        lam_nodes = torch.empty(nn, **dev32)
         grads = torch.zeros(3, **dev)
         self._keep += [lam_nodes, grads]
         b.lam_nodes, b.grads = lam_nodes.data_ptr(), grads.data_ptr()
