@@ -324,19 +324,20 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
                 // 6 Wy = 6 Q^2 - 3 Q (x0 + x1) - 3 Q (z0 + z1) + P on the lower-left corner, etc.
                 const long long P = (long long)x0 * (2 * z0 + z1) + (long long)x1 * (z0 + 2 * z1);
                 const long long sx = 3LL * kQOne * (x0 + x1), sz = 3LL * kQOne * (z0 + z1);
-                wadd(w, 2, base, V * (6LL * kQOne * kQOne - sx - sz + P));
-                wadd(w, 2, base + 1, V * (sx - P));
-                wadd(w, 2, base + W, V * (sz - P));
-                wadd(w, 2, base + W + 1, V * P);
+                // all four weights are non-zero except on a cell edge: no per-term test
+                acc64(w.lo[2] + base, w.hi[2] + base, V * (6LL * kQOne * kQOne - sx - sz + P));
+                acc64(w.lo[2] + base + 1, w.hi[2] + base + 1, V * (sx - P));
+                acc64(w.lo[2] + base + W, w.hi[2] + base + W, V * (sz - P));
+                acc64(w.lo[2] + base + W + 1, w.hi[2] + base + W + 1, V * P);
             }
         }
         if (kPair && moved) {
             // node density change: S(new) - S(old) on the four corners
             const long long a0 = kQOne - x0, a1 = kQOne - x1, c0 = kQOne - z0, c1 = kQOne - z1;
-            wadd(w, 0, base, a1 * c1 - a0 * c0);
-            wadd(w, 0, base + 1, (long long)x1 * c1 - (long long)x0 * c0);
-            wadd(w, 0, base + W, a1 * z1 - a0 * z0);
-            wadd(w, 0, base + W + 1, (long long)x1 * z1 - (long long)x0 * z0);
+            acc64(w.lo[0] + base, w.hi[0] + base, a1 * c1 - a0 * c0);
+            acc64(w.lo[0] + base + 1, w.hi[0] + base + 1, (long long)x1 * c1 - (long long)x0 * c0);
+            acc64(w.lo[0] + base + W, w.hi[0] + base + W, a1 * z1 - a0 * z0);
+            acc64(w.lo[0] + base + W + 1, w.hi[0] + base + W + 1, (long long)x1 * z1 - (long long)x0 * z0);
         }
     } else if (inwin) {
         // a cell edge was crossed: 3 x 3 Esirkepov stencil in the window
