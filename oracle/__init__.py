@@ -112,6 +112,8 @@ def lib():
                                                         ctypes.c_double]),
             "oracle_D": (ctypes.c_double, [vp]),
             "oracle_E0": (ctypes.c_double, [vp]),
+            "oracle_injected": (ctypes.c_double, [vp]),
+            "oracle3_injected": (ctypes.c_double, [vp]),
             "oracle_full_grad": (None, [vp, ctypes.c_int32, _D, ctypes.c_double, _D]),
             "oracle_full_loss": (ctypes.c_double, [vp, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_double,
                                                    ctypes.c_double, ctypes.c_double]),
@@ -273,7 +275,9 @@ class Oracle:
     def energy(self):
         out = np.empty(5, np.float64)
         lib().oracle_energy(self._s, _p(out, ctypes.c_double))
-        return dict(zip(("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair"), out))
+        d = dict(zip(("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair"), out))
+        d["injected"] = lib().oracle_injected(self._s)
+        return d
 
     def transport_grad(self, nsteps, cw, kin):
         """Continuous-deposition transport run of nsteps with the loss sum(cw * n^) + kin * KE and
@@ -480,7 +484,9 @@ class Oracle3D:
     def energy(self):
         out = np.empty(5, np.float64)
         lib().oracle3_energy(self._s, _p(out, ctypes.c_double))
-        return dict(zip(("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair"), out))
+        d = dict(zip(("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair"), out))
+        d["injected"] = lib().oracle3_injected(self._s)
+        return d
 
 
 def deposit_density3(nx, ny, nz, x, y, z):

@@ -94,6 +94,8 @@ typedef struct {
     /* laser */
     double E0, omega, kwave, t_ant, w_ant, R_ant, gouy_ant, amp_ant;
     int k_ant;
+    double injected;                    /* field energy that crossed the row below the antenna
+                                           towards the slab (J per metre of y)               */
 } ostate;
 
 static int64_t imod(int64_t a, int64_t n) { int64_t r = a % n; return r < 0 ? r + n : r; }
@@ -459,10 +461,25 @@ static void full_step_E(ostate* s)
             Ez[c] += h * (By[c] - By[NODE(s, (i + nx - 1) % nx, k)]) - cjx * (double)s->J[2][c];
             (void)ip;
         }
+    /* injected energy: Poynting flux S_z = (Ex By - Ey Bx) / mu0 through the node row below the
+     * antenna, E at the half step (mean of old and new), B at the half step, B averaged over the
+     * half rows on either side; energy moving towards the slab (-z) counts positive */
+    int kp = s->k_ant - 1;
+    if (kp >= 1 && kp < nz) {
+        double mu0 = 1.0 / (O_EPS0 * O_C * O_C), sum = 0.0;
+        for (int i = 0; i < nx; i++) {
+            size_t c = NODE(s, i, kp), d = NODE(s, i, kp - 1);
+            double ex = 0.5 * (Ex[c] + nEx[c]), ey = 0.5 * (Ey[c] + nEy[c]);
+            sum += ex * 0.5 * (By[d] + By[c]) - ey * 0.5 * (Bx[d] + Bx[c]);
+        }
+        s->injected -= sum / mu0 * s->c.dx * s->dt;
+    }
     memcpy(Ex, nEx, sizeof(double) * nn);
     memcpy(Ey, nEy, sizeof(double) * nn);
     free(nEx); free(nEy);
 }
+
+double oracle_injected(const ostate* s) { return s->injected; }
 
 /* ---------------------------------------------------------------------------------------- */
 /* state management                                                                          */
@@ -766,6 +783,7 @@ typedef struct {
     int64_t step;
     double E0, omega, kwave, t_ant, w_ant, R_ant, gouy_ant, amp_ant;
     int k_ant;
+    double injected;                    /* energy through the plane below the antenna (J)   */
 } ostate3;
 
 static int64_t hat3q(int64_t X, int64_t j) { int64_t d = X - Q3 * j; if (d < 0) d = -d; return d < Q3 ? Q3 - d : 0; }
@@ -1009,10 +1027,24 @@ static void full_step_E3(ostate3* s)
                 /* dEz/dt = c^2 (dBy/dx - dBx/dy) - Jz/eps0 */
                 Ez[c] += h * ((By[c] - By[N3(s, im, j, k)]) - (Bx[c] - Bx[N3(s, i, jm, k)])) - cj * (double)s->J[2][c];
             }
+    /* injected energy through the node plane below the antenna (as in 2D, per cell area dx^2) */
+    int kp = s->k_ant - 1;
+    if (kp >= 1 && kp < nz) {
+        double mu0 = 1.0 / (O_EPS0 * O_C * O_C), sum = 0.0;
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t c = N3(s, i, j, kp), d = N3(s, i, j, kp - 1);
+                double ex = 0.5 * (Ex[c] + nEx[c]), ey = 0.5 * (Ey[c] + nEy[c]);
+                sum += ex * 0.5 * (By[d] + By[c]) - ey * 0.5 * (Bx[d] + Bx[c]);
+            }
+        s->injected -= sum / mu0 * s->c.dx * s->c.dx * s->dt;
+    }
     memcpy(Ex, nEx, sizeof(double) * nn);
     memcpy(Ey, nEy, sizeof(double) * nn);
     free(nEx); free(nEy);
 }
+
+double oracle3_injected(const ostate3* s) { return s->injected; }
 
 static void alloc_species3(ostate3* s, int sp, int64_t n)
 {

@@ -532,3 +532,19 @@ def test_jy_current_drives_ey():
     Ey = o.get_field(1)
     expect = o.dt * QE * n_e * vy / EPS0
     np.testing.assert_allclose(Ey[1:nz], expect[1:nz], rtol=1e-12)
+
+
+def test_injected_energy_of_a_plane_wave_pulse():
+    """The energy the antenna sends towards the slab, summed as the Poynting flux through the row
+    below it over the whole pulse, equals I0 Lx tau sqrt(pi / (4 ln 2)) per metre of y
+    (intensity envelope exp(-4 ln2 t^2 / tau^2)) in vacuum."""
+    nx, nz = 4, 300
+    tau = 5e-15
+    w = workload("tiny", nx=nx, nz=nz, slab_k=100, laser_profile=1, I0=1e17, tau_fwhm=tau, t_peak=15e-15)
+    o = oracle.Oracle(w, with_particles=False)
+    o.step(1300)                          # 29 fs: the whole pulse has crossed the plane
+    expect = 1e17 * nx * w["dx"] * tau * math.sqrt(math.pi / (4 * math.log(2)))
+    assert o.energy()["injected"] == pytest.approx(expect, rel=0.005)
+    # and it is the field energy now in the domain plus what the bottom wall absorbed: no more than injected
+    e = o.energy()
+    assert e["field_E"] + e["field_B"] <= e["injected"] * 1.01
