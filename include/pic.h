@@ -105,6 +105,8 @@ typedef struct pic_info {
 typedef struct pic_energy_t {
     double kinetic_ion, kinetic_electron, field_E, field_B, pair;
     int64_t step;
+    double injected;   /* energy the laser sent towards the slab so far: the Poynting flux through
+                          the node row (plane) below the antenna, summed over the steps */
 } pic_energy_t;
 
 typedef struct pic_ctx pic_ctx;

@@ -46,7 +46,7 @@ class pic_info(ctypes.Structure):
 class pic_energy_t(ctypes.Structure):
     _fields_ = [("kinetic_ion", ctypes.c_double), ("kinetic_electron", ctypes.c_double),
                 ("field_E", ctypes.c_double), ("field_B", ctypes.c_double), ("pair", ctypes.c_double),
-                ("step", ctypes.c_int64)]
+                ("step", ctypes.c_int64), ("injected", ctypes.c_double)]
 
 
 class pic_state_view(ctypes.Structure):

@@ -362,6 +362,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     for (int q = 0; q < 3; q++) ok &= cudaMemsetAsync(c.J[q], 0, 8 * L.nn, c.stream) == cudaSuccess;
     for (int q = 0; q < 2; q++) ok &= cudaMemsetAsync(c.rho[q], 0, 8 * L.nn, c.stream) == cudaSuccess;
     ok &= cudaMemsetAsync(c.mur_save, 0, 4 * 8 * plane, c.stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(c.red_out, 0, 8 * sizeof(double), c.stream) == cudaSuccess;   // incl. the injected-energy sum
     ok &= cudaMemsetAsync(c.status, 0, 16, c.stream) == cudaSuccess;
     if (!ok) {
         delete h;
@@ -472,6 +473,12 @@ int pic_energy(pic_ctx* h, pic_energy_t* out)
     out->field_B = e[3];
     out->pair = e[4];
     out->step = c.step;
+    // injected energy: -sum (Ex By - Ey Bx) / mu0 * (cell edge, or area in 3D) * dt
+    double flux = 0.0;
+    CK(cudaMemcpyAsync(&flux, c.red_out + 5, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    const double mu0 = 1.0 / (kEps0 * kC * kC);
+    out->injected = -flux / mu0 * c.cfg.dx * (c.dims == 3 ? c.cfg.dx : 1.0) * c.dt;
     return PIC_OK;
 }
 
@@ -645,6 +652,7 @@ size_t ckpt_layout(const Ctx& c, size_t* off_sp, size_t* off_tiles, size_t* off_
     t += align256(8 * c.nn);
     *off_j = t;
     t += 3 * align256(8 * c.nn);
+    t += align256(sizeof(double));      // the injected-energy sum
     return t;
 }
 
@@ -669,6 +677,7 @@ int ckpt_copy(pic_ctx* h, char* buf, bool save)
     for (int q = 0; q < 6; q++) CK(cp(c.F[q], of + q * align256(4 * c.nn), 4 * c.nn));
     CK(cp(c.rho[c.cur], orho, 8 * c.nn));
     for (int q = 0; q < 3; q++) CK(cp(c.J[q], oj + q * align256(8 * c.nn), 8 * c.nn));
+    CK(cp(c.red_out + 5, oj + 3 * align256(8 * c.nn), sizeof(double)));
     return PIC_OK;
 }
 

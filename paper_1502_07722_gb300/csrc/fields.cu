@@ -85,16 +85,23 @@ __device__ __forceinline__ float ey_new(const FieldArgs& f, int i, int k, float 
            f.cjy * (float)(long long)f.J[1][c];
 }
 
-__device__ __forceinline__ void E_node(const FieldArgs& f, int i, int k)
+// E update of one node; returns, on the flux row, the node's (Ex By - Ey Bx) at the half step
+// (E the mean of old and new, B averaged over the half rows on either side), else 0
+__device__ __forceinline__ float E_node(const FieldArgs& f, int i, int k)
 {
     const int nx = f.nx, nz = f.nz;
     const size_t c = (size_t)k * nx + i;
     float* Ex = f.F[0];
     float* Ey = f.F[1];
     float* Ez = f.F[2];
+    float s = 0.0f;
     if (k > 0 && k < nz) {
-        Ex[c] = ex_new(f, i, k, Ex[c]);
-        Ey[c] = ey_new(f, i, k, Ey[c]);
+        const float ex0 = Ex[c], ey0 = Ey[c];
+        const float ex1 = ex_new(f, i, k, ex0), ey1 = ey_new(f, i, k, ey0);
+        Ex[c] = ex1;
+        Ey[c] = ey1;
+        if (k == f.k_flux)
+            s = 0.25f * ((ex0 + ex1) * (f.F[4][c - nx] + f.F[4][c]) - (ey0 + ey1) * (f.F[3][c - nx] + f.F[3][c]));
     } else if (k == 0) {
         const float x0 = f.save[0 * nx + i], x1 = f.save[1 * nx + i];
         const float y0 = f.save[4 * nx + i], y1 = f.save[5 * nx + i];
@@ -110,6 +117,15 @@ __device__ __forceinline__ void E_node(const FieldArgs& f, int i, int k)
         const int im = i == 0 ? nx - 1 : i - 1;
         Ez[c] += f.h_e * (f.F[4][c] - f.F[4][(size_t)k * nx + im]) - f.cj * (float)(long long)f.J[2][c];
     }
+    return s;
+}
+
+// the flux row's warp sums into the FP64 accumulator
+__device__ __forceinline__ void add_flux(const FieldArgs& f, int k, float s)
+{
+    if (k != f.k_flux) return;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.0f) atomicAdd(f.flux, (double)s);
 }
 
 __global__ void k_half_B(const FieldArgs f, int save)
@@ -121,7 +137,8 @@ __global__ void k_half_B(const FieldArgs f, int save)
 __global__ void k_E(const FieldArgs f)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < f.nx) E_node(f, i, blockIdx.y);
+    const float s = i < f.nx ? E_node(f, i, blockIdx.y) : 0.0f;
+    add_flux(f, blockIdx.y, s);
 }
 
 __global__ void k_half_B_batch(const FieldArgs* __restrict__ fa, int save)
@@ -135,7 +152,9 @@ __global__ void k_E_batch(const FieldArgs* __restrict__ fa)
 {
     const FieldArgs& f = fa[blockIdx.z];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < f.nx && (int)blockIdx.y <= f.nz) E_node(f, i, blockIdx.y);
+    if ((int)blockIdx.y > f.nz) return;                  // uniform over the block
+    const float s = i < f.nx ? E_node(f, i, blockIdx.y) : 0.0f;
+    add_flux(f, blockIdx.y, s);
 }
 
 AntennaParams make_antenna_params(const Ctx& c)
@@ -168,6 +187,8 @@ FieldArgs make_field_args(const Ctx& c)
     f.antc = c.ant_c;
     f.ants = c.ant_s;
     f.ant = c.ant;
+    f.k_flux = c.k_ant - 1 >= 1 ? c.k_ant - 1 : -1;
+    f.flux = c.red_out + 5;
     return f;
 }
 

@@ -662,6 +662,8 @@ struct Field3 {
     const float* antc;    // nx*ny
     const float* ants;
     const float* ant;
+    int k_flux;           // node plane below the antenna (Poynting flux of the injected energy)
+    double* flux;
 };
 
 __global__ void k_half_B3(const Field3 f, int save)
@@ -721,27 +723,38 @@ __global__ void k_E3(const Field3 f)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const Geo3& g = f.g;
-    if (i >= g.nx) return;
-    const size_t c = idx3(g, i, j, k), plane = (size_t)g.nx * g.ny, q = (size_t)j * g.nx + i;
-    float* Ex = f.F[0];
-    float* Ey = f.F[1];
-    if (k > 0 && k < g.nz) {
-        Ex[c] = ex3_new(f, i, j, k, Ex[c]);
-        Ey[c] = ey3_new(f, i, j, k, Ey[c]);
-    } else if (k == 0) {
-        const float x0 = f.save[q], x1 = f.save[plane + q], y0 = f.save[4 * plane + q], y1 = f.save[5 * plane + q];
-        Ex[c] = x1 + f.mur * (ex3_new(f, i, j, 1, x1) - x0);
-        Ey[c] = y1 + f.mur * (ey3_new(f, i, j, 1, y1) - y0);
-    } else {
-        const float x1 = f.save[2 * plane + q], x0 = f.save[3 * plane + q], y1 = f.save[6 * plane + q],
-                    y0 = f.save[7 * plane + q];
-        Ex[c] = x1 + f.mur * (ex3_new(f, i, j, g.nz - 1, x1) - x0);
-        Ey[c] = y1 + f.mur * (ey3_new(f, i, j, g.nz - 1, y1) - y0);
+    float s = 0.0f;            // on the flux plane: this node's (Ex By - Ey Bx) at the half step
+    if (i < g.nx) {
+        const size_t c = idx3(g, i, j, k), plane = (size_t)g.nx * g.ny, q = (size_t)j * g.nx + i;
+        float* Ex = f.F[0];
+        float* Ey = f.F[1];
+        if (k > 0 && k < g.nz) {
+            const float ex0 = Ex[c], ey0 = Ey[c];
+            const float ex1 = ex3_new(f, i, j, k, ex0), ey1 = ey3_new(f, i, j, k, ey0);
+            Ex[c] = ex1;
+            Ey[c] = ey1;
+            if (k == f.k_flux)
+                s = 0.25f * ((ex0 + ex1) * (f.F[4][c - plane] + f.F[4][c]) -
+                             (ey0 + ey1) * (f.F[3][c - plane] + f.F[3][c]));
+        } else if (k == 0) {
+            const float x0 = f.save[q], x1 = f.save[plane + q], y0 = f.save[4 * plane + q], y1 = f.save[5 * plane + q];
+            Ex[c] = x1 + f.mur * (ex3_new(f, i, j, 1, x1) - x0);
+            Ey[c] = y1 + f.mur * (ey3_new(f, i, j, 1, y1) - y0);
+        } else {
+            const float x1 = f.save[2 * plane + q], x0 = f.save[3 * plane + q], y1 = f.save[6 * plane + q],
+                        y0 = f.save[7 * plane + q];
+            Ex[c] = x1 + f.mur * (ex3_new(f, i, j, g.nz - 1, x1) - x0);
+            Ey[c] = y1 + f.mur * (ey3_new(f, i, j, g.nz - 1, y1) - y0);
+        }
+        if (k < g.nz) {
+            const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+            f.F[2][c] += f.h_e * ((f.F[4][c] - f.F[4][idx3(g, im, j, k)]) - (f.F[3][c] - f.F[3][idx3(g, i, jm, k)])) -
+                         f.cj * (float)(long long)f.J[2][c];
+        }
     }
-    if (k < g.nz) {
-        const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
-        f.F[2][c] += f.h_e * ((f.F[4][c] - f.F[4][idx3(g, im, j, k)]) - (f.F[3][c] - f.F[3][idx3(g, i, jm, k)])) -
-                     f.cj * (float)(long long)f.J[2][c];
+    if (k == f.k_flux) {                                  // uniform over the block
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s != 0.0f) atomicAdd(f.flux, (double)s);
     }
 }
 
@@ -775,6 +788,8 @@ void launch_fields3(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches)
     f.antc = c.ant_c;
     f.ants = c.ant_s;
     f.ant = c.ant;
+    f.k_flux = c.k_ant - 1 >= 1 ? c.k_ant - 1 : -1;
+    f.flux = c.red_out + 5;
     k_antenna3<<<1, 1, 0, st>>>(make_antenna_params(c), (long long)step, c.ant);
     dim3 block(256), grid((c.nx + 255) / 256, c.ny, c.nz + 1);
     k_half_B3<<<grid, block, 0, st>>>(f, 1);

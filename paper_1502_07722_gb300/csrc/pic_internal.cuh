@@ -132,6 +132,8 @@ struct FieldArgs {
     const float* antc;   // nx: amplitude * cos(phase(x))
     const float* ants;   // nx: amplitude * sin(phase(x))
     const float* ant;    // 2: this step's antenna scalars
+    int k_flux;          // node row below the antenna: Poynting flux of the injected energy
+    double* flux;        // accumulates sum (Ex By - Ey Bx) over that row at the half step
 };
 
 // kernels launched from the host side of the library (defined in the .cu files)

@@ -144,9 +144,11 @@ def test_energy3_matches_oracle(gb):
     sim.step(3)
     orc.step(3)
     eg, eo = sim.energy(), orc.energy()
-    tg = sum(v for k, v in eg.items() if k != "step")
-    to = sum(eo.values())
+    stored = ("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair")
+    tg = sum(eg[k] for k in stored)
+    to = sum(eo[k] for k in stored)
     assert tg == pytest.approx(to, rel=1e-3)
+    assert eg["injected"] == pytest.approx(eo["injected"], rel=1e-4, abs=1e-6 * abs(eo["field_E"]))
     assert eg["pair"] == pytest.approx(eo["pair"], rel=1e-3)
     assert eg["kinetic_electron"] == pytest.approx(eo["kinetic_electron"], rel=1e-3)
 
