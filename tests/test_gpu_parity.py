@@ -322,3 +322,44 @@ def test_transport_1000_steps_energy_drift_and_profile():
     pg = sim.get_density().cpu().numpy().sum(axis=1).astype(np.float64)
     po = orc.get_rho().sum(axis=1).astype(np.float64)
     assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-3
+
+
+def test_transport_acoustic_wave_period():
+    """The GPU transport stage carries a small standing acoustic wave (64-cell wavelength, strain
+    1e-3) with the period of the linearised Eqs. (1)-(3), lambda / sqrt(24 D / m), over 2.5
+    periods (8300 steps), like the oracle."""
+    import math
+    nx, nz = 64, 4
+    dt = 50e-15
+    w = workload("transport", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, T_ion_K=0.0, dt_override=dt,
+                 max_particles=nx * nz * 4)
+    sim = gb().Simulation(w, sort_every=0)
+    cells = np.arange(nx * nz)
+    i, k = cells % nx, cells // nx
+    offs = [(0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75)]
+    x0 = np.concatenate([i + a for a, b in offs]).astype(np.float64)
+    z0 = np.concatenate([k + b for a, b in offs]).astype(np.float64)
+    kk = 2 * math.pi / nx
+    eps = 1e-2
+    cell, fx, fz = from_global(x0 + eps * np.sin(kk * x0), z0, nx)
+    zeros = np.zeros(len(x0), np.float32)
+    sim.set_particles(0, cell, fx, fz, zeros, zeros, zeros)
+    g = sim.get_particles(0)                    # the context's order
+    xg, _, _ = to_global(g, nx)
+    xeq = np.round((xg - 0.25) * 2) / 2 + 0.25  # nearest lattice site (0.25 + multiples of 0.5)
+    m = 63.546 * 1.66053906660e-27
+    period = (nx * w["dx"]) / math.sqrt(24 * 0.41 * 1.602176634e-19 / m)
+    amps = []
+    chunk = 20
+    for s in range(0, int(2.5 * period / dt), chunk):
+        sim.step(chunk)
+        x, _, _ = to_global(sim.get_particles(0), nx)
+        d = (x - xeq + nx / 2) % nx - nx / 2
+        amps.append((s + chunk, (d * np.sin(kk * xeq)).sum() / (np.sin(kk * xeq) ** 2).sum()))
+    a = np.array(amps)
+    crossings = [a[j - 1, 0] + (a[j, 0] - a[j - 1, 0]) * a[j - 1, 1] / (a[j - 1, 1] - a[j, 1])
+                 for j in range(1, len(a)) if (a[j - 1, 1] > 0) != (a[j, 1] > 0)]
+    assert len(crossings) >= 4
+    assert 2 * np.diff(crossings).mean() * dt == pytest.approx(period, rel=1e-2)
+    assert np.abs(a[:, 1]).max() == pytest.approx(eps, rel=2e-2)
+    sim.close()

@@ -548,3 +548,40 @@ def test_injected_energy_of_a_plane_wave_pulse():
     # and it is the field energy now in the domain plus what the bottom wall absorbed: no more than injected
     e = o.energy()
     assert e["field_E"] + e["field_B"] <= e["injected"] * 1.01
+
+
+def test_acoustic_wave_speed_of_the_pair_force():
+    """Linearising Eqs. (1)-(3) about the equilibrium lattice (n = n0, rbar = r0) gives the wave
+    equation u_tt = (U''(r0) r0^2 / (3 m)) u_xx = (24 D / m) u_xx for a small longitudinal
+    displacement u: a standing wave of wavelength 64 cells in the transport mode oscillates with
+    period lambda / sqrt(24 D / m) and keeps its amplitude."""
+    nx, nz = 64, 4
+    dt = 50e-15
+    w = workload("transport", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, T_ion_K=0.0, dt_override=dt)
+    o = oracle.Oracle(w, with_particles=False)
+    cells = np.arange(nx * nz)
+    i, k = cells % nx, cells // nx
+    offs = [(0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75)]
+    x0 = np.concatenate([i + a for a, b in offs]).astype(float)
+    z0 = np.concatenate([k + b for a, b in offs]).astype(float)
+    kk = 2 * math.pi / nx
+    eps = 1e-3
+    n = len(x0)
+    o.set_particles(0, x0 + eps * np.sin(kk * x0), z0, np.zeros(n), np.zeros(n), np.zeros(n))
+    m = 63.546 * 1.66053906660e-27
+    period = (nx * w["dx"]) / math.sqrt(24 * 0.41 * QE / m)
+    amps = []
+    chunk = 20
+    for s in range(0, int(2.5 * period / dt), chunk):
+        o.step(chunk)
+        d = (o.get_particles(0)["x"] - x0 + nx / 2) % nx - nx / 2
+        amps.append((s + chunk, (d * np.sin(kk * x0)).sum() / (np.sin(kk * x0) ** 2).sum()))
+    a = np.array(amps)
+    crossings = []
+    for j in range(1, len(a)):
+        if (a[j - 1, 1] > 0) != (a[j, 1] > 0):
+            crossings.append(a[j - 1, 0] + (a[j, 0] - a[j - 1, 0]) * a[j - 1, 1] / (a[j - 1, 1] - a[j, 1]))
+    assert len(crossings) >= 4
+    measured = 2 * np.diff(crossings).mean() * dt
+    assert measured == pytest.approx(period, rel=5e-3)
+    assert np.abs(a[:, 1]).max() == pytest.approx(eps, rel=1e-2)
