@@ -7,25 +7,24 @@
 //  * one CTA owns one tile of T x T cells at a time (particles are sorted into tiles, and by
 //    cell inside a tile);
 //  * the CTA stages a window of (T + 2M + 3)^2 nodes in shared memory: the six field
-//    components and the pair density n / n0 in FP32, and four exact 64-bit accumulators (new
-//    node density, J_x, J_y, J_z), each kept as a (high, low) pair of 32-bit words: the low word
-//    is added atomically with its old value returned and the carry goes to the high word. 32-bit
-//    shared atomics are native; 64-bit ones are not, and with a whole warp on one address they
-//    cost ~20x more;
+//    components and the pair density n / n0 in FP32;
 //  * particles stream through shared memory in chunks of up to 1024: loaded and stored with
 //    coalesced accesses, processed transposed, so that lane l of a warp takes the particle R
 //    places after lane l-1 in the cell-sorted order. Lanes then sit in different cells and their
 //    deposits rarely meet on one address;
+//  * deposits (current, node-density change) are exact 64-bit integer reductions straight into
+//    global memory: fire-and-forget on the SM, native in L2. Measured against exact sums in the
+//    shared-memory window (32-bit (lo, hi) pairs whose low-word atomic must return the old value
+//    for the carry) they are slightly faster and free 17 KB of shared memory per CTA;
 //  * the node density is updated incrementally: the next density starts as a copy of the
 //    current one and each pair particle adds S(new) - S(old) only when its fixed-point position
 //    changed. Ions move ~1e-7 cells per step against a quantum of 1.5e-5 cells, so most of them
 //    deposit nothing; the integer result equals a full re-deposit bit for bit;
 //  * a particle that stays in its cell (almost all of them) deposits on the four corners of the
-//    cell; a particle that crossed a cell edge uses the 3 x 3 Esirkepov stencil; a particle that
-//    drifted beyond the margin since the last sort uses global memory (rare);
+//    cell; a particle that crossed a cell edge uses the 3 x 3 Esirkepov stencil (rare); a particle
+//    that drifted beyond the margin since the last sort gathers from global memory (rare);
 //  * the code is specialised per species kind (ion, electron, neutral atom), so no per-particle
-//    branch tests a species property;
-//  * the window is flushed with one global 64-bit atomic per non-zero node.
+//    branch tests a species property.
 // Integer sums make every result independent of the order of the additions.
 #include "pic_device.cuh"
 
@@ -45,28 +44,17 @@ __device__ __forceinline__ int wrap_any(int i, int nx)
     return r < 0 ? r + nx : r;
 }
 
-// exact 64-bit accumulation into a (hi, lo) pair of shared 32-bit words
-__device__ __forceinline__ void acc64(unsigned* lo, int* hi, long long v)
-{
-    const unsigned l = (unsigned)v;
-    int h = (int)(v >> 32);
-    const unsigned old = atomicAdd(lo, l);
-    h += (old + l < old) ? 1 : 0;
-    if (h != 0) atomicAdd(hi, h);
-}
-
 struct Window {
-    unsigned* lo[4];     // 0: node density change, 1: J_x, 2: J_y, 3: J_z
-    int* hi[4];
     float* f[6];
     float* nh;
     int ox, oz, W;
 };
 
-__device__ __forceinline__ void wadd(const Window& w, int q, int idx, long long v)
+__device__ __forceinline__ void red64g(u64* p, long long v)
 {
-    if (v != 0) acc64(w.lo[q] + idx, w.hi[q] + idx, v);
+    if (v != 0) atomicAdd(p, (u64)v);
 }
+
 
 // exact cell -> (i, k): q = floor(cell / nx) from a multiply-high and one correction
 __device__ __forceinline__ void split_cell(int cell, int nx, unsigned magic, int& i, int& k)
@@ -308,81 +296,34 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     if (!moved && V == 0) return;                 // nothing to deposit (most ions)
 
     if (inwin && (di | dk) == 0) {
-        // the particle stays in its cell: stencil = the four corners of the cell
-        const int base = lz * W + lx;
+        // the particle stays in its cell: stencil = the four corners of the cell (global reductions)
+        const int i1 = i + 1 == nx ? 0 : i + 1;
+        const size_t g00 = (size_t)k * nx + i, g10 = (size_t)k * nx + i1, g01 = g00 + nx, g11 = g10 + nx;
         if (kCurrent) {
             const int dX = kSign * (x1 - x0), dZ = kSign * (z1 - z0);
             if (dX != 0) {
-                acc64(w.lo[1] + base, w.hi[1] + base, (long long)dX * (2 * kQOne - z0 - z1));
-                acc64(w.lo[1] + base + W, w.hi[1] + base + W, (long long)dX * (z0 + z1));
+                red64g(a.J[0] + g00, (long long)dX * (2 * kQOne - z0 - z1));
+                red64g(a.J[0] + g01, (long long)dX * (z0 + z1));
             }
             if (dZ != 0) {
-                acc64(w.lo[3] + base, w.hi[3] + base, (long long)dZ * (2 * kQOne - x0 - x1));
-                acc64(w.lo[3] + base + 1, w.hi[3] + base + 1, (long long)dZ * (x0 + x1));
+                red64g(a.J[2] + g00, (long long)dZ * (2 * kQOne - x0 - x1));
+                red64g(a.J[2] + g10, (long long)dZ * (x0 + x1));
             }
             if (V != 0) {
-                // 6 Wy = 6 Q^2 - 3 Q (x0 + x1) - 3 Q (z0 + z1) + P on the lower-left corner, etc.
                 const long long P = (long long)x0 * (2 * z0 + z1) + (long long)x1 * (z0 + 2 * z1);
                 const long long sx = 3LL * kQOne * (x0 + x1), sz = 3LL * kQOne * (z0 + z1);
-                // all four weights are non-zero except on a cell edge: no per-term test
-                acc64(w.lo[2] + base, w.hi[2] + base, V * (6LL * kQOne * kQOne - sx - sz + P));
-                acc64(w.lo[2] + base + 1, w.hi[2] + base + 1, V * (sx - P));
-                acc64(w.lo[2] + base + W, w.hi[2] + base + W, V * (sz - P));
-                acc64(w.lo[2] + base + W + 1, w.hi[2] + base + W + 1, V * P);
+                red64g(a.J[1] + g00, V * (6LL * kQOne * kQOne - sx - sz + P));
+                red64g(a.J[1] + g10, V * (sx - P));
+                red64g(a.J[1] + g01, V * (sz - P));
+                red64g(a.J[1] + g11, V * P);
             }
         }
         if (kPair && moved) {
-            // node density change: S(new) - S(old) on the four corners
             const long long a0 = kQOne - x0, a1 = kQOne - x1, c0 = kQOne - z0, c1 = kQOne - z1;
-            acc64(w.lo[0] + base, w.hi[0] + base, a1 * c1 - a0 * c0);
-            acc64(w.lo[0] + base + 1, w.hi[0] + base + 1, (long long)x1 * c1 - (long long)x0 * c0);
-            acc64(w.lo[0] + base + W, w.hi[0] + base + W, a1 * z1 - a0 * z0);
-            acc64(w.lo[0] + base + W + 1, w.hi[0] + base + W + 1, (long long)x1 * z1 - (long long)x0 * z0);
-        }
-    } else if (inwin) {
-        // a cell edge was crossed: 3 x 3 Esirkepov stencil in the window
-        const int XL0 = lx * kQOne + x0, XL1 = XL0 + di * kQOne + x1 - x0;
-        const int ZL0 = lz * kQOne + z0, ZL1 = ZL0 + dk * kQOne + z1 - z0;
-        const int bxl = min(XL0, XL1) >> kQBits, bzl = min(ZL0, ZL1) >> kQBits;
-        int S0x[3], S1x[3], S0z[3], S1z[3];
-        hat3(XL0 - bxl * kQOne, S0x[0], S0x[1], S0x[2]);
-        hat3(XL1 - bxl * kQOne, S1x[0], S1x[1], S1x[2]);
-        hat3(ZL0 - bzl * kQOne, S0z[0], S0z[1], S0z[2]);
-        hat3(ZL1 - bzl * kQOne, S1z[0], S1z[1], S1z[2]);
-        const int b0 = bzl * W + bxl;
-        if (kCurrent) {
-#pragma unroll
-            for (int b = 0; b < 3; b++) {
-                const long long wz = kSign * (long long)(S0z[b] + S1z[b]);
-                long long acc = -(long long)(S1x[0] - S0x[0]) * wz;
-                wadd(w, 1, b0 + b * W, acc);
-                acc -= (long long)(S1x[1] - S0x[1]) * wz;
-                wadd(w, 1, b0 + b * W + 1, acc);
-            }
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const long long wx = kSign * (long long)(S0x[c] + S1x[c]);
-                long long acc = -(long long)(S1z[0] - S0z[0]) * wx;
-                wadd(w, 3, b0 + c, acc);
-                acc -= (long long)(S1z[1] - S0z[1]) * wx;
-                wadd(w, 3, b0 + W + c, acc);
-            }
-            if (V != 0) {
-#pragma unroll
-                for (int b = 0; b < 3; b++)
-#pragma unroll
-                    for (int c = 0; c < 3; c++)
-                        wadd(w, 2, b0 + b * W + c,
-                             V * (2LL * S0x[c] * S0z[b] + (long long)S1x[c] * S0z[b] + (long long)S0x[c] * S1z[b] +
-                                  2LL * S1x[c] * S1z[b]));
-            }
-        }
-        if (kPair) {
-#pragma unroll
-            for (int b = 0; b < 3; b++)
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    wadd(w, 0, b0 + b * W + c, (long long)S1x[c] * S1z[b] - (long long)S0x[c] * S0z[b]);
+            red64g(a.rho_next + g00, a1 * c1 - a0 * c0);
+            red64g(a.rho_next + g10, (long long)x1 * c1 - (long long)x0 * c0);
+            red64g(a.rho_next + g01, a1 * z1 - a0 * z0);
+            red64g(a.rho_next + g11, (long long)x1 * z1 - (long long)x0 * z0);
         }
     } else {
         // deposit_global applies the charge sign itself: hand it the unsigned code kSign * V
@@ -399,14 +340,10 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
     const int W = a.W, WW = W * W;
     Window w;
     w.W = W;
-    for (int q = 0; q < 4; q++) {
-        w.lo[q] = smem + (2 * q) * WW;
-        w.hi[q] = reinterpret_cast<int*>(smem + (2 * q + 1) * WW);
-    }
-    float* fbase = reinterpret_cast<float*>(smem + 8 * WW);
+    float* fbase = reinterpret_cast<float*>(smem);
     for (int q = 0; q < 6; q++) w.f[q] = fbase + q * WW;
     w.nh = fbase + 6 * WW;
-    unsigned* chunk = smem + 15 * WW;
+    unsigned* chunk = smem + 7 * WW;
     int* c_cell = reinterpret_cast<int*>(chunk);
     float* c_f[5];
     for (int q = 0; q < 5; q++) c_f[q] = reinterpret_cast<float*>(chunk + (q + 1) * kChunkWords);
@@ -421,11 +358,9 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
         const int tx = t % a.ntx, tz = t / a.ntx;
         w.ox = tx * a.T - kMargin - 1;
         w.oz = tz * a.T - kMargin - 1;
-        // stage the window: zero accumulators, fields, pair density (wall rows doubled)
+        // stage the window: fields, pair density (wall rows doubled)
         for (int j = threadIdx.x; j < WW; j += blockDim.x) {
             const int b = j / W, c = j - b * W;
-#pragma unroll
-            for (int q = 0; q < 4; q++) { w.lo[q][j] = 0u; w.hi[q][j] = 0; }
             const int gx = wrap_any(w.ox + c, a.nx);
             const int gz = w.oz + b;
             const int gn = min(max(gz, 0), a.nz);          // node rows 0..nz
@@ -497,18 +432,6 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
                 __syncthreads();
             }
         }
-        for (int j = threadIdx.x; j < WW; j += blockDim.x) {
-            const int b = j / W, c = j - b * W;
-            const int gz = w.oz + b;
-            if (gz < 0 || gz > a.nz) continue;
-            const size_t g = (size_t)gz * a.nx + wrap_any(w.ox + c, a.nx);
-            u64* dst[4] = {a.rho_next, a.J[0], a.J[1], a.J[2]};
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const long long v = ((long long)w.hi[q][j] << 32) + (long long)w.lo[q][j];
-                if (v != 0) atomicAdd(dst[q] + g, (u64)v);
-            }
-        }
         __syncthreads();
     }
 }
@@ -539,7 +462,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles_batch(int nslab, int to
     }
 }
 
-size_t particle_smem_bytes(int W) { return sizeof(unsigned) * ((size_t)15 * W * W + 6 * kChunkWords); }
+size_t particle_smem_bytes(int W) { return sizeof(unsigned) * ((size_t)7 * W * W + 6 * kChunkWords); }
 
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
 {
