@@ -246,15 +246,18 @@ typedef struct pic_state_view {
 PIC_API int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* in, double* dev_out5, void* stream);
 
 /* ---- checkpoint / resume ------------------------------------------------------------------
- * A checkpoint is a device buffer (caller-owned, 256-byte aligned, pic_checkpoint_size bytes) with
- * the particles, tile offsets, fields, node density, current and step counter of a context.
- * Restoring it into the same context resumes bit for bit: same grids, same particle set (a cell sort
- * after the restore may order the particles of one cell differently). pic_checkpoint_save is
- * asynchronous on the context's stream; pic_checkpoint_restore synchronises (it checks the
- * buffer's header) and returns PIC_EINVAL for a buffer that holds no checkpoint of this layout. */
+ * A checkpoint is a caller-owned buffer of pic_checkpoint_size bytes, in device memory (256-byte
+ * aligned) or host memory (on_host != 0; pinned memory makes the copies faster), holding the
+ * particles, tile offsets, fields, node density, current, the injected-energy sum and the step
+ * counter of a context. Restoring it into the same context, or into a new context made from the
+ * same configuration (another process, after writing the host buffer to disk), resumes bit for
+ * bit: same grids, same particle set (a cell sort after the restore may order the particles of
+ * one cell differently). A device save is asynchronous on the context's stream; a host save and
+ * every restore synchronise. pic_checkpoint_restore returns PIC_EINVAL for a buffer that holds no
+ * checkpoint of this layout. */
 PIC_API int pic_checkpoint_size(pic_ctx* ctx, size_t* bytes);
-PIC_API int pic_checkpoint_save(pic_ctx* ctx, void* dev_buf);
-PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* dev_buf);
+PIC_API int pic_checkpoint_save(pic_ctx* ctx, void* buf, int32_t on_host);
+PIC_API int pic_checkpoint_restore(pic_ctx* ctx, const void* buf, int32_t on_host);
 
 /* ---- differentiable cycle (2D, sort_every = 0, pot_mode 0) ----------------------------------
  * Gradients of L = sum_nodes w(node) n(node)/n0 (pair-species density at the final state)

@@ -92,8 +92,8 @@ _SIGNATURES = {
     "pic_batch_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "pic_batch_free": (None, [_VP]),
     "pic_checkpoint_size": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
-    "pic_checkpoint_save": (ctypes.c_int, [_VP, _VP]),
-    "pic_checkpoint_restore": (ctypes.c_int, [_VP, _VP]),
+    "pic_checkpoint_save": (ctypes.c_int, [_VP, _VP, _I32]),
+    "pic_checkpoint_restore": (ctypes.c_int, [_VP, _VP, _I32]),
     "pic_node_functional": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "pic_adjoint_seed": (ctypes.c_int, [_VP, ctypes.c_double, _VP, ctypes.POINTER(pic_adjoint_buffers),
                                         ctypes.POINTER(ctypes.c_double)]),
@@ -279,12 +279,12 @@ def pic_checkpoint_size(h) -> int:
     return n.value
 
 
-def pic_checkpoint_save(h, dev_ptr):
-    _check(load_library().pic_checkpoint_save(h, dev_ptr), "pic_checkpoint_save")
+def pic_checkpoint_save(h, ptr, on_host=False):
+    _check(load_library().pic_checkpoint_save(h, ptr, 1 if on_host else 0), "pic_checkpoint_save")
 
 
-def pic_checkpoint_restore(h, dev_ptr):
-    _check(load_library().pic_checkpoint_restore(h, dev_ptr), "pic_checkpoint_restore")
+def pic_checkpoint_restore(h, ptr, on_host=False):
+    _check(load_library().pic_checkpoint_restore(h, ptr, 1 if on_host else 0), "pic_checkpoint_restore")
 
 
 def pic_node_functional(h, dev_weights_ptr) -> float:
@@ -349,15 +349,18 @@ class Simulation:
     def sort(self):
         pic_sort(self.h)
 
-    def checkpoint(self, out=None):
-        """Save the whole state into a device buffer (allocated when not given) and return it."""
+    def checkpoint(self, out=None, on_host=False):
+        """Save the whole state into a buffer (allocated when not given: a device tensor, or a
+        pinned host tensor with on_host) and return it."""
         if out is None:
-            out = self.torch.empty(pic_checkpoint_size(self.h), dtype=self.torch.uint8, device="cuda")
-        pic_checkpoint_save(self.h, out.data_ptr())
+            n = pic_checkpoint_size(self.h)
+            out = (self.torch.empty(n, dtype=self.torch.uint8).pin_memory() if on_host
+                   else self.torch.empty(n, dtype=self.torch.uint8, device="cuda"))
+        pic_checkpoint_save(self.h, out.data_ptr(), out.device.type == "cpu")
         return out
 
     def restore(self, buf):
-        pic_checkpoint_restore(self.h, buf.data_ptr())
+        pic_checkpoint_restore(self.h, buf.data_ptr(), buf.device.type == "cpu")
 
     def _shape(self):
         return (self.nz + 1, self.ny, self.nx) if self.dims == 3 else (self.nz + 1, self.nx)

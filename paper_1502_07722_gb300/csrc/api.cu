@@ -656,12 +656,12 @@ size_t ckpt_layout(const Ctx& c, size_t* off_sp, size_t* off_tiles, size_t* off_
     return t;
 }
 
-int ckpt_copy(pic_ctx* h, char* buf, bool save)
+int ckpt_copy(pic_ctx* h, char* buf, bool save, bool on_host)
 {
     Ctx& c = h->c;
     size_t osp[2], otl[2], of, orho, oj;
     ckpt_layout(c, osp, otl, &of, &orho, &oj);
-    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind k = !on_host ? cudaMemcpyDeviceToDevice : (save ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
     auto cp = [&](void* dev, size_t off, size_t bytes) -> cudaError_t {
         return save ? cudaMemcpyAsync(buf + off, dev, bytes, k, c.stream) : cudaMemcpyAsync(dev, buf + off, bytes, k, c.stream);
     };
@@ -691,9 +691,9 @@ int pic_checkpoint_size(pic_ctx* h, size_t* bytes)
     return PIC_OK;
 }
 
-int pic_checkpoint_save(pic_ctx* h, void* dev_buf)
+int pic_checkpoint_save(pic_ctx* h, void* buf, int32_t on_host)
 {
-    if (!h || !dev_buf || ((uintptr_t)dev_buf & 255)) return PIC_EINVAL;
+    if (!h || !buf || (!on_host && ((uintptr_t)buf & 255))) return PIC_EINVAL;
     Ctx& c = h->c;
     if (c.sticky) return c.sticky;
     CkptHeader hd;
@@ -704,23 +704,34 @@ int pic_checkpoint_save(pic_ctx* h, void* dev_buf)
     hd.n[1] = c.nsp > 1 ? c.sp[1].n : 0;
     hd.steps_since_sort = c.steps_since_sort;
     hd.nsp = c.nsp;
+    if (on_host) {
+        memcpy(buf, &hd, sizeof(hd));
+        int r = ckpt_copy(h, (char*)buf, true, true);
+        if (r) return r;
+        CK(cudaStreamSynchronize(c.stream));             // the host copy is complete on return
+        return PIC_OK;
+    }
     // a pageable source: the call returns once the header has been staged, so hd may go out of scope
-    CK(cudaMemcpyAsync(dev_buf, &hd, sizeof(hd), cudaMemcpyHostToDevice, c.stream));
-    return ckpt_copy(h, (char*)dev_buf, true);
+    CK(cudaMemcpyAsync(buf, &hd, sizeof(hd), cudaMemcpyHostToDevice, c.stream));
+    return ckpt_copy(h, (char*)buf, true, false);
 }
 
-int pic_checkpoint_restore(pic_ctx* h, const void* dev_buf)
+int pic_checkpoint_restore(pic_ctx* h, const void* buf, int32_t on_host)
 {
-    if (!h || !dev_buf || ((uintptr_t)dev_buf & 255)) return PIC_EINVAL;
+    if (!h || !buf || (!on_host && ((uintptr_t)buf & 255))) return PIC_EINVAL;
     Ctx& c = h->c;
     CkptHeader hd;
-    CK(cudaMemcpyAsync(&hd, dev_buf, sizeof(hd), cudaMemcpyDeviceToHost, c.stream));
-    CK(cudaStreamSynchronize(c.stream));
+    if (on_host) {
+        memcpy(&hd, buf, sizeof(hd));
+    } else {
+        CK(cudaMemcpyAsync(&hd, buf, sizeof(hd), cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
     if (hd.magic != kCkptMagic || hd.nsp != c.nsp) return PIC_EINVAL;
     for (int s = 0; s < c.nsp; s++)
         if (hd.n[s] < 0 || hd.n[s] > c.sp[s].cap) return PIC_EINVAL;
     for (int s = 0; s < c.nsp; s++) c.sp[s].n = hd.n[s];
-    int r = ckpt_copy(h, (char*)const_cast<void*>(dev_buf), false);
+    int r = ckpt_copy(h, (char*)const_cast<void*>(buf), false, on_host != 0);
     if (r) return r;
     c.step = hd.step;
     c.steps_since_sort = hd.steps_since_sort;

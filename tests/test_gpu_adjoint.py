@@ -55,6 +55,37 @@ def test_checkpoint_resume_bit_exact(gb):
     sim.close()
 
 
+def test_checkpoint_to_disk_resumes_in_a_new_context(gb, tmp_path):
+    """A host checkpoint written to a file and restored into a fresh context of the same
+    configuration continues exactly like the original context (with the injected-energy sum)."""
+    w = workload("tiny", laser_profile=2, w0=0.2e-6, I0=1e19, t_peak=5 * 2.24e-17)
+    sim = gb.Simulation(w, sort_every=3)
+    sim.step(6)
+    path = tmp_path / "state.ckpt"
+    sim.checkpoint(on_host=True).numpy().tofile(path)
+    sim.step(5)
+    a, ea = _state(sim), sim.energy()
+    sim.close()
+    other = gb.Simulation(w, sort_every=3, seed=w["seed"] + 99)     # a different initial slab
+    buf = torch.from_numpy(np.fromfile(path, dtype=np.uint8)).pin_memory()
+    other.restore(buf)
+    assert other.info()["step"] == 6
+    other.step(5)
+    _equal(a, _state(other))
+    eb = other.energy()
+    for k in ("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair", "injected"):
+        assert ea[k] == eb[k], k
+    other.close()
+
+
+def test_checkpoint_rejects_foreign_buffers(gb):
+    sim = gb.Simulation(workload("tiny"))
+    junk = torch.zeros(gb.pic_checkpoint_size(sim.h), dtype=torch.uint8)
+    with pytest.raises(gb.PicError):
+        sim.restore(junk)
+    sim.close()
+
+
 def small_transport(**kw):
     d = dict(nx=24, nz=24, slab_k=12, ppc_ion=4, T_ion_K=3000.0, seed=11)
     d.update(kw)
