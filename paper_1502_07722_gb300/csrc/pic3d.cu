@@ -269,6 +269,66 @@ __device__ __noinline__ void gather_global3(const float* F0, const float* F1, co
     if (pair) density3(rho, g, rho_s, i, j, k, fx, fy, fz, out[6], out + 7);
 }
 
+// In-cell deposit (the particle stayed in its cell): current on the cell's edges and the node
+// density change on its corners, as global 64-bit reductions. Not inlined: it keeps the particle
+// loop small enough for the instruction cache.
+__device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u64* rho_next, int i, int j, int k,
+                                           int x0, int y0, int z0, int x1, int y1, int z1, int jsign, int pair)
+{
+    // stays in its cell: edges and corners of the cell only
+    const int i1 = wrapn(i + 1, g.nx), j1 = wrapn(j + 1, g.ny);
+    if (jsign) {
+        const long long sg = jsign;
+        const long long ay0 = kQ3 - y0, ay1 = kQ3 - y1, az0 = kQ3 - z0, az1 = kQ3 - z1, ax0 = kQ3 - x0,
+                        ax1 = kQ3 - x1;
+        const int dX = x1 - x0, dY = y1 - y0, dZ = z1 - z0;
+        if (dX) {
+            // J6x(i+1/2, j+b, k+c) = dX (2 S0y S0z + S1y S0z + S0y S1z + 2 S1y S1z)
+            const long long p00 = 2 * ay0 * az0 + ay1 * az0 + ay0 * az1 + 2 * ay1 * az1;
+            const long long p10 = 2LL * y0 * az0 + (long long)y1 * az0 + (long long)y0 * az1 + 2LL * y1 * az1;
+            const long long p01 = 2 * ay0 * z0 + ay1 * z0 + ay0 * z1 + 2 * ay1 * z1;
+            const long long p11 = 2LL * y0 * z0 + (long long)y1 * z0 + (long long)y0 * z1 + 2LL * y1 * z1;
+            red64(J0 + idx3(g, i, j, k), sg * dX * p00);
+            red64(J0 + idx3(g, i, j1, k), sg * dX * p10);
+            red64(J0 + idx3(g, i, j, k + 1), sg * dX * p01);
+            red64(J0 + idx3(g, i, j1, k + 1), sg * dX * p11);
+        }
+        if (dY) {
+            const long long p00 = 2 * ax0 * az0 + ax1 * az0 + ax0 * az1 + 2 * ax1 * az1;
+            const long long p10 = 2LL * x0 * az0 + (long long)x1 * az0 + (long long)x0 * az1 + 2LL * x1 * az1;
+            const long long p01 = 2 * ax0 * z0 + ax1 * z0 + ax0 * z1 + 2 * ax1 * z1;
+            const long long p11 = 2LL * x0 * z0 + (long long)x1 * z0 + (long long)x0 * z1 + 2LL * x1 * z1;
+            red64(J1 + idx3(g, i, j, k), sg * dY * p00);
+            red64(J1 + idx3(g, i1, j, k), sg * dY * p10);
+            red64(J1 + idx3(g, i, j, k + 1), sg * dY * p01);
+            red64(J1 + idx3(g, i1, j, k + 1), sg * dY * p11);
+        }
+        if (dZ) {
+            const long long p00 = 2 * ax0 * ay0 + ax1 * ay0 + ax0 * ay1 + 2 * ax1 * ay1;
+            const long long p10 = 2LL * x0 * ay0 + (long long)x1 * ay0 + (long long)x0 * ay1 + 2LL * x1 * ay1;
+            const long long p01 = 2 * ax0 * y0 + ax1 * y0 + ax0 * y1 + 2 * ax1 * y1;
+            const long long p11 = 2LL * x0 * y0 + (long long)x1 * y0 + (long long)x0 * y1 + 2LL * x1 * y1;
+            red64(J2 + idx3(g, i, j, k), sg * dZ * p00);
+            red64(J2 + idx3(g, i1, j, k), sg * dZ * p10);
+            red64(J2 + idx3(g, i, j1, k), sg * dZ * p01);
+            red64(J2 + idx3(g, i1, j1, k), sg * dZ * p11);
+        }
+    }
+    if (pair) {
+        const long long sx0[2] = {kQ3 - x0, x0}, sx1[2] = {kQ3 - x1, x1};
+        const long long sy0[2] = {kQ3 - y0, y0}, sy1[2] = {kQ3 - y1, y1};
+        const long long sz0[2] = {kQ3 - z0, z0}, sz1[2] = {kQ3 - z1, z1};
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int b = 0; b < 2; b++)
+#pragma unroll
+                for (int q = 0; q < 2; q++)
+                    red64(rho_next + idx3(g, q ? i1 : i, b ? j1 : j, k + c),
+                          sx1[q] * sy1[b] * sz1[c] - sx0[q] * sy0[b] * sz0[c]);
+    }
+}
+
 // One particle. PAIR is a run-time flag (the pair species): one instance of this code serves both
 // species, which keeps the kernel inside the instruction cache.
 template <bool FULL>
@@ -365,58 +425,7 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
     const bool moved = (di | dj | dk) != 0 || x1 != x0 || y1 != y0 || z1 != z0;
     if (!moved) return;
     if ((di | dj | dk) == 0) {
-        // stays in its cell: edges and corners of the cell only
-        const int i1 = wrapn(i + 1, g.nx), j1 = wrapn(j + 1, g.ny);
-        if (S.jsign) {
-            const long long sg = S.jsign;
-            const long long ay0 = kQ3 - y0, ay1 = kQ3 - y1, az0 = kQ3 - z0, az1 = kQ3 - z1, ax0 = kQ3 - x0,
-                            ax1 = kQ3 - x1;
-            const int dX = x1 - x0, dY = y1 - y0, dZ = z1 - z0;
-            if (dX) {
-                // J6x(i+1/2, j+b, k+c) = dX (2 S0y S0z + S1y S0z + S0y S1z + 2 S1y S1z)
-                const long long p00 = 2 * ay0 * az0 + ay1 * az0 + ay0 * az1 + 2 * ay1 * az1;
-                const long long p10 = 2LL * y0 * az0 + (long long)y1 * az0 + (long long)y0 * az1 + 2LL * y1 * az1;
-                const long long p01 = 2 * ay0 * z0 + ay1 * z0 + ay0 * z1 + 2 * ay1 * z1;
-                const long long p11 = 2LL * y0 * z0 + (long long)y1 * z0 + (long long)y0 * z1 + 2LL * y1 * z1;
-                red64(a.J[0] + idx3(g, i, j, k), sg * dX * p00);
-                red64(a.J[0] + idx3(g, i, j1, k), sg * dX * p10);
-                red64(a.J[0] + idx3(g, i, j, k + 1), sg * dX * p01);
-                red64(a.J[0] + idx3(g, i, j1, k + 1), sg * dX * p11);
-            }
-            if (dY) {
-                const long long p00 = 2 * ax0 * az0 + ax1 * az0 + ax0 * az1 + 2 * ax1 * az1;
-                const long long p10 = 2LL * x0 * az0 + (long long)x1 * az0 + (long long)x0 * az1 + 2LL * x1 * az1;
-                const long long p01 = 2 * ax0 * z0 + ax1 * z0 + ax0 * z1 + 2 * ax1 * z1;
-                const long long p11 = 2LL * x0 * z0 + (long long)x1 * z0 + (long long)x0 * z1 + 2LL * x1 * z1;
-                red64(a.J[1] + idx3(g, i, j, k), sg * dY * p00);
-                red64(a.J[1] + idx3(g, i1, j, k), sg * dY * p10);
-                red64(a.J[1] + idx3(g, i, j, k + 1), sg * dY * p01);
-                red64(a.J[1] + idx3(g, i1, j, k + 1), sg * dY * p11);
-            }
-            if (dZ) {
-                const long long p00 = 2 * ax0 * ay0 + ax1 * ay0 + ax0 * ay1 + 2 * ax1 * ay1;
-                const long long p10 = 2LL * x0 * ay0 + (long long)x1 * ay0 + (long long)x0 * ay1 + 2LL * x1 * ay1;
-                const long long p01 = 2 * ax0 * y0 + ax1 * y0 + ax0 * y1 + 2 * ax1 * y1;
-                const long long p11 = 2LL * x0 * y0 + (long long)x1 * y0 + (long long)x0 * y1 + 2LL * x1 * y1;
-                red64(a.J[2] + idx3(g, i, j, k), sg * dZ * p00);
-                red64(a.J[2] + idx3(g, i1, j, k), sg * dZ * p10);
-                red64(a.J[2] + idx3(g, i, j1, k), sg * dZ * p01);
-                red64(a.J[2] + idx3(g, i1, j1, k), sg * dZ * p11);
-            }
-        }
-        if (PAIR) {
-            const long long sx0[2] = {kQ3 - x0, x0}, sx1[2] = {kQ3 - x1, x1};
-            const long long sy0[2] = {kQ3 - y0, y0}, sy1[2] = {kQ3 - y1, y1};
-            const long long sz0[2] = {kQ3 - z0, z0}, sz1[2] = {kQ3 - z1, z1};
-#pragma unroll
-            for (int c = 0; c < 2; c++)
-#pragma unroll
-                for (int b = 0; b < 2; b++)
-#pragma unroll
-                    for (int q = 0; q < 2; q++)
-                        red64(a.rho_next + idx3(g, q ? i1 : i, b ? j1 : j, k + c),
-                              sx1[q] * sy1[b] * sz1[c] - sx0[q] * sy0[b] * sz0[c]);
-        }
+        deposit3_cell(g, a.J[0], a.J[1], a.J[2], a.rho_next, i, j, k, x0, y0, z0, x1, y1, z1, S.jsign, PAIR ? 1 : 0);
     } else {
         deposit3_general(g, a.J[0], a.J[1], a.J[2], a.rho_next, i * kQ3 + x0, j * kQ3 + y0, k * kQ3 + z0,
                          (i + di) * kQ3 + x1, (j + dj) * kQ3 + y1, (k + dk) * kQ3 + z1, S.jsign, PAIR ? 1 : 0);
