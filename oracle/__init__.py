@@ -113,6 +113,11 @@ def lib():
             "oracle_D": (ctypes.c_double, [vp]),
             "oracle_E0": (ctypes.c_double, [vp]),
             "oracle_injected": (ctypes.c_double, [vp]),
+            "oracle_init_particle": (None, [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _D]),
+            "oracle_push_one": (None, [vp, ctypes.c_int32, _D]),
+            "oracle3_init_particle": (None, [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64, _D]),
+            "oracle3_push_one": (None, [vp, ctypes.c_int32, _D]),
             "oracle3_injected": (ctypes.c_double, [vp]),
             "oracle_full_grad": (None, [vp, ctypes.c_int32, _D, ctypes.c_double, _D]),
             "oracle_full_loss": (ctypes.c_double, [vp, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_double,
@@ -334,6 +339,19 @@ class Oracle:
     def r0(self):
         return lib().oracle_r0(self._s)
 
+    def init_particle(self, sp, i, k, j):
+        """Initial (x, z, ux, uy, uz) of the particle in slot j of cell (i, k)."""
+        v = np.empty(5, np.float64)
+        lib().oracle_init_particle(self._s, int(sp), int(i), int(k), int(j), _p(v, ctypes.c_double))
+        return v
+
+    def push_one(self, sp, v):
+        """One particle's step (gather, pair force, Boris, move) from the current fields and node
+        density: (x, z, ux, uy, uz) -> new values."""
+        v = _f64(v).copy()
+        lib().oracle_push_one(self._s, int(sp), _p(v, ctypes.c_double))
+        return v
+
     def laser_field(self, x_cells, t):
         return lib().oracle_laser_field(self._s, float(x_cells), float(t))
 
@@ -480,6 +498,18 @@ class Oracle3D:
 
     def step(self, n=1):
         lib().oracle3_step(self._s, int(n))
+
+    def init_particle(self, sp, i, j, k, q):
+        """Initial (x, y, z, ux, uy, uz) of the particle in slot q of cell (i, j, k)."""
+        v = np.empty(6, np.float64)
+        lib().oracle3_init_particle(self._s, int(sp), int(i), int(j), int(k), int(q), _p(v, ctypes.c_double))
+        return v
+
+    def push_one(self, sp, v):
+        """One particle's step from the current fields and node density: (x, y, z, ux, uy, uz)."""
+        v = _f64(v).copy()
+        lib().oracle3_push_one(self._s, int(sp), _p(v, ctypes.c_double))
+        return v
 
     def energy(self):
         out = np.empty(5, np.float64)

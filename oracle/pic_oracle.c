@@ -501,6 +501,27 @@ static void alloc_species(ostate* s, int sp, int64_t n)
 /* Initial state (paper: a damage simulation is initialised for target density and
  * temperature): a slab of cell rows k < slab_k, ppc macro-ions per cell at uniformly drawn
  * positions, Maxwellian momenta; electrons co-located with the ions (zero net charge, E = 0). */
+/* initial state of the particle in slot j of cell (i, k) of species sp: x, z, ux, uy, uz */
+static void init_one(const ostate* s, int sp, int64_t i, int64_t k, int64_t j, double out[5])
+{
+    const ocfg* c = &s->c;
+    int ppc = sp == 0 ? c->ppc_ion : c->ppc_electron;
+    uint64_t cellidx = (uint64_t)k * (uint64_t)c->nx + (uint64_t)i;
+    /* positions: electrons reuse the ion draws of the same (cell, slot) */
+    int pos_sp = (sp == 1 && c->ppc_electron == c->ppc_ion) ? 0 : sp;
+    uint64_t pid_pos = cellidx * (uint64_t)ppc + (uint64_t)j;
+    out[0] = (double)i + draw_unit24(draw_bits(c->seed, pos_sp, pid_pos, 0));
+    out[1] = (double)k + draw_unit24(draw_bits(c->seed, pos_sp, pid_pos, 1));
+    /* Box-Muller normals from two pairs of draws */
+    double r1 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid_pos, 2))));
+    double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 3));
+    double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid_pos, 4))));
+    double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 5));
+    out[2] = s->uth[sp] * r1 * cos(a1);
+    out[3] = s->uth[sp] * r1 * sin(a1);
+    out[4] = s->uth[sp] * r2 * cos(a2);
+}
+
 static void init_particles(ostate* s)
 {
     const ocfg* c = &s->c;
@@ -512,20 +533,10 @@ static void init_particles(ostate* s)
         for (int k = 0; k < c->slab_k; k++)
             for (int i = 0; i < c->nx; i++)
                 for (int j = 0; j < ppc; j++, p++) {
-                    uint64_t cellidx = (uint64_t)k * (uint64_t)c->nx + (uint64_t)i;
-                    /* positions: electrons reuse the ion draws of the same (cell, slot) */
-                    int pos_sp = (sp == 1 && c->ppc_electron == c->ppc_ion) ? 0 : sp;
-                    uint64_t pid_pos = cellidx * (uint64_t)ppc + (uint64_t)j;
-                    s->x[sp][p] = (double)i + draw_unit24(draw_bits(c->seed, pos_sp, pid_pos, 0));
-                    s->z[sp][p] = (double)k + draw_unit24(draw_bits(c->seed, pos_sp, pid_pos, 1));
-                    /* Box-Muller normals from two pairs of draws */
-                    double r1 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid_pos, 2))));
-                    double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 3));
-                    double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid_pos, 4))));
-                    double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 5));
-                    s->ux[sp][p] = s->uth[sp] * r1 * cos(a1);
-                    s->uy[sp][p] = s->uth[sp] * r1 * sin(a1);
-                    s->uz[sp][p] = s->uth[sp] * r2 * cos(a2);
+                    double v[5];
+                    init_one(s, sp, i, k, j, v);
+                    s->x[sp][p] = v[0]; s->z[sp][p] = v[1];
+                    s->ux[sp][p] = v[2]; s->uy[sp][p] = v[3]; s->uz[sp][p] = v[4];
                 }
     }
 }
@@ -642,10 +653,11 @@ void oracle_gather_density(const ostate* s, double x, double z, double out[3])
     gather_density(s, x, z, &out[0], &out[1], &out[2]);
 }
 
-/* advance a single particle: gather, pair force, Boris, move with walls */
-static void push_particle(ostate* s, int sp, int64_t p)
+/* advance one particle (position in cells, u = gamma v / c) through gather, pair force, Boris and
+ * the move with walls, from the context's fields and node density */
+static void push_one(const ostate* s, int sp, double* px, double* pz, double u[3])
 {
-    double x = s->x[sp][p], z = s->z[sp][p];
+    double x = *px, z = *pz;
     double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, Fp[3] = {0, 0, 0};
     if (s->c.mode == 0) {
         E[0] = gather_field(s, s->F[0], x, z, 0.5, 0.0);
@@ -656,7 +668,6 @@ static void push_particle(ostate* s, int sp, int64_t p)
         B[2] = gather_field(s, s->F[5], x, z, 0.5, 0.0);
     }
     if (s->pair[sp]) pair_force_at(s, x, z, Fp, NULL);
-    double u[3] = {s->ux[sp][p], s->uy[sp][p], s->uz[sp][p]};
     oracle_boris(s->q[sp], s->m[sp], s->dt, E, B, Fp, u);
     double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     double xn = x + u[0] * O_C * s->dt / (g * s->c.dx);
@@ -665,8 +676,29 @@ static void push_particle(ostate* s, int sp, int64_t p)
     if (xn >= s->c.nx) xn -= s->c.nx;
     if (zn < 0.0) { zn = -zn; u[2] = -u[2]; }
     if (zn >= s->c.nz) { zn = 2.0 * s->c.nz - zn; u[2] = -u[2]; }
-    s->x[sp][p] = xn; s->z[sp][p] = zn;
+    *px = xn; *pz = zn;
+}
+
+static void push_particle(ostate* s, int sp, int64_t p)
+{
+    double u[3] = {s->ux[sp][p], s->uy[sp][p], s->uz[sp][p]};
+    push_one(s, sp, &s->x[sp][p], &s->z[sp][p], u);
     s->ux[sp][p] = u[0]; s->uy[sp][p] = u[1]; s->uz[sp][p] = u[2];
+}
+
+/* Initial state of one particle (slot j of cell (i, k)) and one particle's push from the current
+ * fields and node density, for checking sampled particles of large runs one by one.
+ * v: x, z, ux, uy, uz (the push updates it in place). */
+void oracle_init_particle(const ostate* s, int32_t sp, int64_t i, int64_t k, int64_t j, double* v)
+{
+    init_one(s, sp, i, k, j, v);
+}
+
+void oracle_push_one(const ostate* s, int32_t sp, double* v)
+{
+    double u[3] = {v[2], v[3], v[4]};
+    push_one(s, sp, &v[0], &v[1], u);
+    v[2] = u[0]; v[3] = u[1]; v[4] = u[2];
 }
 
 /* The Maxwell part of the cycle alone, from the stored current (for checking a field update
@@ -1061,6 +1093,26 @@ static void redeposit3(ostate3* s)
 }
 
 /* initial slab: cell rows k < slab_k over all (i, j); positions draws 0 (x), 6 (y), 1 (z) */
+/* initial state of the particle in slot q of cell (i, j, k): x, y, z, ux, uy, uz */
+static void init_one3(const ostate3* s, int sp, int64_t i, int64_t j, int64_t k, int64_t q, double out[6])
+{
+    const ocfg3* c = &s->c;
+    int ppc = sp == 0 ? c->ppc_ion : c->ppc_electron;
+    uint64_t cellidx = ((uint64_t)k * c->ny + (uint64_t)j) * (uint64_t)c->nx + (uint64_t)i;
+    int pos_sp = (sp == 1 && c->ppc_electron == c->ppc_ion) ? 0 : sp;
+    uint64_t pid = cellidx * (uint64_t)ppc + (uint64_t)q;
+    out[0] = (double)i + draw_unit24(draw_bits(c->seed, pos_sp, pid, 0));
+    out[1] = (double)j + draw_unit24(draw_bits(c->seed, pos_sp, pid, 6));
+    out[2] = (double)k + draw_unit24(draw_bits(c->seed, pos_sp, pid, 1));
+    double r1 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid, 2))));
+    double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 3));
+    double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid, 4))));
+    double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 5));
+    out[3] = s->uth[sp] * r1 * cos(a1);
+    out[4] = s->uth[sp] * r1 * sin(a1);
+    out[5] = s->uth[sp] * r2 * cos(a2);
+}
+
 static void init_particles3(ostate3* s)
 {
     const ocfg3* c = &s->c;
@@ -1073,19 +1125,10 @@ static void init_particles3(ostate3* s)
             for (int j = 0; j < c->ny; j++)
                 for (int i = 0; i < c->nx; i++)
                     for (int q = 0; q < ppc; q++, p++) {
-                        uint64_t cellidx = ((uint64_t)k * c->ny + (uint64_t)j) * (uint64_t)c->nx + (uint64_t)i;
-                        int pos_sp = (sp == 1 && c->ppc_electron == c->ppc_ion) ? 0 : sp;
-                        uint64_t pid = cellidx * (uint64_t)ppc + (uint64_t)q;
-                        s->x[sp][p] = (double)i + draw_unit24(draw_bits(c->seed, pos_sp, pid, 0));
-                        s->y[sp][p] = (double)j + draw_unit24(draw_bits(c->seed, pos_sp, pid, 6));
-                        s->z[sp][p] = (double)k + draw_unit24(draw_bits(c->seed, pos_sp, pid, 1));
-                        double r1 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid, 2))));
-                        double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 3));
-                        double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid, 4))));
-                        double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 5));
-                        s->ux[sp][p] = s->uth[sp] * r1 * cos(a1);
-                        s->uy[sp][p] = s->uth[sp] * r1 * sin(a1);
-                        s->uz[sp][p] = s->uth[sp] * r2 * cos(a2);
+                        double v[6];
+                        init_one3(s, sp, i, j, k, q, v);
+                        s->x[sp][p] = v[0]; s->y[sp][p] = v[1]; s->z[sp][p] = v[2];
+                        s->ux[sp][p] = v[3]; s->uy[sp][p] = v[4]; s->uz[sp][p] = v[5];
                     }
     }
 }
@@ -1187,9 +1230,9 @@ void oracle3_maxwell(ostate3* s)
     half_step_B3(s);
 }
 
-static void push_particle3(ostate3* s, int sp, int64_t p)
+static void push_one3(const ostate3* s, int sp, double* px, double* py, double* pz, double u[3])
 {
-    double x = s->x[sp][p], y = s->y[sp][p], z = s->z[sp][p];
+    double x = *px, y = *py, z = *pz;
     double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, Fp[3] = {0, 0, 0};
     if (s->c.mode == 0) {
         E[0] = gather_field3(s, s->F[0], x, y, z, 0.5, 0.0, 0.0);
@@ -1200,7 +1243,6 @@ static void push_particle3(ostate3* s, int sp, int64_t p)
         B[2] = gather_field3(s, s->F[5], x, y, z, 0.5, 0.5, 0.0);
     }
     if (sp == 0) pair_force3_at(s, x, y, z, Fp, NULL);
-    double u[3] = {s->ux[sp][p], s->uy[sp][p], s->uz[sp][p]};
     oracle_boris(s->q[sp], s->m[sp], s->dt, E, B, Fp, u);
     double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     double k = O_C * s->dt / (g * s->c.dx);
@@ -1211,8 +1253,27 @@ static void push_particle3(ostate3* s, int sp, int64_t p)
     if (yn >= s->c.ny) yn -= s->c.ny;
     if (zn < 0.0) { zn = -zn; u[2] = -u[2]; }
     if (zn >= s->c.nz) { zn = 2.0 * s->c.nz - zn; u[2] = -u[2]; }
-    s->x[sp][p] = xn; s->y[sp][p] = yn; s->z[sp][p] = zn;
+    *px = xn; *py = yn; *pz = zn;
+}
+
+static void push_particle3(ostate3* s, int sp, int64_t p)
+{
+    double u[3] = {s->ux[sp][p], s->uy[sp][p], s->uz[sp][p]};
+    push_one3(s, sp, &s->x[sp][p], &s->y[sp][p], &s->z[sp][p], u);
     s->ux[sp][p] = u[0]; s->uy[sp][p] = u[1]; s->uz[sp][p] = u[2];
+}
+
+/* one particle's initial state and push in 3D; v: x, y, z, ux, uy, uz */
+void oracle3_init_particle(const ostate3* s, int32_t sp, int64_t i, int64_t j, int64_t k, int64_t q, double* v)
+{
+    init_one3(s, sp, i, j, k, q, v);
+}
+
+void oracle3_push_one(const ostate3* s, int32_t sp, double* v)
+{
+    double u[3] = {v[3], v[4], v[5]};
+    push_one3(s, sp, &v[0], &v[1], &v[2], u);
+    v[3] = u[0]; v[4] = u[1]; v[5] = u[2];
 }
 
 void oracle3_step(ostate3* s, int32_t nsteps)
