@@ -35,8 +35,8 @@ constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kChunkRows = 32;          // particles per lane row of a full chunk
 constexpr int kChunk = 32 * kChunkRows; // particles per chunk
-constexpr int kPitch = kChunkRows + 1;  // padded row pitch of the chunk arrays (conflict-free)
-constexpr int kChunkWords = 32 * kPitch;
+constexpr int kPitch = 33;              // padded pitch of a column of 32 lanes (conflict-free)
+constexpr int kChunkWords = kChunkRows * kPitch;
 
 __device__ __forceinline__ int wrap_any(int i, int nx)
 {
@@ -88,26 +88,6 @@ __device__ __forceinline__ float apply(const float* A, int W, const Stencil2& t)
 {
     const float* p = A + t.idx;
     return t.c00 * p[0] + t.c10 * p[1] + t.c01 * p[W] + t.c11 * p[W + 1];
-}
-
-// bilinear gather of a staged component; (hx, hz) = 1 where it sits half a cell up
-__device__ __forceinline__ float win_gather(const float* A, int W, int lx, int lz, float fx, float fz, int hx, int hz)
-{
-    int c = lx, r = lz;
-    float wx = fx, wz = fz;
-    if (hx) {
-        const bool up = fx >= 0.5f;
-        c = up ? lx : lx - 1;
-        wx = up ? fx - 0.5f : fx + 0.5f;
-    }
-    if (hz) {
-        const bool up = fz >= 0.5f;
-        r = up ? lz : lz - 1;
-        wz = up ? fz - 0.5f : fz + 0.5f;
-    }
-    const float* p = A + r * W + c;
-    const float a = p[0], b = p[1], d = p[W], e = p[W + 1];
-    return (1.0f - wz) * ((1.0f - wx) * a + wx * b) + wz * ((1.0f - wx) * d + wx * e);
 }
 
 // Rare path: fields and node density straight from global memory (particle outside the window).
