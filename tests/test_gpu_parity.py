@@ -363,3 +363,24 @@ def test_transport_acoustic_wave_period():
     assert 2 * np.diff(crossings).mean() * dt == pytest.approx(period, rel=1e-2)
     assert np.abs(a[:, 1]).max() == pytest.approx(eps, rel=2e-2)
     sim.close()
+
+
+def test_vacuum_without_particles_matches_oracle():
+    """Degenerate input: no slab at all (slab_k = 0, no particles). The context initialises, the
+    laser propagates, and fields and injected energy follow the oracle."""
+    w = workload("tiny", nx=32, nz=80, slab_k=0, laser_profile=1, I0=1e17, tau_fwhm=5e-15, t_peak=8e-15)
+    sim = gb().Simulation(w)
+    assert sum(sim.info()["num_particles"]) == 0
+    orc = oracle.Oracle(w)
+    sim.step(150)
+    orc.step(150)
+    for f in range(6):
+        g, o = sim.get_field(f).cpu().numpy(), orc.get_field(f)
+        scale = np.abs(o).max()
+        assert scale == 0 or np.abs(g - o).max() <= 1e-5 * scale, f
+    eg, eo = sim.energy(), orc.energy()
+    assert eo["injected"] > 0
+    assert eg["injected"] == pytest.approx(eo["injected"], rel=1e-5)
+    assert eg["kinetic_ion"] == 0.0 and eg["kinetic_electron"] == 0.0 and eg["pair"] == 0.0
+    assert not sim.get_density().any() and not sim.get_current().any()
+    sim.close()
