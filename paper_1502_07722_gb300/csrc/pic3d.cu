@@ -277,6 +277,9 @@ __device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u6
 {
     // stays in its cell: edges and corners of the cell only
     const int i1 = wrapn(i + 1, g.nx), j1 = wrapn(j + 1, g.ny);
+    // one base index and the offsets to the cell's other corners (x, y periodic)
+    const size_t base = idx3(g, i, j, k);
+    const ptrdiff_t ox = i1 - i, oy = (ptrdiff_t)(j1 - j) * g.nx, oz = (ptrdiff_t)g.nx * g.ny;
     if (jsign) {
         const long long sg = jsign;
         const long long ay0 = kQ3 - y0, ay1 = kQ3 - y1, az0 = kQ3 - z0, az1 = kQ3 - z1, ax0 = kQ3 - x0,
@@ -288,30 +291,30 @@ __device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u6
             const long long p10 = 2LL * y0 * az0 + (long long)y1 * az0 + (long long)y0 * az1 + 2LL * y1 * az1;
             const long long p01 = 2 * ay0 * z0 + ay1 * z0 + ay0 * z1 + 2 * ay1 * z1;
             const long long p11 = 2LL * y0 * z0 + (long long)y1 * z0 + (long long)y0 * z1 + 2LL * y1 * z1;
-            red64(J0 + idx3(g, i, j, k), sg * dX * p00);
-            red64(J0 + idx3(g, i, j1, k), sg * dX * p10);
-            red64(J0 + idx3(g, i, j, k + 1), sg * dX * p01);
-            red64(J0 + idx3(g, i, j1, k + 1), sg * dX * p11);
+            red64(J0 + base, sg * dX * p00);
+            red64(J0 + base + oy, sg * dX * p10);
+            red64(J0 + base + oz, sg * dX * p01);
+            red64(J0 + base + oy + oz, sg * dX * p11);
         }
         if (dY) {
             const long long p00 = 2 * ax0 * az0 + ax1 * az0 + ax0 * az1 + 2 * ax1 * az1;
             const long long p10 = 2LL * x0 * az0 + (long long)x1 * az0 + (long long)x0 * az1 + 2LL * x1 * az1;
             const long long p01 = 2 * ax0 * z0 + ax1 * z0 + ax0 * z1 + 2 * ax1 * z1;
             const long long p11 = 2LL * x0 * z0 + (long long)x1 * z0 + (long long)x0 * z1 + 2LL * x1 * z1;
-            red64(J1 + idx3(g, i, j, k), sg * dY * p00);
-            red64(J1 + idx3(g, i1, j, k), sg * dY * p10);
-            red64(J1 + idx3(g, i, j, k + 1), sg * dY * p01);
-            red64(J1 + idx3(g, i1, j, k + 1), sg * dY * p11);
+            red64(J1 + base, sg * dY * p00);
+            red64(J1 + base + ox, sg * dY * p10);
+            red64(J1 + base + oz, sg * dY * p01);
+            red64(J1 + base + ox + oz, sg * dY * p11);
         }
         if (dZ) {
             const long long p00 = 2 * ax0 * ay0 + ax1 * ay0 + ax0 * ay1 + 2 * ax1 * ay1;
             const long long p10 = 2LL * x0 * ay0 + (long long)x1 * ay0 + (long long)x0 * ay1 + 2LL * x1 * ay1;
             const long long p01 = 2 * ax0 * y0 + ax1 * y0 + ax0 * y1 + 2 * ax1 * y1;
             const long long p11 = 2LL * x0 * y0 + (long long)x1 * y0 + (long long)x0 * y1 + 2LL * x1 * y1;
-            red64(J2 + idx3(g, i, j, k), sg * dZ * p00);
-            red64(J2 + idx3(g, i1, j, k), sg * dZ * p10);
-            red64(J2 + idx3(g, i, j1, k), sg * dZ * p01);
-            red64(J2 + idx3(g, i1, j1, k), sg * dZ * p11);
+            red64(J2 + base, sg * dZ * p00);
+            red64(J2 + base + ox, sg * dZ * p10);
+            red64(J2 + base + oy, sg * dZ * p01);
+            red64(J2 + base + ox + oy, sg * dZ * p11);
         }
     }
     if (pair) {
@@ -324,7 +327,7 @@ __device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u6
             for (int b = 0; b < 2; b++)
 #pragma unroll
                 for (int q = 0; q < 2; q++)
-                    red64(rho_next + idx3(g, q ? i1 : i, b ? j1 : j, k + c),
+                    red64(rho_next + base + (q ? ox : 0) + (b ? oy : 0) + (c ? oz : 0),
                           sx1[q] * sy1[b] * sz1[c] - sx0[q] * sy0[b] * sz0[c]);
     }
 }
