@@ -464,7 +464,7 @@ def main():
             "data": "synthetic copper slab (seeded Maxwellian start), one independent slab per GPU",
             "config": {"workload": args.workload, "nx": w["nx"], "nz": w["nz"], "slab_k": w["slab_k"],
                        "ppc": [w["ppc_ion"], w["ppc_electron"]], "particles_per_gpu": n_local,
-                       "tile": sim.cfg.tile or (8 if sim.dims == 3 else 16), "sort_every": sim.cfg.sort_every,
+                       "tile": sim.cfg.tile or (10 if sim.dims == 3 else 16), "sort_every": sim.cfg.sort_every,
                        "dims": sim.dims, "ny": sim.ny,
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (24 * n_local / 1e9),
                        "parallelism": f"replicas x{world}"},

@@ -64,7 +64,7 @@ typedef struct pic_config {
     int32_t ppc_ion, ppc_electron;   /* macroparticles per slab cell (equal in the full mode)   */
     int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (s_rep below r0, c_att above) */
     int32_t laser_profile;   /* PIC_LASER_*                                                     */
-    int32_t tile;            /* tile edge in cells for particle binning (0: 16)                 */
+    int32_t tile;            /* tile edge in cells for particle binning (0: 16 in 2D, 10 in 3D)  */
     int32_t sort_every;      /* steps between cell sorts (0: only after init / set_particles)  */
     int64_t max_particles;   /* per-species capacity (0: the initial count)                    */
     double dx;               /* cell size (m), square cells                                     */

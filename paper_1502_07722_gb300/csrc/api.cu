@@ -64,7 +64,7 @@ int derive_layout(const pic_config* cfg, Layout& L)
     if (cfg->pot_mode != 0 && cfg->pot_mode != 1) return PIC_EINVAL;
     L.nx = cfg->nx;
     L.nz = cfg->nz;
-    L.T = cfg->tile > 0 ? cfg->tile : (L.dims == 3 ? 8 : 16);
+    L.T = cfg->tile > 0 ? cfg->tile : (L.dims == 3 ? 10 : 16);
     if (L.T < 2 || L.T > 64) return PIC_EINVAL;
     L.ntx = (L.nx + L.T - 1) / L.T;
     L.nty = L.dims == 3 ? (L.ny + L.T - 1) / L.T : 1;

@@ -5,10 +5,10 @@
 // (nz+1) x ny x nx, index (k*ny + j)*nx + i. Yee positions: Ex (i+1/2,j,k), Ey (i,j+1/2,k),
 // Ez (i,j,k+1/2), Bx (i,j+1/2,k+1/2), By (i+1/2,j,k+1/2), Bz (i+1/2,j+1/2,k).
 //
-// The particle kernel streams each tile's particles through shared memory and processes them
-// transposed (lanes in different cells), like the 2D kernel; fields and the node density are
-// gathered from global memory (L1-resident within a tile) and deposits use global 64-bit
-// reductions, which are native in L2.
+// The particle kernel stages each tile's fields and node density in shared memory and streams the
+// tile's particles straight from their records in coalesced order; deposits use global 64-bit
+// reductions, which are native in L2 (lanes of one cell hitting the same node need no shared
+// accumulator and no transposed order).
 #include "pic_device.cuh"
 
 namespace gbpic {
@@ -16,10 +16,6 @@ namespace gbpic {
 constexpr int kQ3Bits = 14;
 constexpr int kQ3 = 1 << kQ3Bits;
 constexpr int kBlock3 = 256;
-constexpr int kRows3 = 32;
-constexpr int kPitch3 = 33;
-constexpr int kChunk3 = 32 * kRows3;
-constexpr int kChunkWords3 = kRows3 * kPitch3;
 
 __device__ __forceinline__ int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 __device__ __forceinline__ int qoff3(float f) { return __float2int_rn(f * 16384.0f); }
@@ -201,9 +197,8 @@ __device__ __noinline__ void deposit3_general(Geo3 g, u64* J0, u64* J1, u64* J2,
 // doubled) on W^3 nodes from (ox, oy, oz); x and y wrap, z rows outside 0..nz repeat the edge row
 // (the same values the global gathers clamp to).
 struct Win3 {
-    const float* f[6];
-    const float* nh;
-    int ox, oy, oz, W;
+    const float* f;         // component q (Ex, Ey, Ez, Bx, By, Bz) at f + q W^3, density at f + 6 W^3
+    int ox, oy, oz, W, WWW;
 };
 
 // staggered trilinear gather from the window (the same arithmetic as gather3)
@@ -332,14 +327,17 @@ __device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u6
     }
 }
 
-// One particle. PAIR is a run-time flag (the pair species): one instance of this code serves both
-// species, which keeps the kernel inside the instruction cache.
+// Particle p of species S: its record is read, advanced one step and written back before its
+// deposits, so that little state is live across the (non-inlined) deposit call. PAIR is a run-time
+// flag (the pair species): one instance of this code serves both species, which keeps the kernel
+// inside the instruction cache.
 template <bool FULL>
-__device__ __forceinline__ void process3(const Args3& a, const Species3& S, const Win3& w, const bool PAIR, int& cell,
-                                         float& fx_io, float& fy_io, float& fz_io, float& ux, float& uy, float& uz)
+__device__ __forceinline__ void process3(const Args3& a, const Species3& S, const Win3& w, const bool PAIR, int p)
 {
     const Geo3& g = a.g;
-    const float fx = fx_io, fy = fy_io, fz = fz_io;
+    const int cell = S.cell[p];
+    const float fx = S.fx[p], fy = S.fy[p], fz = S.fz[p];
+    float ux = S.ux[p], uy = S.uy[p], uz = S.uz[p];
     int i, j, k;
     split3(cell, g, i, j, k);
     // window coordinates (x, y periodic: the image closest to the window centre)
@@ -355,14 +353,14 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
     float n = 0.f, gr[3] = {0.f, 0.f, 0.f};
     if (inwin) {
         if (FULL) {
-            kx = S.e_kick * wgather3(w.f[0], W, lx, ly, lz, fx, fy, fz, 1, 0, 0);
-            ky = S.e_kick * wgather3(w.f[1], W, lx, ly, lz, fx, fy, fz, 0, 1, 0);
-            kz = S.e_kick * wgather3(w.f[2], W, lx, ly, lz, fx, fy, fz, 0, 0, 1);
-            bx = wgather3(w.f[3], W, lx, ly, lz, fx, fy, fz, 0, 1, 1);
-            by = wgather3(w.f[4], W, lx, ly, lz, fx, fy, fz, 1, 0, 1);
-            bz = wgather3(w.f[5], W, lx, ly, lz, fx, fy, fz, 1, 1, 0);
+            kx = S.e_kick * wgather3(w.f, W, lx, ly, lz, fx, fy, fz, 1, 0, 0);
+            ky = S.e_kick * wgather3(w.f + 1 * w.WWW, W, lx, ly, lz, fx, fy, fz, 0, 1, 0);
+            kz = S.e_kick * wgather3(w.f + 2 * w.WWW, W, lx, ly, lz, fx, fy, fz, 0, 0, 1);
+            bx = wgather3(w.f + 3 * w.WWW, W, lx, ly, lz, fx, fy, fz, 0, 1, 1);
+            by = wgather3(w.f + 4 * w.WWW, W, lx, ly, lz, fx, fy, fz, 1, 0, 1);
+            bz = wgather3(w.f + 5 * w.WWW, W, lx, ly, lz, fx, fy, fz, 1, 1, 0);
         }
-        if (PAIR) wdensity3(w.nh, W, lx, ly, lz, fx, fy, fz, n, gr);
+        if (PAIR) wdensity3(w.f + 6 * w.WWW, W, lx, ly, lz, fx, fy, fz, n, gr);
     } else {
         float o[10];
         gather_global3(a.F[0], a.F[1], a.F[2], a.F[3], a.F[4], a.F[5], a.rho_cur, g, a.rho_s, FULL ? 1 : 0,
@@ -419,10 +417,13 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
         nfz -= (float)dk;
         if (nfz >= 1.0f) { nfz = 0.0f; dk += 1; }
     }
-    cell = (int)idx3(g, wrapn(i + di, g.nx), wrapn(j + dj, g.ny), k + dk);
-    fx_io = nfx;
-    fy_io = nfy;
-    fz_io = nfz;
+    S.cell[p] = (int)idx3(g, wrapn(i + di, g.nx), wrapn(j + dj, g.ny), k + dk);
+    S.fx[p] = nfx;
+    S.fy[p] = nfy;
+    S.fz[p] = nfz;
+    S.ux[p] = ux;
+    S.uy[p] = uy;
+    S.uz[p] = uz;
 
     const int x0 = qoff3(fx), x1 = qoff3(nfx), y0 = qoff3(fy), y1 = qoff3(nfy), z0 = qoff3(fz), z1 = qoff3(nfz);
     const bool moved = (di | dj | dk) != 0 || x1 != x0 || y1 != y0 || z1 != z0;
@@ -436,19 +437,15 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
 }
 
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock3, 3) k_particles3(const Args3 a)
+__global__ void __launch_bounds__(kBlock3, 3) k_particles3(const __grid_constant__ Args3 a)
 {
     extern __shared__ unsigned smem3[];
     const int W = a.W, WW = W * W, WWW = WW * W;
-    unsigned* chunk = smem3 + 7 * WWW;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int* c_cell = reinterpret_cast<int*>(chunk);
-    float* c_f = reinterpret_cast<float*>(chunk + kChunkWords3);
     Win3 w;
     w.W = W;
     float* wf = reinterpret_cast<float*>(smem3);
-    for (int q = 0; q < 6; q++) w.f[q] = wf + q * WWW;
-    w.nh = wf + 6 * WWW;
+    w.f = wf;
+    w.WWW = WWW;
     const Geo3& g = a.g;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         int cnt = 0;
@@ -484,54 +481,11 @@ __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const Args3 a)
 #pragma unroll 1
         for (int s = 0; s < 2; s++) {
             if (s >= a.nsp) break;
-            const Species3 S = s == 0 ? a.sp[0] : a.sp[1];
+            const Species3& S = a.sp[s];
             const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
-            for (int c0 = p0; c0 < p1; c0 += kChunk3) {
-                const int n = min(kChunk3, p1 - c0);
-                const int lg = n > kChunk3 / 2 ? 5 : 32 - __clz(((n + 31) >> 5) - 1);
-                const int rows = 1 << lg;
-                for (int ci = threadIdx.x; ci < n; ci += kBlock3) {
-                    const int slot = (ci & (rows - 1)) * kPitch3 + (ci >> lg);
-                    c_cell[slot] = S.cell[c0 + ci];
-                    c_f[slot] = S.fx[c0 + ci];
-                    c_f[kChunkWords3 + slot] = S.fy[c0 + ci];
-                    c_f[2 * kChunkWords3 + slot] = S.fz[c0 + ci];
-                    c_f[3 * kChunkWords3 + slot] = S.ux[c0 + ci];
-                    c_f[4 * kChunkWords3 + slot] = S.uy[c0 + ci];
-                    c_f[5 * kChunkWords3 + slot] = S.uz[c0 + ci];
-                }
-                __syncthreads();
-                for (int col = warp; col < rows; col += kBlock3 / 32) {
-                    const int ci = (lane << lg) + col;
-                    if (ci < n) {
-                        const int slot = col * kPitch3 + lane;
-                        int cell = c_cell[slot];
-                        float fx = c_f[slot], fy = c_f[kChunkWords3 + slot], fz = c_f[2 * kChunkWords3 + slot];
-                        float ux = c_f[3 * kChunkWords3 + slot], uy = c_f[4 * kChunkWords3 + slot],
-                              uz = c_f[5 * kChunkWords3 + slot];
-                        process3<FULL>(a, S, w, S.pair != 0, cell, fx, fy, fz, ux, uy, uz);
-                        c_cell[slot] = cell;
-                        c_f[slot] = fx;
-                        c_f[kChunkWords3 + slot] = fy;
-                        c_f[2 * kChunkWords3 + slot] = fz;
-                        c_f[3 * kChunkWords3 + slot] = ux;
-                        c_f[4 * kChunkWords3 + slot] = uy;
-                        c_f[5 * kChunkWords3 + slot] = uz;
-                    }
-                }
-                __syncthreads();
-                for (int ci = threadIdx.x; ci < n; ci += kBlock3) {
-                    const int slot = (ci & (rows - 1)) * kPitch3 + (ci >> lg);
-                    S.cell[c0 + ci] = c_cell[slot];
-                    S.fx[c0 + ci] = c_f[slot];
-                    S.fy[c0 + ci] = c_f[kChunkWords3 + slot];
-                    S.fz[c0 + ci] = c_f[2 * kChunkWords3 + slot];
-                    S.ux[c0 + ci] = c_f[3 * kChunkWords3 + slot];
-                    S.uy[c0 + ci] = c_f[4 * kChunkWords3 + slot];
-                    S.uz[c0 + ci] = c_f[5 * kChunkWords3 + slot];
-                }
-                __syncthreads();
-            }
+            // consecutive threads take consecutive particles: coalesced loads and stores straight
+            // from the records, no block barrier per chunk
+            for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock3) process3<FULL>(a, S, w, S.pair != 0, p);
         }
     }
 }
@@ -578,11 +532,11 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     a.T = c.T;
     a.ntx = c.ntx;
     a.nty = c.nty;
-    // window of the tile plus one node below and two above on each axis; staged when it fits next
-    // to the particle chunk with three CTAs per SM
+    // window of the tile plus one node below and two above on each axis; staged when three CTAs
+    // still fit on one SM
     const int W = c.T + 3;
-    a.W = (size_t)7 * W * W * W * 4 <= 40 * 1024 ? W : 0;
-    const size_t shmem = sizeof(unsigned) * ((size_t)7 * a.W * a.W * a.W + 7 * kChunkWords3);
+    a.W = (size_t)7 * W * W * W * 4 <= 72 * 1024 ? W : 0;
+    const size_t shmem = sizeof(unsigned) * ((size_t)7 * a.W * a.W * a.W);
     static size_t configured = 0;
     if (shmem > configured) {
         cudaFuncSetAttribute(k_particles3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);

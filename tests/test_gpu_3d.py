@@ -89,12 +89,14 @@ def test_density3_and_pair_force(gb):
     assert (np.abs(Fg - Fo) <= 1e-5 * np.abs(Fo) + 1e-5 * scale).all()
 
 
-@pytest.mark.parametrize("seed", [3, 4])
-def test_one_step3_full(gb, seed):
+@pytest.mark.parametrize("seed,tile", [(3, 4), (4, 4), (5, 10), (6, 16)])
+def test_one_step3_full(gb, seed, tile):
     """One 3D cycle: particles to 1e-5, current and node density bit-exact against the oracle's
-    deposition of the GPU's own move, fields against the oracle's Maxwell update."""
+    deposition of the GPU's own move, fields against the oracle's Maxwell update. Tile 4: several
+    tiles with staged windows; tile 10: ragged tiles (14 x 12 x 16 cells); tile 16: the window is
+    too large to stage, every gather and deposit takes the global path."""
     nx, ny, nz = 14, 12, 16
-    w = w3(max_particles=6000, sort_every=0)
+    w = w3(max_particles=6000, sort_every=0, tile=tile)
     sim = gb.Simulation(w)
     orc = oracle.Oracle3D(w, with_particles=False)
     g0 = []
