@@ -61,16 +61,17 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic():
-    """DRAM bytes per launch of the particle kernel from a committed ncu summary, if the kernel
-    source has not changed since it was taken (else None)."""
-    path = os.path.join(ROOT, "profiles", "particle_kernel_traffic.json")
+def kernel_traffic(dims=2):
+    """DRAM bytes per launch of the particle kernel (2D or 3D) from a committed ncu summary, if the
+    kernel source has not changed since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "particle_kernel_traffic.json" if dims == 2 else
+                        "particle_kernel3_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     h = hashlib.sha256()
-    for name in ("particles.cu", "pic_device.cuh", "pic_internal.cuh"):
+    for name in ("particles.cu" if dims == 2 else "pic3d.cu", "pic_device.cuh", "pic_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1502_07722_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     if d.get("source_sha256") != h.hexdigest():
@@ -247,7 +248,7 @@ def run_batched(args, world, rank, dist, gb):
                        "particles_per_gpu": n_local, "tile": tuned["tile"], "sort_every": tuned["sort_every"],
                        "autotuned": [(t["tile"], t["sort_every"], round(t["ms_per_step"], 4)) for t in tuned["trials"]],
                        "graph": True,
-                       "l2": "inputs larger than L2 (particle state %.1f GB)" % (24 * n_local / 1e9),
+                       "l2": "inputs larger than L2 (particle state %.1f GB)" % (BYTES_PER_PARTICLE / 2 * n_local / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": alg / (k_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / (k_ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "k_particles_batch",
@@ -422,7 +423,7 @@ def main():
     k_ms = kms[0] / max(kn[0], 1)
     alg_bytes = BYTES_PER_PARTICLE * n_local + BYTES_PER_NODE * nodes
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
-    tr = kernel_traffic()
+    tr = kernel_traffic(sim.dims)
     traffic = None
     if tr is not None and tr.get("workload") == args.workload:
         traffic = tr["dram_bytes_per_launch"]
@@ -466,10 +467,11 @@ def main():
                        "ppc": [w["ppc_ion"], w["ppc_electron"]], "particles_per_gpu": n_local,
                        "tile": sim.cfg.tile or (10 if sim.dims == 3 else 16), "sort_every": sim.cfg.sort_every,
                        "dims": sim.dims, "ny": sim.ny,
-                       "l2": "inputs larger than L2 (particle state %.1f GB)" % (24 * n_local / 1e9),
+                       "l2": "inputs larger than L2 (particle state %.1f GB)" % (BYTES_PER_PARTICLE / 2 * n_local / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_particles",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_particles3" if sim.dims == 3 else "k_particles",
                          "peak_source": peak_kind, "kernel_ms": k_ms,
                          "alg_bytes_per_launch": alg_bytes},
             "kernel_ms_per_step": {"particles": k_ms, "fields": kms[1] / max(args.steps, 1),

@@ -299,10 +299,11 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
             }
         }
         if (kPair && moved) {
-            const long long a0 = kQOne - x0, a1 = kQOne - x1, c0 = kQOne - z0, c1 = kQOne - z1;
-            red64g(a.rho_next + g00, a1 * c1 - a0 * c0);
+            // weights are at most 2^16: each product is one 32 x 32 -> 64-bit multiply
+            const int a0 = kQOne - x0, a1 = kQOne - x1, c0 = kQOne - z0, c1 = kQOne - z1;
+            red64g(a.rho_next + g00, (long long)a1 * c1 - (long long)a0 * c0);
             red64g(a.rho_next + g10, (long long)x1 * c1 - (long long)x0 * c0);
-            red64g(a.rho_next + g01, a1 * z1 - a0 * z0);
+            red64g(a.rho_next + g01, (long long)a1 * z1 - (long long)a0 * z0);
             red64g(a.rho_next + g11, (long long)x1 * z1 - (long long)x0 * z0);
         }
     } else {

@@ -134,6 +134,8 @@ struct Args3 {
     Species3 sp[2];
 };
 
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ void red64(u64* p, long long v)
 {
     if (v != 0) atomicAdd(p, (u64)v);
@@ -152,43 +154,41 @@ __device__ __noinline__ void deposit3_general(Geo3 g, u64* J0, u64* J1, u64* J2,
     hat3q(Y1 - by * kQ3, S1y[0], S1y[1], S1y[2]);
     hat3q(Z0 - bz * kQ3, S0z[0], S0z[1], S0z[2]);
     hat3q(Z1 - bz * kQ3, S1z[0], S1z[1], S1z[2]);
-    const long long sg = jsign;
+    // edge sums and weight products in 32-bit (at most 6 * 2^28), widened once per term
+    const int sg = jsign;
     for (int c = 0; c < 3; c++)
         for (int b = 0; b < 3; b++) {
             const int jj = wrapn(by + b, g.ny);
             if (jsign) {
-                const long long P = 2LL * S0y[b] * S0z[c] + (long long)S1y[b] * S0z[c] + (long long)S0y[b] * S1z[c] +
-                                    2LL * S1y[b] * S1z[c];
+                const int P = 2 * S0y[b] * S0z[c] + S1y[b] * S0z[c] + S0y[b] * S1z[c] + 2 * S1y[b] * S1z[c];
                 long long acc = 0;
                 for (int q = 0; q < 2; q++) {
-                    acc -= (long long)(S1x[q] - S0x[q]) * P;
-                    red64(J0 + idx3(g, wrapn(bx + q, g.nx), jj, bz + c), sg * acc);
+                    acc -= (long long)(sg * (S1x[q] - S0x[q])) * P;
+                    red64(J0 + idx3(g, wrapn(bx + q, g.nx), jj, bz + c), acc);
                 }
             }
             if (pair)
                 for (int q = 0; q < 3; q++)
                     red64(rho_next + idx3(g, wrapn(bx + q, g.nx), jj, bz + c),
-                          (long long)S1x[q] * S1y[b] * S1z[c] - (long long)S0x[q] * S0y[b] * S0z[c]);
+                          (long long)(S1x[q] * S1y[b]) * S1z[c] - (long long)(S0x[q] * S0y[b]) * S0z[c]);
         }
     if (!jsign) return;
     for (int c = 0; c < 3; c++)
         for (int q = 0; q < 3; q++) {
-            const long long P = 2LL * S0x[q] * S0z[c] + (long long)S1x[q] * S0z[c] + (long long)S0x[q] * S1z[c] +
-                                2LL * S1x[q] * S1z[c];
+            const int P = 2 * S0x[q] * S0z[c] + S1x[q] * S0z[c] + S0x[q] * S1z[c] + 2 * S1x[q] * S1z[c];
             long long acc = 0;
             for (int b = 0; b < 2; b++) {
-                acc -= (long long)(S1y[b] - S0y[b]) * P;
-                red64(J1 + idx3(g, wrapn(bx + q, g.nx), wrapn(by + b, g.ny), bz + c), sg * acc);
+                acc -= (long long)(sg * (S1y[b] - S0y[b])) * P;
+                red64(J1 + idx3(g, wrapn(bx + q, g.nx), wrapn(by + b, g.ny), bz + c), acc);
             }
         }
     for (int b = 0; b < 3; b++)
         for (int q = 0; q < 3; q++) {
-            const long long P = 2LL * S0x[q] * S0y[b] + (long long)S1x[q] * S0y[b] + (long long)S0x[q] * S1y[b] +
-                                2LL * S1x[q] * S1y[b];
+            const int P = 2 * S0x[q] * S0y[b] + S1x[q] * S0y[b] + S0x[q] * S1y[b] + 2 * S1x[q] * S1y[b];
             long long acc = 0;
             for (int c = 0; c < 2; c++) {
-                acc -= (long long)(S1z[c] - S0z[c]) * P;
-                red64(J2 + idx3(g, wrapn(bx + q, g.nx), wrapn(by + b, g.ny), bz + c), sg * acc);
+                acc -= (long long)(sg * (S1z[c] - S0z[c])) * P;
+                red64(J2 + idx3(g, wrapn(bx + q, g.nx), wrapn(by + b, g.ny), bz + c), acc);
             }
         }
 }
@@ -275,47 +275,47 @@ __device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u6
     // one base index and the offsets to the cell's other corners (x, y periodic)
     const size_t base = idx3(g, i, j, k);
     const ptrdiff_t ox = i1 - i, oy = (ptrdiff_t)(j1 - j) * g.nx, oz = (ptrdiff_t)g.nx * g.ny;
+    // Products of two weights (each at most 2^14) and the edge sums 2 S0 S0' + S1 S0' + S0 S1' + 2 S1 S1'
+    // (at most 6 * 2^28 < 2^31) are exact in 32-bit; one widening multiply forms each 64-bit term.
     if (jsign) {
-        const long long sg = jsign;
-        const long long ay0 = kQ3 - y0, ay1 = kQ3 - y1, az0 = kQ3 - z0, az1 = kQ3 - z1, ax0 = kQ3 - x0,
-                        ax1 = kQ3 - x1;
-        const int dX = x1 - x0, dY = y1 - y0, dZ = z1 - z0;
+        const int ay0 = kQ3 - y0, ay1 = kQ3 - y1, az0 = kQ3 - z0, az1 = kQ3 - z1, ax0 = kQ3 - x0, ax1 = kQ3 - x1;
+        const int dX = jsign * (x1 - x0), dY = jsign * (y1 - y0), dZ = jsign * (z1 - z0);
         if (dX) {
             // J6x(i+1/2, j+b, k+c) = dX (2 S0y S0z + S1y S0z + S0y S1z + 2 S1y S1z)
-            const long long p00 = 2 * ay0 * az0 + ay1 * az0 + ay0 * az1 + 2 * ay1 * az1;
-            const long long p10 = 2LL * y0 * az0 + (long long)y1 * az0 + (long long)y0 * az1 + 2LL * y1 * az1;
-            const long long p01 = 2 * ay0 * z0 + ay1 * z0 + ay0 * z1 + 2 * ay1 * z1;
-            const long long p11 = 2LL * y0 * z0 + (long long)y1 * z0 + (long long)y0 * z1 + 2LL * y1 * z1;
-            red64(J0 + base, sg * dX * p00);
-            red64(J0 + base + oy, sg * dX * p10);
-            red64(J0 + base + oz, sg * dX * p01);
-            red64(J0 + base + oy + oz, sg * dX * p11);
+            const int p00 = 2 * ay0 * az0 + ay1 * az0 + ay0 * az1 + 2 * ay1 * az1;
+            const int p10 = 2 * y0 * az0 + y1 * az0 + y0 * az1 + 2 * y1 * az1;
+            const int p01 = 2 * ay0 * z0 + ay1 * z0 + ay0 * z1 + 2 * ay1 * z1;
+            const int p11 = 2 * y0 * z0 + y1 * z0 + y0 * z1 + 2 * y1 * z1;
+            red64(J0 + base, (long long)dX * p00);
+            red64(J0 + base + oy, (long long)dX * p10);
+            red64(J0 + base + oz, (long long)dX * p01);
+            red64(J0 + base + oy + oz, (long long)dX * p11);
         }
         if (dY) {
-            const long long p00 = 2 * ax0 * az0 + ax1 * az0 + ax0 * az1 + 2 * ax1 * az1;
-            const long long p10 = 2LL * x0 * az0 + (long long)x1 * az0 + (long long)x0 * az1 + 2LL * x1 * az1;
-            const long long p01 = 2 * ax0 * z0 + ax1 * z0 + ax0 * z1 + 2 * ax1 * z1;
-            const long long p11 = 2LL * x0 * z0 + (long long)x1 * z0 + (long long)x0 * z1 + 2LL * x1 * z1;
-            red64(J1 + base, sg * dY * p00);
-            red64(J1 + base + ox, sg * dY * p10);
-            red64(J1 + base + oz, sg * dY * p01);
-            red64(J1 + base + ox + oz, sg * dY * p11);
+            const int p00 = 2 * ax0 * az0 + ax1 * az0 + ax0 * az1 + 2 * ax1 * az1;
+            const int p10 = 2 * x0 * az0 + x1 * az0 + x0 * az1 + 2 * x1 * az1;
+            const int p01 = 2 * ax0 * z0 + ax1 * z0 + ax0 * z1 + 2 * ax1 * z1;
+            const int p11 = 2 * x0 * z0 + x1 * z0 + x0 * z1 + 2 * x1 * z1;
+            red64(J1 + base, (long long)dY * p00);
+            red64(J1 + base + ox, (long long)dY * p10);
+            red64(J1 + base + oz, (long long)dY * p01);
+            red64(J1 + base + ox + oz, (long long)dY * p11);
         }
         if (dZ) {
-            const long long p00 = 2 * ax0 * ay0 + ax1 * ay0 + ax0 * ay1 + 2 * ax1 * ay1;
-            const long long p10 = 2LL * x0 * ay0 + (long long)x1 * ay0 + (long long)x0 * ay1 + 2LL * x1 * ay1;
-            const long long p01 = 2 * ax0 * y0 + ax1 * y0 + ax0 * y1 + 2 * ax1 * y1;
-            const long long p11 = 2LL * x0 * y0 + (long long)x1 * y0 + (long long)x0 * y1 + 2LL * x1 * y1;
-            red64(J2 + base, sg * dZ * p00);
-            red64(J2 + base + ox, sg * dZ * p10);
-            red64(J2 + base + oy, sg * dZ * p01);
-            red64(J2 + base + ox + oy, sg * dZ * p11);
+            const int p00 = 2 * ax0 * ay0 + ax1 * ay0 + ax0 * ay1 + 2 * ax1 * ay1;
+            const int p10 = 2 * x0 * ay0 + x1 * ay0 + x0 * ay1 + 2 * x1 * ay1;
+            const int p01 = 2 * ax0 * y0 + ax1 * y0 + ax0 * y1 + 2 * ax1 * y1;
+            const int p11 = 2 * x0 * y0 + x1 * y0 + x0 * y1 + 2 * x1 * y1;
+            red64(J2 + base, (long long)dZ * p00);
+            red64(J2 + base + ox, (long long)dZ * p10);
+            red64(J2 + base + oy, (long long)dZ * p01);
+            red64(J2 + base + ox + oy, (long long)dZ * p11);
         }
     }
     if (pair) {
-        const long long sx0[2] = {kQ3 - x0, x0}, sx1[2] = {kQ3 - x1, x1};
-        const long long sy0[2] = {kQ3 - y0, y0}, sy1[2] = {kQ3 - y1, y1};
-        const long long sz0[2] = {kQ3 - z0, z0}, sz1[2] = {kQ3 - z1, z1};
+        const int sx0[2] = {kQ3 - x0, x0}, sx1[2] = {kQ3 - x1, x1};
+        const int sy0[2] = {kQ3 - y0, y0}, sy1[2] = {kQ3 - y1, y1};
+        const int sz0[2] = {kQ3 - z0, z0}, sz1[2] = {kQ3 - z1, z1};
 #pragma unroll
         for (int c = 0; c < 2; c++)
 #pragma unroll
@@ -323,7 +323,7 @@ __device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u6
 #pragma unroll
                 for (int q = 0; q < 2; q++)
                     red64(rho_next + base + (q ? ox : 0) + (b ? oy : 0) + (c ? oz : 0),
-                          sx1[q] * sy1[b] * sz1[c] - sx0[q] * sy0[b] * sz0[c]);
+                          (long long)(sx1[q] * sy1[b]) * sz1[c] - (long long)(sx0[q] * sy0[b]) * sz0[c]);
     }
 }
 
@@ -485,7 +485,20 @@ __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const __grid_constant
             const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
             // consecutive threads take consecutive particles: coalesced loads and stores straight
             // from the records, no block barrier per chunk
-            for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock3) process3<FULL>(a, S, w, S.pair != 0, p);
+            for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock3) {
+                // the record two iterations ahead into L1: its DRAM latency hides behind this particle
+                const int q = p + 2 * kBlock3;
+                if (q < p1) {
+                    prefetch_l1(S.cell + q);
+                    prefetch_l1(S.fx + q);
+                    prefetch_l1(S.fy + q);
+                    prefetch_l1(S.fz + q);
+                    prefetch_l1(S.ux + q);
+                    prefetch_l1(S.uy + q);
+                    prefetch_l1(S.uz + q);
+                }
+                process3<FULL>(a, S, w, S.pair != 0, p);
+            }
         }
     }
 }
