@@ -141,12 +141,10 @@ __device__ __forceinline__ void split2(int cell, int nx, unsigned magic, int& i,
 }
 
 // Particle of this thread in chunk `ch` (blocks of 256 threads take chunks of 256 consecutive
-// particles): the lanes of a warp take particles 8 apart, so that the cell-sorted particles of one
-// cell fall to different warps and a warp's node atomics rarely share an address.
-__device__ __forceinline__ int64_t spread_index(int64_t ch)
-{
-    return ch * 256 + (int64_t)((threadIdx.x & 31) * 8 + (threadIdx.x >> 5));
-}
+// records). The cell sort's storage layout already gives the 32 consecutive records of a warp 32
+// different cells (runs of the cell order side by side), so a warp's node atomics rarely share an
+// address while its loads stay coalesced.
+__device__ __forceinline__ int64_t spread_index(int64_t ch) { return ch * 256 + (int64_t)threadIdx.x; }
 
 __device__ __forceinline__ double block_sum_d(double v, double* sh)
 {

@@ -4,14 +4,14 @@
 // current deposition (Esirkepov, fixed point) -> node density at the new position.
 //
 // Work decomposition (GB300):
-//  * one CTA owns one tile of T x T cells at a time (particles are sorted into tiles, and by
-//    cell inside a tile);
+//  * one CTA owns one tile of T x T cells at a time (particles are sorted into tiles);
 //  * the CTA stages a window of (T + 2M + 3)^2 nodes in shared memory: the six field
 //    components and the pair density n / n0 in FP32;
-//  * particles stream through shared memory in chunks of up to 1024: loaded and stored with
-//    coalesced accesses, processed transposed, so that lane l of a warp takes the particle R
-//    places after lane l-1 in the cell-sorted order. Lanes then sit in different cells and their
-//    deposits rarely meet on one address;
+//  * thread t of the CTA takes the tile's records t, t + 256, ... straight from global memory
+//    (coalesced loads and stores, no block barrier). The cell sort stores each block of 1024 of
+//    a tile's cell-ordered particles as a 32-row matrix, column by column, so the lanes of a warp
+//    hold particles 32 places apart in the cell order: neighbouring cells, whose deposits go to
+//    distinct nodes that share cache sectors;
 //  * deposits (current, node-density change) are exact 64-bit integer reductions straight into
 //    global memory: fire-and-forget on the SM, native in L2. Measured against exact sums in the
 //    shared-memory window (32-bit (lo, hi) pairs whose low-word atomic must return the old value
@@ -32,11 +32,6 @@ namespace gbpic {
 
 constexpr int kMargin = 2;              // cells a particle may drift out of its tile between sorts
 constexpr int kBlock = 256;
-constexpr int kWarps = kBlock / 32;
-constexpr int kChunkRows = 32;          // particles per lane row of a full chunk
-constexpr int kChunk = 32 * kChunkRows; // particles per chunk
-constexpr int kPitch = 33;              // padded pitch of a column of 32 lanes (conflict-free)
-constexpr int kChunkWords = kChunkRows * kPitch;
 
 __device__ __forceinline__ int wrap_any(int i, int nx)
 {
@@ -313,7 +308,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     }
 }
 
-// One tile of one simulation: stage the window, stream the tile's particles, flush.
+// One tile of one simulation: stage the window, then advance the tile's particles in storage order.
 template <bool FULL>
 __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
 {
@@ -324,11 +319,6 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
     float* fbase = reinterpret_cast<float*>(smem);
     for (int q = 0; q < 6; q++) w.f[q] = fbase + q * WW;
     w.nh = fbase + 6 * WW;
-    unsigned* chunk = smem + 7 * WW;
-    int* c_cell = reinterpret_cast<int*>(chunk);
-    float* c_f[5];
-    for (int q = 0; q < 5; q++) c_f[q] = reinterpret_cast<float*>(chunk + (q + 1) * kChunkWords);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     {
         int cnt = 0;
@@ -364,53 +354,17 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
             if (s >= a.nsp) break;
             const Species& S = a.sp[s];
             const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
-            for (int c0 = p0; c0 < p1; c0 += kChunk) {
-                const int n = min(kChunk, p1 - c0);
-                // particles per lane row: the power of two that holds the chunk (32 when full)
-                const int lg = n > 512 ? 5 : 32 - __clz(((n + 31) >> 5) - 1);
-                const int rows = 1 << lg;
-                // coalesced load: chunk index ci -> (row ci / rows, column ci % rows)
-                for (int ci = threadIdx.x; ci < n; ci += kBlock) {
-                    const int r = ci >> lg, col = ci & (rows - 1);
-                    const int slot = col * kPitch + r;
-                    c_cell[slot] = S.a.cell[c0 + ci];
-                    c_f[0][slot] = S.a.fx[c0 + ci];
-                    c_f[1][slot] = S.a.fz[c0 + ci];
-                    c_f[2][slot] = S.a.ux[c0 + ci];
-                    c_f[3][slot] = S.a.uy[c0 + ci];
-                    c_f[4][slot] = S.a.uz[c0 + ci];
-                }
-                __syncthreads();
-                // transposed processing: lane l takes row l, so lanes are `rows` particles apart
-                for (int col = warp; col < rows; col += kWarps) {
-                    const int ci = (lane << lg) + col;
-                    if (ci < n) {
-                        const int slot = col * kPitch + lane;
-                        int cell = c_cell[slot];
-                        float fx = c_f[0][slot], fz = c_f[1][slot], ux = c_f[2][slot], uy = c_f[3][slot],
-                              uz = c_f[4][slot];
-                        if (s == 0) process_particle<FULL ? kIon : kAtom>(a, S, w, cell, fx, fz, ux, uy, uz);
-                        else process_particle<kElectron>(a, S, w, cell, fx, fz, ux, uy, uz);
-                        c_cell[slot] = cell;
-                        c_f[0][slot] = fx;
-                        c_f[1][slot] = fz;
-                        c_f[2][slot] = ux;
-                        c_f[3][slot] = uy;
-                        c_f[4][slot] = uz;
-                    }
-                }
-                __syncthreads();
-                for (int ci = threadIdx.x; ci < n; ci += kBlock) {
-                    const int r = ci >> lg, col = ci & (rows - 1);
-                    const int slot = col * kPitch + r;
-                    S.a.cell[c0 + ci] = c_cell[slot];
-                    S.a.fx[c0 + ci] = c_f[0][slot];
-                    S.a.fz[c0 + ci] = c_f[1][slot];
-                    S.a.ux[c0 + ci] = c_f[2][slot];
-                    S.a.uy[c0 + ci] = c_f[3][slot];
-                    S.a.uz[c0 + ci] = c_f[4][slot];
-                }
-                __syncthreads();
+            for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock) {
+                int cell = S.a.cell[p];
+                float fx = S.a.fx[p], fz = S.a.fz[p], ux = S.a.ux[p], uy = S.a.uy[p], uz = S.a.uz[p];
+                if (s == 0) process_particle<FULL ? kIon : kAtom>(a, S, w, cell, fx, fz, ux, uy, uz);
+                else process_particle<kElectron>(a, S, w, cell, fx, fz, ux, uy, uz);
+                S.a.cell[p] = cell;
+                S.a.fx[p] = fx;
+                S.a.fz[p] = fz;
+                S.a.ux[p] = ux;
+                S.a.uy[p] = uy;
+                S.a.uz[p] = uz;
             }
         }
         __syncthreads();
@@ -443,7 +397,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_particles_batch(int nslab, int to
     }
 }
 
-size_t particle_smem_bytes(int W) { return sizeof(unsigned) * ((size_t)7 * W * W + 6 * kChunkWords); }
+size_t particle_smem_bytes(int W) { return sizeof(unsigned) * (size_t)7 * W * W; }
 
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
 {

@@ -6,9 +6,10 @@
 // Ez (i,j,k+1/2), Bx (i,j+1/2,k+1/2), By (i+1/2,j,k+1/2), Bz (i+1/2,j+1/2,k).
 //
 // The particle kernel stages each tile's fields and node density in shared memory and streams the
-// tile's particles straight from their records in coalesced order; deposits use global 64-bit
-// reductions, which are native in L2 (lanes of one cell hitting the same node need no shared
-// accumulator and no transposed order).
+// tile's particles straight from their records in coalesced order; the cell sort stores each
+// block of 256 of a tile's cell-ordered particles column by column as a 32-row matrix, so the
+// lanes of a warp hold particles 8 places apart in the cell order (neighbouring cells). Deposits
+// use global 64-bit reductions, which are native in L2.
 #include "pic_device.cuh"
 
 namespace gbpic {

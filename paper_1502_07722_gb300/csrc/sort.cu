@@ -1,8 +1,13 @@
 // Cell sort of one species into tiles (counting sort by a tile-major cell key):
 // count per key -> exclusive scan -> scatter into the second buffer -> swap.
 // The key of cell (i, k) is tile * T^2 + (k mod T) * T + (i mod T), tile = (k / T) * ntx + i / T
-// (in 3D likewise with T^3 cells per tile), so the particles of a tile are contiguous and, within
-// a tile, ordered by cell.
+// (in 3D likewise with T^3 cells per tile), so the particles of a tile are contiguous.
+// Inside a tile the cell-ordered list is cut into blocks of kLayoutBlock particles (1024 in 2D,
+// 256 in 3D: 32 x the particles per cell of a typical slab) and each block is stored column by
+// column as a 32-row matrix whose rows are consecutive runs of the cell order. The particle
+// kernels read their records in memory order, coalesced, and the 32 lanes of a warp then hold
+// particles one run apart: neighbouring cells, so a warp's deposits go to distinct nodes that
+// share cache sectors, without a transposing copy through shared memory.
 // The order of particles inside one cell is not fixed (atomic cursors); nothing downstream
 // depends on it because every deposit is an exact integer sum.
 #include "pic_internal.cuh"
@@ -14,7 +19,22 @@ constexpr int kScanItems = 2 * kScanBlock;
 
 struct KeyGeo {
     int nx, ny, T, ntx, nty, dims;
+    int TT;     // cells per tile
 };
+
+constexpr int kLayoutBlock2 = 1024, kLayoutBlock3 = 256;
+
+// Storage slot, relative to its tile, of the particle at place ci of the tile's cell order (nt
+// particles in the tile): block ci / B, and inside a block of nb particles the element (row
+// j / C, column j mod C) of a row-major matrix with C = ceil(nb / 32) columns, stored column-major
+// (the last row may be short, so column c holds R + (c < rem) elements). A bijection of 0..nt-1.
+__device__ __forceinline__ int layout_slot(int ci, int nt, int B)
+{
+    const int blk = ci / B, j = ci - blk * B, nb = min(B, nt - blk * B);
+    const int C = (nb + 31) >> 5, R = nb / C, rem = nb - R * C;
+    const int r = j / C, c = j - r * C;
+    return blk * B + c * R + min(c, rem) + r;
+}
 
 // 2D: cell = k*nx + i; 3D: cell = (k*ny + j)*nx + i. Tiles of T^dims cells, tile-major.
 __device__ __forceinline__ int cell_key(int cell, const KeyGeo& g)
@@ -124,7 +144,8 @@ __global__ void k_tile_starts(const int32_t* __restrict__ off, int ntiles, int T
     if (t <= ntiles) tile_start[t] = off[(size_t)t * TT];
 }
 
-__global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, KeyGeo kg, int32_t* cursor)
+__global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, KeyGeo kg, int32_t* cursor,
+                          const int32_t* __restrict__ tile_start)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nround = (n + 31) & ~(int64_t)31;
@@ -140,7 +161,10 @@ __global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, KeyGeo kg, 
         if (valid && (int)lane == leader) base = atomicAdd(cursor + key, __popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (!valid) continue;
-        const int q = base + __popc(peers & ((1u << lane) - 1u));
+        // place in the cell order -> storage slot of the tile's block layout
+        const int t = key / kg.TT, ts = tile_start[t];
+        const int q = ts + layout_slot(base + __popc(peers & ((1u << lane) - 1u)) - ts, tile_start[t + 1] - ts,
+                                       kg.dims == 3 ? kLayoutBlock3 : kLayoutBlock2);
         dst.cell[q] = c;
         dst.fx[q] = src.fx[p];
         if (kg.dims == 3) dst.fy[q] = src.fy[p];
@@ -157,7 +181,7 @@ void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* laun
 {
     Species& S = c.sp[s];
     const int TT = c.dims == 3 ? c.T * c.T * c.T : c.T * c.T;
-    const KeyGeo kg = {c.nx, c.ny, c.T, c.ntx, c.nty, c.dims};
+    const KeyGeo kg = {c.nx, c.ny, c.T, c.ntx, c.nty, c.dims, TT};
     int64_t g = (S.n + 255) / 256;
     if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
     if (g < 1) g = 1;
@@ -171,7 +195,7 @@ void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* laun
     // the cursor reuses the count array (counts are consumed by the scan)
     k_scan_add<<<(c.nkeys + 255) / 256, 256, 0, st>>>(c.keys_off, c.scan_tmp, c.nkeys, c.keys_count, (int32_t)S.n);
     k_tile_starts<<<(c.ntiles + 1 + 255) / 256, 256, 0, st>>>(c.keys_off, c.ntiles, TT, S.tile_start);
-    if (S.n > 0) k_scatter<<<(int)g, 256, 0, st>>>(src, dst, S.n, kg, c.keys_count);
+    if (S.n > 0) k_scatter<<<(int)g, 256, 0, st>>>(src, dst, S.n, kg, c.keys_count, S.tile_start);
     if (!from_b) {
         SpeciesBuf t = S.a;
         S.a = S.b;

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from paper_1502_07722_gb300.workloads import workload
 from tests import inputs
+from tests.sort_layout import cell_key, undo_layout
 
 pytestmark = pytest.mark.gpu
 
@@ -232,16 +233,15 @@ def test_sort_is_a_permutation_into_tiles():
     sim.sort()
     after = [sim.get_particles(s) for s in (0, 1)]
     T, nx = 16, 70
-    ntx = (nx + T - 1) // T
     for b, a in zip(before, after):
         kb = np.lexsort([b[k].cpu().numpy() for k in ("uz", "uy", "ux", "fz", "fx", "cell")])
         ka = np.lexsort([a[k].cpu().numpy() for k in ("uz", "uy", "ux", "fz", "fx", "cell")])
         for k in b:
             assert np.array_equal(b[k].cpu().numpy()[kb], a[k].cpu().numpy()[ka])
-        cell = a["cell"].cpu().numpy()
-        i, kk = cell % nx, cell // nx
-        key = ((kk // T) * ntx + i // T) * T * T + (kk % T) * T + (i % T)
-        assert (np.diff(key) >= 0).all()
+        # tile-major; inside a tile the cell order, stored by blocks of 1024 as 32-row matrices
+        key = cell_key(a["cell"].cpu().numpy().astype(np.int64), nx, 1, T, 2)
+        ordered, _ = undo_layout(key, T * T, 1024)
+        assert (np.diff(ordered) >= 0).all()
 
 
 def test_deterministic_grids():
