@@ -45,6 +45,8 @@ class OracleConfig(ctypes.Structure):
         ("s_rep", ctypes.c_double), ("lambda_", ctypes.c_double), ("I0", ctypes.c_double),
         ("tau_fwhm", ctypes.c_double), ("w0", ctypes.c_double), ("t_peak", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
     ]
 
 
@@ -125,6 +127,7 @@ def lib():
             "oracle_maxwell_cont": (None, [vp, _D, _D, ctypes.c_double, ctypes.c_int64]),
             "oracle_maxwell_cont_T": (None, [vp, _D, _D, ctypes.c_int64, _D]),
             "oracle_r0": (ctypes.c_double, [vp]),
+            "oracle_crater_profile": (None, [vp, _I64, _I64, _D]),
             "oracle3_create": (vp, [ctypes.POINTER(OracleConfig3), ctypes.c_int32]),
             "oracle3_free": (None, [vp]),
             "oracle3_num_particles": (ctypes.c_int64, [vp, ctypes.c_int32]),
@@ -249,6 +252,17 @@ class Oracle:
     def set_rho(self, a):
         a = np.ascontiguousarray(a, np.int64).reshape(-1)
         lib().oracle_set_rho(self._s, _p(a, ctypes.c_int64))
+
+    def crater_profile(self, rho0, rho=None):
+        """Material missing from each node column of the original slab (m of solid-density
+        material) between node sums rho0 and rho (default: the state's own)."""
+        r0 = np.ascontiguousarray(rho0, np.int64).reshape(-1)
+        assert r0.size == self._nn()
+        r = None if rho is None else np.ascontiguousarray(rho, np.int64).reshape(-1)
+        out = np.empty(self.nx, np.float64)
+        lib().oracle_crater_profile(self._s, _p(r0, ctypes.c_int64),
+                                    None if r is None else _p(r, ctypes.c_int64), _p(out, ctypes.c_double))
+        return out
 
     def get_current(self):
         out = np.empty(3 * self._nn(), np.int64)
@@ -534,3 +548,29 @@ def deposit_current3(nx, ny, nz, sign, x0, y0, z0, x1, y1, z1, out=None):
     lib().oracle3_deposit_current(nx, ny, nz, len(a[0]), sign, *[_p(v, ctypes.c_double) for v in a],
                                   _p(out[0], ctypes.c_int64), _p(out[1], ctypes.c_int64), _p(out[2], ctypes.c_int64))
     return out
+
+
+def crater_width(profile, dx, threshold=None):
+    """Width of the crater around its deepest column: the columns above the threshold that join
+    the deepest one form the crater; each edge is placed where the straight line between the last
+    column inside and the first outside meets the threshold. x periodic. Returns (depth, width) in
+    metres."""
+    d = np.asarray(profile, np.float64)
+    th = 0.5 * dx if threshold is None else threshold
+    n = d.size
+    c = int(np.argmax(d))
+    if d[c] <= th:
+        return float(d[c]), 0.0
+    rolled = np.roll(d, n // 2 - c)                 # deepest column in the middle
+    mid = n // 2
+    inside = rolled > th
+    hi = mid
+    while hi + 1 < n and inside[hi + 1]:
+        hi += 1
+    lo = mid
+    while lo - 1 >= 0 and inside[lo - 1]:
+        lo -= 1
+    def edge(j_in, j_out):
+        t = (rolled[j_in] - th) / (rolled[j_in] - rolled[j_out % n])
+        return j_in + t * (j_out - j_in)
+    return float(d[c]), float((edge(hi, hi + 1) - edge(lo, lo - 1)) * dx)

@@ -77,6 +77,9 @@ typedef struct {
     double c_att, s_rep;     /* altered potential: factor on the attractive / repulsive side */
     double lambda, I0, tau_fwhm, w0, t_peak;   /* laser (m, W/m^2, s, m, s)                  */
     uint64_t seed;
+    int32_t temp_profile;    /* 0: uniform T_ion_K; 1: lattice temperature of a laser spot       */
+    int32_t reserved0;
+    double T_spot_K, spot_w, spot_depth;       /* K, m (1/e^2 radius), m (1/e depth)         */
 } ocfg;
 
 typedef struct {
@@ -501,6 +504,18 @@ static void alloc_species(ostate* s, int sp, int64_t n)
 /* Initial state (paper: a damage simulation is initialised for target density and
  * temperature): a slab of cell rows k < slab_k, ppc macro-ions per cell at uniformly drawn
  * positions, Maxwellian momenta; electrons co-located with the ions (zero net charge, E = 0). */
+/* Lattice temperature the atomic-transport run starts from (paper: initialisation paragraph and
+ * Fig. 2, the lattice temperature once electrons and lattice have equilibrated; the figure itself
+ * is not available, so a synthetic laser spot stands in for it): at the surface row slab_k the
+ * temperature rises from T_ion_K to T_spot_K on the axis x = nx/2 with a Gaussian of 1/e^2
+ * radius spot_w, and decays into the slab with 1/e depth spot_depth. (x, z) in cells. */
+static double spot_temperature(const ocfg* c, double x, double z)
+{
+    double lateral = (x - 0.5 * c->nx) * c->dx / c->spot_w;
+    double depth = (c->slab_k - z) * c->dx / c->spot_depth;
+    return c->T_ion_K + (c->T_spot_K - c->T_ion_K) * exp(-2.0 * lateral * lateral) * exp(-depth);
+}
+
 /* initial state of the particle in slot j of cell (i, k) of species sp: x, z, ux, uy, uz */
 static void init_one(const ostate* s, int sp, int64_t i, int64_t k, int64_t j, double out[5])
 {
@@ -517,9 +532,12 @@ static void init_one(const ostate* s, int sp, int64_t i, int64_t k, int64_t j, d
     double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 3));
     double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid_pos, 4))));
     double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid_pos, 5));
-    out[2] = s->uth[sp] * r1 * cos(a1);
-    out[3] = s->uth[sp] * r1 * sin(a1);
-    out[4] = s->uth[sp] * r2 * cos(a2);
+    double uth = s->uth[sp];
+    if (sp == 0 && c->temp_profile == 1)
+        uth = sqrt(O_KB * spot_temperature(c, out[0], out[1]) / (s->m[0] * O_C * O_C));
+    out[2] = uth * r1 * cos(a1);
+    out[3] = uth * r1 * sin(a1);
+    out[4] = uth * r2 * cos(a2);
 }
 
 static void init_particles(ostate* s)
@@ -684,6 +702,24 @@ static void push_particle(ostate* s, int sp, int64_t p)
     double u[3] = {s->ux[sp][p], s->uy[sp][p], s->uz[sp][p]};
     push_one(s, sp, &s->x[sp][p], &s->z[sp][p], u);
     s->ux[sp][p] = u[0]; s->uy[sp][p] = u[1]; s->uz[sp][p] = u[2];
+}
+
+/* Crater profile (paper: after solidification the crater's width and depth are read off the
+ * density map): for every node column i, the material missing from the original slab as a
+ * thickness of solid-density material (m): dx * sum over node rows k = 0..slab_k of the density
+ * drop (rho0 - rho)(k, i) in units of the solid density. rho NULL: the state's own node sums. */
+void oracle_crater_profile(const ostate* s, const int64_t* rho0, const int64_t* rho, double* out)
+{
+    const ocfg* c = &s->c;
+    const int64_t* now = rho ? rho : s->rho;
+    int top = c->slab_k < c->nz ? c->slab_k : c->nz;
+    /* a node sum counts 2^-32 macro-atoms per cell area: density = sum * w / (2^32 dx^2) */
+    double to_solid = s->w / (4294967296.0 * c->dx * c->dx) / c->n_atoms;
+    for (int i = 0; i < c->nx; i++) {
+        int64_t missing = 0;
+        for (int k = 0; k <= top; k++) missing += rho0[NODE(s, i, k)] - now[NODE(s, i, k)];
+        out[i] = c->dx * ((double)missing * to_solid);
+    }
 }
 
 /* Initial state of one particle (slot j of cell (i, k)) and one particle's push from the current

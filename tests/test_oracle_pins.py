@@ -585,3 +585,91 @@ def test_acoustic_wave_speed_of_the_pair_force():
     measured = 2 * np.diff(crossings).mean() * dt
     assert measured == pytest.approx(period, rel=5e-3)
     assert np.abs(a[:, 1]).max() == pytest.approx(eps, rel=1e-2)
+
+
+def _kinetic_temperature(o, w, sel):
+    """m c^2 <u_x^2 + u_y^2 + u_z^2> / (3 k_B) of the selected atoms (u in units of c)."""
+    p = o.get_particles(0)
+    u2 = p["ux"][sel] ** 2 + p["uy"][sel] ** 2 + p["uz"][sel] ** 2
+    m = w["ion_mass_amu"] * 1.66053906660e-27
+    return m * 299792458.0 ** 2 * u2.mean() / (3 * 1.380649e-23), int(sel.sum())
+
+
+def test_spot_temperature_uniform_case_is_the_uniform_start():
+    """A spot at the base temperature reduces bit for bit to the uniform start."""
+    w = workload("transport", nx=24, nz=20, slab_k=10)
+    a = oracle.Oracle(w).get_particles(0)
+    b = oracle.Oracle(dict(w, temp_profile=1, T_spot_K=w["T_ion_K"], spot_w=50e-9, spot_depth=30e-9)).get_particles(0)
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+
+
+def test_spot_temperature_sampled_by_the_momenta():
+    """Lattice-temperature start (synthetic laser spot, reading of the initialisation paragraph):
+    the kinetic temperature of the sampled momenta is T_spot on the axis at the surface, falls to
+    the base plus (T_spot - base)/e at the 1/e depth and to the base far from the axis. Bins of
+    ~4000 atoms: the sample temperature has a relative spread sqrt(2/(3n)) ~ 1.3 %; 5 % bounds."""
+    base, top = 300.0, 9000.0
+    w = workload("transport", nx=96, nz=44, slab_k=40, ppc_ion=1024, temp_profile=1, T_ion_K=base,
+                 T_spot_K=top, spot_w=200e-9, spot_depth=100e-9)
+    o = oracle.Oracle(w)
+    p = o.get_particles(0)
+    x, z = p["x"], p["z"]
+    xc, zs = 48.0, 40.0
+    near_axis = np.abs(x - xc) < 1.0
+    t_top, n_top = _kinetic_temperature(o, w, near_axis & (z > zs - 2.0))
+    # axis, top two rows: lateral factor ~1, depth factor averaged over 0..2 cells of a 10-cell depth
+    expect_top = base + (top - base) * np.mean(np.exp(-np.linspace(0, 2, 201) / 10.0))
+    assert n_top > 3000 and t_top == pytest.approx(expect_top, rel=0.05)
+    t_deep, n_deep = _kinetic_temperature(o, w, near_axis & (np.abs(z - (zs - 10.0)) < 1.0))
+    assert n_deep > 3000 and t_deep == pytest.approx(base + (top - base) / math.e, rel=0.05)
+    t_far, n_far = _kinetic_temperature(o, w, (np.abs(x - xc) > 40.0) & (z > zs - 2.0))
+    assert n_far > 3000 and t_far == pytest.approx(base, rel=0.05)
+    # the 1/e^2 point of the lateral Gaussian: x - xc = spot_w / dx = 20 cells
+    t_w, n_w = _kinetic_temperature(o, w, (np.abs(np.abs(x - xc) - 20.0) < 0.5) & (z > zs - 2.0))
+    expect_w = base + (top - base) * math.exp(-2.0) * np.mean(np.exp(-np.linspace(0, 2, 201) / 10.0))
+    assert n_w > 3000 and t_w == pytest.approx(expect_w, rel=0.05)
+
+
+def test_crater_profile_counts_the_removed_material():
+    """Removing every atom of the top h rows of m columns of the slab leaves h m cells of solid
+    material missing: the column profile sums to h m dx (each cell of ppc macro-atoms is one cell
+    of solid-density material), spread over the node columns i1..i2 that bound those cells and
+    none other."""
+    w = workload("transport", nx=40, nz=30, slab_k=20, ppc_ion=9)
+    o = oracle.Oracle(w)
+    rho0 = o.get_rho()
+    p = o.get_particles(0)
+    i1, i2, h = 12, 19, 3
+    gone = (p["x"] >= i1) & (p["x"] < i2) & (p["z"] >= w["slab_k"] - h)
+    o.set_particles(0, *(p[k][~gone] for k in ("x", "z", "ux", "uy", "uz")))
+    o.set_rho(oracle.deposit_density(w["nx"], w["nz"], p["x"][~gone], p["z"][~gone]))
+    prof = o.crater_profile(rho0)
+    assert prof.sum() == pytest.approx(h * (i2 - i1) * w["dx"], rel=1e-12)
+    assert (prof[:i1] == 0).all() and (prof[i2 + 1:] == 0).all() and (prof[i1:i2 + 1] > 0).all()
+
+
+def test_crater_width_closed_forms():
+    """A flat-bottomed pit of depth D over columns i1..i2-1 (zero outside): the threshold t is met
+    a fraction (D - t) / D of a column outside each edge, width (i2 - 1 - i1 + 2 (D - t) / D) dx.
+    A parabolic crater d0 (1 - (x/R)^2): width 2 R sqrt(1 - t/d0), up to the linear interpolation
+    between columns. Eq. (5): F_th = F at zero width, F / e at a width equal to the beam diameter."""
+    from paper_1502_07722_gb300 import crater
+    dx, D, t = 10e-9, 40e-9, 5e-9
+    prof = np.zeros(64)
+    prof[20:31] = D
+    expect = (30 - 20 + 2 * (D - t) / D) * dx
+    depth, width = oracle.crater_width(prof, dx, t)
+    assert depth == D and width == pytest.approx(expect, rel=1e-12)
+    assert crater.crater_metrics(prof, dx, t)["width"] == pytest.approx(expect, rel=1e-12)
+    x = np.arange(200) - 100.3
+    R, d0 = 37.0, 80e-9
+    par = np.maximum(d0 * (1 - (x / R) ** 2), 0.0)
+    _, wpar = oracle.crater_width(par, dx, t)
+    assert wpar == pytest.approx(2 * R * math.sqrt(1 - t / d0) * dx, abs=0.05 * dx)
+    assert crater.crater_metrics(par, dx, t)["width"] == pytest.approx(wpar, rel=1e-12)
+    # wrapped across the periodic seam
+    assert crater.crater_metrics(np.roll(prof, -25), dx, t)["width"] == pytest.approx(expect, rel=1e-12)
+    assert oracle.crater_width(np.roll(prof, -25), dx, t)[1] == pytest.approx(expect, rel=1e-12)
+    assert crater.threshold_fluence(2.0, 0.0, 1e-6) == 2.0
+    assert crater.threshold_fluence(2.0, 1e-6, 1e-6) == pytest.approx(2.0 / math.e, rel=1e-15)
