@@ -394,10 +394,14 @@ def main():
     info = sim.info()
     n_local = sum(info["num_particles"])
     nodes = (w["nz"] + 1) * w["nx"] * sim.ny
+    global BYTES_PER_PARTICLE, BYTES_PER_NODE
     if sim.dims == 3:
         # per particle 56 B (28-byte record read and written), per node the same 64 B
-        global BYTES_PER_PARTICLE
         BYTES_PER_PARTICLE = 56
+    if w.get("mode", 0) == 1:
+        # neutral atoms: no fields, no current; per node the density read and the next density written
+        BYTES_PER_NODE = 16
+    rho0 = sim.deposit_density()[0] if w.get("temp_profile", 0) else None
 
     sim.step(args.warmup)
     gb.pic_set_timing(sim.h, True)
@@ -481,6 +485,14 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        if rho0 is not None:
+            from paper_1502_07722_gb300 import crater
+            m = crater.crater_metrics(sim.crater_profile(rho0).cpu().numpy(), w["dx"], far_field=True)
+            line["crater"] = {"time_s": sim.info()["time"], "depth_m": m["depth"], "width_m": m["width"],
+                              "far_field_level_m": m["level"],
+                              "note": "column profile of missing solid material at the end of the timed "
+                                      "steps, below the far-field surface level (a crater forms over "
+                                      "~3 ns = 250 000 steps)"}
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:

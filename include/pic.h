@@ -85,7 +85,21 @@ typedef struct pic_config {
                                 (k*ny + j)*nx + i; a particle also has fy; fixed point 2^14 per
                                 axis (weights of a node sum in units 2^-42); current J6x, J6y, J6z
                                 with J_x = J6x * e w / (6 * 2^42 dx^2 dt); dt = cfl dx / (c sqrt 3) */
+    int32_t temp_profile;    /* PIC_TEMP_UNIFORM: species 0 starts at T_ion_K everywhere.
+                                PIC_TEMP_SPOT (2D only): the lattice temperature a laser spot left
+                                behind (paper, Fig. 2 and the initialisation paragraph: the atomic-
+                                transport run starts from the lattice temperature after electrons
+                                and lattice equilibrate), for species 0 at its initial position
+                                (x, z) in cells: T = T_ion_K + (T_spot_K - T_ion_K)
+                                * exp(-2 ((x - nx/2) dx / spot_w)^2) * exp(-(slab_k - z) dx / spot_depth) */
+    int32_t reserved0;       /* 0 */
+    double T_spot_K;         /* peak temperature on the axis at the surface (K)                  */
+    double spot_w;           /* 1/e^2 radius of the lateral Gaussian (m)                          */
+    double spot_depth;       /* 1/e depth of the temperature below the surface (m)                */
 } pic_config;
+
+#define PIC_TEMP_UNIFORM 0
+#define PIC_TEMP_SPOT 1
 
 typedef struct pic_info {
     double dt;               /* s                                                               */
@@ -135,6 +149,17 @@ PIC_API int pic_step(pic_ctx* ctx, int32_t nsteps);
  * in units 2^-32 of one macroparticle (device pointer, caller-owned). *scale_out (host, may be
  * NULL) receives the factor from a sum to a density in m^-3. Recomputed from the particles. */
 PIC_API int pic_deposit_density(pic_ctx* ctx, int64_t* dev_out, double* scale_out);
+
+/* Crater profile (paper: after the crater has solidified its width and depth are measured from
+ * the density map; Eq. 5 turns the width into a threshold fluence). For every column of nodes
+ * (nx in 2D, ny*nx in 3D, index j*nx + i) the material missing from the original slab as a
+ * thickness of solid-density material, in metres:
+ *     dev_out[col] = dx * scale / n_atoms * sum_{k = 0..slab_k} (dev_rho0 - rho)(k, col),
+ * rho the node sums of the pair species at the current positions, dev_rho0 earlier node sums in
+ * the layout of pic_deposit_density (typically taken right after pic_init), scale the factor
+ * pic_deposit_density returns. The column sums are exact integers. Device pointers, caller-owned;
+ * asynchronous on the context's stream. Errors: PIC_EINVAL for NULL pointers. */
+PIC_API int pic_crater_profile(pic_ctx* ctx, const int64_t* dev_rho0, double* dev_out);
 
 /* Pair-potential force (N, per atom) on every macro-ion from the current node density
  * (paper: Eqs. 1-3, density and gradient interpolated back to the particle). dev_out:

@@ -550,6 +550,18 @@ def deposit_current3(nx, ny, nz, sign, x0, y0, z0, x1, y1, z1, out=None):
     return out
 
 
+def far_field(profile):
+    """Median of the profile over the columns at least a quarter of the period away from the
+    deepest column (the half of the columns farthest from it)."""
+    d = np.asarray(profile, np.float64)
+    n = d.size
+    c = int(np.argmax(d))
+    away = [(min((i - c) % n, (c - i) % n), i) for i in range(n)]
+    away.sort(key=lambda t: t[0])
+    keep = [i for _, i in away[n - n // 2:]]
+    return float(np.median(d[keep])) if keep else 0.0
+
+
 def crater_width(profile, dx, threshold=None):
     """Width of the crater around its deepest column: the columns above the threshold that join
     the deepest one form the crater; each edge is placed where the straight line between the last
@@ -561,6 +573,8 @@ def crater_width(profile, dx, threshold=None):
     c = int(np.argmax(d))
     if d[c] <= th:
         return float(d[c]), 0.0
+    if np.all(d > th):
+        return float(d[c]), float(n * dx)
     rolled = np.roll(d, n // 2 - c)                 # deepest column in the middle
     mid = n // 2
     inside = rolled > th

@@ -18,6 +18,7 @@ LIBPATH = os.path.join(HERE, "libgbpic.so")
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENAN, PIC_EMOVE, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PIC_MODE_FULL, PIC_MODE_TRANSPORT = 0, 1
 PIC_LASER_NONE, PIC_LASER_PLANE, PIC_LASER_GAUSSIAN = 0, 1, 2
+PIC_TEMP_UNIFORM, PIC_TEMP_SPOT = 0, 1
 FIELDS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
@@ -34,6 +35,8 @@ class pic_config(ctypes.Structure):
         ("lambda_", ctypes.c_double), ("I0", ctypes.c_double), ("tau_fwhm", ctypes.c_double),
         ("w0", ctypes.c_double), ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("ny", ctypes.c_int32), ("dims", ctypes.c_int32),
+        ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
     ]
 
 
@@ -71,6 +74,7 @@ _SIGNATURES = {
     "pic_step": (ctypes.c_int, [_VP, _I32]),
     "pic_deposit_density": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "pic_pair_force": (ctypes.c_int, [_VP, _VP]),
+    "pic_crater_profile": (ctypes.c_int, [_VP, _VP, _VP]),
     "pic_energy": (ctypes.c_int, [_VP, ctypes.POINTER(pic_energy_t)]),
     "pic_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pic_info)]),
     "pic_get_particles": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
@@ -174,6 +178,10 @@ def pic_deposit_density(h, dev_out_ptr: int) -> float:
 
 def pic_pair_force(h, dev_out_ptr: int):
     _check(load_library().pic_pair_force(h, dev_out_ptr), "pic_pair_force")
+
+
+def pic_crater_profile(h, dev_rho0_ptr: int, dev_out_ptr: int):
+    _check(load_library().pic_crater_profile(h, dev_rho0_ptr, dev_out_ptr), "pic_crater_profile")
 
 
 def pic_energy(h) -> dict:
@@ -372,6 +380,14 @@ class Simulation:
         out = self._grid(self.torch.int64)
         scale = pic_deposit_density(self.h, out.data_ptr())
         return out, scale
+
+    def crater_profile(self, rho0):
+        """Material missing from each column of the original slab (m of solid-density material)
+        against the node sums rho0 of an earlier state (from deposit_density)."""
+        out = self.torch.empty((self.ny, self.nx) if self.dims == 3 else (self.nx,), dtype=self.torch.float64,
+                               device="cuda")
+        pic_crater_profile(self.h, rho0.data_ptr(), out.data_ptr())
+        return out
 
     def pair_force(self):
         n = self.info()["num_particles"][0]

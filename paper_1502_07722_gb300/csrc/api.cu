@@ -62,6 +62,10 @@ int derive_layout(const pic_config* cfg, Layout& L)
         return PIC_EINVAL;
     if (cfg->laser_profile == PIC_LASER_GAUSSIAN && !(cfg->w0 > 0)) return PIC_EINVAL;
     if (cfg->pot_mode != 0 && cfg->pot_mode != 1) return PIC_EINVAL;
+    if (cfg->temp_profile != PIC_TEMP_UNIFORM && cfg->temp_profile != PIC_TEMP_SPOT) return PIC_EINVAL;
+    if (cfg->temp_profile == PIC_TEMP_SPOT &&
+        (L.dims != 2 || !(cfg->spot_w > 0) || !(cfg->spot_depth > 0) || !(cfg->T_spot_K >= 0)))
+        return PIC_EINVAL;
     L.nx = cfg->nx;
     L.nz = cfg->nz;
     L.T = cfg->tile > 0 ? cfg->tile : (L.dims == 3 ? 10 : 16);
@@ -444,6 +448,18 @@ int pic_deposit_density(pic_ctx* h, int64_t* dev_out, double* scale_out)
     if (scale_out)
         *scale_out = c.dims == 3 ? c.w / (4398046511104.0 * c.cfg.dx * c.cfg.dx * c.cfg.dx)
                                  : c.w / (4294967296.0 * c.cfg.dx * c.cfg.dx);
+    return PIC_OK;
+}
+
+int pic_crater_profile(pic_ctx* h, const int64_t* dev_rho0, double* dev_out)
+{
+    if (!h || !dev_rho0 || !dev_out) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.sticky) return c.sticky;
+    const double scale = c.dims == 3 ? c.w / (4398046511104.0 * c.cfg.dx * c.cfg.dx * c.cfg.dx)
+                                     : c.w / (4294967296.0 * c.cfg.dx * c.cfg.dx);
+    launch_crater_profile(c, (const u64*)dev_rho0, c.cfg.dx * scale / c.cfg.n_atoms, dev_out, c.stream);
+    CK(cudaGetLastError());
     return PIC_OK;
 }
 

@@ -1,6 +1,7 @@
 // Initial state of a damage simulation (paper: the simulation is initialised for target density
 // and temperature): ppc macroparticles per slab cell at uniformly drawn offsets, Maxwellian
-// momenta; electrons reuse the ion positions so the start is neutral with E = 0.
+// momenta at a uniform temperature or, for species 0, at the local lattice temperature of a laser
+// spot; electrons reuse the ion positions so the start is neutral with E = 0.
 //
 // Random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used counter-style, one draw =
 // the first output of a generator seeded with seed ^ key, key = ((species 2^40 + particle) 8 + d).
@@ -22,8 +23,19 @@ __device__ __forceinline__ uint64_t draw(uint64_t seed, int s, uint64_t pid, int
     return smix_first(seed ^ (((((uint64_t)s << 40) + pid) << 3) + (uint64_t)d));
 }
 
+// Lattice temperature of a laser spot (PIC_TEMP_SPOT): T at the particle's initial position (x, z)
+// in cells; the thermal momentum scale is sqrt(k_B T / (m c^2)) with the same operation order as
+// the uniform case.
+struct TempSpot {
+    int on;
+    double T_base, T_spot;     // K
+    double xc, zs;             // axis (cells) and slab surface row
+    double cx, cz;             // dx / spot_w, dx / spot_depth
+    double kb, mc2;            // k_B, m c^2
+};
+
 __global__ void k_init(SpeciesBuf out, int64_t n, int ppc, int nx, int species, int pos_species, double uth,
-                       uint64_t seed)
+                       uint64_t seed, TempSpot ts)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t cellidx = (uint64_t)p / (uint64_t)ppc;     // row-major slab cell
@@ -37,9 +49,16 @@ __global__ void k_init(SpeciesBuf out, int64_t n, int ppc, int nx, int species, 
         const double u2 = ((double)(draw(seed, species, (uint64_t)p, 4) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
         const double a2 = 2.0 * kPi * (double)(draw(seed, species, (uint64_t)p, 5) >> 40) * (1.0 / 16777216.0);
         const double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u2));
-        out.ux[p] = (float)(uth * r1 * cos(a1));
-        out.uy[p] = (float)(uth * r1 * sin(a1));
-        out.uz[p] = (float)(uth * r2 * cos(a2));
+        double u = uth;
+        if (ts.on) {
+            const double x = (double)i + (double)out.fx[p], z = (double)k + (double)out.fz[p];
+            const double ex = (x - ts.xc) * ts.cx, T = ts.T_base + (ts.T_spot - ts.T_base) *
+                                                               exp(-2.0 * ex * ex) * exp(-(ts.zs - z) * ts.cz);
+            u = sqrt(ts.kb * T / ts.mc2);
+        }
+        out.ux[p] = (float)(u * r1 * cos(a1));
+        out.uy[p] = (float)(u * r1 * sin(a1));
+        out.uz[p] = (float)(u * r2 * cos(a2));
     }
 }
 
@@ -50,7 +69,19 @@ void launch_init_particles(Ctx& c, int s, cudaStream_t st)
     int64_t g = (S.n + 255) / 256;
     if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
     const int pos_species = (s == 1 && c.cfg.ppc_electron == c.cfg.ppc_ion) ? 0 : s;
-    k_init<<<(int)g, 256, 0, st>>>(S.b, S.n, S.ppc, c.nx, s, pos_species, S.uth, c.cfg.seed);
+    TempSpot ts = {};
+    if (s == 0 && c.cfg.temp_profile == PIC_TEMP_SPOT) {
+        ts.on = 1;
+        ts.T_base = c.cfg.T_ion_K;
+        ts.T_spot = c.cfg.T_spot_K;
+        ts.xc = 0.5 * c.nx;
+        ts.zs = c.cfg.slab_k;
+        ts.cx = c.cfg.dx / c.cfg.spot_w;
+        ts.cz = c.cfg.dx / c.cfg.spot_depth;
+        ts.kb = kKb;
+        ts.mc2 = S.mass * kC * kC;
+    }
+    k_init<<<(int)g, 256, 0, st>>>(S.b, S.n, S.ppc, c.nx, s, pos_species, S.uth, c.cfg.seed, ts);
 }
 
 }  // namespace gbpic

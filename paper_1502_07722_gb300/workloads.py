@@ -64,6 +64,14 @@ WORKLOADS = {
     "transport": dict(COPPER, nx=64, nz=64, slab_k=32, ppc_ion=16, ppc_electron=0, mode=1,
                       ion_charge=0.0, T_ion_K=3000.0, dt_override=12e-15, laser_profile=0,
                       I0=0.0, w0=0.0, t_peak=0.0, seed=7, steps=1000),
+    # atomic-transport crater run (paper: 10 nm cells, 12 fs steps, a 4.5-6 um wide and 0.75-1 um
+    # thick copper target, several ns): 6 um x 1 um slab under 1.56 um of vacuum, 128 macro-atoms
+    # per cell (7.68 M), started from the lattice temperature of a 1 um laser spot (synthetic: the
+    # paper's Fig. 2 profile is not available), 250 000 steps = 3 ns
+    "crater": dict(COPPER, nx=600, nz=256, slab_k=100, ppc_ion=128, ppc_electron=0, mode=1,
+                   ion_charge=0.0, T_ion_K=300.0, dt_override=12e-15, laser_profile=0,
+                   I0=0.0, w0=0.0, t_peak=0.0, temp_profile=1, T_spot_K=20000.0, spot_w=1e-6,
+                   spot_depth=80e-9, seed=8, steps=250000),
 }
 
 

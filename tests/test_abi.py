@@ -70,7 +70,8 @@ def test_init_rejects_bad_workspace_without_touching_the_gpu(lib):
 
 def test_config_struct_layout_matches_header():
     # 10 int32 + 1 int64 + 17 double + 1 uint64 + 2 int32
-    assert ctypes.sizeof(gb.pic_config) == 10 * 4 + 8 + 17 * 8 + 8 + 2 * 4
+    assert ctypes.sizeof(gb.pic_config) == 10 * 4 + 8 + 17 * 8 + 8 + 2 * 4 + 2 * 4 + 3 * 8
+    assert gb.pic_config.T_spot_K.offset == 10 * 4 + 8 + 17 * 8 + 8 + 4 * 4
     assert gb.pic_config.max_particles.offset == 40
     assert ctypes.sizeof(gb.pic_energy_t) == 7 * 8
     assert gb.pic_energy_t.injected.offset == 48

@@ -1,0 +1,116 @@
+"""The atomic-transport stage beyond the cycle itself, through the C ABI against the oracle: the
+lattice-temperature start of a laser spot (a synthetic stand-in for the paper's Fig. 2) and the
+crater measurement (column profile of missing material, width, Eq. 5).
+
+The crater profile is an exact integer column sum times one FP64 factor, so the GPU's profile of
+its own density maps equals the oracle's profile of the same maps to the last bits of that factor
+(relative 1e-14)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_07722_gb300.workloads import workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1502_07722_gb300 import _build
+    _build.build()
+    oracle.build()
+    import paper_1502_07722_gb300 as m
+    return m
+
+
+def spot(**kw):
+    w = dict(workload("transport"), nx=72, nz=48, slab_k=30, ppc_ion=16, temp_profile=1, T_ion_K=300.0,
+             T_spot_K=20000.0, spot_w=150e-9, spot_depth=60e-9, sort_every=10)
+    w.update(kw)
+    return w
+
+
+def test_spot_start_matches_oracle(gb):
+    """Same seed: positions bit-exact, momenta at the local spot temperature to FP32 rounding."""
+    w = spot()
+    sim = gb.Simulation(w)
+    orc = oracle.Oracle(w)
+    g = sim.get_particles(0)
+    cell = g["cell"].cpu().numpy().astype(np.int64)
+    x = cell % w["nx"] + g["fx"].cpu().numpy().astype(np.float64)
+    z = cell // w["nx"] + g["fz"].cpu().numpy().astype(np.float64)
+    o = orc.get_particles(0)
+    kg, ko = np.lexsort((z, x)), np.lexsort((o["z"], o["x"]))
+    assert np.array_equal(x[kg], o["x"][ko]) and np.array_equal(z[kg], o["z"][ko])
+    for comp in ("ux", "uy", "uz"):
+        u = g[comp].cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(u[kg], o[comp][ko], rtol=1e-6, atol=1e-7 * np.abs(o[comp]).max())
+    # hotter on the axis than at the edges
+    ax = np.abs(x - w["nx"] / 2) < 4
+    u2 = sum(g[c].cpu().numpy().astype(np.float64) ** 2 for c in ("ux", "uy", "uz"))
+    assert u2[ax].mean() > 10 * u2[np.abs(x - w["nx"] / 2) > 30].mean()
+    sim.close()
+
+
+def test_spot_start_rejected_outside_2d(gb):
+    with pytest.raises(gb.PicError) as e:
+        gb.Simulation(dict(spot(), spot_w=0.0))
+    assert e.value.code == gb.PIC_EINVAL
+    with pytest.raises(gb.PicError) as e:
+        gb.Simulation(dict(spot(), dims=3, ny=8))
+    assert e.value.code == gb.PIC_EINVAL
+
+
+def test_crater_profile_matches_oracle(gb):
+    """A hot spot expands and evaporates for 2000 steps (24 ps): the GPU's profile of its own maps
+    equals the oracle's profile of the same maps; width and depth agree between the two
+    measurements."""
+    from paper_1502_07722_gb300 import crater
+    w = spot()
+    sim = gb.Simulation(w)
+    rho0, _ = sim.deposit_density()
+    assert float(sim.crater_profile(rho0).abs().max()) == 0.0
+    sim.step(2000)
+    prof = sim.crater_profile(rho0).cpu().numpy()
+    orc = oracle.Oracle(w, with_particles=False)
+    expect = orc.crater_profile(rho0.cpu().numpy(), sim.get_density().cpu().numpy())
+    np.testing.assert_allclose(prof, expect, rtol=1e-14, atol=0)
+    assert prof.max() > 0.5 * w["dx"]                          # material has left the hot spot
+    m = crater.crater_metrics(prof, w["dx"])
+    depth, width = oracle.crater_width(expect, w["dx"])
+    assert m["depth"] == pytest.approx(depth, rel=1e-14)
+    assert m["width"] == pytest.approx(width, rel=1e-9)
+    assert 0 < m["width"] < w["nx"] * w["dx"]
+    mf = crater.crater_metrics(prof, w["dx"], far_field=True)
+    assert mf["level"] == pytest.approx(oracle.far_field(expect), rel=1e-12)
+    assert mf["width"] == pytest.approx(oracle.crater_width(expect - oracle.far_field(expect), w["dx"])[1], rel=1e-9)
+    f_th = crater.threshold_fluence(2.0, m["width"], 2 * w["spot_w"])
+    assert f_th == pytest.approx(2.0 * math.exp(-(width / (2 * w["spot_w"])) ** 2), rel=1e-9)
+    sim.close()
+
+
+def test_crater_profile_3d_counts_removed_material(gb):
+    """3D: removing the atoms of the top h cell rows of an m_x x m_y block of columns leaves
+    h m_x m_y cells of solid material missing; the (ny, nx) profile sums to h m_x m_y dx."""
+    w = dict(workload("tiny"), dims=3, nx=16, ny=12, nz=14, slab_k=8, ppc_ion=4, ppc_electron=4, mode=1,
+             ion_charge=0.0, laser_profile=0, tile=4)
+    sim = gb.Simulation(w)
+    rho0, _ = sim.deposit_density()
+    g = {k: v.cpu().numpy() for k, v in sim.get_particles(0).items()}
+    cell = g["cell"].astype(np.int64)
+    i, j, k = cell % 16, (cell // 16) % 12, cell // (16 * 12)
+    h, gone = 2, (i >= 5) & (i < 9) & (j >= 3) & (j < 6) & (k >= w["slab_k"] - 2)
+    keep = ~gone
+    sim.set_particles(0, cell[keep].astype(np.int32), g["fx"][keep], g["fz"][keep], g["ux"][keep], g["uy"][keep],
+                      g["uz"][keep], fy=g["fy"][keep])
+    prof = sim.crater_profile(rho0).cpu().numpy()
+    assert prof.shape == (12, 16)
+    assert prof.sum() == pytest.approx(h * 4 * 3 * w["dx"], rel=1e-12)
+    assert (prof[:, :5] == 0).all() and (prof[:, 10:] == 0).all() and (prof[:3] == 0).all() and (prof[7:] == 0).all()
+    sim.close()

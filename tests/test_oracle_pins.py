@@ -671,5 +671,15 @@ def test_crater_width_closed_forms():
     # wrapped across the periodic seam
     assert crater.crater_metrics(np.roll(prof, -25), dx, t)["width"] == pytest.approx(expect, rel=1e-12)
     assert oracle.crater_width(np.roll(prof, -25), dx, t)[1] == pytest.approx(expect, rel=1e-12)
+    # a uniform loss everywhere (the relaxed slab) plus the pit: measured from the far field the
+    # width is the pit's again, and the far-field level is the uniform loss
+    lifted = prof + 70e-9
+    assert oracle.far_field(lifted) == pytest.approx(70e-9, rel=1e-15)
+    m = crater.crater_metrics(lifted, dx, t, far_field=True)
+    assert m["level"] == pytest.approx(70e-9, rel=1e-15) and m["width"] == pytest.approx(expect, rel=1e-9)
+    assert oracle.crater_width(lifted - oracle.far_field(lifted), dx, t)[1] == pytest.approx(expect, rel=1e-9)
+    # every column above the threshold: the crater spans the periodic width
+    assert oracle.crater_width(np.full(50, D), dx, t)[1] == pytest.approx(50 * dx, rel=1e-15)
+    assert crater.crater_metrics(np.full(50, D), dx, t)["width"] == pytest.approx(50 * dx, rel=1e-15)
     assert crater.threshold_fluence(2.0, 0.0, 1e-6) == 2.0
     assert crater.threshold_fluence(2.0, 1e-6, 1e-6) == pytest.approx(2.0 / math.e, rel=1e-15)
