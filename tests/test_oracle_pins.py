@@ -683,3 +683,31 @@ def test_crater_width_closed_forms():
     assert crater.crater_metrics(np.full(50, D), dx, t)["width"] == pytest.approx(50 * dx, rel=1e-15)
     assert crater.threshold_fluence(2.0, 0.0, 1e-6) == 2.0
     assert crater.threshold_fluence(2.0, 1e-6, 1e-6) == pytest.approx(2.0 / math.e, rel=1e-15)
+
+
+@pytest.mark.parametrize("L", [2.0, 8.0])
+def test_calibration_work_is_the_closed_form(L):
+    """The c_att calibration integrates the pair force on one probe pulled out through a surface.
+    To first order in the gradient (the cells are ~44 r0 wide, so g is small), Eqs. (1)-(3) give
+    F = U''(rbar) rbar drbar/dz, whose integral is [rbar U'(rbar) - U(rbar)] between the densities
+    at the two ends: derived by hand from Eqs. 2-3, it is -D for a slab at n0 pulled to infinity.
+    A tanh surface of width L cells, integrated from 5L below to 5L above: work = G(n_end) -
+    G(n_start) with G(n) = rbar U' - U at rbar = n^(-1/3) r0, to 1e-4 D."""
+    D = 0.41 * 1.602176634e-19
+
+    def G(n):
+        r = n ** (-1.0 / 3.0)
+        return r * D * (-12 * r ** -13 + 12 * r ** -7) - D * (r ** -12 - 2 * r ** -6)
+
+    nz = int(12 * L) + 20
+    w = workload("transport", nx=4, nz=nz, slab_k=nz // 2, ppc_ion=16, D_eV=0.41)
+    o = oracle.Oracle(w, with_particles=False)
+    zs = nz // 2
+    nh = 0.5 * (1 - np.tanh((np.arange(nz + 1) - zs) / L))
+    rho = np.rint(np.outer(nh, np.ones(4)) / o.rho_scale).astype(np.int64)
+    n_at = rho[:, 0] * o.rho_scale
+    a, b = int(zs - 5 * L), int(zs + 5 * L)
+    c_att, w_att, w_rep = oracle.calibrate_c_att(w, rho, a, b)
+    assert w_att + w_rep == pytest.approx(G(n_at[b]) - G(n_at[a]), abs=1e-4 * D)
+    assert G(n_at[b]) - G(n_at[a]) == pytest.approx(-D, rel=2e-3)      # ~ one bond
+    assert c_att == pytest.approx(-(D + w_rep) / w_att, rel=1e-15)
