@@ -166,6 +166,17 @@ PIC_API int pic_crater_profile(pic_ctx* ctx, const int64_t* dev_rho0, double* de
  * device float[3 * num_particles(0)], (Fx, Fy, Fz) per particle, in the context's particle order. */
 PIC_API int pic_pair_force(pic_ctx* ctx, float* dev_out);
 
+/* Pair-potential force (N, per atom) at n probe positions from the current node density, the
+ * probes adding nothing to it (paper: the attractive correction factor is found by integrating the
+ * force on a single atom leaving the target out to infinity). dev_cell, dev_fx, dev_fz: device
+ * arrays of n probes (cell k*nx + i, offsets in [0,1) x [0,1]); pot_mode, c_att, s_rep as in
+ * pic_config, applied to this call only (so one context yields the attractive and the repulsive
+ * parts of the force separately). dev_out: device float[3n], (Fx, 0, Fz). A probe outside the
+ * grid gets NaN. 2D contexts; asynchronous on the context's stream. Errors: PIC_EINVAL (n < 0,
+ * NULL pointers with n > 0, pot_mode not 0 or 1), PIC_ESTATE in 3D. */
+PIC_API int pic_pair_force_at(pic_ctx* ctx, int64_t n, const int32_t* dev_cell, const float* dev_fx,
+                              const float* dev_fz, int32_t pot_mode, double c_att, double s_rep, float* dev_out);
+
 /* Total energies of the current state, FP64 reductions on the device (paper: the pair-potential
  * cycle is energy conserving). Synchronises. host_out: host pointer. */
 PIC_API int pic_energy(pic_ctx* ctx, pic_energy_t* host_out);

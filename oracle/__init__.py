@@ -590,34 +590,36 @@ def crater_width(profile, dx, threshold=None):
     return float(d[c]), float((edge(hi, hi + 1) - edge(lo, lo - 1)) * dx)
 
 
-def calibrate_c_att(phys, rho, k_from, k_to, points=12, s_rep=1.0):
-    """Attractive correction factor from the work done on one probe atom pulled out of the slab
-    whose node sums are rho (paper: the factor is found by integrating the force on a single atom
-    leaving the target out to infinity). Probes on every column x = i + 1/2 cross the cell rows
-    k_from .. k_to - 1; inside each row the column-averaged z force is integrated with a
-    `points`-point Gauss-Legendre rule (the force is smooth inside a cell and jumps at its edges),
-    once for the attractive branch alone and once for the repulsive branch (scaled by s_rep).
-    Removing one atom of the cubic lattice along the normal costs one bond, D, so
-    c_att = -(D + W_rep) / W_att. Returns (c_att, W_att, W_rep)."""
-    nodes, weights = np.polynomial.legendre.leggauss(points)
+def calibrate_c_att(phys, rho, k_from, k_to, points=8, halvings=20):
+    """Attractive correction factor from the work the attractive branch of the pair force does on
+    one probe atom pulled out of the slab whose node sums are rho (paper: the factor is found by
+    integrating the force on a single atom leaving the target out to infinity). Probes on every
+    column x = i + 1/2 cross the cell rows k_from .. k_to - 1. Each row is cut at 1/2, 1/4, ...,
+    2^-halvings from both of its edges and each piece gets a `points`-point Gauss-Legendre rule:
+    where the density tail meets the vacuum, Eq. 2 brings the lower neighbour arbitrarily close,
+    which gives the attraction a narrow spike next to the edge (and makes the repulsion diverge,
+    so the repulsive branch is left out). Removing one atom of the cubic lattice along the normal
+    costs one bond, D, so c_att = -D / W_att. Returns (c_att, W_att)."""
+    t, wt = np.polynomial.legendre.leggauss(points)
+    cuts = [0.0, 1.0]
+    for j in range(1, halvings + 1):
+        cuts += [0.5 ** j, 1.0 - 0.5 ** j]
+    cuts = sorted(set(cuts))
     nx = phys["nx"]
     zs, ws = [], []
     for k in range(k_from, k_to):
-        for t, wgt in zip(nodes, weights):
-            zs.append(k + 0.5 * (1.0 + t))
-            ws.append(0.5 * wgt)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            for ti, wi in zip(t, wt):
+                zs.append(k + a + 0.5 * (b - a) * (ti + 1.0))
+                ws.append(0.5 * (b - a) * wi)
     zs, ws = np.array(zs), np.array(ws)
     px = np.tile(np.arange(nx) + 0.5, zs.size)
     pz = np.repeat(zs, nx)
     zero = np.zeros(px.size)
-
-    def work(c_att, s):
-        o = Oracle(dict(phys, pot_mode=1, c_att=c_att, s_rep=s), with_particles=False)
-        o.set_particles(0, px, pz, zero, zero, zero)
-        o.set_rho(rho)
-        fz = o.pair_force()[:, 2].reshape(zs.size, nx).mean(axis=1)
-        return float(np.dot(fz, ws) * phys["dx"])
-
-    w_att, w_rep = work(1.0, 0.0), work(0.0, s_rep)
+    o = Oracle(dict(phys, pot_mode=1, c_att=1.0, s_rep=0.0), with_particles=False)
+    o.set_particles(0, px, pz, zero, zero, zero)
+    o.set_rho(rho)
+    fz = o.pair_force()[:, 2].reshape(zs.size, nx).mean(axis=1)
+    w_att = float(np.dot(fz, ws) * phys["dx"])
     D = phys["D_eV"] * 1.602176634e-19
-    return -(D + w_rep) / w_att, w_att, w_rep
+    return -D / w_att, w_att

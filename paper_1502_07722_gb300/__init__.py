@@ -75,6 +75,7 @@ _SIGNATURES = {
     "pic_deposit_density": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "pic_pair_force": (ctypes.c_int, [_VP, _VP]),
     "pic_crater_profile": (ctypes.c_int, [_VP, _VP, _VP]),
+    "pic_pair_force_at": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _I32, ctypes.c_double, ctypes.c_double, _VP]),
     "pic_energy": (ctypes.c_int, [_VP, ctypes.POINTER(pic_energy_t)]),
     "pic_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pic_info)]),
     "pic_get_particles": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I32]),
@@ -182,6 +183,12 @@ def pic_pair_force(h, dev_out_ptr: int):
 
 def pic_crater_profile(h, dev_rho0_ptr: int, dev_out_ptr: int):
     _check(load_library().pic_crater_profile(h, dev_rho0_ptr, dev_out_ptr), "pic_crater_profile")
+
+
+def pic_pair_force_at(h, n: int, cell_ptr: int, fx_ptr: int, fz_ptr: int, pot_mode: int, c_att: float, s_rep: float,
+                      out_ptr: int):
+    _check(load_library().pic_pair_force_at(h, int(n), cell_ptr, fx_ptr, fz_ptr, int(pot_mode), float(c_att),
+                                            float(s_rep), out_ptr), "pic_pair_force_at")
 
 
 def pic_energy(h) -> dict:
@@ -387,6 +394,22 @@ class Simulation:
         out = self.torch.empty((self.ny, self.nx) if self.dims == 3 else (self.nx,), dtype=self.torch.float64,
                                device="cuda")
         pic_crater_profile(self.h, rho0.data_ptr(), out.data_ptr())
+        return out
+
+    def pair_force_at(self, cell, fx, fz, pot_mode=None, c_att=None, s_rep=None):
+        """Pair force (N) at probe positions (cell index, offsets) from the current node density;
+        the probes add nothing to it. pot_mode / c_att / s_rep default to the configuration's."""
+        t = self.torch
+        cell = t.as_tensor(cell, dtype=t.int32).cuda().contiguous()
+        fx = t.as_tensor(fx, dtype=t.float32).cuda().contiguous()
+        fz = t.as_tensor(fz, dtype=t.float32).cuda().contiguous()
+        out = t.empty((cell.numel(), 3), dtype=t.float32, device="cuda")
+        self.stream.synchronize()
+        pic_pair_force_at(self.h, cell.numel(), cell.data_ptr(), fx.data_ptr(), fz.data_ptr(),
+                          self.cfg.pot_mode if pot_mode is None else pot_mode,
+                          self.cfg.c_att if c_att is None else c_att, self.cfg.s_rep if s_rep is None else s_rep,
+                          out.data_ptr())
+        self.stream.synchronize()
         return out
 
     def pair_force(self):

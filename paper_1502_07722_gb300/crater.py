@@ -91,7 +91,57 @@ if __name__ == "__main__":
     ap.add_argument("--every", type=int, default=10000)
     ap.add_argument("--fluence", type=float, default=None, help="J/cm^2 the start stands for (Eq. 5)")
     ap.add_argument("--beam-diameter", type=float, default=None, help="m (Eq. 5)")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="run the altered potential with c_att calibrated on the initial slab")
     a = ap.parse_args()
     w = workload(a.workload)
+    if a.calibrate:
+        from . import Simulation
+        probe = Simulation(w)
+        cal = calibrate_c_att(probe)
+        probe.close()
+        print(json.dumps({"calibration": cal}), flush=True)
+        w = dict(w, pot_mode=1, c_att=cal["c_att"], s_rep=1.0)
     for m in run_crater(w, a.steps or w["steps"], a.every, a.fluence, a.beam_diameter):
         print(json.dumps(m), flush=True)
+
+
+def _cell_rule(order: int, levels: int):
+    """Quadrature nodes and weights on [0, 1]: `order`-point Gauss-Legendre on subintervals that
+    halve towards both ends (breakpoints 2^-j and 1 - 2^-j, j = 1..levels), so that features
+    next to a cell edge are resolved."""
+    t, wt = np.polynomial.legendre.leggauss(order)
+    b = sorted({0.0, 1.0, *[2.0 ** -j for j in range(1, levels + 1)], *[1.0 - 2.0 ** -j for j in range(1, levels + 1)]})
+    nodes, weights = [], []
+    for a, c in zip(b[:-1], b[1:]):
+        nodes.append(a + 0.5 * (c - a) * (t + 1.0))
+        weights.append(0.5 * (c - a) * wt)
+    return np.concatenate(nodes), np.concatenate(weights)
+
+
+def calibrate_c_att(sim, z_from: int = None, z_to: int = None, order: int = 8, levels: int = 20) -> dict:
+    """Attractive correction factor of the altered potential (paper: a multiplicative factor on the
+    attractive force, found by integrating the force on a single atom that leaves the target and
+    travels out to infinity). Probes cross the surface of the context's current slab along z on
+    every column (x = i + 1/2), cell row by cell row from z_from to z_to (default slab_k - 1 to
+    slab_k + 2, where the density has fallen to zero); the lateral mean of the z force of the
+    attractive branch alone (c_att = 1, no repulsion) is integrated over each cell with
+    `_cell_rule`. Where the density tail meets the vacuum, Eq. 2 puts the lower neighbour at
+    rbar / (1 + g/2) -> 0: the attraction has a narrow spike there (resolved by the halving
+    subintervals) and the repulsion diverges (not integrable, so it takes no part). Taking one atom
+    out of the model's cubic lattice along the normal costs one bond, D (the first-order force of
+    Eq. 2 integrates to exactly -D across a smooth surface), so c_att = -D / W_att."""
+    nx, slab_k, dx = sim.nx, sim.cfg.slab_k, sim.cfg.dx
+    k0 = slab_k - 1 if z_from is None else int(z_from)
+    k1 = slab_k + 2 if z_to is None else int(z_to)
+    f_in, w_in = _cell_rule(order, levels)
+    rows = np.arange(k0, k1)
+    K, J, I = np.meshgrid(rows, np.arange(f_in.size), np.arange(nx), indexing="ij")
+    cell = (K * nx + I).astype(np.int32).ravel()
+    fx = np.full(cell.size, 0.5, np.float32)
+    fz = f_in[J].astype(np.float32).ravel()
+    f = sim.pair_force_at(cell, fx, fz, pot_mode=1, c_att=1.0, s_rep=0.0)[:, 2].cpu().numpy()
+    fm = f.astype(np.float64).reshape(rows.size, f_in.size, nx).mean(axis=2)
+    w_att = float((fm * w_in).sum() * dx)
+    D = sim.cfg.D_eV * 1.602176634e-19
+    return {"c_att": -D / w_att, "W_att": w_att, "D": D}

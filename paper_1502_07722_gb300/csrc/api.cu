@@ -451,6 +451,19 @@ int pic_deposit_density(pic_ctx* h, int64_t* dev_out, double* scale_out)
     return PIC_OK;
 }
 
+int pic_pair_force_at(pic_ctx* h, int64_t n, const int32_t* dev_cell, const float* dev_fx, const float* dev_fz,
+                      int32_t pot_mode, double c_att, double s_rep, float* dev_out)
+{
+    if (!h || n < 0 || (n > 0 && (!dev_cell || !dev_fx || !dev_fz || !dev_out))) return PIC_EINVAL;
+    if (pot_mode != 0 && pot_mode != 1) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (c.dims == 3) return PIC_ESTATE;
+    if (c.sticky) return c.sticky;
+    launch_pair_force_probe(c, n, dev_cell, dev_fx, dev_fz, pot_mode, c_att, s_rep, dev_out, c.stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
 int pic_crater_profile(pic_ctx* h, const int64_t* dev_rho0, double* dev_out)
 {
     if (!h || !dev_rho0 || !dev_out) return PIC_EINVAL;

@@ -40,6 +40,32 @@ __global__ void k_pair_force(const int32_t* __restrict__ cell, const float* __re
     }
 }
 
+// Pair force at probe positions that add nothing to the density (the calibration of the attractive
+// factor follows one atom out of the target). A probe outside the grid or with an offset outside
+// [0, 1) x [0, 1] reads nothing and gets NaN.
+__global__ void k_pair_force_probe(const int32_t* __restrict__ cell, const float* __restrict__ fx,
+                                   const float* __restrict__ fz, int64_t n, int nx, int nz,
+                                   const u64* __restrict__ rho, float rho_s, float h_coef, int pot_mode,
+                                   float c_att, float s_rep, float f_unit, float* __restrict__ out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int c = cell[p];
+        const float a = fx[p], b = fz[p];
+        if (c < 0 || c >= nx * nz || !(a >= 0.0f && a < 1.0f && b >= 0.0f && b <= 1.0f)) {
+            out[3 * p + 0] = out[3 * p + 1] = out[3 * p + 2] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const int k = c / nx, i = c - k * nx;
+        float dens, dnx, dnz;
+        gather_density(rho, nx, nz, rho_s, i, k, a, b, dens, dnx, dnz);
+        float Fx, Fz;
+        pair_force_xz<true>(dens, dnx, dnz, h_coef, pot_mode, c_att, s_rep, Fx, Fz);
+        out[3 * p + 0] = f_unit * Fx;
+        out[3 * p + 1] = 0.0f;
+        out[3 * p + 2] = f_unit * Fz;
+    }
+}
+
 // Flags particles outside the grid or with offsets outside [0,1) x [0,1] (bit 0 of *bad).
 __global__ void k_validate(const int32_t* __restrict__ cell, const float* __restrict__ fx,
                            const float* __restrict__ fy, const float* __restrict__ fz, int64_t n, int64_t ncell,
@@ -74,6 +100,15 @@ void launch_validate(Ctx& c, const SpeciesBuf& b, int64_t n, unsigned* bad, cuda
     if (n == 0) return;
     k_validate<<<grid_for(c, n), 256, 0, st>>>(b.cell, b.fx, c.dims == 3 ? b.fy : nullptr, b.fz, n,
                                                (int64_t)c.nx * c.ny * c.nz, bad);
+}
+
+void launch_pair_force_probe(Ctx& c, int64_t n, const int32_t* cell, const float* fx, const float* fz, int pot_mode,
+                             double c_att, double s_rep, float* out, cudaStream_t st)
+{
+    if (n == 0) return;
+    k_pair_force_probe<<<grid_for(c, n), 256, 0, st>>>(cell, fx, fz, n, c.nx, c.nz, c.rho[c.cur], (float)c.rho_scale,
+                                                      (float)(c.r0 / (6.0 * c.cfg.dx)), pot_mode, (float)c_att,
+                                                      (float)s_rep, (float)(c.D / c.r0), out);
 }
 
 void launch_pair_force(Ctx& c, float* out, cudaStream_t st)

@@ -59,6 +59,9 @@ __device__ __forceinline__ float branch(int pot_mode, float c_att, float s_rep, 
 // With both neighbours finite and on the same branch the difference is evaluated without
 // cancellation: (1-h)^p - (1+h)^p = -2 P_p(h), P_p the odd part of (1+h)^p, so
 //   F = 24 [ c n^4 P13(h) - c n^2 P7(h) ].
+// ZERO_SKIP: a branch whose factor is 0 contributes nothing even where U' overflows FP32 (a
+// neighbour pulled arbitrarily close at the vacuum edge); the probe calls of the calibration use it.
+template <bool ZERO_SKIP = false>
 __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float dn, float h_coef,
                                            int pot_mode, float c_att, float s_rep)
 {
@@ -74,11 +77,18 @@ __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float 
             float n2 = n * n;
             return fp * 24.0f * c * n2 * (n2 * p13 - p7);
         }
+        if (ZERO_SKIP) return (fp != 0.0f ? fp * lj_dU_inv(ip) : 0.0f) - (fm != 0.0f ? fm * lj_dU_inv(im) : 0.0f);
         return fp * lj_dU_inv(ip) - fm * lj_dU_inv(im);
     }
     float f = 0.0f;
-    if (ip > 0.0f) f += branch(pot_mode, c_att, s_rep, ip) * lj_dU_inv(ip);
-    if (im > 0.0f) f -= branch(pot_mode, c_att, s_rep, im) * lj_dU_inv(im);
+    if (ip > 0.0f) {
+        const float fp = branch(pot_mode, c_att, s_rep, ip);
+        if (!ZERO_SKIP || fp != 0.0f) f += fp * lj_dU_inv(ip);
+    }
+    if (im > 0.0f) {
+        const float fm = branch(pot_mode, c_att, s_rep, im);
+        if (!ZERO_SKIP || fm != 0.0f) f -= fm * lj_dU_inv(im);
+    }
     return f;
 }
 
@@ -202,6 +212,7 @@ namespace gbpic {
 
 // Pair-potential half kick components (units D / r0) along x and z at local density n (units
 // n0) with gradient (dnx, dnz) per cell: Eqs. (1)-(3) via pair_axis.
+template <bool ZERO_SKIP = false>
 __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, float h_coef, int pot_mode, float c_att,
                                               float s_rep, float& fx, float& fz)
 {
@@ -210,8 +221,8 @@ __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, flo
     if (n > 0.0f) {
         const float c = fast_cbrt(n);
         const float inv43 = fast_rcp(n * c);
-        fx = pair_axis(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
-        fz = pair_axis(n, c, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
+        fx = pair_axis<ZERO_SKIP>(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
+        fz = pair_axis<ZERO_SKIP>(n, c, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
     }
 }
 
