@@ -128,6 +128,8 @@ def lib():
             "oracle_maxwell_cont_T": (None, [vp, _D, _D, ctypes.c_int64, _D]),
             "oracle_r0": (ctypes.c_double, [vp]),
             "oracle_crater_profile": (None, [vp, _I64, _I64, _D]),
+            "oracle_cell_temperature": (None, [vp, ctypes.c_int32, _D]),
+            "oracle_set_temperature": (None, [vp, ctypes.c_int32, _D, ctypes.c_double]),
             "oracle3_create": (vp, [ctypes.POINTER(OracleConfig3), ctypes.c_int32]),
             "oracle3_free": (None, [vp]),
             "oracle3_num_particles": (ctypes.c_int64, [vp, ctypes.c_int32]),
@@ -252,6 +254,18 @@ class Oracle:
     def set_rho(self, a):
         a = np.ascontiguousarray(a, np.int64).reshape(-1)
         lib().oracle_set_rho(self._s, _p(a, ctypes.c_int64))
+
+    def cell_temperature(self, sp):
+        """Kinetic temperature (K) of species sp per cell about the cell's mean flow, (nz, nx)."""
+        out = np.empty(self.nx * self.nz, np.float64)
+        lib().oracle_cell_temperature(self._s, sp, _p(out, ctypes.c_double))
+        return out.reshape(self.nz, self.nx)
+
+    def set_temperature(self, sp, T, T_from):
+        """Scale species sp's momenta by sqrt(T_cell / T_from), T a (nz, nx) map."""
+        t = np.ascontiguousarray(T, np.float64).reshape(-1)
+        assert t.size == self.nx * self.nz
+        lib().oracle_set_temperature(self._s, sp, _p(t, ctypes.c_double), float(T_from))
 
     def crater_profile(self, rho0, rho=None):
         """Material missing from each node column of the original slab (m of solid-density

@@ -704,6 +704,53 @@ static void push_particle(ostate* s, int sp, int64_t p)
     s->ux[sp][p] = u[0]; s->uy[sp][p] = u[1]; s->uz[sp][p] = u[2];
 }
 
+/* Lattice temperature per cell (paper: the transport run starts from the lattice temperature the
+ * laser stage leaves once electrons and lattice have equilibrated): for the N particles of
+ * species sp in cell (i, k), T = m c^2 / (3 k_B) * sum |u - mean u|^2 / (N - 1), u = gamma v / c:
+ * the thermal spread about the cell's mean flow (unbiased over the cell's sample). Cells with
+ * fewer than two particles get 0.
+ * out: nz * nx values, index k * nx + i. */
+void oracle_cell_temperature(const ostate* s, int32_t sp, double* out)
+{
+    const ocfg* c = &s->c;
+    size_t ncell = (size_t)c->nx * (size_t)c->nz;
+    double* acc = calloc(5 * ncell, sizeof(double));
+    for (int64_t p = 0; p < s->np[sp]; p++) {
+        int64_t i = (int64_t)floor(s->x[sp][p]), k = (int64_t)floor(s->z[sp][p]);
+        if (k >= c->nz) k = c->nz - 1;                 /* a particle on the top wall */
+        size_t q = (size_t)k * c->nx + (size_t)imod(i, c->nx);
+        double ux = s->ux[sp][p], uy = s->uy[sp][p], uz = s->uz[sp][p];
+        acc[q] += 1.0;
+        acc[ncell + q] += ux;
+        acc[2 * ncell + q] += uy;
+        acc[3 * ncell + q] += uz;
+        acc[4 * ncell + q] += ux * ux + uy * uy + uz * uz;
+    }
+    double mc2_3k = s->m[sp] * O_C * O_C / (3.0 * O_KB);
+    for (size_t q = 0; q < ncell; q++) {
+        double n = acc[q];
+        if (n < 2.0) { out[q] = 0.0; continue; }
+        double mx = acc[ncell + q] / n, my = acc[2 * ncell + q] / n, mz = acc[3 * ncell + q] / n;
+        out[q] = mc2_3k * (acc[4 * ncell + q] - n * (mx * mx + my * my + mz * mz)) / (n - 1.0);
+    }
+    free(acc);
+}
+
+/* Re-temper species sp to a temperature map: momenta drawn at the uniform temperature T_from become
+ * the same draws at the temperature of their cell (T: nz * nx values): u -> u sqrt(T_cell / T_from). */
+void oracle_set_temperature(ostate* s, int32_t sp, const double* T, double T_from)
+{
+    const ocfg* c = &s->c;
+    for (int64_t p = 0; p < s->np[sp]; p++) {
+        int64_t i = (int64_t)floor(s->x[sp][p]), k = (int64_t)floor(s->z[sp][p]);
+        if (k >= c->nz) k = c->nz - 1;
+        double f = sqrt(T[(size_t)k * c->nx + (size_t)imod(i, c->nx)] / T_from);
+        s->ux[sp][p] *= f;
+        s->uy[sp][p] *= f;
+        s->uz[sp][p] *= f;
+    }
+}
+
 /* Crater profile (paper: after solidification the crater's width and depth are read off the
  * density map): for every node column i, the material missing from the original slab as a
  * thickness of solid-density material (m): dx * sum over node rows k = 0..slab_k of the density

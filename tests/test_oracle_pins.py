@@ -713,3 +713,41 @@ def test_calibration_work_is_the_closed_form(L):
     assert w_att == pytest.approx(G(n_at[b]) - G(n_at[a]), abs=1e-4 * D)
     assert G(n_at[b]) - G(n_at[a]) == pytest.approx(-D, rel=2e-3)      # ~ one bond
     assert c_att == pytest.approx(-D / w_att, rel=1e-15) and c_att == pytest.approx(1.0, abs=3e-3)
+
+
+def test_cell_temperature_of_a_maxwellian_and_its_flow():
+    """Lattice temperature per cell (thermal spread about the cell's mean flow, unbiased): a uniform
+    5000 K start is read back as 5000 K (400 atoms per cell: one cell's estimate spreads by
+    sqrt(2/1197) = 4.1 %, the mean over 72 cells by 0.48 %; bounds 1.5 % and 25 %); a common drift
+    of several thermal speeds leaves it unchanged; a cell with a single atom reads 0."""
+    w = workload("transport", nx=12, nz=10, slab_k=6, ppc_ion=400, T_ion_K=5000.0)
+    o = oracle.Oracle(w)
+    T = o.cell_temperature(0)
+    slab = T[:6]
+    assert slab.mean() == pytest.approx(5000.0, rel=1.5e-2)
+    assert (np.abs(slab / 5000.0 - 1) < 0.25).all() and (T[6:] == 0).all()
+    p = o.get_particles(0)
+    u_th = math.sqrt(1.380649e-23 * 5000.0 / (w["ion_mass_amu"] * 1.66053906660e-27)) / 299792458.0
+    o.set_particles(0, p["x"], p["z"], p["ux"] + 3 * u_th, p["uy"] - 2 * u_th, p["uz"])
+    np.testing.assert_allclose(o.cell_temperature(0)[:6], slab, rtol=1e-9)
+    o.set_particles(0, p["x"][:1], p["z"][:1], p["ux"][:1], p["uy"][:1], p["uz"][:1])
+    assert (o.cell_temperature(0) == 0).all()
+
+
+def test_set_temperature_scales_the_draws():
+    """Re-tempering to a map: momenta drawn at T_from become the same normal draws at the cell's
+    temperature, so every cell's temperature scales by exactly T_cell / T_from (each momentum by
+    the square root)."""
+    w = workload("transport", nx=10, nz=8, slab_k=5, ppc_ion=50, T_ion_K=300.0)
+    o = oracle.Oracle(w)
+    before = o.cell_temperature(0)
+    u0 = o.get_particles(0)["ux"]
+    Tmap = np.full((8, 10), 300.0)
+    Tmap[:, 5:] = 1200.0
+    o.set_temperature(0, Tmap, 300.0)
+    after = o.cell_temperature(0)
+    np.testing.assert_allclose(after[:5, :5], before[:5, :5], rtol=1e-12)
+    np.testing.assert_allclose(after[:5, 5:], 4.0 * before[:5, 5:], rtol=1e-12)
+    p = o.get_particles(0)
+    hot = np.floor(p["x"]) >= 5
+    np.testing.assert_allclose(p["ux"][hot], 2.0 * u0[hot], rtol=1e-15)
