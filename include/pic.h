@@ -161,6 +161,24 @@ PIC_API int pic_deposit_density(pic_ctx* ctx, int64_t* dev_out, double* scale_ou
  * asynchronous on the context's stream. Errors: PIC_EINVAL for NULL pointers. */
 PIC_API int pic_crater_profile(pic_ctx* ctx, const int64_t* dev_rho0, double* dev_out);
 
+/* Lattice temperature per cell of one species (paper: the transport run starts from the lattice
+ * temperature the laser-interaction run leaves once electrons and lattice have equilibrated):
+ * for the N particles of `species` in a cell, T = m c^2 / (3 k_B) * sum |u - mean u|^2 / (N - 1)
+ * in K (u = gamma v / c; the spread about the cell's mean flow); cells with fewer than two
+ * particles get 0. dev_T: double[ncell], ncell = nz*nx (2D, index k*nx + i) or nz*ny*nx (3D,
+ * (k*ny + j)*nx + i); dev_work: caller-owned scratch of 5*ncell doubles. FP64 per-cell sums by
+ * atomics (the last bits depend on their order). Asynchronous on the context's stream.
+ * Errors: PIC_EINVAL (NULL pointers, species not present). */
+PIC_API int pic_cell_temperature(pic_ctx* ctx, int32_t species, double* dev_work, double* dev_T);
+
+/* Re-temper one species to a temperature map: momenta drawn at the uniform temperature T_from (K)
+ * become the same draws at the temperature of their cell, u -> u sqrt(T_cell / T_from), taken in
+ * FP64 and rounded to FP32 (the two-stage coupling: a transport context started at T_from takes
+ * the lattice temperature of a laser-stage context). dev_T: double[ncell] as for
+ * pic_cell_temperature, every value >= 0. Asynchronous on the context's stream.
+ * Errors: PIC_EINVAL (NULL pointer, species not present, T_from <= 0). */
+PIC_API int pic_set_temperature(pic_ctx* ctx, int32_t species, const double* dev_T, double T_from);
+
 /* Pair-potential force (N, per atom) on every macro-ion from the current node density
  * (paper: Eqs. 1-3, density and gradient interpolated back to the particle). dev_out:
  * device float[3 * num_particles(0)], (Fx, Fy, Fz) per particle, in the context's particle order. */

@@ -10,6 +10,8 @@ There is no CPU fallback: if the library is missing or no GPU is present, calls 
 from __future__ import annotations
 
 import ctypes
+
+import numpy as np
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -75,6 +77,8 @@ _SIGNATURES = {
     "pic_deposit_density": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "pic_pair_force": (ctypes.c_int, [_VP, _VP]),
     "pic_crater_profile": (ctypes.c_int, [_VP, _VP, _VP]),
+    "pic_cell_temperature": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
+    "pic_set_temperature": (ctypes.c_int, [_VP, _I32, _VP, ctypes.c_double]),
     "pic_pair_force_at": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _I32, ctypes.c_double, ctypes.c_double, _VP]),
     "pic_energy": (ctypes.c_int, [_VP, ctypes.POINTER(pic_energy_t)]),
     "pic_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pic_info)]),
@@ -189,6 +193,14 @@ def pic_pair_force_at(h, n: int, cell_ptr: int, fx_ptr: int, fz_ptr: int, pot_mo
                       out_ptr: int):
     _check(load_library().pic_pair_force_at(h, int(n), cell_ptr, fx_ptr, fz_ptr, int(pot_mode), float(c_att),
                                             float(s_rep), out_ptr), "pic_pair_force_at")
+
+
+def pic_cell_temperature(h, species: int, dev_work_ptr: int, dev_T_ptr: int):
+    _check(load_library().pic_cell_temperature(h, int(species), dev_work_ptr, dev_T_ptr), "pic_cell_temperature")
+
+
+def pic_set_temperature(h, species: int, dev_T_ptr: int, T_from: float):
+    _check(load_library().pic_set_temperature(h, int(species), dev_T_ptr, float(T_from)), "pic_set_temperature")
 
 
 def pic_energy(h) -> dict:
@@ -387,6 +399,28 @@ class Simulation:
         out = self._grid(self.torch.int64)
         scale = pic_deposit_density(self.h, out.data_ptr())
         return out, scale
+
+    def _cells(self):
+        return (self.nz, self.ny, self.nx) if self.dims == 3 else (self.nz, self.nx)
+
+    def cell_temperature(self, species):
+        """Lattice temperature (K) of a species per cell, about each cell's mean flow."""
+        t = self.torch
+        shape = self._cells()
+        work = t.empty(5 * int(np.prod(shape)), dtype=t.float64, device="cuda")
+        out = t.empty(shape, dtype=t.float64, device="cuda")
+        pic_cell_temperature(self.h, species, work.data_ptr(), out.data_ptr())
+        self.stream.synchronize()
+        return out
+
+    def set_temperature(self, species, T, T_from):
+        """Scale a species' momenta (drawn at T_from) to the per-cell temperatures T (K)."""
+        t = self.torch
+        T = t.as_tensor(T, dtype=t.float64).cuda().contiguous()
+        assert tuple(T.shape) == self._cells()
+        self.stream.synchronize()
+        pic_set_temperature(self.h, species, T.data_ptr(), T_from)
+        self.stream.synchronize()
 
     def crater_profile(self, rho0):
         """Material missing from each column of the original slab (m of solid-density material)

@@ -145,3 +145,20 @@ def calibrate_c_att(sim, z_from: int = None, z_to: int = None, order: int = 8, l
     w_att = float((fm * w_in).sum() * dx)
     D = sim.cfg.D_eV * 1.602176634e-19
     return {"c_att": -D / w_att, "W_att": w_att, "D": D}
+
+
+def transport_from_laser(laser, transport_phys: dict):
+    """Second stage of the two-stage run (paper: the atomic-transport run starts from the lattice
+    temperature the laser-interaction run leaves): a transport context on the same grid whose
+    atoms, drawn at the transport start temperature T_ion_K, are re-tempered to the ion temperature
+    of `laser` cell by cell (cells the laser stage leaves colder or without ions keep T_ion_K)."""
+    import torch
+
+    from . import Simulation
+    assert (laser.nx, laser.nz, laser.dims) == (transport_phys["nx"], transport_phys["nz"],
+                                                 3 if transport_phys.get("dims") == 3 else 2)
+    T_from = float(transport_phys["T_ion_K"])
+    T = torch.clamp(laser.cell_temperature(0), min=T_from)
+    tr = Simulation(transport_phys)
+    tr.set_temperature(0, T, T_from)
+    return tr

@@ -464,6 +464,28 @@ int pic_pair_force_at(pic_ctx* h, int64_t n, const int32_t* dev_cell, const floa
     return PIC_OK;
 }
 
+int pic_cell_temperature(pic_ctx* h, int32_t species, double* dev_work, double* dev_T)
+{
+    if (!h || !dev_work || !dev_T) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (species < 0 || species >= c.nsp) return PIC_EINVAL;
+    if (c.sticky) return c.sticky;
+    launch_cell_temperature(c, species, dev_work, dev_T, c.stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+int pic_set_temperature(pic_ctx* h, int32_t species, const double* dev_T, double T_from)
+{
+    if (!h || !dev_T || !(T_from > 0)) return PIC_EINVAL;
+    Ctx& c = h->c;
+    if (species < 0 || species >= c.nsp) return PIC_EINVAL;
+    if (c.sticky) return c.sticky;
+    launch_set_temperature(c, species, dev_T, T_from, c.stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
 int pic_crater_profile(pic_ctx* h, const int64_t* dev_rho0, double* dev_out)
 {
     if (!h || !dev_rho0 || !dev_out) return PIC_EINVAL;

@@ -136,3 +136,78 @@ def test_c_att_calibration_matches_oracle(gb):
     f = sim.pair_force_at([-1, 0], [0.5, 1.5], [0.5, 0.5]).cpu().numpy()
     assert np.isnan(f).all()
     sim.close()
+
+
+def _laser_stage(gb, steps=120):
+    w = dict(workload("tiny"), nx=48, nz=40, slab_k=20, ppc_ion=12, ppc_electron=12, I0=3e19,
+             t_peak=30 * 2.24072e-17, sort_every=20)
+    sim = gb.Simulation(w)
+    sim.step(steps)
+    return w, sim
+
+
+def _oracle_from(w, parts):
+    """An oracle state holding given particle arrays (one dict per species, in the GPU's layout:
+    cell index and offsets), positions turned into global coordinates."""
+    orc = oracle.Oracle(w, with_particles=False)
+    for sp, g in enumerate(parts):
+        cell = np.asarray(g["cell"], np.int64)
+        x = cell % w["nx"] + np.asarray(g["fx"], np.float64)
+        z = cell // w["nx"] + np.asarray(g["fz"], np.float64)
+        orc.set_particles(sp, x, z, *(np.asarray(g[k], np.float64) for k in ("ux", "uy", "uz")))
+    return orc
+
+
+def _host(sim, sp):
+    return {k: v.cpu().numpy() for k, v in sim.get_particles(sp).items()}
+
+
+def test_cell_temperature_matches_oracle(gb):
+    """Ion and electron temperature maps after 120 laser steps against the oracle's maps of the
+    same particles (FP64 sums on both sides; only their order differs)."""
+    w, sim = _laser_stage(gb)
+    orc = _oracle_from(w, [_host(sim, 0), _host(sim, 1)])
+    for sp in (0, 1):
+        got = sim.cell_temperature(sp).cpu().numpy()
+        exp = orc.cell_temperature(sp)
+        np.testing.assert_allclose(got, exp, rtol=1e-9, atol=1e-12 * exp.max())
+        assert (got[w["slab_k"] + 2:] == 0).all() and (got[:w["slab_k"] - 1] > 0).all()
+    with pytest.raises(gb.PicError) as e:
+        sim.cell_temperature(2)
+    assert e.value.code == gb.PIC_EINVAL
+    sim.close()
+
+
+def test_two_stage_start_matches_oracle(gb):
+    """The transport context takes the laser stage's ion temperature map: the re-tempered momenta
+    equal the oracle's re-tempering of the same draws to the last bit (one FP64 multiply, rounded
+    to FP32), and each cell's temperature scales by its map value over the start temperature."""
+    from paper_1502_07722_gb300 import crater
+    w, las = _laser_stage(gb)
+    tw = dict(workload("transport"), nx=w["nx"], nz=w["nz"], slab_k=w["slab_k"], ppc_ion=12, T_ion_K=300.0)
+    cold = gb.Simulation(tw)
+    before = _host(cold, 0)
+    T_before = cold.cell_temperature(0).cpu().numpy()
+    cold.close()
+    tr = crater.transport_from_laser(las, tw)
+    Tmap = np.maximum(las.cell_temperature(0).cpu().numpy(), 300.0)
+    after = _host(tr, 0)
+    # two contexts order a cell's particles differently (atomic cursors of the sort): match them by
+    # position, which is unique
+    ka = np.lexsort((after["fz"], after["fx"], after["cell"]))
+    kb = np.lexsort((before["fz"], before["fx"], before["cell"]))
+    for k in ("cell", "fx", "fz"):
+        assert np.array_equal(after[k][ka], before[k][kb])
+    orc = _oracle_from(tw, [before])
+    orc.set_temperature(0, Tmap, 300.0)
+    o = orc.get_particles(0)
+    for k in ("ux", "uy", "uz"):
+        assert np.array_equal(after[k][ka], o[k].astype(np.float32)[kb])
+    T_after = tr.cell_temperature(0).cpu().numpy()
+    slab = T_before > 0
+    np.testing.assert_allclose(T_after[slab], T_before[slab] * Tmap[slab] / 300.0, rtol=2e-6)
+    with pytest.raises(gb.PicError) as e:
+        tr.set_temperature(0, Tmap, 0.0)
+    assert e.value.code == gb.PIC_EINVAL
+    tr.close()
+    las.close()
