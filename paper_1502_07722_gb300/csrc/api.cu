@@ -408,9 +408,14 @@ int pic_step(pic_ctx* h, int32_t nsteps)
             int r = sort_all(h);
             if (r) return r;
         }
-        for (int q = 0; q < 3; q++) CK(cudaMemsetAsync(c.J[q], 0, 8 * c.nn, c.stream));
-        // the next node density starts from the current one; the particle kernel adds the changes
-        CK(cudaMemcpyAsync(c.rho[1 - c.cur], c.rho[c.cur], 8 * c.nn, cudaMemcpyDeviceToDevice, c.stream));
+        {
+            // clear the currents; the next node density starts from the current one (the particle
+            // kernel adds the changes)
+            const CopySeg prep[4] = {{nullptr, c.J[0], 8 * c.nn}, {nullptr, c.J[1], 8 * c.nn},
+                                     {nullptr, c.J[2], 8 * c.nn}, {c.rho[c.cur], c.rho[1 - c.cur], 8 * c.nn}};
+            c.nlaunch[3] += launch_copy_segments(c, prep, 4, c.stream);
+            CK(cudaGetLastError());
+        }
         int r = ev_begin(h, 0);
         if (r) return r;
         if (c.dims == 3) launch_particle_step3(c, c.stream);
@@ -712,8 +717,14 @@ int ckpt_copy(pic_ctx* h, char* buf, bool save, bool on_host)
     Ctx& c = h->c;
     size_t osp[2], otl[2], of, orho, oj;
     ckpt_layout(c, osp, otl, &of, &orho, &oj);
-    const cudaMemcpyKind k = !on_host ? cudaMemcpyDeviceToDevice : (save ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    const cudaMemcpyKind k = save ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+    // device buffers: all segments in one vectorised copy kernel; host buffers: one copy each
+    std::vector<CopySeg> segs;
     auto cp = [&](void* dev, size_t off, size_t bytes) -> cudaError_t {
+        if (!on_host) {
+            segs.push_back(save ? CopySeg{dev, buf + off, bytes} : CopySeg{buf + off, dev, bytes});
+            return cudaSuccess;
+        }
         return save ? cudaMemcpyAsync(buf + off, dev, bytes, k, c.stream) : cudaMemcpyAsync(dev, buf + off, bytes, k, c.stream);
     };
     for (int s = 0; s < c.nsp; s++) {
@@ -729,6 +740,10 @@ int ckpt_copy(pic_ctx* h, char* buf, bool save, bool on_host)
     CK(cp(c.rho[c.cur], orho, 8 * c.nn));
     for (int q = 0; q < 3; q++) CK(cp(c.J[q], oj + q * align256(8 * c.nn), 8 * c.nn));
     CK(cp(c.red_out + 5, oj + 3 * align256(8 * c.nn), sizeof(double)));
+    if (!on_host) {
+        launch_copy_segments(c, segs.data(), (int)segs.size(), c.stream);
+        CK(cudaGetLastError());
+    }
     return PIC_OK;
 }
 

@@ -141,6 +141,16 @@ void launch_init_particles(Ctx& c, int s, cudaStream_t st);
 void launch_sort_species(Ctx& c, int s, cudaStream_t st, int64_t* launches);
 void launch_deposit_density(Ctx& c, u64* out, cudaStream_t st);
 void launch_crater_profile(Ctx& c, const u64* rho0, double depth_scale, double* out, cudaStream_t st);
+// One device-to-device copy (src != NULL) or clear (src == NULL) of `bytes` bytes.
+struct CopySeg {
+    const void* src;
+    void* dst;
+    size_t bytes;
+};
+constexpr int kMaxCopySegs = 32;
+// copies / clears a list of segments with a vectorised kernel (one launch per 32 segments); returns
+// the number of launches
+int launch_copy_segments(const Ctx& c, const CopySeg* segs, int n, cudaStream_t st);
 void launch_cell_temperature(Ctx& c, int s, double* work, double* T, cudaStream_t st);
 void launch_set_temperature(Ctx& c, int s, const double* T, double T_from, cudaStream_t st);
 void launch_pair_force_probe(Ctx& c, int64_t n, const int32_t* cell, const float* fx, const float* fz, int pot_mode,
