@@ -82,6 +82,15 @@ struct DensAt {
     int i, i1, k;
 };
 
+// int64 -> FP32 through two 32-bit conversions: the 64-bit conversion runs on GB300's slow FP64 pipe
+// (9 per particle here); the result differs from the correctly rounded one by at most one rounding
+__device__ __forceinline__ float i64f(long long v)
+{
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)v;
+    return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
+
 __device__ __forceinline__ long long node_sum(const u64* rho, int nx, int nz, int i, int k)
 {
     const long long v = (long long)rho[(size_t)k * nx + i];
@@ -100,13 +109,13 @@ __device__ __forceinline__ DensAt dens_at(const u64* rho, float rho_s, int nx, i
     d.fz = fz;
     const long long N00 = node_sum(rho, nx, nz, d.i, ck), N10 = node_sum(rho, nx, nz, d.i1, ck);
     const long long N01 = node_sum(rho, nx, nz, d.i, ck + 1), N11 = node_sum(rho, nx, nz, d.i1, ck + 1);
-    const float n00 = rho_s * (float)N00, n10 = rho_s * (float)N10, n01 = rho_s * (float)N01, n11 = rho_s * (float)N11;
+    const float n00 = rho_s * i64f(N00), n10 = rho_s * i64f(N10), n01 = rho_s * i64f(N01), n11 = rho_s * i64f(N11);
     d.n = (1 - fx) * (1 - fz) * n00 + fx * (1 - fz) * n10 + (1 - fx) * fz * n01 + fx * fz * n11;
-    const float ex0 = rho_s * (float)(N10 - N00), ex1 = rho_s * (float)(N11 - N01);
-    const float ez0 = rho_s * (float)(N01 - N00), ez1 = rho_s * (float)(N11 - N10);
+    const float ex0 = rho_s * i64f(N10 - N00), ex1 = rho_s * i64f(N11 - N01);
+    const float ez0 = rho_s * i64f(N01 - N00), ez1 = rho_s * i64f(N11 - N10);
     d.qx = (1 - fz) * ex0 + fz * ex1;
     d.qz = (1 - fx) * ez0 + fx * ez1;
-    d.gxz = rho_s * (float)(N11 - N01 - N10 + N00);
+    d.gxz = rho_s * i64f(N11 - N01 - N10 + N00);
     return d;
 }
 
