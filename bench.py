@@ -42,8 +42,10 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # 40 timed steps hold one cell sort (every 40 steps), its share of the job
-    ap.add_argument("--steps", type=int, default=40)
+    # default: the workload's configured run (warm-up + timed steps, capped at 2000 steps), so that
+    # `value` is the whole job's throughput as the run evolves (the laser heats the electrons and
+    # the particle step slows down) and holds its share of the cell sorts; 40 on the CPU oracle
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large2d")
@@ -354,8 +356,18 @@ def run_differentiable(args, world, rank, dist, gb):
         dist.destroy_process_group()
 
 
+def job_steps(name, warmup):
+    """Timed steps of the default job: the workload's configured steps (capped at 2000) after the
+    warm-up steps."""
+    from paper_1502_07722_gb300.workloads import workload
+    total = 1000 if name == "batched" else int(workload(name).get("steps", 40))
+    return max(1, min(total, 2000) - warmup)
+
+
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = 40 if args.impl == "reference" else job_steps(args.workload, args.warmup)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         if world > 1:

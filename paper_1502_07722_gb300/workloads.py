@@ -39,7 +39,7 @@ WORKLOADS = {
                  I0=1e17, w0=0.0, t_peak=100 * DT_2D, seed=1, steps=200),
     # 2048 x 2048 cells, slab depth 1024, 32 + 32 ppc, 2 um focus at 5e13 W/cm^2, 2000 steps
     "large2d": dict(COPPER, nx=2048, nz=2048, slab_k=1024, ppc_ion=32, ppc_electron=32, laser_profile=2,
-                    I0=5e17, w0=2e-6, t_peak=1000 * DT_2D, seed=2, steps=2000),
+                    I0=5e17, w0=2e-6, t_peak=1000 * DT_2D, seed=2, steps=2000, sort_every=160),
     # 1024 x 1024 cells, slab depth 512, 32 + 32 ppc (33.5 M particles, state larger than L2):
     # the same per-cell load as large2d at a quarter of the size, for profiling captures
     "mid2d": dict(COPPER, nx=1024, nz=1024, slab_k=512, ppc_ion=32, ppc_electron=32, laser_profile=2,
