@@ -162,3 +162,28 @@ def transport_from_laser(laser, transport_phys: dict):
     tr = Simulation(transport_phys)
     tr.set_temperature(0, T, T_from)
     return tr
+
+
+def laser_from_transport(transport, laser_phys: dict):
+    """The next shot of a few-shot study (paper: the target structure a transport run leaves, as a
+    density and temperature profile, initialises another laser-interaction run): a laser-stage
+    context on the same grid whose ions are the transport stage's atoms (positions and lattice
+    momenta) and whose electrons sit on the same positions (a neutral start) with the thermal
+    momenta the new context drew for its own electrons. The two stages need the same particle
+    count per species (same slab and ppc)."""
+    import torch
+
+    from . import Simulation
+    las = Simulation(laser_phys)
+    atoms = transport.get_particles(0)
+    n = atoms["cell"].numel()
+    if las.info()["num_particles"][1] != n:
+        las.close()
+        raise ValueError("the laser stage needs as many electrons as the transport stage has atoms")
+    electrons = las.get_particles(1)
+    fy = atoms.get("fy")
+    las.set_particles(0, atoms["cell"], atoms["fx"], atoms["fz"], atoms["ux"], atoms["uy"], atoms["uz"], fy=fy)
+    las.set_particles(1, atoms["cell"], atoms["fx"], atoms["fz"], electrons["ux"], electrons["uy"], electrons["uz"],
+                      fy=fy)
+    torch.cuda.synchronize()
+    return las

@@ -211,3 +211,26 @@ def test_two_stage_start_matches_oracle(gb):
     assert e.value.code == gb.PIC_EINVAL
     tr.close()
     las.close()
+
+
+def test_few_shot_hand_back(gb):
+    """Transport stage -> next laser stage: the laser context's ions are the transport atoms (same
+    positions and momenta, hence the same node density bit for bit), its electrons sit on the same
+    positions (neutral start), and it steps."""
+    from paper_1502_07722_gb300 import crater
+    tw = dict(workload("transport"), nx=40, nz=36, slab_k=18, ppc_ion=8, T_ion_K=3000.0)
+    tr = gb.Simulation(tw)
+    tr.step(30)
+    lw = dict(workload("tiny"), nx=40, nz=36, slab_k=18, ppc_ion=8, ppc_electron=8)
+    las = crater.laser_from_transport(tr, lw)
+    a, ions, el = _host(tr, 0), _host(las, 0), _host(las, 1)
+    ka, ki, ke = (np.lexsort((d["fz"], d["fx"], d["cell"])) for d in (a, ions, el))
+    for k in ("cell", "fx", "fz", "ux", "uy", "uz"):
+        assert np.array_equal(ions[k][ki], a[k][ka]), k
+    for k in ("cell", "fx", "fz"):
+        assert np.array_equal(el[k][ke], a[k][ka]), k
+    assert np.array_equal(las.get_density().cpu().numpy(), tr.get_density().cpu().numpy())
+    las.step(5)
+    assert las.info()["step"] == 5
+    las.close()
+    tr.close()
