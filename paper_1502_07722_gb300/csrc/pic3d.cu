@@ -484,8 +484,8 @@ __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const __grid_constant
             if (s >= a.nsp) break;
             const Species3& S = a.sp[s];
             const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
-            // consecutive threads take consecutive particles: coalesced loads and stores straight
-            // from the records, no block barrier per chunk
+            // consecutive threads take consecutive records (coalesced); the cell sort's block
+            // layout gives a warp's lanes neighbouring cells
             for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock3) {
                 // the record two iterations ahead into L1: its DRAM latency hides behind this particle
                 const int q = p + 2 * kBlock3;
