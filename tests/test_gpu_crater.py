@@ -234,3 +234,35 @@ def test_few_shot_hand_back(gb):
     assert las.info()["step"] == 5
     las.close()
     tr.close()
+
+
+def test_new_entry_points_refuse_bad_arguments(gb):
+    """Argument checks of the transport-stage entry points, before any kernel runs."""
+    w = dict(workload("transport"), nx=16, nz=16, slab_k=8, ppc_ion=4)
+    sim = gb.Simulation(w)
+    out = torch.empty(3, dtype=torch.float32, device="cuda")
+    idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    half = torch.full((1,), 0.5, dtype=torch.float32, device="cuda")
+    cases = [
+        lambda: gb.pic_crater_profile(sim.h, 0, out.data_ptr()),                      # NULL rho0
+        lambda: gb.pic_pair_force_at(sim.h, -1, idx.data_ptr(), half.data_ptr(), half.data_ptr(), 0, 1.0, 1.0,
+                                     out.data_ptr()),                                 # n < 0
+        lambda: gb.pic_pair_force_at(sim.h, 1, idx.data_ptr(), half.data_ptr(), half.data_ptr(), 2, 1.0, 1.0,
+                                     out.data_ptr()),                                 # pot_mode 2
+        lambda: gb.pic_pair_force_at(sim.h, 1, 0, half.data_ptr(), half.data_ptr(), 0, 1.0, 1.0,
+                                     out.data_ptr()),                                 # NULL cells
+        lambda: gb.pic_cell_temperature(sim.h, 0, 0, out.data_ptr()),                  # NULL scratch
+        lambda: gb.pic_set_temperature(sim.h, 1, out.data_ptr(), 300.0),               # no species 1
+    ]
+    for call in cases:
+        with pytest.raises(gb.PicError) as e:
+            call()
+        assert e.value.code == gb.PIC_EINVAL
+    # the context stays usable
+    sim.step(2)
+    sim.close()
+    s3 = gb.Simulation(dict(workload("tiny"), dims=3, nx=8, ny=8, nz=8, slab_k=4, ppc_ion=2, ppc_electron=2, tile=4))
+    with pytest.raises(gb.PicError) as e:
+        gb.pic_pair_force_at(s3.h, 1, idx.data_ptr(), half.data_ptr(), half.data_ptr(), 0, 1.0, 1.0, out.data_ptr())
+    assert e.value.code == gb.PIC_ESTATE
+    s3.close()
