@@ -26,6 +26,8 @@
 //  * the code is specialised per species kind (ion, electron, neutral atom), so no per-particle
 //    branch tests a species property.
 // Integer sums make every result independent of the order of the additions.
+#include <atomic>
+
 #include "pic_device.cuh"
 
 namespace gbpic {
@@ -402,14 +404,17 @@ size_t particle_smem_bytes(int W) { return sizeof(unsigned) * (size_t)7 * W * W;
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
 {
     const size_t shmem = particle_smem_bytes(a.W);
-    static size_t configured = 0;
-    if (shmem > configured) {
+    // the attributes are per device: remember what each device has been given
+    static std::atomic<size_t> configured[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    if (shmem > configured[dev].load()) {
         cudaFuncSetAttribute(k_particles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         cudaFuncSetAttribute(k_particles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         // the largest carve-out, so that several CTAs fit on one SM
         cudaFuncSetAttribute(k_particles<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaFuncSetAttribute(k_particles<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        configured = shmem;
+        configured[dev].store(shmem);
     }
     int grid = a.ntiles;
     const int cap = c.nsm * 4;
@@ -427,13 +432,16 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
     cudaMemcpyToSymbolAsync(c_batch_args, args_dev, sizeof(StepArgs) * nslab, 0, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyToSymbolAsync(c_tile_base, tile_base_dev, sizeof(int) * (nslab + 1), 0, cudaMemcpyDeviceToDevice, st);
     const size_t shmem = particle_smem_bytes(maxW);
-    static size_t configured = 0;
-    if (shmem > configured) {
+    // the attributes are per device: remember what each device has been given
+    static std::atomic<size_t> configured[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    if (shmem > configured[dev].load()) {
         cudaFuncSetAttribute(k_particles_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         cudaFuncSetAttribute(k_particles_batch<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        configured = shmem;
+        configured[dev].store(shmem);
     }
     int grid = total_tiles < nsm * 4 ? total_tiles : nsm * 4;
     if (grid < 1) grid = 1;

@@ -10,6 +10,8 @@
 // block of 256 of a tile's cell-ordered particles column by column as a 32-row matrix, so the
 // lanes of a warp hold particles 8 places apart in the cell order (neighbouring cells). Deposits
 // use global 64-bit reductions, which are native in L2.
+#include <atomic>
+
 #include "pic_device.cuh"
 
 namespace gbpic {
@@ -551,13 +553,16 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     const int W = c.T + 3;
     a.W = (size_t)7 * W * W * W * 4 <= 72 * 1024 ? W : 0;
     const size_t shmem = sizeof(unsigned) * ((size_t)7 * a.W * a.W * a.W);
-    static size_t configured = 0;
-    if (shmem > configured) {
+    // the attributes are per device: remember what each device has been given
+    static std::atomic<size_t> configured[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    if (shmem > configured[dev].load()) {
         cudaFuncSetAttribute(k_particles3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         cudaFuncSetAttribute(k_particles3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         cudaFuncSetAttribute(k_particles3<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaFuncSetAttribute(k_particles3<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        configured = shmem;
+        configured[dev].store(shmem);
     }
     int grid = c.ntiles < c.nsm * 3 ? c.ntiles : c.nsm * 3;
     if (grid < 1) grid = 1;

@@ -148,6 +148,7 @@ struct CopySeg {
     size_t bytes;
 };
 constexpr int kMaxCopySegs = 32;
+constexpr int kMaxDevices = 64;   // per-device launch attributes are tracked up to this device index
 // copies / clears a list of segments with a vectorised kernel (one launch per 32 segments); returns
 // the number of launches
 int launch_copy_segments(const Ctx& c, const CopySeg* segs, int n, cudaStream_t st);
