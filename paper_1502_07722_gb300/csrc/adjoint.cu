@@ -592,8 +592,46 @@ __device__ void cur_T(const FullAdjArgs& a, int ci, int ck, float x0, float z0, 
     g[4] += gby;
 }
 
-__device__ __constant__ float c_stag[6][2] = {{0.5f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.5f},
-                                              {0.0f, 0.5f}, {0.5f, 0.5f}, {0.5f, 0.0f}};
+// two fields with the same stagger pattern through one stencil (index, clamping, weights)
+__device__ __forceinline__ void gather_stag2(const FullAdjArgs& a, int fA, int fB, int ci, int ck, float fx, float fz,
+                                             float sx, float sz, float lvA, float lvB, float& lx, float& lz,
+                                             float& vA, float& vB)
+{
+    const int nx = a.nx, nz = a.nz;
+    float xs = fx - sx, fzz = fz - sz;
+    int i = ci, k = ck;
+    if (xs < 0.0f) { xs += 1.0f; i -= 1; }
+    if (fzz < 0.0f) { fzz += 1.0f; k -= 1; }
+    const int rows = sz > 0.0f ? nz : nz + 1;
+    bool clamped = false;
+    if (k < 0) { k = 0; fzz = 0.0f; clamped = true; }
+    else if (k > rows - 1 || (k == rows - 1 && fzz > 0.0f)) { k = rows - 1; fzz = 0.0f; clamped = true; }
+    if (k >= rows - 1) { k = rows - 2; fzz = 1.0f; }
+    const int i0 = i < 0 ? i + nx : i;
+    const int i1 = i0 + 1 == nx ? 0 : i0 + 1;
+    const size_t r0 = (size_t)k * nx, r1 = r0 + nx;
+    const float w00 = (1 - xs) * (1 - fzz), w10 = xs * (1 - fzz), w01 = (1 - xs) * fzz, w11 = xs * fzz;
+    const size_t nn = (size_t)(nz + 1) * nx;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int f = h ? fB : fA;
+        const float lv = h ? lvB : lvA;
+        const float* A = a.F[f];
+        const float a00 = A[r0 + i0], a10 = A[r0 + i1], a01 = A[r1 + i0], a11 = A[r1 + i1];
+        if (lv != 0.0f) {
+            float* L = a.lF + (size_t)f * nn;
+            atomicAdd(L + r0 + i0, lv * w00);
+            atomicAdd(L + r0 + i1, lv * w10);
+            atomicAdd(L + r1 + i0, lv * w01);
+            atomicAdd(L + r1 + i1, lv * w11);
+            lx += lv * ((1 - fzz) * (a10 - a00) + fzz * (a11 - a01));
+            if (!clamped) lz += lv * ((1 - xs) * (a01 - a00) + xs * (a11 - a10));
+        }
+        const float v = w00 * a00 + w10 * a10 + w01 * a01 + w11 * a11;
+        if (h) vB = v; else vA = v;
+    }
+}
+
 
 __global__ void __launch_bounds__(256, 2) k_adjoint_full(const FullAdjArgs a)
 {
@@ -607,11 +645,10 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_full(const FullAdjArgs a)
         const float fx = a.fx[p], fz = a.fz[p];
         // ---- forward recompute (FP32, positions local to the cell) ----
         float E[3], B[3], dummy = 0.0f;
-#pragma unroll
-        for (int f = 0; f < 6; f++) {
-            const float v = gather_stag(a, f, ci, ck, fx, fz, c_stag[f][0], c_stag[f][1], 0.0f, dummy, dummy);
-            if (f < 3) E[f] = v; else B[f - 3] = v;
-        }
+        gather_stag2(a, 0, 5, ci, ck, fx, fz, 0.5f, 0.0f, 0.0f, 0.0f, dummy, dummy, E[0], B[2]);
+        gather_stag2(a, 2, 3, ci, ck, fx, fz, 0.0f, 0.5f, 0.0f, 0.0f, dummy, dummy, E[2], B[0]);
+        E[1] = gather_stag(a, 1, ci, ck, fx, fz, 0.0f, 0.0f, 0.0f, dummy, dummy);
+        B[1] = gather_stag(a, 4, ci, ck, fx, fz, 0.5f, 0.5f, 0.0f, dummy, dummy);
         DensAt d = {};
         PairD px = {0.0f, 0.0f, 0.0f, 0.0f}, pz = px;
         if (a.pair) {
@@ -699,10 +736,12 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_full(const FullAdjArgs a)
         a.lam_u[3 * p + 1] = lum[1];
         a.lam_u[3 * p + 2] = lum[2];
         // field gathers
-#pragma unroll
-        for (int f = 0; f < 6; f++) {
-            const float lv = f < 3 ? a.eps * la[f] : lB[f - 3];
-            gather_stag(a, f, ci, ck, fx, fz, c_stag[f][0], c_stag[f][1], lv, lx0, lz0);
+        {
+            float t0, t1;
+            gather_stag2(a, 0, 5, ci, ck, fx, fz, 0.5f, 0.0f, a.eps * la[0], lB[2], lx0, lz0, t0, t1);
+            gather_stag2(a, 2, 3, ci, ck, fx, fz, 0.0f, 0.5f, a.eps * la[2], lB[0], lx0, lz0, t0, t1);
+            gather_stag(a, 1, ci, ck, fx, fz, 0.0f, 0.0f, a.eps * la[1], lx0, lz0);
+            gather_stag(a, 4, ci, ck, fx, fz, 0.5f, 0.5f, lB[1], lx0, lz0);
         }
         if (a.pair) pair_T(d, px, pz, a.fk * la[0], a.fk * la[2], a.inv_r0, a.nx, a.lam_nodes, lx0, lz0, gFF, gR);
         a.lam_pos[2 * p] = lx0;
