@@ -70,15 +70,17 @@ __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float 
     float im = c * (1.0f + h);      // r0 / dist to the neighbour on the - side
     if (ip > 0.0f && im > 0.0f) {
         float fp = branch(pot_mode, c_att, s_rep, ip), fm = branch(pot_mode, c_att, s_rep, im);
-        if (fp == fm) {
-            float h2 = h * h;
-            float p7 = h * (7.0f + h2 * (35.0f + h2 * (21.0f + h2)));
-            float p13 = h * (13.0f + h2 * (286.0f + h2 * (1287.0f + h2 * (1716.0f + h2 * (715.0f + h2 * (78.0f + h2))))));
-            float n2 = n * n;
-            return fp * 24.0f * c * n2 * (n2 * p13 - p7);
-        }
-        if (ZERO_SKIP) return (fp != 0.0f ? fp * lj_dU_inv(ip) : 0.0f) - (fm != 0.0f ? fm * lj_dU_inv(im) : 0.0f);
-        return fp * lj_dU_inv(ip) - fm * lj_dU_inv(im);
+        if (ZERO_SKIP && fp != fm)
+            return (fp != 0.0f ? fp * lj_dU_inv(ip) : 0.0f) - (fm != 0.0f ? fm * lj_dU_inv(im) : 0.0f);
+        float h2 = h * h;
+        float p7 = h * (7.0f + h2 * (35.0f + h2 * (21.0f + h2)));
+        float p13 = h * (13.0f + h2 * (286.0f + h2 * (1287.0f + h2 * (1716.0f + h2 * (715.0f + h2 * (78.0f + h2))))));
+        float n2 = n * n;
+        const float d = 24.0f * c * n2 * (n2 * p13 - p7);     // U'(dist+) - U'(dist-), no cancellation
+        if (fp == fm) return fp * d;
+        // the neighbours on different branches of the altered potential:
+        // fp U'(+) - fm U'(-) = fp (U'(+) - U'(-)) + (fp - fm) U'(-), neither term cancelling
+        return fp * d + (fp - fm) * lj_dU_inv(im);
     }
     float f = 0.0f;
     if (ip > 0.0f) {

@@ -280,6 +280,39 @@ def test_pair_force_first_order_closed_form_and_sign():
             assert F[0] > 0                            # beyond the inflection: pulled towards higher density
 
 
+def test_altered_potential_special_cases():
+    """The altered potential (pot_mode 1, reading of the altered-potential paragraph) scales the
+    force of a neighbour inside r0 by s_rep and of one outside by c_att: with both factors 1 it is
+    Eq. (3) bit for bit; on a compressed lattice with a gentle gradient both neighbours sit inside
+    r0 and the force is s_rep times Eq. (3)'s; on a dilute one both sit outside and it is c_att
+    times Eq. (3)'s; the pair energy follows the same factors. Tolerance 1e-11: the factor scales
+    the two neighbours' terms before their difference, which cancels to ~1e-3 of each term."""
+    nz, nx = 16, 16
+    k, i = np.mgrid[0:nz + 1, 0:nx]
+    pts = ([5.3, 9.8, 2.2], [7.6, 3.1, 11.4])
+
+    def force_energy(n_a, slope, **pot):
+        w = workload("tiny", nx=nx, nz=nz, slab_k=nz, laser_profile=0, **pot)
+        o = oracle.Oracle(w, with_particles=False)
+        grid = np.rint((n_a + slope * np.minimum(i, 12)) / o.rho_scale).astype(np.int64)
+        o.set_particles(0, pts[0], pts[1], [0.0] * 3, [0.0] * 3, [0.0] * 3)
+        o.set_rho(grid)
+        return o.pair_force(), o.energy()["pair"]
+
+    for n_a, slope in ((1.25, 2e-3), (0.7, -3e-3), (1.0, 1e-1)):
+        F0, E0 = force_energy(n_a, slope)
+        F1, E1 = force_energy(n_a, slope, pot_mode=1, c_att=1.0, s_rep=1.0)
+        assert np.array_equal(F0, F1) and E0 == E1
+    Fc, Ec = force_energy(1.25, 2e-3)
+    Fs, Es = force_energy(1.25, 2e-3, pot_mode=1, c_att=0.2, s_rep=3.0)     # both neighbours inside r0
+    np.testing.assert_allclose(Fs, 3.0 * Fc, rtol=1e-11)
+    assert Es == pytest.approx(3.0 * Ec, rel=1e-11)
+    Fd, Ed = force_energy(0.7, -3e-3)
+    Fa, Ea = force_energy(0.7, -3e-3, pot_mode=1, c_att=0.45, s_rep=7.0)    # both outside r0
+    np.testing.assert_allclose(Fa, 0.45 * Fd, rtol=1e-11)
+    assert Ea == pytest.approx(0.45 * Ed, rel=1e-11)
+
+
 # ---- Boris push -------------------------------------------------------------------------
 
 def test_boris_gyration_closed_form():
