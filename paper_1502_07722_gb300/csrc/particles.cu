@@ -7,8 +7,9 @@
 //  * one CTA owns one tile of T x T cells at a time (particles are sorted into tiles);
 //  * the CTA stages a window of (T + 2M + 3)^2 nodes in shared memory: the six field
 //    components and the pair density n / n0 in FP32;
-//  * thread t of the CTA takes the tile's records t, t + 256, ... straight from global memory
-//    (coalesced loads and stores, no block barrier). The cell sort stores each block of 1024 of
+//  * thread t of the CTA (128 threads, 8 CTAs per SM) takes the tile's records t, t + 128, ...
+//    straight from global memory (coalesced loads and stores, no block barrier). The cell sort
+//    stores each block of 1024 of
 //    a tile's cell-ordered particles as a 32-row matrix, column by column, so the lanes of a warp
 //    hold particles 32 places apart in the cell order: neighbouring cells, whose deposits go to
 //    distinct nodes that share cache sectors;
@@ -33,7 +34,8 @@
 namespace gbpic {
 
 constexpr int kMargin = 2;              // cells a particle may drift out of its tile between sorts
-constexpr int kBlock = 256;
+constexpr int kBlock = 128;                // threads per CTA (8 CTAs per SM)
+constexpr int kCtasPerSm = 8;
 
 __device__ __forceinline__ int wrap_any(int i, int nx)
 {
@@ -374,7 +376,7 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
 }
 
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock, 4) k_particles(const StepArgs a)
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles(const StepArgs a)
 {
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) run_tile<FULL>(a, t);
 }
@@ -390,7 +392,7 @@ __constant__ int c_tile_base[kMaxBatchSlabs + 1];
 // All simulations of a batch in one persistent launch: the tiles of every simulation form one
 // work list (c_tile_base[s] = first global tile of simulation s).
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock, 4) k_particles_batch(int nslab, int total)
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles_batch(int nslab, int total)
 {
     for (int g = blockIdx.x; g < total; g += gridDim.x) {
         int s = 0;
@@ -417,7 +419,7 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
         configured[dev].store(shmem);
     }
     int grid = a.ntiles;
-    const int cap = c.nsm * 4;
+    const int cap = c.nsm * kCtasPerSm;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     if (a.full) k_particles<true><<<grid, kBlock, shmem, st>>>(a);
@@ -443,7 +445,7 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
         cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         configured[dev].store(shmem);
     }
-    int grid = total_tiles < nsm * 4 ? total_tiles : nsm * 4;
+    int grid = total_tiles < nsm * kCtasPerSm ? total_tiles : nsm * kCtasPerSm;
     if (grid < 1) grid = 1;
     if (full) k_particles_batch<true><<<grid, kBlock, shmem, st>>>(nslab, total_tiles);
     else k_particles_batch<false><<<grid, kBlock, shmem, st>>>(nslab, total_tiles);
