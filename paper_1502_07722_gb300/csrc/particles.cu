@@ -312,9 +312,16 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     }
 }
 
-// One tile of one simulation: stage the window, then advance the tile's particles in storage order.
+// Part `sub` of `nsub` of one tile of one simulation: stage the tile's window, then advance that
+// part of each species' particles of the tile in storage order (tiles holding many particles are
+// split over several CTAs when the tiles are fewer than the CTA slots).
+__device__ __forceinline__ int part_start(int p0, int p1, int sub, int nsub)
+{
+    return p0 + (int)(((long long)(p1 - p0) * sub) / nsub);
+}
+
 template <bool FULL>
-__device__ __forceinline__ void run_tile(const StepArgs& a, int t)
+__device__ __forceinline__ void run_tile(const StepArgs& a, int t, int sub, int nsub)
 {
     extern __shared__ unsigned smem[];
     const int W = a.W, WW = W * W;
@@ -328,7 +335,10 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
         int cnt = 0;
 #pragma unroll
         for (int s = 0; s < 2; s++)
-            if (s < a.nsp) cnt += a.sp[s].tile_start[t + 1] - a.sp[s].tile_start[t];
+            if (s < a.nsp) {
+                const int p0 = a.sp[s].tile_start[t], p1 = a.sp[s].tile_start[t + 1];
+                cnt += part_start(p0, p1, sub + 1, nsub) - part_start(p0, p1, sub, nsub);
+            }
         if (cnt == 0) return;
         const int tx = t % a.ntx, tz = t / a.ntx;
         w.ox = tx * a.T - kMargin - 1;
@@ -357,7 +367,8 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
         for (int s = 0; s < 2; s++) {
             if (s >= a.nsp) break;
             const Species& S = a.sp[s];
-            const int p0 = S.tile_start[t], p1 = S.tile_start[t + 1];
+            const int q0 = S.tile_start[t], q1 = S.tile_start[t + 1];
+            const int p0 = part_start(q0, q1, sub, nsub), p1 = part_start(q0, q1, sub + 1, nsub);
             for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock) {
                 int cell = S.a.cell[p];
                 float fx = S.a.fx[p], fz = S.a.fz[p], ux = S.a.ux[p], uy = S.a.uy[p], uz = S.a.uz[p];
@@ -376,9 +387,9 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t)
 }
 
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles(const StepArgs a)
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles(const StepArgs a, int nsub)
 {
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) run_tile<FULL>(a, t);
+    for (int g = blockIdx.x; g < a.ntiles * nsub; g += gridDim.x) run_tile<FULL>(a, g / nsub, g % nsub, nsub);
 }
 
 // Arguments of the simulations of a batch for the current step, in constant memory: the slab
@@ -392,13 +403,21 @@ __constant__ int c_tile_base[kMaxBatchSlabs + 1];
 // All simulations of a batch in one persistent launch: the tiles of every simulation form one
 // work list (c_tile_base[s] = first global tile of simulation s).
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles_batch(int nslab, int total)
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles_batch(int nslab, int total, int nsub)
 {
-    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    for (int g = blockIdx.x; g < total * nsub; g += gridDim.x) {
+        const int tile = g / nsub;
         int s = 0;
-        while (s + 1 < nslab && c_tile_base[s + 1] <= g) s++;
-        run_tile<FULL>(c_batch_args[s], g - c_tile_base[s]);
+        while (s + 1 < nslab && c_tile_base[s + 1] <= tile) s++;
+        run_tile<FULL>(c_batch_args[s], tile - c_tile_base[s], g % nsub, nsub);
     }
+}
+
+// parts per tile: about four work items per CTA slot (a slab often fills under half of the tiles)
+static int parts_per_tile(int ntiles, int slots)
+{
+    int nsub = (4 * slots + ntiles - 1) / (ntiles > 0 ? ntiles : 1);
+    return nsub < 1 ? 1 : (nsub > 16 ? 16 : nsub);
 }
 
 size_t particle_smem_bytes(int W) { return sizeof(unsigned) * (size_t)7 * W * W; }
@@ -418,12 +437,13 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
         cudaFuncSetAttribute(k_particles<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         configured[dev].store(shmem);
     }
-    int grid = a.ntiles;
     const int cap = c.nsm * kCtasPerSm;
+    const int nsub = parts_per_tile(a.ntiles, cap);
+    int grid = a.ntiles * nsub;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    if (a.full) k_particles<true><<<grid, kBlock, shmem, st>>>(a);
-    else k_particles<false><<<grid, kBlock, shmem, st>>>(a);
+    if (a.full) k_particles<true><<<grid, kBlock, shmem, st>>>(a, nsub);
+    else k_particles<false><<<grid, kBlock, shmem, st>>>(a, nsub);
 }
 
 int max_batch_slabs() { return kMaxBatchSlabs; }
@@ -445,10 +465,12 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
         cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         configured[dev].store(shmem);
     }
-    int grid = total_tiles < nsm * kCtasPerSm ? total_tiles : nsm * kCtasPerSm;
+    const int cap = nsm * kCtasPerSm;
+    const int nsub = parts_per_tile(total_tiles, cap);
+    int grid = total_tiles * nsub < cap ? total_tiles * nsub : cap;
     if (grid < 1) grid = 1;
-    if (full) k_particles_batch<true><<<grid, kBlock, shmem, st>>>(nslab, total_tiles);
-    else k_particles_batch<false><<<grid, kBlock, shmem, st>>>(nslab, total_tiles);
+    if (full) k_particles_batch<true><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
+    else k_particles_batch<false><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
 }
 
 int tile_window(int T) { return T + 2 * kMargin + 3; }
