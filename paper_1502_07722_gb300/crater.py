@@ -132,8 +132,10 @@ def calibrate_c_att(sim, z_from: int = None, z_to: int = None, order: int = 8, l
     out of the model's cubic lattice along the normal costs one bond, D (the first-order force of
     Eq. 2 integrates to exactly -D across a smooth surface), so c_att = -D / W_att."""
     nx, slab_k, dx = sim.nx, sim.cfg.slab_k, sim.cfg.dx
-    k0 = slab_k - 1 if z_from is None else int(z_from)
-    k1 = slab_k + 2 if z_to is None else int(z_to)
+    k0 = max(slab_k - 1, 0) if z_from is None else int(z_from)
+    k1 = min(slab_k + 2, sim.nz) if z_to is None else int(z_to)
+    if not 0 <= k0 < k1 <= sim.nz:
+        raise ValueError("probe rows must lie inside the grid")
     f_in, w_in = _cell_rule(order, levels)
     rows = np.arange(k0, k1)
     K, J, I = np.meshgrid(rows, np.arange(f_in.size), np.arange(nx), indexing="ij")
