@@ -62,6 +62,8 @@ class OracleConfig3(ctypes.Structure):
         ("s_rep", ctypes.c_double), ("lambda_", ctypes.c_double), ("I0", ctypes.c_double),
         ("tau_fwhm", ctypes.c_double), ("w0", ctypes.c_double), ("t_peak", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
     ]
 
 
@@ -566,8 +568,24 @@ def deposit_current3(nx, ny, nz, sign, x0, y0, z0, x1, y1, z1, out=None):
 
 def far_field(profile):
     """Median of the profile over the columns at least a quarter of the period away from the
-    deepest column (the half of the columns farthest from it)."""
+    deepest column (the half of the columns farthest from it). A 3D profile (ny, nx): the distance
+    is the periodic one in the x-y plane, compared squared in whole cells; columns at equal
+    distance stay in row-major order."""
     d = np.asarray(profile, np.float64)
+    if d.ndim == 2:
+        ny, nx = d.shape
+        flat = d.ravel()
+        c = int(np.argmax(flat))
+        cj, ci = c // nx, c % nx
+        away = []
+        for j in range(ny):
+            for i in range(nx):
+                ddx = min((i - ci) % nx, (ci - i) % nx)
+                ddy = min((j - cj) % ny, (cj - j) % ny)
+                away.append((ddx * ddx + ddy * ddy, j * nx + i))
+        away.sort(key=lambda t: t[0])
+        keep = [q for _, q in away[flat.size - flat.size // 2:]]
+        return float(np.median(flat[keep])) if keep else 0.0
     n = d.size
     c = int(np.argmax(d))
     away = [(min((i - c) % n, (c - i) % n), i) for i in range(n)]
@@ -589,19 +607,31 @@ def crater_width(profile, dx, threshold=None):
         return float(d[c]), 0.0
     if np.all(d > th):
         return float(d[c]), float(n * dx)
-    rolled = np.roll(d, n // 2 - c)                 # deepest column in the middle
-    mid = n // 2
-    inside = rolled > th
-    hi = mid
-    while hi + 1 < n and inside[hi + 1]:
+    # walk the periodic line from the deepest column to the first column at or below the
+    # threshold on each side (one exists: not every column is above it)
+    hi = c
+    while d[(hi + 1) % n] > th:
         hi += 1
-    lo = mid
-    while lo - 1 >= 0 and inside[lo - 1]:
+    lo = c
+    while d[(lo - 1) % n] > th:
         lo -= 1
     def edge(j_in, j_out):
-        t = (rolled[j_in] - th) / (rolled[j_in] - rolled[j_out % n])
+        t = (d[j_in % n] - th) / (d[j_in % n] - d[j_out % n])
         return j_in + t * (j_out - j_in)
     return float(d[c]), float((edge(hi, hi + 1) - edge(lo, lo - 1)) * dx)
+
+
+def crater_width_3d(profile, dx, threshold=None):
+    """3D crater (profile (ny, nx), both axes periodic): depth at the deepest column and the widths
+    of the crater along the row and along the column through it, each measured as crater_width
+    does on that line. Returns (depth, width_x, width_y) in metres."""
+    d = np.asarray(profile, np.float64)
+    ny, nx = d.shape
+    c = int(np.argmax(d.ravel()))
+    cj, ci = c // nx, c % nx
+    depth, wx = crater_width(d[cj, :], dx, threshold)
+    _, wy = crater_width(d[:, ci], dx, threshold)
+    return depth, wx, wy
 
 
 def calibrate_c_att(phys, rho, k_from, k_to, points=8, halvings=20):

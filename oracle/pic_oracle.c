@@ -884,6 +884,9 @@ typedef struct {
     double dx, cfl, dt_override, n_atoms, T_ion_K, T_electron_eV, ion_charge, ion_mass_amu;
     double D_eV, r0, c_att, s_rep, lambda, I0, tau_fwhm, w0, t_peak;
     uint64_t seed;
+    int32_t temp_profile;    /* 0: uniform T_ion_K; 1: lattice temperature of a laser spot       */
+    int32_t reserved0;
+    double T_spot_K, spot_w, spot_depth;
 } ocfg3;
 
 typedef struct {
@@ -1177,6 +1180,17 @@ static void redeposit3(ostate3* s)
 
 /* initial slab: cell rows k < slab_k over all (i, j); positions draws 0 (x), 6 (y), 1 (z) */
 /* initial state of the particle in slot q of cell (i, j, k): x, y, z, ux, uy, uz */
+/* The laser-spot lattice temperature of the 2D start (Fig. 2 and the initialisation of the
+   atomic-transport run) around an axis through the middle of the x-y plane: the Gaussian's
+   argument is the squared radius from the axis. */
+static double spot_temperature3(const ocfg3* c, double x, double y, double z)
+{
+    double rx = (x - 0.5 * c->nx) * c->dx / c->spot_w;
+    double ry = (y - 0.5 * c->ny) * c->dx / c->spot_w;
+    double depth = (c->slab_k - z) * c->dx / c->spot_depth;
+    return c->T_ion_K + (c->T_spot_K - c->T_ion_K) * exp(-2.0 * (rx * rx + ry * ry)) * exp(-depth);
+}
+
 static void init_one3(const ostate3* s, int sp, int64_t i, int64_t j, int64_t k, int64_t q, double out[6])
 {
     const ocfg3* c = &s->c;
@@ -1191,9 +1205,12 @@ static void init_one3(const ostate3* s, int sp, int64_t i, int64_t j, int64_t k,
     double a1 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 3));
     double r2 = sqrt(-2.0 * log(draw_open53(draw_bits(c->seed, sp, pid, 4))));
     double a2 = 2.0 * O_PI * draw_unit24(draw_bits(c->seed, sp, pid, 5));
-    out[3] = s->uth[sp] * r1 * cos(a1);
-    out[4] = s->uth[sp] * r1 * sin(a1);
-    out[5] = s->uth[sp] * r2 * cos(a2);
+    double uth = s->uth[sp];
+    if (sp == 0 && c->temp_profile == 1)
+        uth = sqrt(O_KB * spot_temperature3(c, out[0], out[1], out[2]) / (s->m[0] * O_C * O_C));
+    out[3] = uth * r1 * cos(a1);
+    out[4] = uth * r1 * sin(a1);
+    out[5] = uth * r2 * cos(a2);
 }
 
 static void init_particles3(ostate3* s)

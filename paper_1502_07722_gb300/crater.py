@@ -12,33 +12,36 @@ import math
 import numpy as np
 
 
+def _periodic_offsets(n: int, i0: int) -> np.ndarray:
+    """Signed distance (cells) of each index from i0 on a period of n, in [-n/2, n/2)."""
+    return (np.arange(n) - i0 + n // 2) % n - n // 2
+
+
 def far_field_level(profile) -> float:
     """Surface level far from the crater: the median of the profile over the half of the columns
     farthest (periodic distance) from the deepest column. The whole slab of the model relaxes (its
     density settles slightly below the start density, so material leaves the original rows
-    everywhere); the crater is the loss beyond that level."""
-    d = np.asarray(profile, dtype=np.float64).ravel()
+    everywhere); the crater is the loss beyond that level. A 3D profile (ny, nx) takes the squared
+    distance in the x-y plane; columns at equal distance keep their row-major order."""
+    d = np.asarray(profile, dtype=np.float64)
+    if d.ndim == 2:
+        j0, i0 = np.unravel_index(int(np.argmax(d)), d.shape)
+        dy, dxc = _periodic_offsets(d.shape[0], j0), _periodic_offsets(d.shape[1], i0)
+        dist = (dy[:, None] ** 2 + dxc[None, :] ** 2).ravel()
+        d = d.ravel()
+    else:
+        d = d.ravel()
+        dist = np.abs(_periodic_offsets(d.size, int(np.argmax(d))))
     n = d.size
-    dist = np.abs((np.arange(n) - int(np.argmax(d)) + n // 2) % n - n // 2)
     far = np.argsort(dist, kind="stable")[n - n // 2:]
     return float(np.median(d[far])) if far.size else 0.0
 
 
-def crater_metrics(profile, dx: float, threshold: float = None, far_field: bool = False) -> dict:
-    """depth (m, the deepest column), width (m), left / right crossings (m). threshold: missing
-    material that counts as crater (default half a cell). far_field: measure from the far-field
-    surface level (`far_field_level`, returned as "level") instead of the original surface."""
-    d = np.asarray(profile, dtype=np.float64).ravel()
-    level = far_field_level(d) if far_field else 0.0
-    d = d - level
-    th = 0.5 * dx if threshold is None else float(threshold)
+def _width_1d(d: np.ndarray, i0: int, th: float, dx: float):
+    """Width and crossings of the run of columns above th that holds column i0 (periodic)."""
     n = len(d)
-    i0 = int(np.argmax(d))
-    depth = float(d[i0])
-    if depth <= th:
-        return {"depth": depth, "width": 0.0, "left": None, "right": None, "level": level}
-    if (d > th).all():                       # no edge: the whole surface is below the threshold
-        return {"depth": depth, "width": n * dx, "left": None, "right": None, "level": level}
+    if (d > th).all():                       # no edge: the whole line is below the threshold
+        return n * dx, None, None
     r = i0
     while r - i0 < n - 1 and d[(r + 1) % n] > th:
         r += 1
@@ -49,7 +52,38 @@ def crater_metrics(profile, dx: float, threshold: float = None, far_field: bool 
         left_i -= 1
     a, b = d[left_i % n], d[(left_i - 1) % n]
     left = left_i - (a - th) / (a - b)
-    return {"depth": depth, "width": (right - left) * dx, "left": left * dx, "right": right * dx, "level": level}
+    return (right - left) * dx, left * dx, right * dx
+
+
+def crater_metrics(profile, dx: float, threshold: float = None, far_field: bool = False) -> dict:
+    """depth (m, the deepest column), width (m), left / right crossings (m). threshold: missing
+    material that counts as crater (default half a cell). far_field: measure from the far-field
+    surface level (`far_field_level`, returned as "level") instead of the original surface.
+
+    A 3D profile (ny, nx) is measured along the row and the column through the deepest column:
+    width_x and width_y, and width = their mean, the diameter Eq. (5) takes; left / right are the
+    crossings along x."""
+    d = np.asarray(profile, dtype=np.float64)
+    level = far_field_level(d) if far_field else 0.0
+    d = d - level
+    th = 0.5 * dx if threshold is None else float(threshold)
+    if d.ndim == 2:
+        j0, i0 = np.unravel_index(int(np.argmax(d)), d.shape)
+        depth = float(d[j0, i0])
+        if depth <= th:
+            return {"depth": depth, "width": 0.0, "width_x": 0.0, "width_y": 0.0, "left": None,
+                    "right": None, "level": level}
+        wx, left, right = _width_1d(d[j0, :], int(i0), th, dx)
+        wy, _, _ = _width_1d(d[:, i0], int(j0), th, dx)
+        return {"depth": depth, "width": 0.5 * (wx + wy), "width_x": wx, "width_y": wy, "left": left,
+                "right": right, "level": level}
+    d = d.ravel()
+    i0 = int(np.argmax(d))
+    depth = float(d[i0])
+    if depth <= th:
+        return {"depth": depth, "width": 0.0, "left": None, "right": None, "level": level}
+    width, left, right = _width_1d(d, i0, th, dx)
+    return {"depth": depth, "width": width, "left": left, "right": right, "level": level}
 
 
 def threshold_fluence(fluence: float, width: float, beam_diameter: float) -> float:

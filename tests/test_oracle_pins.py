@@ -664,6 +664,106 @@ def test_spot_temperature_sampled_by_the_momenta():
     assert n_w > 3000 and t_w == pytest.approx(expect_w, rel=0.05)
 
 
+def _spot3(**kw):
+    w = workload("transport", dims=3, nx=40, ny=36, nz=16, slab_k=12, ppc_ion=4, T_ion_K=300.0)
+    w.update(kw)
+    return w
+
+
+def test_spot_temperature_3d_uniform_case_is_the_uniform_start():
+    """3D: a spot at the base temperature reduces bit for bit to the uniform start."""
+    a = oracle.Oracle3D(_spot3()).get_particles(0)
+    b = oracle.Oracle3D(_spot3(temp_profile=1, T_spot_K=300.0, spot_w=80e-9, spot_depth=40e-9)).get_particles(0)
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+
+
+def test_spot_temperature_3d_is_radial():
+    """3D lattice-temperature start: the spot and the uniform start draw the same normals, so
+    T_p = T_base |u_spot|^2 / |u_uniform|^2 is each atom's start temperature. A least-squares fit
+    of ln((T_p - T_base) / (T_spot - T_base)) over (squared distance from the axis in x, squared
+    distance in y, depth below the surface, 1) recovers -2 / spot_w^2 on both lateral axes (the
+    Gaussian is radial, its 1/e^2 radius spot_w), -1 / spot_depth (1/e depth) and 0 (T_spot on
+    the axis at the surface), with residuals at rounding level."""
+    base, top, sw, sd = 300.0, 12000.0, 80e-9, 40e-9
+    a = oracle.Oracle3D(_spot3()).get_particles(0)
+    b = oracle.Oracle3D(_spot3(temp_profile=1, T_spot_K=top, spot_w=sw, spot_depth=sd)).get_particles(0)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["z"], b["z"])
+    u2a = a["ux"] ** 2 + a["uy"] ** 2 + a["uz"] ** 2
+    u2b = b["ux"] ** 2 + b["uy"] ** 2 + b["uz"] ** 2
+    T = base * u2b / u2a
+    hot = (T - base) > 1e-3 * (top - base)
+    assert hot.sum() > 2000 and (~hot).sum() > 2000
+    dx = workload("transport")["dx"]
+    X = np.stack([(b["x"] - 20.0) ** 2, (b["y"] - 18.0) ** 2, 12.0 - b["z"], np.ones(len(T))], axis=1)[hot]
+    y = np.log((T[hot] - base) / (top - base))
+    coef, *_ = np.linalg.lstsq(X, y, rcond=None)       # per cell^2 and per cell
+    assert coef[0] * (sw / dx) ** 2 == pytest.approx(-2.0, rel=1e-7)
+    assert coef[1] * (sw / dx) ** 2 == pytest.approx(-2.0, rel=1e-7)
+    assert coef[2] * (sd / dx) == pytest.approx(-1.0, rel=1e-7)
+    assert abs(coef[3]) < 1e-7
+    assert np.abs(X @ coef - y).max() < 1e-6
+    # species 0 only: the uniform start of a second species is untouched
+    assert T.min() >= base * (1 - 1e-12)
+
+
+def test_crater_width_3d_closed_forms():
+    """3D crater profile (ny, nx): a square pyramid d = D - max(s_x |x|, s_y |y|) about the column
+    (j0, i0) is linear along the row and the column through its apex, so the threshold t is met at
+    |x| = (D - t) / s_x and |y| = (D - t) / s_y: widths 2 (D - t) / s_x dx and 2 (D - t) / s_y dx,
+    different on purpose so that transposed axes fail. A uniform loss added everywhere is the
+    far-field level; measured from it the widths stay."""
+    from paper_1502_07722_gb300 import crater
+    dx, D, t = 10e-9, 60e-9, 5e-9
+    ny, nx, j0, i0 = 30, 44, 11, 27
+    sx, sy = 5e-9, 11e-9
+    xo = np.abs((np.arange(nx) - i0 + nx // 2) % nx - nx // 2)
+    yo = np.abs((np.arange(ny) - j0 + ny // 2) % ny - ny // 2)
+    prof = np.maximum(D - np.maximum(sx * xo[None, :], sy * yo[:, None]), 0.0)
+    wx, wy = 2 * (D - t) / sx * dx, 2 * (D - t) / sy * dx
+    depth, gx, gy = oracle.crater_width_3d(prof, dx, t)
+    assert depth == D and gx == pytest.approx(wx, rel=1e-12) and gy == pytest.approx(wy, rel=1e-12)
+    m = crater.crater_metrics(prof, dx, t)
+    assert m["depth"] == D and m["width_x"] == pytest.approx(wx, rel=1e-12)
+    assert m["width_y"] == pytest.approx(wy, rel=1e-12) and m["width"] == pytest.approx(0.5 * (wx + wy), rel=1e-12)
+    # across both periodic seams
+    rolled = np.roll(np.roll(prof, 20, axis=1), 25, axis=0)
+    assert oracle.crater_width_3d(rolled, dx, t)[1:] == pytest.approx((wx, wy), rel=1e-12)
+    assert crater.crater_metrics(rolled, dx, t)["width_y"] == pytest.approx(wy, rel=1e-12)
+    lifted = prof + 70e-9
+    assert oracle.far_field(lifted) == pytest.approx(70e-9, rel=1e-15)
+    m = crater.crater_metrics(lifted, dx, t, far_field=True)
+    assert m["level"] == pytest.approx(70e-9, rel=1e-15)
+    assert (m["width_x"], m["width_y"]) == pytest.approx((wx, wy), rel=1e-9)
+    # the far half of the columns: a crater covering the near half is not the level
+    near = np.zeros((ny, nx))
+    near[:, :] = 3e-9
+    cy, cx = np.meshgrid(yo, xo, indexing="ij")
+    close = np.argsort((cy ** 2 + cx ** 2).ravel(), kind="stable")[: near.size // 2]
+    near.ravel()[close] = 50e-9
+    near[j0, i0] = 90e-9
+    assert oracle.far_field(near) == 3e-9 and crater.far_field_level(near) == 3e-9
+
+
+def test_crater_metrics_3d_match_the_oracle_on_random_profiles():
+    """Host logic against the oracle: random smooth 3D profiles with a crater and a relaxed level."""
+    from paper_1502_07722_gb300 import crater
+    rng = np.random.default_rng(5)
+    dx = 10e-9
+    for _ in range(20):
+        ny, nx = rng.integers(8, 40, size=2)
+        yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        cy, cx = rng.uniform(0, ny), rng.uniform(0, nx)
+        r2 = ((xx - cx) / rng.uniform(2, 8)) ** 2 + ((yy - cy) / rng.uniform(2, 8)) ** 2
+        prof = 80e-9 * np.exp(-r2) + rng.uniform(0, 8e-9) + rng.normal(0, 1e-9, size=(ny, nx))
+        level = oracle.far_field(prof)
+        m = crater.crater_metrics(prof, dx, far_field=True)
+        assert m["level"] == level
+        depth, wx, wy = oracle.crater_width_3d(prof - level, dx)
+        assert m["depth"] == pytest.approx(depth, rel=1e-15)
+        assert (m["width_x"], m["width_y"]) == pytest.approx((wx, wy), rel=1e-9)
+
+
 def test_crater_profile_counts_the_removed_material():
     """Removing every atom of the top h rows of m columns of the slab leaves h m cells of solid
     material missing: the column profile sums to h m dx (each cell of ppc macro-atoms is one cell
@@ -711,6 +811,16 @@ def test_crater_width_closed_forms():
     m = crater.crater_metrics(lifted, dx, t, far_field=True)
     assert m["level"] == pytest.approx(70e-9, rel=1e-15) and m["width"] == pytest.approx(expect, rel=1e-9)
     assert oracle.crater_width(lifted - oracle.far_field(lifted), dx, t)[1] == pytest.approx(expect, rel=1e-9)
+    # a lopsided crater: a flat pit of depth D on columns 6..32 of 40 whose deepest column (33,
+    # D + e) is at its right end reaches 27 columns to one side, more than half the period;
+    # edges at 6 - (D - t) / D and 33 + (D + e - t) / (D + e)
+    e = 1e-9
+    lop = np.zeros(40)
+    lop[6:33] = D
+    lop[33] = D + e
+    expect_l = (33 + (D + e - t) / (D + e) - (6 - (D - t) / D)) * dx
+    assert oracle.crater_width(lop, dx, t)[1] == pytest.approx(expect_l, rel=1e-12)
+    assert crater.crater_metrics(lop, dx, t)["width"] == pytest.approx(expect_l, rel=1e-12)
     # every column above the threshold: the crater spans the periodic width
     assert oracle.crater_width(np.full(50, D), dx, t)[1] == pytest.approx(50 * dx, rel=1e-15)
     assert crater.crater_metrics(np.full(50, D), dx, t)["width"] == pytest.approx(50 * dx, rel=1e-15)
