@@ -86,12 +86,14 @@ typedef struct pic_config {
                                 axis (weights of a node sum in units 2^-42); current J6x, J6y, J6z
                                 with J_x = J6x * e w / (6 * 2^42 dx^2 dt); dt = cfl dx / (c sqrt 3) */
     int32_t temp_profile;    /* PIC_TEMP_UNIFORM: species 0 starts at T_ion_K everywhere.
-                                PIC_TEMP_SPOT (2D only): the lattice temperature a laser spot left
+                                PIC_TEMP_SPOT: the lattice temperature a laser spot left
                                 behind (paper, Fig. 2 and the initialisation paragraph: the atomic-
                                 transport run starts from the lattice temperature after electrons
                                 and lattice equilibrate), for species 0 at its initial position
                                 (x, z) in cells: T = T_ion_K + (T_spot_K - T_ion_K)
-                                * exp(-2 ((x - nx/2) dx / spot_w)^2) * exp(-(slab_k - z) dx / spot_depth) */
+                                * exp(-2 ((x - nx/2) dx / spot_w)^2) * exp(-(slab_k - z) dx / spot_depth);
+                                in 3D the lateral term takes the radius from the axis,
+                                ((x - nx/2)^2 + (y - ny/2)^2) dx^2 / spot_w^2 */
     int32_t reserved0;       /* 0 */
     double T_spot_K;         /* peak temperature on the axis at the surface (K)                  */
     double spot_w;           /* 1/e^2 radius of the lateral Gaussian (m)                          */

@@ -64,7 +64,7 @@ int derive_layout(const pic_config* cfg, Layout& L)
     if (cfg->pot_mode != 0 && cfg->pot_mode != 1) return PIC_EINVAL;
     if (cfg->temp_profile != PIC_TEMP_UNIFORM && cfg->temp_profile != PIC_TEMP_SPOT) return PIC_EINVAL;
     if (cfg->temp_profile == PIC_TEMP_SPOT &&
-        (L.dims != 2 || !(cfg->spot_w > 0) || !(cfg->spot_depth > 0) || !(cfg->T_spot_K >= 0)))
+        (!(cfg->spot_w > 0) || !(cfg->spot_depth > 0) || !(cfg->T_spot_K >= 0)))
         return PIC_EINVAL;
     L.nx = cfg->nx;
     L.nz = cfg->nz;

@@ -883,52 +883,4 @@ void launch_energy3(Ctx& c, cudaStream_t st, double* host_out5)
     host_out5[4] = 0.5 * c.D * raw[4] * c.w;
 }
 
-// ---- initial state -------------------------------------------------------------------------
-
-__device__ __forceinline__ uint64_t smix3(uint64_t state)
-{
-    uint64_t z = state + 0x9E3779B97F4A7C15ULL;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ uint64_t draw3(uint64_t seed, int s, uint64_t pid, int d)
-{
-    return smix3(seed ^ (((((uint64_t)s << 40) + pid) << 3) + (uint64_t)d));
-}
-
-// slab cells k < slab_k over all (i, j), row-major; positions from draws 0 (x), 6 (y), 1 (z)
-__global__ void k_init3(SpeciesBuf out, int64_t n, int ppc, int nx, int ny, int species, int pos_species, double uth,
-                        uint64_t seed)
-{
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t cellidx = (uint64_t)p / (uint64_t)ppc;
-        out.cell[p] = (int32_t)cellidx;
-        out.fx[p] = (float)(draw3(seed, pos_species, (uint64_t)p, 0) >> 40) * (1.0f / 16777216.0f);
-        out.fy[p] = (float)(draw3(seed, pos_species, (uint64_t)p, 6) >> 40) * (1.0f / 16777216.0f);
-        out.fz[p] = (float)(draw3(seed, pos_species, (uint64_t)p, 1) >> 40) * (1.0f / 16777216.0f);
-        const double u1 = ((double)(draw3(seed, species, (uint64_t)p, 2) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
-        const double a1 = 2.0 * kPi * (double)(draw3(seed, species, (uint64_t)p, 3) >> 40) * (1.0 / 16777216.0);
-        const double u2 = ((double)(draw3(seed, species, (uint64_t)p, 4) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
-        const double a2 = 2.0 * kPi * (double)(draw3(seed, species, (uint64_t)p, 5) >> 40) * (1.0 / 16777216.0);
-        const double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u2));
-        out.ux[p] = (float)(uth * r1 * cos(a1));
-        out.uy[p] = (float)(uth * r1 * sin(a1));
-        out.uz[p] = (float)(uth * r2 * cos(a2));
-    }
-    (void)nx;
-    (void)ny;
-}
-
-void launch_init_particles3(Ctx& c, int s, cudaStream_t st)
-{
-    Species& S = c.sp[s];
-    if (S.n == 0) return;
-    int64_t g = (S.n + 255) / 256;
-    if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
-    const int pos_species = (s == 1 && c.cfg.ppc_electron == c.cfg.ppc_ion) ? 0 : s;
-    k_init3<<<(int)g, 256, 0, st>>>(S.b, S.n, S.ppc, c.nx, c.ny, s, pos_species, S.uth, c.cfg.seed);
-}
-
 }  // namespace gbpic

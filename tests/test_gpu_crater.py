@@ -58,13 +58,40 @@ def test_spot_start_matches_oracle(gb):
     sim.close()
 
 
-def test_spot_start_rejected_outside_2d(gb):
+def test_spot_start_rejected_without_a_spot(gb):
     with pytest.raises(gb.PicError) as e:
         gb.Simulation(dict(spot(), spot_w=0.0))
     assert e.value.code == gb.PIC_EINVAL
     with pytest.raises(gb.PicError) as e:
-        gb.Simulation(dict(spot(), dims=3, ny=8))
+        gb.Simulation(dict(spot(), dims=3, ny=8, spot_depth=-1.0))
     assert e.value.code == gb.PIC_EINVAL
+
+
+@pytest.mark.parametrize("tile", [4, 10])
+def test_spot_start_3d_matches_oracle(gb, tile):
+    """3D lattice-temperature start (radial Gaussian about the axis through the middle of the x-y
+    plane): positions bit-exact, momenta to FP32 rounding, on a grid whose sides are not
+    multiples of the tile."""
+    w = spot(dims=3, nx=26, ny=22, nz=18, slab_k=11, ppc_ion=6, tile=tile, spot_w=60e-9, spot_depth=40e-9)
+    sim = gb.Simulation(w)
+    orc = oracle.Oracle3D(w)
+    g = {k: v.cpu().numpy() for k, v in sim.get_particles(0).items()}
+    cell = g["cell"].astype(np.int64)
+    x = cell % w["nx"] + g["fx"].astype(np.float64)
+    y = (cell // w["nx"]) % w["ny"] + g["fy"].astype(np.float64)
+    z = cell // (w["nx"] * w["ny"]) + g["fz"].astype(np.float64)
+    o = orc.get_particles(0)
+    kg, ko = np.lexsort((z, y, x)), np.lexsort((o["z"], o["y"], o["x"]))
+    for a, b in ((x, "x"), (y, "y"), (z, "z")):
+        assert np.array_equal(a[kg], o[b][ko])
+    for comp in ("ux", "uy", "uz"):
+        u = g[comp].astype(np.float64)
+        np.testing.assert_allclose(u[kg], o[comp][ko], rtol=1e-6, atol=1e-7 * np.abs(o[comp]).max())
+    r2 = (x - w["nx"] / 2) ** 2 + (y - w["ny"] / 2) ** 2
+    u2 = sum(g[c].astype(np.float64) ** 2 for c in ("ux", "uy", "uz"))
+    top = z > w["slab_k"] - 2
+    assert u2[(r2 < 4) & top].mean() > 10 * u2[(r2 > 100) & top].mean()
+    sim.close()
 
 
 def test_crater_profile_matches_oracle(gb):
