@@ -144,6 +144,7 @@ def lib():
             "oracle3_get_field": (None, [vp, ctypes.c_int32, _D]),
             "oracle3_set_field": (None, [vp, ctypes.c_int32, _D]),
             "oracle3_get_rho": (None, [vp, _I64]),
+            "oracle3_crater_profile": (None, [vp, _I64, _I64, _D]),
             "oracle3_set_rho": (None, [vp, _I64]),
             "oracle3_get_current": (None, [vp, _I64]),
             "oracle3_set_current": (None, [vp, _I64]),
@@ -503,6 +504,17 @@ class Oracle3D:
         out = np.empty(self._nn(), np.int64)
         lib().oracle3_get_rho(self._s, _p(out, ctypes.c_int64))
         return out.reshape(self._shape())
+
+    def crater_profile(self, rho0, rho=None):
+        """Material missing from each node column (j, i) of the original slab (m of solid-density
+        material) between node sums rho0 and rho (default: the state's own); shape (ny, nx)."""
+        r0 = np.ascontiguousarray(rho0, np.int64).reshape(-1)
+        assert r0.size == self.nx * self.ny * (self.nz + 1)
+        r = None if rho is None else np.ascontiguousarray(rho, np.int64).reshape(-1)
+        out = np.empty((self.ny, self.nx), np.float64)
+        lib().oracle3_crater_profile(self._s, _p(r0, ctypes.c_int64),
+                                     None if r is None else _p(r, ctypes.c_int64), _p(out, ctypes.c_double))
+        return out
 
     def set_rho(self, a):
         a = np.ascontiguousarray(a, np.int64).reshape(-1)

@@ -1286,6 +1286,25 @@ int64_t oracle3_num_particles(const ostate3* s, int32_t sp) { return sp < s->nsp
 double oracle3_dt(const ostate3* s) { return s->dt; }
 double oracle3_weight(const ostate3* s) { return s->w; }
 double oracle3_rho_scale(const ostate3* s) { return s->rho_scale; }
+
+/* Crater profile in 3D (the density-map measurement of the crater, Eq. 5's diameter): material
+ * missing from node column (i, j) of the original slab rows 0..slab_k between the node sums rho0
+ * and rho (NULL: the state's own), in metres of solid-density material; out is (ny, nx). A node
+ * sum counts 2^-42 macro-atoms per cell volume. */
+void oracle3_crater_profile(const ostate3* s, const int64_t* rho0, const int64_t* rho, double* out)
+{
+    const ocfg3* c = &s->c;
+    const int64_t* now = rho ? rho : s->rho;
+    int top = c->slab_k < c->nz ? c->slab_k : c->nz;
+    double to_solid = s->w / (4398046511104.0 * c->dx * c->dx * c->dx) / c->n_atoms;
+    for (int j = 0; j < c->ny; j++)
+        for (int i = 0; i < c->nx; i++) {
+            int64_t missing = 0;
+            for (int k = 0; k <= top; k++) missing += rho0[N3(s, i, j, k)] - now[N3(s, i, j, k)];
+            out[(size_t)j * c->nx + i] = c->dx * ((double)missing * to_solid);
+        }
+}
+
 void oracle3_set_step(ostate3* s, int64_t step) { s->step = step; }
 
 void oracle3_get_particles(const ostate3* s, int32_t sp, double* x, double* y, double* z, double* ux, double* uy, double* uz)

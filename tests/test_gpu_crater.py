@@ -143,6 +143,30 @@ def test_crater_profile_3d_counts_removed_material(gb):
     sim.close()
 
 
+def test_crater_3d_matches_oracle(gb):
+    """3D spot run (800 steps, 9.6 ps): the GPU's (ny, nx) profile of its own maps equals the
+    oracle's profile of the same maps; depth and the widths along x and y agree between the two
+    measurements."""
+    from paper_1502_07722_gb300 import crater
+    w = spot(dims=3, nx=28, ny=24, nz=20, slab_k=12, ppc_ion=8, tile=10, spot_w=80e-9, spot_depth=40e-9)
+    sim = gb.Simulation(w)
+    rho0, _ = sim.deposit_density()
+    assert float(sim.crater_profile(rho0).abs().max()) == 0.0
+    sim.step(800)
+    prof = sim.crater_profile(rho0).cpu().numpy()
+    assert prof.shape == (24, 28)
+    orc = oracle.Oracle3D(w, with_particles=False)
+    expect = orc.crater_profile(rho0.cpu().numpy(), sim.get_density().cpu().numpy())
+    np.testing.assert_allclose(prof, expect, rtol=1e-14, atol=0)
+    th = 0.25 * w["dx"]
+    m = crater.crater_metrics(prof, w["dx"], threshold=th)
+    depth, wx, wy = oracle.crater_width_3d(expect, w["dx"], th)
+    assert m["depth"] == pytest.approx(depth, rel=1e-14)
+    assert (m["width_x"], m["width_y"]) == pytest.approx((wx, wy), rel=1e-9)
+    assert prof.max() > th                                 # material has left the hot spot
+    sim.close()
+
+
 def test_c_att_calibration_matches_oracle(gb):
     """The attractive-factor calibration on the GPU's initial slab (probe forces through the C ABI)
     against the oracle's calibration on the same node sums, with the same rule per cell (8-point

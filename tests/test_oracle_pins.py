@@ -782,6 +782,26 @@ def test_crater_profile_counts_the_removed_material():
     assert (prof[:i1] == 0).all() and (prof[i2 + 1:] == 0).all() and (prof[i1:i2 + 1] > 0).all()
 
 
+def test_crater_profile_3d_counts_the_removed_material():
+    """3D: removing every atom of the top h rows of an m_x x m_y block of columns leaves
+    h m_x m_y cells of solid material missing: the (ny, nx) profile sums to h m_x m_y dx, spread
+    over the node columns that bound those cells and none other; a profile of the unchanged state
+    is zero."""
+    w = workload("transport", dims=3, nx=20, ny=16, nz=12, slab_k=8, ppc_ion=5)
+    o = oracle.Oracle3D(w)
+    rho0 = o.get_rho()
+    assert np.array_equal(o.crater_profile(rho0), np.zeros((16, 20)))
+    p = o.get_particles(0)
+    h = 2
+    gone = (p["x"] >= 6) & (p["x"] < 11) & (p["y"] >= 4) & (p["y"] < 7) & (p["z"] >= w["slab_k"] - h)
+    keep = ~gone
+    o.set_rho(oracle.deposit_density3(20, 16, 12, p["x"][keep], p["y"][keep], p["z"][keep]))
+    prof = o.crater_profile(rho0)
+    assert prof.sum() == pytest.approx(h * 5 * 3 * w["dx"], rel=1e-12)
+    assert (prof[:, :6] == 0).all() and (prof[:, 12:] == 0).all()
+    assert (prof[:4] == 0).all() and (prof[8:] == 0).all()
+
+
 def test_crater_width_closed_forms():
     """A flat-bottomed pit of depth D over columns i1..i2-1 (zero outside): the threshold t is met
     a fraction (D - t) / D of a column outside each edge, width (i2 - 1 - i1 + 2 (D - t) / D) dx.
