@@ -47,6 +47,7 @@ class OracleConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
+        ("morse_a", ctypes.c_double),
     ]
 
 
@@ -64,6 +65,7 @@ class OracleConfig3(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
+        ("morse_a", ctypes.c_double),
     ]
 
 
@@ -103,6 +105,8 @@ def lib():
             "oracle_laser_field": (ctypes.c_double, [vp, ctypes.c_double, ctypes.c_double]),
             "oracle_lj_U": (ctypes.c_double, [ctypes.c_double]),
             "oracle_lj_dU": (ctypes.c_double, [ctypes.c_double]),
+            "oracle_morse_U": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+            "oracle_morse_dU": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "oracle_neighbor_distances": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]),
             "oracle_boris": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
             "oracle_jy_code": (ctypes.c_int64, [ctypes.c_float, ctypes.c_float, ctypes.c_float]),
@@ -395,6 +399,15 @@ def lj_U(r):
 
 def lj_dU(r):
     return lib().oracle_lj_dU(float(r))
+
+
+def morse_U(a, r):
+    """Morse potential (units D, r in units of r0, minimum -1 at r = 1), stiffness a = alpha r0."""
+    return lib().oracle_morse_U(float(a), float(r))
+
+
+def morse_dU(a, r):
+    return lib().oracle_morse_dU(float(a), float(r))
 
 
 def neighbor_distances(n, dn, r0_dx):

@@ -63,7 +63,7 @@ typedef struct {
     int32_t slab_k;          /* the copper slab fills cell rows k < slab_k                    */
     int32_t mode;            /* 0: ions + electrons + fields; 1: neutral atoms only           */
     int32_t ppc_ion, ppc_electron;
-    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (scaled branches)       */
+    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (scaled branches); 2: Morse */
     int32_t laser_profile;   /* 0: none; 1: plane wave; 2: focused Gaussian beam              */
     double dx;               /* cell size (m), square cells                                   */
     double cfl;              /* dt = cfl * dx / (c * sqrt(2)) when dt_override <= 0          */
@@ -80,6 +80,7 @@ typedef struct {
     int32_t temp_profile;    /* 0: uniform T_ion_K; 1: lattice temperature of a laser spot       */
     int32_t reserved0;
     double T_spot_K, spot_w, spot_depth;       /* K, m (1/e^2 radius), m (1/e depth)         */
+    double morse_a;          /* Morse stiffness alpha r0 (pot_mode 2)                           */
 } ocfg;
 
 typedef struct {
@@ -141,9 +142,21 @@ static double branch_factor_p(int pot_mode, double c_att, double s_rep, double r
     if (pot_mode == 0) return 1.0;
     return r < 1.0 ? s_rep : c_att;
 }
-static double branch_factor(const ostate* s, double r)
+/* Morse potential (pot_mode 2; the paper names it as one the density-to-distance mapping takes
+ * as it is), units of D with r in units of r0 and its minimum -1 at r = 1 like Eq. (3):
+ * U = e^(-2 a (r - 1)) - 2 e^(-a (r - 1)), a = alpha r0 */
+double oracle_morse_U(double a, double r) { double e = exp(-a * (r - 1.0)); return e * e - 2.0 * e; }
+/* dU/dr (units D / r0) */
+double oracle_morse_dU(double a, double r) { double e = exp(-a * (r - 1.0)); return 2.0 * a * e * (1.0 - e); }
+
+/* the pair potential and its derivative selected by pot_mode */
+static double pot_U(int pm, double c_att, double s_rep, double a, double r)
 {
-    return branch_factor_p(s->c.pot_mode, s->c.c_att, s->c.s_rep, r);
+    return pm == 2 ? oracle_morse_U(a, r) : branch_factor_p(pm, c_att, s_rep, r) * oracle_lj_U(r);
+}
+static double pot_dU(int pm, double c_att, double s_rep, double a, double r)
+{
+    return pm == 2 ? oracle_morse_dU(a, r) : branch_factor_p(pm, c_att, s_rep, r) * oracle_lj_dU(r);
 }
 
 /* Eq. (1)-(2): nearest-neighbour distances (units r0) along one axis from the local density
@@ -345,19 +358,21 @@ static void pair_force_at(const ostate* s, double x, double z, double F[3], doub
     double rbar = oracle_neighbor_distances(n, dnx, r0_dx, &ap, &am);
     oracle_neighbor_distances(n, dnz, r0_dx, &bp, &bm);
     double f_unit = s->D / s->r0;
-    double dUap = isinf(ap) ? 0.0 : branch_factor(s, ap) * oracle_lj_dU(ap);
-    double dUam = isinf(am) ? 0.0 : branch_factor(s, am) * oracle_lj_dU(am);
-    double dUbp = isinf(bp) ? 0.0 : branch_factor(s, bp) * oracle_lj_dU(bp);
-    double dUbm = isinf(bm) ? 0.0 : branch_factor(s, bm) * oracle_lj_dU(bm);
+    int pm = s->c.pot_mode;
+    double ca = s->c.c_att, sr = s->c.s_rep, ma = s->c.morse_a;
+    double dUap = isinf(ap) ? 0.0 : pot_dU(pm, ca, sr, ma, ap);
+    double dUam = isinf(am) ? 0.0 : pot_dU(pm, ca, sr, ma, am);
+    double dUbp = isinf(bp) ? 0.0 : pot_dU(pm, ca, sr, ma, bp);
+    double dUbm = isinf(bm) ? 0.0 : pot_dU(pm, ca, sr, ma, bm);
     F[0] = f_unit * (dUap - dUam);
     F[2] = f_unit * (dUbp - dUbm);
     if (energy) {
         double u = 0.0;
-        if (!isinf(ap)) u += branch_factor(s, ap) * oracle_lj_U(ap);
-        if (!isinf(am)) u += branch_factor(s, am) * oracle_lj_U(am);
-        if (!isinf(bp)) u += branch_factor(s, bp) * oracle_lj_U(bp);
-        if (!isinf(bm)) u += branch_factor(s, bm) * oracle_lj_U(bm);
-        u += 2.0 * branch_factor(s, rbar) * oracle_lj_U(rbar);
+        if (!isinf(ap)) u += pot_U(pm, ca, sr, ma, ap);
+        if (!isinf(am)) u += pot_U(pm, ca, sr, ma, am);
+        if (!isinf(bp)) u += pot_U(pm, ca, sr, ma, bp);
+        if (!isinf(bm)) u += pot_U(pm, ca, sr, ma, bm);
+        u += 2.0 * pot_U(pm, ca, sr, ma, rbar);
         *energy = 0.5 * s->D * u;
     }
 }
@@ -887,6 +902,7 @@ typedef struct {
     int32_t temp_profile;    /* 0: uniform T_ion_K; 1: lattice temperature of a laser spot       */
     int32_t reserved0;
     double T_spot_K, spot_w, spot_depth;
+    double morse_a;
 } ocfg3;
 
 typedef struct {
@@ -1061,11 +1077,11 @@ static void pair_force3_at(const ostate3* s, double x, double y, double z, doubl
     for (int d = 0; d < 3; d++) {
         double ap, am;
         oracle_neighbor_distances(n, g[d], r0_dx, &ap, &am);
-        double dUp = isinf(ap) ? 0.0 : branch_factor_p(pm, s->c.c_att, s->c.s_rep, ap) * oracle_lj_dU(ap);
-        double dUm = isinf(am) ? 0.0 : branch_factor_p(pm, s->c.c_att, s->c.s_rep, am) * oracle_lj_dU(am);
+        double dUp = isinf(ap) ? 0.0 : pot_dU(pm, s->c.c_att, s->c.s_rep, s->c.morse_a, ap);
+        double dUm = isinf(am) ? 0.0 : pot_dU(pm, s->c.c_att, s->c.s_rep, s->c.morse_a, am);
         F[d] = f_unit * (dUp - dUm);
-        if (!isinf(ap)) u += branch_factor_p(pm, s->c.c_att, s->c.s_rep, ap) * oracle_lj_U(ap);
-        if (!isinf(am)) u += branch_factor_p(pm, s->c.c_att, s->c.s_rep, am) * oracle_lj_U(am);
+        if (!isinf(ap)) u += pot_U(pm, s->c.c_att, s->c.s_rep, s->c.morse_a, ap);
+        if (!isinf(am)) u += pot_U(pm, s->c.c_att, s->c.s_rep, s->c.morse_a, am);
     }
     if (energy) *energy = 0.5 * s->D * u;
 }

@@ -72,11 +72,13 @@ def test_current3_continuity_and_dipole():
         assert int(Jp[2].sum()) == 6 * Q3 * Q3 * dZ
 
 
-def test_uniform_lattice3_zero_force_and_energy():
+@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 4.0}], ids=["lj", "morse"])
+def test_uniform_lattice3_zero_force_and_energy(pot):
     """Identical offsets in every cell of a full-height slab: uniform node density, zero force,
-    and -3 D per atom at the equilibrium density (six neighbours at r0)."""
+    and -3 D per atom at the equilibrium density (six neighbours at r0; both potentials have their
+    minimum -D there)."""
     nx, ny, nz = 6, 5, 6
-    w = cfg3(nx=nx, ny=ny, nz=nz, slab_k=nz, ppc_ion=2, ppc_electron=2)
+    w = cfg3(nx=nx, ny=ny, nz=nz, slab_k=nz, ppc_ion=2, ppc_electron=2, **pot)
     o = oracle.Oracle3D(w, with_particles=False)
     cells = np.arange(nx * ny * nz)
     i, j, k = cells % nx, (cells // nx) % ny, cells // (nx * ny)
@@ -90,21 +92,22 @@ def test_uniform_lattice3_zero_force_and_energy():
     assert o.energy()["pair"] == pytest.approx(-3 * D * n * o.weight, rel=1e-12)
 
 
-def test_pair_force_3d_equals_2d_on_y_uniform_state():
+@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 4.0}], ids=["lj", "morse"])
+def test_pair_force_3d_equals_2d_on_y_uniform_state(pot):
     """The 2D method is the 3D method on a state that does not vary along y: same x and z forces
-    (the y force vanishes)."""
+    (the y force vanishes), for either pair potential."""
     nx, nz, ny = 12, 10, 4
     rng = np.random.default_rng(5)
     ncell = nx * 5
     cells = np.repeat(np.arange(ncell), 4)
     xs = cells % nx + np.floor(rng.random(len(cells)) * Q3) / Q3
     zs = cells // nx + np.floor(rng.random(len(cells)) * 0.8 * Q3) / Q3
-    w2 = workload("tiny", nx=nx, nz=nz, slab_k=5, ppc_ion=4, ppc_electron=4, laser_profile=0)
+    w2 = workload("tiny", nx=nx, nz=nz, slab_k=5, ppc_ion=4, ppc_electron=4, laser_profile=0, **pot)
     o2 = oracle.Oracle(w2, with_particles=False)
     n = len(xs)
     o2.set_particles(0, xs, zs, np.zeros(n), np.zeros(n), np.zeros(n))
     F2 = o2.pair_force()
-    w3 = cfg3(nx=nx, ny=ny, nz=nz, slab_k=5, ppc_ion=4, ppc_electron=4)
+    w3 = cfg3(nx=nx, ny=ny, nz=nz, slab_k=5, ppc_ion=4, ppc_electron=4, **pot)
     o3 = oracle.Oracle3D(w3, with_particles=False)
     X = np.tile(xs, ny)
     Y = np.repeat(np.arange(ny) + 0.5, n)

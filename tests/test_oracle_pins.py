@@ -245,11 +245,33 @@ def test_gather_reproduces_linear_density():
         assert dnz == pytest.approx(bz * s, rel=1e-12)
 
 
-def test_pair_force_first_order_closed_form_and_sign():
+# ---- Morse potential (pot_mode 2): another pair potential the density mapping takes ----------
+
+@pytest.mark.parametrize("a", [3.0, 4.0, 6.5])
+def test_morse_closed_forms(a):
+    """U = e^(-2a(r-1)) - 2e^(-a(r-1)) (units D, r in r0): minimum U(1) = -1 with U'(1) = 0;
+    U = 0 where e^(-a(r-1)) = 2, r = 1 - ln2 / a; U(1 + ln2 / a) = 1/4 - 1 = -3/4; U''(1) = 2a^2
+    (central differences of U'); U' is the derivative of U; U and U' vanish far away."""
+    assert oracle.morse_U(a, 1.0) == -1.0 and oracle.morse_dU(a, 1.0) == 0.0
+    assert oracle.morse_U(a, 1 - math.log(2) / a) == pytest.approx(0.0, abs=1e-15)
+    assert oracle.morse_U(a, 1 + math.log(2) / a) == pytest.approx(-0.75, rel=1e-15)
+    h = 1e-5
+    d2 = (oracle.morse_dU(a, 1 + h) - oracle.morse_dU(a, 1 - h)) / (2 * h)
+    assert d2 == pytest.approx(2 * a * a, rel=1e-8)
+    for r in (0.8, 0.95, 1.1, 1.5, 2.5):
+        fd = (oracle.morse_U(a, r + h) - oracle.morse_U(a, r - h)) / (2 * h)
+        assert oracle.morse_dU(a, r) == pytest.approx(fd, rel=1e-8, abs=1e-10)
+    assert abs(oracle.morse_U(a, 30.0)) < 1e-30 and abs(oracle.morse_dU(a, 30.0)) < 1e-30
+
+
+@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 4.0}], ids=["lj", "morse"])
+def test_pair_force_first_order_closed_form_and_sign(pot):
     """For a small gradient, Eqs. (1)-(3) reduce to F = U''(rbar) * (a - b) with
     a - b = rbar g (to first order): F_x ~ -(1/3) U''(rbar) rbar n^(-4/3) dn/dx. Atoms in a
-    compressed region (rbar < r0) are pushed down the density gradient."""
-    o = _grid_oracle(16, 16)
+    compressed region (rbar < r0) are pushed down the density gradient. The same holds for the
+    Morse form with its own U''."""
+    o = oracle.Oracle(dict(workload("tiny", nx=16, nz=16, slab_k=16, laser_profile=0), **pot), with_particles=False)
+    dU = (lambda r: oracle.morse_dU(pot["morse_a"], r)) if pot else oracle.lj_dU
     nz, nx = 16, 16
     k, i = np.mgrid[0:nz + 1, 0:nx]
     s = o.rho_scale
@@ -269,7 +291,7 @@ def test_pair_force_first_order_closed_form_and_sign():
         n, dnx, dnz = o.gather_density(x, z)
         rbar = n ** (-1 / 3)
         h = 1e-4
-        U2 = (oracle.lj_dU(rbar + h) - oracle.lj_dU(rbar - h)) / (2 * h)      # units D/r0^2
+        U2 = (dU(rbar + h) - dU(rbar - h)) / (2 * h)                          # units D/r0^2
         g = -(1 / 3) * dnx * n ** (-4 / 3) * r0_dx
         F_lin = (D / r0) * U2 * rbar * g
         assert F[0] == pytest.approx(F_lin, rel=2e-3)
@@ -531,11 +553,12 @@ def test_field_energy_of_uniform_fields():
     assert e["field_B"] == pytest.approx(3 * 0.25 / (2 * mu0) * area, rel=1e-13)
 
 
-def test_pair_energy_of_equilibrium_lattice():
+@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 3.0}], ids=["lj", "morse"])
+def test_pair_energy_of_equilibrium_lattice(pot):
     """At the equilibrium density every atom has its six cubic-lattice neighbours at r0:
-    pair energy per atom = (1/2) * 6 * U(r0) = -3 D."""
+    pair energy per atom = (1/2) * 6 * U(r0) = -3 D (both potentials have their minimum -D at r0)."""
     nx, nz = 16, 12
-    o = oracle.Oracle(workload("tiny", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, laser_profile=0),
+    o = oracle.Oracle(workload("tiny", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, laser_profile=0, **pot),
                       with_particles=False)
     n = nx * nz * 4
     cell = np.repeat(np.arange(nx * nz), 4)
@@ -583,14 +606,16 @@ def test_injected_energy_of_a_plane_wave_pulse():
     assert e["field_E"] + e["field_B"] <= e["injected"] * 1.01
 
 
-def test_acoustic_wave_speed_of_the_pair_force():
+@pytest.mark.parametrize("pot,curv", [({}, 72.0), ({"pot_mode": 2, "morse_a": 4.0}, 32.0)], ids=["lj", "morse"])
+def test_acoustic_wave_speed_of_the_pair_force(pot, curv):
     """Linearising Eqs. (1)-(3) about the equilibrium lattice (n = n0, rbar = r0) gives the wave
-    equation u_tt = (U''(r0) r0^2 / (3 m)) u_xx = (24 D / m) u_xx for a small longitudinal
-    displacement u: a standing wave of wavelength 64 cells in the transport mode oscillates with
-    period lambda / sqrt(24 D / m) and keeps its amplitude."""
+    equation u_tt = (U''(r0) r0^2 / (3 m)) u_xx for a small longitudinal displacement u, with
+    U''(r0) r0^2 = 72 D for Eq. (3) (24 D / m) and 2 a^2 D for the Morse form (a = 4: 32 D / (3 m)):
+    a standing wave of wavelength 64 cells in the transport mode oscillates with period
+    lambda / sqrt(U''(r0) r0^2 / (3 m)) and keeps its amplitude."""
     nx, nz = 64, 4
     dt = 50e-15
-    w = workload("transport", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, T_ion_K=0.0, dt_override=dt)
+    w = workload("transport", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, T_ion_K=0.0, dt_override=dt, **pot)
     o = oracle.Oracle(w, with_particles=False)
     cells = np.arange(nx * nz)
     i, k = cells % nx, cells // nx
@@ -602,7 +627,7 @@ def test_acoustic_wave_speed_of_the_pair_force():
     n = len(x0)
     o.set_particles(0, x0 + eps * np.sin(kk * x0), z0, np.zeros(n), np.zeros(n), np.zeros(n))
     m = 63.546 * 1.66053906660e-27
-    period = (nx * w["dx"]) / math.sqrt(24 * 0.41 * QE / m)
+    period = (nx * w["dx"]) / math.sqrt(curv * 0.41 * QE / (3 * m))
     amps = []
     chunk = 20
     for s in range(0, int(2.5 * period / dt), chunk):
