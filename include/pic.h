@@ -62,7 +62,10 @@ typedef struct pic_config {
     int32_t mode;            /* PIC_MODE_FULL: Cu+ ions, electrons, fields (ion_charge = 1);
                                 PIC_MODE_TRANSPORT: neutral atoms and the pair force only        */
     int32_t ppc_ion, ppc_electron;   /* macroparticles per slab cell (equal in the full mode)   */
-    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (s_rep below r0, c_att above) */
+    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (s_rep below r0, c_att above);
+                                2: Morse, U = D [e^(-2a(r/r0-1)) - 2 e^(-a(r/r0-1))], a = morse_a (the
+                                paper: the density-to-distance mapping takes any pair potential,
+                                the Morse potential among them); its minimum is -D at r0 like Eq. (3) */
     int32_t laser_profile;   /* PIC_LASER_*                                                     */
     int32_t tile;            /* tile edge in cells for particle binning (0: 16 in 2D, 10 in 3D)  */
     int32_t sort_every;      /* steps between cell sorts (0: only after init / set_particles)  */
@@ -98,6 +101,8 @@ typedef struct pic_config {
     double T_spot_K;         /* peak temperature on the axis at the surface (K)                  */
     double spot_w;           /* 1/e^2 radius of the lateral Gaussian (m)                          */
     double spot_depth;       /* 1/e depth of the temperature below the surface (m)                */
+    double morse_a;          /* Morse stiffness alpha r0 (dimensionless, 0 < morse_a < 1000) for
+                                pot_mode 2; unused otherwise                                      */
 } pic_config;
 
 #define PIC_TEMP_UNIFORM 0
@@ -126,6 +131,10 @@ typedef struct pic_energy_t {
 } pic_energy_t;
 
 typedef struct pic_ctx pic_ctx;
+
+/* sizeof(pic_config) as this library was built: a binding checks its own copy of the struct
+ * against it. Host only; no errors. (Not a step of the paper's method.) */
+PIC_API size_t pic_config_bytes(void);
 
 /* Bytes of device workspace pic_init needs for cfg. */
 PIC_API int pic_workspace_size(const pic_config* cfg, size_t* bytes);
@@ -191,9 +200,10 @@ PIC_API int pic_pair_force(pic_ctx* ctx, float* dev_out);
  * force on a single atom leaving the target out to infinity). dev_cell, dev_fx, dev_fz: device
  * arrays of n probes (cell k*nx + i, offsets in [0,1) x [0,1]); pot_mode, c_att, s_rep as in
  * pic_config, applied to this call only (so one context yields the attractive and the repulsive
- * parts of the force separately). dev_out: device float[3n], (Fx, 0, Fz). A probe outside the
+ * parts of the force separately); pot_mode 2 takes the context's morse_a and ignores c_att, s_rep. dev_out: device float[3n], (Fx, 0, Fz). A probe outside the
  * grid gets NaN. 2D contexts; asynchronous on the context's stream. Errors: PIC_EINVAL (n < 0,
- * NULL pointers with n > 0, pot_mode not 0 or 1), PIC_ESTATE in 3D. */
+ * NULL pointers with n > 0, pot_mode not 0, 1 or 2, pot_mode 2 with morse_a <= 0), PIC_ESTATE in
+ * 3D. */
 PIC_API int pic_pair_force_at(pic_ctx* ctx, int64_t n, const int32_t* dev_cell, const float* dev_fx,
                               const float* dev_fz, int32_t pot_mode, double c_att, double s_rep, float* dev_out);
 

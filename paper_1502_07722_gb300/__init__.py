@@ -39,6 +39,7 @@ class pic_config(ctypes.Structure):
         ("ny", ctypes.c_int32), ("dims", ctypes.c_int32),
         ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
+        ("morse_a", ctypes.c_double),
     ]
 
 
@@ -70,6 +71,7 @@ class pic_adjoint_buffers(ctypes.Structure):
 _VP = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _SIGNATURES = {
+    "pic_config_bytes": (ctypes.c_size_t, []),
     "pic_workspace_size": (ctypes.c_int, [ctypes.POINTER(pic_config), ctypes.POINTER(ctypes.c_size_t)]),
     "pic_init": (ctypes.c_int, [ctypes.POINTER(pic_config), _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
     "pic_free": (None, [_VP]),
@@ -123,6 +125,8 @@ def load_library():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        if L.pic_config_bytes() != ctypes.sizeof(pic_config):
+            raise RuntimeError(f"{LIBPATH} was built with another pic_config layout: rebuild it")
         _lib = L
     return _lib
 

@@ -61,7 +61,8 @@ int derive_layout(const pic_config* cfg, Layout& L)
         !(cfg->lambda > 0 && cfg->tau_fwhm > 0))
         return PIC_EINVAL;
     if (cfg->laser_profile == PIC_LASER_GAUSSIAN && !(cfg->w0 > 0)) return PIC_EINVAL;
-    if (cfg->pot_mode != 0 && cfg->pot_mode != 1) return PIC_EINVAL;
+    if (cfg->pot_mode < 0 || cfg->pot_mode > 2) return PIC_EINVAL;
+    if (cfg->pot_mode == 2 && !(cfg->morse_a > 0 && cfg->morse_a < 1e3)) return PIC_EINVAL;
     if (cfg->temp_profile != PIC_TEMP_UNIFORM && cfg->temp_profile != PIC_TEMP_SPOT) return PIC_EINVAL;
     if (cfg->temp_profile == PIC_TEMP_SPOT &&
         (!(cfg->spot_w > 0) || !(cfg->spot_depth > 0) || !(cfg->T_spot_K >= 0)))
@@ -197,7 +198,7 @@ StepArgs make_step_args(Ctx& c)
     a.rho_s = (float)c.rho_scale;
     a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
     a.pot_mode = c.cfg.pot_mode;
-    a.c_att = (float)c.cfg.c_att;
+    a.c_att = pot_param(c.cfg);
     a.s_rep = (float)c.cfg.s_rep;
     for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
     a.rho_cur = c.rho[c.cur];
@@ -212,6 +213,8 @@ StepArgs make_step_args(Ctx& c)
 }  // namespace gbpic
 
 extern "C" {
+
+size_t pic_config_bytes(void) { return sizeof(pic_config); }
 
 int pic_workspace_size(const pic_config* cfg, size_t* bytes)
 {
@@ -460,8 +463,10 @@ int pic_pair_force_at(pic_ctx* h, int64_t n, const int32_t* dev_cell, const floa
                       int32_t pot_mode, double c_att, double s_rep, float* dev_out)
 {
     if (!h || n < 0 || (n > 0 && (!dev_cell || !dev_fx || !dev_fz || !dev_out))) return PIC_EINVAL;
-    if (pot_mode != 0 && pot_mode != 1) return PIC_EINVAL;
+    if (pot_mode < 0 || pot_mode > 2) return PIC_EINVAL;
     Ctx& c = h->c;
+    if (pot_mode == 2 && !(c.cfg.morse_a > 0 && c.cfg.morse_a < 1e3)) return PIC_EINVAL;
+    if (pot_mode == 2) c_att = c.cfg.morse_a;
     if (c.dims == 3) return PIC_ESTATE;
     if (c.sticky) return c.sticky;
     launch_pair_force_probe(c, n, dev_cell, dev_fx, dev_fz, pot_mode, c_att, s_rep, dev_out, c.stream);

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kEBlock) k_energy(const EnergyArgs a)
                     const float inv43 = fast_rcp(n * cr);
                     float e = pair_energy_axis(cr, inv43, dnx, a.h_coef, a.pot_mode, a.c_att, a.s_rep) +
                               pair_energy_axis(cr, inv43, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep) +
-                              2.0f * branch(a.pot_mode, a.c_att, a.s_rep, cr) * lj_U_inv(cr);
+                              2.0f * pair_U(a.pot_mode, a.c_att, a.s_rep, cr);
                     pe += (double)e;
                 }
             }
@@ -112,7 +112,7 @@ void launch_energy(Ctx& c, cudaStream_t st, double* host_out5)
     a.rho = c.rho[c.cur];
     a.rho_s = (float)c.rho_scale;
     a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
-    a.c_att = (float)c.cfg.c_att;
+    a.c_att = pot_param(c.cfg);
     a.s_rep = (float)c.cfg.s_rep;
     a.pot_mode = c.cfg.pot_mode;
     a.partials = c.partials;
@@ -244,7 +244,7 @@ extern "C" int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* i
     a.rho = reinterpret_cast<const u64*>(in->rho);
     a.rho_s = (float)rho_scale;
     a.h_coef = (float)(r0 / (6.0 * cfg->dx));
-    a.c_att = (float)cfg->c_att;
+    a.c_att = pot_param(*cfg);
     a.s_rep = (float)cfg->s_rep;
     a.pot_mode = cfg->pot_mode;
     a.partials = scratch;    // every block overwrites its own record: nothing to clear

@@ -529,7 +529,7 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     a.cdt_dx = (float)(kC * c.dt / c.cfg.dx);
     a.rho_s = (float)c.rho_scale;
     a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
-    a.c_att = (float)c.cfg.c_att;
+    a.c_att = pot_param(c.cfg);
     a.s_rep = (float)c.cfg.s_rep;
     for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
     a.rho_cur = c.rho[c.cur];
@@ -631,7 +631,7 @@ void launch_pair_force3(Ctx& c, float* out, cudaStream_t st)
     if (S.n == 0) return;
     k_pair_force3<<<grid3(c, S.n), 256, 0, st>>>(S.a.cell, S.a.fx, S.a.fy, S.a.fz, S.n, geo_of(c), c.rho[c.cur],
                                                   (float)c.rho_scale, (float)(c.r0 / (6.0 * c.cfg.dx)),
-                                                  c.cfg.pot_mode, (float)c.cfg.c_att, (float)c.cfg.s_rep,
+                                                  c.cfg.pot_mode, pot_param(c.cfg), (float)c.cfg.s_rep,
                                                   (float)(c.D / c.r0), out);
 }
 
@@ -869,7 +869,7 @@ void launch_energy3(Ctx& c, cudaStream_t st, double* host_out5)
     const int nb = c.nsm * 4;
     k_energy3<<<nb, 256, 0, st>>>(sp[0], sp[1], c.sp[0].n, c.nsp > 1 ? c.sp[1].n : 0, c.nsp, geo_of(c), c.F[0], c.F[1],
                                   c.F[2], c.F[3], c.F[4], c.F[5], c.rho[c.cur], (float)c.rho_scale,
-                                  (float)(c.r0 / (6.0 * c.cfg.dx)), c.cfg.pot_mode, (float)c.cfg.c_att,
+                                  (float)(c.r0 / (6.0 * c.cfg.dx)), c.cfg.pot_mode, pot_param(c.cfg),
                                   (float)c.cfg.s_rep, c.partials);
     k_energy3_final<<<1, 256, 0, st>>>(c.partials, nb, c.red_out);
     double raw[5];

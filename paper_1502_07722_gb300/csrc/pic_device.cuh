@@ -51,6 +51,44 @@ __device__ __forceinline__ float branch(int pot_mode, float c_att, float s_rep, 
     return pot_mode == 0 ? 1.0f : (inv > 1.0f ? s_rep : c_att);
 }
 
+// Morse potential (pot_mode 2; the paper's mapping of density to neighbour distance takes any pair
+// potential): U = E^2 - 2E, E = exp(-a (r - 1)), units D with r in r0; minimum -1 at r = 1 like
+// Eq. (3). The pair functions below take the stiffness a in their c_att argument.
+__device__ __forceinline__ float morse_U_inv(float inv, float a)
+{
+    const float e = expf(-a * (1.0f / inv - 1.0f));
+    return e * (e - 2.0f);
+}
+__device__ __forceinline__ float morse_dU_inv(float inv, float a)    // U'(r), units D / r0
+{
+    const float e = expf(-a * (1.0f / inv - 1.0f));
+    return 2.0f * a * e * (1.0f - e);
+}
+
+// Eq. (3)'s force difference for the Morse form: with both neighbours finite
+//   U'(r+) - U'(r-) = 2a (E+ - E-) (1 - E+ - E-),  E+ - E- = E- expm1(-a (r+ - r-)),
+//   r+ - r- = 2h / (c (1 - h^2)),
+// free of cancellation. Kept out of line: the Lennard-Jones instances keep their code size.
+static __device__ __noinline__ float morse_axis(float c, float h, float a)
+{
+    const float ip = c * (1.0f - h), im = c * (1.0f + h);
+    if (ip > 0.0f && im > 0.0f) {
+        const float ep = expf(-a * (1.0f / ip - 1.0f)), em = expf(-a * (1.0f / im - 1.0f));
+        const float dr = 2.0f * h / (c * (1.0f - h * h));
+        return 2.0f * a * em * expm1f(-a * dr) * (1.0f - ep - em);
+    }
+    float f = 0.0f;
+    if (ip > 0.0f) f += morse_dU_inv(ip, a);
+    if (im > 0.0f) f -= morse_dU_inv(im, a);
+    return f;
+}
+
+// Pair energy U(r) (units D) of one neighbour at r0 / r = inv under pot_mode.
+__device__ __forceinline__ float pair_U(int pot_mode, float c_att, float s_rep, float inv)
+{
+    return pot_mode == 2 ? morse_U_inv(inv, c_att) : branch(pot_mode, c_att, s_rep, inv) * lj_U_inv(inv);
+}
+
 // Dimensionless pair force along one axis (units D / r0) on an atom at local density n (> 0)
 // with c = n^(1/3) and gradient dn along that axis.
 //   Eq. (1): g = d rbar / dx = -(1/3) (r0 / dx) n^(-4/3) dn;  h = g / 2
@@ -66,6 +104,7 @@ __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float 
                                            int pot_mode, float c_att, float s_rep)
 {
     float h = -h_coef * dn * inv43;
+    if (pot_mode == 2) return morse_axis(c, h, c_att);
     float ip = c * (1.0f - h);      // r0 / dist to the neighbour on the + side
     float im = c * (1.0f + h);      // r0 / dist to the neighbour on the - side
     if (ip > 0.0f && im > 0.0f) {
@@ -101,8 +140,8 @@ __device__ __forceinline__ float pair_energy_axis(float c, float inv43, float dn
     float h = -h_coef * dn * inv43;
     float ip = c * (1.0f - h), im = c * (1.0f + h);
     float e = 0.0f;
-    if (ip > 0.0f) e += branch(pot_mode, c_att, s_rep, ip) * lj_U_inv(ip);
-    if (im > 0.0f) e += branch(pot_mode, c_att, s_rep, im) * lj_U_inv(im);
+    if (ip > 0.0f) e += pair_U(pot_mode, c_att, s_rep, ip);
+    if (im > 0.0f) e += pair_U(pot_mode, c_att, s_rep, im);
     return e;
 }
 

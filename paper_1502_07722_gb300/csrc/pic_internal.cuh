@@ -53,6 +53,10 @@ struct Species {
     double mass, uth;
 };
 
+// The second parameter of the device pair functions: the Morse stiffness for pot_mode 2, the
+// attractive factor of the altered potential otherwise (the functions take it as c_att).
+inline float pot_param(const pic_config& cfg) { return (float)(cfg.pot_mode == 2 ? cfg.morse_a : cfg.c_att); }
+
 // Everything a kernel of the step needs, passed by value.
 struct StepArgs {
     int32_t nx, nz, T, ntx, ntz, ntiles, W;   // W: window edge (nodes) of a tile

@@ -73,8 +73,9 @@ def test_init3_matches_oracle(gb):
     assert np.array_equal(sim.get_density().cpu().numpy(), orc.get_rho())
 
 
-def test_density3_and_pair_force(gb):
-    w = w3(max_particles=6000)
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0)], ids=["lj", "morse"])
+def test_density3_and_pair_force(gb, pot):
+    w = w3(max_particles=6000, **pot)
     sim = gb.Simulation(w)
     orc = oracle.Oracle3D(w, with_particles=False)
     x, y, z, u = random_state(1, 14, 12, 16, 8, 3000, 1e-4)
@@ -155,8 +156,9 @@ def test_energy3_matches_oracle(gb):
     assert eg["kinetic_electron"] == pytest.approx(eo["kinetic_electron"], rel=1e-3)
 
 
-def test_transport3_steps(gb):
-    w = w3(mode=1, ion_charge=0.0, ppc_electron=0, laser_profile=0, dt_override=12e-15, T_ion_K=3000.0)
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0)], ids=["lj", "morse"])
+def test_transport3_steps(gb, pot):
+    w = w3(mode=1, ion_charge=0.0, ppc_electron=0, laser_profile=0, dt_override=12e-15, T_ion_K=3000.0, **pot)
     sim = gb.Simulation(w)
     orc = oracle.Oracle3D(w)
     sim.step(20)

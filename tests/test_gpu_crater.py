@@ -189,6 +189,39 @@ def test_c_att_calibration_matches_oracle(gb):
     sim.close()
 
 
+def test_morse_probe_forces_match_oracle(gb):
+    """Probe forces of the Morse form (pot_mode 2, a = 4) around the surface of a transport slab
+    against the oracle's force on atoms at the same positions over the same node sums, and the
+    context's own stiffness used when the configuration is L-J; tolerance as for the pair force."""
+    w = dict(workload("transport"), nx=32, nz=30, slab_k=16, ppc_ion=8, pot_mode=2, morse_a=4.0)
+    sim = gb.Simulation(w)
+    rho = sim.get_density().cpu().numpy()
+    rng = np.random.default_rng(3)
+    n = 600
+    x = rng.uniform(0, 32, n)
+    z = rng.uniform(8, 19.999, n)
+    i, k = np.floor(x).astype(np.int64), np.floor(z).astype(np.int64)
+    fx, fz = (x - i).astype(np.float32), (z - k).astype(np.float32)
+    cell = (k * 32 + i).astype(np.int32)
+    Fg = sim.pair_force_at(cell, fx, fz).cpu().numpy().astype(np.float64)
+    orc = oracle.Oracle(w, with_particles=False)
+    zeros = np.zeros(n)
+    orc.set_particles(0, i + fx.astype(np.float64), k + fz.astype(np.float64), zeros, zeros, zeros)
+    orc.set_rho(rho)
+    Fo = orc.pair_force()
+    scale = np.abs(Fo).max()
+    assert scale > 0
+    assert (np.abs(Fg - Fo) <= 1e-5 * np.abs(Fo) + 1e-5 * scale).all(), np.abs(Fg - Fo).max() / scale
+    assert not Fg[:, 1].any()
+    sim.close()
+    # an L-J context has no Morse stiffness to lend
+    lj = gb.Simulation(dict(w, pot_mode=0, morse_a=0.0))
+    with pytest.raises(gb.PicError) as e:
+        lj.pair_force_at(cell[:4], fx[:4], fz[:4], pot_mode=2)
+    assert e.value.code == gb.PIC_EINVAL
+    lj.close()
+
+
 def _laser_stage(gb, steps=120):
     w = dict(workload("tiny"), nx=48, nz=40, slab_k=20, ppc_ion=12, ppc_electron=12, I0=3e19,
              t_peak=30 * 2.24072e-17, sort_every=20)
@@ -299,7 +332,9 @@ def test_new_entry_points_refuse_bad_arguments(gb):
         lambda: gb.pic_pair_force_at(sim.h, -1, idx.data_ptr(), half.data_ptr(), half.data_ptr(), 0, 1.0, 1.0,
                                      out.data_ptr()),                                 # n < 0
         lambda: gb.pic_pair_force_at(sim.h, 1, idx.data_ptr(), half.data_ptr(), half.data_ptr(), 2, 1.0, 1.0,
-                                     out.data_ptr()),                                 # pot_mode 2
+                                     out.data_ptr()),                                 # Morse, no stiffness
+        lambda: gb.pic_pair_force_at(sim.h, 1, idx.data_ptr(), half.data_ptr(), half.data_ptr(), 3, 1.0, 1.0,
+                                     out.data_ptr()),                                 # pot_mode 3
         lambda: gb.pic_pair_force_at(sim.h, 1, 0, half.data_ptr(), half.data_ptr(), 0, 1.0, 1.0,
                                      out.data_ptr()),                                 # NULL cells
         lambda: gb.pic_cell_temperature(sim.h, 0, 0, out.data_ptr()),                  # NULL scratch

@@ -98,12 +98,14 @@ def test_deposit_density_bit_exact(shape):
     assert scale == pytest.approx(orc.weight / (2 ** 32 * w["dx"] ** 2), rel=1e-15)
 
 
-def test_pair_force_matches_oracle():
-    """Eqs. (1)-(3) on a perturbed slab with a free surface. Tolerance: 1e-5 relative, plus an
-    absolute floor of 1e-5 of the largest force for atoms whose force is a near-cancellation
-    (FP32 rounding of the node densities, ~6e-8 relative, limits those)."""
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0)], ids=["lj", "morse"])
+def test_pair_force_matches_oracle(pot):
+    """Eqs. (1)-(3) on a perturbed slab with a free surface, with Eq. (3) and with the Morse form.
+    Tolerance: 1e-5 relative, plus an absolute floor of 1e-5 of the largest force for atoms whose
+    force is a near-cancellation (FP32 rounding of the node densities, ~6e-8 relative, limits
+    those)."""
     nx, nz = 48, 40
-    w = workload("tiny", nx=nx, nz=nz, slab_k=20, max_particles=20000)
+    w = workload("tiny", nx=nx, nz=nz, slab_k=20, max_particles=20000, **pot)
     sim = gb().Simulation(w)
     orc = oracle.Oracle(w, with_particles=False)
     d = inputs.slab_particles(21, nx, nz, 20, 8, 1e-4, clump=0.25)
@@ -194,12 +196,14 @@ def test_one_step_full_mode(seed):
         np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
 
 
-@pytest.mark.parametrize("pot", [{}, dict(pot_mode=1, c_att=0.65, s_rep=2.5)])
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=1, c_att=0.65, s_rep=2.5), dict(pot_mode=2, morse_a=4.0)],
+                         ids=["lj", "altered", "morse"])
 def test_one_step_transport_mode(pot):
-    """One transport step (pair force only) against the oracle, with Eq. (3) as printed and with
-    the altered potential (attractive and repulsive branches scaled). The altered force changes its
-    factor at a neighbour distance of r0: a distance within FP32 rounding of r0 can fall on the
-    other branch than in FP64, so there isolated momenta differ at up to ~1e-4 (2e-4 bound)."""
+    """One transport step (pair force only) against the oracle, with Eq. (3) as printed, with
+    the altered potential (attractive and repulsive branches scaled) and with the Morse form. The
+    altered force changes its factor at a neighbour distance of r0: a distance within FP32
+    rounding of r0 can fall on the other branch than in FP64, so there isolated momenta differ at
+    up to ~1e-4 (2e-4 bound)."""
     nx, nz, sk = 40, 30, 15
     w = workload("transport", nx=nx, nz=nz, slab_k=sk, max_particles=nx * sk * 16, **pot)
     sim = gb().Simulation(w, sort_every=0)
@@ -208,14 +212,16 @@ def test_one_step_transport_mode(pot):
     g0 = set_both(sim, orc, 0, d)
     sim.step(1)
     orc.step(1)
-    _compare_particles(sim.get_particles(0), orc.get_particles(0), g0, nx, rtol=2e-4 if pot else 1e-5)
+    _compare_particles(sim.get_particles(0), orc.get_particles(0), g0, nx,
+                       rtol=2e-4 if pot.get("pot_mode") == 1 else 1e-5)
     x1, z1, _ = to_global(sim.get_particles(0), nx)
     assert np.array_equal(sim.get_density().cpu().numpy(), oracle.deposit_density(nx, nz, x1, z1))
 
 
-def test_energy_matches_oracle():
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0)], ids=["lj", "morse"])
+def test_energy_matches_oracle(pot):
     nx, nz, sk = 48, 40, 20
-    w = workload("tiny", nx=nx, nz=nz, slab_k=sk, max_particles=nx * sk * 8)
+    w = workload("tiny", nx=nx, nz=nz, slab_k=sk, max_particles=nx * sk * 8, **pot)
     sim = gb().Simulation(w)
     orc = oracle.Oracle(w, with_particles=False)
     ions, els, fields = _random_state(nx, nz, sk, 51, w)
@@ -329,15 +335,17 @@ def test_transport_1000_steps_energy_drift_and_profile():
     assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-3
 
 
-def test_transport_acoustic_wave_period():
+@pytest.mark.parametrize("pot,curv", [({}, 72.0), (dict(pot_mode=2, morse_a=4.0), 32.0)], ids=["lj", "morse"])
+def test_transport_acoustic_wave_period(pot, curv):
     """The GPU transport stage carries a small standing acoustic wave (64-cell wavelength, strain
-    1e-3) with the period of the linearised Eqs. (1)-(3), lambda / sqrt(24 D / m), over 2.5
-    periods (8300 steps), like the oracle."""
+    1e-3) with the period of the linearised Eqs. (1)-(3), lambda / sqrt(U''(r0) r0^2 / (3 m)),
+    over 2.5 periods (8300 steps for Eq. 3, U''(r0) r0^2 = 72 D; 12 450 for the Morse form with
+    a = 4, 2 a^2 D = 32 D), like the oracle."""
     import math
     nx, nz = 64, 4
     dt = 50e-15
     w = workload("transport", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, T_ion_K=0.0, dt_override=dt,
-                 max_particles=nx * nz * 4)
+                 max_particles=nx * nz * 4, **pot)
     sim = gb().Simulation(w, sort_every=0)
     cells = np.arange(nx * nz)
     i, k = cells % nx, cells // nx
@@ -353,7 +361,7 @@ def test_transport_acoustic_wave_period():
     xg, _, _ = to_global(g, nx)
     xeq = np.round((xg - 0.25) * 2) / 2 + 0.25  # nearest lattice site (0.25 + multiples of 0.5)
     m = 63.546 * 1.66053906660e-27
-    period = (nx * w["dx"]) / math.sqrt(24 * 0.41 * 1.602176634e-19 / m)
+    period = (nx * w["dx"]) / math.sqrt(curv * 0.41 * 1.602176634e-19 / (3 * m))
     amps = []
     chunk = 20
     for s in range(0, int(2.5 * period / dt), chunk):
