@@ -249,7 +249,7 @@ PIC_API int pic_get_timing(pic_ctx* ctx, double ms[3], int64_t n[4]);
 
 /* ---- batched intensity sweep --------------------------------------------------------------
  * Several independent slabs (sizes, particle counts, intensities and seeds may differ; all in the
- * same mode) advanced together: per step one persistent particle-kernel launch over the tiles of
+ * same mode, and either all or none with the Morse potential) advanced together: per step one persistent particle-kernel launch over the tiles of
  * every slab and one launch per field kernel for all slabs, recorded once as a CUDA graph and
  * replayed. Each slab is an ordinary context (pic_batch_slab) for reading and writing state,
  * energies and forces; pic_step on such a context returns PIC_ESTATE (step the batch instead).

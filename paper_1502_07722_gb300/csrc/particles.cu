@@ -161,7 +161,7 @@ enum Kind { kIon = 0, kElectron = 1, kAtom = 2 };
 //   kIon:      Lorentz force + pair force, current (charge +e), node density
 //   kElectron: Lorentz force, current (charge -e)
 //   kAtom:     pair force, node density (neutral atoms of the transport stage)
-template <int KIND>
+template <int KIND, int POT>
 __device__ __forceinline__ void process_particle(const StepArgs& a, const Species& S, const Window& w, int& cell,
                                                  float& fx_io, float& fz_io, float& ux, float& uy, float& uz)
 {
@@ -222,7 +222,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     }
     if (kPair) {
         float pfx, pfz;
-        pair_force_xz(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz);
+        pair_force_xz<false, POT>(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz);
         kx += S.p_kick * pfx;
         kz += S.p_kick * pfz;
     }
@@ -320,7 +320,7 @@ __device__ __forceinline__ int part_start(int p0, int p1, int sub, int nsub)
     return p0 + (int)(((long long)(p1 - p0) * sub) / nsub);
 }
 
-template <bool FULL>
+template <bool FULL, int POT>
 __device__ __forceinline__ void run_tile(const StepArgs& a, int t, int sub, int nsub)
 {
     extern __shared__ unsigned smem[];
@@ -372,8 +372,8 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t, int sub, int 
             for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock) {
                 int cell = S.a.cell[p];
                 float fx = S.a.fx[p], fz = S.a.fz[p], ux = S.a.ux[p], uy = S.a.uy[p], uz = S.a.uz[p];
-                if (s == 0) process_particle<FULL ? kIon : kAtom>(a, S, w, cell, fx, fz, ux, uy, uz);
-                else process_particle<kElectron>(a, S, w, cell, fx, fz, ux, uy, uz);
+                if (s == 0) process_particle<FULL ? kIon : kAtom, POT>(a, S, w, cell, fx, fz, ux, uy, uz);
+                else process_particle<kElectron, POT>(a, S, w, cell, fx, fz, ux, uy, uz);
                 S.a.cell[p] = cell;
                 S.a.fx[p] = fx;
                 S.a.fz[p] = fz;
@@ -386,10 +386,10 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t, int sub, int 
     }
 }
 
-template <bool FULL>
+template <bool FULL, int POT>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles(const StepArgs a, int nsub)
 {
-    for (int g = blockIdx.x; g < a.ntiles * nsub; g += gridDim.x) run_tile<FULL>(a, g / nsub, g % nsub, nsub);
+    for (int g = blockIdx.x; g < a.ntiles * nsub; g += gridDim.x) run_tile<FULL, POT>(a, g / nsub, g % nsub, nsub);
 }
 
 // Arguments of the simulations of a batch for the current step, in constant memory: the slab
@@ -402,14 +402,14 @@ __constant__ int c_tile_base[kMaxBatchSlabs + 1];
 
 // All simulations of a batch in one persistent launch: the tiles of every simulation form one
 // work list (c_tile_base[s] = first global tile of simulation s).
-template <bool FULL>
+template <bool FULL, int POT>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles_batch(int nslab, int total, int nsub)
 {
     for (int g = blockIdx.x; g < total * nsub; g += gridDim.x) {
         const int tile = g / nsub;
         int s = 0;
         while (s + 1 < nslab && c_tile_base[s + 1] <= tile) s++;
-        run_tile<FULL>(c_batch_args[s], tile - c_tile_base[s], g % nsub, nsub);
+        run_tile<FULL, POT>(c_batch_args[s], tile - c_tile_base[s], g % nsub, nsub);
     }
 }
 
@@ -430,11 +430,12 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        cudaFuncSetAttribute(k_particles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-        cudaFuncSetAttribute(k_particles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
         // the largest carve-out, so that several CTAs fit on one SM
-        cudaFuncSetAttribute(k_particles<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_particles<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        for (const void* k : {(const void*)k_particles<true, kPotLJ>, (const void*)k_particles<false, kPotLJ>,
+                              (const void*)k_particles<true, kPotMorse>, (const void*)k_particles<false, kPotMorse>}) {
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
         configured[dev].store(shmem);
     }
     const int cap = c.nsm * kCtasPerSm;
@@ -442,14 +443,17 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
     int grid = a.ntiles * nsub;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    if (a.full) k_particles<true><<<grid, kBlock, shmem, st>>>(a, nsub);
-    else k_particles<false><<<grid, kBlock, shmem, st>>>(a, nsub);
+    const bool morse = a.pot_mode == 2;
+    if (a.full && !morse) k_particles<true, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub);
+    else if (!morse) k_particles<false, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub);
+    else if (a.full) k_particles<true, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub);
+    else k_particles<false, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub);
 }
 
 int max_batch_slabs() { return kMaxBatchSlabs; }
 
 void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
-                                int full, int maxW, int nsm, cudaStream_t st)
+                                int full, int morse, int maxW, int nsm, cudaStream_t st)
 {
     cudaMemcpyToSymbolAsync(c_batch_args, args_dev, sizeof(StepArgs) * nslab, 0, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyToSymbolAsync(c_tile_base, tile_base_dev, sizeof(int) * (nslab + 1), 0, cudaMemcpyDeviceToDevice, st);
@@ -459,18 +463,22 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        cudaFuncSetAttribute(k_particles_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-        cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-        cudaFuncSetAttribute(k_particles_batch<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_particles_batch<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        for (const void* k : {(const void*)k_particles_batch<true, kPotLJ>, (const void*)k_particles_batch<false, kPotLJ>,
+                              (const void*)k_particles_batch<true, kPotMorse>,
+                              (const void*)k_particles_batch<false, kPotMorse>}) {
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
         configured[dev].store(shmem);
     }
     const int cap = nsm * kCtasPerSm;
     const int nsub = parts_per_tile(total_tiles, cap);
     int grid = total_tiles * nsub < cap ? total_tiles * nsub : cap;
     if (grid < 1) grid = 1;
-    if (full) k_particles_batch<true><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
-    else k_particles_batch<false><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
+    if (full && !morse) k_particles_batch<true, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
+    else if (!morse) k_particles_batch<false, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
+    else if (full) k_particles_batch<true, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
+    else k_particles_batch<false, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
 }
 
 int tile_window(int T) { return T + 2 * kMargin + 3; }

@@ -334,7 +334,7 @@ __device__ __noinline__ void deposit3_cell(Geo3 g, u64* J0, u64* J1, u64* J2, u6
 // deposits, so that little state is live across the (non-inlined) deposit call. PAIR is a run-time
 // flag (the pair species): one instance of this code serves both species, which keeps the kernel
 // inside the instruction cache.
-template <bool FULL>
+template <bool FULL, int POT>
 __device__ __forceinline__ void process3(const Args3& a, const Species3& S, const Win3& w, const bool PAIR, int p)
 {
     const Geo3& g = a.g;
@@ -378,9 +378,9 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
         if (n > 0.0f) {
             const float c = fast_cbrt(n);
             const float inv43 = fast_rcp(n * c);
-            kx += S.p_kick * pair_axis(n, c, inv43, gr[0], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
-            ky += S.p_kick * pair_axis(n, c, inv43, gr[1], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
-            kz += S.p_kick * pair_axis(n, c, inv43, gr[2], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+            kx += S.p_kick * pair_axis<false, POT>(n, c, inv43, gr[0], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+            ky += S.p_kick * pair_axis<false, POT>(n, c, inv43, gr[1], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+            kz += S.p_kick * pair_axis<false, POT>(n, c, inv43, gr[2], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
         }
     }
     const float ux0 = ux, uy0 = uy, uz0 = uz;
@@ -439,7 +439,7 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
     }
 }
 
-template <bool FULL>
+template <bool FULL, int POT>
 __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const __grid_constant__ Args3 a)
 {
     extern __shared__ unsigned smem3[];
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kBlock3, 3) k_particles3(const __grid_constant
                     prefetch_l1(S.uy + q);
                     prefetch_l1(S.uz + q);
                 }
-                process3<FULL>(a, S, w, S.pair != 0, p);
+                process3<FULL, POT>(a, S, w, S.pair != 0, p);
             }
         }
     }
@@ -558,16 +558,20 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        cudaFuncSetAttribute(k_particles3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-        cudaFuncSetAttribute(k_particles3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-        cudaFuncSetAttribute(k_particles3<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_particles3<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        for (const void* k : {(const void*)k_particles3<true, kPotLJ>, (const void*)k_particles3<false, kPotLJ>,
+                              (const void*)k_particles3<true, kPotMorse>, (const void*)k_particles3<false, kPotMorse>}) {
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
         configured[dev].store(shmem);
     }
     int grid = c.ntiles < c.nsm * 3 ? c.ntiles : c.nsm * 3;
     if (grid < 1) grid = 1;
-    if (a.full) k_particles3<true><<<grid, kBlock3, shmem, st>>>(a);
-    else k_particles3<false><<<grid, kBlock3, shmem, st>>>(a);
+    const bool morse = a.pot_mode == 2;
+    if (a.full && !morse) k_particles3<true, kPotLJ><<<grid, kBlock3, shmem, st>>>(a);
+    else if (!morse) k_particles3<false, kPotLJ><<<grid, kBlock3, shmem, st>>>(a);
+    else if (a.full) k_particles3<true, kPotMorse><<<grid, kBlock3, shmem, st>>>(a);
+    else k_particles3<false, kPotMorse><<<grid, kBlock3, shmem, st>>>(a);
 }
 
 // ---- stand-alone node density and pair force ------------------------------------------------

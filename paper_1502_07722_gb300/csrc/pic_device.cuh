@@ -68,7 +68,8 @@ __device__ __forceinline__ float morse_dU_inv(float inv, float a)    // U'(r), u
 // Eq. (3)'s force difference for the Morse form: with both neighbours finite
 //   U'(r+) - U'(r-) = 2a (E+ - E-) (1 - E+ - E-),  E+ - E- = E- expm1(-a (r+ - r-)),
 //   r+ - r- = 2h / (c (1 - h^2)),
-// free of cancellation. Kept out of line: the Lennard-Jones instances keep their code size.
+// free of cancellation. Kept out of line (only the Morse kernel instances and the run-time
+// dispatch of the diagnostics call it).
 static __device__ __noinline__ float morse_axis(float c, float h, float a)
 {
     const float ip = c * (1.0f - h), im = c * (1.0f + h);
@@ -99,12 +100,19 @@ __device__ __forceinline__ float pair_U(int pot_mode, float c_att, float s_rep, 
 //   F = 24 [ c n^4 P13(h) - c n^2 P7(h) ].
 // ZERO_SKIP: a branch whose factor is 0 contributes nothing even where U' overflows FP32 (a
 // neighbour pulled arbitrarily close at the vacuum edge); the probe calls of the calibration use it.
-template <bool ZERO_SKIP = false>
+// POT: the potential family compiled in. kPotLJ: Eq. (3) and the altered potential (pot_mode 0, 1);
+// kPotMorse: the Morse form only; kPotRuntime: chosen by pot_mode at run time (diagnostics). The
+// particle kernels take kPotLJ or kPotMorse as a template argument, so that the Lennard-Jones
+// instances carry no Morse branch (a uniform run-time branch to the out-of-line Morse call cost
+// 6 % of the 3D particle kernel's time).
+enum { kPotRuntime = -1, kPotLJ = 0, kPotMorse = 2 };
+
+template <bool ZERO_SKIP = false, int POT = kPotRuntime>
 __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float dn, float h_coef,
                                            int pot_mode, float c_att, float s_rep)
 {
     float h = -h_coef * dn * inv43;
-    if (pot_mode == 2) return morse_axis(c, h, c_att);
+    if (POT == kPotMorse || (POT == kPotRuntime && pot_mode == 2)) return morse_axis(c, h, c_att);
     float ip = c * (1.0f - h);      // r0 / dist to the neighbour on the + side
     float im = c * (1.0f + h);      // r0 / dist to the neighbour on the - side
     if (ip > 0.0f && im > 0.0f) {
@@ -253,7 +261,7 @@ namespace gbpic {
 
 // Pair-potential half kick components (units D / r0) along x and z at local density n (units
 // n0) with gradient (dnx, dnz) per cell: Eqs. (1)-(3) via pair_axis.
-template <bool ZERO_SKIP = false>
+template <bool ZERO_SKIP = false, int POT = kPotRuntime>
 __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, float h_coef, int pot_mode, float c_att,
                                               float s_rep, float& fx, float& fz)
 {
@@ -262,8 +270,8 @@ __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, flo
     if (n > 0.0f) {
         const float c = fast_cbrt(n);
         const float inv43 = fast_rcp(n * c);
-        fx = pair_axis<ZERO_SKIP>(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
-        fz = pair_axis<ZERO_SKIP>(n, c, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
+        fx = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
+        fz = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
     }
 }
 

@@ -169,7 +169,7 @@ void launch_fields_batch(const FieldArgs* fa_dev, const AntennaParams* ap_dev, l
 FieldArgs make_field_args(const Ctx& c);
 AntennaParams make_antenna_params(const Ctx& c);
 void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
-                                int full, int maxW, int nsm, cudaStream_t st);
+                                int full, int morse, int maxW, int nsm, cudaStream_t st);
 size_t particle_smem_bytes(int W);
 void launch_particle_step3(Ctx& c, cudaStream_t st);
 void launch_deposit_density3(Ctx& c, u64* out, cudaStream_t st);
