@@ -52,6 +52,12 @@ def test_workspace_size_and_validation(lib):
         gb.pic_workspace_size(gb.make_config(workload("tiny"), dims=3, ny=2))
     with pytest.raises(gb.PicError):
         gb.pic_workspace_size(gb.make_config(workload("tiny"), dims=4))
+    # a batch runs one particle-kernel instance: all slabs Morse or none
+    lj, mo = gb.make_config(workload("tiny")), gb.make_config(workload("tiny"), pot_mode=2, morse_a=3.0)
+    assert gb.pic_batch_workspace_size([mo, mo]) > 0
+    with pytest.raises(gb.PicError) as e:
+        gb.pic_batch_workspace_size([lj, mo])
+    assert e.value.code == gb.PIC_EINVAL
     # transport mode: neutral atoms only
     gb.pic_workspace_size(gb.make_config(workload("transport")))
     with pytest.raises(gb.PicError):

@@ -61,11 +61,13 @@ def _state(sim):
             [_multiset(sim, s) for s in range(sim.nspecies)])
 
 
-@pytest.mark.parametrize("timing", [False, True])
-def test_batch_equals_single_runs(gb, timing):
+@pytest.mark.parametrize("timing,pot", [(False, {}), (True, {}), (False, dict(pot_mode=2, morse_a=3.0))],
+                         ids=["graph", "timing", "morse"])
+def test_batch_equals_single_runs(gb, timing, pot):
     """Every slab of a batch ends with the same grids (bit for bit) and the same particles as the
-    same slab run alone (graph replay and the direct-launch timing path alike), across cell sorts."""
-    ws = small_sweep()
+    same slab run alone (graph replay and the direct-launch timing path alike, and with the Morse
+    instance of the batched kernel), across cell sorts."""
+    ws = [dict(w, **pot) for w in small_sweep()]
     batch = gb.Batch(ws, sort_every=3)
     if timing:
         gb.pic_batch_set_timing(batch.b, True)
