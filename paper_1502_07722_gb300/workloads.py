@@ -73,6 +73,11 @@ WORKLOADS = {
                    I0=0.0, w0=0.0, t_peak=0.0, temp_profile=1, T_spot_K=20000.0, spot_w=1e-6,
                    spot_depth=80e-9, seed=8, steps=250000),
 }
+# the same crater run with the Morse form of the pair force (pot_mode 2): stiffness
+# a = alpha r0 = 1.3588 / A x 2.2744 A = 3.09, alpha from Girifalco and Weizer's copper Morse fit
+# (Phys. Rev. 114, 687 (1959); not from the paper), r0 the cubic-lattice spacing at n0, depth D
+# as for Eq. (3)
+WORKLOADS["crater_morse"] = dict(WORKLOADS["crater"], pot_mode=2, morse_a=3.09)
 
 
 def workload(name: str, **overrides) -> dict:

@@ -60,6 +60,7 @@ def test_workspace_size_and_validation(lib):
     assert e.value.code == gb.PIC_EINVAL
     # transport mode: neutral atoms only
     gb.pic_workspace_size(gb.make_config(workload("transport")))
+    gb.pic_workspace_size(gb.make_config(workload("crater_morse")))
     with pytest.raises(gb.PicError):
         gb.pic_workspace_size(gb.make_config(workload("transport"), ion_charge=1.0))
 
