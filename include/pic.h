@@ -308,7 +308,8 @@ typedef struct pic_state_view {
  * cfg: the configuration the state belongs to (physical constants). in: device pointers.
  * dev_out5: device double[5] receiving kinetic_ion, kinetic_electron, field_E, field_B, pair
  * (J per metre of y). Work is queued on stream; the call does not synchronise. Refuses (PIC_EINVAL)
- * particle counts above 2^31 - 1, grids outside 3 <= nx, 4 <= nz < 32768, and missing pointers. */
+ * particle counts above 2^31 - 1, grids outside 3 <= nx, 4 <= nz < 32768, missing pointers and
+ * a pot_mode outside 0..2 (2 without 0 < morse_a < 1000). */
 PIC_API int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* in, double* dev_out5, void* stream);
 
 /* ---- checkpoint / resume ------------------------------------------------------------------

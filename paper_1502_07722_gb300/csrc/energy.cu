@@ -200,6 +200,8 @@ extern "C" int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* i
     if (cfg->nx < 3 || cfg->nz < 4 || cfg->nx >= 32768 || cfg->nz >= 32768) return PIC_EINVAL;
     if (cfg->mode != PIC_MODE_FULL && cfg->mode != PIC_MODE_TRANSPORT) return PIC_EINVAL;
     if (!(cfg->dx > 0) || !(cfg->n_atoms > 0) || !(cfg->ion_mass_amu > 0) || cfg->ppc_ion <= 0) return PIC_EINVAL;
+    if (cfg->pot_mode < 0 || cfg->pot_mode > 2) return PIC_EINVAL;
+    if (cfg->pot_mode == 2 && !(cfg->morse_a > 0 && cfg->morse_a < 1e3)) return PIC_EINVAL;
     const int nsp = cfg->mode == PIC_MODE_FULL ? 2 : 1;
     for (int s = 0; s < nsp; s++) {
         // sizes beyond what the kernels index with 32-bit cells are refused

@@ -47,11 +47,12 @@ def _view(gb, sim):
     return v, keep
 
 
-@pytest.mark.parametrize("name", ["tiny", "transport"])
-def test_noalloc_energy_equals_pic_energy_twice(gb, name):
+@pytest.mark.parametrize("name,pot", [("tiny", {}), ("transport", {}), ("transport", dict(pot_mode=2, morse_a=3.0))],
+                         ids=["tiny", "transport", "transport-morse"])
+def test_noalloc_energy_equals_pic_energy_twice(gb, name, pot):
     """Same five energies as pic_energy (same kernels, same summation order), on two calls in a
     row; the output is poisoned before each call so that each call must write all of it."""
-    w = workload(name, nx=48, nz=40, slab_k=20)
+    w = workload(name, nx=48, nz=40, slab_k=20, **pot)
     sim = gb.Simulation(w)
     sim.step(4)
     ref = sim.energy()
@@ -89,3 +90,19 @@ def test_noalloc_energy_refuses_bad_sizes(gb):
     v.rho = 256
     assert lib.pic_energy_noalloc(ctypes.byref(cfg), ctypes.byref(v), out, None) == gb.PIC_EINVAL
     assert lib.pic_energy_noalloc(ctypes.byref(cfg), ctypes.byref(v), None, None) == gb.PIC_EINVAL
+
+
+def test_noalloc_energy_refuses_unknown_potentials(gb):
+    """A pot_mode outside 0..2, or the Morse form without a stiffness, is refused (the view points
+    at a live context's buffers, so nothing else would stop the call)."""
+    w = workload("transport", nx=48, nz=40, slab_k=20)
+    sim = gb.Simulation(w)
+    view, keep = _view(gb, sim)
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
+    lib = gb.load_library()
+    for bad in (dict(pot_mode=3), dict(pot_mode=-1), dict(pot_mode=2, morse_a=0.0)):
+        cfg = gb.make_config(w, **bad)
+        assert lib.pic_energy_noalloc(ctypes.byref(cfg), ctypes.byref(view), out.data_ptr(), None) == gb.PIC_EINVAL
+    torch.cuda.synchronize()
+    del keep
+    sim.close()
