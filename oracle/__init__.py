@@ -45,7 +45,7 @@ class OracleConfig(ctypes.Structure):
         ("s_rep", ctypes.c_double), ("lambda_", ctypes.c_double), ("I0", ctypes.c_double),
         ("tau_fwhm", ctypes.c_double), ("w0", ctypes.c_double), ("t_peak", ctypes.c_double),
         ("seed", ctypes.c_uint64),
-        ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("temp_profile", ctypes.c_int32), ("lattice", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
         ("morse_a", ctypes.c_double),
     ]
@@ -63,7 +63,7 @@ class OracleConfig3(ctypes.Structure):
         ("s_rep", ctypes.c_double), ("lambda_", ctypes.c_double), ("I0", ctypes.c_double),
         ("tau_fwhm", ctypes.c_double), ("w0", ctypes.c_double), ("t_peak", ctypes.c_double),
         ("seed", ctypes.c_uint64),
-        ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("temp_profile", ctypes.c_int32), ("lattice", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
         ("morse_a", ctypes.c_double),
     ]

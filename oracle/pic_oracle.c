@@ -78,7 +78,7 @@ typedef struct {
     double lambda, I0, tau_fwhm, w0, t_peak;   /* laser (m, W/m^2, s, m, s)                  */
     uint64_t seed;
     int32_t temp_profile;    /* 0: uniform T_ion_K; 1: lattice temperature of a laser spot       */
-    int32_t reserved0;
+    int32_t lattice;         /* 0: cubic (the paper's); 1: hexagonal close-packed, c axis along z */
     double T_spot_K, spot_w, spot_depth;       /* K, m (1/e^2 radius), m (1/e depth)         */
     double morse_a;          /* Morse stiffness alpha r0 (pot_mode 2)                           */
 } ocfg;
@@ -171,6 +171,61 @@ double oracle_neighbor_distances(double n, double dn, double r0_dx, double* plus
     *plus = dp > 0.0 ? rbar / dp : INFINITY;
     *minus = dm > 0.0 ? rbar / dm : INFINITY;
     return rbar;
+}
+
+/* Nearest-neighbour directions (unit vectors) and weights of the lattice the atoms are assumed
+ * to form (paper: a cubic lattice, readily replaced by a hexagonal close-packed one).
+ * Cubic: the six axis directions, weight 1. HCP with the ideal axial ratio and the c axis along z:
+ * six neighbours in the basal plane at 60-degree steps from +x (weight 1), and three above and
+ * three below the plane at in-plane radius 1/sqrt(3) and height sqrt(2/3); the two sublattices
+ * place those triples 60 degrees apart and a density field cannot tell them apart, so both
+ * sublattices' twelve out-of-plane directions enter with weight 1/2. Returns the count. */
+static int lattice_dirs(int lattice, double e[18][3], double w[18])
+{
+    int m = 0;
+    if (lattice == 0) {
+        for (int d = 0; d < 3; d++)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                e[m][0] = e[m][1] = e[m][2] = 0.0;
+                e[m][d] = sg;
+                w[m++] = 1.0;
+            }
+        return m;
+    }
+    for (int q = 0; q < 6; q++) {
+        double th = q * O_PI / 3.0;
+        e[m][0] = cos(th); e[m][1] = sin(th); e[m][2] = 0.0; w[m++] = 1.0;
+    }
+    double rin = 1.0 / sqrt(3.0), h = sqrt(2.0 / 3.0);
+    for (int q = 0; q < 6; q++) {                    /* phi = 30, 90, ..., 330 degrees */
+        double ph = O_PI / 6.0 + q * O_PI / 3.0;
+        for (int sg = -1; sg <= 1; sg += 2) {
+            e[m][0] = rin * cos(ph); e[m][1] = rin * sin(ph); e[m][2] = sg * h; w[m++] = 0.5;
+        }
+    }
+    return m;
+}
+
+/* Pair force (units D / r0, per axis) and energy (units D, half the sum of U) of an atom at local
+ * density n (units n0) with density gradient grad (units n0 per cell) on a lattice of directions
+ * e_k: each neighbour sits where Eq. (2), taken along e_k, puts it (rbar over 1 - (grad rbar . e_k)
+ * / 2, from Eq. 1 along e_k), and the force is the sum of w_k U'(r_k) e_k. */
+static void lattice_pair(int lattice, int pm, double ca, double sr, double ma, double n, const double grad[3],
+                         double r0_dx, double F[3], double* u)
+{
+    double e[18][3], w[18];
+    int m = lattice_dirs(lattice, e, w);
+    F[0] = F[1] = F[2] = 0.0;
+    *u = 0.0;
+    for (int k = 0; k < m; k++) {
+        double dn = e[k][0] * grad[0] + e[k][1] * grad[1] + e[k][2] * grad[2];
+        double rk, unused;
+        oracle_neighbor_distances(n, dn, r0_dx, &rk, &unused);
+        if (isinf(rk)) continue;
+        double du = w[k] * pot_dU(pm, ca, sr, ma, rk);
+        for (int d = 0; d < 3; d++) F[d] += du * e[k][d];
+        *u += 0.5 * w[k] * pot_U(pm, ca, sr, ma, rk);
+    }
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -354,6 +409,13 @@ static void pair_force_at(const ostate* s, double x, double z, double F[3], doub
     if (energy) *energy = 0.0;
     if (!(n > 0.0)) return;
     double r0_dx = s->r0 / s->c.dx;
+    if (s->c.lattice == 1) {
+        double grad[3] = {dnx, 0.0, dnz}, Fu[3], u;
+        lattice_pair(1, s->c.pot_mode, s->c.c_att, s->c.s_rep, s->c.morse_a, n, grad, r0_dx, Fu, &u);
+        for (int d = 0; d < 3; d++) F[d] = (s->D / s->r0) * Fu[d];
+        if (energy) *energy = s->D * u;
+        return;
+    }
     double ap, am, bp, bm;
     double rbar = oracle_neighbor_distances(n, dnx, r0_dx, &ap, &am);
     oracle_neighbor_distances(n, dnz, r0_dx, &bp, &bm);
@@ -900,7 +962,7 @@ typedef struct {
     double D_eV, r0, c_att, s_rep, lambda, I0, tau_fwhm, w0, t_peak;
     uint64_t seed;
     int32_t temp_profile;    /* 0: uniform T_ion_K; 1: lattice temperature of a laser spot       */
-    int32_t reserved0;
+    int32_t lattice;
     double T_spot_K, spot_w, spot_depth;
     double morse_a;
 } ocfg3;
@@ -1074,6 +1136,13 @@ static void pair_force3_at(const ostate3* s, double x, double y, double z, doubl
     if (!(n > 0.0)) return;
     double r0_dx = s->r0 / s->c.dx, f_unit = s->D / s->r0, u = 0.0;
     int pm = s->c.pot_mode;
+    if (s->c.lattice == 1) {
+        double Fu[3];
+        lattice_pair(1, pm, s->c.c_att, s->c.s_rep, s->c.morse_a, n, g, r0_dx, Fu, &u);
+        for (int d = 0; d < 3; d++) F[d] = f_unit * Fu[d];
+        if (energy) *energy = s->D * u;
+        return;
+    }
     for (int d = 0; d < 3; d++) {
         double ap, am;
         oracle_neighbor_distances(n, g[d], r0_dx, &ap, &am);

@@ -553,10 +553,12 @@ def test_field_energy_of_uniform_fields():
     assert e["field_B"] == pytest.approx(3 * 0.25 / (2 * mu0) * area, rel=1e-13)
 
 
-@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 3.0}], ids=["lj", "morse"])
-def test_pair_energy_of_equilibrium_lattice(pot):
-    """At the equilibrium density every atom has its six cubic-lattice neighbours at r0:
-    pair energy per atom = (1/2) * 6 * U(r0) = -3 D (both potentials have their minimum -D at r0)."""
+@pytest.mark.parametrize("pot,bonds", [({}, 6), ({"pot_mode": 2, "morse_a": 3.0}, 6), ({"lattice": 1}, 12)],
+                         ids=["lj", "morse", "hcp"])
+def test_pair_energy_of_equilibrium_lattice(pot, bonds):
+    """At the equilibrium density every atom has its nearest neighbours at r0: pair energy per atom
+    = (1/2) * 6 * U(r0) = -3 D on the cubic lattice (both potentials have their minimum -D at r0)
+    and (1/2) * 12 * U(r0) = -6 D on the hexagonal close-packed one."""
     nx, nz = 16, 12
     o = oracle.Oracle(workload("tiny", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, laser_profile=0, **pot),
                       with_particles=False)
@@ -566,7 +568,39 @@ def test_pair_energy_of_equilibrium_lattice(pot):
     z = cell // nx + 0.5
     o.set_particles(0, x, z, np.zeros(n), np.zeros(n), np.zeros(n))
     D = 0.41 * QE
-    assert o.energy()["pair"] == pytest.approx(-3 * D * n * o.weight, rel=1e-12)
+    assert o.energy()["pair"] == pytest.approx(-bonds / 2 * D * n * o.weight, rel=1e-12)
+    F = o.pair_force()
+    assert (not F.any()) if not pot.get("lattice") else np.abs(F).max() < 1e-25   # HCP: directions' rounding
+
+
+@pytest.mark.parametrize("axis", ["x", "z"])
+@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 4.0}], ids=["lj", "morse"])
+def test_hcp_first_order_force_is_twice_the_cubic(axis, pot):
+    """To first order in the gradient each neighbour sits at rbar (1 + (g . e_k) / 2), so
+    F = (1/2) U''(rbar) rbar sum_k w_k e_k (e_k . g). The cubic directions give sum e e^T = 2 I; the
+    ideal HCP's twelve (basal six, three above and three below, sublattices averaged) give 4 I, the
+    same along x and along the c axis z: the HCP force is 2 U''(rbar) rbar g, twice the cubic
+    one, along the gradient, with no component across it."""
+    nx, nz = 16, 16
+    k, i = np.mgrid[0:nz + 1, 0:nx]
+    x, z = 5.3, 7.6
+    out = {}
+    for lat in (0, 1):
+        o = oracle.Oracle(workload("tiny", nx=nx, nz=nz, slab_k=nz, laser_profile=0, lattice=lat, **pot),
+                          with_particles=False)
+        ramp = np.minimum(i, 12) if axis == "x" else np.minimum(k, 12)
+        grid = np.rint((1.1 + 1e-4 * ramp) / o.rho_scale).astype(np.int64)
+        grid[0] //= 2
+        grid[nz] //= 2
+        o.set_particles(0, [x], [z], [0.0], [0.0], [0.0])
+        o.set_rho(grid)
+        out[lat] = o.pair_force()[0]
+        n, dnx, dnz = o.gather_density(x, z)
+    a, b = (0, 2) if axis == "x" else (2, 0)
+    assert out[0][a] != 0.0
+    assert out[1][a] == pytest.approx(2 * out[0][a], rel=2e-3)
+    # the y component: the directions' rounding (~1e-16) times U'(rbar), against a force of first order in g
+    assert abs(out[1][b]) < 1e-3 * abs(out[1][a]) and abs(out[1][1]) < 1e-9 * abs(out[1][a])
 
 
 def test_jy_current_drives_ey():
@@ -606,13 +640,16 @@ def test_injected_energy_of_a_plane_wave_pulse():
     assert e["field_E"] + e["field_B"] <= e["injected"] * 1.01
 
 
-@pytest.mark.parametrize("pot,curv", [({}, 72.0), ({"pot_mode": 2, "morse_a": 4.0}, 32.0)], ids=["lj", "morse"])
+@pytest.mark.parametrize("pot,curv", [({}, 72.0), ({"pot_mode": 2, "morse_a": 4.0}, 32.0), ({"lattice": 1}, 144.0)],
+                         ids=["lj", "morse", "hcp"])
 def test_acoustic_wave_speed_of_the_pair_force(pot, curv):
     """Linearising Eqs. (1)-(3) about the equilibrium lattice (n = n0, rbar = r0) gives the wave
     equation u_tt = (U''(r0) r0^2 / (3 m)) u_xx for a small longitudinal displacement u, with
     U''(r0) r0^2 = 72 D for Eq. (3) (24 D / m) and 2 a^2 D for the Morse form (a = 4: 32 D / (3 m)):
     a standing wave of wavelength 64 cells in the transport mode oscillates with period
-    lambda / sqrt(U''(r0) r0^2 / (3 m)) and keeps its amplitude."""
+    lambda / sqrt(U''(r0) r0^2 / (3 m)) and keeps its amplitude. The HCP lattice doubles the
+    restoring force (second moment of its neighbour directions 4 I against 2 I): an effective
+    144 D, period shorter by sqrt(2)."""
     nx, nz = 64, 4
     dt = 50e-15
     w = workload("transport", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, T_ion_K=0.0, dt_override=dt, **pot)
