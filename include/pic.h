@@ -97,7 +97,13 @@ typedef struct pic_config {
                                 * exp(-2 ((x - nx/2) dx / spot_w)^2) * exp(-(slab_k - z) dx / spot_depth);
                                 in 3D the lateral term takes the radius from the axis,
                                 ((x - nx/2)^2 + (y - ny/2)^2) dx^2 / spot_w^2 */
-    int32_t reserved0;       /* 0 */
+    int32_t lattice;         /* PIC_LATTICE_CUBIC (0): the paper's cubic lattice, six neighbours on the
+                                axes. PIC_LATTICE_HCP (1): hexagonal close-packed (the paper: the method
+                                adapts to it), ideal axial ratio, c axis along z: six basal neighbours,
+                                three above and three below the basal plane, both sublattices' out-of-
+                                plane triples averaged (weight 1/2 each). Eq. (2) along each neighbour
+                                direction e puts it at rbar / (1 - (grad rbar . e) / 2); the force is the
+                                sum of U'(r_e) e. r0 stays the equilibrium nearest-neighbour distance. */
     double T_spot_K;         /* peak temperature on the axis at the surface (K)                  */
     double spot_w;           /* 1/e^2 radius of the lateral Gaussian (m)                          */
     double spot_depth;       /* 1/e depth of the temperature below the surface (m)                */
@@ -107,6 +113,8 @@ typedef struct pic_config {
 
 #define PIC_TEMP_UNIFORM 0
 #define PIC_TEMP_SPOT 1
+#define PIC_LATTICE_CUBIC 0
+#define PIC_LATTICE_HCP 1
 
 typedef struct pic_info {
     double dt;               /* s                                                               */

@@ -21,6 +21,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENAN, PIC_EMOVE, PIC_ESTATE = 0, 
 PIC_MODE_FULL, PIC_MODE_TRANSPORT = 0, 1
 PIC_LASER_NONE, PIC_LASER_PLANE, PIC_LASER_GAUSSIAN = 0, 1, 2
 PIC_TEMP_UNIFORM, PIC_TEMP_SPOT = 0, 1
+PIC_LATTICE_CUBIC, PIC_LATTICE_HCP = 0, 1
 FIELDS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
@@ -37,7 +38,7 @@ class pic_config(ctypes.Structure):
         ("lambda_", ctypes.c_double), ("I0", ctypes.c_double), ("tau_fwhm", ctypes.c_double),
         ("w0", ctypes.c_double), ("t_peak", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("ny", ctypes.c_int32), ("dims", ctypes.c_int32),
-        ("temp_profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("temp_profile", ctypes.c_int32), ("lattice", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
         ("morse_a", ctypes.c_double),
     ]

@@ -63,6 +63,7 @@ int derive_layout(const pic_config* cfg, Layout& L)
     if (cfg->laser_profile == PIC_LASER_GAUSSIAN && !(cfg->w0 > 0)) return PIC_EINVAL;
     if (cfg->pot_mode < 0 || cfg->pot_mode > 2) return PIC_EINVAL;
     if (cfg->pot_mode == 2 && !(cfg->morse_a > 0 && cfg->morse_a < 1e3)) return PIC_EINVAL;
+    if (cfg->lattice != PIC_LATTICE_CUBIC && cfg->lattice != PIC_LATTICE_HCP) return PIC_EINVAL;
     if (cfg->temp_profile != PIC_TEMP_UNIFORM && cfg->temp_profile != PIC_TEMP_SPOT) return PIC_EINVAL;
     if (cfg->temp_profile == PIC_TEMP_SPOT &&
         (!(cfg->spot_w > 0) || !(cfg->spot_depth > 0) || !(cfg->T_spot_K >= 0)))
@@ -197,7 +198,7 @@ StepArgs make_step_args(Ctx& c)
     a.cdt_dx = (float)(kC * c.dt / c.cfg.dx);
     a.rho_s = (float)c.rho_scale;
     a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
-    a.pot_mode = c.cfg.pot_mode;
+    a.pot_mode = pot_code(c.cfg);
     a.c_att = pot_param(c.cfg);
     a.s_rep = (float)c.cfg.s_rep;
     for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
@@ -469,7 +470,8 @@ int pic_pair_force_at(pic_ctx* h, int64_t n, const int32_t* dev_cell, const floa
     if (pot_mode == 2) c_att = c.cfg.morse_a;
     if (c.dims == 3) return PIC_ESTATE;
     if (c.sticky) return c.sticky;
-    launch_pair_force_probe(c, n, dev_cell, dev_fx, dev_fz, pot_mode, c_att, s_rep, dev_out, c.stream);
+    launch_pair_force_probe(c, n, dev_cell, dev_fx, dev_fz, pot_mode | (pot_code(c.cfg) & 4), c_att, s_rep, dev_out,
+                            c.stream);
     CK(cudaGetLastError());
     return PIC_OK;
 }
@@ -815,7 +817,7 @@ int pic_checkpoint_restore(pic_ctx* h, const void* buf, int32_t on_host)
 static int adjoint_ok(const Ctx& c, const pic_adjoint_buffers* b)
 {
     if (c.sticky) return c.sticky;
-    if (c.dims != 2 || c.cfg.sort_every != 0 || c.cfg.pot_mode != 0) return PIC_ESTATE;
+    if (c.dims != 2 || c.cfg.sort_every != 0 || c.cfg.pot_mode != 0 || c.cfg.lattice != 0) return PIC_ESTATE;
     for (int s = 0; s < c.nsp; s++)
         if (!b->lam_pos[s] || !b->lam_u[s]) return PIC_EINVAL;
     if (!b->lam_nodes || !b->grads) return PIC_EINVAL;

@@ -40,7 +40,7 @@ struct pic_batch {
     int n;
     pic_ctx* slab[kMaxSlabs];
     cudaStream_t st;
-    int full, morse, maxW, max_nx, max_nz, total_tiles, nsm, sort_every, steps_since_sort;
+    int full, pot, maxW, max_nx, max_nz, total_tiles, nsm, sort_every, steps_since_sort;
     size_t max_nn;
     int64_t step;
     StepArgs* args_dev;          // [2][n]: parity 0 (density in buffer 0) and parity 1
@@ -92,7 +92,7 @@ void enqueue_step(pic_batch* b, int parity)
     dim3 pg((unsigned)((b->max_nn + 1023) / 1024 > 4096 ? 4096 : (b->max_nn + 1023) / 1024), b->n);
     k_prepare_batch<<<pg, 256, 0, b->st>>>(args);
     if (b->timing) cudaEventRecord(b->ev[0], b->st);
-    launch_particle_step_batch(args, b->tile_base_dev, b->n, b->total_tiles, b->full, b->morse, b->maxW, b->nsm, b->st);
+    launch_particle_step_batch(args, b->tile_base_dev, b->n, b->total_tiles, b->full, b->pot, b->maxW, b->nsm, b->st);
     if (b->timing) cudaEventRecord(b->ev[1], b->st);
     if (b->full)
         launch_fields_batch(b->fargs_dev, b->ap_dev, b->step_dev, b->ant_dev, b->n, b->max_nx, b->max_nz, b->st);
@@ -124,7 +124,8 @@ int pic_batch_workspace_size(const pic_config* cfgs, int32_t n, size_t* bytes)
     size_t t = 0;
     for (int s = 0; s < n; s++) {
         if (cfgs[s].mode != cfgs[0].mode || (cfgs[s].dims != 0 && cfgs[s].dims != 2)) return PIC_EINVAL;
-        if ((cfgs[s].pot_mode == 2) != (cfgs[0].pot_mode == 2)) return PIC_EINVAL;   // one kernel instance
+        if ((cfgs[s].pot_mode == 2) != (cfgs[0].pot_mode == 2) || cfgs[s].lattice != cfgs[0].lattice)
+            return PIC_EINVAL;   // one kernel instance
         size_t b = 0;
         const int r = pic_workspace_size(&cfgs[s], &b);
         if (r) return r;
@@ -170,7 +171,7 @@ int pic_batch_init(const pic_config* cfgs, int32_t n, void* workspace, size_t by
     }
     b->total_tiles = tile_base[n];
     b->full = cfgs[0].mode == PIC_MODE_FULL;
-    b->morse = cfgs[0].pot_mode == 2;
+    b->pot = (cfgs[0].pot_mode == 2 ? 2 : 0) | (cfgs[0].lattice == PIC_LATTICE_HCP ? 4 : 0);   // kernel instance
     b->sort_every = cfgs[0].sort_every;
     b->args_dev = reinterpret_cast<StepArgs*>(p);
     p += a256(sizeof(StepArgs) * 2 * n);

@@ -117,7 +117,7 @@ void launch_pair_force(Ctx& c, float* out, cudaStream_t st)
     if (S.n == 0) return;
     k_pair_force<<<grid_for(c, S.n), 256, 0, st>>>(S.a.cell, S.a.fx, S.a.fz, S.n, c.nx, c.nz, c.rho[c.cur],
                                                    (float)c.rho_scale, (float)(c.r0 / (6.0 * c.cfg.dx)),
-                                                   c.cfg.pot_mode, pot_param(c.cfg), (float)c.cfg.s_rep,
+                                                   pot_code(c.cfg), pot_param(c.cfg), (float)c.cfg.s_rep,
                                                    (float)(c.D / c.r0), out);
 }
 

@@ -431,8 +431,14 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
         // the largest carve-out, so that several CTAs fit on one SM
-        for (const void* k : {(const void*)k_particles<true, kPotLJ>, (const void*)k_particles<false, kPotLJ>,
-                              (const void*)k_particles<true, kPotMorse>, (const void*)k_particles<false, kPotMorse>}) {
+        for (const void* k : {(const void*)k_particles<true, kPotLJ>,
+                              (const void*)k_particles<true, kPotMorse>,
+                              (const void*)k_particles<true, kPotLJ | kLatHcp>,
+                              (const void*)k_particles<true, kPotMorse | kLatHcp>,
+                              (const void*)k_particles<false, kPotLJ>,
+                              (const void*)k_particles<false, kPotMorse>,
+                              (const void*)k_particles<false, kPotLJ | kLatHcp>,
+                              (const void*)k_particles<false, kPotMorse | kLatHcp>}) {
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         }
@@ -443,17 +449,23 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
     int grid = a.ntiles * nsub;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    const bool morse = a.pot_mode == 2;
-    if (a.full && !morse) k_particles<true, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub);
-    else if (!morse) k_particles<false, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub);
-    else if (a.full) k_particles<true, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub);
-    else k_particles<false, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub);
+    // the instance with the potential family (L-J forms or Morse) and the lattice compiled in
+    switch ((((a.pot_mode & 3) == 2 ? kPotMorse : kPotLJ) | (a.pot_mode & kLatHcp)) | (a.full ? 8 : 0)) {
+    case 8 | kPotLJ: k_particles<true, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    case 8 | kPotMorse: k_particles<true, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    case 8 | kPotLJ | kLatHcp: k_particles<true, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    case 8 | kPotMorse | kLatHcp: k_particles<true, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    case kPotLJ: k_particles<false, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    case kPotMorse: k_particles<false, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    case kPotLJ | kLatHcp: k_particles<false, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    case kPotMorse | kLatHcp: k_particles<false, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    }
 }
 
 int max_batch_slabs() { return kMaxBatchSlabs; }
 
 void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
-                                int full, int morse, int maxW, int nsm, cudaStream_t st)
+                                int full, int pot, int maxW, int nsm, cudaStream_t st)
 {
     cudaMemcpyToSymbolAsync(c_batch_args, args_dev, sizeof(StepArgs) * nslab, 0, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyToSymbolAsync(c_tile_base, tile_base_dev, sizeof(int) * (nslab + 1), 0, cudaMemcpyDeviceToDevice, st);
@@ -463,9 +475,14 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        for (const void* k : {(const void*)k_particles_batch<true, kPotLJ>, (const void*)k_particles_batch<false, kPotLJ>,
+        for (const void* k : {(const void*)k_particles_batch<true, kPotLJ>,
                               (const void*)k_particles_batch<true, kPotMorse>,
-                              (const void*)k_particles_batch<false, kPotMorse>}) {
+                              (const void*)k_particles_batch<true, kPotLJ | kLatHcp>,
+                              (const void*)k_particles_batch<true, kPotMorse | kLatHcp>,
+                              (const void*)k_particles_batch<false, kPotLJ>,
+                              (const void*)k_particles_batch<false, kPotMorse>,
+                              (const void*)k_particles_batch<false, kPotLJ | kLatHcp>,
+                              (const void*)k_particles_batch<false, kPotMorse | kLatHcp>}) {
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         }
@@ -475,10 +492,17 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
     const int nsub = parts_per_tile(total_tiles, cap);
     int grid = total_tiles * nsub < cap ? total_tiles * nsub : cap;
     if (grid < 1) grid = 1;
-    if (full && !morse) k_particles_batch<true, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
-    else if (!morse) k_particles_batch<false, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
-    else if (full) k_particles_batch<true, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
-    else k_particles_batch<false, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub);
+    // pot: the instance code of every slab (kPotLJ or kPotMorse, with kLatHcp)
+    switch (pot | (full ? 8 : 0)) {
+    case 8 | kPotLJ: k_particles_batch<true, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    case 8 | kPotMorse: k_particles_batch<true, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    case 8 | kPotLJ | kLatHcp: k_particles_batch<true, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    case 8 | kPotMorse | kLatHcp: k_particles_batch<true, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    case kPotLJ: k_particles_batch<false, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    case kPotMorse: k_particles_batch<false, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    case kPotLJ | kLatHcp: k_particles_batch<false, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    case kPotMorse | kLatHcp: k_particles_batch<false, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    }
 }
 
 int tile_window(int T) { return T + 2 * kMargin + 3; }

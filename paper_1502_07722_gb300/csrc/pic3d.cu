@@ -378,9 +378,11 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
         if (n > 0.0f) {
             const float c = fast_cbrt(n);
             const float inv43 = fast_rcp(n * c);
-            kx += S.p_kick * pair_axis<false, POT>(n, c, inv43, gr[0], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
-            ky += S.p_kick * pair_axis<false, POT>(n, c, inv43, gr[1], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
-            kz += S.p_kick * pair_axis<false, POT>(n, c, inv43, gr[2], a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+            float pf[3];
+            pair_force3<POT>(n, c, inv43, gr, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pf);
+            kx += S.p_kick * pf[0];
+            ky += S.p_kick * pf[1];
+            kz += S.p_kick * pf[2];
         }
     }
     const float ux0 = ux, uy0 = uy, uz0 = uz;
@@ -525,7 +527,7 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     a.ntiles = c.ntiles;
     a.nsp = c.nsp;
     a.full = c.cfg.mode == PIC_MODE_FULL;
-    a.pot_mode = c.cfg.pot_mode;
+    a.pot_mode = pot_code(c.cfg);
     a.cdt_dx = (float)(kC * c.dt / c.cfg.dx);
     a.rho_s = (float)c.rho_scale;
     a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
@@ -558,8 +560,14 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        for (const void* k : {(const void*)k_particles3<true, kPotLJ>, (const void*)k_particles3<false, kPotLJ>,
-                              (const void*)k_particles3<true, kPotMorse>, (const void*)k_particles3<false, kPotMorse>}) {
+        for (const void* k : {(const void*)k_particles3<true, kPotLJ>,
+                              (const void*)k_particles3<true, kPotMorse>,
+                              (const void*)k_particles3<true, kPotLJ | kLatHcp>,
+                              (const void*)k_particles3<true, kPotMorse | kLatHcp>,
+                              (const void*)k_particles3<false, kPotLJ>,
+                              (const void*)k_particles3<false, kPotMorse>,
+                              (const void*)k_particles3<false, kPotLJ | kLatHcp>,
+                              (const void*)k_particles3<false, kPotMorse | kLatHcp>}) {
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         }
@@ -567,11 +575,17 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     }
     int grid = c.ntiles < c.nsm * 3 ? c.ntiles : c.nsm * 3;
     if (grid < 1) grid = 1;
-    const bool morse = a.pot_mode == 2;
-    if (a.full && !morse) k_particles3<true, kPotLJ><<<grid, kBlock3, shmem, st>>>(a);
-    else if (!morse) k_particles3<false, kPotLJ><<<grid, kBlock3, shmem, st>>>(a);
-    else if (a.full) k_particles3<true, kPotMorse><<<grid, kBlock3, shmem, st>>>(a);
-    else k_particles3<false, kPotMorse><<<grid, kBlock3, shmem, st>>>(a);
+    // the instance with the potential family (L-J forms or Morse) and the lattice compiled in
+    switch ((((a.pot_mode & 3) == 2 ? kPotMorse : kPotLJ) | (a.pot_mode & kLatHcp)) | (a.full ? 8 : 0)) {
+    case 8 | kPotLJ: k_particles3<true, kPotLJ><<<grid, kBlock3, shmem, st>>>(a); break;
+    case 8 | kPotMorse: k_particles3<true, kPotMorse><<<grid, kBlock3, shmem, st>>>(a); break;
+    case 8 | kPotLJ | kLatHcp: k_particles3<true, kPotLJ | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
+    case 8 | kPotMorse | kLatHcp: k_particles3<true, kPotMorse | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
+    case kPotLJ: k_particles3<false, kPotLJ><<<grid, kBlock3, shmem, st>>>(a); break;
+    case kPotMorse: k_particles3<false, kPotMorse><<<grid, kBlock3, shmem, st>>>(a); break;
+    case kPotLJ | kLatHcp: k_particles3<false, kPotLJ | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
+    case kPotMorse | kLatHcp: k_particles3<false, kPotMorse | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
+    }
 }
 
 // ---- stand-alone node density and pair force ------------------------------------------------
@@ -606,7 +620,8 @@ __global__ void k_pair_force3(const int32_t* __restrict__ cell, const float* __r
         if (dens > 0.0f) {
             const float cr = fast_cbrt(dens);
             const float inv43 = fast_rcp(dens * cr);
-            for (int d = 0; d < 3; d++) F[d] = f_unit * pair_axis(dens, cr, inv43, gr[d], h_coef, pot_mode, c_att, s_rep);
+            pair_force3(dens, cr, inv43, gr, h_coef, pot_mode, c_att, s_rep, F);
+            for (int d = 0; d < 3; d++) F[d] *= f_unit;
         }
         out[3 * p] = F[0];
         out[3 * p + 1] = F[1];
@@ -635,7 +650,7 @@ void launch_pair_force3(Ctx& c, float* out, cudaStream_t st)
     if (S.n == 0) return;
     k_pair_force3<<<grid3(c, S.n), 256, 0, st>>>(S.a.cell, S.a.fx, S.a.fy, S.a.fz, S.n, geo_of(c), c.rho[c.cur],
                                                   (float)c.rho_scale, (float)(c.r0 / (6.0 * c.cfg.dx)),
-                                                  c.cfg.pot_mode, pot_param(c.cfg), (float)c.cfg.s_rep,
+                                                  pot_code(c.cfg), pot_param(c.cfg), (float)c.cfg.s_rep,
                                                   (float)(c.D / c.r0), out);
 }
 
@@ -812,7 +827,7 @@ __global__ void __launch_bounds__(256) k_energy3(const Species3 s0, const Specie
                 if (dens > 0.0f) {
                     const float cr = fast_cbrt(dens), inv43 = fast_rcp(dens * cr);
                     float e = 0.0f;
-                    for (int d = 0; d < 3; d++) e += pair_energy_axis(cr, inv43, gr[d], h_coef, pot_mode, c_att, s_rep);
+                    e += pair_energy3(cr, inv43, gr, h_coef, pot_mode, c_att, s_rep);
                     pe += (double)e;
                 }
             }
@@ -873,7 +888,7 @@ void launch_energy3(Ctx& c, cudaStream_t st, double* host_out5)
     const int nb = c.nsm * 4;
     k_energy3<<<nb, 256, 0, st>>>(sp[0], sp[1], c.sp[0].n, c.nsp > 1 ? c.sp[1].n : 0, c.nsp, geo_of(c), c.F[0], c.F[1],
                                   c.F[2], c.F[3], c.F[4], c.F[5], c.rho[c.cur], (float)c.rho_scale,
-                                  (float)(c.r0 / (6.0 * c.cfg.dx)), c.cfg.pot_mode, pot_param(c.cfg),
+                                  (float)(c.r0 / (6.0 * c.cfg.dx)), pot_code(c.cfg), pot_param(c.cfg),
                                   (float)c.cfg.s_rep, c.partials);
     k_energy3_final<<<1, 256, 0, st>>>(c.partials, nb, c.red_out);
     double raw[5];

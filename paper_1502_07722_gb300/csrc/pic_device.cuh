@@ -48,7 +48,7 @@ __device__ __forceinline__ float lj_U_inv(float inv)
 // Branch factor of the altered potential: s_rep inside r0 (inv > 1), c_att outside.
 __device__ __forceinline__ float branch(int pot_mode, float c_att, float s_rep, float inv)
 {
-    return pot_mode == 0 ? 1.0f : (inv > 1.0f ? s_rep : c_att);
+    return (pot_mode & 3) == 0 ? 1.0f : (inv > 1.0f ? s_rep : c_att);
 }
 
 // Morse potential (pot_mode 2; the paper's mapping of density to neighbour distance takes any pair
@@ -87,7 +87,7 @@ static __device__ __noinline__ float morse_axis(float c, float h, float a)
 // Pair energy U(r) (units D) of one neighbour at r0 / r = inv under pot_mode.
 __device__ __forceinline__ float pair_U(int pot_mode, float c_att, float s_rep, float inv)
 {
-    return pot_mode == 2 ? morse_U_inv(inv, c_att) : branch(pot_mode, c_att, s_rep, inv) * lj_U_inv(inv);
+    return (pot_mode & 3) == 2 ? morse_U_inv(inv, c_att) : branch(pot_mode, c_att, s_rep, inv) * lj_U_inv(inv);
 }
 
 // Dimensionless pair force along one axis (units D / r0) on an atom at local density n (> 0)
@@ -100,19 +100,20 @@ __device__ __forceinline__ float pair_U(int pot_mode, float c_att, float s_rep, 
 //   F = 24 [ c n^4 P13(h) - c n^2 P7(h) ].
 // ZERO_SKIP: a branch whose factor is 0 contributes nothing even where U' overflows FP32 (a
 // neighbour pulled arbitrarily close at the vacuum edge); the probe calls of the calibration use it.
-// POT: the potential family compiled in. kPotLJ: Eq. (3) and the altered potential (pot_mode 0, 1);
-// kPotMorse: the Morse form only; kPotRuntime: chosen by pot_mode at run time (diagnostics). The
-// particle kernels take kPotLJ or kPotMorse as a template argument, so that the Lennard-Jones
-// instances carry no Morse branch (a uniform run-time branch to the out-of-line Morse call cost
-// 6 % of the 3D particle kernel's time).
-enum { kPotRuntime = -1, kPotLJ = 0, kPotMorse = 2 };
+// POT: the potential code compiled in (bits 0-1 the family, bit 2 the HCP lattice). kPotLJ: Eq. (3)
+// and the altered potential (pot_mode 0, 1); kPotMorse: the Morse form only; kPotRuntime: the code
+// is read from pot_mode at run time (diagnostics). The particle kernels take the code as a template
+// argument, so that the cubic Lennard-Jones instances carry no Morse or HCP branch (a uniform
+// run-time branch to the out-of-line Morse call cost 6 % of the 3D particle kernel's time).
+enum { kPotRuntime = -1, kPotLJ = 0, kPotMorse = 2, kLatHcp = 4 };
 
 template <bool ZERO_SKIP = false, int POT = kPotRuntime>
 __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float dn, float h_coef,
                                            int pot_mode, float c_att, float s_rep)
 {
     float h = -h_coef * dn * inv43;
-    if (POT == kPotMorse || (POT == kPotRuntime && pot_mode == 2)) return morse_axis(c, h, c_att);
+    if ((POT >= 0 && (POT & 3) == kPotMorse) || (POT == kPotRuntime && (pot_mode & 3) == 2))
+        return morse_axis(c, h, c_att);
     float ip = c * (1.0f - h);      // r0 / dist to the neighbour on the + side
     float im = c * (1.0f + h);      // r0 / dist to the neighbour on the - side
     if (ip > 0.0f && im > 0.0f) {
@@ -261,6 +262,13 @@ namespace gbpic {
 
 // Pair-potential half kick components (units D / r0) along x and z at local density n (units
 // n0) with gradient (dnx, dnz) per cell: Eqs. (1)-(3) via pair_axis.
+// HCP (ideal axial ratio, c axis along z, sublattices averaged) in the x-z plane of a y-uniform state:
+// the twelve neighbours pair up with their opposites into directions (1, 0) (weight 1), (1/2, 0)
+// (the two basal pairs at +-60 degrees, weight 2) and (e, s) with e = 1/2, 0, -1/2, s = sqrt(2/3)
+// (weight 1 each); a pair along the unit vector u contributes (U'(r+) - U'(r-)) u, r+- from Eq. (2)
+// with the density derivative along u. Their y components cancel.
+constexpr float kHcpS = 0.816496580927726f;    // sqrt(2/3)
+
 template <bool ZERO_SKIP = false, int POT = kPotRuntime>
 __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, float h_coef, int pot_mode, float c_att,
                                               float s_rep, float& fx, float& fz)
@@ -270,9 +278,94 @@ __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, flo
     if (n > 0.0f) {
         const float c = fast_cbrt(n);
         const float inv43 = fast_rcp(n * c);
-        fx = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
-        fz = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
+        const bool hcp = POT >= 0 ? (POT & kLatHcp) != 0 : (pot_mode & kLatHcp) != 0;
+        if (!hcp) {
+            fx = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
+            fz = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnz, h_coef, pot_mode, c_att, s_rep);
+        } else {
+            const float a1 = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
+            const float a2 = pair_axis<ZERO_SKIP, POT>(n, c, inv43, 0.5f * dnx, h_coef, pot_mode, c_att, s_rep);
+            const float bp = pair_axis<ZERO_SKIP, POT>(n, c, inv43, 0.5f * dnx + kHcpS * dnz, h_coef, pot_mode, c_att,
+                                                       s_rep);
+            const float b0 = pair_axis<ZERO_SKIP, POT>(n, c, inv43, kHcpS * dnz, h_coef, pot_mode, c_att, s_rep);
+            const float bm = pair_axis<ZERO_SKIP, POT>(n, c, inv43, -0.5f * dnx + kHcpS * dnz, h_coef, pot_mode, c_att,
+                                                       s_rep);
+            fx = a1 + a2 + 0.5f * (bp - bm);
+            fz = kHcpS * (bp + b0 + bm);
+        }
     }
+}
+
+// Pair energy of an atom (units D, twice the per-atom share: the caller halves it) in the x-z plane:
+// cubic: the +-x and +-z pairs and the two y neighbours at rbar; HCP: the pairs above.
+__device__ __forceinline__ float pair_energy_xz(float cr, float inv43, float dnx, float dnz, float h_coef, int pot_mode,
+                                                float c_att, float s_rep)
+{
+    if ((pot_mode & kLatHcp) == 0)
+        return pair_energy_axis(cr, inv43, dnx, h_coef, pot_mode, c_att, s_rep) +
+               pair_energy_axis(cr, inv43, dnz, h_coef, pot_mode, c_att, s_rep) + 2.0f * pair_U(pot_mode, c_att, s_rep, cr);
+    return pair_energy_axis(cr, inv43, dnx, h_coef, pot_mode, c_att, s_rep) +
+           2.0f * pair_energy_axis(cr, inv43, 0.5f * dnx, h_coef, pot_mode, c_att, s_rep) +
+           pair_energy_axis(cr, inv43, 0.5f * dnx + kHcpS * dnz, h_coef, pot_mode, c_att, s_rep) +
+           pair_energy_axis(cr, inv43, kHcpS * dnz, h_coef, pot_mode, c_att, s_rep) +
+           pair_energy_axis(cr, inv43, -0.5f * dnx + kHcpS * dnz, h_coef, pot_mode, c_att, s_rep);
+}
+
+// 3D: the same lattices with the full gradient g. HCP pairs: basal (1, 0, 0), (1/2, h, 0),
+// (-1/2, h, 0) with h = sqrt(3)/2 (weight 1), and the six out-of-plane directions
+// (cos p / sqrt 3, sin p / sqrt 3, sqrt(2/3)), p = 30, 90, ..., 330 degrees, each paired with its
+// opposite (weight 1/2: the two sublattices averaged).
+constexpr float kHcpH = 0.866025403784439f;    // sqrt(3)/2
+constexpr float kHcpR = 0.577350269189626f;    // 1/sqrt(3)
+
+template <int POT = kPotRuntime>
+__device__ __forceinline__ void pair_force3(float n, float c, float inv43, const float g[3], float h_coef, int pot_mode,
+                                            float c_att, float s_rep, float F[3])
+{
+    const bool hcp = POT >= 0 ? (POT & kLatHcp) != 0 : (pot_mode & kLatHcp) != 0;
+    if (!hcp) {
+        for (int d = 0; d < 3; d++) F[d] = pair_axis<false, POT>(n, c, inv43, g[d], h_coef, pot_mode, c_att, s_rep);
+        return;
+    }
+    const float b0 = pair_axis<false, POT>(n, c, inv43, g[0], h_coef, pot_mode, c_att, s_rep);
+    const float b1 = pair_axis<false, POT>(n, c, inv43, 0.5f * g[0] + kHcpH * g[1], h_coef, pot_mode, c_att, s_rep);
+    const float b2 = pair_axis<false, POT>(n, c, inv43, -0.5f * g[0] + kHcpH * g[1], h_coef, pot_mode, c_att, s_rep);
+    F[0] = b0 + 0.5f * (b1 - b2);
+    F[1] = kHcpH * (b1 + b2);
+    F[2] = 0.0f;
+    #pragma unroll
+    for (int q = 0; q < 6; q++) {
+        // cos and sin of 30 + 60 q degrees
+        const float cq = q == 0 || q == 5 ? kHcpH : (q == 2 || q == 3 ? -kHcpH : 0.0f);
+        const float sq = q == 1 ? 1.0f : (q == 4 ? -1.0f : (q == 0 || q == 2 ? 0.5f : -0.5f));
+        const float ux = kHcpR * cq, uy = kHcpR * sq;
+        const float a = 0.5f * pair_axis<false, POT>(n, c, inv43, ux * g[0] + uy * g[1] + kHcpS * g[2], h_coef,
+                                                     pot_mode, c_att, s_rep);
+        F[0] += a * ux;
+        F[1] += a * uy;
+        F[2] += a * kHcpS;
+    }
+}
+
+// 3D pair energy (units D, twice the per-atom share).
+__device__ __forceinline__ float pair_energy3(float cr, float inv43, const float g[3], float h_coef, int pot_mode,
+                                             float c_att, float s_rep)
+{
+    if ((pot_mode & kLatHcp) == 0) {
+        float e = 0.0f;
+        for (int d = 0; d < 3; d++) e += pair_energy_axis(cr, inv43, g[d], h_coef, pot_mode, c_att, s_rep);
+        return e;
+    }
+    float e = pair_energy_axis(cr, inv43, g[0], h_coef, pot_mode, c_att, s_rep) +
+              pair_energy_axis(cr, inv43, 0.5f * g[0] + kHcpH * g[1], h_coef, pot_mode, c_att, s_rep) +
+              pair_energy_axis(cr, inv43, -0.5f * g[0] + kHcpH * g[1], h_coef, pot_mode, c_att, s_rep);
+    for (int q = 0; q < 6; q++) {
+        const float cq = q == 0 || q == 5 ? kHcpH : (q == 2 || q == 3 ? -kHcpH : 0.0f);
+        const float sq = q == 1 ? 1.0f : (q == 4 ? -1.0f : (q == 0 || q == 2 ? 0.5f : -0.5f));
+        e += 0.5f * pair_energy_axis(cr, inv43, kHcpR * (cq * g[0] + sq * g[1]) + kHcpS * g[2], h_coef, pot_mode,
+                                     c_att, s_rep);
+    }
+    return e;
 }
 
 }  // namespace gbpic

@@ -57,6 +57,10 @@ struct Species {
 // attractive factor of the altered potential otherwise (the functions take it as c_att).
 inline float pot_param(const pic_config& cfg) { return (float)(cfg.pot_mode == 2 ? cfg.morse_a : cfg.c_att); }
 
+// The potential code the device pair functions and the particle-kernel instances take: pot_mode
+// in bits 0-1, the HCP lattice in bit 2 (kLatHcp).
+inline int pot_code(const pic_config& cfg) { return cfg.pot_mode | (cfg.lattice == PIC_LATTICE_HCP ? 4 : 0); }
+
 // Everything a kernel of the step needs, passed by value.
 struct StepArgs {
     int32_t nx, nz, T, ntx, ntz, ntiles, W;   // W: window edge (nodes) of a tile
@@ -169,7 +173,7 @@ void launch_fields_batch(const FieldArgs* fa_dev, const AntennaParams* ap_dev, l
 FieldArgs make_field_args(const Ctx& c);
 AntennaParams make_antenna_params(const Ctx& c);
 void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
-                                int full, int morse, int maxW, int nsm, cudaStream_t st);
+                                int full, int pot, int maxW, int nsm, cudaStream_t st);
 size_t particle_smem_bytes(int W);
 void launch_particle_step3(Ctx& c, cudaStream_t st);
 void launch_deposit_density3(Ctx& c, u64* out, cudaStream_t st);

@@ -40,7 +40,7 @@ def test_workspace_size_and_validation(lib):
     big = gb.pic_workspace_size(gb.make_config(workload("large2d")))
     assert big > 2 * 2 * 67108864 * 24
     for bad in (dict(nx=2), dict(nz=3), dict(slab_k=65), dict(ion_charge=2.0), dict(ppc_electron=4),
-                dict(tile=1), dict(pot_mode=3), dict(pot_mode=2), dict(pot_mode=2, morse_a=-1.0),
+                dict(tile=1), dict(pot_mode=3), dict(pot_mode=2), dict(pot_mode=2, morse_a=-1.0), dict(lattice=2),
                 dict(laser_profile=2, w0=0.0), dict(cfl=1.5)):
         with pytest.raises(gb.PicError) as e:
             gb.pic_workspace_size(gb.make_config(workload("tiny"), **bad))
@@ -55,9 +55,10 @@ def test_workspace_size_and_validation(lib):
     # a batch runs one particle-kernel instance: all slabs Morse or none
     lj, mo = gb.make_config(workload("tiny")), gb.make_config(workload("tiny"), pot_mode=2, morse_a=3.0)
     assert gb.pic_batch_workspace_size([mo, mo]) > 0
-    with pytest.raises(gb.PicError) as e:
-        gb.pic_batch_workspace_size([lj, mo])
-    assert e.value.code == gb.PIC_EINVAL
+    for mixed in ([lj, mo], [lj, gb.make_config(workload("tiny"), lattice=1)]):
+        with pytest.raises(gb.PicError) as e:
+            gb.pic_batch_workspace_size(mixed)
+        assert e.value.code == gb.PIC_EINVAL
     # transport mode: neutral atoms only
     gb.pic_workspace_size(gb.make_config(workload("transport")))
     gb.pic_workspace_size(gb.make_config(workload("crater_morse")))

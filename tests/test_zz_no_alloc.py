@@ -47,8 +47,9 @@ def _view(gb, sim):
     return v, keep
 
 
-@pytest.mark.parametrize("name,pot", [("tiny", {}), ("transport", {}), ("transport", dict(pot_mode=2, morse_a=3.0))],
-                         ids=["tiny", "transport", "transport-morse"])
+@pytest.mark.parametrize("name,pot", [("tiny", {}), ("transport", {}), ("transport", dict(pot_mode=2, morse_a=3.0)),
+                                      ("transport", dict(lattice=1))],
+                         ids=["tiny", "transport", "transport-morse", "transport-hcp"])
 def test_noalloc_energy_equals_pic_energy_twice(gb, name, pot):
     """Same five energies as pic_energy (same kernels, same summation order), on two calls in a
     row; the output is poisoned before each call so that each call must write all of it."""
@@ -100,7 +101,7 @@ def test_noalloc_energy_refuses_unknown_potentials(gb):
     view, keep = _view(gb, sim)
     out = torch.empty(5, dtype=torch.float64, device="cuda")
     lib = gb.load_library()
-    for bad in (dict(pot_mode=3), dict(pot_mode=-1), dict(pot_mode=2, morse_a=0.0)):
+    for bad in (dict(pot_mode=3), dict(pot_mode=-1), dict(pot_mode=2, morse_a=0.0), dict(lattice=2)):
         cfg = gb.make_config(w, **bad)
         assert lib.pic_energy_noalloc(ctypes.byref(cfg), ctypes.byref(view), out.data_ptr(), None) == gb.PIC_EINVAL
     torch.cuda.synchronize()
