@@ -78,6 +78,8 @@ WORKLOADS = {
 # (Phys. Rev. 114, 687 (1959); not from the paper), r0 the cubic-lattice spacing at n0, depth D
 # as for Eq. (3)
 WORKLOADS["crater_morse"] = dict(WORKLOADS["crater"], pot_mode=2, morse_a=3.09)
+# the same crater run on the hexagonal close-packed neighbour geometry (lattice 1, c axis along z)
+WORKLOADS["crater_hcp"] = dict(WORKLOADS["crater"], lattice=1)
 
 
 def workload(name: str, **overrides) -> dict:

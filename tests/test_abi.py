@@ -62,6 +62,7 @@ def test_workspace_size_and_validation(lib):
     # transport mode: neutral atoms only
     gb.pic_workspace_size(gb.make_config(workload("transport")))
     gb.pic_workspace_size(gb.make_config(workload("crater_morse")))
+    gb.pic_workspace_size(gb.make_config(workload("crater_hcp")))
     with pytest.raises(gb.PicError):
         gb.pic_workspace_size(gb.make_config(workload("transport"), ion_charge=1.0))
 
