@@ -18,12 +18,12 @@
  *   3. Lorentz push (+ pair force), current deposition, Maxwell (Yee) field update.
  *
  * Readings where the paper is silent (all listed in the design notes of the repository):
- *   - "nearest surrounding nodes": linear (cloud-in-cell) weights onto the 2 x 2 cell corners.
+ *   - the nodes nearest a particle: linear (cloud-in-cell) weights onto the 2 x 2 cell corners.
  *     Weights are fixed point: a coordinate X = rint(x * 2^16) (x in cell units), node weight
  *     S_j(X) = max(0, 2^16 - |X - 2^16 j|). Node sums are exact integers.
  *   - the gradient at the half nodes is the edge difference of the node density, interpolated
  *     linearly along the other axis; together with the bilinear node density this is the exact
- *     gradient of the interpolated density ("self-consistent").
+ *     gradient of the interpolated density, hence consistent with the deposit.
  *   - densities are used in units of n0 = r0^-3, so rbar/r0 = (n/n0)^(-1/3).
  *   - Eq. (2): the neighbour on the +x side sits at rbar / (1 - g/2), the one on the -x side at
  *     rbar / (1 + g/2), g = d rbar / dx; a non-positive denominator puts that neighbour at
@@ -38,6 +38,12 @@
  *     both half electric kicks.
  *   - fields: 2D3V Yee, B advanced in two half steps around the E update, first-order Mur at
  *     z = 0 and z = nz, laser launched by a J_x current sheet two node rows below the top.
+ *   - variants the paper names as compatible: the Morse potential (pot_mode 2, minimum -D at r0)
+ *     and the hexagonal close-packed lattice (lattice 1: Eq. 2 along each neighbour direction,
+ *     ideal axial ratio, c axis along z, both sublattices' out-of-plane neighbours at weight 1/2).
+ *   - the crater (Eq. 5's diameter, measured from the density map): material missing from each
+ *     node column of the original slab, exact integer column sums times one factor (2D and 3D).
+ * Every function is pinned by the tests against closed forms, invariants or brute force.
  */
 #include <math.h>
 #include <stdint.h>
