@@ -208,7 +208,8 @@ PIC_API int pic_pair_force(pic_ctx* ctx, float* dev_out);
  * force on a single atom leaving the target out to infinity). dev_cell, dev_fx, dev_fz: device
  * arrays of n probes (cell k*nx + i, offsets in [0,1) x [0,1]); pot_mode, c_att, s_rep as in
  * pic_config, applied to this call only (so one context yields the attractive and the repulsive
- * parts of the force separately); pot_mode 2 takes the context's morse_a and ignores c_att, s_rep. dev_out: device float[3n], (Fx, 0, Fz). A probe outside the
+ * parts of the force separately); pot_mode 2 takes the context's morse_a and ignores c_att, s_rep;
+ * the context's lattice applies. dev_out: device float[3n], (Fx, 0, Fz). A probe outside the
  * grid gets NaN. 2D contexts; asynchronous on the context's stream. Errors: PIC_EINVAL (n < 0,
  * NULL pointers with n > 0, pot_mode not 0, 1 or 2, pot_mode 2 with morse_a <= 0), PIC_ESTATE in
  * 3D. */
