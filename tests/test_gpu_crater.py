@@ -189,11 +189,14 @@ def test_c_att_calibration_matches_oracle(gb):
     sim.close()
 
 
-def test_morse_probe_forces_match_oracle(gb):
-    """Probe forces of the Morse form (pot_mode 2, a = 4) around the surface of a transport slab
-    against the oracle's force on atoms at the same positions over the same node sums, and the
-    context's own stiffness used when the configuration is L-J; tolerance as for the pair force."""
-    w = dict(workload("transport"), nx=32, nz=30, slab_k=16, ppc_ion=8, pot_mode=2, morse_a=4.0)
+@pytest.mark.parametrize("pot", [dict(pot_mode=2, morse_a=4.0), dict(pot_mode=2, morse_a=4.0, lattice=1)],
+                         ids=["morse", "morse-hcp"])
+def test_morse_probe_forces_match_oracle(gb, pot):
+    """Probe forces of the Morse form (pot_mode 2, a = 4; on the cubic and the HCP lattice) around
+    the surface of a transport slab against the oracle's force on atoms at the same positions over
+    the same node sums, and the context's own stiffness used when the configuration is L-J;
+    tolerance as for the pair force."""
+    w = dict(workload("transport"), nx=32, nz=30, slab_k=16, ppc_ion=8, **pot)
     sim = gb.Simulation(w)
     rho = sim.get_density().cpu().numpy()
     rng = np.random.default_rng(3)
