@@ -80,6 +80,9 @@ WORKLOADS = {
 WORKLOADS["crater_morse"] = dict(WORKLOADS["crater"], pot_mode=2, morse_a=3.09)
 # the same crater run on the hexagonal close-packed neighbour geometry (lattice 1, c axis along z)
 WORKLOADS["crater_hcp"] = dict(WORKLOADS["crater"], lattice=1)
+# the crater run in 3D: 3 um x 3 um x 1.6 um box, slab 1 um thick, 16 macro-atoms per cell
+# (144 M), a round 1 um spot (radius from the axis through the middle of the x-y plane)
+WORKLOADS["crater3d"] = dict(WORKLOADS["crater"], dims=3, nx=300, ny=300, nz=160, slab_k=100, ppc_ion=16, seed=9)
 
 
 def workload(name: str, **overrides) -> dict:

@@ -63,6 +63,7 @@ def test_workspace_size_and_validation(lib):
     gb.pic_workspace_size(gb.make_config(workload("transport")))
     gb.pic_workspace_size(gb.make_config(workload("crater_morse")))
     gb.pic_workspace_size(gb.make_config(workload("crater_hcp")))
+    gb.pic_workspace_size(gb.make_config(workload("crater3d")))
     with pytest.raises(gb.PicError):
         gb.pic_workspace_size(gb.make_config(workload("transport"), ion_charge=1.0))
 
