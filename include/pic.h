@@ -22,8 +22,8 @@
  * any summation order (deterministic) and bit-comparable with a CPU reference.
  *
  * Return codes: 0 on success, a negative PIC_E* code on error. Errors raised inside kernels
- * (non-finite momentum, a move of a cell or more) are sticky: pic_step reports them and every
- * later call on the context returns them until pic_free.
+ * (non-finite momentum, a move of a cell or more, a bounded wait that gave up) are sticky:
+ * pic_step reports them and every later call on the context returns them until pic_free.
  */
 #ifndef GBPIC_PIC_H
 #define GBPIC_PIC_H
@@ -48,7 +48,9 @@ enum {
     PIC_ECUDA = -3,      /* a CUDA runtime call failed                                     */
     PIC_ENAN = -4,       /* a particle momentum became non-finite                          */
     PIC_EMOVE = -5,      /* a particle moved a cell or more in one step (CFL is violated)  */
-    PIC_ESTATE = -6      /* call not valid in this mode (e.g. fields in transport mode)    */
+    PIC_ESTATE = -6,     /* call not valid in this mode (e.g. fields in transport mode)    */
+    PIC_EOVERFLOW = -7,  /* an int64 fixed-point node sum could overflow (refused at init)  */
+    PIC_ETIMEOUT = -8    /* a kernel's bounded wait on its own asynchronous copies gave up   */
 };
 
 enum { PIC_MODE_FULL = 0, PIC_MODE_TRANSPORT = 1 };

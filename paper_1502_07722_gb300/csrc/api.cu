@@ -130,6 +130,7 @@ int finish_status(pic_ctx* h)
     }
     if (st & kErrNan) c.sticky = PIC_ENAN;
     else if (st & kErrMove) c.sticky = PIC_EMOVE;
+    else if (st & kErrTimeout) c.sticky = PIC_ETIMEOUT;
     return c.sticky;
 }
 
@@ -882,6 +883,8 @@ const char* pic_strerror(int code)
     case PIC_ENAN: return "non-finite particle momentum";
     case PIC_EMOVE: return "a particle moved one cell or more in one step";
     case PIC_ESTATE: return "operation not valid in this mode";
+    case PIC_EOVERFLOW: return "a fixed-point node sum could overflow int64 for this configuration";
+    case PIC_ETIMEOUT: return "a kernel's bounded wait on its own asynchronous copies gave up";
     default: return "unknown error";
     }
 }

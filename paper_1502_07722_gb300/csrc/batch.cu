@@ -124,7 +124,7 @@ int pic_batch_workspace_size(const pic_config* cfgs, int32_t n, size_t* bytes)
     size_t t = 0;
     for (int s = 0; s < n; s++) {
         if (cfgs[s].mode != cfgs[0].mode || (cfgs[s].dims != 0 && cfgs[s].dims != 2)) return PIC_EINVAL;
-        if ((cfgs[s].pot_mode == 2) != (cfgs[0].pot_mode == 2) || cfgs[s].lattice != cfgs[0].lattice)
+        if (cfgs[s].pot_mode != cfgs[0].pot_mode || cfgs[s].lattice != cfgs[0].lattice)
             return PIC_EINVAL;   // one kernel instance
         size_t b = 0;
         const int r = pic_workspace_size(&cfgs[s], &b);
@@ -171,7 +171,7 @@ int pic_batch_init(const pic_config* cfgs, int32_t n, void* workspace, size_t by
     }
     b->total_tiles = tile_base[n];
     b->full = cfgs[0].mode == PIC_MODE_FULL;
-    b->pot = (cfgs[0].pot_mode == 2 ? 2 : 0) | (cfgs[0].lattice == PIC_LATTICE_HCP ? 4 : 0);   // kernel instance
+    b->pot = pot_code(cfgs[0]);   // kernel instance
     b->sort_every = cfgs[0].sort_every;
     b->args_dev = reinterpret_cast<StepArgs*>(p);
     p += a256(sizeof(StepArgs) * 2 * n);
@@ -286,6 +286,7 @@ int pic_batch_step(pic_batch* b, int32_t nsteps)
         if (cudaMemcpy(&stw, c.status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
         if (stw & kErrNan) c.sticky = PIC_ENAN;
         else if (stw & kErrMove) c.sticky = PIC_EMOVE;
+        else if (stw & kErrTimeout) c.sticky = PIC_ETIMEOUT;
         if (c.sticky && !b->sticky) b->sticky = c.sticky;
     }
     return b->sticky;

@@ -6,9 +6,11 @@
 // Work decomposition (GB300):
 //  * one CTA owns one tile of T x T cells at a time (particles are sorted into tiles);
 //  * the CTA stages a window of (T + 2M + 3)^2 nodes in shared memory: the six field
-//    components and the pair density n / n0 in FP32;
+//    components and the pair density n / n0 in FP32, components of one Yee stagger side by side
+//    (one 64-bit load per corner fetches two of them);
 //  * thread t of the CTA (128 threads, 8 CTAs per SM) takes the tile's records t, t + 128, ...
-//    straight from global memory (coalesced loads and stores, no block barrier). The cell sort
+//    straight from global memory (coalesced loads and stores, no block barrier); the position of
+//    its next record is loaded one iteration ahead. The cell sort
 //    stores each block of 1024 of
 //    a tile's cell-ordered particles as a 32-row matrix, column by column, so the lanes of a warp
 //    hold particles 32 places apart in the cell order: neighbouring cells, whose deposits go to
@@ -22,10 +24,12 @@
 //    changed. Ions move ~1e-7 cells per step against a quantum of 1.5e-5 cells, so most of them
 //    deposit nothing; the integer result equals a full re-deposit bit for bit;
 //  * a particle that stays in its cell (almost all of them) deposits on the four corners of the
-//    cell; a particle that crossed a cell edge uses the 3 x 3 Esirkepov stencil (rare); a particle
-//    that drifted beyond the margin since the last sort gathers from global memory (rare);
-//  * the code is specialised per species kind (ion, electron, neutral atom), so no per-particle
-//    branch tests a species property.
+//    cell (an electron without per-term zero tests: its terms are almost never zero); a particle
+//    that crossed a cell edge uses the 3 x 3 Esirkepov stencil (rare); a particle that drifted
+//    beyond the margin since the last sort gathers from global memory (rare);
+//  * the code is specialised per species kind (ion, electron, neutral atom) and per potential
+//    and lattice, so no per-particle branch tests a species or potential property; Eq. (3) as
+//    printed evaluates both in-plane axes at once with packed FP32x2 arithmetic.
 // Integer sums make every result independent of the order of the additions.
 #include <atomic>
 
@@ -43,8 +47,15 @@ __device__ __forceinline__ int wrap_any(int i, int nx)
     return r < 0 ? r + nx : r;
 }
 
+// The tile's window in shared memory. Field instances keep the components that share a Yee
+// stagger side by side, so one 64-bit load fetches both at a corner: (Ex, Bz) at (i + 1/2, k),
+// (Ez, Bx) at (i, k + 1/2), (Ey, n / n0) at (i, k), By at (i + 1/2, k + 1/2). Transport
+// instances keep n / n0 alone.
 struct Window {
-    float* f[6];
+    float2* exbz;
+    float2* ezbx;
+    float2* eyn;
+    float* by;
     float* nh;
     int ox, oz, W;
 };
@@ -63,30 +74,6 @@ __device__ __forceinline__ void split_cell(int cell, int nx, unsigned magic, int
     if (r >= nx) { q++; r -= nx; }
     k = (int)q;
     i = r;
-}
-
-// Weights of one stagger pattern: the four corner coefficients and the corner index.
-struct Stencil2 {
-    int idx;
-    float c00, c10, c01, c11;
-};
-
-__device__ __forceinline__ Stencil2 make_stencil(int idx, float wx, float wz)
-{
-    Stencil2 t;
-    t.idx = idx;
-    const float gx = 1.0f - wx, gz = 1.0f - wz;
-    t.c00 = gx * gz;
-    t.c10 = wx * gz;
-    t.c01 = gx * wz;
-    t.c11 = wx * wz;
-    return t;
-}
-
-__device__ __forceinline__ float apply(const float* A, int W, const Stencil2& t)
-{
-    const float* p = A + t.idx;
-    return t.c00 * p[0] + t.c10 * p[1] + t.c01 * p[W] + t.c11 * p[W + 1];
 }
 
 // Rare path: fields and node density straight from global memory (particle outside the window).
@@ -171,8 +158,9 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     constexpr int kSign = KIND == kElectron ? -1 : 1;
     const int nx = a.nx, nz = a.nz, W = w.W;
     const float fx = fx_io, fz = fz_io;
+    const int cell0 = cell;
     int i, k;
-    split_cell(cell, nx, a.nx_magic, i, k);
+    split_cell(cell0, nx, a.nx_magic, i, k);
 
     // window coordinates (x is periodic: take the image closest to the window centre)
     int lx = i - w.ox;
@@ -185,27 +173,43 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     float kx = 0.f, ky = 0.f, kz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
     float n = 0.f, dnx = 0.f, dnz = 0.f;
     if (inwin) {
+        const int base = lz * W + lx;
+        const float gx = 1.0f - fx, gz = 1.0f - fz;
         if (kFields) {
-            // four stagger patterns: (0,0) Ey; (1/2,0) Ex, Bz; (0,1/2) Ez, Bx; (1/2,1/2) By
-            const int base = lz * W + lx;
+            // four stagger patterns: (0,0) Ey, n; (1/2,0) Ex, Bz; (0,1/2) Ez, Bx; (1/2,1/2) By
             const bool ux_ = fx >= 0.5f, uz_ = fz >= 0.5f;
             const int ox_ = ux_ ? 0 : -1, oz_ = uz_ ? 0 : -W;
-            const float hxw = ux_ ? fx - 0.5f : fx + 0.5f, hzw = uz_ ? fz - 0.5f : fz + 0.5f;
-            const Stencil2 s00 = make_stencil(base, fx, fz);
-            const Stencil2 s10 = make_stencil(base + ox_, hxw, fz);
-            const Stencil2 s01 = make_stencil(base + oz_, fx, hzw);
-            const Stencil2 s11 = make_stencil(base + ox_ + oz_, hxw, hzw);
-            kx = S.e_kick * apply(w.f[0], W, s10);
-            ky = S.e_kick * apply(w.f[1], W, s00);
-            kz = S.e_kick * apply(w.f[2], W, s01);
-            bx = apply(w.f[3], W, s01);
-            by = apply(w.f[4], W, s11);
-            bz = apply(w.f[5], W, s10);
-        }
-        if (kPair) {
-            const float* q = w.nh + lz * W + lx;
+            const float hx = ux_ ? fx - 0.5f : fx + 0.5f, hz = uz_ ? fz - 0.5f : fz + 0.5f;
+            const float ghx = 1.0f - hx, ghz = 1.0f - hz;
+            {
+                const float2* q = w.eyn + base;
+                const float2 c00 = q[0], c10 = q[1], c01 = q[W], c11 = q[W + 1];
+                ky = S.e_kick * (gz * (gx * c00.x + fx * c10.x) + fz * (gx * c01.x + fx * c11.x));
+                if (kPair) {
+                    n = gz * (gx * c00.y + fx * c10.y) + fz * (gx * c01.y + fx * c11.y);
+                    dnx = gz * (c10.y - c00.y) + fz * (c11.y - c01.y);
+                    dnz = gx * (c01.y - c00.y) + fx * (c11.y - c10.y);
+                }
+            }
+            {
+                const float2* q = w.exbz + base + ox_;
+                const float2 c00 = q[0], c10 = q[1], c01 = q[W], c11 = q[W + 1];
+                kx = S.e_kick * (gz * (ghx * c00.x + hx * c10.x) + fz * (ghx * c01.x + hx * c11.x));
+                bz = gz * (ghx * c00.y + hx * c10.y) + fz * (ghx * c01.y + hx * c11.y);
+            }
+            {
+                const float2* q = w.ezbx + base + oz_;
+                const float2 c00 = q[0], c10 = q[1], c01 = q[W], c11 = q[W + 1];
+                kz = S.e_kick * (ghz * (gx * c00.x + fx * c10.x) + hz * (gx * c01.x + fx * c11.x));
+                bx = ghz * (gx * c00.y + fx * c10.y) + hz * (gx * c01.y + fx * c11.y);
+            }
+            {
+                const float* q = w.by + base + ox_ + oz_;
+                by = ghz * (ghx * q[0] + hx * q[1]) + hz * (ghx * q[W] + hx * q[W + 1]);
+            }
+        } else if (kPair) {
+            const float* q = w.nh + base;
             const float n00 = q[0], n10 = q[1], n01 = q[W], n11 = q[W + 1];
-            const float gx = 1.0f - fx, gz = 1.0f - fz;
             n = gz * (gx * n00 + fx * n10) + fz * (gx * n01 + fx * n11);
             dnx = gz * (n10 - n00) + fz * (n11 - n01);
             dnz = gx * (n01 - n00) + fx * (n11 - n10);
@@ -222,7 +226,8 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     }
     if (kPair) {
         float pfx, pfz;
-        pair_force_xz<false, POT>(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz);
+        if (POT == kPotLJ) lj_pair_xz2(n, dnx, dnz, a.h_coef, pfx, pfz);
+        else pair_force_xz<false, POT>(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz);
         kx += S.p_kick * pfx;
         kz += S.p_kick * pfz;
     }
@@ -230,8 +235,8 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     // relativistic Boris: half kick, rotation, half kick
     ux += kx; uy += ky; uz += kz;
     if (kFields) {
-        const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
-        const float tx = S.b_rot * ig * bx, ty = S.b_rot * ig * by, tz = S.b_rot * ig * bz;
+        const float rot = S.b_rot * rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        const float tx = rot * bx, ty = rot * by, tz = rot * bz;
         const float s = 2.0f * fast_rcp(1.0f + tx * tx + ty * ty + tz * tz);
         const float px = ux + (uy * tz - uz * ty);
         const float py = uy + (uz * tx - ux * tz);
@@ -243,8 +248,8 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     ux += kx; uy += ky; uz += kz;
 
     // move (in-plane), cells per step = u c dt / (gamma dx)
-    const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
-    float dxi = ux * a.cdt_dx * ig, dze = uz * a.cdt_dx * ig;
+    const float step = a.cdt_dx * rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+    float dxi = ux * step, dze = uz * step;
     if (!(fabsf(dxi) < 1.0f && fabsf(dze) < 1.0f)) {
         atomicOr(a.status, (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? kErrMove : kErrNan);
         ux = ux0; uy = uy0; uz = uz0; dxi = 0.0f; dze = 0.0f;
@@ -269,41 +274,71 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     fz_io = nfz;
 
     const int x0 = qoff(fx), x1 = qoff(nfx), z0 = qoff(fz), z1 = qoff(nfz);
-    const bool moved = (di | dk) != 0 || x1 != x0 || z1 != z0;
     // |u_y| < 2^-19 gives |beta_y| 2^18 < 1/2, i.e. V = 0 without evaluating the code
     const int V = (kCurrent && fabsf(uy) >= 1.9073486328125e-06f) ? kSign * jy_code(ux, uy, uz) : 0;
+    const bool incell = inwin && (di | dk) == 0;
+    if (KIND == kElectron && incell) {
+        // an electron that stays in its cell (almost every electron): it always moves in fixed
+        // point and almost always has V != 0, so the eight reductions onto the cell's corners are
+        // issued without per-term tests (a zero term adds nothing). The out-of-plane weights are
+        // 6 W = A0 U0 + A1 U1 with A = 2^16 - x and U0 = 2 C0 + C1, U1 = C0 + 2 C1 (C = 2^16 - z)
+        // on the lower-left corner, and likewise with x for A and z for C on the others: two
+        // widening 32 x 32-bit products per corner.
+        const int d1 = i + 1 == nx ? 1 - nx : 1;
+        u64* jx = a.J[0] + cell0;
+        u64* jy = a.J[1] + cell0;
+        u64* jz = a.J[2] + cell0;
+        const int dX = x0 - x1, dZ = z0 - z1;          // charge sign -1
+        atomicAdd(jx, (u64)((long long)dX * (2 * kQOne - z0 - z1)));
+        atomicAdd(jx + nx, (u64)((long long)dX * (z0 + z1)));
+        atomicAdd(jz, (u64)((long long)dZ * (2 * kQOne - x0 - x1)));
+        atomicAdd(jz + d1, (u64)((long long)dZ * (x0 + x1)));
+        const int A0 = kQOne - x0, A1 = kQOne - x1, C0 = kQOne - z0, C1 = kQOne - z1;
+        const int U0 = 2 * C0 + C1, U1 = C0 + 2 * C1, Z0 = 2 * z0 + z1, Z1 = z0 + 2 * z1;
+        const long long w00 = (long long)A0 * U0 + (long long)A1 * U1;
+        const long long w10 = (long long)x0 * U0 + (long long)x1 * U1;
+        const long long w01 = (long long)A0 * Z0 + (long long)A1 * Z1;
+        const long long w11 = (long long)x0 * Z0 + (long long)x1 * Z1;
+        atomicAdd(jy, (u64)(V * w00));
+        atomicAdd(jy + d1, (u64)(V * w10));
+        atomicAdd(jy + nx, (u64)(V * w01));
+        atomicAdd(jy + nx + d1, (u64)(V * w11));
+        return;
+    }
+    const bool moved = (di | dk) != 0 || x1 != x0 || z1 != z0;
     if (!moved && V == 0) return;                 // nothing to deposit (most ions)
 
-    if (inwin && (di | dk) == 0) {
+    if (incell) {
         // the particle stays in its cell: stencil = the four corners of the cell (global reductions)
-        const int i1 = i + 1 == nx ? 0 : i + 1;
-        const size_t g00 = (size_t)k * nx + i, g10 = (size_t)k * nx + i1, g01 = g00 + nx, g11 = g10 + nx;
+        const int d1 = i + 1 == nx ? 1 - nx : 1;
         if (kCurrent) {
             const int dX = kSign * (x1 - x0), dZ = kSign * (z1 - z0);
             if (dX != 0) {
-                red64g(a.J[0] + g00, (long long)dX * (2 * kQOne - z0 - z1));
-                red64g(a.J[0] + g01, (long long)dX * (z0 + z1));
+                red64g(a.J[0] + cell0, (long long)dX * (2 * kQOne - z0 - z1));
+                red64g(a.J[0] + cell0 + nx, (long long)dX * (z0 + z1));
             }
             if (dZ != 0) {
-                red64g(a.J[2] + g00, (long long)dZ * (2 * kQOne - x0 - x1));
-                red64g(a.J[2] + g10, (long long)dZ * (x0 + x1));
+                red64g(a.J[2] + cell0, (long long)dZ * (2 * kQOne - x0 - x1));
+                red64g(a.J[2] + cell0 + d1, (long long)dZ * (x0 + x1));
             }
             if (V != 0) {
-                const long long P = (long long)x0 * (2 * z0 + z1) + (long long)x1 * (z0 + 2 * z1);
-                const long long sx = 3LL * kQOne * (x0 + x1), sz = 3LL * kQOne * (z0 + z1);
-                red64g(a.J[1] + g00, V * (6LL * kQOne * kQOne - sx - sz + P));
-                red64g(a.J[1] + g10, V * (sx - P));
-                red64g(a.J[1] + g01, V * (sz - P));
-                red64g(a.J[1] + g11, V * P);
+                const int A0 = kQOne - x0, A1 = kQOne - x1, C0 = kQOne - z0, C1 = kQOne - z1;
+                const int U0 = 2 * C0 + C1, U1 = C0 + 2 * C1, Z0 = 2 * z0 + z1, Z1 = z0 + 2 * z1;
+                u64* jy = a.J[1] + cell0;
+                red64g(jy, V * ((long long)A0 * U0 + (long long)A1 * U1));
+                red64g(jy + d1, V * ((long long)x0 * U0 + (long long)x1 * U1));
+                red64g(jy + nx, V * ((long long)A0 * Z0 + (long long)A1 * Z1));
+                red64g(jy + nx + d1, V * ((long long)x0 * Z0 + (long long)x1 * Z1));
             }
         }
         if (kPair && moved) {
             // weights are at most 2^16: each product is one 32 x 32 -> 64-bit multiply
             const int a0 = kQOne - x0, a1 = kQOne - x1, c0 = kQOne - z0, c1 = kQOne - z1;
-            red64g(a.rho_next + g00, (long long)a1 * c1 - (long long)a0 * c0);
-            red64g(a.rho_next + g10, (long long)x1 * c1 - (long long)x0 * c0);
-            red64g(a.rho_next + g01, (long long)a1 * z1 - (long long)a0 * z0);
-            red64g(a.rho_next + g11, (long long)x1 * z1 - (long long)x0 * z0);
+            u64* r = a.rho_next + cell0;
+            red64g(r, (long long)a1 * c1 - (long long)a0 * c0);
+            red64g(r + d1, (long long)x1 * c1 - (long long)x0 * c0);
+            red64g(r + nx, (long long)a1 * z1 - (long long)a0 * z0);
+            red64g(r + nx + d1, (long long)x1 * z1 - (long long)x0 * z0);
         }
     } else {
         // deposit_global applies the charge sign itself: hand it the unsigned code kSign * V
@@ -328,8 +363,11 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t, int sub, int 
     Window w;
     w.W = W;
     float* fbase = reinterpret_cast<float*>(smem);
-    for (int q = 0; q < 6; q++) w.f[q] = fbase + q * WW;
-    w.nh = fbase + 6 * WW;
+    w.exbz = reinterpret_cast<float2*>(fbase);
+    w.ezbx = reinterpret_cast<float2*>(fbase + 2 * WW);
+    w.eyn = reinterpret_cast<float2*>(fbase + 4 * WW);
+    w.by = fbase + 6 * WW;
+    w.nh = fbase;
 
     {
         int cnt = 0;
@@ -351,16 +389,16 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t, int sub, int 
             const int gn = min(max(gz, 0), a.nz);          // node rows 0..nz
             const int gh = min(max(gz, 0), a.nz - 1);      // half rows 0..nz-1 (edge rows repeat)
             const size_t in = (size_t)gn * a.nx + gx, ih = (size_t)gh * a.nx + gx;
-            if (FULL) {
-                w.f[0][j] = __ldg(a.F[0] + in);
-                w.f[1][j] = __ldg(a.F[1] + in);
-                w.f[2][j] = __ldg(a.F[2] + ih);
-                w.f[3][j] = __ldg(a.F[3] + ih);
-                w.f[4][j] = __ldg(a.F[4] + ih);
-                w.f[5][j] = __ldg(a.F[5] + in);
-            }
             const long long r = (long long)__ldg(a.rho_cur + in);
-            w.nh[j] = a.rho_s * (float)((gn == 0 || gn == a.nz) ? 2 * r : r);
+            const float nh = a.rho_s * (float)((gn == 0 || gn == a.nz) ? 2 * r : r);
+            if (FULL) {
+                w.exbz[j] = make_float2(__ldg(a.F[0] + in), __ldg(a.F[5] + in));
+                w.ezbx[j] = make_float2(__ldg(a.F[2] + ih), __ldg(a.F[3] + ih));
+                w.eyn[j] = make_float2(__ldg(a.F[1] + in), nh);
+                w.by[j] = __ldg(a.F[4] + ih);
+            } else {
+                w.nh[j] = nh;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -369,9 +407,24 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int t, int sub, int 
             const Species& S = a.sp[s];
             const int q0 = S.tile_start[t], q1 = S.tile_start[t + 1];
             const int p0 = part_start(q0, q1, sub, nsub), p1 = part_start(q0, q1, sub + 1, nsub);
+            // the next record's position is loaded one iteration ahead (its first use is at the top
+            // of the iteration); the momenta, first used after the gathers, are loaded in the iteration
+            int ncell = 0;
+            float nfx = 0.0f, nfz = 0.0f;
+            if (p0 + (int)threadIdx.x < p1) {
+                const int q = p0 + (int)threadIdx.x;
+                ncell = S.a.cell[q];
+                nfx = S.a.fx[q];
+                nfz = S.a.fz[q];
+            }
             for (int p = p0 + (int)threadIdx.x; p < p1; p += kBlock) {
-                int cell = S.a.cell[p];
-                float fx = S.a.fx[p], fz = S.a.fz[p], ux = S.a.ux[p], uy = S.a.uy[p], uz = S.a.uz[p];
+                int cell = ncell;
+                float fx = nfx, fz = nfz, ux = S.a.ux[p], uy = S.a.uy[p], uz = S.a.uz[p];
+                if (p + kBlock < p1) {
+                    ncell = S.a.cell[p + kBlock];
+                    nfx = S.a.fx[p + kBlock];
+                    nfz = S.a.fz[p + kBlock];
+                }
                 if (s == 0) process_particle<FULL ? kIon : kAtom, POT>(a, S, w, cell, fx, fz, ux, uy, uz);
                 else process_particle<kElectron, POT>(a, S, w, cell, fx, fz, ux, uy, uz);
                 S.a.cell[p] = cell;
@@ -422,6 +475,18 @@ static int parts_per_tile(int ntiles, int slots)
 
 size_t particle_smem_bytes(int W) { return sizeof(unsigned) * (size_t)7 * W * W; }
 
+// The kernel instances: Eq. (3), the altered potential and the Morse form, on the cubic and the
+// HCP lattice (potential code in bits 0-1, kLatHcp in bit 2), with and without fields.
+#define GBPIC_FOR_EACH_POT(X) X(kPotLJ) X(kPotAlt) X(kPotMorse) X(kPotLJ | kLatHcp) X(kPotAlt | kLatHcp) \
+    X(kPotMorse | kLatHcp)
+
+static void set_smem(const void* k, size_t shmem)
+{
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    // the largest carve-out, so that several CTAs fit on one SM
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
 {
     const size_t shmem = particle_smem_bytes(a.W);
@@ -430,18 +495,9 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        // the largest carve-out, so that several CTAs fit on one SM
-        for (const void* k : {(const void*)k_particles<true, kPotLJ>,
-                              (const void*)k_particles<true, kPotMorse>,
-                              (const void*)k_particles<true, kPotLJ | kLatHcp>,
-                              (const void*)k_particles<true, kPotMorse | kLatHcp>,
-                              (const void*)k_particles<false, kPotLJ>,
-                              (const void*)k_particles<false, kPotMorse>,
-                              (const void*)k_particles<false, kPotLJ | kLatHcp>,
-                              (const void*)k_particles<false, kPotMorse | kLatHcp>}) {
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        }
+#define GBPIC_ATTR(P) set_smem((const void*)k_particles<true, (P)>, shmem); set_smem((const void*)k_particles<false, (P)>, shmem);
+        GBPIC_FOR_EACH_POT(GBPIC_ATTR)
+#undef GBPIC_ATTR
         configured[dev].store(shmem);
     }
     const int cap = c.nsm * kCtasPerSm;
@@ -449,16 +505,13 @@ void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st)
     int grid = a.ntiles * nsub;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    // the instance with the potential family (L-J forms or Morse) and the lattice compiled in
-    switch ((((a.pot_mode & 3) == 2 ? kPotMorse : kPotLJ) | (a.pot_mode & kLatHcp)) | (a.full ? 8 : 0)) {
-    case 8 | kPotLJ: k_particles<true, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub); break;
-    case 8 | kPotMorse: k_particles<true, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub); break;
-    case 8 | kPotLJ | kLatHcp: k_particles<true, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
-    case 8 | kPotMorse | kLatHcp: k_particles<true, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
-    case kPotLJ: k_particles<false, kPotLJ><<<grid, kBlock, shmem, st>>>(a, nsub); break;
-    case kPotMorse: k_particles<false, kPotMorse><<<grid, kBlock, shmem, st>>>(a, nsub); break;
-    case kPotLJ | kLatHcp: k_particles<false, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
-    case kPotMorse | kLatHcp: k_particles<false, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+    // the instance with the potential and the lattice compiled in
+    switch ((a.pot_mode & 7) | (a.full ? 8 : 0)) {
+#define GBPIC_CASE(P)                                                                                 \
+    case 8 | (P): k_particles<true, (P)><<<grid, kBlock, shmem, st>>>(a, nsub); break;                \
+    case (P): k_particles<false, (P)><<<grid, kBlock, shmem, st>>>(a, nsub); break;
+        GBPIC_FOR_EACH_POT(GBPIC_CASE)
+#undef GBPIC_CASE
     }
 }
 
@@ -475,33 +528,22 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        for (const void* k : {(const void*)k_particles_batch<true, kPotLJ>,
-                              (const void*)k_particles_batch<true, kPotMorse>,
-                              (const void*)k_particles_batch<true, kPotLJ | kLatHcp>,
-                              (const void*)k_particles_batch<true, kPotMorse | kLatHcp>,
-                              (const void*)k_particles_batch<false, kPotLJ>,
-                              (const void*)k_particles_batch<false, kPotMorse>,
-                              (const void*)k_particles_batch<false, kPotLJ | kLatHcp>,
-                              (const void*)k_particles_batch<false, kPotMorse | kLatHcp>}) {
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        }
+#define GBPIC_ATTR(P) set_smem((const void*)k_particles_batch<true, (P)>, shmem); set_smem((const void*)k_particles_batch<false, (P)>, shmem);
+        GBPIC_FOR_EACH_POT(GBPIC_ATTR)
+#undef GBPIC_ATTR
         configured[dev].store(shmem);
     }
     const int cap = nsm * kCtasPerSm;
     const int nsub = parts_per_tile(total_tiles, cap);
     int grid = total_tiles * nsub < cap ? total_tiles * nsub : cap;
     if (grid < 1) grid = 1;
-    // pot: the instance code of every slab (kPotLJ or kPotMorse, with kLatHcp)
-    switch (pot | (full ? 8 : 0)) {
-    case 8 | kPotLJ: k_particles_batch<true, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
-    case 8 | kPotMorse: k_particles_batch<true, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
-    case 8 | kPotLJ | kLatHcp: k_particles_batch<true, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
-    case 8 | kPotMorse | kLatHcp: k_particles_batch<true, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
-    case kPotLJ: k_particles_batch<false, kPotLJ><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
-    case kPotMorse: k_particles_batch<false, kPotMorse><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
-    case kPotLJ | kLatHcp: k_particles_batch<false, kPotLJ | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
-    case kPotMorse | kLatHcp: k_particles_batch<false, kPotMorse | kLatHcp><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+    // pot: the instance code shared by every slab (potential and lattice)
+    switch ((pot & 7) | (full ? 8 : 0)) {
+#define GBPIC_CASE(P)                                                                                          \
+    case 8 | (P): k_particles_batch<true, (P)><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;   \
+    case (P): k_particles_batch<false, (P)><<<grid, kBlock, shmem, st>>>(nslab, total_tiles, nsub); break;
+        GBPIC_FOR_EACH_POT(GBPIC_CASE)
+#undef GBPIC_CASE
     }
 }
 

@@ -16,6 +16,11 @@
 
 namespace gbpic {
 
+// The kernel instances: Eq. (3), the altered potential and the Morse form, on the cubic and the
+// HCP lattice (potential code in bits 0-1, kLatHcp in bit 2).
+#define GBPIC_FOR_EACH_POT3(X) X(kPotLJ) X(kPotAlt) X(kPotMorse) X(kPotLJ | kLatHcp) X(kPotAlt | kLatHcp) \
+    X(kPotMorse | kLatHcp)
+
 constexpr int kQ3Bits = 14;
 constexpr int kQ3 = 1 << kQ3Bits;
 constexpr int kBlock3 = 256;
@@ -560,31 +565,24 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     if (shmem > configured[dev].load()) {
-        for (const void* k : {(const void*)k_particles3<true, kPotLJ>,
-                              (const void*)k_particles3<true, kPotMorse>,
-                              (const void*)k_particles3<true, kPotLJ | kLatHcp>,
-                              (const void*)k_particles3<true, kPotMorse | kLatHcp>,
-                              (const void*)k_particles3<false, kPotLJ>,
-                              (const void*)k_particles3<false, kPotMorse>,
-                              (const void*)k_particles3<false, kPotLJ | kLatHcp>,
-                              (const void*)k_particles3<false, kPotMorse | kLatHcp>}) {
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+#define GBPIC_ATTR(P)                                                                                   \
+        for (const void* k : {(const void*)k_particles3<true, (P)>, (const void*)k_particles3<false, (P)>}) { \
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);           \
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);                \
         }
+        GBPIC_FOR_EACH_POT3(GBPIC_ATTR)
+#undef GBPIC_ATTR
         configured[dev].store(shmem);
     }
     int grid = c.ntiles < c.nsm * 3 ? c.ntiles : c.nsm * 3;
     if (grid < 1) grid = 1;
-    // the instance with the potential family (L-J forms or Morse) and the lattice compiled in
-    switch ((((a.pot_mode & 3) == 2 ? kPotMorse : kPotLJ) | (a.pot_mode & kLatHcp)) | (a.full ? 8 : 0)) {
-    case 8 | kPotLJ: k_particles3<true, kPotLJ><<<grid, kBlock3, shmem, st>>>(a); break;
-    case 8 | kPotMorse: k_particles3<true, kPotMorse><<<grid, kBlock3, shmem, st>>>(a); break;
-    case 8 | kPotLJ | kLatHcp: k_particles3<true, kPotLJ | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
-    case 8 | kPotMorse | kLatHcp: k_particles3<true, kPotMorse | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
-    case kPotLJ: k_particles3<false, kPotLJ><<<grid, kBlock3, shmem, st>>>(a); break;
-    case kPotMorse: k_particles3<false, kPotMorse><<<grid, kBlock3, shmem, st>>>(a); break;
-    case kPotLJ | kLatHcp: k_particles3<false, kPotLJ | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
-    case kPotMorse | kLatHcp: k_particles3<false, kPotMorse | kLatHcp><<<grid, kBlock3, shmem, st>>>(a); break;
+    // the instance with the potential and the lattice compiled in
+    switch ((a.pot_mode & 7) | (a.full ? 8 : 0)) {
+#define GBPIC_CASE(P)                                                                   \
+    case 8 | (P): k_particles3<true, (P)><<<grid, kBlock3, shmem, st>>>(a); break;      \
+    case (P): k_particles3<false, (P)><<<grid, kBlock3, shmem, st>>>(a); break;
+        GBPIC_FOR_EACH_POT3(GBPIC_CASE)
+#undef GBPIC_CASE
     }
 }
 

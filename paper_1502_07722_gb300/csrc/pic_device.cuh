@@ -100,12 +100,16 @@ __device__ __forceinline__ float pair_U(int pot_mode, float c_att, float s_rep, 
 //   F = 24 [ c n^4 P13(h) - c n^2 P7(h) ].
 // ZERO_SKIP: a branch whose factor is 0 contributes nothing even where U' overflows FP32 (a
 // neighbour pulled arbitrarily close at the vacuum edge); the probe calls of the calibration use it.
-// POT: the potential code compiled in (bits 0-1 the family, bit 2 the HCP lattice). kPotLJ: Eq. (3)
-// and the altered potential (pot_mode 0, 1); kPotMorse: the Morse form only; kPotRuntime: the code
-// is read from pot_mode at run time (diagnostics). The particle kernels take the code as a template
-// argument, so that the cubic Lennard-Jones instances carry no Morse or HCP branch (a uniform
-// run-time branch to the out-of-line Morse call cost 6 % of the 3D particle kernel's time).
-enum { kPotRuntime = -1, kPotLJ = 0, kPotMorse = 2, kLatHcp = 4 };
+// POT: the potential code compiled in (bits 0-1 the potential, bit 2 the HCP lattice). kPotLJ: Eq. (3)
+// as printed (pot_mode 0); kPotAlt: the altered potential (pot_mode 1); kPotMorse: the Morse form
+// (pot_mode 2); kPotRuntime: the code is read from pot_mode at run time (diagnostics). The particle
+// kernels take the code as a template argument, so that the plain Lennard-Jones instances carry no
+// branch factor, Morse or HCP code (a uniform run-time branch to the out-of-line Morse call cost 6 %
+// of the 3D particle kernel's time).
+enum { kPotRuntime = -1, kPotLJ = 0, kPotAlt = 1, kPotMorse = 2, kLatHcp = 4 };
+
+// The kernel instance code of a run-time potential code (pot_mode in bits 0-1, kLatHcp in bit 2).
+inline int pot_instance(int code) { return code & 7; }
 
 template <bool ZERO_SKIP = false, int POT = kPotRuntime>
 __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float dn, float h_coef,
@@ -114,10 +118,11 @@ __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float 
     float h = -h_coef * dn * inv43;
     if ((POT >= 0 && (POT & 3) == kPotMorse) || (POT == kPotRuntime && (pot_mode & 3) == 2))
         return morse_axis(c, h, c_att);
+    const int pm = POT >= 0 ? (POT & 3) : pot_mode;
     float ip = c * (1.0f - h);      // r0 / dist to the neighbour on the + side
     float im = c * (1.0f + h);      // r0 / dist to the neighbour on the - side
     if (ip > 0.0f && im > 0.0f) {
-        float fp = branch(pot_mode, c_att, s_rep, ip), fm = branch(pot_mode, c_att, s_rep, im);
+        float fp = branch(pm, c_att, s_rep, ip), fm = branch(pm, c_att, s_rep, im);
         if (ZERO_SKIP && fp != fm)
             return (fp != 0.0f ? fp * lj_dU_inv(ip) : 0.0f) - (fm != 0.0f ? fm * lj_dU_inv(im) : 0.0f);
         float h2 = h * h;
@@ -132,11 +137,11 @@ __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float 
     }
     float f = 0.0f;
     if (ip > 0.0f) {
-        const float fp = branch(pot_mode, c_att, s_rep, ip);
+        const float fp = branch(pm, c_att, s_rep, ip);
         if (!ZERO_SKIP || fp != 0.0f) f += fp * lj_dU_inv(ip);
     }
     if (im > 0.0f) {
-        const float fm = branch(pot_mode, c_att, s_rep, im);
+        const float fm = branch(pm, c_att, s_rep, im);
         if (!ZERO_SKIP || fm != 0.0f) f -= fm * lj_dU_inv(im);
     }
     return f;
@@ -294,6 +299,42 @@ __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, flo
             fz = kHcpS * (bp + b0 + bm);
         }
     }
+}
+
+// Eq. (3) as printed on the cubic lattice, both in-plane axes at once: the cancellation-free form of
+// pair_axis evaluated on (x, z) pairs with packed FP32x2 arithmetic (one instruction per pair).
+// Falls back to pair_axis when a neighbour sits at infinity on either axis (|h| >= 1).
+__device__ __forceinline__ void lj_pair_xz2(float n, float dnx, float dnz, float h_coef, float& fx, float& fz)
+{
+    fx = 0.0f;
+    fz = 0.0f;
+    if (!(n > 0.0f)) return;
+    const float c = fast_cbrt(n);
+    const float inv43 = fast_rcp(n * c);
+    const float hx = -h_coef * dnx * inv43, hz = -h_coef * dnz * inv43;
+    if (fabsf(hx) < 1.0f && fabsf(hz) < 1.0f) {
+        const float2 h = make_float2(hx, hz);
+        const float2 h2 = __fmul2_rn(h, h);
+        float2 t = __fadd2_rn(h2, make_float2(21.0f, 21.0f));
+        t = __ffma2_rn(h2, t, make_float2(35.0f, 35.0f));
+        t = __ffma2_rn(h2, t, make_float2(7.0f, 7.0f));
+        const float2 p7 = __fmul2_rn(h, t);
+        float2 u = __fadd2_rn(h2, make_float2(78.0f, 78.0f));
+        u = __ffma2_rn(h2, u, make_float2(715.0f, 715.0f));
+        u = __ffma2_rn(h2, u, make_float2(1716.0f, 1716.0f));
+        u = __ffma2_rn(h2, u, make_float2(1287.0f, 1287.0f));
+        u = __ffma2_rn(h2, u, make_float2(286.0f, 286.0f));
+        u = __ffma2_rn(h2, u, make_float2(13.0f, 13.0f));
+        const float2 p13 = __fmul2_rn(h, u);
+        // 24 c n^2 (n^2 P13 - P7)
+        const float n2 = n * n, s = 24.0f * c * n2;
+        const float2 d = __ffma2_rn(make_float2(s * n2, s * n2), p13, __fmul2_rn(make_float2(-s, -s), p7));
+        fx = d.x;
+        fz = d.y;
+        return;
+    }
+    fx = pair_axis<false, kPotLJ>(n, c, inv43, dnx, h_coef, 0, 1.0f, 1.0f);
+    fz = pair_axis<false, kPotLJ>(n, c, inv43, dnz, h_coef, 0, 1.0f, 1.0f);
 }
 
 // Pair energy of an atom (units D, twice the per-atom share: the caller halves it) in the x-z plane:

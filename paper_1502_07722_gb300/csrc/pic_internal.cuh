@@ -25,6 +25,7 @@ constexpr int32_t kQOne = 1 << kQBits;
 // status word bits (device, sticky)
 constexpr unsigned kErrNan = 1u;
 constexpr unsigned kErrMove = 2u;
+constexpr unsigned kErrTimeout = 4u;     // a bounded wait on the kernel's own bulk copies gave up
 
 typedef unsigned long long u64;
 
