@@ -649,7 +649,7 @@ ostate* oracle_create(const ocfg* cfg, int32_t with_particles)
     const ocfg* c = &s->c;
     s->dt = c->dt_override > 0 ? c->dt_override : c->cfl * c->dx / (O_C * sqrt(2.0));
     s->nsp = c->mode == 0 ? 2 : 1;
-    s->w = c->n_atoms * c->dx * c->dx / (double)c->ppc_ion;          /* atoms per metre of y */
+    s->w = c->n_atoms * c->dx * c->dx / (double)(c->ppc_ion > 0 ? c->ppc_ion : 1);   /* atoms per metre of y */
     s->r0 = c->r0 > 0 ? c->r0 : pow(c->n_atoms, -1.0 / 3.0);
     s->D = c->D_eV * O_QE;
     /* node sum (units 2^-32 of one macro-atom) -> density in units of n0 = r0^-3 */
@@ -1331,7 +1331,7 @@ ostate3* oracle3_create(const ocfg3* cfg, int32_t with_particles)
     const ocfg3* c = &s->c;
     s->dt = c->dt_override > 0 ? c->dt_override : c->cfl * c->dx / (O_C * sqrt(3.0));
     s->nsp = c->mode == 0 ? 2 : 1;
-    s->w = c->n_atoms * c->dx * c->dx * c->dx / (double)c->ppc_ion;
+    s->w = c->n_atoms * c->dx * c->dx * c->dx / (double)(c->ppc_ion > 0 ? c->ppc_ion : 1);
     s->r0 = c->r0 > 0 ? c->r0 : pow(c->n_atoms, -1.0 / 3.0);
     s->D = c->D_eV * O_QE;
     s->rho_scale = s->w / (4398046511104.0 * c->dx * c->dx * c->dx) * pow(s->r0, 3.0);   /* 2^42 */

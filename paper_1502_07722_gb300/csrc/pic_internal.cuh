@@ -109,7 +109,7 @@ struct Ctx {
     int32_t* scan_tmp;    // block sums
     double* partials;     // energy block partials
     double* red_out;      // 8 doubles
-    unsigned* status;
+    unsigned* status;     // 4 words: sticky error bits, validation count, particle-kernel ticket, spare
     int64_t step;
     int32_t steps_since_sort;
     int sticky;
