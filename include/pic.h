@@ -19,11 +19,22 @@
  *
  * Fixed point: a coordinate x (cells) deposits with X = i*2^16 + rint(f * 2^16); node weight
  * S_j = max(0, 2^16 - |X - 2^16 j|). Node sums are int64 and exact, so they are identical for
- * any summation order (deterministic) and bit-comparable with a CPU reference.
+ * any summation order (deterministic) and bit-comparable with a CPU reference. The out-of-plane
+ * current uses the code V = rint(beta_y 2^b), b = 18 unless the slab's particles per cell (both
+ * species, with a quarter headroom) could overflow J6y at that resolution, then the largest b
+ * that cannot. A node collects from the particles of 4 x 4 cells (4^3 in 3D); the largest
+ * contribution of one particle is 6 * 2^(32+b) to J6y, 2^34 to J2x/J2z and 2^33 to the density
+ * in 2D, 3 * 2^44 to a 3D current and 2^43 to the 3D density. So the sums are exact while no cell
+ * holds more than 2^63 / (16 * 6 * 2^(32+b)) particles (85 at b = 18) in the 2D full mode, 2730
+ * in the 3D full mode, 2^28 and 2^17 without currents (transport mode). pic_init refuses a slab
+ * whose initial particles per cell exceed the limit (PIC_EOVERFLOW); every cell sort checks the
+ * largest cell count of each species and raises a sticky PIC_EOVERFLOW when their sum exceeds it
+ * (a pile-up between two sorts is found at the next sort).
  *
  * Return codes: 0 on success, a negative PIC_E* code on error. Errors raised inside kernels
- * (non-finite momentum, a move of a cell or more, a bounded wait that gave up) are sticky:
- * pic_step reports them and every later call on the context returns them until pic_free.
+ * (non-finite momentum, a move of a cell or more, a cell holding more particles than the fixed-point
+ * range allows) are sticky: pic_step reports them and every later call on the context returns them
+ * until pic_free.
  */
 #ifndef GBPIC_PIC_H
 #define GBPIC_PIC_H
@@ -49,8 +60,8 @@ enum {
     PIC_ENAN = -4,       /* a particle momentum became non-finite                          */
     PIC_EMOVE = -5,      /* a particle moved a cell or more in one step (CFL is violated)  */
     PIC_ESTATE = -6,     /* call not valid in this mode (e.g. fields in transport mode)    */
-    PIC_EOVERFLOW = -7,  /* an int64 fixed-point node sum could overflow (refused at init)  */
-    PIC_ETIMEOUT = -8    /* a kernel's bounded wait on its own asynchronous copies gave up   */
+    PIC_EOVERFLOW = -7   /* more particles in one cell than the int64 node sums are proven
+                            exact for: refused at init, sticky when a sort finds a pile-up    */
 };
 
 enum { PIC_MODE_FULL = 0, PIC_MODE_TRANSPORT = 1 };
@@ -146,7 +157,9 @@ typedef struct pic_ctx pic_ctx;
  * against it. Host only; no errors. (Not a step of the paper's method.) */
 PIC_API size_t pic_config_bytes(void);
 
-/* Bytes of device workspace pic_init needs for cfg. */
+/* Bytes of device workspace pic_init needs for cfg. Returns PIC_EINVAL for an invalid cfg and
+ * PIC_EOVERFLOW for a slab whose particles per cell exceed the fixed-point range (see above);
+ * makes no CUDA call. */
 PIC_API int pic_workspace_size(const pic_config* cfg, size_t* bytes);
 
 /* Create a simulation on the current device: generate the initial slab (paper: the damage

@@ -99,6 +99,7 @@ def lib():
             "oracle_set_step": (None, [vp, ctypes.c_int64]),
             "oracle_pair_force": (None, [vp, _D]),
             "oracle_gather_density": (None, [vp, ctypes.c_double, ctypes.c_double, _D]),
+            "oracle_gather_fields": (None, [vp, ctypes.c_double, ctypes.c_double, _D]),
             "oracle_step": (None, [vp, ctypes.c_int32]),
             "oracle_maxwell": (None, [vp]),
             "oracle_energy": (None, [vp, _D]),
@@ -109,10 +110,11 @@ def lib():
             "oracle_morse_dU": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "oracle_neighbor_distances": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]),
             "oracle_boris": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
-            "oracle_jy_code": (ctypes.c_int64, [ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+            "oracle_jy_code": (ctypes.c_int64, [ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int32]),
+            "oracle_jy_bits": (ctypes.c_int32, [ctypes.c_int64]),
             "oracle_deposit_density": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D, _I64]),
             "oracle_deposit_current": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
-                                              _D, _D, _D, _D, _F, _F, _F, _I64, _I64, _I64]),
+                                              _D, _D, _D, _D, _F, _F, _F, ctypes.c_int32, _I64, _I64, _I64]),
         }
         sig.update({
             "oracle_transport_grad": (None, [vp, ctypes.c_int32, _D, ctypes.c_double, _D]),
@@ -153,6 +155,7 @@ def lib():
             "oracle3_get_current": (None, [vp, _I64]),
             "oracle3_set_current": (None, [vp, _I64]),
             "oracle3_pair_force": (None, [vp, _D]),
+            "oracle3_gather_fields": (None, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]),
             "oracle3_maxwell": (None, [vp]),
             "oracle3_step": (None, [vp, ctypes.c_int32]),
             "oracle3_energy": (None, [vp, _D]),
@@ -312,6 +315,12 @@ class Oracle:
         lib().oracle_gather_density(self._s, float(x), float(z), _p(out, ctypes.c_double))
         return out
 
+    def gather_fields(self, x, z):
+        """(Ex, Ey, Ez, Bx, By, Bz) interpolated to the point (x, z) in cells, as the push sees them."""
+        out = np.zeros(6)
+        lib().oracle_gather_fields(self._s, float(x), float(z), _p(out, ctypes.c_double))
+        return out
+
     def energy(self):
         out = np.empty(5, np.float64)
         lib().oracle_energy(self._s, _p(out, ctypes.c_double))
@@ -425,8 +434,14 @@ def boris(q, m, dt, E, B, F, u):
     return u
 
 
-def jy_code(ux, uy, uz):
-    return lib().oracle_jy_code(float(np.float32(ux)), float(np.float32(uy)), float(np.float32(uz)))
+def jy_code(ux, uy, uz, bits=18):
+    """J_y code V = rint(beta_y 2^bits) of one particle, taken in FP32 as the kernel takes it."""
+    return lib().oracle_jy_code(float(np.float32(ux)), float(np.float32(uy)), float(np.float32(uz)), int(bits))
+
+
+def jy_bits(per_cell):
+    """Resolution of the J_y code for a 2D slab with per_cell macroparticles per cell (both species)."""
+    return lib().oracle_jy_bits(int(per_cell))
 
 
 def deposit_density(nx, nz, x, z):
@@ -437,14 +452,14 @@ def deposit_density(nx, nz, x, z):
     return out.reshape(nz + 1, nx)
 
 
-def deposit_current(nx, nz, sign, x0, z0, x1, z1, ux, uy, uz, out=None):
+def deposit_current(nx, nz, sign, x0, z0, x1, z1, ux, uy, uz, out=None, bits=18):
     x0, z0, x1, z1 = (_f64(a) for a in (x0, z0, x1, z1))
     ux, uy, uz = (np.ascontiguousarray(a, np.float32) for a in (ux, uy, uz))
     if out is None:
         out = np.zeros((3, nz + 1, nx), np.int64)
     lib().oracle_deposit_current(nx, nz, len(x0), sign, _p(x0, ctypes.c_double), _p(z0, ctypes.c_double),
                                  _p(x1, ctypes.c_double), _p(z1, ctypes.c_double), _p(ux, ctypes.c_float),
-                                 _p(uy, ctypes.c_float), _p(uz, ctypes.c_float),
+                                 _p(uy, ctypes.c_float), _p(uz, ctypes.c_float), int(bits),
                                  _p(out[0], ctypes.c_int64), _p(out[1], ctypes.c_int64), _p(out[2], ctypes.c_int64))
     return out
 
@@ -547,6 +562,12 @@ class Oracle3D:
         out = np.empty(3 * n, np.float64)
         lib().oracle3_pair_force(self._s, _p(out, ctypes.c_double))
         return out.reshape(n, 3)
+
+    def gather_fields(self, x, y, z):
+        """(Ex, Ey, Ez, Bx, By, Bz) interpolated to the point (x, y, z) in cells, as the push sees them."""
+        out = np.zeros(6)
+        lib().oracle3_gather_fields(self._s, float(x), float(y), float(z), _p(out, ctypes.c_double))
+        return out
 
     def maxwell(self):
         lib().oracle3_maxwell(self._s)

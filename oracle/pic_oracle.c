@@ -33,7 +33,9 @@
  *     doubled (mirror image of the slab behind the wall). x is periodic.
  *   - current deposition (not described in the paper) is Esirkepov's charge-conserving scheme
  *     for linear weights, evaluated in the same fixed point; J_y uses the code
- *     V = rint(beta_y * 2^18) taken in FP32 exactly as the kernel takes it.
+ *     V = rint(beta_y * 2^b) taken in FP32 exactly as the kernel takes it, b = 18 unless the
+ *     slab's particles per cell could overflow the int64 J_y node sums at that resolution
+ *     (jy_bits below).
  *   - push: relativistic Boris with u = gamma v / c at half steps; the pair force is added to
  *     both half electric kicks.
  *   - fields: 2D3V Yee, B advanced in two half steps around the E update, first-order Mur at
@@ -106,6 +108,7 @@ typedef struct {
     int k_ant;
     double injected;                    /* field energy that crossed the row below the antenna
                                            towards the slab (J per metre of y)               */
+    int32_t jy_bits;                    /* resolution of the J_y code (oracle_jy_bits)        */
 } ostate;
 
 static int64_t imod(int64_t a, int64_t n) { int64_t r = a % n; return r < 0 ? r + n : r; }
@@ -317,11 +320,11 @@ static void deposit_current_one(int nx, int nz, int64_t* J2x, int64_t* J6y, int6
     }
 }
 
-/* J_y code: V = rint(beta_y * 2^18), beta_y = u_y / gamma, all in FP32 without fused
+/* J_y code: V = rint(beta_y * 2^bits), beta_y = u_y / gamma, all in FP32 without fused
  * multiply-add, so that the decision is the kernel's (this file is built with contraction off).
  * The kernel's definition of 1/gamma: for u^2 < 2^-10 the series 1 - u^2 (1/2 - 3/8 u^2),
  * otherwise 1 / sqrt(1 + u^2). */
-int64_t oracle_jy_code(float ux, float uy, float uz)
+int64_t oracle_jy_code(float ux, float uy, float uz, int32_t bits)
 {
     float u2 = ux * ux;
     u2 = u2 + uy * uy;
@@ -336,7 +339,22 @@ int64_t oracle_jy_code(float ux, float uy, float uz)
         float g = sqrtf(1.0f + u2);
         by = uy / g;
     }
-    return (int64_t)rintf(by * 262144.0f);
+    return (int64_t)rintf(by * ldexpf(1.0f, bits));
+}
+
+/* Resolution of the J_y code for a 2D slab with the given macroparticles per cell (both species).
+ * One particle adds at most 2^bits * 6 * 2^32 to a J_y node sum (|beta_y| < 1; the six-fold
+ * weight of a node is at most 6 * 2^32) and the particles that reach a node sit in a block of
+ * 4 x 4 cells, so the int64 sum cannot overflow while such a block holds at most
+ * floor(2^63 / (6 * 2^(32+bits))) particles. bits = 18, or the largest bits whose limit holds
+ * 1.25 times the 16 * per_cell particles of a block of the initial slab. */
+int32_t oracle_jy_bits(int64_t per_cell)
+{
+    for (int32_t b = 18; b >= 1; b--) {
+        int64_t limit = (INT64_C(1) << 31) / (INT64_C(6) << b);
+        if ((double)limit >= 1.25 * 16.0 * (double)per_cell) return b;
+    }
+    return 0;
 }
 
 /* Unwrap the new x coordinate (periodic, period nx) to within half a period of the old one. */
@@ -352,13 +370,13 @@ static int64_t unwrap_X(int64_t X0, int64_t X1, int nx)
  * (FP32, the state the kernel stores). Accumulates into J2x, J6y, J2z. */
 void oracle_deposit_current(int32_t nx, int32_t nz, int64_t n, int32_t sign,
                             const double* x0, const double* z0, const double* x1, const double* z1,
-                            const float* ux, const float* uy, const float* uz,
+                            const float* ux, const float* uy, const float* uz, int32_t bits,
                             int64_t* J2x, int64_t* J6y, int64_t* J2z)
 {
     for (int64_t p = 0; p < n; p++) {
         int64_t X0 = llrint(x0[p] * (double)QS), Z0 = llrint(z0[p] * (double)QS);
         int64_t X1 = unwrap_X(X0, llrint(x1[p] * (double)QS), nx), Z1 = llrint(z1[p] * (double)QS);
-        deposit_current_one(nx, nz, J2x, J6y, J2z, sign, X0, Z0, X1, Z1, oracle_jy_code(ux[p], uy[p], uz[p]));
+        deposit_current_one(nx, nz, J2x, J6y, J2z, sign, X0, Z0, X1, Z1, oracle_jy_code(ux[p], uy[p], uz[p], bits));
     }
 }
 
@@ -515,7 +533,7 @@ static void full_step_E(ostate* s)
     double* nEy = malloc(sizeof(double) * nn);
     /* J (integer) -> dt J / eps0 */
     double cjx = O_QE * s->w / (8589934592.0 * s->c.dx * O_EPS0);                 /* 2^33 */
-    double cjy = O_QE * s->w * O_C * s->dt / (6.0 * 1125899906842624.0 * s->c.dx * s->c.dx * O_EPS0); /* 6*2^50 */
+    double cjy = O_QE * s->w * O_C * s->dt / (6.0 * ldexp(1.0, 32 + s->jy_bits) * s->c.dx * s->c.dx * O_EPS0);
     double tmid = ((double)s->step + 0.5) * s->dt;
     for (int k = 0; k <= nz; k++)
         for (int i = 0; i < nx; i++) {
@@ -670,6 +688,7 @@ ostate* oracle_create(const ocfg* cfg, int32_t with_particles)
     s->E0 = sqrt(2.0 * c->I0 / (O_EPS0 * O_C));
     s->omega = c->lambda > 0 ? 2.0 * O_PI * O_C / c->lambda : 0.0;
     s->kwave = s->omega / O_C;
+    s->jy_bits = oracle_jy_bits((int64_t)c->ppc_ion + (int64_t)c->ppc_electron);
     s->k_ant = c->nz - 2;
     double L = (double)(s->k_ant - c->slab_k) * c->dx;                 /* antenna -> focus */
     s->t_ant = c->t_peak - L / O_C;
@@ -754,20 +773,31 @@ void oracle_gather_density(const ostate* s, double x, double z, double out[3])
     gather_density(s, x, z, &out[0], &out[1], &out[2]);
 }
 
+/* E and B at a point (x, z) in cells: each Yee component interpolated bilinearly from its own
+ * staggered positions (paper, the PIC-cycle paragraph: fields interpolated to the particle) */
+static void gather_EB(const ostate* s, double x, double z, double E[3], double B[3])
+{
+    E[0] = gather_field(s, s->F[0], x, z, 0.5, 0.0);
+    E[1] = gather_field(s, s->F[1], x, z, 0.0, 0.0);
+    E[2] = gather_field(s, s->F[2], x, z, 0.0, 0.5);
+    B[0] = gather_field(s, s->F[3], x, z, 0.0, 0.5);
+    B[1] = gather_field(s, s->F[4], x, z, 0.5, 0.5);
+    B[2] = gather_field(s, s->F[5], x, z, 0.5, 0.0);
+}
+
+/* the fields the push sees at (x, z): out = Ex, Ey, Ez, Bx, By, Bz, for pinning the gather */
+void oracle_gather_fields(const ostate* s, double x, double z, double out[6])
+{
+    gather_EB(s, x, z, out, out + 3);
+}
+
 /* advance one particle (position in cells, u = gamma v / c) through gather, pair force, Boris and
  * the move with walls, from the context's fields and node density */
 static void push_one(const ostate* s, int sp, double* px, double* pz, double u[3])
 {
     double x = *px, z = *pz;
     double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, Fp[3] = {0, 0, 0};
-    if (s->c.mode == 0) {
-        E[0] = gather_field(s, s->F[0], x, z, 0.5, 0.0);
-        E[1] = gather_field(s, s->F[1], x, z, 0.0, 0.0);
-        E[2] = gather_field(s, s->F[2], x, z, 0.0, 0.5);
-        B[0] = gather_field(s, s->F[3], x, z, 0.0, 0.5);
-        B[1] = gather_field(s, s->F[4], x, z, 0.5, 0.5);
-        B[2] = gather_field(s, s->F[5], x, z, 0.5, 0.0);
-    }
+    if (s->c.mode == 0) gather_EB(s, x, z, E, B);
     if (s->pair[sp]) pair_force_at(s, x, z, Fp, NULL);
     oracle_boris(s->q[sp], s->m[sp], s->dt, E, B, Fp, u);
     double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -895,7 +925,7 @@ void oracle_step(ostate* s, int32_t nsteps)
                 for (int64_t p = 0; p < n; p++) {
                     float fux = (float)s->ux[sp][p], fuy = (float)s->uy[sp][p], fuz = (float)s->uz[sp][p];
                     oracle_deposit_current(s->c.nx, s->c.nz, 1, sign, x0 + p, z0 + p, s->x[sp] + p, s->z[sp] + p,
-                                           &fux, &fuy, &fuz, s->J[0], s->J[1], s->J[2]);
+                                           &fux, &fuy, &fuz, s->jy_bits, s->J[0], s->J[1], s->J[2]);
                 }
             }
             free(x0); free(z0);
@@ -1440,18 +1470,28 @@ void oracle3_maxwell(ostate3* s)
     half_step_B3(s);
 }
 
+/* 3D E and B at (x, y, z): trilinear interpolation of each component from its own staggered
+ * positions */
+static void gather_EB3(const ostate3* s, double x, double y, double z, double E[3], double B[3])
+{
+    E[0] = gather_field3(s, s->F[0], x, y, z, 0.5, 0.0, 0.0);
+    E[1] = gather_field3(s, s->F[1], x, y, z, 0.0, 0.5, 0.0);
+    E[2] = gather_field3(s, s->F[2], x, y, z, 0.0, 0.0, 0.5);
+    B[0] = gather_field3(s, s->F[3], x, y, z, 0.0, 0.5, 0.5);
+    B[1] = gather_field3(s, s->F[4], x, y, z, 0.5, 0.0, 0.5);
+    B[2] = gather_field3(s, s->F[5], x, y, z, 0.5, 0.5, 0.0);
+}
+
+void oracle3_gather_fields(const ostate3* s, double x, double y, double z, double out[6])
+{
+    gather_EB3(s, x, y, z, out, out + 3);
+}
+
 static void push_one3(const ostate3* s, int sp, double* px, double* py, double* pz, double u[3])
 {
     double x = *px, y = *py, z = *pz;
     double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, Fp[3] = {0, 0, 0};
-    if (s->c.mode == 0) {
-        E[0] = gather_field3(s, s->F[0], x, y, z, 0.5, 0.0, 0.0);
-        E[1] = gather_field3(s, s->F[1], x, y, z, 0.0, 0.5, 0.0);
-        E[2] = gather_field3(s, s->F[2], x, y, z, 0.0, 0.0, 0.5);
-        B[0] = gather_field3(s, s->F[3], x, y, z, 0.0, 0.5, 0.5);
-        B[1] = gather_field3(s, s->F[4], x, y, z, 0.5, 0.0, 0.5);
-        B[2] = gather_field3(s, s->F[5], x, y, z, 0.5, 0.5, 0.0);
-    }
+    if (s->c.mode == 0) gather_EB3(s, x, y, z, E, B);
     if (sp == 0) pair_force3_at(s, x, y, z, Fp, NULL);
     oracle_boris(s->q[sp], s->m[sp], s->dt, E, B, Fp, u);
     double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);

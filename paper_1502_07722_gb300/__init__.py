@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libgbpic.so")
 
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENAN, PIC_EMOVE, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PIC_EOVERFLOW, PIC_ETIMEOUT = -7, -8
+PIC_EOVERFLOW = -7
 PIC_MODE_FULL, PIC_MODE_TRANSPORT = 0, 1
 PIC_LASER_NONE, PIC_LASER_PLANE, PIC_LASER_GAUSSIAN = 0, 1, 2
 PIC_TEMP_UNIFORM, PIC_TEMP_SPOT = 0, 1

@@ -28,7 +28,8 @@ namespace {
 constexpr int kMaxEnergyBlocks = 1024;
 
 struct Layout {
-    int32_t dims, nx, ny, nz, T, ntx, nty, ntz, ntiles, nkeys, nsp;
+    int32_t dims, nx, ny, nz, T, ntx, nty, ntz, ntiles, nkeys, nsp, jy_bits;
+    int64_t count_limit;
     size_t nn;
     int64_t cap[2], n0[2];
     size_t total;
@@ -88,6 +89,13 @@ int derive_layout(const pic_config* cfg, Layout& L)
         L.cap[s] = s < L.nsp ? (cfg->max_particles > 0 ? cfg->max_particles : L.n0[s]) : 0;
         if (L.cap[s] < L.n0[s] || L.cap[s] >= (1LL << 31)) return PIC_EINVAL;
     }
+    // fixed-point range of the node sums (PIC_EOVERFLOW): the initial particles per cell must fit
+    const int64_t per_cell = (int64_t)(cfg->ppc_ion > 0 ? cfg->ppc_ion : 0) + (L.nsp > 1 ? cfg->ppc_electron : 0);
+    const int full = cfg->mode == PIC_MODE_FULL;
+    L.jy_bits = (L.dims == 2 && full) ? choose_jy_bits(per_cell) : 18;
+    if (L.jy_bits < 1) return PIC_EOVERFLOW;
+    L.count_limit = count_limit(L.dims, full, L.jy_bits);
+    if ((L.dims == 3 ? 64 : 16) * per_cell > L.count_limit) return PIC_EOVERFLOW;
     size_t t = 0;
     const int arrays = L.dims == 3 ? 7 : 6;
     for (int s = 0; s < 2; s++) t += 2 * arrays * align256(4 * (size_t)L.cap[s]) + align256(4 * (size_t)(L.ntiles + 1));
@@ -96,7 +104,7 @@ int derive_layout(const pic_config* cfg, Layout& L)
     t += align256(4 * 8 * plane) + 2 * align256(4 * plane) + align256(8);
     t += 2 * align256(4 * ((size_t)L.nkeys + 1));
     t += align256(4 * (((size_t)L.nkeys + 2047) / 2048 + 1));
-    t += align256(8 * 5 * (size_t)kMaxEnergyBlocks) + align256(8 * 8) + align256(16);
+    t += align256(8 * 5 * (size_t)kMaxEnergyBlocks) + align256(8 * 8) + align256(32);
     L.total = t;
     return PIC_OK;
 }
@@ -130,7 +138,7 @@ int finish_status(pic_ctx* h)
     }
     if (st & kErrNan) c.sticky = PIC_ENAN;
     else if (st & kErrMove) c.sticky = PIC_EMOVE;
-    else if (st & kErrTimeout) c.sticky = PIC_ETIMEOUT;
+    else if (st & kErrOverflow) c.sticky = PIC_EOVERFLOW;
     return c.sticky;
 }
 
@@ -209,6 +217,8 @@ StepArgs make_step_args(Ctx& c)
     a.status = c.status;
     a.nsp = c.nsp;
     for (int s = 0; s < 2; s++) a.sp[s] = c.sp[s];
+    a.jy_scale = ldexpf(1.0f, c.jy_bits);
+    a.jy_zero = ldexpf(1.0f, -(c.jy_bits + 1));
     return a;
 }
 
@@ -261,6 +271,8 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     c.nn = L.nn;
     c.nsp = L.nsp;
     c.k_ant = L.nz - 2;
+    c.jy_bits = L.jy_bits;
+    c.count_limit = (int32_t)(L.count_limit < 2147483647 ? L.count_limit : 2147483647);
     // derived physics
     const bool d3 = L.dims == 3;
     c.dt = cfg->dt_override > 0 ? cfg->dt_override : cfg->cfl * cfg->dx / (kC * sqrt(d3 ? 3.0 : 2.0));
@@ -307,7 +319,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     c.scan_tmp = cv.take<int32_t>(((size_t)L.nkeys + 2047) / 2048 + 1);
     c.partials = cv.take<double>(5 * (size_t)kMaxEnergyBlocks);
     c.red_out = cv.take<double>(8);
-    c.status = cv.take<unsigned>(4);
+    c.status = cv.take<unsigned>(8);
     if (cv.p > cv.end) {
         delete h;
         return PIC_ENOMEM;
@@ -372,7 +384,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
     for (int q = 0; q < 2; q++) ok &= cudaMemsetAsync(c.rho[q], 0, 8 * L.nn, c.stream) == cudaSuccess;
     ok &= cudaMemsetAsync(c.mur_save, 0, 4 * 8 * plane, c.stream) == cudaSuccess;
     ok &= cudaMemsetAsync(c.red_out, 0, 8 * sizeof(double), c.stream) == cudaSuccess;   // incl. the injected-energy sum
-    ok &= cudaMemsetAsync(c.status, 0, 16, c.stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(c.status, 0, 32, c.stream) == cudaSuccess;
     if (!ok) {
         delete h;
         return PIC_ECUDA;
@@ -884,7 +896,7 @@ const char* pic_strerror(int code)
     case PIC_EMOVE: return "a particle moved one cell or more in one step";
     case PIC_ESTATE: return "operation not valid in this mode";
     case PIC_EOVERFLOW: return "a fixed-point node sum could overflow int64 for this configuration";
-    case PIC_ETIMEOUT: return "a kernel's bounded wait on its own asynchronous copies gave up";
+
     default: return "unknown error";
     }
 }

@@ -286,7 +286,7 @@ int pic_batch_step(pic_batch* b, int32_t nsteps)
         if (cudaMemcpy(&stw, c.status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
         if (stw & kErrNan) c.sticky = PIC_ENAN;
         else if (stw & kErrMove) c.sticky = PIC_EMOVE;
-        else if (stw & kErrTimeout) c.sticky = PIC_ETIMEOUT;
+        else if (stw & kErrOverflow) c.sticky = PIC_EOVERFLOW;
         if (c.sticky && !b->sticky) b->sticky = c.sticky;
     }
     return b->sticky;

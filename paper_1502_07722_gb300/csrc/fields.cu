@@ -178,7 +178,7 @@ FieldArgs make_field_args(const Ctx& c)
     f.h_b = (float)(0.5 * c.dt / c.cfg.dx);
     f.h_e = (float)(kC * kC * c.dt / c.cfg.dx);
     f.cj = (float)(kQe * c.w / (8589934592.0 * c.cfg.dx * kEps0));
-    f.cjy = (float)(kQe * c.w * kC * c.dt / (6.0 * 1125899906842624.0 * c.cfg.dx * c.cfg.dx * kEps0));
+    f.cjy = (float)(kQe * c.w * kC * c.dt / (6.0 * ldexp(1.0, 32 + c.jy_bits) * c.cfg.dx * c.cfg.dx * kEps0));
     const double cdt = kC * c.dt;
     f.mur = (float)((cdt - c.cfg.dx) / (cdt + c.cfg.dx));
     for (int q = 0; q < 6; q++) f.F[q] = c.F[q];

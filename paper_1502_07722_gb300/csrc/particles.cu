@@ -275,8 +275,8 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     fz_io = nfz;
 
     const int x0 = qoff(fx), x1 = qoff(nfx), z0 = qoff(fz), z1 = qoff(nfz);
-    // |u_y| < 2^-19 gives |beta_y| 2^18 < 1/2, i.e. V = 0 without evaluating the code
-    const int V = (kCurrent && fabsf(uy) >= 1.9073486328125e-06f) ? kSign * jy_code(ux, uy, uz) : 0;
+    // |u_y| < 2^-(b+1) gives |beta_y| 2^b < 1/2, i.e. V = 0 without evaluating the code
+    const int V = (kCurrent && fabsf(uy) >= a.jy_zero) ? kSign * jy_code(ux, uy, uz, a.jy_scale) : 0;
     const bool incell = inwin && (di | dk) == 0;
     if (KIND == kElectron && incell) {
         // an electron that stays in its cell (almost every electron): it always moves in fixed

@@ -206,11 +206,12 @@ __device__ __forceinline__ void boris(float& ux, float& uy, float& uz, float ex,
     ux += e_kick * ex; uy += e_kick * ey; uz += e_kick * ez;
 }
 
-// J_y code V = rint(beta_y 2^18), beta_y = u_y / gamma, taken in FP32 with explicit rounding (no
-// fused multiply-add) so that it is reproducible outside the GPU. For u^2 < 2^-10 the inverse
-// Lorentz factor is the series 1 - u^2 (1/2 - 3/8 u^2) (next term 5/16 u^6 < 3e-10); otherwise
-// it is 1 / sqrt(1 + u^2) with IEEE square root and division.
-__device__ __forceinline__ int jy_code(float ux, float uy, float uz)
+// J_y code V = rint(beta_y 2^b), beta_y = u_y / gamma, taken in FP32 with explicit rounding (no
+// fused multiply-add) so that it is reproducible outside the GPU; scale = 2^b (b = 18 unless the
+// slab's particles per cell call for a coarser code, see choose_jy_bits). For u^2 < 2^-10 the
+// inverse Lorentz factor is the series 1 - u^2 (1/2 - 3/8 u^2) (next term 5/16 u^6 < 3e-10);
+// otherwise it is 1 / sqrt(1 + u^2) with IEEE square root and division.
+__device__ __forceinline__ int jy_code(float ux, float uy, float uz, float scale)
 {
     float u2 = __fmul_rn(ux, ux);
     u2 = __fadd_rn(u2, __fmul_rn(uy, uy));
@@ -224,7 +225,7 @@ __device__ __forceinline__ int jy_code(float ux, float uy, float uz)
     } else {
         by = __fdiv_rn(uy, __fsqrt_rn(__fadd_rn(1.0f, u2)));
     }
-    return __float2int_rn(__fmul_rn(by, 262144.0f));
+    return __float2int_rn(__fmul_rn(by, scale));
 }
 
 // approximate transcendental helpers (hardware ex2 / lg2 / rcp, relative error ~1e-7)

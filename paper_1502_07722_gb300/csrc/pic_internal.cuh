@@ -25,7 +25,7 @@ constexpr int32_t kQOne = 1 << kQBits;
 // status word bits (device, sticky)
 constexpr unsigned kErrNan = 1u;
 constexpr unsigned kErrMove = 2u;
-constexpr unsigned kErrTimeout = 4u;     // a bounded wait on the kernel's own bulk copies gave up
+constexpr unsigned kErrOverflow = 8u;    // more particles per cell than the int64 node sums are proven for
 
 typedef unsigned long long u64;
 
@@ -79,6 +79,8 @@ struct StepArgs {
     unsigned* status;
     int32_t nsp;
     Species sp[2];
+    float jy_scale;                           // 2^jy_bits: the J_y code V = rint(beta_y 2^jy_bits)
+    float jy_zero;                            // 2^-(jy_bits + 1): |u_y| below it gives V = 0
 };
 
 struct Ctx {
@@ -109,7 +111,11 @@ struct Ctx {
     int32_t* scan_tmp;    // block sums
     double* partials;     // energy block partials
     double* red_out;      // 8 doubles
-    unsigned* status;     // 4 words: sticky error bits, validation count, particle-kernel ticket, spare
+    unsigned* status;     // 8 words: sticky error bits, validation count, particle-kernel ticket, spare,
+                          // largest particle count of one block of 4^dims cells per species (last sort)
+    int32_t jy_bits;      // resolution of the J_y code (2D full mode)
+    int32_t count_limit;  // particles per block of 4^dims cells (both species) for which no int64
+                          // node sum can overflow
     int64_t step;
     int32_t steps_since_sort;
     int sticky;
@@ -148,6 +154,11 @@ struct FieldArgs {
 // kernels launched from the host side of the library (defined in the .cu files)
 void launch_init_particles(Ctx& c, int s, cudaStream_t st);
 void launch_sort_species(Ctx& c, int s, cudaStream_t st, int64_t* launches);
+// Fixed-point range: the J_y code resolution for a 2D full-mode slab of n particles per cell (both
+// species) and the particle count per block of 4^dims cells up to which every int64 node sum is
+// proven exact.
+int choose_jy_bits(int64_t n_per_cell);
+int64_t count_limit(int dims, int full, int jy_bits);
 void launch_deposit_density(Ctx& c, u64* out, cudaStream_t st);
 void launch_crater_profile(Ctx& c, const u64* rho0, double depth_scale, double* out, cudaStream_t st);
 // One device-to-device copy (src != NULL) or clear (src == NULL) of `bytes` bytes.

@@ -10,6 +10,8 @@
 // share cache sectors, without a transposing copy through shared memory.
 // The order of particles inside one cell is not fixed (atomic cursors); nothing downstream
 // depends on it because every deposit is an exact integer sum.
+#include <cmath>
+
 #include "pic_internal.cuh"
 
 namespace gbpic {
@@ -138,6 +140,58 @@ __global__ void k_scan_add(int32_t* out, const int32_t* __restrict__ bsum, int n
     if (j == 0) out[n] = total;
 }
 
+// Key of cell (i, j, k) (j = 0 in 2D), as cell_key computes it from the cell index.
+__device__ __forceinline__ int key_of(int i, int j, int k, const KeyGeo& g)
+{
+    const int tx = i / g.T, tz = k / g.T;
+    if (g.dims == 2) return (tz * g.ntx + tx) * g.T * g.T + (k - tz * g.T) * g.T + (i - tx * g.T);
+    const int ty = j / g.T;
+    const int tile = (tz * g.nty + ty) * g.ntx + tx;
+    return ((tile * g.T + (k - tz * g.T)) * g.T + (j - ty * g.T)) * g.T + (i - tx * g.T);
+}
+
+// The largest particle count (of one species) over the blocks of 4 cells per axis (x, y periodic;
+// blocks reaching past the last row of cells are cut there): the particles that can reach one
+// node in a step sit in such a block. One atomicMax per warp into *out.
+__global__ void k_block_max(const int32_t* __restrict__ count, KeyGeo kg, int nz, unsigned* out)
+{
+    const int64_t ncell = (int64_t)kg.nx * kg.ny * nz;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nround = (ncell + 31) & ~(int64_t)31;
+    unsigned m = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nround; c += stride) {
+        if (c < ncell) {
+            const int i = (int)(c % kg.nx);
+            const int64_t q = c / kg.nx;
+            const int j = (int)(q % kg.ny), k = (int)(q / kg.ny);
+            unsigned s = 0;
+            for (int dk = 0; dk < 4 && k + dk < nz; dk++)
+                for (int dj = 0; dj < (kg.dims == 3 ? 4 : 1); dj++) {
+                    const int jj = (j + dj) % kg.ny;
+                    for (int di = 0; di < 4; di++) s += (unsigned)count[key_of((i + di) % kg.nx, jj, k + dk, kg)];
+                }
+            m = max(m, s);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+static int64_t ncell_blocks(const Ctx& c)
+{
+    const int64_t ncell = (int64_t)c.nx * c.ny * c.nz;
+    return (ncell + 255) / 256 > 0 ? (ncell + 255) / 256 : 1;
+}
+
+// Fixed-point range: every int64 node sum is exact while the particles that can reach one node
+// (both species: bounded by the sum of the two species' largest block counts from their last
+// sorts) stay within the limit the context was set up for; beyond it the sticky overflow bit is
+// raised.
+__global__ void k_count_check(unsigned* status, long long limit)
+{
+    if (threadIdx.x == 0 && (long long)status[4] + (long long)status[5] > limit) atomicOr(status, kErrOverflow);
+}
+
 __global__ void k_tile_starts(const int32_t* __restrict__ off, int ntiles, int TT, int32_t* tile_start)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -186,27 +240,69 @@ void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* laun
     if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
     if (g < 1) g = 1;
     cudaMemsetAsync(c.keys_count, 0, sizeof(int32_t) * (size_t)(c.nkeys + 1), st);
+    cudaMemsetAsync(c.status + 4 + s, 0, sizeof(unsigned), st);
     SpeciesBuf src = from_b ? S.b : S.a;
     SpeciesBuf dst = from_b ? S.a : S.b;
     if (S.n > 0) k_count<<<(int)g, 256, 0, st>>>(src.cell, S.n, kg, c.keys_count);
     const int nb = (c.nkeys + kScanItems - 1) / kScanItems;
+    // the most particles of this species in one block of 4 cells per axis (counts are consumed below)
+    k_block_max<<<(int)(ncell_blocks(c) < (int64_t)c.nsm * 16 ? ncell_blocks(c) : (int64_t)c.nsm * 16), 256, 0, st>>>(
+        c.keys_count, kg, c.nz, c.status + 4 + s);
     k_scan_block<<<nb, kScanBlock, 0, st>>>(c.keys_count, c.keys_off, c.scan_tmp, c.nkeys);
     k_scan_sums<<<1, kScanBlock, 0, st>>>(c.scan_tmp, nb);
     // the cursor reuses the count array (counts are consumed by the scan)
     k_scan_add<<<(c.nkeys + 255) / 256, 256, 0, st>>>(c.keys_off, c.scan_tmp, c.nkeys, c.keys_count, (int32_t)S.n);
     k_tile_starts<<<(c.ntiles + 1 + 255) / 256, 256, 0, st>>>(c.keys_off, c.ntiles, TT, S.tile_start);
     if (S.n > 0) k_scatter<<<(int)g, 256, 0, st>>>(src, dst, S.n, kg, c.keys_count, S.tile_start);
+    k_count_check<<<1, 32, 0, st>>>(c.status, c.count_limit);
     if (!from_b) {
         SpeciesBuf t = S.a;
         S.a = S.b;
         S.b = t;
     }
-    if (launches) *launches += 5 + (S.n > 0 ? 2 : 0);
+    if (launches) *launches += 7 + (S.n > 0 ? 2 : 0);
 }
 
 void launch_sort_species(Ctx& c, int s, cudaStream_t st, int64_t* launches)
 {
     sort_species_impl(c, s, st, 0, launches);
+}
+
+// Largest contribution of one particle to one node sum (a particle's stencil starts at the lower of
+// its old and new cells and spans 3 nodes per axis, so a node collects from a block of 4 cells per
+// axis):
+//   2D J6y: |V| W6 <= 2^b * 6 * 2^32 (|beta_y| < 1; W6 = 2 S0xS0z + S1xS0z + S0xS1z + 2 S1xS1z);
+//   2D J2x, J2z: <= 2 * 2^16 * 2^17 = 2^34 (prefix sums of dS * (S0 + S1));
+//   2D density: weight products <= 2^32, old and new positions both counted while the kernel updates
+//   the sum incrementally: 2^33;
+//   3D currents: <= 2 * 2^14 * 6 * 2^28 = 3 * 2^44; 3D density 2 * 2^42.
+// A node sum stays below 2^63 while the particles of one block (both species) number fewer than
+// 2^63 / (largest contribution): the limit returned (particles per block of 4^dims cells).
+int64_t count_limit(int dims, int full, int jy_bits)
+{
+    const double two63 = 9223372036854775808.0;
+    double lim;
+    if (dims == 3) {
+        lim = two63 / (2.0 * 4398046511104.0);                                     // density
+        if (full) lim = fmin(lim, two63 / (3.0 * 17592186044416.0));              // currents
+    } else {
+        lim = two63 / (2.0 * 4294967296.0);                                        // density
+        if (full) {
+            lim = fmin(lim, two63 / 17179869184.0);                                // J2x, J2z
+            lim = fmin(lim, two63 / (6.0 * 4294967296.0 * ldexp(1.0, jy_bits)));  // J6y
+        }
+    }
+    return (int64_t)floor(lim - 1e-9);
+}
+
+// The J_y code resolution: 2^18 unless a uniform slab of n particles per cell (16 n per block, with
+// a quarter headroom for compression) could overflow J6y at that resolution; then the largest b
+// whose limit holds them.
+int choose_jy_bits(int64_t n_per_cell)
+{
+    for (int b = 18; b >= 1; b--)
+        if ((double)count_limit(2, 1, b) >= 1.25 * 16.0 * (double)n_per_cell) return b;
+    return 0;
 }
 
 }  // namespace gbpic

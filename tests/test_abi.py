@@ -88,3 +88,26 @@ def test_config_struct_layout_matches_header(lib):
     assert gb.pic_config.max_particles.offset == 40
     assert ctypes.sizeof(gb.pic_energy_t) == 7 * 8
     assert gb.pic_energy_t.injected.offset == 48
+
+
+def test_fixed_point_range_is_checked_at_sizing(lib):
+    """The int64 node sums stay exact while a cell holds at most 2^63 / (F * c) particles (F the
+    cells whose particles reach one node, c one particle's largest contribution): in 3D with
+    currents 2730 per cell (F = 64, c = 3 * 2^44), 16383 without (c = 2 * 2^42: the density while
+    it is updated). A slab configured beyond that is refused with
+    PIC_EOVERFLOW before any CUDA call; in 2D the J_y code resolution is lowered instead (the
+    paper's 900 electrons per cell are accepted)."""
+    def size(w):
+        cfg = gb.make_config(w)
+        n = ctypes.c_size_t(0)
+        return lib.pic_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
+    w3 = dict(workload("3d", nx=16, ny=16, nz=16, slab_k=4))
+    assert size(dict(w3, ppc_ion=1365, ppc_electron=1365)) == 0
+    assert size(dict(w3, ppc_ion=1366, ppc_electron=1366)) == gb.PIC_EOVERFLOW
+    assert size(dict(w3, ppc_ion=200000, ppc_electron=200000)) == gb.PIC_EOVERFLOW
+    assert size(dict(w3, mode=1, ion_charge=0.0, ppc_ion=16383, ppc_electron=0)) == 0       # no currents: below 2^20 per block
+    assert size(dict(w3, mode=1, ion_charge=0.0, ppc_ion=16384, ppc_electron=0)) == gb.PIC_EOVERFLOW
+    assert size(dict(workload("tiny"), ppc_ion=25, ppc_electron=900)) == gb.PIC_EINVAL      # unequal in full mode
+    assert size(dict(workload("tiny"), ppc_ion=900, ppc_electron=900)) == 0
+    assert size(dict(workload("tiny", nx=4, nz=4, slab_k=1), ppc_ion=6_000_000, ppc_electron=6_000_000)) == \
+        gb.PIC_EOVERFLOW

@@ -122,3 +122,75 @@ def test_autotuner_picks_and_caches(gb, tmp_path, monkeypatch):
     assert len(r["trials"]) == 4 and r["ms_per_step"] == min(t["ms_per_step"] for t in r["trials"])
     again = autotune.tune_batch(ws, tiles=(8, 16), sorts=(2, 4), warmup=1)
     assert again == r                      # served from the cache
+
+
+def _match(x1, z1, ox, oz, nx, nz):
+    """Index of the oracle particle each GPU particle is (the cell sort at the start of the step
+    reorders the GPU's particles; particles of one species are distinct points, far apart compared
+    with the FP32 rounding of a step). Checked to be a bijection."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(np.stack([np.mod(ox, nx), oz], 1), boxsize=[nx, 4 * nz])
+    d, idx = tree.query(np.stack([np.mod(x1, nx), z1], 1))
+    assert len(np.unique(idx)) == len(idx) and d.max() < 1e-3
+    return idx
+
+
+@pytest.mark.parametrize("slab", [1, 2])
+def test_batch_slab_step_matches_oracle(gb, slab):
+    """A slab of a batch against the FP64 oracle directly (not against the single-run GPU path):
+    the three-slab sweep runs 3 steps with a cell sort every 3 steps, so the compared step starts
+    with a sort that rewrites the batch's argument table. The oracle takes the slab's state before
+    that step (particles, fields, step count); after one step of the batch and one of the oracle
+    the particles agree to 1e-5 (matched by position: the sort reorders them), the current and the
+    node density equal the oracle's deposition of the GPU's own move bit for bit, and the fields
+    equal the oracle's Maxwell update from the same start and current to 1e-5."""
+    pytest.importorskip("scipy")
+    import oracle
+    from tests.test_gpu_parity import to_global
+    oracle.build()
+    ws = small_sweep()
+    batch = gb.Batch(ws, sort_every=3)
+    batch.step(3)
+    sl, w = batch.slabs[slab], ws[slab]
+    nx, nz = w["nx"], w["nz"]
+    orc = oracle.Oracle(w, with_particles=False)
+    before = []
+    for sp in (0, 1):
+        before.append(to_global(sl.get_particles(sp), nx))
+        orc.set_particles(sp, before[sp][0], before[sp][1], *before[sp][2])
+    fields = [sl.get_field(f).cpu().numpy().astype(np.float64) for f in range(6)]
+    for f, a in enumerate(fields):
+        orc.set_field(f, a)
+    n0 = sl.info()["step"]
+    orc.set_step(n0)
+    assert np.array_equal(sl.get_density().cpu().numpy(), orc.get_rho())
+    batch.step(1)
+    orc.step(1)
+    J = np.zeros((3, nz + 1, nx), np.int64)
+    for sp, sign in ((0, 1), (1, -1)):
+        x1, z1, u1 = to_global(sl.get_particles(sp), nx)
+        o = orc.get_particles(sp)
+        idx = _match(x1, z1, o["x"], o["z"], nx, nz)
+        x0, z0 = before[sp][0][idx], before[sp][1][idx]
+        # displacement to 1e-5 relative plus the FP32 rounding of the offset (2^-22 cells)
+        dx = np.mod(o["x"][idx] - x0 + nx / 2, nx) - nx / 2
+        assert (np.abs(np.mod(x1 - o["x"][idx] + nx / 2, nx) - nx / 2) <= 1e-5 * np.abs(dx) + 2.0 ** -22).all()
+        assert (np.abs(z1 - o["z"][idx]) <= 1e-5 * np.abs(o["z"][idx] - z0) + 2.0 ** -22).all()
+        for c, comp in enumerate(("ux", "uy", "uz")):
+            ref = o[comp][idx]
+            np.testing.assert_allclose(u1[c], ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+        oracle.deposit_current(nx, nz, sign, x0, z0, x1, z1, *[v.astype(np.float32) for v in u1], out=J)
+    assert np.array_equal(sl.get_current().cpu().numpy(), J)
+    x1, z1, _ = to_global(sl.get_particles(0), nx)
+    assert np.array_equal(sl.get_density().cpu().numpy(), oracle.deposit_density(nx, nz, x1, z1))
+    fo = oracle.Oracle(w, with_particles=False)
+    for f, a in enumerate(fields):
+        fo.set_field(f, a)
+    fo.set_step(n0)
+    fo.set_current(J)
+    fo.maxwell()
+    for f in range(6):
+        a = sl.get_field(f).cpu().numpy().astype(np.float64)
+        b = fo.get_field(f)
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+    batch.close()

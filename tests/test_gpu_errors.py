@@ -82,3 +82,31 @@ def test_invalid_particles_are_refused_before_any_kernel(gb):
     sim.set_particles(0, p["cell"], p["fx"], p["fz"], p["ux"], p["uy"], p["uz"])
     sim.step(2)
     sim.close()
+
+
+def test_particle_pile_up_beyond_the_fixed_point_range_is_a_sticky_error(gb):
+    """The int64 node sums are proven exact while a block of 4 x 4 cells (the cells whose particles
+    can reach one node) holds at most 1365 particles in the 2D full mode at the 2^18 J_y code. A
+    host-made state piles 1200 electrons into one cell of a slab of 8 + 8 per cell: the sort that
+    follows pic_set_particles finds the crowded block, and the next step reports the sticky
+    PIC_EOVERFLOW; the seeded slab (256 per block) runs on."""
+    extra = 1200
+    w = workload("tiny", nx=32, nz=32, slab_k=16, max_particles=32 * 16 * 8 + extra)
+    sim = gb.Simulation(w, sort_every=0)
+    sim.step(1)                                        # the seeded slab (8 + 8 per cell) is fine
+    p = sim.get_particles(1)
+    n0 = p["cell"].numel()
+    cell = torch.cat([p["cell"], torch.full((extra,), 5 * 32 + 7, dtype=torch.int32, device=p["cell"].device)])
+    f = torch.linspace(0.05, 0.95, extra, device=p["cell"].device)
+    fx, fz = torch.cat([p["fx"], f]), torch.cat([p["fz"], f.flip(0)])
+    z = torch.zeros(extra, device=p["cell"].device)
+    ux, uy, uz = (torch.cat([p[k], z]) for k in ("ux", "uy", "uz"))
+    sim.set_particles(1, cell, fx, fz, ux, uy, uz)
+    assert sim.info()["num_particles"][1] == n0 + extra
+    with pytest.raises(gb.PicError) as e:
+        sim.step(1)
+    assert e.value.code == gb.PIC_EOVERFLOW
+    with pytest.raises(gb.PicError) as e:              # sticky
+        sim.step(1)
+    assert e.value.code == gb.PIC_EOVERFLOW
+    sim.close()

@@ -19,6 +19,10 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+C = 299792458.0
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _built():
@@ -156,13 +160,17 @@ def _compare_particles(g, o_after, g_before, nx, rtol=1e-5):
         np.testing.assert_allclose(u[c], ref, rtol=rtol, atol=1e-6 * scale)
 
 
-@pytest.mark.parametrize("seed", [31, 32])
-def test_one_step_full_mode(seed):
+@pytest.mark.parametrize("seed,ppc", [(31, 8), (32, 8), (33, 40)])
+def test_one_step_full_mode(seed, ppc):
     """One full cycle from identical state (random fields, perturbed slab): particles and
     fields to 1e-5; the current and the new node density bit-exact against the oracle's
-    deposition of the GPU's own new positions."""
+    deposition of the GPU's own new positions. A slab configured with 40 + 40 particles per cell
+    takes the J_y code at 2^17 (its int64 node sums would not be proven exact at 2^18)."""
     nx, nz, sk = 56, 44, 22
-    w = workload("tiny", nx=nx, nz=nz, slab_k=sk, max_particles=nx * sk * 8, I0=1e19)
+    w = workload("tiny", nx=nx, nz=nz, slab_k=sk, max_particles=nx * sk * max(ppc, 8), I0=1e19, ppc_ion=ppc,
+                 ppc_electron=ppc)
+    bits = oracle.jy_bits(2 * ppc)
+    assert bits == (18 if ppc == 8 else 17)
     sim = gb().Simulation(w, sort_every=0)
     orc = oracle.Oracle(w, with_particles=False)
     ions, els, fields = _random_state(nx, nz, sk, seed, w)
@@ -181,7 +189,7 @@ def test_one_step_full_mode(seed):
     for sp, sign in ((0, 1), (1, -1)):
         x0, z0, _ = to_global(g0[sp], nx)
         x1, z1, u1 = to_global(g1[sp], nx)
-        oracle.deposit_current(nx, nz, sign, x0, z0, x1, z1, *[v.astype(np.float32) for v in u1], out=J)
+        oracle.deposit_current(nx, nz, sign, x0, z0, x1, z1, *[v.astype(np.float32) for v in u1], out=J, bits=bits)
     assert np.array_equal(sim.get_current().cpu().numpy(), J)
     x1, z1, _ = to_global(g1[0], nx)
     assert np.array_equal(sim.get_density().cpu().numpy(), oracle.deposit_density(nx, nz, x1, z1))
@@ -195,6 +203,55 @@ def test_one_step_full_mode(seed):
         a = sim.get_field(f).cpu().numpy().astype(np.float64)
         b = fo.get_field(f)
         np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+
+
+def test_electric_gather_reproduces_linear_fields():
+    """The E gather of the particle kernel against a closed form, not against the oracle: Ex, Ey,
+    Ez are each set to their own linear function a + b x + c z at their own Yee positions, B = 0,
+    and electrons at rest take one step of a tiny dt (1e-21 s: they move ~1e-12 cells). With
+    B = 0 the two half kicks give u = 2 (q dt / 2 m c) E at the particle, so u / (q dt / m c) must
+    be the linear function at the particle's position (a wrong half-cell offset is off by half a
+    slope: more than 1e-3 here). Positions span several tiles, the tiles' edges and the rows next
+    to both walls (where the half-row Ez takes its edge row)."""
+    nx, nz = 40, 24
+    w = workload("tiny", nx=nx, nz=nz, slab_k=nz, ppc_ion=1, ppc_electron=1, tile=8, dt_override=1e-21,
+                 laser_profile=0, max_particles=5000)
+    sim = gb().Simulation(w, sort_every=0)
+    rng = np.random.default_rng(11)
+    n = 4000
+    x = np.concatenate([rng.uniform(1.0, nx - 2.0, n), rng.uniform(1.0, nx - 2.0, 200)])
+    z = np.concatenate([rng.uniform(0.0, nz, n), rng.uniform(0.0, 0.5, 100), rng.uniform(nz - 0.5, nz, 100)])
+    x = np.floor(x * 2 ** 20) / 2 ** 20
+    z = np.minimum(np.floor(z * 2 ** 20) / 2 ** 20, nz - 2 ** -20)
+    cell, fx, fz = from_global(x, z, nx)
+    zero = np.zeros(len(x), np.float32)
+    sim.set_particles(1, cell, fx, fz, zero, zero, zero)
+    sim.set_particles(0, cell[:0], fx[:0], fz[:0], zero[:0], zero[:0], zero[:0])
+    k, i = np.mgrid[0:nz + 1, 0:nx]
+    coef = {0: (0.0, 3e5, 1e5), 1: (0.0, -2e5, 4e5), 2: (0.0, 1e5, -3e5)}     # V/m per cell
+    stag = {0: (0.5, 0.0, False), 1: (0.0, 0.0, False), 2: (0.0, 0.5, True)}
+    for f in range(6):
+        grid = np.zeros((nz + 1, nx))
+        if f in coef:
+            a, b, c = coef[f]
+            sx, sz, half = stag[f]
+            grid = a + b * (i + sx) + c * (k + sz)
+            if half:
+                grid[nz] = 0.0
+        sim.set_field(f, grid.astype(np.float32))
+    g0 = sim.get_particles(1)
+    x0, z0, _ = to_global(g0, nx)
+    sim.step(1)
+    g1 = sim.get_particles(1)
+    scale = QE * w["dt_override"] / (ME * C)          # u per V/m after the two half kicks
+    for f in range(3):
+        a, b, c = coef[f]
+        sx, sz, half = stag[f]
+        zc = np.clip(z0, 0.5, nz - 0.5) if half else z0
+        expect = -(a + b * x0 + c * zc)                 # electrons: q = -e
+        got = g1[("ux", "uy", "uz")[f]].cpu().numpy().astype(np.float64) / scale
+        np.testing.assert_allclose(got, expect, rtol=1e-5, atol=1e-5 * np.abs(expect).max())
+    sim.close()
 
 
 @pytest.mark.parametrize("pot", [{}, dict(pot_mode=1, c_att=0.65, s_rep=2.5), dict(pot_mode=2, morse_a=4.0),
@@ -314,6 +371,72 @@ def test_tiny_workload_200_steps_aggregates():
     assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-3
 
 
+STORED = ("kinetic_ion", "kinetic_electron", "field_E", "field_B", "pair")
+
+
+@pytest.mark.slow
+def test_full_cycle_1000_steps_resolved_plasma():
+    """The full cycle (Cu+ ions with the pair force, electrons, fields) over 1000 steps on the tiny
+    slab's geometry (64 x 64 cells, 8 + 8 ppc) at a density whose Debye length the 10 nm cells
+    resolve (n = 1e26 m^-3, 100 eV electrons: lambda_D = 0.74 cells, w_pe dt = 0.013). Here the
+    cycle is not chaotic at the scale of the bars: rounding the oracle's initial momenta to FP32
+    moves its 1000-step energies by 5e-8. With the laser on (1e13 W/cm^2, peak at the surface at
+    step 500) the stored energy, the injected energy and the depth profile of the node density
+    agree with the oracle within 1e-3; with the laser off the stored energy drifts (by +1.1 % in
+    the oracle: mild numerical heating at lambda_D ~ dx) and the GPU's drift equals the oracle's
+    within 1e-4."""
+    base = dict(n_atoms=1e26, T_electron_eV=100.0, t_peak=500 * 2.24072e-17)
+    for I0 in (1e17, 0.0):
+        w = workload("tiny", I0=I0, **base)
+        sim = gb().Simulation(w)
+        orc = oracle.Oracle(w)
+        e0g, e0o = sim.energy(), orc.energy()
+        t0g, t0o = sum(e0g[k] for k in STORED), sum(e0o[k] for k in STORED)
+        assert t0g == pytest.approx(t0o, rel=1e-6)
+        sim.step(1000)
+        orc.step(1000)
+        eg, eo = sim.energy(), orc.energy()
+        tg, to = sum(eg[k] for k in STORED), sum(eo[k] for k in STORED)
+        if I0 > 0:
+            assert eo["injected"] > 0.5 * to
+            assert tg == pytest.approx(to, rel=1e-3)
+            assert eg["injected"] == pytest.approx(eo["injected"], rel=1e-3)
+            pg = sim.get_density().cpu().numpy().sum(axis=1).astype(np.float64)
+            po = orc.get_rho().sum(axis=1).astype(np.float64)
+            assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-3
+        else:
+            dg, do = (tg - t0g) / abs(t0g), (to - t0o) / abs(t0o)
+            assert abs(do) > 1e-3                       # the oracle's drift is measurable
+            assert abs(dg - do) <= 1e-4, (dg, do)
+        sim.close()
+
+
+@pytest.mark.slow
+def test_tiny_workload_1000_steps_full_cycle():
+    """The tiny workload itself (solid density, 1 eV electrons, laser on) over 1000 steps. Its
+    10 nm cells are 400 Debye lengths: the explicit cycle heats the electrons by the finite-grid
+    instability (their kinetic energy grows 1000-fold in the oracle) and amplifies rounding, so the
+    1000-step energies are not reproducible below a few per cent by any implementation: the oracle
+    against itself with its initial momenta rounded to FP32, with one momentum component scaled by
+    1 + 1e-7, or with its state rounded to FP32 after one step differs by +2.3 %, -0.9 % and +5.1 %
+    in the stored energy. The bar on the energies is therefore that ensemble's spread (3 sigma,
+    10 %); the depth profile of the node density (the ions barely move in 1000 steps) keeps the
+    1e-3 bar (the ensemble: 2.5e-5)."""
+    w = workload("tiny", t_peak=500 * 2.24072e-17)
+    sim = gb().Simulation(w)
+    orc = oracle.Oracle(w)
+    sim.step(1000)
+    orc.step(1000)
+    eg, eo = sim.energy(), orc.energy()
+    tg, to = sum(eg[k] for k in STORED), sum(eo[k] for k in STORED)
+    assert tg == pytest.approx(to, rel=0.1)
+    assert eg["kinetic_electron"] == pytest.approx(eo["kinetic_electron"], rel=0.1)
+    pg = sim.get_density().cpu().numpy().sum(axis=1).astype(np.float64)
+    po = orc.get_rho().sum(axis=1).astype(np.float64)
+    assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-3
+    sim.close()
+
+
 @pytest.mark.slow
 def test_transport_1000_steps_energy_drift_and_profile():
     """Transport mode (neutral atoms, pair force only), 1000 steps of 12 fs: the GPU's energy
@@ -380,19 +503,27 @@ def test_transport_acoustic_wave_period(pot, curv):
     sim.close()
 
 
-def test_vacuum_without_particles_matches_oracle():
-    """Degenerate input: no slab at all (slab_k = 0, no particles). The context initialises, the
-    laser propagates, and fields and injected energy follow the oracle."""
-    w = workload("tiny", nx=32, nz=80, slab_k=0, laser_profile=1, I0=1e17, tau_fwhm=5e-15, t_peak=8e-15)
+@pytest.mark.parametrize("profile,slab_k", [(1, 0), (2, 0), (2, 10)])
+def test_vacuum_without_particles_matches_oracle(profile, slab_k):
+    """Degenerate input: no particles (slab_k = 0, or a slab row without macroparticles, ppc 0).
+    The context initialises, the laser propagates, and fields and injected energy follow the oracle
+    after one step and after 150 steps: the plane wave (profile 1) and the focused Gaussian beam
+    (profile 2: width, wavefront curvature and half Gouy phase at the antenna, focus at row
+    slab_k)."""
+    over = dict(ppc_ion=0, ppc_electron=0) if slab_k else {}
+    w = workload("tiny", nx=128, nz=80, slab_k=slab_k, laser_profile=profile, w0=0.4e-6, I0=1e17,
+                 tau_fwhm=5e-15, t_peak=8e-15, **over)
     sim = gb().Simulation(w)
     assert sum(sim.info()["num_particles"]) == 0
-    orc = oracle.Oracle(w)
-    sim.step(150)
-    orc.step(150)
-    for f in range(6):
-        g, o = sim.get_field(f).cpu().numpy(), orc.get_field(f)
-        scale = np.abs(o).max()
-        assert scale == 0 or np.abs(g - o).max() <= 1e-5 * scale, f
+    orc = oracle.Oracle(w, with_particles=False)
+    for nsteps in (1, 149):
+        sim.step(nsteps)
+        orc.step(nsteps)
+        for f in range(6):
+            g, o = sim.get_field(f).cpu().numpy(), orc.get_field(f)
+            scale = np.abs(o).max()
+            assert scale == 0 or np.abs(g - o).max() <= 1e-5 * scale, (nsteps, f)
+
     eg, eo = sim.energy(), orc.energy()
     assert eo["injected"] > 0
     assert eg["injected"] == pytest.approx(eo["injected"], rel=1e-5)

@@ -176,3 +176,35 @@ def test_init3_statistics():
     cell = (np.floor(ions["z"]) * 5 + np.floor(ions["y"])) * 6 + np.floor(ions["x"])
     assert np.array_equal(np.bincount(cell.astype(int), minlength=120), np.full(120, 8))
     assert o.get_rho().sum() == len(ions["x"]) * 2 ** 42
+
+
+# Yee positions of the 3D field components (offsets along x, y, z) and whether they live on the nz
+# half planes (True) or on the nz + 1 node planes
+STAGGER_3D = [(0.5, 0.0, 0.0, False), (0.0, 0.5, 0.0, False), (0.0, 0.0, 0.5, True),   # Ex Ey Ez
+              (0.0, 0.5, 0.5, True), (0.5, 0.0, 0.5, True), (0.5, 0.5, 0.0, False)]    # Bx By Bz
+
+
+def test_field_gather3_reproduces_linear_fields():
+    """3D fields seen by the push: each Yee component set to its own linear function
+    a + b x + c y + d z at its staggered positions is returned exactly at interior points (a wrong
+    half-cell offset along any axis is off by half a slope); near a wall a half-plane component
+    returns its edge plane's value (z clamped to [1/2, nz - 1/2])."""
+    nx, ny, nz = 12, 10, 9
+    o = oracle.Oracle3D(cfg3(nx=nx, ny=ny, nz=nz, slab_k=nz, dims=3), with_particles=False)
+    k, j, i = np.mgrid[0:nz + 1, 0:ny, 0:nx]
+    rng = np.random.default_rng(6)
+    coef = rng.uniform(1.0, 3.0, (6, 4)) * np.array([1.0, 0.1, 0.15, 0.2])
+    for f, (sx, sy, sz, half) in enumerate(STAGGER_3D):
+        a, b, c, d = coef[f]
+        grid = a + b * (i + sx) + c * (j + sy) + d * (k + sz)
+        if half:
+            grid[nz] = 0.0
+        o.set_field(f, grid)
+    pts = [(rng.uniform(1.0, nx - 2.0), rng.uniform(1.0, ny - 2.0), rng.uniform(0.0, nz)) for _ in range(60)]
+    pts += [(rng.uniform(1.0, nx - 2.0), rng.uniform(1.0, ny - 2.0), z) for z in (0.0, 0.3, 0.5, nz - 0.5, nz - 0.2)]
+    for x, y, z in pts:
+        got = o.gather_fields(x, y, z)
+        for f, (sx, sy, sz, half) in enumerate(STAGGER_3D):
+            a, b, c, d = coef[f]
+            zc = min(max(z, 0.5), nz - 0.5) if half else z
+            assert got[f] == pytest.approx(a + b * x + c * y + d * zc, rel=1e-13, abs=1e-13), (f, x, y, z)

@@ -202,6 +202,35 @@ def _grid_oracle(nx=16, nz=16):
     return oracle.Oracle(w, with_particles=False)
 
 
+@pytest.mark.parametrize("per_cell", [2, 16, 64, 68, 80, 200, 925, 5000])
+def test_jy_code_resolution_keeps_the_node_sums_exact(per_cell):
+    """The J_y code resolution b of a slab with per_cell macroparticles per cell: one particle adds
+    at most |V| W6 <= 2^b * 6 * 2^32 to a J_y node sum (the six-fold weight of one node is at most
+    6 * 2^32: brute-force maximum over positions below) and the particles that reach a node sit in
+    a block of 4 x 4 cells, so 16 * (1.25 per_cell) * 6 * 2^(32 + b) must stay below 2^63; b is the
+    largest such b up to 18. The code at that b is beta_y 2^b within half a code step (a coarser
+    code only for crowded slabs: b = 18 for every benchmark slab, 14 for the paper's 900 + 25 per
+    cell)."""
+    b = oracle.jy_bits(per_cell)
+    assert 1 <= b <= 18
+    bound = lambda bits: 16 * 1.25 * per_cell * 6 * 2.0 ** (32 + bits)
+    assert bound(b) < 2.0 ** 63
+    assert b == 18 or bound(b + 1) >= 2.0 ** 63
+    if per_cell <= 68:
+        assert b == 18
+    # the largest six-fold weight of one node over in-cell moves (fixed point 2^16)
+    Q = 2 ** 16
+    g = np.arange(0, Q + 1, Q // 8)
+    S0x, S1x, S0z, S1z = np.meshgrid(g, g, g, g, indexing="ij")
+    w6 = 2 * S0x * S0z + S1x * S0z + S0x * S1z + 2 * S1x * S1z
+    assert w6.max() == 6 * Q * Q
+    rng = np.random.default_rng(per_cell)
+    for _ in range(200):
+        u = rng.normal(0, 0.3, 3).astype(np.float32)
+        exact = float(u[1]) / math.sqrt(1.0 + float(u @ u.astype(np.float64))) * 2.0 ** b
+        assert abs(oracle.jy_code(u[0], u[1], u[2], bits=b) - exact) <= 0.5 + 1e-6 * abs(exact)
+
+
 def test_uniform_lattice_gives_zero_force():
     """A uniform lattice has zero density gradient, hence Eq. (2) gives equal distances on
     both sides and the pair force vanishes exactly, at every particle position."""
@@ -243,6 +272,40 @@ def test_gather_reproduces_linear_density():
         assert n == pytest.approx((a + bx * x + bz * z) * s, rel=1e-13)
         assert dnx == pytest.approx(bx * s, rel=1e-12)
         assert dnz == pytest.approx(bz * s, rel=1e-12)
+
+
+# Yee positions of the field components (offsets in cells along x and z) and whether they live on
+# the nz half rows (True) or on the nz + 1 node rows
+STAGGER_2D = [(0.5, 0.0, False), (0.0, 0.0, False), (0.0, 0.5, True),      # Ex Ey Ez
+              (0.0, 0.5, True), (0.5, 0.5, True), (0.5, 0.0, False)]       # Bx By Bz
+
+
+def test_field_gather_reproduces_linear_fields():
+    """The fields the push sees (paper, the PIC-cycle paragraph: fields interpolated to the
+    particle). Each Yee component is set to its own linear function a + b x + c z sampled at its
+    own staggered positions (x = i + sx, z = k + sz); the gather returns that linear function
+    exactly at interior points, so a component read with a wrong half-cell offset along x or z is
+    off by b/2 or c/2. Within half a cell of a wall a half-row component (rows at z = k + 1/2,
+    k = 0..nz-1) returns its edge row's value, a + b x + c z clamped to [1/2, nz - 1/2]."""
+    nx, nz = 20, 14
+    o = _grid_oracle(nx, nz)
+    k, i = np.mgrid[0:nz + 1, 0:nx]
+    rng = np.random.default_rng(5)
+    coef = rng.uniform(1.0, 3.0, (6, 3)) * np.array([1.0, 0.1, 0.2])
+    for f, (sx, sz, half) in enumerate(STAGGER_2D):
+        a, b, c = coef[f]
+        grid = a + b * (i + sx) + c * (k + sz)
+        if half:
+            grid[nz] = 0.0                                  # row nz of a half-row component is unused
+        o.set_field(f, grid)
+    pts = [(rng.uniform(1.0, nx - 2.0), rng.uniform(0.0, nz)) for _ in range(60)]
+    pts += [(rng.uniform(1.0, nx - 2.0), z) for z in (0.0, 0.2, 0.49, 0.5, nz - 0.5, nz - 0.3, nz - 1e-9)]
+    for x, z in pts:
+        got = o.gather_fields(x, z)
+        for f, (sx, sz, half) in enumerate(STAGGER_2D):
+            a, b, c = coef[f]
+            zc = min(max(z, 0.5), nz - 0.5) if half else z
+            assert got[f] == pytest.approx(a + b * x + c * zc, rel=1e-13, abs=1e-13), (f, x, z)
 
 
 # ---- Morse potential (pot_mode 2): another pair potential the density mapping takes ----------
@@ -448,6 +511,122 @@ def test_antenna_launches_the_requested_amplitude():
     assert peak == pytest.approx(E0, rel=0.03)
     # nothing leaks upwards past the top wall region
     assert np.abs(o.get_field(0)[nz - 1]).max() < 0.05 * E0
+
+
+def _beam_run(make, nrow, sk, axis_field, tau, lam, nsteps_of):
+    """Steps a vacuum oracle once per step; returns the times, the on-axis E_x at the focal row and
+    the time integral of E_x^2 on the focal row and on the row below the antenna."""
+    o = make()
+    ts, ef, acc = [], [], None
+    for n in range(nsteps_of(o.dt)):
+        o.step(1)
+        Ex = o.get_field(0)
+        sq = Ex[[sk, nrow - 3]] ** 2
+        acc = sq if acc is None else acc + sq
+        ts.append((n + 1) * o.dt)
+        ef.append(axis_field(Ex))
+    return np.array(ts), np.array(ef), acc
+
+
+def _carrier(ts, ef, t_peak, tau, lam):
+    """Amplitude and phase of E(t) = A env(t - t_peak) sin(w (t - t_peak) + phi), least squares."""
+    om = 2 * math.pi * C / lam
+    env = np.exp(-2 * math.log(2) * (ts - t_peak) ** 2 / tau ** 2)
+    basis = np.stack([env * np.sin(om * (ts - t_peak)), env * np.cos(om * (ts - t_peak))], 1)
+    (a, b), *_ = np.linalg.lstsq(basis, ef, rcond=None)
+    return math.hypot(a, b), math.atan2(b, a)
+
+
+def _width(x, prof):
+    """1/e^2 half-width of a Gaussian intensity profile from its second moment (w = 2 sigma)."""
+    return 2 * math.sqrt((x * x * prof).sum() / prof.sum())
+
+
+@pytest.mark.slow
+def test_gaussian_beam_focus_2d():
+    """The focused antenna (laser_profile 2) launches a paraxial Gaussian beam that comes to its
+    waist w0 at the slab surface (the laser-stage paragraph: the pulse is focused to a spot). In
+    vacuum, from the antenna to the focal row L = 300 cells below (L / zR = 0.53), the oracle must
+    give: the 1/e^2 half-width of the time-integrated E_x^2 equal to w0 at the focal row and to
+    w0 sqrt(1 + (L/zR)^2) below the antenna, growing monotonically in between; the peak field at
+    the focus equal to E0 (the requested intensity is reached at the focus: a line focus grows as
+    (w_a/w0)^(1/2)); the same power through every row; and the carrier phase at the focus equal
+    to that of a plane wave launched the same way (the half Gouy phase of a 2D beam, 0.24 rad here,
+    is undone on the way to the focus). Closed forms are the paraxial ones, whose corrections are
+    of order (lambda / (pi w0))^2 = 4.5 % at w0 = 1.2 um; the measured deviations are about 2 %."""
+    nx, nz, sk, w0, tau, lam, dx = 768, 310, 8, 1.2e-6, 10e-15, 800e-9, 10e-9
+    L = (nz - 2 - sk) * dx
+    t_peak = L / C + 2 * tau
+    zR = math.pi * w0 ** 2 / lam
+    E0 = math.sqrt(2 * 1e17 / (EPS0 * C))
+
+    def make(profile, n):
+        return lambda: oracle.Oracle(workload("tiny", nx=n, nz=nz, slab_k=sk, ppc_ion=0, ppc_electron=0,
+                                              laser_profile=profile, w0=w0, I0=1e17, tau_fwhm=tau,
+                                              t_peak=t_peak), with_particles=False)
+
+    steps = lambda dt: int((t_peak + 2.5 * tau) / dt)
+    rows = [sk, sk + 75, sk + 150, nz - 3]
+    o = make(2, nx)()
+    ts, ef, prof = [], [], np.zeros((len(rows), nx))
+    for n in range(steps(o.dt)):
+        o.step(1)
+        Ex = o.get_field(0)
+        prof += Ex[rows] ** 2
+        ts.append((n + 1) * o.dt)
+        ef.append(0.5 * (Ex[sk, nx // 2 - 1] + Ex[sk, nx // 2]))
+    x = (np.arange(nx) + 0.5 - nx / 2) * dx
+    widths = [_width(x, p) for p in prof]
+    assert widths[0] == pytest.approx(w0, rel=0.035)
+    assert widths[-1] == pytest.approx(w0 * math.sqrt(1 + (L / zR) ** 2), rel=0.03)
+    assert all(a < b for a, b in zip(widths, widths[1:]))            # converging onto the focal row
+    power = prof.sum(1)
+    assert power.max() / power.min() < 1.01
+    amp, phase = _carrier(np.array(ts), np.array(ef), t_peak, tau, lam)
+    assert amp == pytest.approx(E0, rel=0.035)
+    # the plane wave (uniform in x: 4 columns suffice) through the same rows and steps
+    tp, ep, _ = _beam_run(make(1, 4), nz, sk, lambda E: E[sk, 2], tau, lam, steps)
+    _, phase_plane = _carrier(tp, ep, t_peak, tau, lam)
+    assert abs(phase - phase_plane) < 0.06
+
+
+@pytest.mark.slow
+def test_gaussian_beam_focus_3d():
+    """The 3D focused antenna: a round paraxial Gaussian beam whose waist w0 sits at the slab
+    surface, with amplitude (w0/w) and the full Gouy phase at the antenna. Scaled to a 200 nm
+    wavelength (20 cells per wavelength) so that the oracle can run it: w0 = 0.2 um, L = 50 cells
+    = 0.8 zR. Checked: the half-widths of the time-integrated E_x^2 along x and y at the focal row
+    (w0) and below the antenna (w0 sqrt(1 + (L/zR)^2)), the peak field at the focus (E0), the power
+    through both rows, and the carrier phase at the focus against a plane wave launched the same
+    way (the Gouy phase at the antenna, atan(L/zR) = 0.67 rad, must be undone; half of it would
+    leave 0.34 rad). Paraxial corrections at w0 = lambda: (lambda / (pi w0))^2 = 10 %; measured
+    deviations are within 4 %."""
+    n, nz, sk, w0, tau, lam, dx = 128, 60, 8, 0.2e-6, 2e-15, 200e-9, 10e-9
+    L = (nz - 2 - sk) * dx
+    t_peak = L / C + 2 * tau
+    zR = math.pi * w0 ** 2 / lam
+    E0 = math.sqrt(2 * 1e17 / (EPS0 * C))
+
+    def make(profile, m):
+        return lambda: oracle.Oracle3D(workload("3d", nx=m, ny=m, nz=nz, slab_k=sk, ppc_ion=0, ppc_electron=0,
+                                                laser_profile=profile, w0=w0, I0=1e17, tau_fwhm=tau,
+                                                t_peak=t_peak, **{"lambda": lam}), with_particles=False)
+
+    steps = lambda dt: int((t_peak + 2.5 * tau) / dt)
+    ts, ef, prof = _beam_run(make(2, n), nz, sk, lambda E: 0.5 * (E[sk, n // 2, n // 2 - 1] + E[sk, n // 2, n // 2]),
+                             tau, lam, steps)
+    x = (np.arange(n) + 0.5 - n / 2) * dx       # E_x at (i + 1/2, j)
+    y = (np.arange(n) - n / 2) * dx
+    w_ant = w0 * math.sqrt(1 + (L / zR) ** 2)
+    for p, expect in zip(prof, (w0, w_ant)):
+        assert _width(x, p.sum(0)) == pytest.approx(expect, rel=0.04)
+        assert _width(y, p.sum(1)) == pytest.approx(expect, rel=0.04)
+    assert prof[0].sum() == pytest.approx(prof[1].sum(), rel=0.01)
+    amp, phase = _carrier(ts, ef, t_peak, tau, lam)
+    assert amp == pytest.approx(E0, rel=0.03)
+    tp, ep, _ = _beam_run(make(1, 4), nz, sk, lambda E: E[sk, 2, 2], tau, lam, steps)
+    _, phase_plane = _carrier(tp, ep, t_peak, tau, lam)
+    assert abs(phase - phase_plane) < 0.12
 
 
 def test_gauss_law_is_preserved():
