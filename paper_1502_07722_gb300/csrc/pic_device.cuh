@@ -68,9 +68,11 @@ __device__ __forceinline__ float morse_dU_inv(float inv, float a)    // U'(r), u
 // Eq. (3)'s force difference for the Morse form: with both neighbours finite
 //   U'(r+) - U'(r-) = 2a (E+ - E-) (1 - E+ - E-),  E+ - E- = E- expm1(-a (r+ - r-)),
 //   r+ - r- = 2h / (c (1 - h^2)),
-// free of cancellation. Kept out of line (only the Morse kernel instances and the run-time
-// dispatch of the diagnostics call it).
-static __device__ __noinline__ float morse_axis(float c, float h, float a)
+// free of cancellation. Inlined into the kernel instances that compile the Morse form in (an
+// out-of-line call cost the transport kernel its registers' round trips through local memory:
+// 0.165 -> 0.196 ms per launch on the crater slab once the call site changed); the run-time
+// dispatch of the diagnostics calls the out-of-line copy below.
+__device__ __forceinline__ float morse_axis_inl(float c, float h, float a)
 {
     const float ip = c * (1.0f - h), im = c * (1.0f + h);
     if (ip > 0.0f && im > 0.0f) {
@@ -83,6 +85,8 @@ static __device__ __noinline__ float morse_axis(float c, float h, float a)
     if (im > 0.0f) f -= morse_dU_inv(im, a);
     return f;
 }
+
+static __device__ __noinline__ float morse_axis(float c, float h, float a) { return morse_axis_inl(c, h, a); }
 
 // Pair energy U(r) (units D) of one neighbour at r0 / r = inv under pot_mode.
 __device__ __forceinline__ float pair_U(int pot_mode, float c_att, float s_rep, float inv)
@@ -116,8 +120,8 @@ __device__ __forceinline__ float pair_axis(float n, float c, float inv43, float 
                                            int pot_mode, float c_att, float s_rep)
 {
     float h = -h_coef * dn * inv43;
-    if ((POT >= 0 && (POT & 3) == kPotMorse) || (POT == kPotRuntime && (pot_mode & 3) == 2))
-        return morse_axis(c, h, c_att);
+    if (POT >= 0 && (POT & 3) == kPotMorse) return morse_axis_inl(c, h, c_att);
+    if (POT == kPotRuntime && (pot_mode & 3) == 2) return morse_axis(c, h, c_att);
     const int pm = POT >= 0 ? (POT & 3) : pot_mode;
     float ip = c * (1.0f - h);      // r0 / dist to the neighbour on the + side
     float im = c * (1.0f + h);      // r0 / dist to the neighbour on the - side

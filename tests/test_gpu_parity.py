@@ -260,8 +260,9 @@ def test_one_step_transport_mode(pot):
     """One transport step (pair force only) against the oracle, with Eq. (3) as printed, with
     the altered potential (attractive and repulsive branches scaled) and with the Morse form. The
     altered force changes its factor at a neighbour distance of r0: a distance within FP32
-    rounding of r0 can fall on the other branch than in FP64, so there isolated momenta differ at
-    up to ~1e-4 (2e-4 bound)."""
+    rounding of r0 can fall on the other branch than in FP64. So with the altered potential all
+    momenta but those few are held to 1e-5 (at most 0.2 % of the atoms may exceed it; measured: a
+    handful of the 9600), and those few to 2e-4 (measured up to ~1e-4)."""
     nx, nz, sk = 40, 30, 15
     w = workload("transport", nx=nx, nz=nz, slab_k=sk, max_particles=nx * sk * 16, **pot)
     sim = gb().Simulation(w, sort_every=0)
@@ -270,8 +271,16 @@ def test_one_step_transport_mode(pot):
     g0 = set_both(sim, orc, 0, d)
     sim.step(1)
     orc.step(1)
-    _compare_particles(sim.get_particles(0), orc.get_particles(0), g0, nx,
-                       rtol=2e-4 if pot.get("pot_mode") == 1 else 1e-5)
+    altered = pot.get("pot_mode") == 1
+    g1, o1 = sim.get_particles(0), orc.get_particles(0)
+    _compare_particles(g1, o1, g0, nx, rtol=2e-4 if altered else 1e-5)
+    if altered:
+        _, _, u = to_global(g1, nx)
+        off_branch = np.zeros(len(u[0]), bool)
+        for c, comp in enumerate(("ux", "uy", "uz")):
+            ref = o1[comp]
+            off_branch |= np.abs(u[c] - ref) > 1e-5 * np.abs(ref) + 1e-6 * np.abs(ref).max()
+        assert off_branch.sum() <= max(2, len(off_branch) // 500), off_branch.sum()
     x1, z1, _ = to_global(sim.get_particles(0), nx)
     assert np.array_equal(sim.get_density().cpu().numpy(), oracle.deposit_density(nx, nz, x1, z1))
 
