@@ -48,6 +48,8 @@ class OracleConfig(ctypes.Structure):
         ("temp_profile", ctypes.c_int32), ("lattice", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
         ("morse_a", ctypes.c_double),
+        ("eam_ec", ctypes.c_double), ("eam_phi", ctypes.c_double), ("eam_alpha", ctypes.c_double),
+        ("eam_beta", ctypes.c_double), ("eam_gamma", ctypes.c_double),
     ]
 
 
@@ -66,6 +68,8 @@ class OracleConfig3(ctypes.Structure):
         ("temp_profile", ctypes.c_int32), ("lattice", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
         ("morse_a", ctypes.c_double),
+        ("eam_ec", ctypes.c_double), ("eam_phi", ctypes.c_double), ("eam_alpha", ctypes.c_double),
+        ("eam_beta", ctypes.c_double), ("eam_gamma", ctypes.c_double),
     ]
 
 
@@ -112,6 +116,7 @@ def lib():
             "oracle_boris": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
             "oracle_jy_code": (ctypes.c_int64, [ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int32]),
             "oracle_jy_bits": (ctypes.c_int32, [ctypes.c_int64]),
+            "oracle_eam_atom2": (None, [ctypes.c_double] * 10 + [_D]),
             "oracle_deposit_density": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D, _I64]),
             "oracle_deposit_current": (None, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                               _D, _D, _D, _D, _F, _F, _F, ctypes.c_int32, _I64, _I64, _I64]),
@@ -437,6 +442,16 @@ def boris(q, m, dt, E, B, F, u):
 def jy_code(ux, uy, uz, bits=18):
     """J_y code V = rint(beta_y 2^bits) of one particle, taken in FP32 as the kernel takes it."""
     return lib().oracle_jy_code(float(np.float32(ux)), float(np.float32(uy)), float(np.float32(uz)), int(bits))
+
+
+def eam_atom2(phys, n, dnx, dnz, r0_dx):
+    """Embedded-atom force along x and z (units D / r0) and energy (units D) of one atom at density
+    n (units n0) with gradient (dnx, dnz) per cell; r0_dx = r0 / dx."""
+    out = np.zeros(3)
+    lib().oracle_eam_atom2(phys["D_eV"], phys["eam_ec"], phys["eam_phi"], phys["eam_alpha"], phys["eam_beta"],
+                           phys["eam_gamma"], float(n), float(dnx), float(dnz), float(r0_dx),
+                           _p(out, ctypes.c_double))
+    return out
 
 
 def jy_bits(per_cell):

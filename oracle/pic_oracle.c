@@ -71,7 +71,8 @@ typedef struct {
     int32_t slab_k;          /* the copper slab fills cell rows k < slab_k                    */
     int32_t mode;            /* 0: ions + electrons + fields; 1: neutral atoms only           */
     int32_t ppc_ion, ppc_electron;
-    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (scaled branches); 2: Morse */
+    int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (scaled branches); 2: Morse;
+                                3: embedded-atom form (cubic lattice)                            */
     int32_t laser_profile;   /* 0: none; 1: plane wave; 2: focused Gaussian beam              */
     double dx;               /* cell size (m), square cells                                   */
     double cfl;              /* dt = cfl * dx / (c * sqrt(2)) when dt_override <= 0          */
@@ -89,6 +90,9 @@ typedef struct {
     int32_t lattice;         /* 0: cubic (the paper's); 1: hexagonal close-packed, c axis along z */
     double T_spot_K, spot_w, spot_depth;       /* K, m (1/e^2 radius), m (1/e depth)         */
     double morse_a;          /* Morse stiffness alpha r0 (pot_mode 2)                           */
+    double eam_ec, eam_phi;  /* embedded-atom form (pot_mode 3): cohesive energy E_c and pair scale
+                                phi_e (eV)                                                          */
+    double eam_alpha, eam_beta, eam_gamma;   /* its exponents (dimensionless, r in units of r0)  */
 } ocfg;
 
 typedef struct {
@@ -235,6 +239,100 @@ static void lattice_pair(int lattice, int pm, double ca, double sr, double ma, d
         for (int d = 0; d < 3; d++) F[d] += du * e[k][d];
         *u += 0.5 * w[k] * pot_U(pm, ca, sr, ma, rk);
     }
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* embedded-atom form (pot_mode 3): the paper notes that other potentials are readily adapted  */
+/* to its mapping of density to neighbour distance. The analytic nearest-neighbour EAM of      */
+/* Johnson (Phys. Rev. B 37, 3924, 1988), rebuilt for the paper's cubic lattice of six        */
+/* nearest neighbours, with r in units of r0 (the equilibrium spacing) and energies in units  */
+/* of D:                                                                                       */
+/*   electron density of one neighbour  f(r)   = exp(-beta (r - 1))                            */
+/*   pair term                          phi(r) = phi_e exp(-gamma (r - 1))                     */
+/*   embedding energy                   F(rho) = -E_c (1 - (alpha/beta) ln x) x^(alpha/beta)   */
+/*                                               - 3 phi_e x^(gamma/beta),  x = rho / 6        */
+/* so that a uniform lattice of spacing r has E = F(6 f(r)) + 3 phi(r) = -E_c (1 + a) e^(-a),  */
+/* a = alpha (r - 1) (the universal binding curve), -E_c at r = 1.                             */
+/* Reading of the one-atom environment: atom i's embedding density is the sum of f over its   */
+/* six Eq. (2) neighbours (+-y at rbar in 2D); neighbour j's own embedding density is          */
+/* 6 f(rbar_j) with rbar_j = n_j^(-1/3) and n_j the interpolated density at j's position, taken */
+/* along the axis from the atom's density and its gradient (n + s dn, s the neighbour's offset */
+/* in cells); the bond to j pulls with T = phi'(r) + (F'(rho_i) + F'(rho_j)) f'(r), and the   */
+/* force along an axis is T(r+) - T(r-), as U'(r+) - U'(r-) for a pair potential.             */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    double ec, phi, alpha, beta, gamma;      /* ec, phi in units of D */
+} eam_p;
+
+static double eam_f(const eam_p* p, double r) { return exp(-p->beta * (r - 1.0)); }
+static double eam_df(const eam_p* p, double r) { return -p->beta * exp(-p->beta * (r - 1.0)); }
+static double eam_phi(const eam_p* p, double r) { return p->phi * exp(-p->gamma * (r - 1.0)); }
+static double eam_dphi(const eam_p* p, double r) { return -p->gamma * p->phi * exp(-p->gamma * (r - 1.0)); }
+static double eam_F(const eam_p* p, double rho)
+{
+    if (!(rho > 0.0)) return 0.0;
+    double x = rho / 6.0, k = p->alpha / p->beta, m = p->gamma / p->beta;
+    return -p->ec * (1.0 - k * log(x)) * pow(x, k) - 3.0 * p->phi * pow(x, m);
+}
+static double eam_dF(const eam_p* p, double rho)          /* dF / d rho */
+{
+    if (!(rho > 0.0)) return 0.0;
+    double x = rho / 6.0, k = p->alpha / p->beta, m = p->gamma / p->beta;
+    return (p->ec * k * k * log(x) * pow(x, k - 1.0) - 3.0 * p->phi * m * pow(x, m - 1.0)) / 6.0;
+}
+
+/* Force (units D / r0) and energy (units D) of an atom at density n with gradient grad (n0 per
+ * cell) under the embedded-atom form; axes: 2 (x and z, the y neighbours at rbar) or 3. */
+static void eam_atom(const eam_p* p, double n, const double grad[3], int three_d, double r0_dx, double F[3],
+                     double* u)
+{
+    double rp[3], rm[3];
+    double rbar = pow(n, -1.0 / 3.0), rho = 0.0, upair = 0.0;
+    F[0] = F[1] = F[2] = 0.0;
+    for (int d = 0; d < 3; d++) {
+        if (!three_d && d == 1) {                 /* 2D: the +-y neighbours at rbar */
+            rp[d] = rm[d] = rbar;
+        } else {
+            oracle_neighbor_distances(n, grad[d], r0_dx, &rp[d], &rm[d]);
+        }
+        if (!isinf(rp[d])) { rho += eam_f(p, rp[d]); upair += eam_phi(p, rp[d]); }
+        if (!isinf(rm[d])) { rho += eam_f(p, rm[d]); upair += eam_phi(p, rm[d]); }
+    }
+    double dFi = eam_dF(p, rho);
+    for (int d = 0; d < 3; d++) {
+        if (!three_d && d == 1) continue;
+        double T[2] = {0.0, 0.0};
+        for (int side = 0; side < 2; side++) {
+            double r = side == 0 ? rp[d] : rm[d];
+            if (isinf(r)) continue;
+            double nj = n + (side == 0 ? 1.0 : -1.0) * r * r0_dx * grad[d];
+            double dFj = nj > 0.0 ? eam_dF(p, 6.0 * eam_f(p, pow(nj, -1.0 / 3.0))) : 0.0;
+            T[side] = eam_dphi(p, r) + (dFi + dFj) * eam_df(p, r);
+        }
+        F[d] = T[0] - T[1];
+    }
+    *u = eam_F(p, rho) + 0.5 * upair;
+}
+
+/* the form's parameters in units of D */
+static eam_p eam_params(double D_eV, double ec, double phi, double alpha, double beta, double gamma)
+{
+    eam_p p = {ec / D_eV, phi / D_eV, alpha, beta, gamma};
+    return p;
+}
+
+/* Force (units D / r0) and energy (units D) on an atom at density n, gradient dnx, dnz (2D), for
+ * the probes of the tests */
+void oracle_eam_atom2(double D_eV, double ec, double phi, double alpha, double beta, double gamma, double n,
+                      double dnx, double dnz, double r0_dx, double out[3])
+{
+    eam_p p = eam_params(D_eV, ec, phi, alpha, beta, gamma);
+    double grad[3] = {dnx, 0.0, dnz}, F[3], u;
+    if (!(n > 0.0)) { out[0] = out[1] = out[2] = 0.0; return; }
+    eam_atom(&p, n, grad, 0, r0_dx, F, &u);
+    out[0] = F[0];
+    out[1] = F[2];
+    out[2] = u;
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -433,6 +531,14 @@ static void pair_force_at(const ostate* s, double x, double z, double F[3], doub
     if (energy) *energy = 0.0;
     if (!(n > 0.0)) return;
     double r0_dx = s->r0 / s->c.dx;
+    if (s->c.pot_mode == 3) {
+        eam_p p = eam_params(s->c.D_eV, s->c.eam_ec, s->c.eam_phi, s->c.eam_alpha, s->c.eam_beta, s->c.eam_gamma);
+        double grad[3] = {dnx, 0.0, dnz}, Fu[3], u;
+        eam_atom(&p, n, grad, 0, r0_dx, Fu, &u);
+        for (int d = 0; d < 3; d++) F[d] = (s->D / s->r0) * Fu[d];
+        if (energy) *energy = s->D * u;
+        return;
+    }
     if (s->c.lattice == 1) {
         double grad[3] = {dnx, 0.0, dnz}, Fu[3], u;
         lattice_pair(1, s->c.pot_mode, s->c.c_att, s->c.s_rep, s->c.morse_a, n, grad, r0_dx, Fu, &u);
@@ -1001,6 +1107,7 @@ typedef struct {
     int32_t lattice;
     double T_spot_K, spot_w, spot_depth;
     double morse_a;
+    double eam_ec, eam_phi, eam_alpha, eam_beta, eam_gamma;
 } ocfg3;
 
 typedef struct {
@@ -1172,6 +1279,14 @@ static void pair_force3_at(const ostate3* s, double x, double y, double z, doubl
     if (!(n > 0.0)) return;
     double r0_dx = s->r0 / s->c.dx, f_unit = s->D / s->r0, u = 0.0;
     int pm = s->c.pot_mode;
+    if (pm == 3) {
+        eam_p p = eam_params(s->c.D_eV, s->c.eam_ec, s->c.eam_phi, s->c.eam_alpha, s->c.eam_beta, s->c.eam_gamma);
+        double Fu[3];
+        eam_atom(&p, n, g, 1, r0_dx, Fu, &u);
+        for (int d = 0; d < 3; d++) F[d] = f_unit * Fu[d];
+        if (energy) *energy = s->D * u;
+        return;
+    }
     if (s->c.lattice == 1) {
         double Fu[3];
         lattice_pair(1, pm, s->c.c_att, s->c.s_rep, s->c.morse_a, n, g, r0_dx, Fu, &u);

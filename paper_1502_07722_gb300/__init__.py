@@ -42,6 +42,8 @@ class pic_config(ctypes.Structure):
         ("temp_profile", ctypes.c_int32), ("lattice", ctypes.c_int32),
         ("T_spot_K", ctypes.c_double), ("spot_w", ctypes.c_double), ("spot_depth", ctypes.c_double),
         ("morse_a", ctypes.c_double),
+        ("eam_ec", ctypes.c_double), ("eam_phi", ctypes.c_double), ("eam_alpha", ctypes.c_double),
+        ("eam_beta", ctypes.c_double), ("eam_gamma", ctypes.c_double),
     ]
 
 

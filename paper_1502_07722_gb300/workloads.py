@@ -24,6 +24,10 @@ COPPER = dict(
     c_att=1.0,
     s_rep=1.0,
     pot_mode=0,
+    # embedded-atom form (pot_mode 3): Johnson's analytic nearest-neighbour EAM for copper
+    # (Phys. Rev. B 37, 3924, 1988), its published fcc values used as they are on the cubic lattice
+    # (an assumption: the paper names no EAM parameters)
+    eam_ec=3.54, eam_phi=0.59, eam_alpha=5.09, eam_beta=5.85, eam_gamma=8.00,
     mode=0,
     **{"lambda": 800e-9},
     tau_fwhm=30e-15,

@@ -94,10 +94,12 @@ def test_uniform_lattice3_zero_force_and_energy(pot):
     assert o.energy()["pair"] == pytest.approx(-bonds / 2 * D * n * o.weight, rel=1e-12)
 
 
-@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 4.0}, {"lattice": 1}], ids=["lj", "morse", "hcp"])
+@pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 4.0}, {"lattice": 1}, {"pot_mode": 3}],
+                         ids=["lj", "morse", "hcp", "eam"])
 def test_pair_force_3d_equals_2d_on_y_uniform_state(pot):
     """The 2D method is the 3D method on a state that does not vary along y: same x and z forces
-    (the y force vanishes), for either pair potential."""
+    (the y force vanishes), for either pair potential, the HCP geometry and the embedded-atom form
+    (whose 2D form puts the +-y neighbours at rbar with their own density n)."""
     nx, nz, ny = 12, 10, 4
     rng = np.random.default_rng(5)
     ncell = nx * 5

@@ -801,6 +801,67 @@ def test_pair_energy_of_equilibrium_lattice(pot, bonds):
     assert (not F.any()) if not pot.get("lattice") else np.abs(F).max() < 1e-25   # HCP: directions' rounding
 
 
+# ---- embedded-atom form (pot_mode 3): the density mapping adapted to a many-body potential --------
+
+def _rose(w, r):
+    """Universal binding curve of the uniform cubic lattice, units D: -E_c (1 + a) e^-a, a = alpha (r - 1),
+    and its second derivative E_c alpha^2 (1 - a) e^-a."""
+    ec, al = w["eam_ec"] / w["D_eV"], w["eam_alpha"]
+    a = al * (r - 1.0)
+    return -ec * (1.0 + a) * math.exp(-a), ec * al * al * (1.0 - a) * math.exp(-a)
+
+
+@pytest.mark.parametrize("n", [0.6, 0.8, 1.0, 1.2, 1.5])
+def test_eam_uniform_lattice_follows_the_binding_curve(n):
+    """The embedded-atom form on the paper's cubic lattice: an atom in a uniform density n (all six
+    neighbours at rbar = n^(-1/3)) has the energy of the universal binding curve the form is built
+    on, -E_c (1 + a) e^(-a) with a = alpha (rbar - 1): -E_c at the equilibrium density, and no force."""
+    w = workload("transport", pot_mode=3)
+    r0_dx = w["n_atoms"] ** (-1 / 3) / w["dx"]
+    Fx, Fz, u = oracle.eam_atom2(w, n, 0.0, 0.0, r0_dx)
+    assert Fx == 0.0 and Fz == 0.0
+    assert u == pytest.approx(_rose(w, n ** (-1 / 3))[0], rel=1e-13)
+
+
+@pytest.mark.parametrize("n", [0.7, 0.9, 1.0, 1.1, 1.3])
+def test_eam_first_order_force_is_the_binding_curve_stiffness(n):
+    """To first order in the density gradient the embedded-atom force along an axis is
+    (1/3) E''(rbar) rbar g, E the binding curve and g = d rbar / dx from Eq. (1) (derived by hand:
+    the bond tension phi' + 2 F' f' changes by (phi'' + 2 F' f'') rbar g across the atom, the two
+    neighbours' embedding densities differ by 12 f' rbar g, and E'' = 3 phi'' + 6 F' f'' + 36 F'' f'^2
+    for E = F(6 f) + 3 phi). It depends on E_c and alpha only, so a slip in F', in the neighbours'
+    densities or in a sign breaks it. Atoms in a compressed region (rbar < 1) are pushed down the
+    gradient."""
+    w = workload("transport", pot_mode=3)
+    r0_dx = w["n_atoms"] ** (-1 / 3) / w["dx"]
+    rbar = n ** (-1 / 3)
+    for dn in (1e-5, -2e-5):
+        g = -(1.0 / 3.0) * r0_dx * n ** (-4.0 / 3.0) * dn
+        expect = _rose(w, rbar)[1] * rbar * g / 3.0
+        Fx, Fz, _ = oracle.eam_atom2(w, n, dn, 0.0, r0_dx)
+        assert Fx == pytest.approx(expect, rel=1e-5)
+        assert Fz == 0.0
+        _, Fz2, _ = oracle.eam_atom2(w, n, 0.0, dn, r0_dx)
+        assert Fz2 == pytest.approx(expect, rel=1e-5)
+        if rbar < 1.0 and dn > 0:
+            assert Fx < 0.0
+
+
+def test_eam_equilibrium_slab_energy_and_zero_force():
+    """A uniform slab at the equilibrium density (the wall rows mirrored) under the embedded-atom
+    form: pair energy -E_c per atom and exactly zero force."""
+    nx, nz = 16, 12
+    w = workload("tiny", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, laser_profile=0, pot_mode=3)
+    o = oracle.Oracle(w, with_particles=False)
+    n = nx * nz * 4
+    cell = np.repeat(np.arange(nx * nz), 4)
+    x = cell % nx + np.tile([0.1, 0.35, 0.6, 0.85], nx * nz)
+    z = cell // nx + 0.5
+    o.set_particles(0, x, z, np.zeros(n), np.zeros(n), np.zeros(n))
+    assert not o.pair_force().any()
+    assert o.energy()["pair"] == pytest.approx(-w["eam_ec"] * QE * n * o.weight, rel=1e-12)
+
+
 @pytest.mark.parametrize("axis", ["x", "z"])
 @pytest.mark.parametrize("pot", [{}, {"pot_mode": 2, "morse_a": 4.0}], ids=["lj", "morse"])
 def test_hcp_first_order_force_is_twice_the_cubic(axis, pot):
