@@ -78,7 +78,8 @@ typedef struct pic_config {
     int32_t pot_mode;        /* 0: Eq. (3) as printed; 1: altered L-J (s_rep below r0, c_att above);
                                 2: Morse, U = D [e^(-2a(r/r0-1)) - 2 e^(-a(r/r0-1))], a = morse_a (the
                                 paper: the density-to-distance mapping takes any pair potential,
-                                the Morse potential among them); its minimum is -D at r0 like Eq. (3) */
+                                the Morse potential among them); its minimum is -D at r0 like Eq. (3);
+                                3: the embedded-atom form (eam_* below)                            */
     int32_t laser_profile;   /* PIC_LASER_*                                                     */
     int32_t tile;            /* tile edge in cells for particle binning (0: 16 in 2D, 10 in 3D)  */
     int32_t sort_every;      /* steps between cell sorts (0: only after init / set_particles)  */
@@ -122,6 +123,18 @@ typedef struct pic_config {
     double spot_depth;       /* 1/e depth of the temperature below the surface (m)                */
     double morse_a;          /* Morse stiffness alpha r0 (dimensionless, 0 < morse_a < 1000) for
                                 pot_mode 2; unused otherwise                                      */
+    double eam_ec, eam_phi;  /* pot_mode 3, the embedded-atom form on the cubic lattice (the paper:
+                                other potentials adapt to its density mapping), r in units of r0:
+                                f(r) = exp(-eam_beta (r - 1)) per neighbour, pair term
+                                phi(r) = eam_phi exp(-eam_gamma (r - 1)), embedding energy
+                                F(rho) = -eam_ec (1 - (a/b) ln x) x^(a/b) - 3 eam_phi x^(g/b),
+                                x = rho / 6 (a, b, g = eam_alpha, eam_beta, eam_gamma), so that a
+                                uniform lattice follows -eam_ec (1 + a(r - 1)) e^(-a(r - 1)). Atom i's
+                                embedding density sums f over its six Eq. (2) neighbours; neighbour j's
+                                is 6 f(n_j^(-1/3)), n_j the density at j's position (n + s dn along the
+                                axis, s its offset); each bond pulls with phi' + (F'(rho_i) + F'(rho_j)) f'.
+                                eam_ec, eam_phi in eV (> 0); exponents > 0. Cubic lattice only.       */
+    double eam_alpha, eam_beta, eam_gamma;
 } pic_config;
 
 #define PIC_TEMP_UNIFORM 0

@@ -62,9 +62,10 @@ int derive_layout(const pic_config* cfg, Layout& L)
         !(cfg->lambda > 0 && cfg->tau_fwhm > 0))
         return PIC_EINVAL;
     if (cfg->laser_profile == PIC_LASER_GAUSSIAN && !(cfg->w0 > 0)) return PIC_EINVAL;
-    if (cfg->pot_mode < 0 || cfg->pot_mode > 2) return PIC_EINVAL;
+    if (cfg->pot_mode < 0 || cfg->pot_mode > 3) return PIC_EINVAL;
     if (cfg->pot_mode == 2 && !(cfg->morse_a > 0 && cfg->morse_a < 1e3)) return PIC_EINVAL;
     if (cfg->lattice != PIC_LATTICE_CUBIC && cfg->lattice != PIC_LATTICE_HCP) return PIC_EINVAL;
+    if (!eam_config_ok(*cfg)) return PIC_EINVAL;
     if (cfg->temp_profile != PIC_TEMP_UNIFORM && cfg->temp_profile != PIC_TEMP_SPOT) return PIC_EINVAL;
     if (cfg->temp_profile == PIC_TEMP_SPOT &&
         (!(cfg->spot_w > 0) || !(cfg->spot_depth > 0) || !(cfg->T_spot_K >= 0)))
@@ -217,6 +218,7 @@ StepArgs make_step_args(Ctx& c)
     a.status = c.status;
     a.nsp = c.nsp;
     for (int s = 0; s < 2; s++) a.sp[s] = c.sp[s];
+    a.eam = eam_params(c.cfg);
     a.jy_scale = ldexpf(1.0f, c.jy_bits);
     a.jy_zero = ldexpf(1.0f, -(c.jy_bits + 1));
     return a;

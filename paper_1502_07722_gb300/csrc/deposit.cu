@@ -25,7 +25,7 @@ __global__ void k_deposit_density(const int32_t* __restrict__ cell, const float*
 __global__ void k_pair_force(const int32_t* __restrict__ cell, const float* __restrict__ fx,
                              const float* __restrict__ fz, int64_t n, int nx, int nz, const u64* __restrict__ rho,
                              float rho_s, float h_coef, int pot_mode, float c_att, float s_rep, float f_unit,
-                             float* __restrict__ out)
+                             EamP eam, float* __restrict__ out)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int c = cell[p];
@@ -33,7 +33,7 @@ __global__ void k_pair_force(const int32_t* __restrict__ cell, const float* __re
         float dens, dnx, dnz;
         gather_density(rho, nx, nz, rho_s, i, k, fx[p], fz[p], dens, dnx, dnz);
         float Fx, Fz;
-        pair_force_xz(dens, dnx, dnz, h_coef, pot_mode, c_att, s_rep, Fx, Fz);
+        pair_force_xz(dens, dnx, dnz, h_coef, pot_mode, c_att, s_rep, Fx, Fz, eam);
         out[3 * p + 0] = f_unit * Fx;
         out[3 * p + 1] = 0.0f;
         out[3 * p + 2] = f_unit * Fz;
@@ -46,7 +46,7 @@ __global__ void k_pair_force(const int32_t* __restrict__ cell, const float* __re
 __global__ void k_pair_force_probe(const int32_t* __restrict__ cell, const float* __restrict__ fx,
                                    const float* __restrict__ fz, int64_t n, int nx, int nz,
                                    const u64* __restrict__ rho, float rho_s, float h_coef, int pot_mode,
-                                   float c_att, float s_rep, float f_unit, float* __restrict__ out)
+                                   float c_att, float s_rep, float f_unit, EamP eam, float* __restrict__ out)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int c = cell[p];
@@ -59,7 +59,7 @@ __global__ void k_pair_force_probe(const int32_t* __restrict__ cell, const float
         float dens, dnx, dnz;
         gather_density(rho, nx, nz, rho_s, i, k, a, b, dens, dnx, dnz);
         float Fx, Fz;
-        pair_force_xz<true>(dens, dnx, dnz, h_coef, pot_mode, c_att, s_rep, Fx, Fz);
+        pair_force_xz<true>(dens, dnx, dnz, h_coef, pot_mode, c_att, s_rep, Fx, Fz, eam);
         out[3 * p + 0] = f_unit * Fx;
         out[3 * p + 1] = 0.0f;
         out[3 * p + 2] = f_unit * Fz;
@@ -108,7 +108,7 @@ void launch_pair_force_probe(Ctx& c, int64_t n, const int32_t* cell, const float
     if (n == 0) return;
     k_pair_force_probe<<<grid_for(c, n), 256, 0, st>>>(cell, fx, fz, n, c.nx, c.nz, c.rho[c.cur], (float)c.rho_scale,
                                                       (float)(c.r0 / (6.0 * c.cfg.dx)), pot_mode, (float)c_att,
-                                                      (float)s_rep, (float)(c.D / c.r0), out);
+                                                      (float)s_rep, (float)(c.D / c.r0), eam_params(c.cfg), out);
 }
 
 void launch_pair_force(Ctx& c, float* out, cudaStream_t st)
@@ -118,7 +118,7 @@ void launch_pair_force(Ctx& c, float* out, cudaStream_t st)
     k_pair_force<<<grid_for(c, S.n), 256, 0, st>>>(S.a.cell, S.a.fx, S.a.fz, S.n, c.nx, c.nz, c.rho[c.cur],
                                                    (float)c.rho_scale, (float)(c.r0 / (6.0 * c.cfg.dx)),
                                                    pot_code(c.cfg), pot_param(c.cfg), (float)c.cfg.s_rep,
-                                                   (float)(c.D / c.r0), out);
+                                                   (float)(c.D / c.r0), eam_params(c.cfg), out);
 }
 
 }  // namespace gbpic

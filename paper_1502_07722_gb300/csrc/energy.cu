@@ -30,6 +30,7 @@ struct EnergyArgs {
     const u64* rho;
     float rho_s, h_coef, c_att, s_rep;
     int pot_mode;
+    EamP eam;
     double* partials;   // gridDim.x * kSlots
 };
 
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(kEBlock) k_energy(const EnergyArgs a)
                 if (n > 0.0f) {
                     const float cr = fast_cbrt(n);
                     const float inv43 = fast_rcp(n * cr);
-                    float e = pair_energy_xz(cr, inv43, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep);
+                    float e = pair_energy_xz(cr, inv43, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, a.eam);
                     pe += (double)e;
                 }
             }
@@ -113,6 +114,7 @@ void launch_energy(Ctx& c, cudaStream_t st, double* host_out5)
     a.c_att = pot_param(c.cfg);
     a.s_rep = (float)c.cfg.s_rep;
     a.pot_mode = pot_code(c.cfg);
+    a.eam = eam_params(c.cfg);
     a.partials = c.partials;
     const int nb = energy_blocks(c);
     k_energy<<<nb, kEBlock, 0, st>>>(a);
@@ -198,9 +200,10 @@ extern "C" int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* i
     if (cfg->nx < 3 || cfg->nz < 4 || cfg->nx >= 32768 || cfg->nz >= 32768) return PIC_EINVAL;
     if (cfg->mode != PIC_MODE_FULL && cfg->mode != PIC_MODE_TRANSPORT) return PIC_EINVAL;
     if (!(cfg->dx > 0) || !(cfg->n_atoms > 0) || !(cfg->ion_mass_amu > 0) || cfg->ppc_ion <= 0) return PIC_EINVAL;
-    if (cfg->pot_mode < 0 || cfg->pot_mode > 2) return PIC_EINVAL;
+    if (cfg->pot_mode < 0 || cfg->pot_mode > 3) return PIC_EINVAL;
     if (cfg->pot_mode == 2 && !(cfg->morse_a > 0 && cfg->morse_a < 1e3)) return PIC_EINVAL;
     if (cfg->lattice != PIC_LATTICE_CUBIC && cfg->lattice != PIC_LATTICE_HCP) return PIC_EINVAL;
+    if (!eam_config_ok(*cfg)) return PIC_EINVAL;
     const int nsp = cfg->mode == PIC_MODE_FULL ? 2 : 1;
     for (int s = 0; s < nsp; s++) {
         // sizes beyond what the kernels index with 32-bit cells are refused
@@ -248,6 +251,7 @@ extern "C" int pic_energy_noalloc(const pic_config* cfg, const pic_state_view* i
     a.c_att = pot_param(*cfg);
     a.s_rep = (float)cfg->s_rep;
     a.pot_mode = pot_code(*cfg);
+    a.eam = eam_params(*cfg);
     a.partials = scratch;    // every block overwrites its own record: nothing to clear
     const cudaStream_t st = (cudaStream_t)stream;
     const double vol = cfg->dx * cfg->dx;

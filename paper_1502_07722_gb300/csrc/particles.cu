@@ -228,7 +228,7 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
     if (kPair) {
         float pfx, pfz;
         if (POT == kPotLJ) lj_pair_xz2(n, dnx, dnz, a.h_coef, pfx, pfz);
-        else pair_force_xz<false, POT>(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz);
+        else pair_force_xz<false, POT>(n, dnx, dnz, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pfx, pfz, a.eam);
         kx += S.p_kick * pfx;
         kz += S.p_kick * pfz;
     }
@@ -497,8 +497,9 @@ static int parts_per_tile(int ntiles, int slots)
 size_t particle_smem_bytes(int W) { return sizeof(unsigned) * (size_t)7 * W * W; }
 
 // The kernel instances: Eq. (3), the altered potential and the Morse form, on the cubic and the
-// HCP lattice (potential code in bits 0-1, kLatHcp in bit 2), with and without fields.
-#define GBPIC_FOR_EACH_POT(X) X(kPotLJ) X(kPotAlt) X(kPotMorse) X(kPotLJ | kLatHcp) X(kPotAlt | kLatHcp) \
+// HCP lattice, and the embedded-atom form on the cubic lattice (potential code in bits 0-1,
+// kLatHcp in bit 2), with and without fields.
+#define GBPIC_FOR_EACH_POT(X) X(kPotLJ) X(kPotAlt) X(kPotMorse) X(kPotEam) X(kPotLJ | kLatHcp) X(kPotAlt | kLatHcp) \
     X(kPotMorse | kLatHcp)
 
 static void set_smem(const void* k, size_t shmem)

@@ -19,9 +19,10 @@
 namespace gbpic {
 
 // The kernel instances: Eq. (3), the altered potential and the Morse form, on the cubic and the
-// HCP lattice (potential code in bits 0-1, kLatHcp in bit 2).
-#define GBPIC_FOR_EACH_POT3(X) X(kPotLJ) X(kPotAlt) X(kPotMorse) X(kPotLJ | kLatHcp) X(kPotAlt | kLatHcp) \
-    X(kPotMorse | kLatHcp)
+// HCP lattice, and the embedded-atom form on the cubic lattice (potential code in bits 0-1,
+// kLatHcp in bit 2).
+#define GBPIC_FOR_EACH_POT3(X) X(kPotLJ) X(kPotAlt) X(kPotMorse) X(kPotEam) X(kPotLJ | kLatHcp) \
+    X(kPotAlt | kLatHcp) X(kPotMorse | kLatHcp)
 
 constexpr int kQ3Bits = 14;
 constexpr int kQ3 = 1 << kQ3Bits;
@@ -136,6 +137,7 @@ struct Args3 {
     int ntiles, nsp, full, pot_mode;
     int T, ntx, nty, W;     // tile edge, tiles along x and y, staged window edge (0: no window)
     float cdt_dx, rho_s, h_coef, c_att, s_rep;
+    EamP eam;
     const float* F[6];
     const u64* rho_cur;
     u64* rho_next;
@@ -385,7 +387,7 @@ __device__ __forceinline__ void process3(const Args3& a, const Species3& S, cons
             const float c = fast_cbrt(n);
             const float inv43 = fast_rcp(n * c);
             float pf[3];
-            pair_force3<POT>(n, c, inv43, gr, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pf);
+            pair_force3<POT>(n, c, inv43, gr, a.h_coef, a.pot_mode, a.c_att, a.s_rep, pf, a.eam);
             kx += S.p_kick * pf[0];
             ky += S.p_kick * pf[1];
             kz += S.p_kick * pf[2];
@@ -550,6 +552,7 @@ void launch_particle_step3(Ctx& c, cudaStream_t st)
     a.h_coef = (float)(c.r0 / (6.0 * c.cfg.dx));
     a.c_att = pot_param(c.cfg);
     a.s_rep = (float)c.cfg.s_rep;
+    a.eam = eam_params(c.cfg);
     for (int q = 0; q < 6; q++) a.F[q] = c.F[q];
     a.rho_cur = c.rho[c.cur];
     a.rho_next = c.rho[1 - c.cur];
@@ -619,7 +622,7 @@ __global__ void k_deposit_density3(const int32_t* __restrict__ cell, const float
 __global__ void k_pair_force3(const int32_t* __restrict__ cell, const float* __restrict__ fx,
                               const float* __restrict__ fy, const float* __restrict__ fz, int64_t n, Geo3 g,
                               const u64* __restrict__ rho, float rho_s, float h_coef, int pot_mode, float c_att,
-                              float s_rep, float f_unit, float* __restrict__ out)
+                              float s_rep, float f_unit, EamP eam, float* __restrict__ out)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -630,7 +633,7 @@ __global__ void k_pair_force3(const int32_t* __restrict__ cell, const float* __r
         if (dens > 0.0f) {
             const float cr = fast_cbrt(dens);
             const float inv43 = fast_rcp(dens * cr);
-            pair_force3(dens, cr, inv43, gr, h_coef, pot_mode, c_att, s_rep, F);
+            pair_force3(dens, cr, inv43, gr, h_coef, pot_mode, c_att, s_rep, F, eam);
             for (int d = 0; d < 3; d++) F[d] *= f_unit;
         }
         out[3 * p] = F[0];
@@ -661,7 +664,7 @@ void launch_pair_force3(Ctx& c, float* out, cudaStream_t st)
     k_pair_force3<<<grid3(c, S.n), 256, 0, st>>>(S.a.cell, S.a.fx, S.a.fy, S.a.fz, S.n, geo_of(c), c.rho[c.cur],
                                                   (float)c.rho_scale, (float)(c.r0 / (6.0 * c.cfg.dx)),
                                                   pot_code(c.cfg), pot_param(c.cfg), (float)c.cfg.s_rep,
-                                                  (float)(c.D / c.r0), out);
+                                                  (float)(c.D / c.r0), eam_params(c.cfg), out);
 }
 
 // ---- 3D Yee --------------------------------------------------------------------------------
@@ -817,7 +820,8 @@ void launch_fields3(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches)
 __global__ void __launch_bounds__(256) k_energy3(const Species3 s0, const Species3 s1, int64_t n0, int64_t n1, int nsp, Geo3 g,
                                                  const float* F0, const float* F1, const float* F2, const float* F3,
                                                  const float* F4, const float* F5, const u64* rho, float rho_s,
-                                                 float h_coef, int pot_mode, float c_att, float s_rep, double* partials)
+                                                 float h_coef, int pot_mode, float c_att, float s_rep, EamP eam,
+                                                 double* partials)
 {
     __shared__ double sh[256];
     const int64_t tid = blockIdx.x * (int64_t)256 + threadIdx.x, stride = (int64_t)gridDim.x * 256;
@@ -837,7 +841,7 @@ __global__ void __launch_bounds__(256) k_energy3(const Species3 s0, const Specie
                 if (dens > 0.0f) {
                     const float cr = fast_cbrt(dens), inv43 = fast_rcp(dens * cr);
                     float e = 0.0f;
-                    e += pair_energy3(cr, inv43, gr, h_coef, pot_mode, c_att, s_rep);
+                    e += pair_energy3(cr, inv43, gr, h_coef, pot_mode, c_att, s_rep, eam);
                     pe += (double)e;
                 }
             }
@@ -899,7 +903,7 @@ void launch_energy3(Ctx& c, cudaStream_t st, double* host_out5)
     k_energy3<<<nb, 256, 0, st>>>(sp[0], sp[1], c.sp[0].n, c.nsp > 1 ? c.sp[1].n : 0, c.nsp, geo_of(c), c.F[0], c.F[1],
                                   c.F[2], c.F[3], c.F[4], c.F[5], c.rho[c.cur], (float)c.rho_scale,
                                   (float)(c.r0 / (6.0 * c.cfg.dx)), pot_code(c.cfg), pot_param(c.cfg),
-                                  (float)c.cfg.s_rep, c.partials);
+                                  (float)c.cfg.s_rep, eam_params(c.cfg), c.partials);
     k_energy3_final<<<1, 256, 0, st>>>(c.partials, nb, c.red_out);
     double raw[5];
     cudaMemcpyAsync(raw, c.red_out, sizeof(raw), cudaMemcpyDeviceToHost, st);

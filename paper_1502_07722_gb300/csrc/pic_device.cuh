@@ -110,8 +110,9 @@ __device__ __forceinline__ float pair_U(int pot_mode, float c_att, float s_rep, 
 // kernels take the code as a template argument, so that the plain Lennard-Jones instances carry no
 // branch factor, Morse or HCP code (a uniform run-time branch to the out-of-line Morse call cost 6 %
 // of the 3D particle kernel's time).
-enum { kPotRuntime = -1, kPotLJ = 0, kPotAlt = 1, kPotMorse = 2, kLatHcp = 4 };
+enum { kPotRuntime = -1, kPotLJ = 0, kPotAlt = 1, kPotMorse = 2, kPotEam = 3, kLatHcp = 4 };
 
+// kPotEam: the embedded-atom form (pot_mode 3, cubic lattice only; see eam_forces below).
 // The kernel instance code of a run-time potential code (pot_mode in bits 0-1, kLatHcp in bit 2).
 inline int pot_instance(int code) { return code & 7; }
 
@@ -279,15 +280,131 @@ namespace gbpic {
 // with the density derivative along u. Their y components cancel.
 constexpr float kHcpS = 0.816496580927726f;    // sqrt(2/3)
 
+// ---- the embedded-atom form (pot_mode 3) on the cubic lattice (the paper: other potentials are
+// readily adapted to its mapping of density to neighbour distance). Atom i's embedding density is
+// the sum of f over its six Eq. (2) neighbours; neighbour j's own is 6 f(n_j^(-1/3)), n_j the
+// interpolated density at j's position taken along the axis, n + s dn (s = the neighbour's offset
+// in cells: its distance in r0 times r0 / dx = 6 h_coef); each bond pulls with
+// T = phi'(r) + (F'(rho_i) + F'(rho_j)) f'(r) and the force along an axis is T(r+) - T(r-).
+__device__ __forceinline__ float eam_f(const EamP& e, float r) { return expf(-e.beta * (r - 1.0f)); }
+__device__ __forceinline__ float eam_phi(const EamP& e, float r) { return e.phi * expf(-e.gamma * (r - 1.0f)); }
+// dF / d rho
+__device__ __forceinline__ float eam_dF(const EamP& e, float rho)
+{
+    if (!(rho > 0.0f)) return 0.0f;
+    const float lx = logf(rho * (1.0f / 6.0f)), k = e.alpha / e.beta, m = e.gamma / e.beta;
+    return (e.ec * k * k * lx * expf((k - 1.0f) * lx) - 3.0f * e.phi * m * expf((m - 1.0f) * lx)) * (1.0f / 6.0f);
+}
+__device__ __forceinline__ float eam_F(const EamP& e, float rho)
+{
+    if (!(rho > 0.0f)) return 0.0f;
+    const float lx = logf(rho * (1.0f / 6.0f)), k = e.alpha / e.beta, m = e.gamma / e.beta;
+    return -e.ec * (1.0f - k * lx) * expf(k * lx) - 3.0f * e.phi * expf(m * lx);
+}
+
+// F'(rho) of a neighbour whose own environment is uniform at spacing rb (rho = 6 f(rb)), as a
+// function of rb: with L = ln(rho / 6) = -beta (rb - 1),
+//   F' = -(1/6) [ec k^2 beta (rb - 1) e^(-(alpha - beta)(rb - 1)) + 3 phi m e^(-(gamma - beta)(rb - 1))].
+__device__ __forceinline__ float eam_dF_rb(const EamP& e, float rb)
+{
+    const float k = e.alpha / e.beta, m = e.gamma / e.beta, t = rb - 1.0f;
+    return -(1.0f / 6.0f) *
+           (e.ec * k * k * e.beta * t * expf(-(e.alpha - e.beta) * t) + 3.0f * e.phi * m * expf(-(e.gamma - e.beta) * t));
+}
+
+// F'(rb+) - F'(rb-) from rb- and dl = rb+ - rb- without cancellation (expm1 of the exponents'
+// differences; the (rb - 1) factor moves by dl).
+__device__ __forceinline__ float eam_dF_rb_diff(const EamP& e, float rbm, float dl)
+{
+    const float k = e.alpha / e.beta, m = e.gamma / e.beta, t = rbm - 1.0f;
+    const float a = e.alpha - e.beta, b = e.gamma - e.beta;
+    const float ea = expf(-a * t), eb = expf(-b * t);
+    const float d1 = t * expm1f(-a * dl) + dl * expf(-a * dl);        // (t + dl) e^(-a dl) - t
+    return -(1.0f / 6.0f) * (e.ec * k * k * e.beta * ea * d1 + 3.0f * e.phi * m * eb * expm1f(-b * dl));
+}
+
+// Force (units D / r0) along the axes and energy (units D, the atom's full share: the callers
+// that halve pair energies get twice it) of an atom at density n (c = n^(1/3), inv43 = n^(-4/3))
+// with gradient g per cell. NAX axes carry Eq. (2) neighbours (2: x and z, g[1] unused, the +-y
+// neighbours at rbar with their own density n; 3: x, y, z). With both neighbours of an axis
+// finite and inside the slab, T(r+) - T(r-) is formed without cancellation:
+//   -gamma [phi(r+) - phi(r-)] - beta F'_i [f(r+) - f(r-)] - beta [(F'_+ - F'_-) f(r+) + F'_- (f(r+) - f(r-))],
+//   phi(r+) - phi(r-) = phi(r-) expm1(-gamma dr), f(r+) - f(r-) = f(r-) expm1(-beta dr),
+//   dr = r+ - r- = 2h / (c (1 - h^2)), and F'_+ - F'_- from the neighbours' spacings, whose
+//   difference is (n-^(1/3) - n+^(1/3)) / (n+ n-)^(1/3) with n+^(1/3) - n-^(1/3) = (n+ - n-) / (sum
+//   of the three products of their cube roots), n+ - n- = s (r+ + r-) dn.
+template <int NAX>
+__device__ __forceinline__ void eam_forces(const EamP& e, float n, float c, float inv43, const float g[3], float h_coef,
+                                           float F[3], float* u)
+{
+    constexpr int nax = 3;
+    float rp[nax], rm[nax], hh[nax], rho = 0.0f, up = 0.0f;
+#pragma unroll
+    for (int d = 0; d < nax; d++) {
+        hh[d] = 0.0f;
+        if (NAX == 2 && d == 1) {
+            rp[d] = rm[d] = 1.0f / c;
+        } else {
+            const float h = -h_coef * g[d] * inv43;
+            const float ip = c * (1.0f - h), im = c * (1.0f + h);
+            hh[d] = h;
+            rp[d] = ip > 0.0f ? 1.0f / ip : 0.0f;        // 0: the neighbour is at infinity
+            rm[d] = im > 0.0f ? 1.0f / im : 0.0f;
+        }
+        if (rp[d] > 0.0f) { rho += eam_f(e, rp[d]); up += eam_phi(e, rp[d]); }
+        if (rm[d] > 0.0f) { rho += eam_f(e, rm[d]); up += eam_phi(e, rm[d]); }
+    }
+    const float dFi = eam_dF(e, rho), s = 6.0f * h_coef;
+#pragma unroll
+    for (int d = 0; d < nax; d++) {
+        F[d] = 0.0f;
+        if (NAX == 2 && d == 1) continue;
+        const float npl = n + rp[d] * s * g[d], nmi = n - rm[d] * s * g[d];
+        if (rp[d] > 0.0f && rm[d] > 0.0f && npl > 0.0f && nmi > 0.0f) {
+            const float h = hh[d];
+            const float dr = 2.0f * h / (c * (1.0f - h * h));
+            const float cp = fast_cbrt(npl), cm = fast_cbrt(nmi);
+            const float rbm = 1.0f / cm;
+            // rb+ - rb- = (cm - cp) / (cp cm), cp - cm = (n+ - n-) / (cp^2 + cp cm + cm^2)
+            const float dn = (rp[d] + rm[d]) * s * g[d];
+            const float dl = -dn / ((cp * cp + cp * cm + cm * cm) * cp * cm);
+            const float fm = eam_f(e, rm[d]), fp = eam_f(e, rp[d]), df = fm * expm1f(-e.beta * dr);
+            const float dFm = eam_dF_rb(e, rbm);
+            F[d] = -e.gamma * eam_phi(e, rm[d]) * expm1f(-e.gamma * dr) - e.beta * dFi * df -
+                   e.beta * (eam_dF_rb_diff(e, rbm, dl) * fp + dFm * df);
+            continue;
+        }
+        float T[2] = {0.0f, 0.0f};
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            const float r = side == 0 ? rp[d] : rm[d];
+            if (!(r > 0.0f)) continue;
+            const float nj = side == 0 ? npl : nmi;
+            const float dFj = nj > 0.0f ? eam_dF(e, 6.0f * eam_f(e, 1.0f / fast_cbrt(nj))) : 0.0f;
+            T[side] = -e.gamma * eam_phi(e, r) - e.beta * (dFi + dFj) * eam_f(e, r);
+        }
+        F[d] = T[0] - T[1];
+    }
+    if (u) *u = eam_F(e, rho) + 0.5f * up;
+}
+
 template <bool ZERO_SKIP = false, int POT = kPotRuntime>
 __device__ __forceinline__ void pair_force_xz(float n, float dnx, float dnz, float h_coef, int pot_mode, float c_att,
-                                              float s_rep, float& fx, float& fz)
+                                              float s_rep, float& fx, float& fz, const EamP& eam = EamP{})
 {
     fx = 0.0f;
     fz = 0.0f;
     if (n > 0.0f) {
         const float c = fast_cbrt(n);
         const float inv43 = fast_rcp(n * c);
+        if ((POT >= 0 && (POT & 3) == kPotEam) || (POT == kPotRuntime && (pot_mode & 3) == 3)) {
+            const float g[3] = {dnx, 0.0f, dnz};
+            float F[3];
+            eam_forces<2>(eam, n, c, inv43, g, h_coef, F, nullptr);
+            fx = F[0];
+            fz = F[2];
+            return;
+        }
         const bool hcp = POT >= 0 ? (POT & kLatHcp) != 0 : (pot_mode & kLatHcp) != 0;
         if (!hcp) {
             fx = pair_axis<ZERO_SKIP, POT>(n, c, inv43, dnx, h_coef, pot_mode, c_att, s_rep);
@@ -345,8 +462,14 @@ __device__ __forceinline__ void lj_pair_xz2(float n, float dnx, float dnz, float
 // Pair energy of an atom (units D, twice the per-atom share: the caller halves it) in the x-z plane:
 // cubic: the +-x and +-z pairs and the two y neighbours at rbar; HCP: the pairs above.
 __device__ __forceinline__ float pair_energy_xz(float cr, float inv43, float dnx, float dnz, float h_coef, int pot_mode,
-                                                float c_att, float s_rep)
+                                                float c_att, float s_rep, const EamP& eam = EamP{})
 {
+    if ((pot_mode & 3) == 3) {
+        const float g[3] = {dnx, 0.0f, dnz};
+        float F[3], u;
+        eam_forces<2>(eam, cr * cr * cr, cr, inv43, g, h_coef, F, &u);
+        return 2.0f * u;
+    }
     if ((pot_mode & kLatHcp) == 0)
         return pair_energy_axis(cr, inv43, dnx, h_coef, pot_mode, c_att, s_rep) +
                pair_energy_axis(cr, inv43, dnz, h_coef, pot_mode, c_att, s_rep) + 2.0f * pair_U(pot_mode, c_att, s_rep, cr);
@@ -366,8 +489,12 @@ constexpr float kHcpR = 0.577350269189626f;    // 1/sqrt(3)
 
 template <int POT = kPotRuntime>
 __device__ __forceinline__ void pair_force3(float n, float c, float inv43, const float g[3], float h_coef, int pot_mode,
-                                            float c_att, float s_rep, float F[3])
+                                            float c_att, float s_rep, float F[3], const EamP& eam = EamP{})
 {
+    if ((POT >= 0 && (POT & 3) == kPotEam) || (POT == kPotRuntime && (pot_mode & 3) == 3)) {
+        eam_forces<3>(eam, n, c, inv43, g, h_coef, F, nullptr);
+        return;
+    }
     const bool hcp = POT >= 0 ? (POT & kLatHcp) != 0 : (pot_mode & kLatHcp) != 0;
     if (!hcp) {
         for (int d = 0; d < 3; d++) F[d] = pair_axis<false, POT>(n, c, inv43, g[d], h_coef, pot_mode, c_att, s_rep);
@@ -395,8 +522,13 @@ __device__ __forceinline__ void pair_force3(float n, float c, float inv43, const
 
 // 3D pair energy (units D, twice the per-atom share).
 __device__ __forceinline__ float pair_energy3(float cr, float inv43, const float g[3], float h_coef, int pot_mode,
-                                             float c_att, float s_rep)
+                                             float c_att, float s_rep, const EamP& eam = EamP{})
 {
+    if ((pot_mode & 3) == 3) {
+        float F[3], u;
+        eam_forces<3>(eam, cr * cr * cr, cr, inv43, g, h_coef, F, &u);
+        return 2.0f * u;
+    }
     if ((pot_mode & kLatHcp) == 0) {
         float e = 0.0f;
         for (int d = 0; d < 3; d++) e += pair_energy_axis(cr, inv43, g[d], h_coef, pot_mode, c_att, s_rep);

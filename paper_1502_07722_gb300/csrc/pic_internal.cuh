@@ -54,6 +54,32 @@ struct Species {
     double mass, uth;
 };
 
+// The embedded-atom form (pot_mode 3), energies in units of D, r in units of r0: f(r) =
+// exp(-beta (r - 1)), phi(r) = phi exp(-gamma (r - 1)), F(rho) = -ec (1 - (alpha/beta) ln x)
+// x^(alpha/beta) - 3 phi x^(gamma/beta), x = rho / 6.
+struct EamP {
+    float ec, phi, alpha, beta, gamma;
+};
+inline EamP eam_params(const pic_config& cfg)
+{
+    EamP e;
+    e.ec = (float)(cfg.eam_ec / cfg.D_eV);
+    e.phi = (float)(cfg.eam_phi / cfg.D_eV);
+    e.alpha = (float)cfg.eam_alpha;
+    e.beta = (float)cfg.eam_beta;
+    e.gamma = (float)cfg.eam_gamma;
+    return e;
+}
+
+// pot_mode 3 asks for the cubic lattice and positive parameters (eam_phi may be 0).
+inline bool eam_config_ok(const pic_config& cfg)
+{
+    if (cfg.pot_mode != 3) return true;
+    return cfg.lattice == PIC_LATTICE_CUBIC && cfg.eam_ec > 0 && cfg.eam_ec < 1e3 && cfg.eam_phi >= 0 &&
+           cfg.eam_phi < 1e3 && cfg.eam_alpha > 0 && cfg.eam_alpha < 1e3 && cfg.eam_beta > 0 && cfg.eam_beta < 1e3 &&
+           cfg.eam_gamma > 0 && cfg.eam_gamma < 1e3;
+}
+
 // The second parameter of the device pair functions: the Morse stiffness for pot_mode 2, the
 // attractive factor of the altered potential otherwise (the functions take it as c_att).
 inline float pot_param(const pic_config& cfg) { return (float)(cfg.pot_mode == 2 ? cfg.morse_a : cfg.c_att); }
@@ -79,6 +105,7 @@ struct StepArgs {
     unsigned* status;
     int32_t nsp;
     Species sp[2];
+    EamP eam;                                 // the embedded-atom form's parameters (pot_mode 3)
     float jy_scale;                           // 2^jy_bits: the J_y code V = rint(beta_y 2^jy_bits)
     float jy_zero;                            // 2^-(jy_bits + 1): |u_y| below it gives V = 0
 };

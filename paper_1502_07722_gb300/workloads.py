@@ -82,6 +82,8 @@ WORKLOADS = {
 # (Phys. Rev. 114, 687 (1959); not from the paper), r0 the cubic-lattice spacing at n0, depth D
 # as for Eq. (3)
 WORKLOADS["crater_morse"] = dict(WORKLOADS["crater"], pot_mode=2, morse_a=3.09)
+# the crater run with the embedded-atom form (pot_mode 3, Johnson's copper values above)
+WORKLOADS["crater_eam"] = dict(WORKLOADS["crater"], pot_mode=3)
 # the same crater run on the hexagonal close-packed neighbour geometry (lattice 1, c axis along z)
 WORKLOADS["crater_hcp"] = dict(WORKLOADS["crater"], lattice=1)
 # the crater run in 3D: 3 um x 3 um x 1.6 um box, slab 1 um thick, 16 macro-atoms per cell

@@ -40,7 +40,8 @@ def test_workspace_size_and_validation(lib):
     big = gb.pic_workspace_size(gb.make_config(workload("large2d")))
     assert big > 2 * 2 * 67108864 * 24
     for bad in (dict(nx=2), dict(nz=3), dict(slab_k=65), dict(ion_charge=2.0), dict(ppc_electron=4),
-                dict(tile=1), dict(pot_mode=3), dict(pot_mode=2), dict(pot_mode=2, morse_a=-1.0), dict(lattice=2),
+                dict(tile=1), dict(pot_mode=4), dict(pot_mode=2), dict(pot_mode=2, morse_a=-1.0), dict(lattice=2),
+                dict(pot_mode=3, lattice=1), dict(pot_mode=3, eam_ec=0.0), dict(pot_mode=3, eam_gamma=-1.0),
                 dict(laser_profile=2, w0=0.0), dict(cfl=1.5)):
         with pytest.raises(gb.PicError) as e:
             gb.pic_workspace_size(gb.make_config(workload("tiny"), **bad))
@@ -80,10 +81,11 @@ def test_init_rejects_bad_workspace_without_touching_the_gpu(lib):
 
 
 def test_config_struct_layout_matches_header(lib):
-    # 10 int32 + 1 int64 + 17 double + 1 uint64 + 2 int32 + 2 int32 + 4 double
-    assert ctypes.sizeof(gb.pic_config) == 10 * 4 + 8 + 17 * 8 + 8 + 2 * 4 + 2 * 4 + 4 * 8
+    # 10 int32 + 1 int64 + 17 double + 1 uint64 + 2 int32 + 2 int32 + 4 double + 5 double (EAM)
+    assert ctypes.sizeof(gb.pic_config) == 10 * 4 + 8 + 17 * 8 + 8 + 2 * 4 + 2 * 4 + 4 * 8 + 5 * 8
     assert ctypes.sizeof(gb.pic_config) == lib.pic_config_bytes()
-    assert gb.pic_config.morse_a.offset == ctypes.sizeof(gb.pic_config) - 8
+    assert gb.pic_config.morse_a.offset == ctypes.sizeof(gb.pic_config) - 6 * 8
+    assert gb.pic_config.eam_gamma.offset == ctypes.sizeof(gb.pic_config) - 8
     assert gb.pic_config.T_spot_K.offset == 10 * 4 + 8 + 17 * 8 + 8 + 4 * 4
     assert gb.pic_config.max_particles.offset == 40
     assert ctypes.sizeof(gb.pic_energy_t) == 7 * 8

@@ -73,7 +73,8 @@ def test_init3_matches_oracle(gb):
     assert np.array_equal(sim.get_density().cpu().numpy(), orc.get_rho())
 
 
-@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1)], ids=["lj", "morse", "hcp"])
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1), dict(pot_mode=3)],
+                         ids=["lj", "morse", "hcp", "eam"])
 def test_density3_and_pair_force(gb, pot):
     w = w3(max_particles=6000, **pot)
     sim = gb.Simulation(w)
@@ -156,7 +157,8 @@ def test_energy3_matches_oracle(gb):
     assert eg["kinetic_electron"] == pytest.approx(eo["kinetic_electron"], rel=1e-3)
 
 
-@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1)], ids=["lj", "morse", "hcp"])
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1), dict(pot_mode=3)],
+                         ids=["lj", "morse", "hcp", "eam"])
 def test_transport3_steps(gb, pot):
     w = w3(mode=1, ion_charge=0.0, ppc_electron=0, laser_profile=0, dt_override=12e-15, T_ion_K=3000.0, **pot)
     sim = gb.Simulation(w)

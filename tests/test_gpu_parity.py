@@ -102,8 +102,8 @@ def test_deposit_density_bit_exact(shape):
     assert scale == pytest.approx(orc.weight / (2 ** 32 * w["dx"] ** 2), rel=1e-15)
 
 
-@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1), dict(lattice=1, pot_mode=2, morse_a=4.0)],
-                         ids=["lj", "morse", "hcp", "hcp-morse"])
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1), dict(lattice=1, pot_mode=2, morse_a=4.0),
+                                 dict(pot_mode=3)], ids=["lj", "morse", "hcp", "hcp-morse", "eam"])
 def test_pair_force_matches_oracle(pot):
     """Eqs. (1)-(3) on a perturbed slab with a free surface, with Eq. (3) and with the Morse form.
     Tolerance: 1e-5 relative, plus an absolute floor of 1e-5 of the largest force for atoms whose
@@ -255,7 +255,7 @@ def test_electric_gather_reproduces_linear_fields():
 
 
 @pytest.mark.parametrize("pot", [{}, dict(pot_mode=1, c_att=0.65, s_rep=2.5), dict(pot_mode=2, morse_a=4.0),
-                                 dict(lattice=1)], ids=["lj", "altered", "morse", "hcp"])
+                                 dict(lattice=1), dict(pot_mode=3)], ids=["lj", "altered", "morse", "hcp", "eam"])
 def test_one_step_transport_mode(pot):
     """One transport step (pair force only) against the oracle, with Eq. (3) as printed, with
     the altered potential (attractive and repulsive branches scaled) and with the Morse form. The
@@ -285,7 +285,8 @@ def test_one_step_transport_mode(pot):
     assert np.array_equal(sim.get_density().cpu().numpy(), oracle.deposit_density(nx, nz, x1, z1))
 
 
-@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1)], ids=["lj", "morse", "hcp"])
+@pytest.mark.parametrize("pot", [{}, dict(pot_mode=2, morse_a=4.0), dict(lattice=1), dict(pot_mode=3)],
+                         ids=["lj", "morse", "hcp", "eam"])
 def test_energy_matches_oracle(pot):
     nx, nz, sk = 48, 40, 20
     w = workload("tiny", nx=nx, nz=nz, slab_k=sk, max_particles=nx * sk * 8, **pot)
@@ -468,8 +469,9 @@ def test_transport_1000_steps_energy_drift_and_profile():
     assert np.linalg.norm(pg - po) / np.linalg.norm(po) < 1e-3
 
 
-@pytest.mark.parametrize("pot,curv", [({}, 72.0), (dict(pot_mode=2, morse_a=4.0), 32.0), (dict(lattice=1), 144.0)],
-                         ids=["lj", "morse", "hcp"])
+@pytest.mark.parametrize("pot,curv", [({}, 72.0), (dict(pot_mode=2, morse_a=4.0), 32.0), (dict(lattice=1), 144.0),
+                                      (dict(pot_mode=3), 5.09 ** 2 * (3.54 / 0.41) / 3.0)],
+                         ids=["lj", "morse", "hcp", "eam"])
 def test_transport_acoustic_wave_period(pot, curv):
     """The GPU transport stage carries a small standing acoustic wave (64-cell wavelength, strain
     1e-3) with the period of the linearised Eqs. (1)-(3), lambda / sqrt(U''(r0) r0^2 / (3 m)),

@@ -929,8 +929,9 @@ def test_injected_energy_of_a_plane_wave_pulse():
     assert e["field_E"] + e["field_B"] <= e["injected"] * 1.01
 
 
-@pytest.mark.parametrize("pot,curv", [({}, 72.0), ({"pot_mode": 2, "morse_a": 4.0}, 32.0), ({"lattice": 1}, 144.0)],
-                         ids=["lj", "morse", "hcp"])
+@pytest.mark.parametrize("pot,curv", [({}, 72.0), ({"pot_mode": 2, "morse_a": 4.0}, 32.0), ({"lattice": 1}, 144.0),
+                                      ({"pot_mode": 3}, 5.09 ** 2 * (3.54 / 0.41) / 3.0)],
+                         ids=["lj", "morse", "hcp", "eam"])
 def test_acoustic_wave_speed_of_the_pair_force(pot, curv):
     """Linearising Eqs. (1)-(3) about the equilibrium lattice (n = n0, rbar = r0) gives the wave
     equation u_tt = (U''(r0) r0^2 / (3 m)) u_xx for a small longitudinal displacement u, with
@@ -938,7 +939,8 @@ def test_acoustic_wave_speed_of_the_pair_force(pot, curv):
     a standing wave of wavelength 64 cells in the transport mode oscillates with period
     lambda / sqrt(U''(r0) r0^2 / (3 m)) and keeps its amplitude. The HCP lattice doubles the
     restoring force (second moment of its neighbour directions 4 I against 2 I): an effective
-    144 D, period shorter by sqrt(2)."""
+    144 D, period shorter by sqrt(2). The embedded-atom form's first-order force (1/3) E''(r0) r0 g
+    (E the binding curve, E'' = alpha^2 E_c) acts like U''(r0) r0^2 = alpha^2 E_c / 3."""
     nx, nz = 64, 4
     dt = 50e-15
     w = workload("transport", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, T_ion_K=0.0, dt_override=dt, **pot)

@@ -101,7 +101,8 @@ def test_noalloc_energy_refuses_unknown_potentials(gb):
     view, keep = _view(gb, sim)
     out = torch.empty(5, dtype=torch.float64, device="cuda")
     lib = gb.load_library()
-    for bad in (dict(pot_mode=3), dict(pot_mode=-1), dict(pot_mode=2, morse_a=0.0), dict(lattice=2)):
+    for bad in (dict(pot_mode=4), dict(pot_mode=-1), dict(pot_mode=2, morse_a=0.0), dict(lattice=2),
+                dict(pot_mode=3, lattice=1), dict(pot_mode=3, eam_beta=0.0)):
         cfg = gb.make_config(w, **bad)
         assert lib.pic_energy_noalloc(ctypes.byref(cfg), ctypes.byref(view), out.data_ptr(), None) == gb.PIC_EINVAL
     torch.cuda.synchronize()
