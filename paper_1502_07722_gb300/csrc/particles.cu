@@ -61,6 +61,23 @@ struct Window {
     int ox, oz, W;
 };
 
+// bilinear sum of the corners (c00, c10, c01, c11) of a stagger pair, both components at once
+__device__ __forceinline__ float2 bilerp2(float2 c00, float2 c10, float2 c01, float2 c11, float2 gx, float2 wx,
+                                          float2 gz, float2 wz)
+{
+    const float2 b0 = __ffma2_rn(wx, c10, __fmul2_rn(gx, c00));
+    const float2 b1 = __ffma2_rn(wx, c11, __fmul2_rn(gx, c01));
+    return __ffma2_rn(wz, b1, __fmul2_rn(gz, b0));
+}
+
+__device__ __forceinline__ float bilerp1(float c00, float c10, float c01, float c11, float gx, float wx, float gz,
+                                         float wz)
+{
+    const float b0 = __fmaf_rn(wx, c10, __fmul_rn(gx, c00));
+    const float b1 = __fmaf_rn(wx, c11, __fmul_rn(gx, c01));
+    return __fmaf_rn(wz, b1, __fmul_rn(gz, b0));
+}
+
 __device__ __forceinline__ void red64g(u64* p, long long v)
 {
     if (v != 0) atomicAdd(p, (u64)v);
@@ -182,31 +199,39 @@ __device__ __forceinline__ void process_particle(const StepArgs& a, const Specie
             const int ox_ = ux_ ? 0 : -1, oz_ = uz_ ? 0 : -W;
             const float hx = ux_ ? fx - 0.5f : fx + 0.5f, hz = uz_ ? fz - 0.5f : fz + 0.5f;
             const float ghx = 1.0f - hx, ghz = 1.0f - hz;
+            // the two components of a stagger pair share their weights: one packed FP32x2 bilinear
+            // sum interpolates both. Every operation here is an explicit intrinsic (no contraction
+            // left to the compiler), so the single and the batched kernel round alike.
+            const float2 gx2 = make_float2(gx, gx), fx2 = make_float2(fx, fx);
+            const float2 gz2 = make_float2(gz, gz), fz2 = make_float2(fz, fz);
             {
                 const float2* q = w.eyn + base;
                 const float2 c00 = q[0], c10 = q[1], c01 = q[W], c11 = q[W + 1];
-                ky = S.e_kick * (gz * (gx * c00.x + fx * c10.x) + fz * (gx * c01.x + fx * c11.x));
                 if (kPair) {
-                    n = gz * (gx * c00.y + fx * c10.y) + fz * (gx * c01.y + fx * c11.y);
-                    dnx = gz * (c10.y - c00.y) + fz * (c11.y - c01.y);
-                    dnz = gx * (c01.y - c00.y) + fx * (c11.y - c10.y);
+                    const float2 r = bilerp2(c00, c10, c01, c11, gx2, fx2, gz2, fz2);
+                    ky = __fmul_rn(S.e_kick, r.x);
+                    n = r.y;
+                    dnx = __fmaf_rn(fz, __fsub_rn(c11.y, c01.y), __fmul_rn(gz, __fsub_rn(c10.y, c00.y)));
+                    dnz = __fmaf_rn(fx, __fsub_rn(c11.y, c10.y), __fmul_rn(gx, __fsub_rn(c01.y, c00.y)));
+                } else {
+                    ky = __fmul_rn(S.e_kick, bilerp1(c00.x, c10.x, c01.x, c11.x, gx, fx, gz, fz));
                 }
             }
             {
                 const float2* q = w.exbz + base + ox_;
-                const float2 c00 = q[0], c10 = q[1], c01 = q[W], c11 = q[W + 1];
-                kx = S.e_kick * (gz * (ghx * c00.x + hx * c10.x) + fz * (ghx * c01.x + hx * c11.x));
-                bz = gz * (ghx * c00.y + hx * c10.y) + fz * (ghx * c01.y + hx * c11.y);
+                const float2 r = bilerp2(q[0], q[1], q[W], q[W + 1], make_float2(ghx, ghx), make_float2(hx, hx), gz2, fz2);
+                kx = __fmul_rn(S.e_kick, r.x);
+                bz = r.y;
             }
             {
                 const float2* q = w.ezbx + base + oz_;
-                const float2 c00 = q[0], c10 = q[1], c01 = q[W], c11 = q[W + 1];
-                kz = S.e_kick * (ghz * (gx * c00.x + fx * c10.x) + hz * (gx * c01.x + fx * c11.x));
-                bx = ghz * (gx * c00.y + fx * c10.y) + hz * (gx * c01.y + fx * c11.y);
+                const float2 r = bilerp2(q[0], q[1], q[W], q[W + 1], gx2, fx2, make_float2(ghz, ghz), make_float2(hz, hz));
+                kz = __fmul_rn(S.e_kick, r.x);
+                bx = r.y;
             }
             {
                 const float* q = w.by + base + ox_ + oz_;
-                by = ghz * (ghx * q[0] + hx * q[1]) + hz * (ghx * q[W] + hx * q[W + 1]);
+                by = bilerp1(q[0], q[1], q[W], q[W + 1], ghx, hx, ghz, hz);
             }
         } else if (kPair) {
             const float* q = w.nh + base;
