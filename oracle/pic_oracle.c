@@ -257,8 +257,11 @@ static void lattice_pair(int lattice, int pm, double ca, double sr, double ma, d
 /* six Eq. (2) neighbours (+-y at rbar in 2D); neighbour j's own embedding density is          */
 /* 6 f(rbar_j) with rbar_j = n_j^(-1/3) and n_j the interpolated density at j's position, taken */
 /* along the axis from the atom's density and its gradient (n + s dn, s the neighbour's offset */
-/* in cells); the bond to j pulls with T = phi'(r) + (F'(rho_i) + F'(rho_j)) f'(r), and the   */
-/* force along an axis is T(r+) - T(r-), as U'(r+) - U'(r-) for a pair potential.             */
+/* in cells), but never less than f(r), the density of its own bond back to the atom (any     */
+/* neighbour holds that bond; in a steep gradient, as at a free surface, n_j can fall towards  */
+/* zero, where F'(rho) diverges like rho^(alpha/beta - 1) ln rho); the bond to j pulls with    */
+/* T = phi'(r) + (F'(rho_i) + F'(rho_j)) f'(r), and the force along an axis is T(r+) - T(r-),  */
+/* as U'(r+) - U'(r-) for a pair potential.                                                    */
 /* ---------------------------------------------------------------------------------------- */
 typedef struct {
     double ec, phi, alpha, beta, gamma;      /* ec, phi in units of D */
@@ -306,7 +309,9 @@ static void eam_atom(const eam_p* p, double n, const double grad[3], int three_d
             double r = side == 0 ? rp[d] : rm[d];
             if (isinf(r)) continue;
             double nj = n + (side == 0 ? 1.0 : -1.0) * r * r0_dx * grad[d];
-            double dFj = nj > 0.0 ? eam_dF(p, 6.0 * eam_f(p, pow(nj, -1.0 / 3.0))) : 0.0;
+            double rhoj = nj > 0.0 ? 6.0 * eam_f(p, pow(nj, -1.0 / 3.0)) : 0.0;
+            if (rhoj < eam_f(p, r)) rhoj = eam_f(p, r);     /* at least the bond back to the atom */
+            double dFj = eam_dF(p, rhoj);
             T[side] = eam_dphi(p, r) + (dFi + dFj) * eam_df(p, r);
         }
         F[d] = T[0] - T[1];

@@ -284,8 +284,9 @@ constexpr float kHcpS = 0.816496580927726f;    // sqrt(2/3)
 // readily adapted to its mapping of density to neighbour distance). Atom i's embedding density is
 // the sum of f over its six Eq. (2) neighbours; neighbour j's own is 6 f(n_j^(-1/3)), n_j the
 // interpolated density at j's position taken along the axis, n + s dn (s = the neighbour's offset
-// in cells: its distance in r0 times r0 / dx = 6 h_coef); each bond pulls with
-// T = phi'(r) + (F'(rho_i) + F'(rho_j)) f'(r) and the force along an axis is T(r+) - T(r-).
+// in cells: its distance in r0 times r0 / dx = 6 h_coef), but never less than f(r), the density of
+// its bond back to the atom; each bond pulls with T = phi'(r) + (F'(rho_i) + F'(rho_j)) f'(r) and
+// the force along an axis is T(r+) - T(r-).
 __device__ __forceinline__ float eam_f(const EamP& e, float r) { return expf(-e.beta * (r - 1.0f)); }
 __device__ __forceinline__ float eam_phi(const EamP& e, float r) { return e.phi * expf(-e.gamma * (r - 1.0f)); }
 // dF / d rho
@@ -327,7 +328,8 @@ __device__ __forceinline__ float eam_dF_rb_diff(const EamP& e, float rbm, float 
 // that halve pair energies get twice it) of an atom at density n (c = n^(1/3), inv43 = n^(-4/3))
 // with gradient g per cell. NAX axes carry Eq. (2) neighbours (2: x and z, g[1] unused, the +-y
 // neighbours at rbar with their own density n; 3: x, y, z). With both neighbours of an axis
-// finite and inside the slab, T(r+) - T(r-) is formed without cancellation:
+// finite, inside the slab and with their own densities above their bonds' (the floor inactive),
+// T(r+) - T(r-) is formed without cancellation:
 //   -gamma [phi(r+) - phi(r-)] - beta F'_i [f(r+) - f(r-)] - beta [(F'_+ - F'_-) f(r+) + F'_- (f(r+) - f(r-))],
 //   phi(r+) - phi(r-) = phi(r-) expm1(-gamma dr), f(r+) - f(r-) = f(r-) expm1(-beta dr),
 //   dr = r+ - r- = 2h / (c (1 - h^2)), and F'_+ - F'_- from the neighbours' spacings, whose
@@ -354,34 +356,40 @@ __device__ __forceinline__ void eam_forces(const EamP& e, float n, float c, floa
         if (rp[d] > 0.0f) { rho += eam_f(e, rp[d]); up += eam_phi(e, rp[d]); }
         if (rm[d] > 0.0f) { rho += eam_f(e, rm[d]); up += eam_phi(e, rm[d]); }
     }
-    const float dFi = eam_dF(e, rho), s = 6.0f * h_coef;
+    const float dFi = eam_dF(e, rho), s = 6.0f * h_coef, ln6b = 1.791759469f / e.beta;
 #pragma unroll
     for (int d = 0; d < nax; d++) {
         F[d] = 0.0f;
         if (NAX == 2 && d == 1) continue;
         const float npl = n + rp[d] * s * g[d], nmi = n - rm[d] * s * g[d];
         if (rp[d] > 0.0f && rm[d] > 0.0f && npl > 0.0f && nmi > 0.0f) {
-            const float h = hh[d];
-            const float dr = 2.0f * h / (c * (1.0f - h * h));
             const float cp = fast_cbrt(npl), cm = fast_cbrt(nmi);
-            const float rbm = 1.0f / cm;
-            // rb+ - rb- = (cm - cp) / (cp cm), cp - cm = (n+ - n-) / (cp^2 + cp cm + cm^2)
-            const float dn = (rp[d] + rm[d]) * s * g[d];
-            const float dl = -dn / ((cp * cp + cp * cm + cm * cm) * cp * cm);
-            const float fm = eam_f(e, rm[d]), fp = eam_f(e, rp[d]), df = fm * expm1f(-e.beta * dr);
-            const float dFm = eam_dF_rb(e, rbm);
-            F[d] = -e.gamma * eam_phi(e, rm[d]) * expm1f(-e.gamma * dr) - e.beta * dFi * df -
-                   e.beta * (eam_dF_rb_diff(e, rbm, dl) * fp + dFm * df);
-            continue;
+            // both neighbours' own densities 6 f(rb) above their bonds' f(r) (rb <= r + ln 6 / beta):
+            // the floor below is inactive
+            if (cp * (rp[d] + ln6b) >= 1.0f && cm * (rm[d] + ln6b) >= 1.0f) {
+                const float h = hh[d];
+                const float dr = 2.0f * h / (c * (1.0f - h * h));
+                const float rbm = 1.0f / cm;
+                // rb+ - rb- = (cm - cp) / (cp cm), cp - cm = (n+ - n-) / (cp^2 + cp cm + cm^2)
+                const float dn = (rp[d] + rm[d]) * s * g[d];
+                const float dl = -dn / ((cp * cp + cp * cm + cm * cm) * cp * cm);
+                const float fm = eam_f(e, rm[d]), fp = eam_f(e, rp[d]), df = fm * expm1f(-e.beta * dr);
+                const float dFm = eam_dF_rb(e, rbm);
+                F[d] = -e.gamma * eam_phi(e, rm[d]) * expm1f(-e.gamma * dr) - e.beta * dFi * df -
+                       e.beta * (eam_dF_rb_diff(e, rbm, dl) * fp + dFm * df);
+                continue;
+            }
         }
         float T[2] = {0.0f, 0.0f};
 #pragma unroll
         for (int side = 0; side < 2; side++) {
             const float r = side == 0 ? rp[d] : rm[d];
             if (!(r > 0.0f)) continue;
-            const float nj = side == 0 ? npl : nmi;
-            const float dFj = nj > 0.0f ? eam_dF(e, 6.0f * eam_f(e, 1.0f / fast_cbrt(nj))) : 0.0f;
-            T[side] = -e.gamma * eam_phi(e, r) - e.beta * (dFi + dFj) * eam_f(e, r);
+            const float nj = side == 0 ? npl : nmi, fr = eam_f(e, r);
+            // the neighbour holds at least its bond back to the atom: rho_j >= f(r) (a neighbour
+            // density from n_j alone diverges F' as n_j -> 0 at a free surface)
+            const float rhoj = fmaxf(nj > 0.0f ? 6.0f * eam_f(e, 1.0f / fast_cbrt(nj)) : 0.0f, fr);
+            T[side] = -e.gamma * eam_phi(e, r) - e.beta * (dFi + eam_dF(e, rhoj)) * fr;
         }
         F[d] = T[0] - T[1];
     }

@@ -124,6 +124,45 @@ def test_pair_force_matches_oracle(pot):
     assert not Fg[:, 1].any()
 
 
+def test_eam_force_in_vapour_above_the_surface_matches_oracle():
+    """The embedded-atom form with vapour above a dense slab (128 atoms per cell): clusters of 12
+    atoms, each with a lone atom at the edge of the cluster's support. The lone atom's -x neighbour
+    sits where the interpolated density has nearly vanished, so its embedding density is held at its
+    bond's f(r) (the floor branch of the kernel; the floor moves these forces by ~0.6 %). All atoms
+    at the pair-force tolerance, the lone atoms' x force at 1e-4 of its own size."""
+    nx, nz, ppc, sk = 32, 40, 128, 6
+    w = workload("tiny", nx=nx, nz=nz, slab_k=sk, ppc_ion=ppc, ppc_electron=ppc, max_particles=40000, pot_mode=3)
+    sim = gb().Simulation(w)
+    orc = oracle.Oracle(w, with_particles=False)
+    d = inputs.slab_particles(23, nx, nz, sk, ppc, 1e-4, clump=0.25)
+    rng = np.random.default_rng(24)
+    ns = 12
+    ci, ck = rng.integers(0, nx - 3, ns), rng.integers(10, 36, ns)
+    cx = np.repeat(ci, 12) + 1.5 + rng.uniform(-0.05, 0.05, 12 * ns)
+    cz = np.repeat(ck, 12) + 0.5 + rng.uniform(-0.05, 0.05, 12 * ns)
+    lx, lz = ci + rng.uniform(0.01, 0.05, ns), ck + rng.uniform(0.4, 0.6, ns)
+    nv = 13 * ns
+    vx = np.concatenate([cx, lx]).astype(np.float32).astype(np.float64)
+    vz = np.concatenate([cz, lz]).astype(np.float32).astype(np.float64)
+    d = {k: np.concatenate([d[k], v]) for k, v in
+         dict(x=vx, z=vz, ux=np.zeros(nv), uy=np.zeros(nv), uz=np.zeros(nv)).items()}
+    g = set_both(sim, orc, 0, d)
+    Fg = sim.pair_force().cpu().numpy().astype(np.float64)
+    Fo = orc.pair_force()
+    assert np.isfinite(Fo).all()
+    scale = np.abs(Fo).max()
+    err = np.abs(Fg - Fo)
+    assert (err <= 1e-5 * np.abs(Fo) + 1e-5 * scale).all(), err.max() / scale
+    # the lone atoms, found in the context's order by their positions
+    x, z, _ = to_global(g, nx)
+    lone = np.zeros(len(x), bool)
+    for a, b in zip(lx, lz):
+        lone |= (np.abs(x - np.float32(a)) < 1e-6) & (np.abs(z - np.float32(b)) < 1e-6)
+    assert lone.sum() == ns
+    assert (err[lone, 0] <= 1e-4 * np.abs(Fo[lone, 0])).all(), (err[lone, 0] / np.abs(Fo[lone, 0])).max()
+    sim.close()
+
+
 def test_uniform_lattice_zero_force_on_gpu():
     nx, nz = 32, 16
     w = workload("tiny", nx=nx, nz=nz, slab_k=nz, ppc_ion=4, ppc_electron=4, max_particles=4096)

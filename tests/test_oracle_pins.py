@@ -847,6 +847,24 @@ def test_eam_first_order_force_is_the_binding_curve_stiffness(n):
             assert Fx < 0.0
 
 
+def test_eam_force_stays_bounded_where_a_neighbour_sits_in_vacuum():
+    """At a free surface the gradient can put a neighbour's interpolated density n + s dn at or
+    below zero. Every neighbour holds at least its bond back to the atom, so its embedding density
+    never falls below f(r): the force stays finite and continuous as n_j passes through zero, and
+    grows steadily with the gradient. (F'(rho) diverges like rho^(alpha/beta - 1) ln rho as rho -> 0;
+    a neighbour density taken from n_j alone feeds that divergence into the bond tension, a spike of
+    millions of D / r0 at the crossing.)"""
+    w = workload("transport", pot_mode=3)
+    r0_dx = w["n_atoms"] ** (-1 / 3) / w["dx"]
+    n = 0.5
+    dns = np.linspace(0.0, 80.0, 8001)        # the -x neighbour's n_j crosses zero near dn = 15
+    F = np.array([oracle.eam_atom2(w, n, dn, 0.0, r0_dx)[0] for dn in dns])
+    assert np.isfinite(F).all()
+    big = np.abs(F).max()
+    assert np.argmax(np.abs(F)) == len(F) - 1
+    assert np.abs(np.diff(F)).max() < 1e-3 * big
+
+
 def test_eam_equilibrium_slab_energy_and_zero_force():
     """A uniform slab at the equilibrium density (the wall rows mirrored) under the embedded-atom
     form: pair energy -E_c per atom and exactly zero force."""
