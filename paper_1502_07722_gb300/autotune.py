@@ -12,8 +12,8 @@ import json
 import os
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), ".autotune_cache.json")
-TILES = (8, 12, 16)
-SORTS = (20, 40, 80)
+TILES = (12, 16, 20)
+SORTS = (40, 80, 160)
 
 
 def _signature(phys_list) -> str:

@@ -40,6 +40,12 @@ namespace gbpic {
 constexpr int kMargin = 2;              // cells a particle may drift out of its tile between sorts
 constexpr int kBlock = 128;                // threads per CTA (8 CTAs per SM)
 constexpr int kCtasPerSm = 8;
+// The batched kernel reads each slab's arguments from a constant-memory table with a run-time
+// index: every use is an indexed constant load into a register, so it needs more registers than
+// the single kernel for the same code. At 64 registers it spilled ~100 bytes per thread; at 72
+// (7 CTAs per SM) the particle launch of the 16-slab sweep takes 2.03 ms against 2.39 (6 CTAs
+// at 80 registers: 2.23).
+constexpr int kCtasPerSmBatch = 7;
 
 
 __device__ __forceinline__ int wrap_any(int i, int nx)
@@ -499,7 +505,7 @@ __constant__ int c_tile_base[kMaxBatchSlabs + 1];
 // All simulations of a batch in one persistent launch: the tiles of every simulation form one
 // work list (c_tile_base[s] = first global tile of simulation s).
 template <bool FULL, int POT>
-__global__ void __launch_bounds__(kBlock, kCtasPerSm) k_particles_batch(int nslab, int total, int nsub)
+__global__ void __launch_bounds__(kBlock, kCtasPerSmBatch) k_particles_batch(int nslab, int total, int nsub)
 {
     // one ticket counter for the whole batch: the first simulation's
     __shared__ int slot;
@@ -580,7 +586,7 @@ void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_d
 #undef GBPIC_ATTR
         configured[dev].store(shmem);
     }
-    const int cap = nsm * kCtasPerSm;
+    const int cap = nsm * kCtasPerSmBatch;
     const int nsub = parts_per_tile(total_tiles, cap);
     int grid = total_tiles * nsub < cap ? total_tiles * nsub : cap;
     if (grid < 1) grid = 1;
