@@ -19,6 +19,7 @@ void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* laun
 int max_batch_slabs();
 
 constexpr int kMaxSlabs = 48;    // the constant-memory argument table of the batched particle kernel
+static_assert(kMaxSlabs <= kMaxFieldSlabs, "every slab's field arguments fit the batched field kernels' parameters");
 
 __global__ void k_prepare_batch(const StepArgs* __restrict__ args)
 {
@@ -44,7 +45,7 @@ struct pic_batch {
     size_t max_nn;
     int64_t step;
     StepArgs* args_dev;          // [2][n]: parity 0 (density in buffer 0) and parity 1
-    FieldArgs* fargs_dev;        // [n]
+    FieldBatch fields;           // every slab's field arguments (host copy, passed by value)
     AntennaParams* ap_dev;       // [n]
     long long* step_dev;         // [n]
     float* ant_dev;              // [n][2]
@@ -64,8 +65,8 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t batch_tail_bytes(int n)
 {
-    return a256(sizeof(StepArgs) * 2 * n) + a256(sizeof(FieldArgs) * n) + a256(sizeof(AntennaParams) * n) +
-           a256(8 * (size_t)n) + a256(8 * (size_t)n) + a256(4 * ((size_t)n + 1));
+    return a256(sizeof(StepArgs) * 2 * n) + a256(sizeof(AntennaParams) * n) + a256(8 * (size_t)n) +
+           a256(8 * (size_t)n) + a256(4 * ((size_t)n + 1));
 }
 
 int upload_args(pic_batch* b)
@@ -95,7 +96,7 @@ void enqueue_step(pic_batch* b, int parity)
     launch_particle_step_batch(args, b->tile_base_dev, b->n, b->total_tiles, b->full, b->pot, b->maxW, b->nsm, b->st);
     if (b->timing) cudaEventRecord(b->ev[1], b->st);
     if (b->full)
-        launch_fields_batch(b->fargs_dev, b->ap_dev, b->step_dev, b->ant_dev, b->n, b->max_nx, b->max_nz, b->st);
+        launch_fields_batch(b->fields, b->ap_dev, b->step_dev, b->ant_dev, b->st);
     if (b->timing) cudaEventRecord(b->ev[2], b->st);
 }
 
@@ -175,8 +176,6 @@ int pic_batch_init(const pic_config* cfgs, int32_t n, void* workspace, size_t by
     b->sort_every = cfgs[0].sort_every;
     b->args_dev = reinterpret_cast<StepArgs*>(p);
     p += a256(sizeof(StepArgs) * 2 * n);
-    b->fargs_dev = reinterpret_cast<FieldArgs*>(p);
-    p += a256(sizeof(FieldArgs) * n);
     b->ap_dev = reinterpret_cast<AntennaParams*>(p);
     p += a256(sizeof(AntennaParams) * n);
     b->step_dev = reinterpret_cast<long long*>(p);
@@ -184,16 +183,15 @@ int pic_batch_init(const pic_config* cfgs, int32_t n, void* workspace, size_t by
     b->ant_dev = reinterpret_cast<float*>(p);
     p += a256(8 * (size_t)n);
     b->tile_base_dev = reinterpret_cast<int*>(p);
-    std::vector<FieldArgs> fa(n);
     std::vector<AntennaParams> ap(n);
+    b->fields.n = n;
     for (int s = 0; s < n; s++) {
-        fa[s] = make_field_args(b->slab[s]->c);
-        fa[s].ant = b->ant_dev + 2 * s;     // the batch's per-slab antenna scalars
+        b->fields.f[s] = make_field_args(b->slab[s]->c);
+        b->fields.f[s].ant = b->ant_dev + 2 * s;     // the batch's per-slab antenna scalars
         ap[s] = make_antenna_params(b->slab[s]->c);
     }
-    bool ok = cudaMemcpyAsync(b->fargs_dev, fa.data(), sizeof(FieldArgs) * n, cudaMemcpyHostToDevice, b->st) ==
-                  cudaSuccess &&
-              cudaMemcpyAsync(b->ap_dev, ap.data(), sizeof(AntennaParams) * n, cudaMemcpyHostToDevice, b->st) ==
+    field_row_blocks(b->fields);
+    bool ok = cudaMemcpyAsync(b->ap_dev, ap.data(), sizeof(AntennaParams) * n, cudaMemcpyHostToDevice, b->st) ==
                   cudaSuccess &&
               cudaMemcpyAsync(b->tile_base_dev, tile_base.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice,
                               b->st) == cudaSuccess &&

@@ -141,20 +141,41 @@ __global__ void k_E(const FieldArgs f)
     add_flux(f, blockIdx.y, s);
 }
 
-__global__ void k_half_B_batch(const FieldArgs* __restrict__ fa, int save)
+// Batched field kernels: blockIdx.x runs over every slab's (row, 256-node segment) blocks, slab s
+// owning blocks rb[s] .. rb[s + 1] - 1. Every slab's arguments travel in the launch's parameter
+// block (a grid over the largest slab's rows for every slab, reading the arguments from global
+// memory, took 0.27 ms per step of the 16-slab sweep).
+__device__ __forceinline__ int batch_slab(const FieldBatch& P, int g)
 {
-    const FieldArgs& f = fa[blockIdx.z];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < f.nx && (int)blockIdx.y <= f.nz) half_B_node(f, i, blockIdx.y, save);
+    int s = 0;
+    while (s + 1 < P.n && P.rb[s + 1] <= g) s++;
+    return s;
 }
 
-__global__ void k_E_batch(const FieldArgs* __restrict__ fa)
+__global__ void k_half_B_batch(const __grid_constant__ FieldBatch P, int save)
 {
-    const FieldArgs& f = fa[blockIdx.z];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if ((int)blockIdx.y > f.nz) return;                  // uniform over the block
-    const float s = i < f.nx ? E_node(f, i, blockIdx.y) : 0.0f;
-    add_flux(f, blockIdx.y, s);
+    const int s = batch_slab(P, (int)blockIdx.x);
+    const FieldArgs& f = P.f[s];
+    const int local = (int)blockIdx.x - P.rb[s], nxb = (f.nx + 255) >> 8;
+    const int k = local / nxb, i = (local - k * nxb) * 256 + (int)threadIdx.x;
+    if (i < f.nx) half_B_node(f, i, k, save);
+}
+
+__global__ void k_E_batch(const __grid_constant__ FieldBatch P)
+{
+    const int s = batch_slab(P, (int)blockIdx.x);
+    const FieldArgs& f = P.f[s];
+    const int local = (int)blockIdx.x - P.rb[s], nxb = (f.nx + 255) >> 8;
+    const int k = local / nxb, i = (local - k * nxb) * 256 + (int)threadIdx.x;   // k uniform over the block
+    const float v = i < f.nx ? E_node(f, i, k) : 0.0f;
+    add_flux(f, k, v);
+}
+
+// each slab's first block (rb[n] = the total)
+void field_row_blocks(FieldBatch& P)
+{
+    P.rb[0] = 0;
+    for (int s = 0; s < P.n; s++) P.rb[s + 1] = P.rb[s] + (P.f[s].nz + 1) * ((P.f[s].nx + 255) / 256);
 }
 
 AntennaParams make_antenna_params(const Ctx& c)
@@ -204,16 +225,15 @@ void launch_fields(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches)
     if (launches) *launches += 4;
 }
 
-void launch_fields_batch(const FieldArgs* fa_dev, const AntennaParams* ap_dev, long long* step_dev, float* ant_dev,
-                         int nslab, int max_nx, int max_nz, cudaStream_t st)
+void launch_fields_batch(const FieldBatch& P, const AntennaParams* ap_dev, long long* step_dev, float* ant_dev,
+                         cudaStream_t st)
 {
-    k_antenna_batch<<<1, 32, 0, st>>>(ap_dev, step_dev, ant_dev, nslab);
-    dim3 block(256);
-    dim3 grid((max_nx + 255) / 256, max_nz + 1, nslab);
-    k_half_B_batch<<<grid, block, 0, st>>>(fa_dev, 1);
-    k_E_batch<<<grid, block, 0, st>>>(fa_dev);
-    k_half_B_batch<<<grid, block, 0, st>>>(fa_dev, 0);
-    k_step_done<<<1, 32, 0, st>>>(step_dev, nslab);
+    k_antenna_batch<<<1, 32, 0, st>>>(ap_dev, step_dev, ant_dev, P.n);
+    const int blocks = P.rb[P.n];
+    k_half_B_batch<<<blocks, 256, 0, st>>>(P, 1);
+    k_E_batch<<<blocks, 256, 0, st>>>(P);
+    k_half_B_batch<<<blocks, 256, 0, st>>>(P, 0);
+    k_step_done<<<1, 32, 0, st>>>(step_dev, P.n);
 }
 
 }  // namespace gbpic

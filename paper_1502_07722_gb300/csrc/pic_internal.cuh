@@ -207,8 +207,16 @@ void launch_pair_force(Ctx& c, float* out, cudaStream_t st);
 void launch_validate(Ctx& c, const SpeciesBuf& b, int64_t n, unsigned* bad, cudaStream_t st);
 void launch_particle_step(Ctx& c, const StepArgs& a, cudaStream_t st);
 void launch_fields(Ctx& c, cudaStream_t st, int64_t step, int64_t* launches);
-void launch_fields_batch(const FieldArgs* fa_dev, const AntennaParams* ap_dev, long long* step_dev, float* ant_dev,
-                         int nslab, int max_nx, int max_nz, cudaStream_t st);
+// the field arguments of every slab of a batch, passed in the kernels' parameter block
+constexpr int kMaxFieldSlabs = 48;
+struct FieldBatch {
+    FieldArgs f[kMaxFieldSlabs];
+    int rb[kMaxFieldSlabs + 1];      // first (row, 256-node segment) block of each slab
+    int n;
+};
+void launch_fields_batch(const FieldBatch& P, const AntennaParams* ap_dev, long long* step_dev, float* ant_dev,
+                         cudaStream_t st);
+void field_row_blocks(FieldBatch& P);
 FieldArgs make_field_args(const Ctx& c);
 AntennaParams make_antenna_params(const Ctx& c);
 void launch_particle_step_batch(const StepArgs* args_dev, const int* tile_base_dev, int nslab, int total_tiles,
