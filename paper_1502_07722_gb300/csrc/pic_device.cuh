@@ -51,17 +51,64 @@ __device__ __forceinline__ float branch(int pot_mode, float c_att, float s_rep, 
     return (pot_mode & 3) == 0 ? 1.0f : (inv > 1.0f ? s_rep : c_att);
 }
 
+// approximate transcendental helpers (hardware ex2 / lg2 / rcp, relative error ~1e-7)
+__device__ __forceinline__ float fast_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fast_lg2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fast_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// n^(1/3) for n > 0
+__device__ __forceinline__ float fast_cbrt(float n) { return fast_ex2(fast_lg2(n) * (1.0f / 3.0f)); }
+
+// e^x from the hardware base-2 exponential, ex2(x log2 e): relative error ~2^-22 plus the rounding
+// of x log2 e (~|x| 2^-24), below 3e-6 for the |x| < 40 the pair potentials take
+__device__ __forceinline__ float exp_hw(float x) { return fast_ex2(x * 1.44269504088896341f); }
+// ln x from the hardware base-2 logarithm (absolute error ~1e-7 for x near 1)
+__device__ __forceinline__ float log_hw(float x) { return fast_lg2(x) * 0.693147180559945309f; }
+// e^x - 1 without cancellation: for |x| < 1/2 its Taylor series to x^9 / 9! (the first omitted
+// term is below 3e-10 of the sum), else exp_hw(x) - 1 (at most e^(1/2) / (e^(1/2) - 1) ~ 2.5 times
+// the relative error of exp_hw)
+__device__ __forceinline__ float expm1_hw(float x)
+{
+    if (fabsf(x) < 0.5f) {
+        float p = 2.75573192e-6f;                // 1 / 9!
+        p = fmaf(p, x, 2.48015873e-5f);          // 1 / 8!
+        p = fmaf(p, x, 1.98412698e-4f);          // 1 / 7!
+        p = fmaf(p, x, 1.38888889e-3f);          // 1 / 6!
+        p = fmaf(p, x, 8.33333333e-3f);          // 1 / 5!
+        p = fmaf(p, x, 4.16666667e-2f);          // 1 / 4!
+        p = fmaf(p, x, 1.66666667e-1f);          // 1 / 3!
+        p = fmaf(p, x, 0.5f);
+        p = fmaf(p, x, 1.0f);
+        return x * p;
+    }
+    return exp_hw(x) - 1.0f;
+}
+
 // Morse potential (pot_mode 2; the paper's mapping of density to neighbour distance takes any pair
 // potential): U = E^2 - 2E, E = exp(-a (r - 1)), units D with r in r0; minimum -1 at r = 1 like
 // Eq. (3). The pair functions below take the stiffness a in their c_att argument.
 __device__ __forceinline__ float morse_U_inv(float inv, float a)
 {
-    const float e = expf(-a * (1.0f / inv - 1.0f));
+    const float e = exp_hw(-a * (1.0f / inv - 1.0f));
     return e * (e - 2.0f);
 }
 __device__ __forceinline__ float morse_dU_inv(float inv, float a)    // U'(r), units D / r0
 {
-    const float e = expf(-a * (1.0f / inv - 1.0f));
+    const float e = exp_hw(-a * (1.0f / inv - 1.0f));
     return 2.0f * a * e * (1.0f - e);
 }
 
@@ -76,9 +123,9 @@ __device__ __forceinline__ float morse_axis_inl(float c, float h, float a)
 {
     const float ip = c * (1.0f - h), im = c * (1.0f + h);
     if (ip > 0.0f && im > 0.0f) {
-        const float ep = expf(-a * (1.0f / ip - 1.0f)), em = expf(-a * (1.0f / im - 1.0f));
+        const float ep = exp_hw(-a * (1.0f / ip - 1.0f)), em = exp_hw(-a * (1.0f / im - 1.0f));
         const float dr = 2.0f * h / (c * (1.0f - h * h));
-        return 2.0f * a * em * expm1f(-a * dr) * (1.0f - ep - em);
+        return 2.0f * a * em * expm1_hw(-a * dr) * (1.0f - ep - em);
     }
     float f = 0.0f;
     if (ip > 0.0f) f += morse_dU_inv(ip, a);
@@ -233,28 +280,6 @@ __device__ __forceinline__ int jy_code(float ux, float uy, float uz, float scale
     return __float2int_rn(__fmul_rn(by, scale));
 }
 
-// approximate transcendental helpers (hardware ex2 / lg2 / rcp, relative error ~1e-7)
-__device__ __forceinline__ float fast_ex2(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float fast_lg2(float x)
-{
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float fast_rcp(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-// n^(1/3) for n > 0
-__device__ __forceinline__ float fast_cbrt(float n) { return fast_ex2(fast_lg2(n) * (1.0f / 3.0f)); }
-
 // Fixed-point offset Q(f) = rint(f 2^16) in [0, 2^16].
 __device__ __forceinline__ int qoff(float f) { return __float2int_rn(f * 65536.0f); }
 
@@ -287,20 +312,20 @@ constexpr float kHcpS = 0.816496580927726f;    // sqrt(2/3)
 // in cells: its distance in r0 times r0 / dx = 6 h_coef), but never less than f(r), the density of
 // its bond back to the atom; each bond pulls with T = phi'(r) + (F'(rho_i) + F'(rho_j)) f'(r) and
 // the force along an axis is T(r+) - T(r-).
-__device__ __forceinline__ float eam_f(const EamP& e, float r) { return expf(-e.beta * (r - 1.0f)); }
-__device__ __forceinline__ float eam_phi(const EamP& e, float r) { return e.phi * expf(-e.gamma * (r - 1.0f)); }
+__device__ __forceinline__ float eam_f(const EamP& e, float r) { return exp_hw(-e.beta * (r - 1.0f)); }
+__device__ __forceinline__ float eam_phi(const EamP& e, float r) { return e.phi * exp_hw(-e.gamma * (r - 1.0f)); }
 // dF / d rho
 __device__ __forceinline__ float eam_dF(const EamP& e, float rho)
 {
     if (!(rho > 0.0f)) return 0.0f;
-    const float lx = logf(rho * (1.0f / 6.0f)), k = e.alpha / e.beta, m = e.gamma / e.beta;
-    return (e.ec * k * k * lx * expf((k - 1.0f) * lx) - 3.0f * e.phi * m * expf((m - 1.0f) * lx)) * (1.0f / 6.0f);
+    const float lx = log_hw(rho * (1.0f / 6.0f)), k = e.alpha / e.beta, m = e.gamma / e.beta;
+    return (e.ec * k * k * lx * exp_hw((k - 1.0f) * lx) - 3.0f * e.phi * m * exp_hw((m - 1.0f) * lx)) * (1.0f / 6.0f);
 }
 __device__ __forceinline__ float eam_F(const EamP& e, float rho)
 {
     if (!(rho > 0.0f)) return 0.0f;
-    const float lx = logf(rho * (1.0f / 6.0f)), k = e.alpha / e.beta, m = e.gamma / e.beta;
-    return -e.ec * (1.0f - k * lx) * expf(k * lx) - 3.0f * e.phi * expf(m * lx);
+    const float lx = log_hw(rho * (1.0f / 6.0f)), k = e.alpha / e.beta, m = e.gamma / e.beta;
+    return -e.ec * (1.0f - k * lx) * exp_hw(k * lx) - 3.0f * e.phi * exp_hw(m * lx);
 }
 
 // F'(rho) of a neighbour whose own environment is uniform at spacing rb (rho = 6 f(rb)), as a
@@ -310,7 +335,7 @@ __device__ __forceinline__ float eam_dF_rb(const EamP& e, float rb)
 {
     const float k = e.alpha / e.beta, m = e.gamma / e.beta, t = rb - 1.0f;
     return -(1.0f / 6.0f) *
-           (e.ec * k * k * e.beta * t * expf(-(e.alpha - e.beta) * t) + 3.0f * e.phi * m * expf(-(e.gamma - e.beta) * t));
+           (e.ec * k * k * e.beta * t * exp_hw(-(e.alpha - e.beta) * t) + 3.0f * e.phi * m * exp_hw(-(e.gamma - e.beta) * t));
 }
 
 // F'(rb+) - F'(rb-) from rb- and dl = rb+ - rb- without cancellation (expm1 of the exponents'
@@ -319,9 +344,9 @@ __device__ __forceinline__ float eam_dF_rb_diff(const EamP& e, float rbm, float 
 {
     const float k = e.alpha / e.beta, m = e.gamma / e.beta, t = rbm - 1.0f;
     const float a = e.alpha - e.beta, b = e.gamma - e.beta;
-    const float ea = expf(-a * t), eb = expf(-b * t);
-    const float d1 = t * expm1f(-a * dl) + dl * expf(-a * dl);        // (t + dl) e^(-a dl) - t
-    return -(1.0f / 6.0f) * (e.ec * k * k * e.beta * ea * d1 + 3.0f * e.phi * m * eb * expm1f(-b * dl));
+    const float ea = exp_hw(-a * t), eb = exp_hw(-b * t);
+    const float d1 = t * expm1_hw(-a * dl) + dl * exp_hw(-a * dl);        // (t + dl) e^(-a dl) - t
+    return -(1.0f / 6.0f) * (e.ec * k * k * e.beta * ea * d1 + 3.0f * e.phi * m * eb * expm1_hw(-b * dl));
 }
 
 // Force (units D / r0) along the axes and energy (units D, the atom's full share: the callers
@@ -373,9 +398,9 @@ __device__ __forceinline__ void eam_forces(const EamP& e, float n, float c, floa
                 // rb+ - rb- = (cm - cp) / (cp cm), cp - cm = (n+ - n-) / (cp^2 + cp cm + cm^2)
                 const float dn = (rp[d] + rm[d]) * s * g[d];
                 const float dl = -dn / ((cp * cp + cp * cm + cm * cm) * cp * cm);
-                const float fm = eam_f(e, rm[d]), fp = eam_f(e, rp[d]), df = fm * expm1f(-e.beta * dr);
+                const float fm = eam_f(e, rm[d]), fp = eam_f(e, rp[d]), df = fm * expm1_hw(-e.beta * dr);
                 const float dFm = eam_dF_rb(e, rbm);
-                F[d] = -e.gamma * eam_phi(e, rm[d]) * expm1f(-e.gamma * dr) - e.beta * dFi * df -
+                F[d] = -e.gamma * eam_phi(e, rm[d]) * expm1_hw(-e.gamma * dr) - e.beta * dFi * df -
                        e.beta * (eam_dF_rb_diff(e, rbm, dl) * fp + dFm * df);
                 continue;
             }
