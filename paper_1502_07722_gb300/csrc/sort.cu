@@ -19,9 +19,30 @@ namespace gbpic {
 constexpr int kScanBlock = 1024;
 constexpr int kScanItems = 2 * kScanBlock;
 
+// Division by a run-time divisor d >= 1 for 0 <= x < 2^31: q = umulhi(x, m) with m = floor((2^32 - 1) / d)
+// is at most one short of x / d (x m / 2^32 > x / d - x (1 + 1/d) / 2^32 > x / d - 1), so one
+// correction makes it exact.
+struct Div {
+    int d;
+    unsigned m;
+};
+inline Div make_div(int d) { return Div{d, (unsigned)(4294967295ULL / (unsigned long long)d)}; }
+__device__ __forceinline__ int divq(int x, Div D, int& r)
+{
+    unsigned q = __umulhi((unsigned)x, D.m);
+    int rr = x - (int)q * D.d;
+    if (rr >= D.d) {
+        q++;
+        rr -= D.d;
+    }
+    r = rr;
+    return (int)q;
+}
+
 struct KeyGeo {
     int nx, ny, T, ntx, nty, dims;
     int TT;     // cells per tile
+    Div dnx, dny, dT, dTT;
 };
 
 constexpr int kLayoutBlock2 = 1024, kLayoutBlock3 = 256;
@@ -30,9 +51,15 @@ constexpr int kLayoutBlock2 = 1024, kLayoutBlock3 = 256;
 // particles in the tile): block ci / B, and inside a block of nb particles the element (row
 // j / C, column j mod C) of a row-major matrix with C = ceil(nb / 32) columns, stored column-major
 // (the last row may be short, so column c holds R + (c < rem) elements). A bijection of 0..nt-1.
-__device__ __forceinline__ int layout_slot(int ci, int nt, int B)
+template <int B>
+__device__ __forceinline__ int layout_slot(int ci, int nt)
 {
     const int blk = ci / B, j = ci - blk * B, nb = min(B, nt - blk * B);
+    if (nb == B) {
+        // a full block: B / 32 columns of 32 (shifts)
+        constexpr int C = B / 32;
+        return blk * B + (j % C) * 32 + j / C;
+    }
     const int C = (nb + 31) >> 5, R = nb / C, rem = nb - R * C;
     const int r = j / C, c = j - r * C;
     return blk * B + c * R + min(c, rem) + r;
@@ -41,15 +68,15 @@ __device__ __forceinline__ int layout_slot(int ci, int nt, int B)
 // 2D: cell = k*nx + i; 3D: cell = (k*ny + j)*nx + i. Tiles of T^dims cells, tile-major.
 __device__ __forceinline__ int cell_key(int cell, const KeyGeo& g)
 {
-    const int i = cell % g.nx, q = cell / g.nx;
-    if (g.dims == 2) {
-        const int k = q, tz = k / g.T, tx = i / g.T;
-        return (tz * g.ntx + tx) * g.T * g.T + (k - tz * g.T) * g.T + (i - tx * g.T);
-    }
-    const int j = q % g.ny, k = q / g.ny;
-    const int tx = i / g.T, ty = j / g.T, tz = k / g.T;
+    int i, j = 0, li, lj, lk;
+    const int q = divq(cell, g.dnx, i);
+    int k = q;
+    if (g.dims == 3) k = divq(q, g.dny, j);
+    const int tx = divq(i, g.dT, li), tz = divq(k, g.dT, lk);
+    if (g.dims == 2) return (tz * g.ntx + tx) * g.TT + lk * g.T + li;
+    const int ty = divq(j, g.dT, lj);
     const int tile = (tz * g.nty + ty) * g.ntx + tx;
-    return ((tile * g.T + (k - tz * g.T)) * g.T + (j - ty * g.T)) * g.T + (i - tx * g.T);
+    return ((tile * g.T + lk) * g.T + lj) * g.T + li;
 }
 
 // Count the particles of every key. The sort's block layout stores B cell-ordered particles as a
@@ -155,11 +182,12 @@ __global__ void k_scan_add(int32_t* out, const int32_t* __restrict__ bsum, int n
 // Key of cell (i, j, k) (j = 0 in 2D), as cell_key computes it from the cell index.
 __device__ __forceinline__ int key_of(int i, int j, int k, const KeyGeo& g)
 {
-    const int tx = i / g.T, tz = k / g.T;
-    if (g.dims == 2) return (tz * g.ntx + tx) * g.T * g.T + (k - tz * g.T) * g.T + (i - tx * g.T);
-    const int ty = j / g.T;
+    int li, lj, lk;
+    const int tx = divq(i, g.dT, li), tz = divq(k, g.dT, lk);
+    if (g.dims == 2) return (tz * g.ntx + tx) * g.TT + lk * g.T + li;
+    const int ty = divq(j, g.dT, lj);
     const int tile = (tz * g.nty + ty) * g.ntx + tx;
-    return ((tile * g.T + (k - tz * g.T)) * g.T + (j - ty * g.T)) * g.T + (i - tx * g.T);
+    return ((tile * g.T + lk) * g.T + lj) * g.T + li;
 }
 
 // The largest particle count (of one species) over the blocks of 4 cells per axis (x, y periodic;
@@ -175,9 +203,10 @@ __global__ void k_counts_to_cells(const int32_t* __restrict__ count, KeyGeo kg, 
     const int64_t ncell = (int64_t)kg.nx * kg.ny * nz;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += stride) {
-        const int i = (int)(c % kg.nx);
-        const int64_t q = c / kg.nx;
-        out[c] = count[key_of(i, (int)(q % kg.ny), (int)(q / kg.ny), kg)];
+        int i, j;
+        const int q = divq((int)c, kg.dnx, i);
+        const int k = divq(q, kg.dny, j);
+        out[c] = count[key_of(i, j, k, kg)];
     }
 }
 
@@ -260,9 +289,10 @@ __global__ void k_scatter(SpeciesBuf src, SpeciesBuf dst, int64_t n, KeyGeo kg, 
         base = __shfl_sync(0xffffffffu, base, leader);
         if (!valid) continue;
         // place in the cell order -> storage slot of the tile's block layout
-        const int t = key / kg.TT, ts = tile_start[t];
-        const int q = ts + layout_slot(base + __popc(peers & ((1u << lane) - 1u)) - ts, tile_start[t + 1] - ts,
-                                       kg.dims == 3 ? kLayoutBlock3 : kLayoutBlock2);
+        int kt;
+        const int t = divq(key, kg.dTT, kt), ts = tile_start[t];
+        const int ci = base + __popc(peers & ((1u << lane) - 1u)) - ts, nt = tile_start[t + 1] - ts;
+        const int q = ts + (kg.dims == 3 ? layout_slot<kLayoutBlock3>(ci, nt) : layout_slot<kLayoutBlock2>(ci, nt));
         dst.cell[q] = c;
         dst.fx[q] = src.fx[p];
         if (kg.dims == 3) dst.fy[q] = src.fy[p];
@@ -279,7 +309,8 @@ void sort_species_impl(Ctx& c, int s, cudaStream_t st, int from_b, int64_t* laun
 {
     Species& S = c.sp[s];
     const int TT = c.dims == 3 ? c.T * c.T * c.T : c.T * c.T;
-    const KeyGeo kg = {c.nx, c.ny, c.T, c.ntx, c.nty, c.dims, TT};
+    const KeyGeo kg = {c.nx, c.ny, c.T, c.ntx, c.nty, c.dims, TT, make_div(c.nx), make_div(c.ny), make_div(c.T),
+                       make_div(TT)};
     int64_t g = (S.n + 255) / 256;
     if (g > (int64_t)c.nsm * 16) g = (int64_t)c.nsm * 16;
     if (g < 1) g = 1;
