@@ -226,6 +226,25 @@ PIC_API int pic_cell_temperature(pic_ctx* ctx, int32_t species, double* dev_work
  * Errors: PIC_EINVAL (NULL pointer, species not present, T_from <= 0). */
 PIC_API int pic_set_temperature(pic_ctx* ctx, int32_t species, const double* dev_T, double T_from);
 
+/* Conservative remap of a cell-centred field (a lattice-temperature map) between two grids of
+ * square cells, for the two-stage coupling when the stages use different cells (paper: the
+ * laser-interaction run, on much finer cells than the transport run, hands its lattice
+ * temperature to the transport run). The grids are placed on each other by the slab's surface
+ * and the laser axis: cell (i, j, k) of a grid (nx, ny, nz, dx, surface) spans
+ * x in [(i - nx/2) dx, (i + 1 - nx/2) dx], y likewise with ny (3D), and depth coordinate
+ * [(k - surface) dx, (k + 1 - surface) dx], surface being the first row of cells above the slab
+ * (slab_k). Each destination cell takes the volume-weighted mean of the source cells it
+ * overlaps; the part of it outside the source grid counts as `fill` (the source grid's periodic
+ * x is not continued: its lateral edge is the edge of the laser stage's data). dims: 2 (ny
+ * ignored, index k*nx + i) or 3 (index (k*ny + j)*nx + i). dev_src: double[src cells],
+ * dev_dst: double[dst cells], device pointers, caller-owned, not overlapping. FP64 throughout;
+ * asynchronous on `stream` (a cudaStream_t, NULL for the default stream); allocates nothing.
+ * Errors: PIC_EINVAL (NULL pointers, dims not 2 or 3, an extent below 1, dx <= 0, a surface
+ * outside 0..nz), PIC_ECUDA (launch failure). */
+PIC_API int pic_regrid_cells(int32_t dims, const double* dev_src, int32_t src_nx, int32_t src_ny, int32_t src_nz,
+                             double src_dx, int32_t src_surface, double* dev_dst, int32_t dst_nx, int32_t dst_ny,
+                             int32_t dst_nz, double dst_dx, int32_t dst_surface, double fill, void* stream);
+
 /* Pair-potential force (N, per atom) on every macro-ion from the current node density
  * (paper: Eqs. 1-3, density and gradient interpolated back to the particle). dev_out:
  * device float[3 * num_particles(0)], (Fx, Fy, Fz) per particle, in the context's particle order. */

@@ -143,6 +143,9 @@ def lib():
             "oracle_crater_profile": (None, [vp, _I64, _I64, _D]),
             "oracle_cell_temperature": (None, [vp, ctypes.c_int32, _D]),
             "oracle_set_temperature": (None, [vp, ctypes.c_int32, _D, ctypes.c_double]),
+            "oracle_regrid_cells": (None, [ctypes.c_int32, _D, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_int32, _D, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_double]),
             "oracle3_create": (vp, [ctypes.POINTER(OracleConfig3), ctypes.c_int32]),
             "oracle3_free": (None, [vp]),
             "oracle3_num_particles": (ctypes.c_int64, [vp, ctypes.c_int32]),
@@ -457,6 +460,21 @@ def eam_atom2(phys, n, dnx, dnz, r0_dx):
 def jy_bits(per_cell):
     """Resolution of the J_y code for a 2D slab with per_cell macroparticles per cell (both species)."""
     return lib().oracle_jy_bits(int(per_cell))
+
+
+def regrid_cells(src, src_grid, dst_grid, fill, dims=2):
+    """Conservative remap of a cell map between grids (nx, ny, nz, dx, surface) placed on each other
+    by the slab surface and the laser axis; src of shape (nz, nx) or (nz, ny, nx)."""
+    snx, sny, snz, sdx, ssf = src_grid
+    dnx, dny, dnz, ddx, dsf = dst_grid
+    if dims == 2:
+        sny = dny = 1
+    a = np.ascontiguousarray(src, dtype=np.float64).reshape(-1)
+    assert a.size == snx * sny * snz
+    out = np.empty(dnx * dny * dnz, np.float64)
+    lib().oracle_regrid_cells(dims, _p(a, ctypes.c_double), snx, sny, snz, float(sdx), ssf, _p(out, ctypes.c_double),
+                              dnx, dny, dnz, float(ddx), dsf, float(fill))
+    return out.reshape((dnz, dny, dnx) if dims == 3 else (dnz, dnx))
 
 
 def deposit_density(nx, nz, x, z):

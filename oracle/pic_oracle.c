@@ -975,6 +975,46 @@ void oracle_set_temperature(ostate* s, int32_t sp, const double* T, double T_fro
     }
 }
 
+/* Regridding a cell map between stages on different cells (paper: the laser-interaction run, on
+ * much finer cells than the transport run, hands over its lattice temperature). The grids are
+ * placed on each other by the slab surface and the laser axis: cell (i, j, k) of a grid (nx, ny,
+ * nz, dx, surface) spans x in [(i - nx/2) dx, (i + 1 - nx/2) dx], y likewise (3D) and depth
+ * [(k - surface) dx, (k + 1 - surface) dx]. Each destination cell takes the volume-weighted mean of
+ * the source cells it overlaps, the part of it outside the source grid counting as fill. Written
+ * as that definition: the overlap of every destination cell with every source cell. */
+static double overlap1(double a0, double a1, double b0, double b1)
+{
+    const double lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
+    return hi > lo ? hi - lo : 0.0;
+}
+
+void oracle_regrid_cells(int32_t dims, const double* src, int32_t snx, int32_t sny, int32_t snz, double sdx,
+                         int32_t ssurf, double* dst, int32_t dnx, int32_t dny, int32_t dnz, double ddx, int32_t dsurf,
+                         double fill)
+{
+    if (dims == 2) sny = dny = 1;
+    const double vol = dims == 3 ? ddx * ddx * ddx : ddx * ddx;
+    for (int32_t k = 0; k < dnz; k++)
+        for (int32_t j = 0; j < dny; j++)
+            for (int32_t i = 0; i < dnx; i++) {
+                const double x0 = (i - 0.5 * dnx) * ddx, y0 = (j - 0.5 * dny) * ddx, z0 = (k - dsurf) * ddx;
+                double sum = 0.0, covered = 0.0;
+                for (int32_t sk = 0; sk < snz; sk++)
+                    for (int32_t sj = 0; sj < sny; sj++)
+                        for (int32_t si = 0; si < snx; si++) {
+                            const double bx = (si - 0.5 * snx) * sdx, by = (sj - 0.5 * sny) * sdx,
+                                         bz = (sk - ssurf) * sdx;
+                            double w = overlap1(x0, x0 + ddx, bx, bx + sdx) * overlap1(z0, z0 + ddx, bz, bz + sdx);
+                            if (dims == 3) w *= overlap1(y0, y0 + ddx, by, by + sdx);
+                            if (w > 0.0) {
+                                sum += w * src[((size_t)sk * sny + sj) * snx + si];
+                                covered += w;
+                            }
+                        }
+                dst[((size_t)k * dny + j) * dnx + i] = (sum + fill * (vol - covered)) / vol;
+            }
+}
+
 /* Crater profile (paper: after solidification the crater's width and depth are read off the
  * density map): for every node column i, the material missing from the original slab as a
  * thickness of solid-density material (m): dx * sum over node rows k = 0..slab_k of the density

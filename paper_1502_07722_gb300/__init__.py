@@ -85,6 +85,8 @@ _SIGNATURES = {
     "pic_crater_profile": (ctypes.c_int, [_VP, _VP, _VP]),
     "pic_cell_temperature": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
     "pic_set_temperature": (ctypes.c_int, [_VP, _I32, _VP, ctypes.c_double]),
+    "pic_regrid_cells": (ctypes.c_int, [_I32, _VP, _I32, _I32, _I32, ctypes.c_double, _I32, _VP, _I32, _I32, _I32,
+                                        ctypes.c_double, _I32, ctypes.c_double, _VP]),
     "pic_pair_force_at": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _I32, ctypes.c_double, ctypes.c_double, _VP]),
     "pic_energy": (ctypes.c_int, [_VP, ctypes.POINTER(pic_energy_t)]),
     "pic_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pic_info)]),
@@ -209,6 +211,29 @@ def pic_cell_temperature(h, species: int, dev_work_ptr: int, dev_T_ptr: int):
 
 def pic_set_temperature(h, species: int, dev_T_ptr: int, T_from: float):
     _check(load_library().pic_set_temperature(h, int(species), dev_T_ptr, float(T_from)), "pic_set_temperature")
+
+
+def pic_regrid_cells(dims: int, src_ptr: int, src_grid: tuple, dst_ptr: int, dst_grid: tuple, fill: float,
+                     stream_ptr: int = 0):
+    """src_grid / dst_grid: (nx, ny, nz, dx, surface) of each grid (ny ignored in 2D)."""
+    snx, sny, snz, sdx, ssf = src_grid
+    dnx, dny, dnz, ddx, dsf = dst_grid
+    _check(load_library().pic_regrid_cells(int(dims), src_ptr, int(snx), int(sny), int(snz), float(sdx), int(ssf),
+                                           dst_ptr, int(dnx), int(dny), int(dnz), float(ddx), int(dsf), float(fill),
+                                           stream_ptr or None), "pic_regrid_cells")
+
+
+def regrid_cells(src, src_grid: tuple, dst_grid: tuple, fill: float, dims: int = 2):
+    """Conservative remap of a cell map (a CUDA float64 tensor of shape (nz, nx) or (nz, ny, nx))
+    from src_grid onto dst_grid, both (nx, ny, nz, dx, surface); returns a new tensor on the
+    current stream (see pic_regrid_cells)."""
+    import torch
+    src = torch.as_tensor(src, dtype=torch.float64).cuda().contiguous()
+    dnx, dny, dnz = dst_grid[0], dst_grid[1], dst_grid[2]
+    out = torch.empty((dnz, dny, dnx) if dims == 3 else (dnz, dnx), dtype=torch.float64, device="cuda")
+    pic_regrid_cells(dims, src.data_ptr(), src_grid, out.data_ptr(), dst_grid, fill,
+                     torch.cuda.current_stream().cuda_stream)
+    return out
 
 
 def pic_energy(h) -> dict:
@@ -410,6 +435,11 @@ class Simulation:
 
     def _cells(self):
         return (self.nz, self.ny, self.nx) if self.dims == 3 else (self.nz, self.nx)
+
+    def cell_grid(self):
+        """(nx, ny, nz, dx, surface) of the context's cells (surface: the first row above the slab),
+        the grid description regrid_cells takes."""
+        return (self.nx, self.ny, self.nz, self.cfg.dx, self.cfg.slab_k)
 
     def cell_temperature(self, species):
         """Lattice temperature (K) of a species per cell, about each cell's mean flow."""

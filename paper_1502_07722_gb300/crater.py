@@ -185,17 +185,23 @@ def calibrate_c_att(sim, z_from: int = None, z_to: int = None, order: int = 8, l
 
 def transport_from_laser(laser, transport_phys: dict):
     """Second stage of the two-stage run (paper: the atomic-transport run starts from the lattice
-    temperature the laser-interaction run leaves): a transport context on the same grid whose
-    atoms, drawn at the transport start temperature T_ion_K, are re-tempered to the ion temperature
-    of `laser` cell by cell (cells the laser stage leaves colder or without ions keep T_ion_K)."""
+    temperature the laser-interaction run leaves): a transport context whose atoms, drawn at the
+    transport start temperature T_ion_K, are re-tempered to the ion temperature of `laser` cell by
+    cell (cells the laser stage leaves colder or without ions keep T_ion_K). The transport grid may
+    differ from the laser stage's (the paper's laser stage uses much finer cells): the temperature
+    map is then remapped conservatively onto it, the grids placed on each other by the slab surface
+    and the laser axis, with T_ion_K where the laser stage has no cells (regrid_cells)."""
     import torch
 
-    from . import Simulation
-    assert (laser.nx, laser.nz, laser.dims) == (transport_phys["nx"], transport_phys["nz"],
-                                                 3 if transport_phys.get("dims") == 3 else 2)
+    from . import Simulation, regrid_cells
+    dims = 3 if transport_phys.get("dims") == 3 else 2
+    assert laser.dims == dims
     T_from = float(transport_phys["T_ion_K"])
     T = torch.clamp(laser.cell_temperature(0), min=T_from)
     tr = Simulation(transport_phys)
+    if laser.cell_grid() != tr.cell_grid():
+        T = regrid_cells(T, laser.cell_grid(), tr.cell_grid(), T_from, dims=dims)
+        torch.cuda.current_stream().synchronize()
     tr.set_temperature(0, T, T_from)
     return tr
 

@@ -355,3 +355,62 @@ def test_new_entry_points_refuse_bad_arguments(gb):
         gb.pic_pair_force_at(s3.h, 1, idx.data_ptr(), half.data_ptr(), half.data_ptr(), 0, 1.0, 1.0, out.data_ptr())
     assert e.value.code == gb.PIC_ESTATE
     s3.close()
+
+
+@pytest.mark.parametrize("dims, src, dst", [
+    (2, (48, 1, 40, 10e-9, 20), (32, 1, 27, 15e-9, 13)),        # coarser, non-integer ratio
+    (2, (30, 1, 24, 15e-9, 12), (67, 1, 50, 6.5e-9, 29)),       # finer and wider than the source
+    (2, (16, 1, 12, 10e-9, 6), (16, 1, 12, 10e-9, 6)),          # the same grid
+    (3, (14, 12, 16, 10e-9, 8), (9, 8, 11, 16e-9, 5)),
+    (3, (9, 8, 11, 16e-9, 5), (20, 17, 25, 7e-9, 12)),
+], ids=["2d-coarser", "2d-finer", "2d-same", "3d-coarser", "3d-finer"])
+def test_regrid_matches_oracle(gb, dims, src, dst):
+    """The conservative remap of a cell map between grids placed on each other by the slab surface
+    and the laser axis, on the GPU against the oracle's definition (FP64 on both sides: 1e-12)."""
+    import torch
+    rng = np.random.default_rng(11)
+    shape = (src[2], src[1], src[0]) if dims == 3 else (src[2], src[0])
+    a = rng.uniform(300.0, 8000.0, shape)
+    out = gb.regrid_cells(torch.tensor(a, device="cuda"), src, dst, 300.0, dims=dims)
+    torch.cuda.synchronize()
+    ref = oracle.regrid_cells(a, src, dst, 300.0, dims=dims)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12)
+    dev = torch.zeros(8, dtype=torch.float64, device="cuda")
+    for bad in (dict(dims=4), dict(src=(4, 1, 2, 0.0, 1)), dict(src=(4, 1, 2, 1.0, 3)), dict(dst=(0, 1, 2, 1.0, 1))):
+        args = dict(dims=2, src=(4, 1, 2, 1.0, 1), dst=(4, 1, 2, 1.0, 1))
+        args.update(bad)
+        with pytest.raises(gb.PicError) as e:
+            gb.pic_regrid_cells(args["dims"], dev.data_ptr(), args["src"], dev.data_ptr(), args["dst"], 0.0)
+        assert e.value.code == gb.PIC_EINVAL
+
+
+def test_two_stage_start_on_coarser_cells_matches_oracle(gb):
+    """The transport stage on cells 1.5 times the laser stage's (the paper's stages use different
+    cells): its atoms are re-tempered to the laser stage's ion temperature remapped onto its own
+    grid; against the oracle's remap of the same map and re-tempering of the same draws (FP32 of
+    one FP64 multiply: 1 ulp)."""
+    from paper_1502_07722_gb300 import crater
+    w, las = _laser_stage(gb)
+    tw = dict(workload("transport"), nx=32, nz=27, slab_k=13, dx=1.5 * w["dx"], ppc_ion=12, T_ion_K=300.0)
+    cold = gb.Simulation(tw)
+    before = _host(cold, 0)
+    cold.close()
+    Tl = np.maximum(las.cell_temperature(0).cpu().numpy(), 300.0)
+    tr = crater.transport_from_laser(las, tw)
+    assert las.cell_grid() != tr.cell_grid()
+    Tmap = oracle.regrid_cells(Tl, las.cell_grid(), tr.cell_grid(), 300.0)
+    assert Tmap.shape == (27, 32) and Tmap.max() > 400.0       # the laser-heated cells arrive
+    after = _host(tr, 0)
+    ka = np.lexsort((after["fz"], after["fx"], after["cell"]))
+    kb = np.lexsort((before["fz"], before["fx"], before["cell"]))
+    for k in ("cell", "fx", "fz"):
+        assert np.array_equal(after[k][ka], before[k][kb])
+    orc = _oracle_from(tw, [before])
+    orc.set_temperature(0, Tmap, 300.0)
+    o = orc.get_particles(0)
+    for k in ("ux", "uy", "uz"):
+        ref = o[k].astype(np.float32)[kb]
+        np.testing.assert_allclose(after[k][ka], ref, rtol=2 ** -23, atol=0)
+    tr.close()
+    las.close()
+
