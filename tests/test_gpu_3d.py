@@ -141,6 +141,36 @@ def test_one_step3_full(gb, seed, tile):
         np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
 
 
+@pytest.mark.parametrize("pot", [dict(pot_mode=2, morse_a=4.0), dict(lattice=1), dict(pot_mode=3)],
+                         ids=["morse", "hcp", "eam"])
+def test_one_step3_transport_variants_compiled_window(gb, pot):
+    """One 3D transport step of each potential and lattice variant with 10-cell tiles, the kernel
+    instances that have the 13-node window edge compiled in (ragged tiles: 14 x 12 x 16 cells):
+    atoms to 1e-5 of the oracle and the node density bit-exact against the oracle's deposit of the
+    GPU's own move."""
+    nx, ny, nz = 14, 12, 16
+    w = w3(max_particles=6000, sort_every=0, tile=10, mode=1, ion_charge=0.0, ppc_electron=0, laser_profile=0,
+           dt_override=12e-15, T_ion_K=3000.0, **pot)
+    sim = gb.Simulation(w)
+    orc = oracle.Oracle3D(w, with_particles=False)
+    # the workload's own start (lattice slab at 3000 K), handed to the oracle as it stands
+    x, y, z, u = to_global3(sim.get_particles(0), nx, ny)
+    g0 = set_both3(sim, orc, 0, x, y, z, u)
+    sim.step(1)
+    orc.step(1)
+    X1, Y1, Z1, U1 = to_global3(sim.get_particles(0), nx, ny)
+    X0, Y0, Z0, _ = to_global3(g0, nx, ny)
+    o = orc.get_particles(0)
+    for a, b, a0 in ((X1, o["x"], X0), (Y1, o["y"], Y0)):
+        d = np.abs(np.mod(a - b + nx / 2, nx) - nx / 2)
+        disp = np.abs(np.mod(b - a0 + nx / 2, nx) - nx / 2)
+        assert (d <= 1e-5 * disp + 2.0 ** -22).all()
+    assert (np.abs(Z1 - o["z"]) <= 1e-5 * np.abs(o["z"] - Z0) + 2.0 ** -22).all()
+    for c, key in enumerate(("ux", "uy", "uz")):
+        np.testing.assert_allclose(U1[c], o[key], rtol=1e-5, atol=1e-5 * np.abs(o[key]).max())
+    assert np.array_equal(sim.get_density().cpu().numpy(), oracle.deposit_density3(nx, ny, nz, X1, Y1, Z1))
+
+
 def test_energy3_matches_oracle(gb):
     w = w3()
     sim = gb.Simulation(w)

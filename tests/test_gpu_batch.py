@@ -62,7 +62,8 @@ def _state(sim):
 
 
 @pytest.mark.parametrize("timing,pot", [(False, {}), (True, {}), (False, dict(pot_mode=2, morse_a=3.0)),
-                                        (False, dict(lattice=1))], ids=["graph", "timing", "morse", "hcp"])
+                                        (False, dict(lattice=1)), (False, dict(pot_mode=3))],
+                         ids=["graph", "timing", "morse", "hcp", "eam"])
 def test_batch_equals_single_runs(gb, timing, pot):
     """Every slab of a batch ends with the same grids (bit for bit) and the same particles as the
     same slab run alone (graph replay and the direct-launch timing path alike, and with the Morse
