@@ -91,14 +91,18 @@ def test_density3_and_pair_force(gb, pot):
     assert (np.abs(Fg - Fo) <= 1e-5 * np.abs(Fo) + 1e-5 * scale).all()
 
 
-@pytest.mark.parametrize("seed,tile", [(3, 4), (4, 4), (5, 10), (6, 16)])
-def test_one_step3_full(gb, seed, tile):
+@pytest.mark.parametrize("seed,tile,pot", [(3, 4, {}), (4, 4, {}), (5, 10, {}), (6, 16, {}),
+                                           (7, 10, dict(pot_mode=2, morse_a=4.0)), (8, 10, dict(lattice=1)),
+                                           (9, 10, dict(pot_mode=3))],
+                         ids=["t4a", "t4b", "t10", "t16", "t10-morse", "t10-hcp", "t10-eam"])
+def test_one_step3_full(gb, seed, tile, pot):
     """One 3D cycle: particles to 1e-5, current and node density bit-exact against the oracle's
     deposition of the GPU's own move, fields against the oracle's Maxwell update. Tile 4: several
-    tiles with staged windows; tile 10: ragged tiles (14 x 12 x 16 cells); tile 16: the window is
-    too large to stage, every gather and deposit takes the global path."""
+    tiles with staged windows; tile 10: ragged tiles (14 x 12 x 16 cells) and the kernel instances
+    with the window edge compiled in, for every potential and lattice variant; tile 16: the window
+    is too large to stage, every gather and deposit takes the global path."""
     nx, ny, nz = 14, 12, 16
-    w = w3(max_particles=6000, sort_every=0, tile=tile)
+    w = w3(max_particles=6000, sort_every=0, tile=tile, **pot)
     sim = gb.Simulation(w)
     orc = oracle.Oracle3D(w, with_particles=False)
     g0 = []
