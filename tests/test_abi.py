@@ -113,3 +113,24 @@ def test_fixed_point_range_is_checked_at_sizing(lib):
     assert size(dict(workload("tiny"), ppc_ion=900, ppc_electron=900)) == 0
     assert size(dict(workload("tiny", nx=4, nz=4, slab_k=1), ppc_ion=6_000_000, ppc_electron=6_000_000)) == \
         gb.PIC_EOVERFLOW
+
+
+def test_regrid_refuses_bad_grids_before_any_cuda_call(lib):
+    """pic_regrid_cells checks its arguments on the host: NULL pointers, dims other than 2 or 3,
+    empty extents, non-positive cell sizes and surfaces outside 0..nz give PIC_EINVAL without a
+    launch (the pointers below are never dereferenced)."""
+    fake = ctypes.c_void_p(256)
+    good = (8, 1, 6, 1e-8, 3)
+
+    def call(dims=2, src=good, dst=good, s=fake, d=fake):
+        return lib.pic_regrid_cells(dims, s, src[0], src[1], src[2], ctypes.c_double(src[3]), src[4], d, dst[0],
+                                    dst[1], dst[2], ctypes.c_double(dst[3]), dst[4], ctypes.c_double(300.0), None)
+    assert call(s=None) == gb.PIC_EINVAL
+    assert call(d=None) == gb.PIC_EINVAL
+    assert call(dims=1) == gb.PIC_EINVAL and call(dims=4) == gb.PIC_EINVAL
+    assert call(src=(0, 1, 6, 1e-8, 3)) == gb.PIC_EINVAL
+    assert call(dst=(8, 1, 0, 1e-8, 0)) == gb.PIC_EINVAL
+    assert call(dims=3, src=(8, 0, 6, 1e-8, 3)) == gb.PIC_EINVAL
+    assert call(src=(8, 1, 6, 0.0, 3)) == gb.PIC_EINVAL and call(dst=(8, 1, 6, -1e-8, 3)) == gb.PIC_EINVAL
+    assert call(src=(8, 1, 6, 1e-8, 7)) == gb.PIC_EINVAL and call(dst=(8, 1, 6, 1e-8, -1)) == gb.PIC_EINVAL
+
