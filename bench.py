@@ -64,16 +64,18 @@ def peaks():
 
 
 def kernel_traffic(dims=2):
-    """DRAM bytes per launch of the particle kernel (2D or 3D) from a committed ncu summary, if the
-    kernel source has not changed since it was taken (else None)."""
-    path = os.path.join(ROOT, "profiles", "particle_kernel_traffic.json" if dims == 2 else
-                        "particle_kernel3_traffic.json")
+    """DRAM bytes per launch of the particle kernel (2D, 3D, or "batch" for the batched sweep) from a
+    committed ncu summary, if the kernel source has not changed since it was taken (else None)."""
+    record = {2: "particle_kernel_traffic.json", 3: "particle_kernel3_traffic.json",
+              "batch": "particle_kernel_batch_traffic.json"}[dims]
+    path = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     h = hashlib.sha256()
-    for name in ("particles.cu" if dims == 2 else "pic3d.cu", "pic_device.cuh", "pic_internal.cuh"):
+    sources = {2: ("particles.cu",), 3: ("pic3d.cu",), "batch": ("particles.cu", "batch.cu")}[dims]
+    for name in sources + ("pic_device.cuh", "pic_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1502_07722_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     if d.get("source_sha256") != h.hexdigest():
@@ -240,6 +242,8 @@ def run_batched(args, world, rank, dist, gb):
     k_ms = kms[0] / max(kn[0], 1)
     peak, peak_kind = peaks()
     alg = BYTES_PER_PARTICLE * n_local + BYTES_PER_NODE * nodes
+    tr = kernel_traffic("batch")
+    traffic = tr["dram_bytes_per_launch"] if tr is not None and tr.get("workload") == "batched" else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": n_local * world * args.steps / (ms_max * 1e-3), "unit": UNIT,
@@ -253,7 +257,7 @@ def run_batched(args, world, rank, dist, gb):
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (BYTES_PER_PARTICLE / 2 * n_local / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": alg / (k_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": alg / (k_ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "k_particles_batch",
+                         "frac": alg / (k_ms * 1e-3) / 1e9 / peak, "traffic": traffic, "kernel": "k_particles_batch",
                          "peak_source": peak_kind, "kernel_ms": k_ms, "alg_bytes_per_launch": alg},
             "kernel_ms_per_step": {"particles": k_ms, "fields": kms[1] / nt, "sort": kms[2] / nt},
             "gpu_launches": 8 * args.steps,
